@@ -1,0 +1,206 @@
+"""ctypes binding of the FP64 CPU oracle (test infrastructure only).
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg import this
+module.  It builds oracle/liborc.so on first use.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_D = C.c_double
+_I = C.c_int32
+_L = C.c_int64
+_P = C.c_void_p
+
+
+class OrcParams(C.Structure):
+    _fields_ = [
+        ("E", _D), ("poisson", _D), ("restitution", _D), ("friction", _D),
+        ("rho_f", _D), ("nu_f", _D), ("g", _D * 3),
+        ("lo", _D * 3), ("hi", _D * 3),
+        ("periodic", _I * 3), ("wall_lo", _I * 3), ("wall_hi", _I * 3),
+        ("dt", _D),
+        ("lubrication", _I), ("drag", _I), ("pressure_grad", _I), ("added_mass", _I),
+        ("lub_h_in_frac", _D), ("lub_h_out_frac", _D), ("c_add", _D), ("eps_max", _D),
+        ("ncell", _I * 3),
+        ("bandwidth", _D * 3), ("n_tau", _I), ("cg_rtol", _D), ("cg_max_iter", _I),
+        ("shift_eps", _I), ("shift_mom", _I), ("shift_force", _I),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.orc_create.restype = _P
+        L.orc_create.argtypes = [C.POINTER(OrcParams)]
+        L.orc_destroy.argtypes = [_P]
+        for name, args in {
+            "orc_set_particles": [_P, _L, _P, _P, _P, _P, _P],
+            "orc_set_accel": [_P, _P],
+            "orc_set_fluid": [_P, _P, _P, _P],
+            "orc_set_eps": [_P, _P],
+            "orc_step": [_P, _I],
+            "orc_forces": [_P, _P, _P, _P, _P],
+            "orc_get_particles": [_P, _P, _P, _P, _P],
+            "orc_get_contacts": [_P, _L, _P, _P],
+            "orc_get_wall_history": [_P, _P],
+            "orc_deposit": [_P, _P],
+            "orc_smooth": [_P, _I, _P, _P, _P],
+            "orc_average": [_P, _P, _P, _P],
+        }.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.orc_num_contacts.argtypes = [_P]
+        L.orc_num_contacts.restype = _L
+        L.orc_neighbors.argtypes = [_P, _D, _I, _P, _P, _L]
+        L.orc_neighbors.restype = _L
+        L.orc_drag.argtypes = [C.POINTER(OrcParams), _D, _P, _D, _P, _P, _P]
+        L.orc_drag.restype = None
+        L.orc_vr.argtypes = [_D, _D]
+        L.orc_vr.restype = _D
+        _lib = L
+    return _lib
+
+
+def make_params(prm: dict) -> OrcParams:
+    """Fill the oracle's own parameter struct from a plain dict of physical inputs."""
+    p = OrcParams()
+    for name, ctype in OrcParams._fields_:
+        if name not in prm:
+            raise KeyError(f"oracle parameter {name!r} missing")
+        val = prm[name]
+        if hasattr(ctype, "_length_"):
+            setattr(p, name, ctype(*val))
+        else:
+            setattr(p, name, val)
+    return p
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _f64(a, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+class Oracle:
+    """One oracle instance: particles, fluid fields and contact history."""
+
+    def __init__(self, prm: dict):
+        self.prm = dict(prm)
+        self._p = make_params(prm)
+        self.C = int(np.prod(prm["ncell"]))
+        self.h = lib().orc_create(C.byref(self._p))
+        self.n = 0
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_destroy(self.h)
+            self.h = None
+
+    def set_particles(self, x, v, w, d, rho):
+        x = _f64(x, (-1, 3)); n = x.shape[0]
+        v = _f64(v, (n, 3)); w = _f64(w, (n, 3))
+        d = _f64(d, (n,)); rho = _f64(rho, (n,))
+        self.n = n
+        self._keep = (x, v, w, d, rho)
+        assert lib().orc_set_particles(self.h, n, _ptr(x), _ptr(v), _ptr(w), _ptr(d), _ptr(rho)) == 0
+
+    def set_accel(self, a):
+        a = _f64(a, (self.n, 3))
+        lib().orc_set_accel(self.h, _ptr(a))
+
+    def set_fluid(self, U=None, grad_p=None, DUDt=None):
+        U = _f64(U, (self.C, 3)); gp = _f64(grad_p, (self.C, 3)); du = _f64(DUDt, (self.C, 3))
+        lib().orc_set_fluid(self.h, _ptr(U), _ptr(gp), _ptr(du))
+
+    def set_eps(self, eps):
+        e = _f64(eps, (self.C,))
+        lib().orc_set_eps(self.h, _ptr(e))
+
+    def step(self, n_sub=1):
+        assert lib().orc_step(self.h, int(n_sub)) == 0
+
+    def forces(self):
+        out = {k: np.zeros((self.n, 3)) for k in ("contact", "lub", "fluid", "torque")}
+        lib().orc_forces(self.h, _ptr(out["contact"]), _ptr(out["lub"]), _ptr(out["fluid"]),
+                         _ptr(out["torque"]))
+        return out
+
+    def get_particles(self):
+        x, v, w, a = (np.zeros((self.n, 3)) for _ in range(4))
+        lib().orc_get_particles(self.h, _ptr(x), _ptr(v), _ptr(w), _ptr(a))
+        return x, v, w, a
+
+    def contacts(self):
+        m = lib().orc_num_contacts(self.h)
+        ij = np.zeros((m, 2), dtype=np.int64); xi = np.zeros((m, 3))
+        if m:
+            assert lib().orc_get_contacts(self.h, m, _ptr(ij), _ptr(xi)) == 0
+        return ij, xi
+
+    def wall_history(self):
+        xw = np.zeros((self.n, 6, 3))
+        lib().orc_get_wall_history(self.h, _ptr(xw))
+        return xw
+
+    def neighbors(self, skin, brute=True):
+        cap = max(64, self.n * 64)
+        while True:
+            off = np.zeros(self.n + 1, dtype=np.int64); idx = np.zeros(cap, dtype=np.int64)
+            tot = lib().orc_neighbors(self.h, float(skin), int(bool(brute)), _ptr(off), _ptr(idx), cap)
+            if tot >= 0:
+                return off, idx[:tot]
+            cap *= 4
+
+    def deposit(self):
+        q = np.zeros((7, self.C), dtype=np.int64)
+        st = lib().orc_deposit(self.h, _ptr(q))
+        if st:
+            raise RuntimeError(f"oracle deposit failed ({st})")
+        return q
+
+    def smooth(self, phi, guess=None, check=True):
+        phi = np.array(phi, dtype=np.float64, copy=True).reshape(-1, self.C)
+        nf = phi.shape[0]
+        g = _f64(guess, (nf, self.C))
+        iters = np.zeros(nf, dtype=np.int32)
+        st = lib().orc_smooth(self.h, nf, _ptr(phi), _ptr(g), _ptr(iters))
+        if st and check:
+            raise RuntimeError(f"oracle smoothing did not converge ({st})")
+        return phi, iters
+
+    def average(self):
+        eps = np.zeros(self.C); Us = np.zeros((self.C, 3)); F = np.zeros((self.C, 3))
+        st = lib().orc_average(self.h, _ptr(eps), _ptr(Us), _ptr(F))
+        if st:
+            raise RuntimeError(f"oracle average failed ({st})")
+        return eps, Us, F
+
+
+def drag(prm: dict, eps_s, w, d):
+    """Single-particle drag of the oracle: (force, V_r, C_d |w|)."""
+    p = make_params(prm)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    f = np.zeros(3); vr = C.c_double(); cdw = C.c_double()
+    lib().orc_drag(C.byref(p), float(eps_s), _ptr(w), float(d), _ptr(f), C.byref(vr), C.byref(cdw))
+    return f, vr.value, cdw.value
+
+
+def vr(eps_f, Re):
+    return lib().orc_vr(float(eps_f), float(Re))

@@ -1,0 +1,107 @@
+/*
+ * FP64 CPU oracle for the particle-side hot path of the SediFoam CFD-DEM method
+ * (Sun & Xiao, "SediFoam: a general-purpose, open-source CFD-DEM solver for
+ * particle-laden flow with emphasis on sediment transport", arXiv 1601.03801).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code is the plain, slow, obviously correct
+ * restatement of the method that the CUDA library is checked against.  Only the
+ * test-suite, the smoke check and the CPU-baseline leg of the benchmark may load
+ * it.  It shares no header, helper, table or constant with the CUDA library.
+ *
+ * Everything here is IEEE binary64, evaluated in source order; the build passes
+ * -ffp-contract=off so no multiply-add is fused.
+ *
+ * Sections of the paper followed:
+ *   Sec. 2.1, Eq. (1a)-(1b)  Newton's equations for translation and rotation
+ *   Sec. 2.3, Eq. (3)-(6)    drag (Syamlal-O'Brien correlation)
+ *   Sec. 2.3, Eq. (8)        added mass (explicit, lagged particle acceleration)
+ *   Sec. 2.4, Eq. (9)-(10)   PCM deposition and diffusion smoothing
+ *   Sec. 2.5                 link-cell neighbour search, soft-sphere contact,
+ *                            Ball-Melrose lubrication, rotation from torques
+ * The readings of garbled or silent passages are listed beside each routine.
+ */
+#pragma once
+#include <cstdint>
+
+extern "C" {
+
+/* Parameters of one oracle instance (all SI units). */
+typedef struct {
+  /* contact material (particles and walls share it) */
+  double E, poisson, restitution, friction;
+  /* fluid */
+  double rho_f, nu_f, g[3];
+  /* box: axis a spans [lo[a], hi[a]); periodic axes wrap, others may carry walls */
+  double lo[3], hi[3];
+  int32_t periodic[3], wall_lo[3], wall_hi[3];
+  /* time step of one DEM substep */
+  double dt;
+  /* force switches */
+  int32_t lubrication, drag, pressure_grad, added_mass;
+  double lub_h_in_frac, lub_h_out_frac; /* fractions of the pair-mean diameter */
+  double c_add;                         /* added-mass coefficient, 0.5 in Sec. 2.3 */
+  double eps_max;                       /* clamp of the solid fraction seen by drag */
+  /* Eulerian mesh (uniform, cell-centred, x fastest) covering the box */
+  int32_t ncell[3];
+  /* averaging: Gaussian bandwidth per axis, pseudo-time steps, CG control */
+  double bandwidth[3];
+  int32_t n_tau;
+  double cg_rtol;
+  int32_t cg_max_iter;
+  /* fixed-point exponents of the deposited fields: solid fraction,
+     momentum (eps*U) and force density */
+  int32_t shift_eps, shift_mom, shift_force;
+} orc_params;
+
+typedef struct orc_handle orc_handle;
+
+orc_handle* orc_create(const orc_params* p);
+void orc_destroy(orc_handle* h);
+
+/* Particles: n, row-major n*3 arrays.  d = diameter, rho = density.
+   v is the velocity at the half step behind the positions (leapfrog). */
+int orc_set_particles(orc_handle* h, int64_t n, const double* x, const double* v,
+                      const double* w, const double* d, const double* rho);
+/* Optional lagged acceleration (n*3) used by the added-mass force. */
+int orc_set_accel(orc_handle* h, const double* a_prev);
+/* Fluid fields, C*3 row-major; NULL grad_p => rho_f*g (hydrostatic); NULL DUDt => 0. */
+int orc_set_fluid(orc_handle* h, const double* U, const double* grad_p, const double* DUDt);
+/* Smoothed solid fraction (C) seen by the drag law. */
+int orc_set_eps(orc_handle* h, const double* eps);
+
+/* Advance n_sub substeps (contact, lubrication, fluid forces, leapfrog). */
+int orc_step(orc_handle* h, int32_t n_sub);
+/* Forces at the current state, without advancing: each n*3 (NULL to skip). */
+int orc_forces(orc_handle* h, double* f_contact, double* f_lub, double* f_fluid,
+               double* torque);
+int orc_get_particles(orc_handle* h, double* x, double* v, double* w, double* a_prev);
+
+/* Tangential history: number of pairs in contact, and (i, j, xi[3]) for each,
+   i < j by particle index.  Wall histories: n*6*3 (walls lo x, hi x, lo y, ...). */
+int64_t orc_num_contacts(orc_handle* h);
+int orc_get_contacts(orc_handle* h, int64_t cap, int64_t* ij, double* xi);
+int orc_get_wall_history(orc_handle* h, double* xi_wall);
+
+/* Neighbour lists: every j != i with |x_j - x_i|^2 < (r_i + r_j + h_out + skin)^2.
+   offsets has n+1 entries; idx receives sorted j per i.  Returns the total count,
+   or -1 if cap is too small.  brute = 1: O(N^2) all pairs; 0: link-cell bins. */
+int64_t orc_neighbors(orc_handle* h, double skin, int32_t brute, int64_t* offsets,
+                      int64_t* idx, int64_t cap);
+
+/* PCM deposition into 7 int64 fixed-point fields [7][C]:
+   eps, eps*U (3), force density on the fluid (3). */
+int orc_deposit(orc_handle* h, int64_t* q);
+/* Diffusion smoothing of nf fields [nf][C] in place.  guess (nf*C or NULL) is an
+   initial guess for the first pseudo-step, projected onto the conserved sum.
+   iters receives the CG iterations per field, summed over pseudo-steps. */
+int orc_smooth(orc_handle* h, int32_t nf, double* phi, const double* guess, int32_t* iters);
+/* Deposition + smoothing; eps (C), Us (C*3), Ffp (C*3), any may be NULL.  The
+   smoothed solid fraction becomes the one the drag law sees. */
+int orc_average(orc_handle* h, double* eps, double* Us, double* Ffp);
+
+/* Single-particle helpers used by the pins. */
+void orc_drag(const orc_params* p, double eps_s, const double w[3], double d,
+              double out_f[3], double* Vr, double* Cd_times_w);
+double orc_vr(double eps_f, double Re);
+
+}  /* extern "C" */

@@ -1,0 +1,88 @@
+/* Internal declarations of the FP64 oracle (test infrastructure only). */
+#pragma once
+#include "orc.h"
+#include <cmath>
+#include <map>
+#include <utility>
+#include <vector>
+
+namespace orc {
+
+struct V3 {
+  double x, y, z;
+};
+inline V3 v3(double x, double y, double z) { return V3{x, y, z}; }
+inline V3 add(V3 a, V3 b) { return V3{a.x + b.x, a.y + b.y, a.z + b.z}; }
+inline V3 sub(V3 a, V3 b) { return V3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+inline V3 scl(double s, V3 a) { return V3{s * a.x, s * a.y, s * a.z}; }
+inline double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+inline double norm(V3 a) { return std::sqrt(dot(a, a)); }
+inline V3 cross(V3 a, V3 b) {
+  return V3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+inline V3 load(const double* p, int64_t i) { return V3{p[3 * i], p[3 * i + 1], p[3 * i + 2]}; }
+inline void store(double* p, int64_t i, V3 a) {
+  p[3 * i] = a.x;
+  p[3 * i + 1] = a.y;
+  p[3 * i + 2] = a.z;
+}
+inline double comp(V3 a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : a.z); }
+inline void set_comp(V3& a, int k, double s) {
+  if (k == 0) a.x = s; else if (k == 1) a.y = s; else a.z = s;
+}
+
+/* Minimum-image difference x_j - x_i on periodic axes (positions are kept in
+   [lo, hi), so one shift of the box length is enough). */
+V3 min_image(const orc_params& p, V3 xi, V3 xj);
+
+/* Result of one contact evaluation for the body "a" of a pair (a, b). */
+struct ContactOut {
+  V3 F;       /* normal + tangential contact force on a */
+  V3 Ta, Tb;  /* contact torques on a and on b */
+  V3 xi;      /* updated tangential spring */
+  bool active;
+};
+
+/* Hertz-Mindlin pair: dx = x_b - x_a (minimum image). */
+ContactOut hm_pair(const orc_params& p, V3 dx, double ra, double rb, double ma, double mb,
+                   V3 va, V3 vb, V3 wa, V3 wb, V3 xi_old);
+/* Hertz-Mindlin sphere-plane: n is the unit normal from the centre towards the
+   wall, dist the centre-to-plane distance. */
+ContactOut hm_wall(const orc_params& p, V3 n, double dist, double r, double m, V3 v, V3 w,
+                   V3 xi_old);
+/* Ball-Melrose normal lubrication on a for the pair (a, b). */
+V3 lub_pair(const orc_params& p, V3 dx, double ra, double rb, V3 va, V3 vb);
+V3 lub_wall(const orc_params& p, V3 n, double dist, double r, V3 v);
+
+/* Fluid-particle force at one particle (Sec. 2.3). */
+struct FluidFields {
+  const std::vector<double>* U;     /* C*3 */
+  const std::vector<double>* gradp; /* C*3 */
+  const std::vector<double>* DUDt;  /* C*3 */
+  const std::vector<double>* eps;   /* C */
+};
+double interp_scalar(const orc_params& p, const std::vector<double>& f, int ncomp, int comp,
+                     V3 x);
+V3 fluid_force(const orc_params& p, const FluidFields& ff, V3 x, V3 u, V3 a_prev, double d);
+V3 drag_force(const orc_params& p, double eps_s, V3 w, double d, double* Vr_out,
+              double* Cdw_out);
+
+/* Pairs (i < j) with |x_j - x_i| < r_i + r_j + extra(i, j). */
+void find_pairs(const orc_params& p, const std::vector<V3>& x, const std::vector<double>& r,
+                double h_out_frac, double skin, bool brute,
+                std::vector<std::pair<int64_t, int64_t>>& out);
+
+}  // namespace orc
+
+struct orc_handle {
+  orc_params p;
+  int64_t n = 0;
+  std::vector<orc::V3> x, v, w, a_prev;
+  std::vector<double> d, rho;
+  /* tangential spring of each pair in contact, keyed by (i, j) with i < j */
+  std::map<std::pair<int64_t, int64_t>, orc::V3> hist;
+  /* tangential spring of each particle against each of the six walls */
+  std::vector<orc::V3> whist; /* n*6 */
+  std::vector<double> U, gradp, DUDt, eps;
+  int64_t ncells() const { return (int64_t)p.ncell[0] * p.ncell[1] * p.ncell[2]; }
+};

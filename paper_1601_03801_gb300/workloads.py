@@ -1,0 +1,296 @@
+"""Seeded synthetic inputs for the particle-side hot path.
+
+This module only draws particles, diameters, velocities and prescribed fluid
+fields; it holds none of the method's arithmetic (no contact law, drag,
+deposition or smoothing).  The CUDA library and the FP64 oracle both consume
+what it returns.
+
+Workloads (the paper's Case 1 and Case 3 / sediment-transport scaling shapes,
+Sec. 3.1, 3.3 and 4.2, Table 1; every one is synthetic):
+
+* ``small``  : 1,000 glass spheres, d = 1 mm, in a 20 x 20 x 40 mm box, periodic
+  in x and y, walls at z = 0 and z = 40 mm, quiescent water, 10 x 10 x 20 mesh.
+* ``bed``    : 200,000 lognormal spheres (median 0.5 mm, sigma_ln = 0.1, cut at
+  +-3 sigma) packed into a bed in a periodic 64 x 32 x 64 mm channel with a wall
+  at z = 0, log-law flow u* = 0.02 m/s, 64 x 32 x 64 mesh.
+* ``large``  : 10,000,000 spheres, d ~ U[0.4, 0.6] mm, 400 x 200 x 100 mm,
+  256 x 128 x 64 mesh, mean flow 0.3 m/s plus filtered noise of rms 0.03 m/s.
+
+Beds are made without any dynamics: a periodic block is seeded on an FCC
+lattice, overlaps are removed by repeated geometric projection (each
+overlapping pair is pushed apart along its centre line, the wall pushes up),
+and the block is tiled over the channel.
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+G = 9.81
+
+
+def default_params(**over) -> dict:
+    """Physical inputs shared by the CUDA library binding and the oracle."""
+    p = dict(
+        E=1.0e7, poisson=0.3, restitution=0.9, friction=0.3,
+        rho_f=1000.0, nu_f=1.0e-6, g=(0.0, 0.0, -G),
+        lo=(0.0, 0.0, 0.0), hi=(20e-3, 20e-3, 40e-3),
+        periodic=(1, 1, 0), wall_lo=(0, 0, 1), wall_hi=(0, 0, 1),
+        dt=1.0e-6,
+        lubrication=1, drag=1, pressure_grad=1, added_mass=1,
+        lub_h_in_frac=1.0e-3, lub_h_out_frac=0.1, c_add=0.5, eps_max=0.9,
+        ncell=(10, 10, 20),
+        bandwidth=(3e-3, 3e-3, 3e-3), n_tau=4, cg_rtol=1e-8, cg_max_iter=500,
+        shift_eps=40, shift_mom=40, shift_force=32,
+        skin=0.05e-3,
+    )
+    for k, v in over.items():
+        if k not in p:
+            raise KeyError(k)
+        p[k] = v
+    return p
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def rsa_spheres(n, d, lo, hi, periodic, seed, zmargin=True, max_tries=2_000_000):
+    """Random sequential addition of n non-overlapping spheres of diameters d."""
+    rng = _rng(seed)
+    lo = np.asarray(lo, float); hi = np.asarray(hi, float); L = hi - lo
+    d = np.broadcast_to(np.asarray(d, float), (n,)).copy()
+    x = np.zeros((n, 3))
+    placed = 0
+    tries = 0
+    while placed < n:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("rsa_spheres: box too full")
+        r = 0.5 * d[placed]
+        c = lo + rng.random(3) * L
+        for a in range(3):
+            if not periodic[a] and zmargin:
+                c[a] = lo[a] + r + rng.random() * (L[a] - 2 * r)
+        if placed:
+            dx = x[:placed] - c
+            for a in range(3):
+                if periodic[a]:
+                    dx[:, a] -= L[a] * np.round(dx[:, a] / L[a])
+            dist2 = np.einsum("ij,ij->i", dx, dx)
+            if np.any(dist2 < (0.5 * (d[:placed] + d[placed])) ** 2):
+                continue
+        x[placed] = c
+        placed += 1
+    return x, d
+
+
+def small_case(seed=1601038011, parity_addon=False):
+    """1,000 monodisperse glass spheres in quiescent water (Case-1-like box)."""
+    prm = default_params()
+    n = 1000
+    x, d = rsa_spheres(n, 1e-3, prm["lo"], prm["hi"], prm["periodic"], seed)
+    v = np.zeros((n, 3)); w = np.zeros((n, 3))
+    rho = np.full(n, 2500.0)
+    if parity_addon:
+        rng = _rng(seed + 7)
+        v = rng.normal(0.0, 0.1, (n, 3))
+        # 5% of the spheres are moved to touch a partner with a small overlap
+        k = n // 20
+        movers = rng.choice(n, size=2 * k, replace=False)
+        L = np.asarray(prm["hi"]) - np.asarray(prm["lo"])
+        for a_i, b_i in movers.reshape(-1, 2):
+            u = rng.normal(size=3); u /= np.linalg.norm(u)
+            dist = 0.5 * (d[a_i] + d[b_i]) - 2e-6
+            c = x[a_i] + dist * u
+            c[2] = np.clip(c[2], prm["lo"][2] + 0.5 * d[b_i], prm["hi"][2] - 0.5 * d[b_i])
+            for a in range(2):
+                c[a] = prm["lo"][a] + np.mod(c[a] - prm["lo"][a], L[a])
+            x[b_i] = c
+            w[a_i] = rng.normal(0.0, 50.0, 3)
+    return prm, dict(x=x, v=v, w=w, d=d, rho=rho)
+
+
+def _fcc_block(n, d_all, Lx, Ly, spacing, seed):
+    """First n sites of an FCC lattice filled from the floor up (periodic x, y)."""
+    rng = _rng(seed)
+    a = np.sqrt(2.0) * spacing
+    nx = max(1, int(round(Lx / a))); ny = max(1, int(round(Ly / a)))
+    ax = Lx / nx; ay = Ly / ny; az = a
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    per_layer = nx * ny * 4
+    nz = n // per_layer + 2
+    ii, jj, kk = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    cells = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], 1)
+    sites = (cells[:, None, :] + basis[None, :, :]).reshape(-1, 3) * np.array([ax, ay, az])
+    sites[:, 2] += 0.5 * d_all.max()
+    order = np.lexsort((rng.random(len(sites)), sites[:, 2]))
+    sites = sites[order[:n]]
+    sites += rng.normal(0.0, 0.02 * spacing, sites.shape)
+    sites[:, 0] %= Lx; sites[:, 1] %= Ly
+    return sites
+
+
+def _relax(x, d, Lx, Ly, iters=400, tol=2e-4):
+    """Remove overlaps by geometric projection (no forces, no time)."""
+    from scipy.spatial import cKDTree
+
+    n = len(x)
+    r = 0.5 * d
+    big = 1e3
+    for _ in range(iters):
+        x[:, 0] %= Lx; x[:, 1] %= Ly
+        x[:, 2] = np.maximum(x[:, 2], r)
+        tree = cKDTree(x, boxsize=(Lx, Ly, big))
+        pairs = tree.query_pairs(d.max() * 1.0001, output_type="ndarray")
+        if len(pairs) == 0:
+            break
+        i, j = pairs[:, 0], pairs[:, 1]
+        dx = x[j] - x[i]
+        dx[:, 0] -= Lx * np.round(dx[:, 0] / Lx)
+        dx[:, 1] -= Ly * np.round(dx[:, 1] / Ly)
+        dist = np.sqrt(np.einsum("ij,ij->i", dx, dx))
+        ov = r[i] + r[j] - dist
+        m = ov > 0
+        if not np.any(m):
+            break
+        worst = np.max(ov[m] / (r[i][m] + r[j][m]))
+        if worst < tol:
+            break
+        i, j, dx, dist, ov = i[m], j[m], dx[m], dist[m], ov[m]
+        u = dx / dist[:, None]
+        push = 0.5 * 1.05 * ov
+        disp = np.zeros_like(x)
+        for a in range(3):
+            disp[:, a] -= np.bincount(i, weights=push * u[:, a], minlength=n)
+            disp[:, a] += np.bincount(j, weights=push * u[:, a], minlength=n)
+        x += disp
+    x[:, 0] %= Lx; x[:, 1] %= Ly
+    x[:, 2] = np.maximum(x[:, 2], r)
+    return x
+
+
+def _cache_path(tag):
+    root = os.environ.get("SEDI_CACHE", "/tmp/sedi_workloads")
+    os.makedirs(root, exist_ok=True)
+    return os.path.join(root, tag + ".npz")
+
+
+def packed_bed(n_total, tiles, block_xy, dsample, seed, spacing):
+    """Tile a relaxed periodic block of n_total / prod(tiles) spheres."""
+    tag = f"bed_{n_total}_{tiles[0]}x{tiles[1]}_{block_xy[0]:.4g}_{block_xy[1]:.4g}_{seed}"
+    path = _cache_path(tag)
+    if os.path.exists(path):
+        z = np.load(path)
+        return z["x"], z["d"]
+    nb = n_total // (tiles[0] * tiles[1])
+    rng = _rng(seed)
+    d = dsample(rng, nb)
+    x = _fcc_block(nb, d, block_xy[0], block_xy[1], spacing, seed + 1)
+    x = _relax(x, d, block_xy[0], block_xy[1])
+    xs, ds = [], []
+    for tx in range(tiles[0]):
+        for ty in range(tiles[1]):
+            xs.append(x + np.array([tx * block_xy[0], ty * block_xy[1], 0.0]))
+            ds.append(d)
+    X = np.concatenate(xs); D = np.concatenate(ds)
+    np.savez(path, x=X, d=D)
+    return X, D
+
+
+def lognormal_d(d50, sigma):
+    def draw(rng, n):
+        z = rng.normal(size=n)
+        bad = np.abs(z) > 3
+        while np.any(bad):
+            z[bad] = rng.normal(size=int(bad.sum()))
+            bad = np.abs(z) > 3
+        return d50 * np.exp(sigma * z)
+    return draw
+
+
+def uniform_d(a, b):
+    def draw(rng, n):
+        return rng.uniform(a, b, n)
+    return draw
+
+
+def log_law(ncell, lo, hi, z_bed, u_star, z0):
+    """Cell-centred log-law velocity u_x(z) = u*/0.41 ln(z'/z0), z' = z - z_bed."""
+    nx, ny, nz = ncell
+    dz = (hi[2] - lo[2]) / nz
+    zc = lo[2] + (np.arange(nz) + 0.5) * dz
+    zp = zc - z_bed
+    ux = np.where(zp > z0, u_star / 0.41 * np.log(np.maximum(zp, z0) / z0), 0.0)
+    U = np.zeros((nz, ny, nx, 3))
+    U[..., 0] = ux[:, None, None]
+    return U.reshape(-1, 3)
+
+
+def bed_case(seed=1601038012, n=200_000):
+    """Sheared sediment bed: 200k lognormal spheres, log-law flow."""
+    Lx, Ly, Lz = 64e-3, 32e-3, 64e-3
+    d50 = 0.5e-3
+    tiles = (4, 2)
+    x, d = packed_bed(n, tiles, (Lx / tiles[0], Ly / tiles[1]), lognormal_d(d50, 0.1), seed,
+                      spacing=1.04 * d50)
+    prm = default_params(hi=(Lx, Ly, Lz), ncell=(64, 32, 64), wall_hi=(0, 0, 0),
+                         bandwidth=(3 * d50,) * 3)
+    z_bed = float(np.quantile(x[:, 2] + 0.5 * d, 0.99))
+    U = log_law(prm["ncell"], prm["lo"], prm["hi"], z_bed, 0.02, d50 / 30.0)
+    nn = len(x)
+    parts = dict(x=x, v=np.zeros((nn, 3)), w=np.zeros((nn, 3)), d=d, rho=np.full(nn, 2500.0))
+    return prm, parts, dict(U=U, z_bed=z_bed)
+
+
+def _gauss_filter_periodic(f, sigma_cells):
+    """Gaussian filter with periodic wrap on every axis (FFT), noise preparation only."""
+    out = f
+    for ax in range(f.ndim):
+        n = f.shape[ax]
+        k = np.fft.fftfreq(n)
+        g = np.exp(-2.0 * (np.pi * k * sigma_cells) ** 2)
+        shape = [1] * f.ndim; shape[ax] = n
+        out = np.real(np.fft.ifft(np.fft.fft(out, axis=ax) * g.reshape(shape), axis=ax))
+    return out
+
+
+def turbulent_like(ncell, lo, hi, mean=(0.3, 0.0, 0.0), rms=0.03, sigma_cells=2.0, seed=0):
+    """Mean flow plus Gaussian-filtered white noise; DU/Dt = U . grad U (central)."""
+    rng = _rng(seed)
+    nx, ny, nz = ncell
+    U = np.zeros((nz, ny, nx, 3))
+    for c in range(3):
+        f = _gauss_filter_periodic(rng.normal(size=(nz, ny, nx)), sigma_cells)
+        f *= rms / f.std()
+        U[..., c] = mean[c] + f
+    h = [(hi[a] - lo[a]) / ncell[a] for a in range(3)]
+    grads = []
+    for ax_arr, hh in ((2, h[0]), (1, h[1]), (0, h[2])):
+        grads.append((np.roll(U, -1, axis=ax_arr) - np.roll(U, 1, axis=ax_arr)) / (2 * hh))
+    DU = U[..., 0:1] * grads[0] + U[..., 1:2] * grads[1] + U[..., 2:3] * grads[2]
+    return U.reshape(-1, 3), DU.reshape(-1, 3)
+
+
+def large_case(seed=1601038013, n=10_000_000):
+    """10M spheres, d ~ U[0.4, 0.6] mm, 400 x 200 x 100 mm, noisy mean flow."""
+    Lx, Ly, Lz = 400e-3, 200e-3, 100e-3
+    tiles = (20, 10)
+    x, d = packed_bed(n, tiles, (Lx / tiles[0], Ly / tiles[1]), uniform_d(0.4e-3, 0.6e-3), seed,
+                      spacing=0.62e-3)
+    prm = default_params(hi=(Lx, Ly, Lz), ncell=(256, 128, 64), wall_hi=(0, 0, 0),
+                         bandwidth=(1.5e-3,) * 3)
+    U, DU = turbulent_like(prm["ncell"], prm["lo"], prm["hi"], seed=seed + 5)
+    nn = len(x)
+    parts = dict(x=x, v=np.zeros((nn, 3)), w=np.zeros((nn, 3)), d=d, rho=np.full(nn, 2500.0))
+    return prm, parts, dict(U=U, DUDt=DU)
+
+
+def random_fields(ncell, nf, seed, scale=1.0):
+    """Non-negative random cell fields [nf, C] (deposition-like sparsity)."""
+    rng = _rng(seed)
+    C = int(np.prod(ncell))
+    f = rng.random((nf, C)) * scale
+    f[rng.random((nf, C)) < 0.5] = 0.0
+    return f

@@ -1,0 +1,180 @@
+"""Pins of the oracle's neighbour search and diffusion-based averaging (CPU only)."""
+import math
+
+import numpy as np
+import pytest
+from scipy import fft as sfft
+
+from paper_1601_03801_gb300.workloads import default_params, random_fields, small_case
+
+RHO = 2500.0
+
+
+def exact_smooth(prm, phi):
+    """Exact discrete answer of n_tau backward-Euler steps of the 7-point
+    Laplacian: periodic axes diagonalised by the DFT, zero-flux axes by the DCT-II."""
+    nx, ny, nz = prm["ncell"]
+    f = phi.reshape(nz, ny, nx).astype(float)
+    axes = {0: 2, 1: 1, 2: 0}  # physical axis -> array axis
+    lam = np.zeros((nz, ny, nx))
+    dtau = 1.0 / prm["n_tau"]
+    for a in range(3):
+        n = prm["ncell"][a]
+        h = (prm["hi"][a] - prm["lo"][a]) / n
+        c = 0.25 * prm["bandwidth"][a] ** 2 / h ** 2
+        k = np.arange(n)
+        if prm["periodic"][a]:
+            ev = 2 - 2 * np.cos(2 * np.pi * k / n)
+        else:
+            ev = 2 - 2 * np.cos(np.pi * k / n)
+        shape = [1, 1, 1]; shape[axes[a]] = n
+        lam = lam + dtau * c * ev.reshape(shape)
+    g = f.astype(complex)
+    for a in range(3):
+        ax = axes[a]
+        if prm["periodic"][a]:
+            g = sfft.fft(g, axis=ax)
+        else:
+            g = sfft.dct(g.real, type=2, norm="ortho", axis=ax) + 1j * sfft.dct(g.imag, type=2, norm="ortho", axis=ax)
+    g = g / (1 + lam) ** prm["n_tau"]
+    for a in range(3):
+        ax = axes[a]
+        if prm["periodic"][a]:
+            g = sfft.ifft(g, axis=ax)
+        else:
+            g = sfft.idct(g.real, type=2, norm="ortho", axis=ax) + 1j * sfft.idct(g.imag, type=2, norm="ortho", axis=ax)
+    return g.real.reshape(-1)
+
+
+@pytest.mark.parametrize("periodic,walls", [((1, 1, 1), (0, 0, 0)), ((1, 0, 0), (0, 1, 1))])
+@pytest.mark.parametrize("n_tau", [1, 4])
+def test_p7_smoothing_equals_spectral_solution(oracle_mod, periodic, walls, n_tau):
+    """P7(i): CG smoothing equals the exact discrete solution computed spectrally,
+    both for periodic faces and for zero-flux faces."""
+    prm = default_params(periodic=periodic, wall_lo=walls, wall_hi=walls, ncell=(12, 10, 8),
+                         hi=(12e-3, 10e-3, 16e-3), bandwidth=(3e-3, 2e-3, 4e-3), n_tau=n_tau,
+                         cg_rtol=1e-14, cg_max_iter=2000)
+    o = oracle_mod.Oracle(prm)
+    phi = random_fields(prm["ncell"], 3, seed=11)
+    out, iters = o.smooth(phi)
+    for f in range(3):
+        ref = exact_smooth(prm, phi[f])
+        assert np.abs(out[f] - ref).max() <= 1e-11 * np.abs(phi[f]).max()
+        assert iters[f] > 0
+
+
+def test_p7_lone_particle_tends_to_gaussian(oracle_mod):
+    """P7(ii): a lone particle's smoothed solid fraction approaches
+    V_p (pi b^2)^(-3/2) exp(-r^2/b^2) as the mesh and pseudo-time step shrink."""
+    errs = []
+    for ncell, n_tau in ((24, 8), (48, 128)):
+        L = 24e-3
+        prm = default_params(periodic=(1, 1, 1), wall_lo=(0, 0, 0), wall_hi=(0, 0, 0),
+                             hi=(L, L, L), ncell=(ncell,) * 3, bandwidth=(3e-3,) * 3,
+                             n_tau=n_tau, drag=0, added_mass=0, pressure_grad=0, lubrication=0,
+                             cg_rtol=1e-12, cg_max_iter=2000)
+        h = L / ncell
+        c = (ncell // 2 + 0.5) * h
+        d = 0.8e-3
+        o = oracle_mod.Oracle(prm)
+        o.set_particles(np.array([[c, c, c]]), np.zeros((1, 3)), np.zeros((1, 3)), np.array([d]),
+                        np.array([RHO]))
+        eps, _, _ = o.average()
+        xs = (np.arange(ncell) + 0.5) * h - c
+        Z, Y, X = np.meshgrid(xs, xs, xs, indexing="ij")
+        b = 3e-3
+        gauss = math.pi / 6 * d ** 3 * (math.pi * b * b) ** -1.5 * np.exp(-(X ** 2 + Y ** 2 + Z ** 2) / b ** 2)
+        errs.append(np.abs(eps - gauss.reshape(-1)).max() / gauss.max())
+        # conserved up to the fixed-point quantum 2^-41 of the deposited value
+        assert abs(eps.sum() * h ** 3 - math.pi / 6 * d ** 3) <= 2.0 ** -40 * h ** 3
+    # implicit-Euler filter (1 + lambda/n)^-n -> exp(-lambda) and O(dx^2): 52% -> 3.7%
+    assert errs[1] < 0.05
+    assert errs[1] < 0.2 * errs[0]
+
+
+@pytest.mark.parametrize("n_tau,max_iter,guess", [(1, 500, False), (4, 500, True), (4, 2, False)])
+def test_p6_smoothing_conserves(oracle_mod, n_tau, max_iter, guess):
+    """P6: the smoothed fields keep their sum (zero-flux walls, periodic sides) for
+    any n_tau, after a projected initial guess, and even when CG is cut short."""
+    prm = default_params(ncell=(10, 10, 20), n_tau=n_tau, cg_max_iter=max_iter)
+    o = oracle_mod.Oracle(prm)
+    phi = random_fields(prm["ncell"], 7, seed=3)
+    g = random_fields(prm["ncell"], 7, seed=5) if guess else None
+    out, _ = o.smooth(phi, guess=g, check=False)
+    for f in range(7):
+        assert abs(out[f].sum() - phi[f].sum()) <= 1e-12 * abs(phi[f]).sum()
+        assert not np.allclose(out[f], phi[f])
+
+
+def test_p8_fixed_point_deposition(oracle_mod):
+    """P8: deposition equals the exact integer sum of per-particle round-to-nearest
+    fixed-point values, and lies within n_k 2^-(S+1) of the FP64 sum."""
+    prm, parts = small_case(parity_addon=True)
+    o = oracle_mod.Oracle(prm)
+    o.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+    rng = np.random.default_rng(9)
+    C = int(np.prod(prm["ncell"]))
+    o.set_eps(rng.uniform(0, 0.5, C))
+    o.set_fluid(U=rng.normal(0, 0.05, (C, 3)))
+    q = o.deposit()
+    ff = o.forces()["fluid"]
+    lo = np.array(prm["lo"]); hi = np.array(prm["hi"]); nc = np.array(prm["ncell"])
+    inv = nc / (hi - lo)
+    cellc = np.clip(np.floor((parts["x"] - lo) * inv).astype(np.int64), 0, nc - 1)
+    cell = (cellc[:, 2] * nc[1] + cellc[:, 1]) * nc[0] + cellc[:, 0]
+    h = (hi - lo) / nc
+    vc = h[0] * h[1] * h[2]
+    d = parts["d"]
+    vfrac = np.pi / 6.0 * d * d * d / vc
+    vals = [vfrac] + [vfrac * parts["v"][:, a] for a in range(3)] + [-ff[:, a] / vc for a in range(3)]
+    shifts = [prm["shift_eps"]] + [prm["shift_mom"]] * 3 + [prm["shift_force"]] * 3
+    counts = np.bincount(cell, minlength=C)
+    for f in range(7):
+        qi = np.rint(np.ldexp(vals[f], shifts[f])).astype(np.int64)
+        ref = np.zeros(C, dtype=np.int64)
+        np.add.at(ref, cell, qi)
+        assert np.array_equal(ref, q[f])
+        fsum = np.zeros(C)
+        np.add.at(fsum, cell, vals[f])
+        err = np.abs(np.ldexp(q[f].astype(float), -shifts[f]) - fsum)
+        assert np.all(err <= counts * 2.0 ** (-shifts[f] - 1) + 1e-15 * np.abs(fsum))
+    # solid volume is conserved by deposition
+    tot = np.ldexp(q[0].astype(float), -prm["shift_eps"]).sum() * vc
+    assert abs(tot - (np.pi / 6 * d ** 3).sum()) < 1e-9 * tot
+
+
+@pytest.mark.parametrize("periodic,skin", [((1, 1, 0), 0.05e-3), ((0, 0, 0), 0.2e-3), ((1, 1, 1), 0.0)])
+def test_p5_neighbor_lists_cell_equals_brute(oracle_mod, periodic, skin):
+    """P5: link-cell lists equal the all-pairs lists, and both equal an independent
+    vectorised evaluation of the same predicate."""
+    rng = np.random.default_rng(21)
+    n = 700
+    prm = default_params(periodic=periodic, hi=(6e-3, 7e-3, 8e-3))
+    x = rng.uniform(0, 1, (n, 3)) * np.array(prm["hi"])
+    d = rng.uniform(0.4e-3, 0.6e-3, n)
+    o = oracle_mod.Oracle(prm)
+    o.set_particles(x, np.zeros((n, 3)), np.zeros((n, 3)), d, np.full(n, RHO))
+    ob, ib = o.neighbors(skin, brute=True)
+    oc, ic = o.neighbors(skin, brute=False)
+    assert np.array_equal(ob, oc) and np.array_equal(ib, ic)
+    L = np.array(prm["hi"])
+    r = 0.5 * d
+    ref = []
+    for i in range(n):
+        dx = x - x[i]
+        for a in range(3):
+            if periodic[a]:
+                s = dx[:, a]
+                s = np.where(s > 0.5 * L[a], s - L[a], np.where(s < -0.5 * L[a], s + L[a], s))
+                dx[:, a] = s
+        d2 = dx[:, 0] * dx[:, 0]
+        d2 = d2 + dx[:, 1] * dx[:, 1]
+        d2 = d2 + dx[:, 2] * dx[:, 2]
+        s = r[i] + r
+        rc = s + prm["lub_h_out_frac"] * s
+        rc = rc + skin
+        m = d2 < rc * rc
+        m[i] = False
+        ref.append(np.nonzero(m)[0])
+    assert np.array_equal(np.concatenate(ref), ib)
+    assert ib.size > n  # non-trivial lists
