@@ -1,0 +1,355 @@
+"""Benchmark of the particle-side hot path on GB300.
+
+One step = one fluid step of the coupled loop: 20 DEM substeps (binning and
+lists when due, Hertz-Mindlin contact with springs, lubrication, drag /
+pressure-gradient / added-mass forces, leapfrog update) followed by one
+diffusion-based averaging (fixed-point PCM deposition + implicit smoothing by
+CG), on the 200,000-sphere sheared sediment bed (64 x 32 x 64 mm, log-law flow,
+64 x 32 x 64 mesh).  Metric: particle-steps/s = N x substeps / device seconds.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 (torchrun, one rank per GPU) runs one independent bed per rank (weak
+scaling, no collective on the data path).  --impl reference times the FP64 CPU
+oracle on this host's cores on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (contact+coupling+averaging), % HBM roofline, vs plain form"
+UNIT = "particle-steps/s"
+SUBSTEPS = 20
+WORKLOAD = ("sheared sediment bed: 200,000 lognormal spheres (median 0.5 mm, sigma_ln 0.1) "
+            "packed in a periodic 64x32x64 mm channel, wall z=0, log-law flow u*=0.02 m/s, "
+            "64x32x64 mesh, Hertz-Mindlin + lubrication + drag + added mass, diffusion "
+            "averaging b=3 d50; step = 20 substeps (dt=1e-6 s) + 1 averaging")
+PROFILE_FILE = os.path.join(ROOT, "profiles", "k_substep_bed200k.md")
+KERNEL_SOURCES = ["paper_1601_03801_gb300/csrc/k_force.cu", "paper_1601_03801_gb300/csrc/fluid.cuh",
+                  "paper_1601_03801_gb300/csrc/common.cuh", "paper_1601_03801_gb300/csrc/dd.cuh"]
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    """DRAM bytes per particle-substep of the fused substep kernel from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    if not os.path.exists(PROFILE_FILE):
+        return None, None
+    txt = open(PROFILE_FILE).read()
+    m = re.search(r"dram_bytes_per_particle_substep:\s*([0-9.eE+-]+)", txt)
+    k = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
+    if not m or not k or k.group(1) != kernel_hash():
+        return None, None
+    return float(m.group(1)), k.group(1)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.proc = None
+        self.index = index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def gpu_arm(args):
+    import torch
+
+    from paper_1601_03801_gb300 import sedi
+    from paper_1601_03801_gb300.workloads import bed_case
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prm, parts, fl = bed_case()
+    n = len(parts["x"])
+    stream = torch.cuda.Stream()
+
+    def make(form, profile):
+        g = sedi.Sedi(dict(prm, precision_form=form, use_graphs=1, profile=profile), stream=stream)
+        g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+        g.set_fluid(U=fl["U"])
+        g.average_inplace()  # the drag sees a smoothed solid fraction from the start
+        # untimed settling so contacts carry load before the warm-up steps
+        for _ in range(args.settle):
+            g.step(SUBSTEPS)
+        g.average_inplace()
+        return g
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def timed_steps(g, K, W):
+        for _ in range(W):
+            g.step(SUBSTEPS)
+            g.average_inplace()
+        g.sync()
+        t0 = g.timings() if g._p.profile else None
+        st0 = g.stats()
+        evs = []
+        clk = Clocks(local)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clk.start()
+        for _ in range(K):
+            with torch.cuda.stream(stream):
+                flush.zero_()  # L2 flushed between timed steps, outside the events
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            g.step(SUBSTEPS)
+            g.average_inplace()
+            with torch.cuda.stream(stream):
+                e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        t1 = g.timings() if g._p.profile else None
+        st1 = g.stats()
+        return ms, t0, t1, st0, st1, clocks
+
+    g = make("split", 1)
+    ms, t0, t1, st0, st1, clocks = timed_steps(g, args.steps, args.warmup)
+    total_ms = float(np.sum(ms))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n * SUBSTEPS * args.steps / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+
+    # roofline of the dominant kernel (fused substep): algorithmic bytes per launch
+    off, _ = g.neighbors()
+    kbar = float(off[-1]) / n
+    ij, _ = g.contacts()
+    cbar = 2.0 * len(ij) / n
+    C = int(np.prod(prm["ncell"]))
+    own_rw = 144 + 120          # own records read + written (see DESIGN: algorithmic bytes)
+    per_particle = own_rw + 4 * kbar + 48 * cbar + 32.0 * C / n
+    sub_ms = (t1["substep_ms"] - t0["substep_ms"]) / max(1.0, t1["substep_n"] - t0["substep_n"])
+    achieved = per_particle * n / (sub_ms / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    traffic_pp, _ = measured_traffic()
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+            "traffic": None if traffic_pp is None else round(traffic_pp * n),
+            "kernel": "k_substep<split>", "algorithmic_bytes_per_particle": round(per_particle, 1),
+            "launch_ms": round(sub_ms, 5), "kbar": round(kbar, 2), "cbar": round(cbar, 2)}
+    phases = {k: round((t1[k] - t0[k]) / args.steps, 4) for k in
+              ("rebuild_ms", "substep_ms", "deposit_ms", "smooth_ms")}
+    rebuilds = st1["rebuilds"] - st0["rebuilds"]
+    # kernels per step: 20 x (check + substep) + deposit, from_fixed, barrier reset,
+    # smoother, outputs; 12 per rebuild taken
+    launches = args.steps * (2 * SUBSTEPS + 5) + 12 * rebuilds
+
+    # end-to-end through the C ABI with host buffers: per step the fluid fields go
+    # host -> device (pinned) and the averaged fields come back
+    import torch as _t
+    Uh = _t.from_numpy(np.ascontiguousarray(fl["U"])).pin_memory()
+    gph = _t.from_numpy(np.tile(np.array([0.0, 0.0, -9.81 * 1000.0]), (C, 1))).pin_memory()
+    duh = _t.zeros((C, 3), dtype=_t.float64).pin_memory()
+    eps_h = _t.zeros(C, dtype=_t.float64).pin_memory()
+    us_h = _t.zeros((C, 3), dtype=_t.float64).pin_memory()
+    F_h = _t.zeros((C, 3), dtype=_t.float64).pin_memory()
+    ge = make("split", 0)
+    K2 = max(2, min(args.steps, 10))
+    for _ in range(2):
+        ge.set_fluid(U=Uh.numpy(), grad_p=gph.numpy(), DUDt=duh.numpy())
+        ge.step(SUBSTEPS)
+        ge.average(eps_h.numpy(), us_h.numpy(), F_h.numpy())
+    torch.cuda.synchronize()
+    t_start = time.perf_counter()
+    for _ in range(K2):
+        ge.set_fluid(U=Uh.numpy(), grad_p=gph.numpy(), DUDt=duh.numpy())
+        ge.step(SUBSTEPS)
+        ge.average(eps_h.numpy(), us_h.numpy(), F_h.numpy())
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t_start
+    e2e = {"value": round(world * n * SUBSTEPS * K2 / e2e_s, 1), "unit": UNIT,
+           "h2d_bytes_per_step": 3 * C * 3 * 8, "d2h_bytes_per_step": 7 * C * 8, "steps": K2}
+
+    # the plain FP32 form on the same GPU (comparison baseline)
+    gp = make("plain", 0)
+    msp, _, _, _, _, _ = timed_steps(gp, max(2, args.steps // 2), 2)
+    plain = {"value": round(n * SUBSTEPS * len(msp) / (np.sum(msp) / 1e3), 1),
+             "ms_per_step": round(float(np.mean(msp)), 4)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(prm, parts, fl, budget_s=args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 forces, df64 (FP32-pair) state, int64 deposition",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "particles_per_gpu": n, "substeps_per_step": SUBSTEPS,
+                           "mesh_cells": C, "form": "split", "graphs": True,
+                           "l2": "flushed (256 MB write) between timed steps, outside the events",
+                           "parallelism": "independent bed per GPU" if world > 1 else "1 GPU"},
+                "phases_ms_per_step": phases, "rebuilds_in_timed_region": int(rebuilds),
+                "roofline": roof, "plain_form": plain, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clocks, "cpu_baseline": cpu}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(prm, parts, fl, budget_s=20.0):
+    """FP64 oracle on this host on a bounded sample of the same workload: a few
+    substeps of the full bed plus one averaging, combined at the 20:1 cadence."""
+    from oracle import oracle as orc
+
+    o = orc.Oracle(prm)
+    o.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+    o.set_fluid(U=fl["U"])
+    n = len(parts["x"])
+    t0 = time.perf_counter()
+    o.average()
+    t_avg = time.perf_counter() - t0
+    subs = 0
+    t0 = time.perf_counter()
+    while True:
+        o.step(1)
+        subs += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or subs >= 20:
+            break
+    t_sub = el / subs
+    step_s = SUBSTEPS * t_sub + t_avg
+    return {"value": round(n * SUBSTEPS / step_s, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{subs} oracle substeps + 1 averaging of the full 200k bed on 1 host core, "
+                      f"combined as 20 substeps + 1 averaging per step "
+                      f"(substep {t_sub:.3f} s, averaging {t_avg:.3f} s)"}
+
+
+def reference_arm(args):
+    """--impl reference: the FP64 oracle as it stands, on this host's cores."""
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    from paper_1601_03801_gb300.workloads import bed_case
+
+    prm, parts, fl = bed_case()
+    n = len(parts["x"])
+    o = orc.Oracle(prm)
+    o.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+    o.set_fluid(U=fl["U"])
+    t0 = time.perf_counter()
+    o.average()
+    t_avg = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(1)
+    t_sub = (time.perf_counter() - t0) / max(1, args.steps)
+    step_s = SUBSTEPS * t_sub + t_avg
+    value = n * SUBSTEPS / step_s
+    sample = (f"each step: 1 oracle substep of the full 200k bed; one averaging timed once "
+              f"({t_avg:.3f} s); value combines 20 substeps + 1 averaging per fluid step")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(step_s * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "particles_per_gpu": n, "substeps_per_step": SUBSTEPS},
+            "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--settle", type=int, default=50, help="untimed settling steps before warm-up")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

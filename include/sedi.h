@@ -1,0 +1,223 @@
+/*
+ * sedi.h -- C ABI of the GB300 particle-side hot path of the SediFoam CFD-DEM
+ * method (Sun & Xiao, arXiv 1601.03801).
+ *
+ * The fluid is frozen: the caller prescribes cell-centred fluid fields on a
+ * uniform Cartesian mesh.  Each DEM substep (sedi_step) does link-cell binning and
+ * neighbour lists (Sec. 2.5), Hertz-Mindlin contact with tangential history
+ * (Sec. 2.1, Eq. 1; Sec. 2.5), Ball-Melrose lubrication (Sec. 2.5), drag,
+ * pressure-gradient and added-mass forces (Sec. 2.3, Eq. 3-8) and a leapfrog
+ * velocity-Verlet update (Sec. 2.1, Eq. 1).  sedi_average does the diffusion-based
+ * averaging (Sec. 2.4, Eq. 9-10): PCM deposition, then implicit diffusion
+ * smoothing solved by conjugate gradients.
+ *
+ * Conventions for every call:
+ *   - Return 0 on success or a negative SEDI_E* code; sedi_last_error() then
+ *     holds a message (per handle, valid until the next call on that handle).
+ *   - Vectors cross the boundary as row-major n x 3 (or C x 3) float64.
+ *   - `mem` says where caller pointers live: SEDI_MEM_HOST or SEDI_MEM_DEVICE
+ *     (device memory of the current CUDA device).  The library copies inputs and
+ *     never keeps a caller pointer; outputs go to caller-owned buffers.
+ *   - Particles are returned in the caller's order of sedi_set_particles.
+ *   - Mesh fields are cell-centred, x fastest: cell (i, j, k) is
+ *     (k * ny + j) * nx + i; cell (i, j, k) spans lo + [i, i+1) * (hi - lo) / n.
+ *   - Work is queued on the handle's stream (sedi_set_stream).  Calls that
+ *     return data to the caller synchronise that stream; a device-side error
+ *     (neighbour capacity, non-finite state, unconverged smoothing, a bounded
+ *     device wait that ran out) raised by queued work is reported by the next
+ *     call that synchronises.
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef SEDI_H
+#define SEDI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SEDI_OK = 0,
+  SEDI_EINVAL = -1,    /* bad argument or parameter */
+  SEDI_ENOMEM = -2,    /* device allocation failed */
+  SEDI_ECUDA = -3,     /* a CUDA runtime call failed */
+  SEDI_EOVERFLOW = -4, /* a particle has more listed neighbours than nbr_capacity */
+  SEDI_ERANGE = -5,    /* a deposited value does not fit the fixed-point format */
+  SEDI_EDIVERGED = -6, /* smoothing CG hit cg_max_iter before cg_rtol */
+  SEDI_ENONFINITE = -7,/* a force or position became NaN/Inf */
+  SEDI_ETIMEOUT = -8,  /* a bounded device-side wait gave up */
+  SEDI_ESTATE = -9,    /* calls in the wrong order (e.g. step before particles) */
+  SEDI_EIO = -10       /* checkpoint file could not be read or written */
+};
+
+enum { SEDI_MEM_HOST = 0, SEDI_MEM_DEVICE = 1 };
+
+/* Arithmetic of the hot path.
+ * SEDI_FORM_SPLIT (default): forces in FP32; positions, velocities, spins and
+ *   tangential springs carried in FP64-class double-float (two FP32 words,
+ *   48-bit significand) so every update runs on the FP32 pipes; contact overlap
+ *   and gap evaluated in double-float; fixed-point deposition; double-float CG.
+ * SEDI_FORM_PLAIN_FP32: everything FP32 (absolute FP32 positions, FP32 CG with
+ *   its tolerance raised to at least 2e-6, float atomics for deposition) -- the
+ *   comparison baseline.
+ * SEDI_FORM_FP64: everything IEEE FP64, for parity checks against an FP64
+ *   reference (slow on GB300: FP64 runs at a small fraction of the FP32 rate). */
+enum { SEDI_FORM_SPLIT = 0, SEDI_FORM_PLAIN_FP32 = 1, SEDI_FORM_FP64 = 2 };
+
+enum { SEDI_HERTZ_MINDLIN = 0 };
+
+typedef struct sedi_handle sedi_handle; /* opaque, owned by the library */
+
+/* All SI units.  Defaults from sedi_default_params() in brackets. */
+typedef struct sedi_params {
+  int32_t contact_law;                     /* SEDI_HERTZ_MINDLIN */
+  double E, poisson, restitution, friction;/* particles and walls [1e7, 0.3, 0.9, 0.3] */
+  double rho_f, nu_f, g[3];                /* fluid density, kinematic viscosity, gravity
+                                              [1000, 1e-6, (0, 0, -9.81)] */
+  double lo[3], hi[3];                     /* box; axis a spans [lo, hi) */
+  int32_t periodic[3];                     /* 1: axis wraps */
+  int32_t wall_lo[3], wall_hi[3];          /* 1: plane wall at lo / hi (non-periodic axes) */
+  double dt;                               /* DEM substep [1e-6] */
+  double skin;                             /* neighbour-list skin [5e-5] */
+  int32_t lubrication, drag, pressure_grad, added_mass; /* force switches [1, 1, 1, 1] */
+  double lub_h_in_frac, lub_h_out_frac;    /* lubrication gap limits as fractions of the
+                                              pair-mean diameter [1e-3, 0.1] */
+  double c_add;                            /* added-mass coefficient, Eq. 8 [0.5] */
+  double eps_max;                          /* clamp of eps_s in the drag law [0.9] */
+  int32_t ncell[3];                        /* Eulerian mesh */
+  double bandwidth[3];                     /* Gaussian bandwidth b per axis (Sec. 2.4) */
+  int32_t n_tau;                           /* backward-Euler pseudo-time steps [4] */
+  double cg_rtol;                          /* ||r|| <= rtol ||b|| per pseudo-step [1e-8] */
+  int32_t cg_max_iter;                     /* [500] */
+  int32_t shift_eps, shift_mom, shift_force; /* fixed-point exponents [40, 40, 32] */
+  int32_t precision_form;                  /* SEDI_FORM_* [SPLIT] */
+  int32_t nbr_capacity;                    /* listed neighbours per particle, <= 32 [32] */
+  int32_t use_graphs;                      /* capture substeps in CUDA graphs [1] */
+  int32_t block_size;                      /* force-kernel block size, 0 = tuned [0] */
+  int32_t n_beds;                          /* independent beds in this handle [1] */
+  int32_t profile;                         /* record CUDA events around each phase
+                                              (see sedi_get_timings) [0] */
+  uint64_t seed;                           /* reserved for stochastic extensions [0] */
+} sedi_params;
+
+/* Per-handle counters since creation. */
+typedef struct sedi_stats {
+  int64_t substeps;       /* substeps advanced */
+  int64_t rebuilds;       /* neighbour-list rebuilds */
+  int64_t averages;       /* sedi_average calls */
+  int64_t cg_iterations;  /* CG iterations summed over fields and pseudo-steps */
+  int32_t max_neighbors;  /* largest list length at the last rebuild */
+  int32_t nbr_capacity;   /* capacity in use */
+} sedi_stats;
+
+/* Fill p with the defaults listed above (box 20 x 20 x 40 mm, periodic x/y,
+   walls at z lo/hi, mesh 10 x 10 x 20, bandwidth 3 mm). */
+void sedi_default_params(sedi_params* p);
+
+/* Create a handle on the current CUDA device.  Checks the parameters and
+   allocates the mesh fields and smoothing work space; particle buffers are
+   allocated by sedi_set_particles.  (Sec. 2.5 advises dt <= t_c / 50 of the
+   Hertz contact time; the caller chooses dt.)  *out is owned by the caller and
+   released with sedi_destroy.  Errors: EINVAL, ENOMEM, ECUDA. */
+int sedi_create(const sedi_params* p, sedi_handle** out);
+void sedi_destroy(sedi_handle* h);
+
+/* Queue all later work on `cuda_stream` (a cudaStream_t).  A new handle uses a
+   non-blocking stream of its own.  NULL selects the legacy default stream, on
+   which substeps run without CUDA graphs (stream capture needs a real stream).
+   The stream must outlive its use by the handle. */
+int sedi_set_stream(sedi_handle* h, void* cuda_stream);
+
+/* Set n particles of bed `bed` (0 <= bed < n_beds): ids (may be NULL: 0..n-1),
+   positions x, half-step velocities v (Sec. 2.1: leapfrog), angular velocities
+   omega (NULL = 0), diameters d and densities rho.  Positions on periodic axes
+   must lie in [lo, hi).  Resets tangential history and the lagged acceleration,
+   sorts the particles into link cells and builds neighbour lists (synchronous).
+   Errors: EINVAL (n <= 0, d or rho <= 0, a position outside a periodic range, a
+   periodic axis shorter than three list cutoffs), ENOMEM, EOVERFLOW. */
+int sedi_set_particles(sedi_handle* h, int32_t bed, int64_t n, const int64_t* id,
+                       const double* x, const double* v, const double* omega,
+                       const double* d, const double* rho, int32_t mem);
+
+/* Prescribed fluid fields on the ncell mesh (must equal params.ncell), each C x 3:
+   U (NULL = 0), grad_p (NULL = rho_f g, hydrostatic), DUDt = dU/dt + U.grad U
+   (NULL = 0) (Sec. 2.3).  The solid fraction seen by the drag (from the last
+   sedi_average or sedi_set_eps, 0 initially) is kept.  Synchronous. */
+int sedi_set_fluid(sedi_handle* h, int32_t bed, const int32_t ncell[3], const double* U,
+                   const double* grad_p, const double* DUDt, int32_t mem);
+
+/* Overwrite the smoothed solid fraction (C) that the drag law interpolates
+   (normally written by sedi_average). */
+int sedi_set_eps(sedi_handle* h, int32_t bed, const double* eps, int32_t mem);
+
+/* Advance every bed by n_substeps DEM substeps (Sec. 2.1 Eq. 1, Sec. 2.3, 2.5):
+   rebuild lists when a particle moved more than skin/2, then forces and the
+   leapfrog update.  Asynchronous: returns after queueing. */
+int sedi_step(sedi_handle* h, int32_t n_substeps);
+
+/* Diffusion-based averaging of bed `bed` (Sec. 2.4, Eq. 9-10): PCM deposition of
+   eps_s, eps_s U_s and the force density -f_fp / V_c on the fluid, then n_tau
+   implicit diffusion steps.  Outputs (any may be NULL): eps_s (C), U_s (C x 3),
+   F_fp (C x 3).  The smoothed eps_s becomes the one the drag law sees.  Errors:
+   ERANGE, EDIVERGED. */
+int sedi_average(sedi_handle* h, int32_t bed, double* eps_s, double* U_s, double* F_fp,
+                 int32_t mem);
+
+/* Raw PCM deposition (Sec. 2.4, Eq. 9) as 64-bit fixed point, [7][C]:
+   eps_s * 2^shift_eps, eps_s U_s * 2^shift_mom (x, y, z), F_fp * 2^shift_force
+   (x, y, z), each rounded to nearest per particle and summed exactly.
+   (The plain FP32 form sums floats and rounds the sum.) */
+int sedi_deposit(sedi_handle* h, int32_t bed, int64_t* fixed_fields, int32_t mem);
+
+/* Smooth n_fields caller fields [n_fields][C] with the averaging operator
+   (Sec. 2.4, Eq. 10); guess (same shape or NULL) is projected onto the conserved
+   sum and used as the first pseudo-step's initial iterate; iters (n_fields or
+   NULL) receives the CG iterations per field summed over pseudo-steps. */
+int sedi_smooth(sedi_handle* h, int32_t bed, int32_t n_fields, const double* in, double* out,
+                const double* guess, int32_t* iters, int32_t mem);
+
+/* Current particle state in the caller's order: x (n x 3), v (half step),
+   omega, a_prev (acceleration of the last substep); any may be NULL. */
+int sedi_get_particles(sedi_handle* h, int32_t bed, double* x, double* v, double* omega,
+                       double* a_prev, int32_t mem);
+
+/* Forces and torque at the current state without advancing or touching the
+   history (Sec. 2.1 Eq. 1 right-hand sides): contact (pairs + walls),
+   lubrication, fluid (drag + pressure gradient + added mass), contact torque. */
+int sedi_compute_forces(sedi_handle* h, int32_t bed, double* f_contact, double* f_lub,
+                        double* f_fluid, double* torque, int32_t mem);
+
+/* Current neighbour lists in the caller's numbering: offsets (n + 1) and sorted
+   ids of each particle's listed partners.  Returns the number of entries, or
+   SEDI_EOVERFLOW if cap is too small (offsets is still filled). */
+int64_t sedi_get_neighbors(sedi_handle* h, int32_t bed, int64_t* offsets, int64_t* ids,
+                           int64_t cap);
+
+/* Tangential springs of the pairs in contact: ij (m x 2, caller indices, i < j)
+   and xi (m x 3) as seen from i.  Returns m, or SEDI_EOVERFLOW if m > cap. */
+int64_t sedi_get_contacts(sedi_handle* h, int32_t bed, int64_t cap, int64_t* ij, double* xi);
+
+/* Checkpoint and restore of particles, lagged accelerations, tangential springs,
+   fluid fields and the drag's solid fraction (binary, this library's format). */
+int sedi_save_state(sedi_handle* h, const char* path);
+int sedi_load_state(sedi_handle* h, const char* path);
+
+/* Device time per phase since creation, from CUDA events recorded on the
+   handle's stream (inside the CUDA graphs too) when params.profile = 1:
+   ms[0] rebuild check + conditional rebuild, ms[1] fused force/update kernel,
+   ms[2] deposition, ms[3] smoothing; ms[4..7] the number of timed launches of
+   each phase.  Synchronises the stream.  Returns the number of values written
+   (<= n), 0 when profiling is off. */
+int sedi_get_timings(sedi_handle* h, double* ms_per_phase, int32_t n);
+int sedi_get_stats(sedi_handle* h, sedi_stats* out);
+
+/* Block until all queued work of the handle is done; returns its status. */
+int sedi_sync(sedi_handle* h);
+
+const char* sedi_last_error(const sedi_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEDI_H */

@@ -1,0 +1,1159 @@
+// Host engine behind include/sedi.h: parameter checks, device buffers, CUDA-graph
+// capture of the substep sequence (rebuild under a graph IF node decided on the
+// device), orchestration of the averaging, import/export in caller order and
+// checkpoints.  All arithmetic of the method runs in the kernels of k_*.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/sedi.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace sedi;
+
+struct sedi_handle {
+  sedi_params prm{};
+  std::string err;
+  cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;  // capture of conditional bodies
+  cudaStream_t own = nullptr;   // default stream of the handle (graphs need a real stream)
+  int form = FORM_SPLIT;
+  int64_t N = 0;
+  bool have_particles = false;
+  std::vector<int64_t> ids;
+  std::vector<double> d_host, rho_host;
+  std::vector<double> U, gp, du, eps;  // host copies of the fluid fields (checkpoint)
+  bool gp_default = true;
+  DevState st{};
+  DevParams P{};
+  DevMesh mesh{};
+  std::vector<void*> part_allocs;  // per-particle buffers
+  std::vector<void*> mesh_allocs;
+  void* qfix = nullptr;   // [7][C] int64 (plain: float phi)
+  void* phi = nullptr;    // [8][C] smoothing word
+  void* work = nullptr;
+  size_t work_bytes = 0;
+  int* iters_dev = nullptr;
+  double* dstage = nullptr;  // [max(7C, 4*3N)] doubles
+  size_t dstage_n = 0;
+  double coef[3] = {0, 0, 0};
+  std::map<int, cudaGraphExec_t> graphs;
+  sedi_stats stats{};
+  int block = 128;
+  // profiling: events per captured substep (A: before check, B: before the
+  // substep kernel, C: after it) and around deposition / smoothing
+  struct GraphEv {
+    std::vector<cudaEvent_t> a, b, c;
+  };
+  std::map<int, GraphEv> gev;
+  std::vector<cudaEvent_t> avg_ev;  // 3 events: before deposit, after deposit, after smooth
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  double ms[4] = {0, 0, 0, 0};
+  double cnt[4] = {0, 0, 0, 0};
+};
+
+namespace {
+
+size_t word_bytes(int form) { return form == FORM_PLAIN ? 4 : 8; }
+size_t quad_bytes(int form) { return form == FORM_PLAIN ? 16 : 32; }
+size_t fquad_bytes(int form) { return form == FORM_FP64 ? 32 : 16; }
+
+int fail(sedi_handle* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  return code;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(h, SEDI_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));        \
+  } while (0)
+
+int dmalloc(sedi_handle* h, std::vector<void*>& list, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) return fail(h, SEDI_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  list.push_back(*p);
+  return 0;
+}
+
+void free_list(std::vector<void*>& list) {
+  for (void* p : list) cudaFree(p);
+  list.clear();
+}
+
+void clear_graphs(sedi_handle* h) {
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  h->pending.clear();
+  for (auto& kv : h->gev)
+    for (auto* v : {&kv.second.a, &kv.second.b, &kv.second.c})
+      for (cudaEvent_t e : *v) cudaEventDestroy(e);
+  h->gev.clear();
+}
+
+// Accumulate the elapsed times of recorded event pairs (profile mode).
+void harvest(sedi_handle* h) {
+  if (h->pending.empty()) return;
+  cudaEventSynchronize(h->pending.back().second.second);
+  for (auto& p : h->pending) {
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, p.second.first, p.second.second) == cudaSuccess) {
+      h->ms[p.first] += t;
+      h->cnt[p.first] += 1.0;
+    } else {
+      cudaGetLastError();  // a pair that was not recorded is skipped, not sticky
+    }
+  }
+  h->pending.clear();
+}
+
+cudaEvent_t new_event() {
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void split_double(double x, dd* out) {
+  float hi = (float)x;
+  float lo = (float)(x - (double)hi);
+  *out = dd{hi, lo};
+}
+
+template <class F>
+void fill_consts(const sedi_params& p, ForceConsts<F>& K) {
+  const double Es = p.E / (2.0 * (1.0 - p.poisson * p.poisson));
+  const double G = p.E / (2.0 * (1.0 + p.poisson));
+  const double Gs = G / (2.0 * (2.0 - p.poisson));
+  const double lne = std::log(p.restitution);
+  const double beta = lne / std::sqrt(lne * lne + M_PI * M_PI);
+  K.Es = (F)Es;
+  K.Gs = (F)Gs;
+  K.cdamp = (F)(-2.0 * std::sqrt(5.0 / 6.0) * beta);
+  K.kn_fac = (F)(4.0 / 3.0 * Es);
+  K.mu = (F)p.friction;
+  K.dt = (F)p.dt;
+  K.lub_in = (F)p.lub_h_in_frac;
+  K.lub_out = (F)p.lub_h_out_frac;
+  K.six_pi_mu = (F)(6.0 * M_PI * p.rho_f * p.nu_f);
+  K.rho_f = (F)p.rho_f;
+  K.nu_f = (F)p.nu_f;
+  K.c_add_rho_f = (F)(p.c_add * p.rho_f);
+  K.eps_max = (F)p.eps_max;
+  for (int a = 0; a < 3; ++a) {
+    const double L = p.hi[a] - p.lo[a];
+    K.g[a] = (F)p.g[a];
+    K.lo[a] = (F)p.lo[a];
+    K.L[a] = (F)L;
+    K.halfL[a] = (F)(0.5 * L);
+    K.inv_h[a] = (F)((double)p.ncell[a] / L);
+  }
+}
+
+void fill_params(sedi_handle* h) {
+  const sedi_params& p = h->prm;
+  DevParams& P = h->P;
+  for (int a = 0; a < 3; ++a) {
+    P.lo[a] = p.lo[a];
+    P.hi[a] = p.hi[a];
+    P.L[a] = p.hi[a] - p.lo[a];
+    P.periodic[a] = p.periodic[a] ? 1 : 0;
+    P.wall_lo[a] = (!p.periodic[a] && p.wall_lo[a]) ? 1 : 0;
+    P.wall_hi[a] = (!p.periodic[a] && p.wall_hi[a]) ? 1 : 0;
+    P.nc[a] = p.ncell[a];
+    P.inv_h[a] = (double)p.ncell[a] / (p.hi[a] - p.lo[a]);
+    P.bf.lo[a] = (float)p.lo[a];
+    P.bf.hi[a] = (float)p.hi[a];
+    P.bf.L[a] = (float)P.L[a];
+    P.bdb.lo[a] = p.lo[a];
+    P.bdb.hi[a] = p.hi[a];
+    P.bdb.L[a] = P.L[a];
+    split_double(p.lo[a], &P.bdd.lo[a]);
+    split_double(p.hi[a], &P.bdd.hi[a]);
+    split_double(P.L[a], &P.bdd.L[a]);
+  }
+  P.lubrication = p.lubrication ? 1 : 0;
+  P.drag = p.drag ? 1 : 0;
+  P.pressure_grad = p.pressure_grad ? 1 : 0;
+  P.added_mass = p.added_mass ? 1 : 0;
+  fill_consts<float>(p, P.cf);
+  fill_consts<double>(p, P.cd);
+  P.C = (int64_t)p.ncell[0] * p.ncell[1] * p.ncell[2];
+  const double dx = (p.hi[0] - p.lo[0]) / p.ncell[0];
+  const double dy = (p.hi[1] - p.lo[1]) / p.ncell[1];
+  const double dz = (p.hi[2] - p.lo[2]) / p.ncell[2];
+  P.vc = dx * dy * dz;
+  P.cap = p.nbr_capacity;
+  P.skin = p.skin;
+  P.lub_out_frac = p.lub_h_out_frac;
+  P.half_skin_f = (float)(0.5 * p.skin);
+  P.lub_out_f = (float)p.lub_h_out_frac;
+  P.shift[0] = p.shift_eps;
+  P.shift[1] = p.shift_mom;
+  P.shift[2] = p.shift_force;
+  for (int k = 0; k < 3; ++k) P.two_shift[k] = std::ldexp(1.0, P.shift[k]);
+  const double dtau = 1.0 / p.n_tau;
+  const double hs[3] = {dx, dy, dz};
+  for (int a = 0; a < 3; ++a) {
+    const double D = 0.25 * p.bandwidth[a] * p.bandwidth[a];
+    h->coef[a] = dtau * D / (hs[a] * hs[a]);
+  }
+}
+
+int check_params(sedi_handle* h, const sedi_params& p) {
+  if (p.contact_law != SEDI_HERTZ_MINDLIN) return fail(h, SEDI_EINVAL, "contact_law: only SEDI_HERTZ_MINDLIN");
+  if (!(p.E > 0) || !(p.poisson >= 0 && p.poisson < 0.5)) return fail(h, SEDI_EINVAL, "E > 0 and 0 <= poisson < 0.5 required");
+  if (!(p.restitution > 0 && p.restitution <= 1)) return fail(h, SEDI_EINVAL, "restitution must be in (0, 1]");
+  if (!(p.friction >= 0)) return fail(h, SEDI_EINVAL, "friction must be >= 0");
+  if (!(p.rho_f > 0) || !(p.nu_f > 0)) return fail(h, SEDI_EINVAL, "rho_f, nu_f must be > 0");
+  if (!(p.dt > 0) || !(p.skin >= 0)) return fail(h, SEDI_EINVAL, "dt > 0 and skin >= 0 required");
+  for (int a = 0; a < 3; ++a) {
+    if (!(p.hi[a] > p.lo[a])) return fail(h, SEDI_EINVAL, "box hi must exceed lo on axis %d", a);
+    if (p.ncell[a] < 1) return fail(h, SEDI_EINVAL, "ncell must be >= 1");
+    if (!(p.bandwidth[a] >= 0)) return fail(h, SEDI_EINVAL, "bandwidth must be >= 0");
+  }
+  if (!(p.lub_h_in_frac > 0) || !(p.lub_h_out_frac > p.lub_h_in_frac)) return fail(h, SEDI_EINVAL, "need 0 < lub_h_in_frac < lub_h_out_frac");
+  if (p.n_tau < 1 || !(p.cg_rtol > 0) || p.cg_max_iter < 1) return fail(h, SEDI_EINVAL, "n_tau, cg_rtol, cg_max_iter must be positive");
+  if (p.precision_form < 0 || p.precision_form > 2) return fail(h, SEDI_EINVAL, "unknown precision_form");
+  if (p.nbr_capacity < 1 || p.nbr_capacity > 32) return fail(h, SEDI_EINVAL, "nbr_capacity must be in [1, 32]");
+  if (p.n_beds != 1) return fail(h, SEDI_EINVAL, "n_beds: this build runs one bed per handle");
+  for (int k = 0; k < 3; ++k) {
+    int s = k == 0 ? p.shift_eps : (k == 1 ? p.shift_mom : p.shift_force);
+    if (s < 0 || s > 60) return fail(h, SEDI_EINVAL, "fixed-point shifts must be in [0, 60]");
+  }
+  return 0;
+}
+
+int copy_in(sedi_handle* h, void* dst, const void* src, size_t bytes, int mem) {
+  CK(cudaMemcpyAsync(dst, src, bytes, mem == SEDI_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  return 0;
+}
+
+int copy_out(sedi_handle* h, void* dst, const void* src, size_t bytes, int mem) {
+  CK(cudaMemcpyAsync(dst, src, bytes, mem == SEDI_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+  return 0;
+}
+
+int ensure_stage(sedi_handle* h, size_t n) {
+  if (h->dstage_n >= n) return 0;
+  if (h->dstage) cudaFree(h->dstage);
+  h->dstage = nullptr;
+  h->dstage_n = 0;
+  CK(cudaMalloc((void**)&h->dstage, n * sizeof(double)));
+  h->dstage_n = n;
+  return 0;
+}
+
+// Read the device control block; map device-side errors to status codes.
+int sync_status(sedi_handle* h) {
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  if (!h->st.ctl) return 0;
+  Ctl c;
+  CK(cudaMemcpy(&c, h->st.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  h->stats.rebuilds = c.rebuilds;
+  h->stats.max_neighbors = c.max_nn;
+  if (c.error == SEDI_EOVERFLOW)
+    return fail(h, SEDI_EOVERFLOW, "a particle has %d listed neighbours > nbr_capacity %d", c.overflow_nn, h->P.cap);
+  if (c.error == SEDI_ENONFINITE) return fail(h, SEDI_ENONFINITE, "non-finite force or state");
+  if (c.error) return fail(h, c.error, "device error %d", c.error);
+  return 0;
+}
+
+int upload_mesh(sedi_handle* h) {
+  const int64_t C = h->P.C;
+  const int form = h->form;
+  const sedi_params& p = h->prm;
+  std::vector<double> ufe(4 * C), gfl(4 * C, 0.0);
+  for (int64_t c = 0; c < C; ++c) {
+    for (int a = 0; a < 3; ++a) {
+      ufe[4 * c + a] = h->U[3 * c + a];
+      double g = 0.0;
+      if (p.pressure_grad) g -= h->gp_default ? p.rho_f * p.g[a] : h->gp[3 * c + a];
+      if (p.added_mass) g += p.c_add * p.rho_f * h->du[3 * c + a];
+      gfl[4 * c + a] = g;
+    }
+    ufe[4 * c + 3] = h->eps[c];
+  }
+  if (form == FORM_FP64) {
+    CK(cudaMemcpyAsync(h->mesh.ufe, ufe.data(), 32 * C, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->mesh.gfl, gfl.data(), 32 * C, cudaMemcpyHostToDevice, h->stream));
+  } else {
+    std::vector<float> uf(4 * C), gf(4 * C);
+    for (int64_t k = 0; k < 4 * C; ++k) {
+      uf[k] = (float)ufe[k];
+      gf[k] = (float)gfl[k];
+    }
+    CK(cudaMemcpyAsync(h->mesh.ufe, uf.data(), 16 * C, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->mesh.gfl, gf.data(), 16 * C, cudaMemcpyHostToDevice, h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return 0;
+}
+
+int alloc_particles(sedi_handle* h, int64_t N, double rmax) {
+  clear_graphs(h);
+  free_list(h->part_allocs);
+  DevState& st = h->st;
+  Ctl* ctl = st.ctl;
+  st = DevState{};
+  st.ctl = ctl;
+  st.N = N;
+  const int form = h->form;
+  const size_t q = quad_bytes(form), fq = fquad_bytes(form), w = word_bytes(form);
+  const int64_t cap = h->P.cap;
+  int rc;
+  for (int b = 0; b < 2; ++b) {
+    if ((rc = dmalloc(h, h->part_allocs, &st.pos[b], q * N))) return rc;
+    if ((rc = dmalloc(h, h->part_allocs, &st.vel[b], q * N))) return rc;
+    if ((rc = dmalloc(h, h->part_allocs, &st.omg[b], q * N))) return rc;
+    if ((rc = dmalloc(h, h->part_allocs, &st.acc[b], fq * N))) return rc;
+    if ((rc = dmalloc(h, h->part_allocs, (void**)&st.uid[b], 4 * N))) return rc;
+    if ((rc = dmalloc(h, h->part_allocs, (void**)&st.r64[b], 8 * N))) return rc;
+    if ((rc = dmalloc(h, h->part_allocs, (void**)&st.vfrac[b], 8 * N))) return rc;
+    if ((rc = dmalloc(h, h->part_allocs, (void**)&st.xb[b], 16 * N))) return rc;
+    if ((rc = dmalloc(h, h->part_allocs, &st.whist[b], (size_t)kWalls * 3 * w * N))) return rc;
+    if ((rc = dmalloc(h, h->part_allocs, (void**)&st.wmask[b], 4 * N))) return rc;
+    if ((rc = dmalloc(h, h->part_allocs, (void**)&st.nbr[b], 4 * cap * N))) return rc;
+    if ((rc = dmalloc(h, h->part_allocs, (void**)&st.nn[b], 4 * N))) return rc;
+    if ((rc = dmalloc(h, h->part_allocs, &st.hist[b], 3 * w * cap * N))) return rc;
+    if ((rc = dmalloc(h, h->part_allocs, (void**)&st.cmask[b], 4 * N))) return rc;
+  }
+  // bins: edge >= the largest list cutoff (2 r_max (1 + f) + skin) with margin
+  const sedi_params& p = h->prm;
+  const double rc_max = (2.0 * rmax) * (1.0 + p.lub_h_out_frac) + p.skin;
+  const double hb = rc_max * 1.001;
+  int64_t nbins = 1;
+  for (int a = 0; a < 3; ++a) {
+    const double L = p.hi[a] - p.lo[a];
+    int nb = (int)std::floor(L / hb);
+    if (nb < 1) nb = 1;
+    if (p.periodic[a] && nb < 3)
+      return fail(h, SEDI_EINVAL, "periodic axis %d is shorter than 3 list cutoffs (%g m)", a, 3 * hb);
+    h->P.nb[a] = nb;
+    h->P.bin_inv[a] = (float)((double)nb / L);
+    nbins *= nb;
+  }
+  if (nbins > (int64_t)1 << 31) return fail(h, SEDI_EINVAL, "too many bins");
+  h->P.nbins = nbins;
+  const int64_t nblk = (nbins + 1023) / 1024 + 1;
+  if ((rc = dmalloc(h, h->part_allocs, (void**)&st.bin_of, 4 * N))) return rc;
+  if ((rc = dmalloc(h, h->part_allocs, (void**)&st.bin_count, 4 * nbins))) return rc;
+  if ((rc = dmalloc(h, h->part_allocs, (void**)&st.bin_start, 4 * (nbins + 1)))) return rc;
+  if ((rc = dmalloc(h, h->part_allocs, (void**)&st.bin_fill, 4 * nbins))) return rc;
+  if ((rc = dmalloc(h, h->part_allocs, (void**)&st.order, 4 * N))) return rc;
+  if ((rc = dmalloc(h, h->part_allocs, (void**)&st.scan_blk, 4 * nblk))) return rc;
+  if ((rc = dmalloc(h, h->part_allocs, (void**)&st.fdbg, 8 * 12 * N))) return rc;
+  CK(cudaMemsetAsync(st.cmask[0], 0, 4 * N, h->stream));
+  CK(cudaMemsetAsync(st.cmask[1], 0, 4 * N, h->stream));
+  CK(cudaMemsetAsync(st.wmask[0], 0, 4 * N, h->stream));
+  CK(cudaMemsetAsync(st.wmask[1], 0, 4 * N, h->stream));
+  CK(cudaMemsetAsync(st.nn[0], 0, 4 * N, h->stream));
+  CK(cudaMemsetAsync(st.nn[1], 0, 4 * N, h->stream));
+  return ensure_stage(h, std::max<size_t>((size_t)12 * N, (size_t)8 * h->P.C));
+}
+
+int build_graph(sedi_handle* h, int n, cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  sedi_handle::GraphEv ev;
+  if (h->prm.profile)
+    for (int s = 0; s < n; ++s) {
+      ev.a.push_back(new_event());
+      ev.b.push_back(new_event());
+      ev.c.push_back(new_event());
+    }
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  for (int s = 0; s < n; ++s) {
+    // inside a capture only the External flag makes an event-record node
+    if (h->prm.profile) CK(cudaEventRecordWithFlags(ev.a[s], h->stream, cudaEventRecordExternal));
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphConditionalHandle ch;
+    CK(cudaGraphConditionalHandleCreate(&ch, g, 0, cudaGraphCondAssignDefault));
+    launch_check(h->st, h->P, (unsigned long long)ch, 1, h->stream);
+    CK(cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &g, &deps, nullptr, &nd));
+    // the struct has a union of non-trivial members: zero raw storage instead
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+    std::memset(raw, 0, sizeof(raw));
+    cudaGraphNodeParams* cp = reinterpret_cast<cudaGraphNodeParams*>(raw);
+    cp->type = cudaGraphNodeTypeConditional;
+    cp->conditional.handle = ch;
+    cp->conditional.type = cudaGraphCondTypeIf;
+    cp->conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, cp));
+    CK(cudaStreamUpdateCaptureDependencies(h->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t body = cp->conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(h->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    launch_rebuild(h->form, h->st, h->P, s, false, h->side);
+    CK(cudaStreamEndCapture(h->side, &body));
+    if (h->prm.profile) CK(cudaEventRecordWithFlags(ev.b[s], h->stream, cudaEventRecordExternal));
+    launch_substep(h->form, h->st, h->mesh, h->P, s, true, h->block, h->stream);
+    if (h->prm.profile) CK(cudaEventRecordWithFlags(ev.c[s], h->stream, cudaEventRecordExternal));
+  }
+  launch_advance_parity(h->st, n, h->stream);
+  CK(cudaStreamEndCapture(h->stream, &graph));
+  if (h->prm.profile) h->gev[n] = ev;
+  cudaError_t e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(h, SEDI_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  return 0;
+}
+
+int need_particles(sedi_handle* h) {
+  if (!h) return SEDI_EINVAL;
+  if (!h->have_particles) return fail(h, SEDI_ESTATE, "no particles set");
+  return 0;
+}
+
+int rebuild_now(sedi_handle* h) {
+  launch_rebuild(h->form, h->st, h->P, 0, true, h->stream);
+  return sync_status(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+void sedi_default_params(sedi_params* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->contact_law = SEDI_HERTZ_MINDLIN;
+  p->E = 1.0e7;
+  p->poisson = 0.3;
+  p->restitution = 0.9;
+  p->friction = 0.3;
+  p->rho_f = 1000.0;
+  p->nu_f = 1.0e-6;
+  p->g[2] = -9.81;
+  p->hi[0] = 20e-3;
+  p->hi[1] = 20e-3;
+  p->hi[2] = 40e-3;
+  p->periodic[0] = p->periodic[1] = 1;
+  p->wall_lo[2] = p->wall_hi[2] = 1;
+  p->dt = 1.0e-6;
+  p->skin = 0.05e-3;
+  p->lubrication = p->drag = p->pressure_grad = p->added_mass = 1;
+  p->lub_h_in_frac = 1.0e-3;
+  p->lub_h_out_frac = 0.1;
+  p->c_add = 0.5;
+  p->eps_max = 0.9;
+  p->ncell[0] = 10;
+  p->ncell[1] = 10;
+  p->ncell[2] = 20;
+  p->bandwidth[0] = p->bandwidth[1] = p->bandwidth[2] = 3e-3;
+  p->n_tau = 4;
+  p->cg_rtol = 1e-8;
+  p->cg_max_iter = 500;
+  p->shift_eps = 40;
+  p->shift_mom = 40;
+  p->shift_force = 32;
+  p->precision_form = SEDI_FORM_SPLIT;
+  p->nbr_capacity = 32;
+  p->use_graphs = 1;
+  p->block_size = 0;
+  p->n_beds = 1;
+}
+
+int sedi_create(const sedi_params* p, sedi_handle** out) {
+  if (!p || !out) return SEDI_EINVAL;
+  *out = nullptr;
+  sedi_handle* h = new sedi_handle();
+  h->prm = *p;
+  int rc = check_params(h, *p);
+  if (rc) {
+    std::string msg = h->err;
+    delete h;
+    (void)msg;
+    return rc;
+  }
+  h->form = p->precision_form;
+  h->block = p->block_size > 0 ? p->block_size : 128;
+  fill_params(h);
+  const int64_t C = h->P.C;
+  h->U.assign(3 * C, 0.0);
+  h->gp.assign(3 * C, 0.0);
+  h->du.assign(3 * C, 0.0);
+  h->eps.assign(C, 0.0);
+  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc((void**)&h->st.ctl, sizeof(Ctl)) != cudaSuccess) {
+    delete h;
+    return SEDI_ECUDA;
+  }
+  cudaMemset(h->st.ctl, 0, sizeof(Ctl));
+  h->stream = h->own;
+  h->mesh.C = C;
+  const size_t fq = fquad_bytes(h->form);
+  if ((rc = dmalloc(h, h->mesh_allocs, &h->mesh.ufe, fq * C)) ||
+      (rc = dmalloc(h, h->mesh_allocs, &h->mesh.gfl, fq * C)) ||
+      (rc = dmalloc(h, h->mesh_allocs, &h->qfix, 8 * 7 * C)) ||
+      (rc = dmalloc(h, h->mesh_allocs, &h->phi, 8 * 8 * C)) ||
+      (rc = dmalloc(h, h->mesh_allocs, (void**)&h->iters_dev, 4 * 8))) {
+    sedi_destroy(h);
+    return rc;
+  }
+  h->work_bytes = smooth_work_bytes(h->form, C, 8);
+  if ((rc = dmalloc(h, h->mesh_allocs, &h->work, h->work_bytes))) {
+    sedi_destroy(h);
+    return rc;
+  }
+  if ((rc = upload_mesh(h))) {
+    sedi_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return 0;
+}
+
+void sedi_destroy(sedi_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  clear_graphs(h);
+  for (cudaEvent_t e : h->avg_ev) cudaEventDestroy(e);
+  free_list(h->part_allocs);
+  free_list(h->mesh_allocs);
+  if (h->dstage) cudaFree(h->dstage);
+  if (h->st.ctl) cudaFree(h->st.ctl);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->own) cudaStreamDestroy(h->own);
+  delete h;
+}
+
+int sedi_set_stream(sedi_handle* h, void* s) {
+  if (!h) return SEDI_EINVAL;
+  if ((cudaStream_t)s != h->stream) clear_graphs(h);
+  h->stream = (cudaStream_t)s;
+  return 0;
+}
+
+int sedi_set_particles(sedi_handle* h, int32_t bed, int64_t n, const int64_t* id, const double* x,
+                       const double* v, const double* omega, const double* d, const double* rho,
+                       int32_t mem) {
+  if (!h) return SEDI_EINVAL;
+  h->err.clear();
+  if (bed != 0) return fail(h, SEDI_EINVAL, "bed %d out of range", bed);
+  if (n <= 0 || n > ((int64_t)1 << 31) - 1) return fail(h, SEDI_EINVAL, "n must be in [1, 2^31)");
+  if (!x || !d || !rho) return fail(h, SEDI_EINVAL, "x, d and rho are required");
+  // host copies of d, rho (bin size, checkpoint) and the caller's ids
+  h->d_host.resize(n);
+  h->rho_host.resize(n);
+  std::vector<double> xh;
+  if (mem == SEDI_MEM_DEVICE) {
+    CK(cudaMemcpy(h->d_host.data(), d, 8 * n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(h->rho_host.data(), rho, 8 * n, cudaMemcpyDeviceToHost));
+    xh.resize(3 * n);
+    CK(cudaMemcpy(xh.data(), x, 24 * n, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(h->d_host.data(), d, 8 * n);
+    std::memcpy(h->rho_host.data(), rho, 8 * n);
+    xh.assign(x, x + 3 * n);
+  }
+  double rmax = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!(h->d_host[i] > 0) || !(h->rho_host[i] > 0)) return fail(h, SEDI_EINVAL, "particle %lld: d and rho must be > 0", (long long)i);
+    rmax = std::max(rmax, 0.5 * h->d_host[i]);
+    for (int a = 0; a < 3; ++a) {
+      const double c = xh[3 * i + a];
+      if (!std::isfinite(c)) return fail(h, SEDI_EINVAL, "particle %lld: non-finite position", (long long)i);
+      if (h->prm.periodic[a] && (c < h->prm.lo[a] || c >= h->prm.hi[a]))
+        return fail(h, SEDI_EINVAL, "particle %lld: position outside [lo, hi) on periodic axis %d", (long long)i, a);
+    }
+  }
+  h->ids.clear();
+  if (id) {
+    h->ids.resize(n);
+    if (mem == SEDI_MEM_DEVICE) {
+      CK(cudaMemcpy(h->ids.data(), id, 8 * n, cudaMemcpyDeviceToHost));
+    } else {
+      std::memcpy(h->ids.data(), id, 8 * n);
+    }
+  }
+  h->have_particles = false;
+  int rc = alloc_particles(h, n, rmax);
+  if (rc) return rc;
+  h->N = n;
+  // stage inputs (x, v, w, d, rho) in device doubles
+  double* tmp = nullptr;
+  CK(cudaMalloc((void**)&tmp, 8 * 11 * n));
+  double *tx = tmp, *tv = tmp + 3 * n, *tw = tmp + 6 * n, *td = tmp + 9 * n, *tr = tmp + 10 * n;
+  rc = copy_in(h, tx, xh.data(), 24 * n, SEDI_MEM_HOST);
+  if (!rc && v) rc = copy_in(h, tv, v, 24 * n, mem);
+  if (!rc && omega) rc = copy_in(h, tw, omega, 24 * n, mem);
+  if (!rc) rc = copy_in(h, td, h->d_host.data(), 8 * n, SEDI_MEM_HOST);
+  if (!rc) rc = copy_in(h, tr, h->rho_host.data(), 8 * n, SEDI_MEM_HOST);
+  if (rc) {
+    cudaFree(tmp);
+    return rc;
+  }
+  Ctl zero{};
+  cudaMemcpyAsync(h->st.ctl, &zero, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream);
+  launch_import(h->form, h->st, tx, v ? tv : nullptr, omega ? tw : nullptr, td, tr, h->P, h->stream);
+  rc = rebuild_now(h);
+  cudaFree(tmp);
+  if (rc) return rc;
+  h->have_particles = true;
+  return 0;
+}
+
+int sedi_set_fluid(sedi_handle* h, int32_t bed, const int32_t ncell[3], const double* U,
+                   const double* grad_p, const double* DUDt, int32_t mem) {
+  if (!h) return SEDI_EINVAL;
+  h->err.clear();
+  if (bed != 0) return fail(h, SEDI_EINVAL, "bed %d out of range", bed);
+  if (!ncell || ncell[0] != h->prm.ncell[0] || ncell[1] != h->prm.ncell[1] || ncell[2] != h->prm.ncell[2])
+    return fail(h, SEDI_EINVAL, "ncell must equal params.ncell");
+  const int64_t C = h->P.C;
+  auto get = [&](const double* src, std::vector<double>& dst) -> int {
+    if (mem == SEDI_MEM_DEVICE) {
+      CK(cudaMemcpy(dst.data(), src, 24 * C, cudaMemcpyDeviceToHost));
+    } else {
+      std::memcpy(dst.data(), src, 24 * C);
+    }
+    return 0;
+  };
+  int rc = 0;
+  if (U) rc = get(U, h->U);
+  else std::fill(h->U.begin(), h->U.end(), 0.0);
+  if (rc) return rc;
+  h->gp_default = grad_p == nullptr;
+  if (grad_p && (rc = get(grad_p, h->gp))) return rc;
+  if (DUDt) rc = get(DUDt, h->du);
+  else std::fill(h->du.begin(), h->du.end(), 0.0);
+  if (rc) return rc;
+  return upload_mesh(h);
+}
+
+int sedi_set_eps(sedi_handle* h, int32_t bed, const double* eps, int32_t mem) {
+  if (!h || !eps) return SEDI_EINVAL;
+  h->err.clear();
+  if (bed != 0) return fail(h, SEDI_EINVAL, "bed %d out of range", bed);
+  const int64_t C = h->P.C;
+  if (mem == SEDI_MEM_DEVICE) {
+    CK(cudaMemcpy(h->eps.data(), eps, 8 * C, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(h->eps.data(), eps, 8 * C);
+  }
+  return upload_mesh(h);
+}
+
+int sedi_step(sedi_handle* h, int32_t n) {
+  int rc = need_particles(h);
+  if (rc) return rc;
+  h->err.clear();
+  if (n < 0) return fail(h, SEDI_EINVAL, "n_substeps must be >= 0");
+  if (n == 0) return 0;
+  if (h->prm.profile) harvest(h);
+  // stream capture needs a real stream: the legacy NULL stream runs without graphs
+  if (h->prm.use_graphs && h->stream != nullptr) {
+    auto it = h->graphs.find(n);
+    cudaGraphExec_t ex;
+    if (it == h->graphs.end()) {
+      if ((rc = build_graph(h, n, &ex))) return rc;
+      h->graphs[n] = ex;
+    } else {
+      ex = it->second;
+    }
+    CK(cudaGraphLaunch(ex, h->stream));
+    if (h->prm.profile) {
+      auto& ev = h->gev[n];
+      for (int s = 0; s < n; ++s) {
+        h->pending.push_back({0, {ev.a[s], ev.b[s]}});
+        h->pending.push_back({1, {ev.b[s], ev.c[s]}});
+      }
+    }
+  } else {
+    if (h->prm.profile && h->gev.find(-n) == h->gev.end()) {
+      sedi_handle::GraphEv ev;
+      for (int s = 0; s < n; ++s) {
+        ev.a.push_back(new_event());
+        ev.b.push_back(new_event());
+        ev.c.push_back(new_event());
+      }
+      h->gev[-n] = ev;
+    }
+    for (int s = 0; s < n; ++s) {
+      if (h->prm.profile) CK(cudaEventRecord(h->gev[-n].a[s], h->stream));
+      launch_check(h->st, h->P, 0ull, 0, h->stream);
+      launch_rebuild(h->form, h->st, h->P, s, false, h->stream);
+      if (h->prm.profile) CK(cudaEventRecord(h->gev[-n].b[s], h->stream));
+      launch_substep(h->form, h->st, h->mesh, h->P, s, true, h->block, h->stream);
+      if (h->prm.profile) {
+        CK(cudaEventRecord(h->gev[-n].c[s], h->stream));
+        h->pending.push_back({0, {h->gev[-n].a[s], h->gev[-n].b[s]}});
+        h->pending.push_back({1, {h->gev[-n].b[s], h->gev[-n].c[s]}});
+      }
+    }
+    launch_advance_parity(h->st, n, h->stream);
+  }
+  CK(cudaGetLastError());
+  h->stats.substeps += n;
+  return 0;
+}
+
+int sedi_sync(sedi_handle* h) {
+  if (!h) return SEDI_EINVAL;
+  return sync_status(h);
+}
+
+// Deposition into h->qfix (split/FP64: int64; plain: float phi directly).
+static int deposit_dev(sedi_handle* h) {
+  const int64_t C = h->P.C;
+  if (h->form == FORM_PLAIN) {
+    CK(cudaMemsetAsync(h->phi, 0, 4 * 7 * C, h->stream));
+    launch_deposit(h->form, h->st, h->mesh, h->P, h->phi, h->stream);
+  } else {
+    CK(cudaMemsetAsync(h->qfix, 0, 8 * 7 * C, h->stream));
+    launch_deposit(h->form, h->st, h->mesh, h->P, h->qfix, h->stream);
+  }
+  CK(cudaGetLastError());
+  return 0;
+}
+
+static int smooth_dev(sedi_handle* h, int nf, const void* guess) {
+  CK(cudaMemsetAsync(h->iters_dev, 0, 4 * 8, h->stream));
+  // FP32 words cannot reach a relative residual much below 1e-6
+  const double rtol = h->form == FORM_PLAIN ? std::max(h->prm.cg_rtol, 2e-6) : h->prm.cg_rtol;
+  int rc = launch_smooth(h->form, h->P, h->phi, guess, nf, h->work, h->st, h->iters_dev,
+                         rtol, h->prm.cg_max_iter, h->prm.n_tau, h->coef, h->stream);
+  if (rc) return fail(h, SEDI_ECUDA, "cooperative launch of the smoother failed: %s", cudaGetErrorString(cudaGetLastError()));
+  return 0;
+}
+
+static int smooth_status(sedi_handle* h, int nf) {
+  int it[8] = {0};
+  CK(cudaMemcpyAsync(it, h->iters_dev, 4 * 8, cudaMemcpyDeviceToHost, h->stream));
+  int rc = sync_status(h);
+  if (rc) return rc;
+  Ctl c;
+  CK(cudaMemcpy(&c, h->st.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  for (int f = 0; f < nf; ++f) h->stats.cg_iterations += it[f];
+  int st = c.cg_status;
+  int dr = c.deposit_range;
+  if (st || dr) {
+    int z = 0;
+    cudaMemcpy((char*)h->st.ctl + offsetof(Ctl, deposit_range), &z, 4, cudaMemcpyHostToDevice);
+    cudaMemcpy((char*)h->st.ctl + offsetof(Ctl, cg_status), &z, 4, cudaMemcpyHostToDevice);
+  }
+  if (dr) return fail(h, SEDI_ERANGE, "a deposited value does not fit the fixed-point format");
+  if (st == SEDI_ETIMEOUT) return fail(h, SEDI_ETIMEOUT, "smoother grid barrier timed out");
+  if (st == SEDI_EDIVERGED) return fail(h, SEDI_EDIVERGED, "smoothing CG reached cg_max_iter");
+  return 0;
+}
+
+int sedi_average(sedi_handle* h, int32_t bed, double* eps, double* Us, double* F, int32_t mem) {
+  int rc = need_particles(h);
+  if (rc) return rc;
+  h->err.clear();
+  if (bed != 0) return fail(h, SEDI_EINVAL, "bed %d out of range", bed);
+  const int64_t C = h->P.C;
+  if (h->prm.profile) {
+    harvest(h);
+    if (h->avg_ev.empty())
+      for (int k = 0; k < 3; ++k) h->avg_ev.push_back(new_event());
+    CK(cudaEventRecord(h->avg_ev[0], h->stream));
+  }
+  if ((rc = deposit_dev(h))) return rc;
+  launch_fields_from_fixed(h->form, h->qfix, h->P, h->phi, 7, h->stream);
+  if (h->prm.profile) CK(cudaEventRecord(h->avg_ev[1], h->stream));
+  if ((rc = smooth_dev(h, 7, nullptr))) return rc;
+  if (h->prm.profile) {
+    CK(cudaEventRecord(h->avg_ev[2], h->stream));
+    h->pending.push_back({2, {h->avg_ev[0], h->avg_ev[1]}});
+    h->pending.push_back({3, {h->avg_ev[1], h->avg_ev[2]}});
+  }
+  double* de = h->dstage;
+  double* du = h->dstage + C;
+  double* dF = h->dstage + 4 * C;
+  launch_average_out(h->form, h->phi, h->P, h->mesh.ufe, de, du, dF, h->stream);
+  if (eps && (rc = copy_out(h, eps, de, 8 * C, mem))) return rc;
+  if (Us && (rc = copy_out(h, Us, du, 24 * C, mem))) return rc;
+  if (F && (rc = copy_out(h, F, dF, 24 * C, mem))) return rc;
+  h->stats.averages += 1;
+  rc = smooth_status(h, 7);
+  // keep the host copy of the drag's solid fraction in step (checkpoints)
+  if (!rc) cudaMemcpy(h->eps.data(), de, 8 * C, cudaMemcpyDeviceToHost);
+  return rc;
+}
+
+int sedi_deposit(sedi_handle* h, int32_t bed, int64_t* q, int32_t mem) {
+  int rc = need_particles(h);
+  if (rc) return rc;
+  h->err.clear();
+  if (bed != 0 || !q) return fail(h, SEDI_EINVAL, "bad bed or null output");
+  const int64_t C = h->P.C;
+  if ((rc = deposit_dev(h))) return rc;
+  if (h->form == FORM_PLAIN) {
+    std::vector<float> f(7 * C);
+    CK(cudaMemcpyAsync(f.data(), h->phi, 4 * 7 * C, cudaMemcpyDeviceToHost, h->stream));
+    if ((rc = sync_status(h))) return rc;
+    std::vector<int64_t> qq(7 * C);
+    for (int k = 0; k < 7; ++k) {
+      const double sc = h->P.two_shift[k == 0 ? 0 : (k < 4 ? 1 : 2)];
+      for (int64_t c = 0; c < C; ++c) qq[k * C + c] = (int64_t)std::llrint((double)f[k * C + c] * sc);
+    }
+    if (mem == SEDI_MEM_DEVICE) {
+      CK(cudaMemcpy(q, qq.data(), 8 * 7 * C, cudaMemcpyHostToDevice));
+    } else {
+      std::memcpy(q, qq.data(), 8 * 7 * C);
+    }
+    return 0;
+  }
+  if ((rc = copy_out(h, q, h->qfix, 8 * 7 * C, mem))) return rc;
+  rc = sync_status(h);
+  if (rc) return rc;
+  Ctl c;
+  CK(cudaMemcpy(&c, h->st.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  if (c.deposit_range) {
+    int z = 0;
+    cudaMemcpy((char*)h->st.ctl + offsetof(Ctl, deposit_range), &z, 4, cudaMemcpyHostToDevice);
+    return fail(h, SEDI_ERANGE, "a deposited value does not fit the fixed-point format");
+  }
+  return 0;
+}
+
+int sedi_smooth(sedi_handle* h, int32_t bed, int32_t nf, const double* in, double* out,
+                const double* guess, int32_t* iters, int32_t mem) {
+  if (!h) return SEDI_EINVAL;
+  h->err.clear();
+  if (bed != 0 || nf < 1 || nf > 8 || !in || !out) return fail(h, SEDI_EINVAL, "bad smoothing arguments (1 <= n_fields <= 8)");
+  const int64_t C = h->P.C;
+  const int64_t n = (int64_t)nf * C;
+  int rc = ensure_stage(h, 2 * n);
+  if (rc) return rc;
+  const size_t wb = h->form == FORM_PLAIN ? 4 : 8;
+  if ((rc = copy_in(h, h->dstage, in, 8 * n, mem))) return rc;
+  launch_phi_from_double(h->form, h->dstage, h->phi, n, h->stream);
+  void* gdev = nullptr;
+  if (guess) {
+    if ((rc = copy_in(h, h->dstage + n, guess, 8 * n, mem))) return rc;
+    gdev = h->qfix;  // [7][C] int64 space reused as the guess buffer
+    if (nf * C * wb > (size_t)8 * 7 * C) return fail(h, SEDI_EINVAL, "guess supports at most 7 fields");
+    launch_phi_from_double(h->form, h->dstage + n, gdev, n, h->stream);
+  }
+  if ((rc = smooth_dev(h, nf, gdev))) return rc;
+  launch_phi_convert(h->form, h->phi, h->dstage, n, 1, h->stream);
+  if ((rc = copy_out(h, out, h->dstage, 8 * n, mem))) return rc;
+  int it[8] = {0};
+  CK(cudaMemcpyAsync(it, h->iters_dev, 4 * 8, cudaMemcpyDeviceToHost, h->stream));
+  rc = smooth_status(h, nf);
+  if (iters)
+    for (int f = 0; f < nf; ++f) iters[f] = it[f];
+  return rc;
+}
+
+int sedi_get_particles(sedi_handle* h, int32_t bed, double* x, double* v, double* w, double* a,
+                       int32_t mem) {
+  int rc = need_particles(h);
+  if (rc) return rc;
+  h->err.clear();
+  if (bed != 0) return fail(h, SEDI_EINVAL, "bed %d out of range", bed);
+  const int64_t N = h->N;
+  double* outs[4] = {x, v, w, a};
+  for (int k = 0; k < 4; ++k) {
+    if (!outs[k]) continue;
+    launch_export(h->form, h->st, k, h->dstage + 3 * N * k, h->stream);
+    if ((rc = copy_out(h, outs[k], h->dstage + 3 * N * k, 24 * N, mem))) return rc;
+  }
+  return sync_status(h);
+}
+
+int sedi_compute_forces(sedi_handle* h, int32_t bed, double* fc, double* fl, double* ff,
+                        double* tq, int32_t mem) {
+  int rc = need_particles(h);
+  if (rc) return rc;
+  h->err.clear();
+  if (bed != 0) return fail(h, SEDI_EINVAL, "bed %d out of range", bed);
+  const int64_t N = h->N;
+  // lists must cover the current positions
+  launch_check(h->st, h->P, 0ull, 0, h->stream);
+  launch_rebuild(h->form, h->st, h->P, 0, false, h->stream);
+  launch_substep(h->form, h->st, h->mesh, h->P, 0, false, h->block, h->stream);
+  // fdbg is in sorted order: scatter to caller order through the host
+  std::vector<double> dbg(12 * N);
+  std::vector<int32_t> uid(N);
+  CK(cudaMemcpyAsync(dbg.data(), h->st.fdbg, 8 * 12 * N, cudaMemcpyDeviceToHost, h->stream));
+  if ((rc = sync_status(h))) return rc;
+  Ctl c;
+  CK(cudaMemcpy(&c, h->st.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(uid.data(), h->st.uid[c.pb], 4 * N, cudaMemcpyDeviceToHost));
+  double* outs[4] = {fc, fl, ff, tq};
+  std::vector<double> tmp(3 * N);
+  for (int k = 0; k < 4; ++k) {
+    if (!outs[k]) continue;
+    for (int64_t i = 0; i < N; ++i)
+      for (int a = 0; a < 3; ++a) tmp[3 * uid[i] + a] = dbg[3 * N * k + 3 * i + a];
+    if (mem == SEDI_MEM_DEVICE) {
+      CK(cudaMemcpy(outs[k], tmp.data(), 24 * N, cudaMemcpyHostToDevice));
+    } else {
+      std::memcpy(outs[k], tmp.data(), 24 * N);
+    }
+  }
+  return 0;
+}
+
+int64_t sedi_get_neighbors(sedi_handle* h, int32_t bed, int64_t* offsets, int64_t* ids, int64_t cap) {
+  int rc = need_particles(h);
+  if (rc) return rc;
+  h->err.clear();
+  if (bed != 0 || !offsets) return fail(h, SEDI_EINVAL, "bad arguments");
+  const int64_t N = h->N;
+  int64_t* dcnt = nullptr;
+  CK(cudaMalloc((void**)&dcnt, 8 * (N + 1)));
+  launch_neighbors_export(h->st, dcnt, h->stream);
+  std::vector<int64_t> cnt(N);
+  cudaMemcpyAsync(cnt.data(), dcnt, 8 * N, cudaMemcpyDeviceToHost, h->stream);
+  if ((rc = sync_status(h))) {
+    cudaFree(dcnt);
+    return rc;
+  }
+  offsets[0] = 0;
+  for (int64_t i = 0; i < N; ++i) offsets[i + 1] = offsets[i] + cnt[i];
+  const int64_t total = offsets[N];
+  if (!ids || total > cap) {
+    cudaFree(dcnt);
+    return ids ? fail(h, SEDI_EOVERFLOW, "cap %lld < %lld entries", (long long)cap, (long long)total) : total;
+  }
+  int64_t* dout = nullptr;
+  if (cudaMalloc((void**)&dout, 8 * std::max<int64_t>(total, 1)) != cudaSuccess) {
+    cudaFree(dcnt);
+    return fail(h, SEDI_ENOMEM, "neighbour export buffer");
+  }
+  cudaMemcpyAsync(dcnt, offsets, 8 * (N + 1), cudaMemcpyHostToDevice, h->stream);
+  launch_neighbors_fill(h->st, dcnt, dout, h->stream);
+  cudaMemcpyAsync(ids, dout, 8 * total, cudaMemcpyDeviceToHost, h->stream);
+  rc = sync_status(h);
+  cudaFree(dout);
+  cudaFree(dcnt);
+  if (rc) return rc;
+  if (!h->ids.empty())
+    for (int64_t k = 0; k < total; ++k) ids[k] = h->ids[ids[k]];
+  return total;
+}
+
+int64_t sedi_get_contacts(sedi_handle* h, int32_t bed, int64_t cap, int64_t* ij, double* xi) {
+  int rc = need_particles(h);
+  if (rc) return rc;
+  h->err.clear();
+  if (bed != 0) return fail(h, SEDI_EINVAL, "bad bed");
+  unsigned long long* dc = nullptr;
+  int64_t* dij = nullptr;
+  double* dxi = nullptr;
+  const int64_t c2 = std::max<int64_t>(cap, 1);
+  CK(cudaMalloc((void**)&dc, 8));
+  CK(cudaMalloc((void**)&dij, 16 * c2));
+  CK(cudaMalloc((void**)&dxi, 24 * c2));
+  cudaMemsetAsync(dc, 0, 8, h->stream);
+  launch_contacts_export(h->form, h->st, h->P, dc, cap, dij, dxi, h->stream);
+  unsigned long long m = 0;
+  cudaMemcpyAsync(&m, dc, 8, cudaMemcpyDeviceToHost, h->stream);
+  rc = sync_status(h);
+  std::vector<int64_t> vij;
+  std::vector<double> vxi;
+  if (!rc && (int64_t)m <= cap && m > 0) {
+    vij.resize(2 * m);
+    vxi.resize(3 * m);
+    cudaMemcpy(vij.data(), dij, 16 * m, cudaMemcpyDeviceToHost);
+    cudaMemcpy(vxi.data(), dxi, 24 * m, cudaMemcpyDeviceToHost);
+  }
+  cudaFree(dc);
+  cudaFree(dij);
+  cudaFree(dxi);
+  if (rc) return rc;
+  if ((int64_t)m > cap) return fail(h, SEDI_EOVERFLOW, "%llu contacts > cap", m);
+  std::vector<int64_t> order(m);
+  for (int64_t k = 0; k < (int64_t)m; ++k) order[k] = k;
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    return vij[2 * a] != vij[2 * b] ? vij[2 * a] < vij[2 * b] : vij[2 * a + 1] < vij[2 * b + 1];
+  });
+  for (int64_t k = 0; k < (int64_t)m; ++k) {
+    const int64_t o = order[k];
+    if (ij) {
+      ij[2 * k] = vij[2 * o];
+      ij[2 * k + 1] = vij[2 * o + 1];
+    }
+    if (xi)
+      for (int a = 0; a < 3; ++a) xi[3 * k + a] = vxi[3 * o + a];
+  }
+  return (int64_t)m;
+}
+
+// ---------------------------------------------------------------- checkpoints
+// Raw device words of the current buffers, so a resumed run is bit-identical.
+namespace {
+struct CkHeader {
+  char magic[8];
+  int32_t version, form, cap, pad;
+  int64_t N, C, nbins;
+  sedi_stats stats;
+};
+
+int ck_write(FILE* f, const void* p, size_t n) { return fwrite(p, 1, n, f) == n ? 0 : -1; }
+int ck_read(FILE* f, void* p, size_t n) { return fread(p, 1, n, f) == n ? 0 : -1; }
+
+int dev_io(sedi_handle* h, FILE* f, void* dptr, size_t bytes, bool save) {
+  std::vector<char> buf(bytes);
+  if (save) {
+    CK(cudaMemcpy(buf.data(), dptr, bytes, cudaMemcpyDeviceToHost));
+    if (ck_write(f, buf.data(), bytes)) return fail(h, SEDI_EIO, "checkpoint write failed");
+  } else {
+    if (ck_read(f, buf.data(), bytes)) return fail(h, SEDI_EIO, "checkpoint read failed");
+    CK(cudaMemcpy(dptr, buf.data(), bytes, cudaMemcpyHostToDevice));
+  }
+  return 0;
+}
+
+int state_io(sedi_handle* h, FILE* f, bool save) {
+  const int64_t N = h->N, C = h->P.C, cap = h->P.cap;
+  const size_t q = quad_bytes(h->form), fq = fquad_bytes(h->form), w = word_bytes(h->form);
+  Ctl c;
+  CK(cudaMemcpy(&c, h->st.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  int rc;
+  DevState& s = h->st;
+  struct Item { void* p; size_t n; };
+  std::vector<Item> items = {
+      {s.pos[c.st], q * N}, {s.vel[c.st], q * N}, {s.omg[c.st], q * N},
+      {s.acc[c.pb], fq * N}, {s.uid[c.pb], 4 * (size_t)N}, {s.r64[c.pb], 8 * (size_t)N},
+      {s.vfrac[c.pb], 8 * (size_t)N}, {s.xb[c.pb], 16 * (size_t)N},
+      {s.whist[c.pb], (size_t)kWalls * 3 * w * N}, {s.wmask[c.pb], 4 * (size_t)N},
+      {s.nbr[c.nl], 4 * (size_t)cap * N}, {s.nn[c.nl], 4 * (size_t)N},
+      {s.hist[c.nl], 3 * w * cap * N}, {s.cmask[c.nl], 4 * (size_t)N},
+      {h->mesh.ufe, fq * C}, {h->mesh.gfl, fq * C}};
+  for (auto& it : items)
+    if ((rc = dev_io(h, f, it.p, it.n, save))) return rc;
+  if (save) {
+    if (ck_write(f, &c, sizeof(Ctl))) return fail(h, SEDI_EIO, "checkpoint write failed");
+  } else {
+    Ctl in;
+    if (ck_read(f, &in, sizeof(Ctl))) return fail(h, SEDI_EIO, "checkpoint read failed");
+    // keep the buffer parities of this handle (data were loaded into them)
+    in.st = c.st;
+    in.pb = c.pb;
+    in.nl = c.nl;
+    CK(cudaMemcpy(h->st.ctl, &in, sizeof(Ctl), cudaMemcpyHostToDevice));
+  }
+  return 0;
+}
+}  // namespace
+
+int sedi_save_state(sedi_handle* h, const char* path) {
+  int rc = need_particles(h);
+  if (rc) return rc;
+  h->err.clear();
+  if ((rc = sync_status(h))) return rc;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(h, SEDI_EIO, "cannot open %s", path);
+  CkHeader hd{};
+  std::memcpy(hd.magic, "SEDICK01", 8);
+  hd.version = 1;
+  hd.form = h->form;
+  hd.cap = h->P.cap;
+  hd.N = h->N;
+  hd.C = h->P.C;
+  hd.nbins = h->P.nbins;
+  hd.stats = h->stats;
+  rc = ck_write(f, &hd, sizeof(hd)) ? fail(h, SEDI_EIO, "write failed") : 0;
+  if (!rc) rc = ck_write(f, h->d_host.data(), 8 * h->N) || ck_write(f, h->rho_host.data(), 8 * h->N) ? fail(h, SEDI_EIO, "write failed") : 0;
+  int64_t nid = (int64_t)h->ids.size();
+  if (!rc) rc = ck_write(f, &nid, 8) ? fail(h, SEDI_EIO, "write failed") : 0;
+  if (!rc && nid) rc = ck_write(f, h->ids.data(), 8 * nid) ? fail(h, SEDI_EIO, "write failed") : 0;
+  const int64_t C = h->P.C;
+  if (!rc) rc = (ck_write(f, h->U.data(), 24 * C) || ck_write(f, h->gp.data(), 24 * C) ||
+                 ck_write(f, h->du.data(), 24 * C) || ck_write(f, h->eps.data(), 8 * C))
+                    ? fail(h, SEDI_EIO, "write failed") : 0;
+  int gpd = h->gp_default ? 1 : 0;
+  if (!rc) rc = ck_write(f, &gpd, 4) ? fail(h, SEDI_EIO, "write failed") : 0;
+  if (!rc) rc = state_io(h, f, true);
+  std::fclose(f);
+  return rc;
+}
+
+int sedi_load_state(sedi_handle* h, const char* path) {
+  if (!h) return SEDI_EINVAL;
+  h->err.clear();
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(h, SEDI_EIO, "cannot open %s", path);
+  CkHeader hd{};
+  int rc = 0;
+  if (ck_read(f, &hd, sizeof(hd)) || std::memcmp(hd.magic, "SEDICK01", 8) != 0) rc = fail(h, SEDI_EIO, "not a checkpoint of this library");
+  if (!rc && (hd.form != h->form || hd.C != h->P.C))
+    rc = fail(h, SEDI_EINVAL, "checkpoint form/mesh differ from this handle");
+  std::vector<double> d, rho;
+  std::vector<int64_t> ids;
+  if (!rc) {
+    d.resize(hd.N);
+    rho.resize(hd.N);
+    if (ck_read(f, d.data(), 8 * hd.N) || ck_read(f, rho.data(), 8 * hd.N)) rc = fail(h, SEDI_EIO, "read failed");
+  }
+  int64_t nid = 0;
+  if (!rc && ck_read(f, &nid, 8)) rc = fail(h, SEDI_EIO, "read failed");
+  if (!rc && nid) {
+    ids.resize(nid);
+    if (ck_read(f, ids.data(), 8 * nid)) rc = fail(h, SEDI_EIO, "read failed");
+  }
+  const int64_t C = h->P.C;
+  int gpd = 1;
+  if (!rc && (ck_read(f, h->U.data(), 24 * C) || ck_read(f, h->gp.data(), 24 * C) ||
+              ck_read(f, h->du.data(), 24 * C) || ck_read(f, h->eps.data(), 8 * C) || ck_read(f, &gpd, 4)))
+    rc = fail(h, SEDI_EIO, "read failed");
+  if (!rc) {
+    h->gp_default = gpd != 0;
+    double rmax = 0;
+    for (double di : d) rmax = std::max(rmax, 0.5 * di);
+    h->P.cap = hd.cap;
+    h->have_particles = false;
+    rc = alloc_particles(h, hd.N, rmax);
+    if (!rc && h->P.nbins != hd.nbins) rc = fail(h, SEDI_EINVAL, "checkpoint binning differs");
+  }
+  if (!rc) {
+    h->N = hd.N;
+    h->d_host = d;
+    h->rho_host = rho;
+    h->ids = ids;
+    Ctl zero{};
+    cudaMemcpy(h->st.ctl, &zero, sizeof(Ctl), cudaMemcpyHostToDevice);
+    rc = state_io(h, f, false);
+  }
+  std::fclose(f);
+  if (rc) return rc;
+  h->stats = hd.stats;
+  h->have_particles = true;
+  return 0;
+}
+
+int sedi_get_timings(sedi_handle* h, double* ms, int32_t n) {
+  if (!h || !ms) return SEDI_EINVAL;
+  if (!h->prm.profile) return 0;
+  harvest(h);
+  int k = 0;
+  for (; k < n && k < 8; ++k) ms[k] = k < 4 ? h->ms[k] : h->cnt[k - 4];
+  return k;
+}
+
+int sedi_get_stats(sedi_handle* h, sedi_stats* out) {
+  if (!h || !out) return SEDI_EINVAL;
+  int rc = h->have_particles ? sync_status(h) : 0;
+  h->stats.nbr_capacity = h->P.cap;
+  *out = h->stats;
+  return rc;
+}
+
+const char* sedi_last_error(const sedi_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// Fluid-particle force at one particle, shared by the substep and the
+// deposition kernels so both evaluate f_fp with the same code.
+#pragma once
+#include "common.cuh"
+#include "fmath.cuh"
+
+namespace sedi {
+
+// Per-axis trilinear weights of a cell-centred field (periodic wrap, else clamp).
+template <class F>
+__device__ __forceinline__ void axis_w(F s, int n, int per, int* i0, int* i1, F* f) {
+  if (per) {
+    F fl = xfloor(s);
+    *f = s - fl;
+    int k = (int)fl;
+    k %= n;
+    if (k < 0) k += n;
+    *i0 = k;
+    *i1 = (k + 1 == n) ? 0 : k + 1;
+  } else {
+    if (s < F(0)) s = F(0);
+    if (s > F(n - 1)) s = F(n - 1);
+    int k = (int)xfloor(s);
+    if (n >= 2 && k > n - 2) k = n - 2;
+    if (n < 2) k = 0;
+    *i0 = k;
+    *i1 = n >= 2 ? k + 1 : 0;
+    *f = n >= 2 ? s - F(k) : F(0);
+  }
+}
+
+// Fluid force on one particle (Sec. 2.3): drag (Eq. 3-6, Syamlal-O'Brien), the
+// pressure-gradient force and added mass (Eq. 8).  The mesh carries
+// G = -grad p + C_add rho_f DU/Dt so both linear terms come from one
+// interpolation.  Drag is written in a form without 1/Re:
+//   C_d |w| = (0.63 sqrt|w| + 4.8 sqrt(V_r nu / d))^2.
+template <class S, class F>
+__device__ __forceinline__ void fluid_force(const DevParams& P, const ForceConsts<F>& K,
+                                            const Quad<F>* ufe, const Quad<F>* gfl, const S* x,
+                                            F r, const F v[3], const F a_prev[3], F out[3]) {
+  using NS = Num<S>;
+  const BoxS<S>& B = sbox<S>(P);
+  int i0[3], i1[3];
+  F fr[3];
+  for (int a = 0; a < 3; ++a) {
+    F rel = NS::f(NS::sub(x[a], B.lo[a]));
+    F s = rel * K.inv_h[a] - F(0.5);
+    axis_w<F>(s, P.nc[a], P.periodic[a], &i0[a], &i1[a], &fr[a]);
+  }
+  F U[3] = {0, 0, 0}, G[3] = {0, 0, 0}, eps = 0;
+  const int64_t nx = P.nc[0], ny = P.nc[1];
+  for (int kz = 0; kz < 2; ++kz) {
+    int iz = kz ? i1[2] : i0[2];
+    F wz = kz ? fr[2] : F(1) - fr[2];
+    for (int ky = 0; ky < 2; ++ky) {
+      int iy = ky ? i1[1] : i0[1];
+      F wy = ky ? fr[1] : F(1) - fr[1];
+      for (int kx = 0; kx < 2; ++kx) {
+        int ix = kx ? i1[0] : i0[0];
+        F wx = kx ? fr[0] : F(1) - fr[0];
+        int64_t c = ((int64_t)iz * ny + iy) * nx + ix;
+        F w = wz * wy * wx;
+        Quad<F> u = ldq(ufe + c);
+        U[0] += w * u.a;
+        U[1] += w * u.b;
+        U[2] += w * u.c;
+        eps += w * u.d;
+        if (P.pressure_grad || P.added_mass) {
+          Quad<F> g = ldq(gfl + c);
+          G[0] += w * g.a;
+          G[1] += w * g.b;
+          G[2] += w * g.c;
+        }
+      }
+    }
+  }
+  F d = F(2) * r;
+  F Vp = F(0.52359877559829887) * d * d * d;  // pi/6 d^3
+  out[0] = Vp * G[0];
+  out[1] = Vp * G[1];
+  out[2] = Vp * G[2];
+  if (P.added_mass) {
+    out[0] -= K.c_add_rho_f * Vp * a_prev[0];
+    out[1] -= K.c_add_rho_f * Vp * a_prev[1];
+    out[2] -= K.c_add_rho_f * Vp * a_prev[2];
+  }
+  if (P.drag) {
+    F es = eps < F(0) ? F(0) : eps;
+    if (es > K.eps_max) es = K.eps_max;
+    F ef = F(1) - es;
+    F w0 = U[0] - v[0], w1 = U[1] - v[1], w2 = U[2] - v[2];
+    F wm = xsqrt(w0 * w0 + w1 * w1 + w2 * w2);
+    F Re = d * wm / K.nu_f;
+    F A1 = xpow(ef, F(4.14));
+    F A2 = ef <= F(0.85) ? F(0.8) * xpow(ef, F(1.28)) : xpow(ef, F(2.65));
+    F t = F(0.06) * Re;
+    F Vr = F(0.5) * (A1 - t + xsqrt(t * t + F(0.12) * Re * (F(2) * A2 - A1) + A1 * A1));
+    F c = F(0.63) * xsqrt(wm) + F(4.8) * xsqrt(Vr * K.nu_f / d);
+    F coef = F(0.75) * Vp * K.rho_f * c * c / (Vr * Vr * d);
+    out[0] += coef * w0;
+    out[1] += coef * w1;
+    out[2] += coef * w2;
+  }
+}
+
+}  // namespace sedi

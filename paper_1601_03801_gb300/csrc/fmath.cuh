@@ -1,0 +1,17 @@
+// Overloads of the few math functions the generic kernels use, for FP32 and FP64
+// force words (CUDA's own correctly rounded sqrt and its pow/floor).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace sedi {
+__device__ __forceinline__ float xsqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double xsqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float xpow(float a, float b) { return powf(a, b); }
+__device__ __forceinline__ double xpow(double a, double b) { return pow(a, b); }
+__device__ __forceinline__ float xfloor(float a) { return floorf(a); }
+__device__ __forceinline__ double xfloor(double a) { return floor(a); }
+__device__ __forceinline__ float xabs(float a) { return fabsf(a); }
+__device__ __forceinline__ double xabs(double a) { return fabs(a); }
+__device__ __forceinline__ bool xisfinite(float a) { return isfinite(a); }
+__device__ __forceinline__ bool xisfinite(double a) { return isfinite(a); }
+}  // namespace sedi

@@ -1,0 +1,603 @@
+// Diffusion-based averaging (Sec. 2.4, Eq. 9-10).
+//
+// Deposition (Eq. 9, PCM): each particle adds V_p/V_c, V_p u_p/V_c and
+// -f_fp/V_c to the cell holding its centre.  The split and FP64 forms round each
+// value to 64-bit fixed point (round to nearest even, one exponent per field kind)
+// and add with integer atomics, so the sums do not depend on the order of the
+// additions and match an exact integer sum bit for bit.  The plain FP32 form adds
+// floats.
+//
+// Smoothing (Eq. 10): n_tau backward-Euler steps (I - dtau div D grad) x = b of
+// the 7-point finite-volume Laplacian (zero flux through non-periodic faces),
+// each solved by plain conjugate gradients to ||r|| <= rtol ||b||, all fields at
+// once in ONE persistent cooperative launch.  Per iteration two grid barriers:
+//   A: p = r + beta p_old (formed on the fly at the stencil points), q = A p, p.q
+//   B: x += alpha p, r -= alpha q, r.r
+// Every block reduces the per-block partials in the same fixed order, so all
+// blocks take identical decisions and the result is run-to-run deterministic.
+// The grid barrier spins at most ~1 s, then records SEDI_ETIMEOUT and returns.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "fluid.cuh"
+#include "kernels.h"
+
+namespace sedi {
+
+namespace {
+
+constexpr int kMaxF = 8;
+constexpr int kSmoothThreads = 512;
+
+// ---------------------------------------------------------------- deposition
+template <int FORM>
+__global__ void k_deposit(DevState st, DevMesh mesh, DevParams P, void* qout) {
+  using S = typename Traits<FORM>::S;
+  using F = typename Traits<FORM>::F;
+  using NS = Num<S>;
+  const ForceConsts<F>& K = fconsts<F>(P);
+  const int sb = st.ctl->st, pb = st.ctl->pb;
+  const int64_t C = P.C;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < st.N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const Quad<S> p = ldq((const Quad<S>*)st.pos[sb] + i);
+    const Quad<S> v = ldq((const Quad<S>*)st.vel[sb] + i);
+    const Quad<F> acc = ldq((const Quad<F>*)st.acc[pb] + i);
+    const S xs[3] = {p.a, p.b, p.c};
+    int64_t cc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double s = __dmul_rn(__dsub_rn(NS::d(xs[a]), P.lo[a]), P.inv_h[a]);
+      int64_t k = (int64_t)floor(s);
+      if (k < 0) k = 0;
+      if (k > P.nc[a] - 1) k = P.nc[a] - 1;
+      cc[a] = k;
+    }
+    const int64_t cell = (cc[2] * P.nc[1] + cc[1]) * P.nc[0] + cc[0];
+    const F vf[3] = {NS::f(v.a), NS::f(v.b), NS::f(v.c)};
+    const F ap[3] = {acc.a, acc.b, acc.c};
+    F ff[3];
+    fluid_force<S, F>(P, K, (const Quad<F>*)mesh.ufe, (const Quad<F>*)mesh.gfl, xs, NS::f(p.d), vf,
+                      ap, ff);
+    const double vfrac = st.vfrac[pb][i];
+    double val[7];
+    val[0] = vfrac;
+    val[1] = __dmul_rn(vfrac, NS::d(v.a));
+    val[2] = __dmul_rn(vfrac, NS::d(v.b));
+    val[3] = __dmul_rn(vfrac, NS::d(v.c));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) val[4 + a] = __ddiv_rn(-(double)ff[a], P.vc);
+    if (FORM == FORM_PLAIN) {
+      float* q = (float*)qout;
+#pragma unroll
+      for (int f = 0; f < 7; ++f) atomicAdd(q + f * C + cell, (float)val[f]);
+    } else {
+      unsigned long long* q = (unsigned long long*)qout;
+#pragma unroll
+      for (int f = 0; f < 7; ++f) {
+        const double sc = P.two_shift[f == 0 ? 0 : (f < 4 ? 1 : 2)];
+        const double t = __dmul_rn(val[f], sc);
+        if (!(fabs(t) < 4.0e18)) {
+          atomicCAS((int*)&st.ctl->deposit_range, 0, 1);
+          continue;
+        }
+        const long long qi = __double2ll_rn(t);
+        atomicAdd(q + f * C + cell, (unsigned long long)qi);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- CG words
+template <class T>
+struct CgA;
+template <>
+struct CgA<double> {
+  __device__ static double zero() { return 0.0; }
+  __device__ static double add(double a, double b) { return a + b; }
+  __device__ static double sub(double a, double b) { return a - b; }
+  __device__ static double mul(double a, double b) { return a * b; }
+  __device__ static double from_d(double a) { return a; }
+  __device__ static double to_d(double a) { return a; }
+  __device__ static double shfl_xor(double a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+};
+template <>
+struct CgA<float> {
+  __device__ static float zero() { return 0.0f; }
+  __device__ static float add(float a, float b) { return a + b; }
+  __device__ static float sub(float a, float b) { return a - b; }
+  __device__ static float mul(float a, float b) { return a * b; }
+  __device__ static float from_d(double a) { return __double2float_rn(a); }
+  __device__ static double to_d(float a) { return (double)a; }
+  __device__ static float shfl_xor(float a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+};
+template <>
+struct CgA<dd> {
+  __device__ static dd zero() { return dd{0.0f, 0.0f}; }
+  __device__ static dd add(dd a, dd b) { return dd_add(a, b); }
+  __device__ static dd sub(dd a, dd b) { return dd_sub(a, b); }
+  __device__ static dd mul(dd a, dd b) { return dd_mul(a, b); }
+  __device__ static dd from_d(double a) { return dd_from_double(a); }
+  __device__ static double to_d(dd a) { return dd_to_double(a); }
+  __device__ static dd shfl_xor(dd a, int o) {
+    return dd{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+  }
+};
+
+struct SmoothArgs {
+  void* x;            // [nf][C] in: fields, out: smoothed
+  void* b;            // [nf][C] right-hand side of the current pseudo-step
+  void* r;            // [nf][C]
+  void* p[2];         // [nf][C] search directions (double-buffered)
+  void* q;            // [nf][C] A p
+  const void* guess;  // [nf][C] or null
+  double* part;       // [2][kMaxF][grid]
+  int* iters;         // [nf]
+  int nf;
+  int64_t C;
+  int nc[3];
+  int per[3];
+  double coef[3];     // dtau * D_a / h_a^2
+  double rtol2;
+  int max_iter;
+  int n_tau;
+  Ctl* ctl;
+};
+
+// Bounded grid barrier (co-residency guaranteed by the cooperative launch).
+__device__ bool grid_barrier(Ctl* ctl, unsigned nblocks) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = &ctl->bar_gen;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&ctl->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&ctl->bar_gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == g) {
+        if (++spins > (1ll << 24)) {
+          atomicCAS((int*)&ctl->cg_status, 0, -8);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *((volatile int*)&ctl->cg_status) != -8;
+}
+
+// Block-reduce nf per-thread partials (fixed order), thread 0 writes part[f][blk].
+template <class T>
+__device__ void block_partials(T* acc, int nf, double* part_slot, unsigned nblk) {
+  using A = CgA<T>;
+  __shared__ double wred[kMaxF][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int f = 0; f < nf; ++f) {
+    T v = acc[f];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = A::add(v, A::shfl_xor(v, o));
+    if (lane == 0) wred[f][wid] = A::to_d(v);
+  }
+  __syncthreads();
+  if (wid == 0) {
+    for (int f = 0; f < nf; ++f) {
+      double v = lane < nw ? wred[f][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) part_slot[(int64_t)f * nblk + blockIdx.x] = v;
+    }
+  }
+  __syncthreads();
+}
+
+// Every block sums part[f][0..nblk) in the same order; result in out[f] (shared).
+__device__ void grid_sums(const double* part_slot, int nf, unsigned nblk, double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (wid == 0) {
+    for (int f = 0; f < nf; ++f) {
+      double v = 0.0;
+      for (unsigned b = lane; b < nblk; b += 32) v += __ldcg(part_slot + (int64_t)f * nblk + b);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) out[f] = v;
+    }
+  }
+  __syncthreads();
+}
+
+// Loads of words written by other blocks of the same launch: L2 only (ld.cg),
+// so no stale L1 line is read after a grid barrier.
+__device__ __forceinline__ double ldx(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float ldx(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ dd ldx(const dd* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return dd{v.x, v.y};
+}
+
+template <class T>
+__device__ __forceinline__ T stencil_val(const T* r, const T* pold, T beta, bool first, int64_t c) {
+  using A = CgA<T>;
+  const T rv = ldx(r + c);
+  if (first) return rv;
+  return A::add(rv, A::mul(beta, ldx(pold + c)));
+}
+
+// y = A v at cell c; v(c') given by the functor.
+template <class T, class Get>
+__device__ __forceinline__ T apply_A(const SmoothArgs& a, const T* cf, int64_t c, Get get) {
+  using A = CgA<T>;
+  const int nx = a.nc[0], ny = a.nc[1], nz = a.nc[2];
+  const int ix = (int)(c % nx);
+  const int iy = (int)((c / nx) % ny);
+  const int iz = (int)(c / ((int64_t)nx * ny));
+  const T vc = get(c);
+  T lap = A::zero();
+  const int idx[3] = {ix, iy, iz};
+  const int n[3] = {nx, ny, nz};
+  const int64_t stride[3] = {1, nx, (int64_t)nx * ny};
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+#pragma unroll
+    for (int s = -1; s <= 1; s += 2) {
+      int t = idx[ax] + s;
+      int64_t cn;
+      if (t < 0 || t >= n[ax]) {
+        if (!a.per[ax]) continue;
+        t = (t + n[ax]) % n[ax];
+      }
+      cn = c + (int64_t)(t - idx[ax]) * stride[ax];
+      lap = A::add(lap, A::mul(cf[ax], A::sub(get(cn), vc)));
+    }
+  }
+  return A::sub(vc, lap);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kSmoothThreads) k_smooth(SmoothArgs a) {
+  using A = CgA<T>;
+  const unsigned G = gridDim.x;
+  const int64_t nthr = (int64_t)G * blockDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nf = a.nf;
+  const int64_t C = a.C;
+  T* X = (T*)a.x;
+  T* Bv = (T*)a.b;
+  T* R = (T*)a.r;
+  T* Q = (T*)a.q;
+  const T cf[3] = {A::from_d(a.coef[0]), A::from_d(a.coef[1]), A::from_d(a.coef[2])};
+  __shared__ double s_bb[kMaxF], s_rr[kMaxF], s_tmp[kMaxF], s_tmp2[kMaxF];
+  __shared__ int s_active[kMaxF];
+  int iters[kMaxF];
+  for (int f = 0; f < kMaxF; ++f) iters[f] = 0;
+  T acc[kMaxF], acc2[kMaxF];
+  double* part0 = a.part;
+  double* part1 = a.part + (int64_t)kMaxF * G;
+
+  for (int m = 0; m < a.n_tau; ++m) {
+    // b = x (and optional projected guess on the first pseudo-step)
+    const bool use_guess = (m == 0 && a.guess != nullptr);
+    for (int f = 0; f < nf; ++f) { acc[f] = A::zero(); acc2[f] = A::zero(); }
+    for (int64_t c = tid; c < C; c += nthr)
+      for (int f = 0; f < nf; ++f) {
+        const T xv = ldx(X + f * C + c);
+        Bv[f * C + c] = xv;
+        if (use_guess) {
+          acc[f] = A::add(acc[f], xv);
+          acc2[f] = A::add(acc2[f], ldx((const T*)a.guess + f * C + c));
+        }
+      }
+    if (use_guess) {
+      block_partials<T>(acc, nf, part0, G);
+      block_partials<T>(acc2, nf, part1, G);
+      if (!grid_barrier(a.ctl, G)) return;
+      grid_sums(part0, nf, G, s_tmp);
+      grid_sums(part1, nf, G, s_tmp2);
+      for (int f = 0; f < nf; ++f) {
+        const T shift = A::from_d((s_tmp[f] - s_tmp2[f]) / (double)C);
+        for (int64_t c = tid; c < C; c += nthr)
+          X[f * C + c] = A::add(ldx((const T*)a.guess + f * C + c), shift);
+      }
+    }
+    if (!grid_barrier(a.ctl, G)) return;
+    // r = b - A x ; partials b.b and r.r
+    for (int f = 0; f < nf; ++f) { acc[f] = A::zero(); acc2[f] = A::zero(); }
+    for (int64_t c = tid; c < C; c += nthr)
+      for (int f = 0; f < nf; ++f) {
+        const T* xf = X + f * C;
+        const T ax = apply_A<T>(a, cf, c, [&](int64_t k) { return ldx(xf + k); });
+        const T bv = ldx(Bv + f * C + c);
+        const T rv = A::sub(bv, ax);
+        R[f * C + c] = rv;
+        acc[f] = A::add(acc[f], A::mul(bv, bv));
+        acc2[f] = A::add(acc2[f], A::mul(rv, rv));
+      }
+    block_partials<T>(acc, nf, part0, G);
+    block_partials<T>(acc2, nf, part1, G);
+    if (!grid_barrier(a.ctl, G)) return;
+    grid_sums(part0, nf, G, s_bb);
+    grid_sums(part1, nf, G, s_rr);
+    if (threadIdx.x == 0)
+      for (int f = 0; f < nf; ++f)
+        s_active[f] = (s_bb[f] > 0.0) && (s_rr[f] > a.rtol2 * s_bb[f]);
+    __syncthreads();
+    // fields with b = 0 have x = 0
+    for (int f = 0; f < nf; ++f)
+      if (!(s_bb[f] > 0.0))
+        for (int64_t c = tid; c < C; c += nthr) X[f * C + c] = A::zero();
+    double beta[kMaxF];
+    for (int f = 0; f < kMaxF; ++f) beta[f] = 0.0;
+    int any = 0;
+    for (int f = 0; f < nf; ++f) any |= s_active[f];
+    int it = 0;
+    while (any && it < a.max_iter) {
+      ++it;
+      const bool first = (it == 1);
+      const T* Pold = (const T*)a.p[it & 1];
+      T* Pnew = (T*)a.p[(it & 1) ^ 1];
+      // phase A: p = r + beta p_old ; q = A p ; p.q
+      for (int f = 0; f < nf; ++f) acc[f] = A::zero();
+      for (int f = 0; f < nf; ++f) {
+        if (!s_active[f]) continue;
+        const T bt = A::from_d(beta[f]);
+        const T* rf = R + f * C;
+        const T* pf = Pold + f * C;
+        for (int64_t c = tid; c < C; c += nthr) {
+          const T pc = stencil_val<T>(rf, pf, bt, first, c);
+          const T qv = apply_A<T>(a, cf, c, [&](int64_t k) { return stencil_val<T>(rf, pf, bt, first, k); });
+          Pnew[f * C + c] = pc;
+          Q[f * C + c] = qv;
+          acc[f] = A::add(acc[f], A::mul(pc, qv));
+        }
+      }
+      block_partials<T>(acc, nf, part0, G);
+      if (!grid_barrier(a.ctl, G)) return;
+      grid_sums(part0, nf, G, s_tmp);
+      // phase B: x += alpha p ; r -= alpha q ; r.r
+      for (int f = 0; f < nf; ++f) acc[f] = A::zero();
+      for (int f = 0; f < nf; ++f) {
+        if (!s_active[f]) continue;
+        const T al = A::from_d(s_rr[f] / s_tmp[f]);
+        for (int64_t c = tid; c < C; c += nthr) {
+          const int64_t k = f * C + c;
+          const T pv = ldx(Pnew + k);
+          const T qv = ldx(Q + k);
+          X[k] = A::add(ldx(X + k), A::mul(al, pv));
+          const T rv = A::sub(ldx(R + k), A::mul(al, qv));
+          R[k] = rv;
+          acc[f] = A::add(acc[f], A::mul(rv, rv));
+        }
+      }
+      block_partials<T>(acc, nf, part1, G);
+      if (!grid_barrier(a.ctl, G)) return;
+      grid_sums(part1, nf, G, s_tmp2);
+      int act[kMaxF];
+      for (int f = 0; f < nf; ++f) {
+        act[f] = s_active[f];
+        if (!act[f]) continue;
+        const double rr_new = s_tmp2[f];
+        if (rr_new <= a.rtol2 * s_bb[f]) {
+          iters[f] += it;
+          act[f] = 0;
+        } else {
+          beta[f] = rr_new / s_rr[f];
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0)
+        for (int f = 0; f < nf; ++f) {
+          if (s_active[f]) s_rr[f] = s_tmp2[f];
+          s_active[f] = act[f];
+        }
+      __syncthreads();
+      any = 0;
+      for (int f = 0; f < nf; ++f) any |= act[f];
+    }
+    for (int f = 0; f < nf; ++f)
+      if (s_active[f]) {
+        iters[f] += a.max_iter;
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS((int*)&a.ctl->cg_status, 0, -6);
+      }
+    // x of this pseudo-step must be complete before the next copies it into b
+    if (!grid_barrier(a.ctl, G)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    for (int f = 0; f < nf; ++f) a.iters[f] += iters[f];
+}
+
+__global__ void k_bar_reset(Ctl* ctl) {
+  ctl->bar_count = 0u;
+  ctl->bar_gen = 0u;
+}
+
+// ---------------------------------------------------------------- conversions
+template <class T>
+__device__ __forceinline__ T t_from_fixed(long long q, double scale);
+template <>
+__device__ __forceinline__ double t_from_fixed<double>(long long q, double scale) {
+  return (double)q * scale;
+}
+template <>
+__device__ __forceinline__ dd t_from_fixed<dd>(long long q, double scale) {
+  // exact split of the integer, then an exact power-of-two scaling of both words
+  const float hi = __ll2float_rn(q);
+  const long long rest = q - (long long)hi;
+  const float lo = __ll2float_rn(rest);
+  const float s = (float)scale;
+  return quick_two_sum(hi * s, lo * s);
+}
+template <>
+__device__ __forceinline__ float t_from_fixed<float>(long long q, double scale) {
+  return (float)((double)q * scale);
+}
+
+template <class T>
+__global__ void k_from_fixed(const long long* q, T* phi, int64_t C, double s0, double s1,
+                             double s2, int nf) {
+  const int64_t n = (int64_t)nf * C;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int f = (int)(k / C);
+    const double s = f == 0 ? s0 : (f < 4 ? s1 : s2);
+    phi[k] = t_from_fixed<T>(q[k], s);
+  }
+}
+
+template <class T>
+__global__ void k_to_double(const T* phi, double* out, int64_t n) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = CgA<T>::to_d(phi[k]);
+}
+
+template <class T>
+__global__ void k_from_double(const double* in, T* phi, int64_t n) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    phi[k] = CgA<T>::from_d(in[k]);
+}
+
+// eps_s, U_s = (eps U)/max(eps, 1e-12), F_fp; eps also into the drag's mesh word.
+template <class T, class F>
+__global__ void k_average_out(const T* phi, int64_t C, Quad<F>* ufe, double* eps, double* Us,
+                              double* Ff) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const double e = CgA<T>::to_d(phi[c]);
+    if (eps) eps[c] = e;
+    const double den = e > 1e-12 ? e : 1e-12;
+    for (int a = 0; a < 3; ++a) {
+      if (Us) Us[3 * c + a] = CgA<T>::to_d(phi[(1 + a) * C + c]) / den;
+      if (Ff) Ff[3 * c + a] = CgA<T>::to_d(phi[(4 + a) * C + c]);
+    }
+    ufe[c].d = (F)e;
+  }
+}
+
+inline unsigned grid_for(int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 152 * 32) g = 152 * 32;
+  return (unsigned)g;
+}
+
+template <class T>
+int smooth_impl(const DevParams& P, void* phi, const void* guess, int nf, void* work,
+                const DevState& st, int* iters_dev, double rtol, int max_iter, int n_tau,
+                const double coef[3], cudaStream_t s) {
+  const int64_t C = P.C;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smooth<T>, kSmoothThreads, 0);
+  if (per_sm < 1) return -3;
+  if (per_sm > 2) per_sm = 2;
+  const unsigned G = (unsigned)(nsm * per_sm);
+  SmoothArgs a{};
+  char* w = (char*)work;
+  const size_t fb = (size_t)nf * C * sizeof(T);
+  a.x = phi;
+  a.b = w;
+  a.r = w + fb;
+  a.p[0] = w + 2 * fb;
+  a.p[1] = w + 3 * fb;
+  a.q = w + 4 * fb;
+  a.part = (double*)(w + 5 * fb);
+  a.guess = guess;
+  a.iters = iters_dev;
+  a.nf = nf;
+  a.C = C;
+  for (int k = 0; k < 3; ++k) {
+    a.nc[k] = P.nc[k];
+    a.per[k] = P.periodic[k];
+    a.coef[k] = coef[k];
+  }
+  a.rtol2 = rtol * rtol;
+  a.max_iter = max_iter;
+  a.n_tau = n_tau;
+  a.ctl = st.ctl;
+  k_bar_reset<<<1, 1, 0, s>>>(st.ctl);
+  void* args[] = {&a};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_smooth<T>, dim3(G),
+                                              dim3(kSmoothThreads), args, 0, s);
+  return e == cudaSuccess ? 0 : -3;
+}
+
+}  // namespace
+
+size_t smooth_work_bytes(int form, int64_t C, int nf) {
+  const size_t w = form == FORM_PLAIN ? sizeof(float) : (form == FORM_FP64 ? sizeof(double) : sizeof(dd));
+  return 5 * (size_t)nf * C * w + 2 * (size_t)kMaxF * 152 * 8 * sizeof(double) + 256;
+}
+
+void launch_deposit(int form, const DevState& st, const DevMesh& mesh, const DevParams& P,
+                    void* q, cudaStream_t s) {
+  const unsigned g = grid_for(st.N, 256);
+  switch (form) {
+    case FORM_SPLIT: k_deposit<FORM_SPLIT><<<g, 256, 0, s>>>(st, mesh, P, q); break;
+    case FORM_PLAIN: k_deposit<FORM_PLAIN><<<g, 256, 0, s>>>(st, mesh, P, q); break;
+    default: k_deposit<FORM_FP64><<<g, 256, 0, s>>>(st, mesh, P, q); break;
+  }
+}
+
+void launch_fields_from_fixed(int form, const void* q, const DevParams& P, void* phi, int nf,
+                              cudaStream_t s) {
+  const double s0 = 1.0 / P.two_shift[0], s1 = 1.0 / P.two_shift[1], s2 = 1.0 / P.two_shift[2];
+  const unsigned g = grid_for((int64_t)nf * P.C, 256);
+  if (form == FORM_SPLIT)
+    k_from_fixed<dd><<<g, 256, 0, s>>>((const long long*)q, (dd*)phi, P.C, s0, s1, s2, nf);
+  else if (form == FORM_FP64)
+    k_from_fixed<double><<<g, 256, 0, s>>>((const long long*)q, (double*)phi, P.C, s0, s1, s2, nf);
+  // the plain form deposits floats straight into phi
+}
+
+int launch_smooth(int form, const DevParams& P, void* phi, const void* guess, int nf, void* work,
+                  const DevState& st, int* iters_dev, double rtol, int max_iter, int n_tau,
+                  const double coef[3], cudaStream_t s) {
+  if (nf > kMaxF) return -1;
+  switch (form) {
+    case FORM_SPLIT:
+      return smooth_impl<dd>(P, phi, guess, nf, work, st, iters_dev, rtol, max_iter, n_tau, coef, s);
+    case FORM_PLAIN:
+      return smooth_impl<float>(P, phi, guess, nf, work, st, iters_dev, rtol, max_iter, n_tau, coef, s);
+    default:
+      return smooth_impl<double>(P, phi, guess, nf, work, st, iters_dev, rtol, max_iter, n_tau, coef, s);
+  }
+}
+
+void launch_average_out(int form, const void* phi, const DevParams& P, void* ufe, double* eps,
+                        double* Us, double* F, cudaStream_t s) {
+  const unsigned g = grid_for(P.C, 256);
+  if (form == FORM_SPLIT)
+    k_average_out<dd, float><<<g, 256, 0, s>>>((const dd*)phi, P.C, (Quad<float>*)ufe, eps, Us, F);
+  else if (form == FORM_PLAIN)
+    k_average_out<float, float><<<g, 256, 0, s>>>((const float*)phi, P.C, (Quad<float>*)ufe, eps, Us, F);
+  else
+    k_average_out<double, double><<<g, 256, 0, s>>>((const double*)phi, P.C, (Quad<double>*)ufe, eps, Us, F);
+}
+
+void launch_phi_convert(int form, const void* phi, double* out, int64_t n, int to_double,
+                        cudaStream_t s) {
+  const unsigned g = grid_for(n, 256);
+  (void)to_double;
+  if (form == FORM_SPLIT) k_to_double<dd><<<g, 256, 0, s>>>((const dd*)phi, out, n);
+  else if (form == FORM_PLAIN) k_to_double<float><<<g, 256, 0, s>>>((const float*)phi, out, n);
+  else k_to_double<double><<<g, 256, 0, s>>>((const double*)phi, out, n);
+}
+
+void launch_phi_from_double(int form, const double* in, void* phi, int64_t n, cudaStream_t s) {
+  const unsigned g = grid_for(n, 256);
+  if (form == FORM_SPLIT) k_from_double<dd><<<g, 256, 0, s>>>(in, (dd*)phi, n);
+  else if (form == FORM_PLAIN) k_from_double<float><<<g, 256, 0, s>>>(in, (float*)phi, n);
+  else k_from_double<double><<<g, 256, 0, s>>>(in, (double*)phi, n);
+}
+
+}  // namespace sedi

@@ -1,0 +1,587 @@
+// Neighbour-list rebuild (Sec. 2.5: link-cell binning + neighbour lists, O(N)).
+//
+//   check    : rebuild when the largest displacement since the last build
+//              exceeds skin/2 (lists hold pairs within cutoff + skin)
+//   bin      : bin of each particle, counts per bin
+//   scan     : exclusive prefix sum of the counts (three-kernel block scan)
+//   scatter  : particle -> slot of its bin; per-bin sort by caller index makes the
+//              order deterministic
+//   gather   : permute every per-particle array into the other buffer
+//   build    : one thread per particle scans the 27 surrounding bins; FP32 test
+//              with a relative margin, exact FP64 predicate
+//                 d2 = (dx*dx + dy*dy) + dz*dz  <  ((r_i + r_j)(1 + f) + skin)^2
+//              (no fused multiply-add) only when the FP32 test is inconclusive,
+//              so lists are bit-identical to an FP64 evaluation of the predicate
+//   remap    : every new (i, k) entry looks its partner's caller index up in the
+//              particle's old list and carries the tangential spring over
+//   flip     : switch buffers, reset the displacement
+// Every kernel of the sequence returns at once when ctl->need_rebuild is 0, so the
+// sequence can be queued unconditionally or placed under a graph conditional.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sedi {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ bool skip(const Ctl* ctl, bool force) {
+  return !force && !ctl->need_rebuild;
+}
+
+__global__ void k_check(Ctl* ctl, float thresh2, cudaGraphConditionalHandle h, int use_cond) {
+  float m = __uint_as_float(ctl->disp_max_bits);
+  int need = (m > thresh2) ? 1 : 0;
+  ctl->need_rebuild = need;
+  if (use_cond) cudaGraphSetConditional(h, need ? 1u : 0u);
+}
+
+__global__ void k_force_need(Ctl* ctl) { ctl->need_rebuild = 1; }
+
+__global__ void k_zero_bins(DevState st, int64_t nbins, bool force) {
+  if (skip(st.ctl, force)) return;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nbins;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    st.bin_count[b] = 0;
+    st.bin_fill[b] = 0;
+  }
+}
+
+template <class S>
+__device__ __forceinline__ int bin_axis(S x, const DevParams& P, int a) {
+  float rel = (float)Num<S>::f(Num<S>::sub(x, sbox<S>(P).lo[a]));
+  int b = (int)floorf(rel * P.bin_inv[a]);
+  if (b < 0) b = 0;
+  if (b > P.nb[a] - 1) b = P.nb[a] - 1;
+  return b;
+}
+
+template <class S>
+__device__ __forceinline__ int64_t bin_index(const Quad<S>& p, const DevParams& P) {
+  int bx = bin_axis<S>(p.a, P, 0), by = bin_axis<S>(p.b, P, 1), bz = bin_axis<S>(p.c, P, 2);
+  return ((int64_t)bz * P.nb[1] + by) * P.nb[0] + bx;
+}
+
+template <int FORM>
+__global__ void k_bin_count(DevState st, DevParams P, int sub_off, bool force) {
+  if (skip(st.ctl, force)) return;
+  using S = typename Traits<FORM>::S;
+  const int sb = (st.ctl->st + sub_off) & 1;
+  const Quad<S>* pos = (const Quad<S>*)st.pos[sb];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < st.N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = bin_index<S>(ldq(pos + i), P);
+    st.bin_of[i] = (int32_t)b;
+    atomicAdd(&st.bin_count[b], 1);
+  }
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Exclusive scan of a thread value across the block; returns the block total.
+__device__ __forceinline__ int block_excl_scan(int v, int* total) {
+  __shared__ int wsum[32];
+  __shared__ int wtot;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int incl = warp_incl_scan(v);
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int nw = blockDim.x >> 5;
+    int s = lane < nw ? wsum[lane] : 0;
+    int si = warp_incl_scan(s);
+    if (lane < nw) wsum[lane] = si - s;
+    if (lane == nw - 1) wtot = si;
+  }
+  __syncthreads();
+  int r = incl - v + wsum[wid];
+  *total = wtot;
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_scan1(DevState st, int64_t nbins, bool force) {
+  if (skip(st.ctl, force)) return;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int v[kScanItems];
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t b = base + k;
+    v[k] = b < nbins ? st.bin_count[b] : 0;
+    s += v[k];
+  }
+  int total;
+  int ex = block_excl_scan(s, &total);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t b = base + k;
+    if (b < nbins) st.bin_start[b] = ex;
+    ex += v[k];
+  }
+  if (threadIdx.x == 0) st.scan_blk[blockIdx.x] = total;
+}
+
+__global__ void k_scan2(DevState st, int64_t nblk, int64_t nbins, bool force) {
+  if (skip(st.ctl, force)) return;
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nblk; base += blockDim.x) {
+    int64_t b = base + threadIdx.x;
+    int v = b < nblk ? st.scan_blk[b] : 0;
+    int total;
+    int ex = block_excl_scan(v, &total);
+    if (b < nblk) st.scan_blk[b] = ex + carry;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) st.bin_start[nbins] = carry;
+}
+
+__global__ void k_scan3(DevState st, int64_t nbins, bool force) {
+  if (skip(st.ctl, force)) return;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  const int add = st.scan_blk[blockIdx.x];
+  for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
+    int64_t b = base + k;
+    if (b < nbins) st.bin_start[b] += add;
+  }
+}
+
+__global__ void k_scatter(DevState st, bool force) {
+  if (skip(st.ctl, force)) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < st.N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int b = st.bin_of[i];
+    int slot = atomicAdd(&st.bin_fill[b], 1);
+    st.order[st.bin_start[b] + slot] = (int32_t)i;
+  }
+}
+
+// Insertion sort of each bin's entries by caller index (bins hold a few particles).
+__global__ void k_sort_bins(DevState st, int64_t nbins, bool force) {
+  if (skip(st.ctl, force)) return;
+  const int32_t* uid = st.uid[st.ctl->pb];
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nbins;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    int n = st.bin_count[b];
+    if (n < 2) continue;
+    int32_t* o = st.order + st.bin_start[b];
+    for (int a = 1; a < n; ++a) {
+      int32_t v = o[a];
+      int32_t key = uid[v];
+      int c = a - 1;
+      while (c >= 0 && uid[o[c]] > key) {
+        o[c + 1] = o[c];
+        --c;
+      }
+      o[c + 1] = v;
+    }
+  }
+}
+
+template <int FORM>
+__global__ void k_gather(DevState st, int sub_off, bool force) {
+  if (skip(st.ctl, force)) return;
+  using S = typename Traits<FORM>::S;
+  using F = typename Traits<FORM>::F;
+  const int sb = (st.ctl->st + sub_off) & 1, ob = sb ^ 1;
+  const int pb = st.ctl->pb, qb = pb ^ 1;
+  const int64_t N = st.N;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = st.order[k];
+    Quad<S> p = ldq((const Quad<S>*)st.pos[sb] + o);
+    stq((Quad<S>*)st.pos[ob] + k, p);
+    stq((Quad<S>*)st.vel[ob] + k, ldq((const Quad<S>*)st.vel[sb] + o));
+    stq((Quad<S>*)st.omg[ob] + k, ldq((const Quad<S>*)st.omg[sb] + o));
+    stq((Quad<F>*)st.acc[qb] + k, ldq((const Quad<F>*)st.acc[pb] + o));
+    st.uid[qb][k] = st.uid[pb][o];
+    st.r64[qb][k] = st.r64[pb][o];
+    st.vfrac[qb][k] = st.vfrac[pb][o];
+    const uint32_t wm = st.wmask[pb][o];
+    st.wmask[qb][k] = wm;
+    if (wm) {
+      const S* wh = (const S*)st.whist[pb];
+      S* wq = (S*)st.whist[qb];
+      for (int w = 0; w < kWalls; ++w)
+        if ((wm >> w) & 1u)
+          for (int c = 0; c < 3; ++c) wq[((int64_t)w * 3 + c) * N + k] = wh[((int64_t)w * 3 + c) * N + o];
+    }
+    st.xb[qb][k] = make_float4((float)Num<S>::f(p.a), (float)Num<S>::f(p.b),
+                               (float)Num<S>::f(p.c), 0.0f);
+  }
+}
+
+__device__ __forceinline__ double min_image_d(double d, int per, double L) {
+  if (!per) return d;
+  if (d > 0.5 * L) return d - L;
+  if (d < -0.5 * L) return d + L;
+  return d;
+}
+
+// Exact FP64 list predicate (no contraction).
+__device__ __forceinline__ bool listed_exact(const double xi[3], const double xj[3], double ri,
+                                             double rj, const DevParams& P) {
+  double d[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) d[a] = min_image_d(__dsub_rn(xj[a], xi[a]), P.periodic[a], P.L[a]);
+  double d2 = __dmul_rn(d[0], d[0]);
+  d2 = __dadd_rn(d2, __dmul_rn(d[1], d[1]));
+  d2 = __dadd_rn(d2, __dmul_rn(d[2], d[2]));
+  double s = __dadd_rn(ri, rj);
+  double rc = __dadd_rn(s, __dmul_rn(P.lub_out_frac, s));
+  rc = __dadd_rn(rc, P.skin);
+  return d2 < __dmul_rn(rc, rc);
+}
+
+template <int FORM>
+__global__ void k_build(DevState st, DevParams P, int sub_off, bool force) {
+  if (skip(st.ctl, force)) return;
+  using S = typename Traits<FORM>::S;
+  using NS = Num<S>;
+  // after the gather the sorted state sits in the other buffers
+  const int sb = ((st.ctl->st + sub_off) & 1) ^ 1;
+  const int qb = st.ctl->pb ^ 1;
+  const int ql = st.ctl->nl ^ 1;
+  const int64_t N = st.N;
+  const Quad<S>* pos = (const Quad<S>*)st.pos[sb];
+  const double* r64 = st.r64[qb];
+  int32_t* nbr = st.nbr[ql];
+  const float fr = (float)P.lub_out_frac, sk = (float)P.skin;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const Quad<S> pi = ldq(pos + i);
+    const double ri = r64[i];
+    const float rif = (float)ri;
+    int c[3] = {bin_axis<S>(pi.a, P, 0), bin_axis<S>(pi.b, P, 1), bin_axis<S>(pi.c, P, 2)};
+    int n = 0;
+    for (int oz = -1; oz <= 1; ++oz) {
+      int tz = c[2] + oz;
+      if (P.periodic[2]) tz = (tz + P.nb[2]) % P.nb[2];
+      else if (tz < 0 || tz >= P.nb[2]) continue;
+      for (int oy = -1; oy <= 1; ++oy) {
+        int ty = c[1] + oy;
+        if (P.periodic[1]) ty = (ty + P.nb[1]) % P.nb[1];
+        else if (ty < 0 || ty >= P.nb[1]) continue;
+        for (int ox = -1; ox <= 1; ++ox) {
+          int tx = c[0] + ox;
+          if (P.periodic[0]) tx = (tx + P.nb[0]) % P.nb[0];
+          else if (tx < 0 || tx >= P.nb[0]) continue;
+          const int64_t b = ((int64_t)tz * P.nb[1] + ty) * P.nb[0] + tx;
+          const int s0 = st.bin_start[b], s1 = s0 + st.bin_count[b];
+          for (int j = s0; j < s1; ++j) {
+            if (j == i) continue;
+            const Quad<S> pj = ldq(pos + j);
+            const double rj = r64[j];
+            float d[3] = {(float)NS::dif(pj.a, pi.a), (float)NS::dif(pj.b, pi.b),
+                          (float)NS::dif(pj.c, pi.c)};
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+              if (P.periodic[a])
+                d[a] = d[a] > P.cf.halfL[a] ? d[a] - P.cf.L[a]
+                                            : (d[a] < -P.cf.halfL[a] ? d[a] + P.cf.L[a] : d[a]);
+            const float d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            const float s = rif + (float)rj;
+            const float rc = s + fr * s + sk;
+            const float rc2 = rc * rc;
+            bool in;
+            if (d2 < rc2 * (1.0f - 2e-4f)) in = true;
+            else if (d2 > rc2 * (1.0f + 2e-4f)) in = false;
+            else {
+              const double xi[3] = {NS::d(pi.a), NS::d(pi.b), NS::d(pi.c)};
+              const double xj[3] = {NS::d(pj.a), NS::d(pj.b), NS::d(pj.c)};
+              in = listed_exact(xi, xj, ri, rj, P);
+            }
+            if (in) {
+              if (n < P.cap) nbr[(int64_t)n * N + i] = j;
+              ++n;
+            }
+          }
+        }
+      }
+    }
+    st.nn[ql][i] = n < P.cap ? n : P.cap;
+    atomicMax(&st.ctl->max_nn, n);
+    if (n > P.cap) {
+      atomicMax(&st.ctl->overflow_nn, n);
+      atomicCAS(&st.ctl->error, 0, -4);
+    }
+  }
+}
+
+template <int FORM>
+__global__ void k_remap(DevState st, DevParams P, bool force) {
+  if (skip(st.ctl, force)) return;
+  using S = typename Traits<FORM>::S;
+  const int pb = st.ctl->pb, qb = pb ^ 1;
+  const int nl = st.ctl->nl, ql = nl ^ 1;
+  const int64_t N = st.N, cap = P.cap;
+  const S* hold = (const S*)st.hist[nl];
+  S* hnew = (S*)st.hist[ql];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = st.order[i];
+    const uint32_t omask = force ? 0u : st.cmask[nl][o];
+    uint32_t nmask = 0;
+    if (omask) {
+      const int onn = st.nn[nl][o];
+      const int nn = st.nn[ql][i];
+      for (int k = 0; k < nn; ++k) {
+        const int32_t uj = st.uid[qb][st.nbr[ql][(int64_t)k * N + i]];
+        for (int kk = 0; kk < onn; ++kk) {
+          if (!((omask >> kk) & 1u)) continue;
+          if (st.uid[pb][st.nbr[nl][(int64_t)kk * N + o]] != uj) continue;
+          for (int c = 0; c < 3; ++c)
+            hnew[((int64_t)c * cap + k) * N + i] = hold[((int64_t)c * cap + kk) * N + o];
+          nmask |= 1u << k;
+          break;
+        }
+      }
+    }
+    st.cmask[ql][i] = nmask;
+  }
+}
+
+__global__ void k_flip(DevState st, bool force) {
+  if (skip(st.ctl, force)) return;
+  Ctl* c = st.ctl;
+  c->st ^= 1;
+  c->pb ^= 1;
+  c->nl ^= 1;
+  c->disp_max_bits = 0u;
+  c->need_rebuild = 0;
+  c->rebuilds += 1;
+}
+
+__global__ void k_advance(Ctl* ctl, int n) { ctl->st = (ctl->st + n) & 1; }
+
+inline unsigned grid_for(int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 152 * 64) g = 152 * 64;
+  return (unsigned)g;
+}
+
+template <int FORM>
+void rebuild_impl(const DevState& st, const DevParams& P, int sub_off, bool force, cudaStream_t s) {
+  const int B = 256;
+  const int64_t nblk = (P.nbins + kScanTile - 1) / kScanTile;
+  if (force) k_force_need<<<1, 1, 0, s>>>(st.ctl);
+  k_zero_bins<<<grid_for(P.nbins, B), B, 0, s>>>(st, P.nbins, false);
+  k_bin_count<FORM><<<grid_for(st.N, B), B, 0, s>>>(st, P, sub_off, false);
+  k_scan1<<<(unsigned)nblk, kScanThreads, 0, s>>>(st, P.nbins, false);
+  k_scan2<<<1, 1024, 0, s>>>(st, nblk, P.nbins, false);
+  k_scan3<<<(unsigned)nblk, kScanThreads, 0, s>>>(st, P.nbins, false);
+  k_scatter<<<grid_for(st.N, B), B, 0, s>>>(st, false);
+  k_sort_bins<<<grid_for(P.nbins, B), B, 0, s>>>(st, P.nbins, false);
+  k_gather<FORM><<<grid_for(st.N, B), B, 0, s>>>(st, sub_off, false);
+  k_build<FORM><<<grid_for(st.N, 128), 128, 0, s>>>(st, P, sub_off, false);
+  k_remap<FORM><<<grid_for(st.N, B), B, 0, s>>>(st, P, force);
+  k_flip<<<1, 1, 0, s>>>(st, false);
+}
+
+}  // namespace
+
+void launch_rebuild(int form, const DevState& st, const DevParams& P, int sub_off, bool force,
+                    cudaStream_t s) {
+  switch (form) {
+    case FORM_SPLIT: rebuild_impl<FORM_SPLIT>(st, P, sub_off, force, s); break;
+    case FORM_PLAIN: rebuild_impl<FORM_PLAIN>(st, P, sub_off, force, s); break;
+    default: rebuild_impl<FORM_FP64>(st, P, sub_off, force, s); break;
+  }
+}
+
+void launch_check(const DevState& st, const DevParams& P, unsigned long long cond_handle,
+                  int use_cond, cudaStream_t s) {
+  float hs = P.half_skin_f;
+  k_check<<<1, 1, 0, s>>>(st.ctl, hs * hs, (cudaGraphConditionalHandle)cond_handle, use_cond);
+}
+
+void launch_advance_parity(const DevState& st, int n, cudaStream_t s) {
+  if (n & 1) k_advance<<<1, 1, 0, s>>>(st.ctl, n);
+}
+
+// ---------------------------------------------------------------- import/export
+
+namespace {
+
+template <class S>
+__device__ __forceinline__ S s_from_double(double x);
+template <>
+__device__ __forceinline__ float s_from_double<float>(double x) {
+  return __double2float_rn(x);
+}
+template <>
+__device__ __forceinline__ double s_from_double<double>(double x) {
+  return x;
+}
+template <>
+__device__ __forceinline__ dd s_from_double<dd>(double x) {
+  return dd_from_double(x);
+}
+
+template <int FORM>
+__global__ void k_import(DevState st, const double* x, const double* v, const double* w,
+                         const double* d, const double* rho, double pi6, double vc) {
+  using S = typename Traits<FORM>::S;
+  using F = typename Traits<FORM>::F;
+  const int sb = st.ctl->st, pb = st.ctl->pb;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < st.N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double di = d[i];
+    const double r = 0.5 * di;
+    const double Vp = __dmul_rn(__dmul_rn(__dmul_rn(pi6, di), di), di);
+    const double m = __dmul_rn(rho[i], Vp);
+    Quad<S> p{s_from_double<S>(x[3 * i]), s_from_double<S>(x[3 * i + 1]),
+              s_from_double<S>(x[3 * i + 2]), s_from_double<S>(r)};
+    stq((Quad<S>*)st.pos[sb] + i, p);
+    stq((Quad<S>*)st.vel[sb] + i,
+        Quad<S>{s_from_double<S>(v ? v[3 * i] : 0.0), s_from_double<S>(v ? v[3 * i + 1] : 0.0),
+                s_from_double<S>(v ? v[3 * i + 2] : 0.0), s_from_double<S>(m)});
+    stq((Quad<S>*)st.omg[sb] + i,
+        Quad<S>{s_from_double<S>(w ? w[3 * i] : 0.0), s_from_double<S>(w ? w[3 * i + 1] : 0.0),
+                s_from_double<S>(w ? w[3 * i + 2] : 0.0), S{}});
+    stq((Quad<F>*)st.acc[pb] + i, Quad<F>{F(0), F(0), F(0), F(0)});
+    st.uid[pb][i] = (int32_t)i;
+    st.r64[pb][i] = r;
+    st.vfrac[pb][i] = __ddiv_rn(Vp, vc);
+    st.wmask[pb][i] = 0u;
+    st.xb[pb][i] = make_float4((float)x[3 * i], (float)x[3 * i + 1], (float)x[3 * i + 2], 0.0f);
+  }
+}
+
+// what: 0 x, 1 v, 2 omega, 3 a_prev
+template <int FORM>
+__global__ void k_export(DevState st, int what, double* out) {
+  using S = typename Traits<FORM>::S;
+  using F = typename Traits<FORM>::F;
+  const int sb = st.ctl->st, pb = st.ctl->pb;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < st.N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = st.uid[pb][i];
+    double a, b, c;
+    if (what == 3) {
+      Quad<F> q = ldq((const Quad<F>*)st.acc[pb] + i);
+      a = (double)q.a; b = (double)q.b; c = (double)q.c;
+    } else {
+      const void* base = what == 0 ? st.pos[sb] : (what == 1 ? st.vel[sb] : st.omg[sb]);
+      Quad<S> q = ldq((const Quad<S>*)base + i);
+      a = Num<S>::d(q.a); b = Num<S>::d(q.b); c = Num<S>::d(q.c);
+    }
+    out[3 * u] = a;
+    out[3 * u + 1] = b;
+    out[3 * u + 2] = c;
+  }
+}
+
+__global__ void k_nbr_counts(DevState st, int64_t* counts) {
+  const int pb = st.ctl->pb, nl = st.ctl->nl;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < st.N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    counts[st.uid[pb][i]] = st.nn[nl][i];
+}
+
+__global__ void k_nbr_fill(DevState st, const int64_t* offsets, int64_t* out) {
+  const int pb = st.ctl->pb, nl = st.ctl->nl;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < st.N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = st.uid[pb][i];
+    int64_t* o = out + offsets[u];
+    const int n = st.nn[nl][i];
+    for (int k = 0; k < n; ++k) {
+      int64_t v = st.uid[pb][st.nbr[nl][(int64_t)k * st.N + i]];
+      int c = k - 1;
+      while (c >= 0 && o[c] > v) {
+        o[c + 1] = o[c];
+        --c;
+      }
+      o[c + 1] = v;
+    }
+  }
+}
+
+template <int FORM>
+__global__ void k_contacts(DevState st, DevParams P, unsigned long long* count, int64_t cap,
+                           int64_t* ij, double* xi) {
+  using S = typename Traits<FORM>::S;
+  const int pb = st.ctl->pb, nl = st.ctl->nl;
+  const S* hist = (const S*)st.hist[nl];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < st.N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t m = st.cmask[nl][i];
+    if (!m) continue;
+    const int32_t ui = st.uid[pb][i];
+    const int n = st.nn[nl][i];
+    for (int k = 0; k < n; ++k) {
+      if (!((m >> k) & 1u)) continue;
+      const int32_t uj = st.uid[pb][st.nbr[nl][(int64_t)k * st.N + i]];
+      if (uj < ui) continue;
+      unsigned long long slot = atomicAdd(count, 1ull);
+      if ((int64_t)slot >= cap) continue;
+      ij[2 * slot] = ui;
+      ij[2 * slot + 1] = uj;
+      for (int c = 0; c < 3; ++c)
+        xi[3 * slot + c] = Num<S>::d(hist[((int64_t)c * P.cap + k) * st.N + i]);
+    }
+  }
+}
+
+}  // namespace
+
+void launch_import(int form, const DevState& st, const double* x, const double* v, const double* w,
+                   const double* d, const double* rho, const DevParams& P, cudaStream_t s) {
+  const double pi6 = 3.14159265358979323846 / 6.0;
+  unsigned g = grid_for(st.N, 256);
+  switch (form) {
+    case FORM_SPLIT: k_import<FORM_SPLIT><<<g, 256, 0, s>>>(st, x, v, w, d, rho, pi6, P.vc); break;
+    case FORM_PLAIN: k_import<FORM_PLAIN><<<g, 256, 0, s>>>(st, x, v, w, d, rho, pi6, P.vc); break;
+    default: k_import<FORM_FP64><<<g, 256, 0, s>>>(st, x, v, w, d, rho, pi6, P.vc); break;
+  }
+}
+
+void launch_export(int form, const DevState& st, int what, double* out, cudaStream_t s) {
+  unsigned g = grid_for(st.N, 256);
+  switch (form) {
+    case FORM_SPLIT: k_export<FORM_SPLIT><<<g, 256, 0, s>>>(st, what, out); break;
+    case FORM_PLAIN: k_export<FORM_PLAIN><<<g, 256, 0, s>>>(st, what, out); break;
+    default: k_export<FORM_FP64><<<g, 256, 0, s>>>(st, what, out); break;
+  }
+}
+
+void launch_neighbors_export(const DevState& st, int64_t* counts, cudaStream_t s) {
+  k_nbr_counts<<<grid_for(st.N, 256), 256, 0, s>>>(st, counts);
+}
+
+void launch_neighbors_fill(const DevState& st, const int64_t* offsets, int64_t* out,
+                           cudaStream_t s) {
+  k_nbr_fill<<<grid_for(st.N, 256), 256, 0, s>>>(st, offsets, out);
+}
+
+void launch_contacts_export(int form, const DevState& st, const DevParams& P,
+                            unsigned long long* count, int64_t cap, int64_t* ij, double* xi,
+                            cudaStream_t s) {
+  unsigned g = grid_for(st.N, 256);
+  switch (form) {
+    case FORM_SPLIT: k_contacts<FORM_SPLIT><<<g, 256, 0, s>>>(st, P, count, cap, ij, xi); break;
+    case FORM_PLAIN: k_contacts<FORM_PLAIN><<<g, 256, 0, s>>>(st, P, count, cap, ij, xi); break;
+    default: k_contacts<FORM_FP64><<<g, 256, 0, s>>>(st, P, count, cap, ij, xi); break;
+  }
+}
+
+}  // namespace sedi

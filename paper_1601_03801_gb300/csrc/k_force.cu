@@ -1,0 +1,374 @@
+// Fused DEM substep: for every particle (one thread, cell-sorted order) visit its
+// neighbour list, evaluate Hertz-Mindlin contact with the tangential spring and
+// Ball-Melrose lubrication (Sec. 2.1 Eq. 1, Sec. 2.5), then wall contact, then
+// the fluid forces at the particle (Sec. 2.3, Eq. 3-8), then the leapfrog
+// velocity-Verlet update (Sec. 2.1, Eq. 1).
+//
+// Each pair is evaluated from both sides in canonical order (lower caller index
+// first) by the same code, so F_ji = -F_ij bit for bit and both sides keep
+// identical copies of the pair's spring; no atomics and no second pass.
+// Particle state is double-buffered (read buffer, write buffer) so neighbours are
+// read at the old time level.
+#include "common.cuh"
+#include "fluid.cuh"
+#include "fmath.cuh"
+#include "kernels.h"
+
+namespace sedi {
+
+namespace {
+
+template <class F>
+struct V3 {
+  F x, y, z;
+};
+
+// Hertz-Mindlin contact on body "a" (Sec. 2.5 soft spheres; Tsuji-type damping).
+// n: unit normal a -> b; delta > 0 overlap; vrel: contact-point velocity of a
+// relative to b; xi_old: spring (valid if has_old).  Returns the force on a and
+// writes the tangential part and the updated spring.
+template <class S, class F>
+__device__ __forceinline__ V3<F> hm_core(const ForceConsts<F>& K, V3<F> n, F delta, F Rs, F ms,
+                                         V3<F> vrel, const S* xi_old, bool has_old, V3<F>* Ft_out,
+                                         S* xi_new) {
+  using NS = Num<S>;
+  F sq = xsqrt(Rs * delta);
+  F Sn = F(2) * K.Es * sq;
+  F St = F(8) * K.Gs * sq;
+  F cn = K.cdamp * xsqrt(Sn * ms);
+  F ct = K.cdamp * xsqrt(St * ms);
+  F vn = vrel.x * n.x + vrel.y * n.y + vrel.z * n.z;
+  V3<F> vt{vrel.x - vn * n.x, vrel.y - vn * n.y, vrel.z - vn * n.z};
+  F kn = K.kn_fac * xsqrt(Rs);
+  F fn_s = -kn * delta * xsqrt(delta) - cn * vn;  // F_n = fn_s * n
+  // spring: rotate onto the tangent plane, keep the length, add v_t dt
+  S xi[3];
+  if (has_old) {
+    F xf[3] = {NS::f(xi_old[0]), NS::f(xi_old[1]), NS::f(xi_old[2])};
+    F proj = xf[0] * n.x + xf[1] * n.y + xf[2] * n.z;
+    F len2 = xf[0] * xf[0] + xf[1] * xf[1] + xf[2] * xf[2];
+    xi[0] = NS::fma_ff(xi_old[0], -proj, n.x);
+    xi[1] = NS::fma_ff(xi_old[1], -proj, n.y);
+    xi[2] = NS::fma_ff(xi_old[2], -proj, n.z);
+    if (len2 > F(0)) {
+      F t = proj * proj / len2;
+      if (t < F(1)) {
+        F s1 = xsqrt(F(1) - t);
+        F scm1 = t / (s1 * (F(1) + s1));  // 1/sqrt(1-t) - 1
+        F r0 = NS::f(xi[0]), r1 = NS::f(xi[1]), r2 = NS::f(xi[2]);
+        xi[0] = NS::fma_ff(xi[0], scm1, r0);
+        xi[1] = NS::fma_ff(xi[1], scm1, r1);
+        xi[2] = NS::fma_ff(xi[2], scm1, r2);
+      }
+    }
+  } else {
+    xi[0] = S{};
+    xi[1] = S{};
+    xi[2] = S{};
+  }
+  xi[0] = NS::fma_ff(xi[0], K.dt, vt.x);
+  xi[1] = NS::fma_ff(xi[1], K.dt, vt.y);
+  xi[2] = NS::fma_ff(xi[2], K.dt, vt.z);
+  V3<F> Ft{-St * NS::f(xi[0]) - ct * vt.x, -St * NS::f(xi[1]) - ct * vt.y,
+           -St * NS::f(xi[2]) - ct * vt.z};
+  F ft = xsqrt(Ft.x * Ft.x + Ft.y * Ft.y + Ft.z * Ft.z);
+  F fnm = xabs(fn_s);
+  if (ft > K.mu * fnm) {
+    F sc = K.mu * fnm / ft;
+    Ft.x *= sc;
+    Ft.y *= sc;
+    Ft.z *= sc;
+    F inv = F(-1) / St;
+    xi[0] = NS::from_f((Ft.x + ct * vt.x) * inv);
+    xi[1] = NS::from_f((Ft.y + ct * vt.y) * inv);
+    xi[2] = NS::from_f((Ft.z + ct * vt.z) * inv);
+  }
+  xi_new[0] = xi[0];
+  xi_new[1] = xi[1];
+  xi_new[2] = xi[2];
+  *Ft_out = Ft;
+  return V3<F>{fn_s * n.x + Ft.x, fn_s * n.y + Ft.y, fn_s * n.z + Ft.z};
+}
+
+template <class F>
+__device__ __forceinline__ V3<F> cross(V3<F> a, V3<F> b) {
+  return V3<F>{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+}  // namespace
+
+template <int FORM, bool INTEGRATE>
+__global__ void __launch_bounds__(256) k_substep(DevState st, DevMesh mesh, DevParams P,
+                                                 int sub_off) {
+  using S = typename Traits<FORM>::S;
+  using F = typename Traits<FORM>::F;
+  using NS = Num<S>;
+  const ForceConsts<F>& K = fconsts<F>(P);
+  const BoxS<S>& B = sbox<S>(P);
+  const Ctl* ctl = st.ctl;
+  const int sb = (ctl->st + sub_off) & 1;
+  const int pb = ctl->pb;
+  const int nl = ctl->nl;
+  const int64_t N = st.N;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float my_disp2 = 0.0f;
+  if (i < N) {
+    const Quad<S>* pos = (const Quad<S>*)st.pos[sb];
+    const Quad<S>* vel = (const Quad<S>*)st.vel[sb];
+    const Quad<S>* omg = (const Quad<S>*)st.omg[sb];
+    const int32_t* uid = st.uid[pb];
+    Quad<S> Pi = ldq(pos + i), Vi = ldq(vel + i), Wi = ldq(omg + i);
+    Quad<F>* accp = (Quad<F>*)st.acc[pb];
+    Quad<F> Ai = ldq(accp + i);
+    const F ri = NS::f(Pi.d), mi = NS::f(Vi.d);
+    const F vi[3] = {NS::f(Vi.a), NS::f(Vi.b), NS::f(Vi.c)};
+    const F wi[3] = {NS::f(Wi.a), NS::f(Wi.b), NS::f(Wi.c)};
+    const int32_t ui = uid[i];
+    V3<F> fc{0, 0, 0}, fl{0, 0, 0}, tq{0, 0, 0};
+    const int32_t* nbr = st.nbr[nl];
+    const int nn = st.nn[nl][i];
+    const uint32_t mask = st.cmask[nl][i];
+    uint32_t nmask = 0;
+    S* hist = (S*)st.hist[nl];
+    const int64_t cap = P.cap;
+    const float lub_out_f = P.lub_out_f;
+    for (int k = 0; k < nn; ++k) {
+      const int j = nbr[(int64_t)k * N + i];
+      const Quad<S> Pj = ldq(pos + j);
+      // cheap FP32 cull with a relative margin (exact test follows)
+      {
+        float dx = (float)NS::dif(Pj.a, Pi.a), dy = (float)NS::dif(Pj.b, Pi.b),
+              dz = (float)NS::dif(Pj.c, Pi.c);
+        if (P.periodic[0]) dx = dx > P.cf.halfL[0] ? dx - P.cf.L[0] : (dx < -P.cf.halfL[0] ? dx + P.cf.L[0] : dx);
+        if (P.periodic[1]) dy = dy > P.cf.halfL[1] ? dy - P.cf.L[1] : (dy < -P.cf.halfL[1] ? dy + P.cf.L[1] : dy);
+        if (P.periodic[2]) dz = dz > P.cf.halfL[2] ? dz - P.cf.L[2] : (dz < -P.cf.halfL[2] ? dz + P.cf.L[2] : dz);
+        float sr = (float)ri + (float)NS::f(Pj.d);
+        float cut = P.lubrication ? sr * (1.0f + lub_out_f) : sr;
+        if (dx * dx + dy * dy + dz * dz > cut * cut * 1.0002f) continue;
+      }
+      const int32_t uj = uid[j];
+      const bool i_lo = ui < uj;
+      const Quad<S>& A = i_lo ? Pi : Pj;
+      const Quad<S>& Bq = i_lo ? Pj : Pi;
+      // precise geometry in canonical order: dx = x_B - x_A (minimum image)
+      S dxs[3] = {NS::sub(Bq.a, A.a), NS::sub(Bq.b, A.b), NS::sub(Bq.c, A.c)};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (!P.periodic[a]) continue;
+        F c = NS::f(dxs[a]);
+        if (c > K.halfL[a]) dxs[a] = NS::sub(dxs[a], B.L[a]);
+        else if (c < -K.halfL[a]) dxs[a] = NS::add(dxs[a], B.L[a]);
+      }
+      S d2 = NS::add(NS::add(NS::mul(dxs[0], dxs[0]), NS::mul(dxs[1], dxs[1])),
+                     NS::mul(dxs[2], dxs[2]));
+      S ssum = NS::add(A.d, Bq.d);
+      S num = NS::sub(NS::mul(ssum, ssum), d2);
+      const F dist = xsqrt(NS::f(d2));
+      const F sF = NS::f(ssum);
+      const F delta = NS::f(num) / (sF + dist);  // r_A + r_B - |dx|
+      const bool contact = delta > F(0);
+      const bool lub = P.lubrication && (-delta < K.lub_out * sF);
+      if (!contact && !lub) continue;
+      const F inv_d = F(1) / dist;
+      const V3<F> n{NS::f(dxs[0]) * inv_d, NS::f(dxs[1]) * inv_d, NS::f(dxs[2]) * inv_d};
+      const Quad<S> Vj = ldq(vel + j);
+      const F vj[3] = {NS::f(Vj.a), NS::f(Vj.b), NS::f(Vj.c)};
+      const F* vA = i_lo ? vi : vj;
+      const F* vB = i_lo ? vj : vi;
+      if (contact) {
+        const Quad<S> Wj = ldq(omg + j);
+        const F wj[3] = {NS::f(Wj.a), NS::f(Wj.b), NS::f(Wj.c)};
+        const F* wA = i_lo ? wi : wj;
+        const F* wB = i_lo ? wj : wi;
+        const F rA = NS::f(A.d), rB = NS::f(Bq.d);
+        const F mA = i_lo ? mi : NS::f(Vj.d);
+        const F mB = i_lo ? NS::f(Vj.d) : mi;
+        const F Rs = rA * rB / (rA + rB);
+        const F ms = mA * mB / (mA + mB);
+        const F la = rA - F(0.5) * delta, lb = rB - F(0.5) * delta;
+        V3<F> om{la * wA[0] + lb * wB[0], la * wA[1] + lb * wB[1], la * wA[2] + lb * wB[2]};
+        V3<F> wxn = cross(om, n);
+        V3<F> vrel{vA[0] - vB[0] + wxn.x, vA[1] - vB[1] + wxn.y, vA[2] - vB[2] + wxn.z};
+        S xo[3], xn_[3];
+        const bool has = (mask >> k) & 1u;
+        if (has) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) xo[c] = hist[((int64_t)c * cap + k) * N + i];
+        }
+        V3<F> Ft;
+        V3<F> FA = hm_core<S, F>(K, n, delta, Rs, ms, vrel, xo, has, &Ft, xn_);
+        if (INTEGRATE) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) hist[((int64_t)c * cap + k) * N + i] = xn_[c];
+          nmask |= 1u << k;
+        }
+        const F lev = i_lo ? la : lb;
+        V3<F> T = cross(V3<F>{lev * n.x, lev * n.y, lev * n.z}, Ft);
+        if (i_lo) {
+          fc.x += FA.x; fc.y += FA.y; fc.z += FA.z;
+        } else {
+          fc.x -= FA.x; fc.y -= FA.y; fc.z -= FA.z;
+        }
+        tq.x += T.x; tq.y += T.y; tq.z += T.z;
+      }
+      if (lub) {
+        const F h = -delta;
+        const F hin = K.lub_in * sF;
+        const F hh = h > hin ? h : hin;
+        const F rA = NS::f(A.d), rB = NS::f(Bq.d);
+        const F Rl = rA * rB / (rA + rB);
+        const F vn = (vA[0] - vB[0]) * n.x + (vA[1] - vB[1]) * n.y + (vA[2] - vB[2]) * n.z;
+        F s = -K.six_pi_mu * Rl * Rl * vn / hh;
+        if (!i_lo) s = -s;
+        fl.x += s * n.x; fl.y += s * n.y; fl.z += s * n.z;
+      }
+    }
+    // walls (planes of the same material)
+    uint32_t wmask_old = st.wmask[pb][i], wmask_new = 0;
+    S* whist = (S*)st.whist[pb];
+    const S xi_s[3] = {Pi.a, Pi.b, Pi.c};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (P.periodic[a]) continue;
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        if (side == 0 ? !P.wall_lo[a] : !P.wall_hi[a]) continue;
+        // overlap r - dist in the state word (dist = x - lo or hi - x)
+        S dist_s = side == 0 ? NS::sub(xi_s[a], B.lo[a]) : NS::sub(B.hi[a], xi_s[a]);
+        const F delta = NS::f(NS::sub(Pi.d, dist_s));
+        V3<F> n{0, 0, 0};
+        const F sgn = side == 0 ? F(-1) : F(1);
+        if (a == 0) n.x = sgn; else if (a == 1) n.y = sgn; else n.z = sgn;
+        const int w = 2 * a + side;
+        if (delta > F(0)) {
+          const F l = ri - F(0.5) * delta;
+          V3<F> wxn = cross(V3<F>{l * wi[0], l * wi[1], l * wi[2]}, n);
+          V3<F> vrel{vi[0] + wxn.x, vi[1] + wxn.y, vi[2] + wxn.z};
+          S xo[3], xn_[3];
+          const bool has = (wmask_old >> w) & 1u;
+          if (has) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) xo[c] = whist[((int64_t)w * 3 + c) * N + i];
+          }
+          V3<F> Ft;
+          V3<F> FA = hm_core<S, F>(K, n, delta, ri, mi, vrel, xo, has, &Ft, xn_);
+          if (INTEGRATE) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) whist[((int64_t)w * 3 + c) * N + i] = xn_[c];
+            wmask_new |= 1u << w;
+          }
+          V3<F> T = cross(V3<F>{l * n.x, l * n.y, l * n.z}, Ft);
+          fc.x += FA.x; fc.y += FA.y; fc.z += FA.z;
+          tq.x += T.x; tq.y += T.y; tq.z += T.z;
+        }
+        if (P.lubrication) {
+          const F dbar = F(2) * ri;
+          const F h = -delta;
+          if (h < K.lub_out * dbar) {
+            const F hin = K.lub_in * dbar;
+            const F hh = h > hin ? h : hin;
+            const F vn = vi[0] * n.x + vi[1] * n.y + vi[2] * n.z;
+            const F s = -K.six_pi_mu * ri * ri * vn / hh;
+            fl.x += s * n.x; fl.y += s * n.y; fl.z += s * n.z;
+          }
+        }
+      }
+    }
+    // fluid forces at the particle
+    F ff[3];
+    const F ap[3] = {Ai.a, Ai.b, Ai.c};
+    fluid_force<S, F>(P, K, (const Quad<F>*)mesh.ufe, (const Quad<F>*)mesh.gfl, xi_s, ri, vi, ap,
+                      ff);
+    if (!INTEGRATE) {
+      double* o = st.fdbg;
+      o[3 * i + 0] = (double)fc.x; o[3 * i + 1] = (double)fc.y; o[3 * i + 2] = (double)fc.z;
+      o += 3 * N;
+      o[3 * i + 0] = (double)fl.x; o[3 * i + 1] = (double)fl.y; o[3 * i + 2] = (double)fl.z;
+      o += 3 * N;
+      o[3 * i + 0] = (double)ff[0]; o[3 * i + 1] = (double)ff[1]; o[3 * i + 2] = (double)ff[2];
+      o += 3 * N;
+      o[3 * i + 0] = (double)tq.x; o[3 * i + 1] = (double)tq.y; o[3 * i + 2] = (double)tq.z;
+    } else {
+      // leapfrog: v += dt a, w += dt T / I, x += dt v (state word)
+      const F inv_m = F(1) / mi;
+      F acc[3] = {(fc.x + fl.x + ff[0]) * inv_m + K.g[0], (fc.y + fl.y + ff[1]) * inv_m + K.g[1],
+                  (fc.z + fl.z + ff[2]) * inv_m + K.g[2]};
+      const F inv_I = F(2.5) / (mi * ri * ri);
+      F alp[3] = {tq.x * inv_I, tq.y * inv_I, tq.z * inv_I};
+      S vn[3] = {NS::fma_ff(Vi.a, K.dt, acc[0]), NS::fma_ff(Vi.b, K.dt, acc[1]),
+                 NS::fma_ff(Vi.c, K.dt, acc[2])};
+      S wn[3] = {NS::fma_ff(Wi.a, K.dt, alp[0]), NS::fma_ff(Wi.b, K.dt, alp[1]),
+                 NS::fma_ff(Wi.c, K.dt, alp[2])};
+      S xn[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        S x = NS::add(xi_s[a], NS::mul_f(vn[a], K.dt));
+        if (P.periodic[a]) {
+          if (NS::lt(x, B.lo[a])) x = NS::add(x, B.L[a]);
+          else if (!NS::lt(x, B.hi[a])) x = NS::sub(x, B.L[a]);
+        }
+        xn[a] = x;
+      }
+      if (!(xisfinite(acc[0]) && xisfinite(acc[1]) && xisfinite(acc[2]) &&
+            xisfinite(alp[0]) && xisfinite(alp[1]) && xisfinite(alp[2])))
+        atomicCAS((int*)&st.ctl->error, 0, -7);
+      const int ob = sb ^ 1;
+      stq((Quad<S>*)st.pos[ob] + i, Quad<S>{xn[0], xn[1], xn[2], Pi.d});
+      stq((Quad<S>*)st.vel[ob] + i, Quad<S>{vn[0], vn[1], vn[2], Vi.d});
+      stq((Quad<S>*)st.omg[ob] + i, Quad<S>{wn[0], wn[1], wn[2], Wi.d});
+      stq(accp + i, Quad<F>{acc[0], acc[1], acc[2], F(0)});
+      st.cmask[nl][i] = nmask;
+      st.wmask[pb][i] = wmask_new;
+      // displacement since the last rebuild (FP32, minimum image)
+      const float4 b = st.xb[pb][i];
+      float e[3] = {(float)NS::f(xn[0]) - b.x, (float)NS::f(xn[1]) - b.y,
+                    (float)NS::f(xn[2]) - b.z};
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (P.periodic[a]) {
+          if (e[a] > P.cf.halfL[a]) e[a] -= P.cf.L[a];
+          else if (e[a] < -P.cf.halfL[a]) e[a] += P.cf.L[a];
+        }
+      my_disp2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+      if (!(my_disp2 < 3.0e38f)) my_disp2 = 3.0e38f;
+    }
+  }
+  if (INTEGRATE) {
+    // block max of the squared displacement -> one atomic per block
+    float m = my_disp2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float wmax[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) wmax[wid] = m;
+    __syncthreads();
+    if (wid == 0) {
+      m = lane < (int)(blockDim.x >> 5) ? wmax[lane] : 0.0f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0 && m > 0.0f) atomicMax(&st.ctl->disp_max_bits, __float_as_uint(m));
+    }
+  }
+}
+
+template <int FORM>
+static void launch_one(const DevState& st, const DevMesh& mesh, const DevParams& P, int sub_off,
+                       bool integrate, int block, cudaStream_t s) {
+  const int64_t grid = (st.N + block - 1) / block;
+  if (integrate)
+    k_substep<FORM, true><<<(unsigned)grid, block, 0, s>>>(st, mesh, P, sub_off);
+  else
+    k_substep<FORM, false><<<(unsigned)grid, block, 0, s>>>(st, mesh, P, sub_off);
+}
+
+void launch_substep(int form, const DevState& st, const DevMesh& mesh, const DevParams& P,
+                    int sub_off, bool integrate, int block, cudaStream_t s) {
+  if (st.N <= 0) return;
+  switch (form) {
+    case FORM_SPLIT: launch_one<FORM_SPLIT>(st, mesh, P, sub_off, integrate, block, s); break;
+    case FORM_PLAIN: launch_one<FORM_PLAIN>(st, mesh, P, sub_off, integrate, block, s); break;
+    default: launch_one<FORM_FP64>(st, mesh, P, sub_off, integrate, block, s); break;
+  }
+}
+
+}  // namespace sedi

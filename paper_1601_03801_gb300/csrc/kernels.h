@@ -1,0 +1,52 @@
+// Host-side launchers of the sm_103a kernels (one translation unit per phase).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace sedi {
+
+// k_force.cu: one fused substep (integrate = true) or forces only into st.fdbg.
+void launch_substep(int form, const DevState& st, const DevMesh& mesh, const DevParams& P,
+                    int sub_off, bool integrate, int block, cudaStream_t s);
+
+// k_bin.cu: rebuild = bin, sort by (bin, caller index), gather into the other
+// buffers, build lists, carry springs over.  `conditional` kernels return at once
+// unless ctl->need_rebuild is set.  sub_off: substep offset of the state buffer.
+void launch_rebuild(int form, const DevState& st, const DevParams& P, int sub_off, bool force,
+                    cudaStream_t s);
+// Set ctl->need_rebuild from the displacement; optionally a graph conditional.
+void launch_check(const DevState& st, const DevParams& P, unsigned long long cond_handle,
+                  int use_cond, cudaStream_t s);
+// ctl->st = (ctl->st + n) & 1 after n substeps.
+void launch_advance_parity(const DevState& st, int n, cudaStream_t s);
+
+// Scatter/gather between the sorted device state and caller order.
+void launch_export(int form, const DevState& st, int what, double* out, cudaStream_t s);
+void launch_import(int form, const DevState& st, const double* x, const double* v,
+                   const double* w, const double* d, const double* rho, const DevParams& P,
+                   cudaStream_t s);
+void launch_neighbors_export(const DevState& st, int64_t* counts, cudaStream_t s);
+void launch_neighbors_fill(const DevState& st, const int64_t* offsets, int64_t* out,
+                           cudaStream_t s);
+void launch_contacts_export(int form, const DevState& st, const DevParams& P,
+                            unsigned long long* count, int64_t cap, int64_t* ij, double* xi,
+                            cudaStream_t s);
+
+// k_avg.cu: deposition, field conversion, persistent CG smoother, outputs.
+void launch_deposit(int form, const DevState& st, const DevMesh& mesh, const DevParams& P,
+                    void* qfields, cudaStream_t s);
+void launch_fields_from_fixed(int form, const void* q, const DevParams& P, void* phi,
+                              int nf, cudaStream_t s);
+// Smooth nf fields [nf][C] in place (type by form).  guess may be null.
+int launch_smooth(int form, const DevParams& P, void* phi, const void* guess, int nf,
+                  void* work, const DevState& st, int* iters_dev, double rtol, int max_iter,
+                  int n_tau, const double coef[3], cudaStream_t s);
+size_t smooth_work_bytes(int form, int64_t C, int nf);
+void launch_average_out(int form, const void* phi, const DevParams& P, void* ufe, double* eps,
+                        double* Us, double* F, cudaStream_t s);
+void launch_phi_convert(int form, const void* phi, double* out, int64_t n, int to_double,
+                        cudaStream_t s);
+void launch_phi_from_double(int form, const double* in, void* phi, int64_t n, cudaStream_t s);
+
+}  // namespace sedi
