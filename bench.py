@@ -335,6 +335,28 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
+def kernels_only(args):
+    """Run the benchmark workload for a few steps without timing (profiling driver:
+    the command an ncu capture wraps)."""
+    import torch
+
+    from paper_1601_03801_gb300 import sedi
+    from paper_1601_03801_gb300.workloads import bed_case
+
+    torch.cuda.set_device(0)
+    prm, parts, fl = bed_case()
+    g = sedi.Sedi(dict(prm, precision_form=args.form, use_graphs=int(args.graphs)))
+    g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+    g.set_fluid(U=fl["U"])
+    g.average_inplace()
+    for _ in range(args.settle + args.steps):
+        g.step(SUBSTEPS)
+        g.average_inplace()
+    g.sync()
+    print(json.dumps({"mode": "kernels", "form": args.form, "steps": args.settle + args.steps,
+                      "stats": g.stats()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -344,8 +366,15 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--settle", type=int, default=50, help="untimed settling steps before warm-up")
+    ap.add_argument("--mode", default="bench", choices=["bench", "kernels"],
+                    help="kernels: run the workload untimed (profiling driver)")
+    ap.add_argument("--form", default="split", choices=["split", "plain", "fp64"])
+    ap.add_argument("--graphs", type=int, default=1,
+                    help="kernels mode: 0 launches kernels one by one (profilers see them)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.mode == "kernels":
+        kernels_only(args)
+    elif args.impl == "reference":
         reference_arm(args)
     else:
         gpu_arm(args)

@@ -9,13 +9,14 @@
 //
 // Smoothing (Eq. 10): n_tau backward-Euler steps (I - dtau div D grad) x = b of
 // the 7-point finite-volume Laplacian (zero flux through non-periodic faces),
-// each solved by plain conjugate gradients to ||r|| <= rtol ||b||, all fields at
-// once in ONE persistent cooperative launch.  Per iteration two grid barriers:
-//   A: p = r + beta p_old (formed on the fly at the stencil points), q = A p, p.q
-//   B: x += alpha p, r -= alpha q, r.r
-// Every block reduces the per-block partials in the same fixed order, so all
-// blocks take identical decisions and the result is run-to-run deterministic.
-// The grid barrier spins at most ~1 s, then records SEDI_ETIMEOUT and returns.
+// each solved to ||r|| <= rtol ||b|| for all fields at once in ONE persistent
+// cooperative launch.  The solver is Chebyshev semi-iteration on the known
+// spectrum of the operator (see k_smooth): one grid barrier per iteration and no
+// inner products except the final residual check.  Every block reduces the
+// per-block partials in the same fixed order, so all blocks take identical
+// decisions and the result is run-to-run deterministic.
+// The grid barrier spins at most ~0.3 s, then records SEDI_ETIMEOUT and returns;
+// the other blocks see the record and return at their next barrier.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -125,6 +126,10 @@ struct CgA<dd> {
   }
 };
 
+struct SmoothArgs;
+template <class T>
+__device__ __forceinline__ T coef_word(const SmoothArgs& a, int k);
+
 struct SmoothArgs {
   void* x;            // [nf][C] in: fields, out: smoothed
   void* b;            // [nf][C] right-hand side of the current pseudo-step
@@ -139,11 +144,26 @@ struct SmoothArgs {
   int nc[3];
   int per[3];
   double coef[3];     // dtau * D_a / h_a^2
+  dd coef_dd[3];      // the same, split into two FP32 words on the host
+  double lmax;        // upper bound of the spectrum of A (1 + 4 sum coef)
   double rtol2;
   int max_iter;
   int n_tau;
   Ctl* ctl;
 };
+
+template <>
+__device__ __forceinline__ double coef_word<double>(const SmoothArgs& a, int k) {
+  return a.coef[k];
+}
+template <>
+__device__ __forceinline__ float coef_word<float>(const SmoothArgs& a, int k) {
+  return a.coef_dd[k].hi;
+}
+template <>
+__device__ __forceinline__ dd coef_word<dd>(const SmoothArgs& a, int k) {
+  return a.coef_dd[k];
+}
 
 // Bounded grid barrier (co-residency guaranteed by the cooperative launch).
 __device__ bool grid_barrier(Ctl* ctl, unsigned nblocks) {
@@ -160,10 +180,12 @@ __device__ bool grid_barrier(Ctl* ctl, unsigned nblocks) {
     } else {
       long long spins = 0;
       while (*gen == g) {
-        if (++spins > (1ll << 24)) {
+        if (++spins > (1ll << 22)) {  // ~0.3 s
           atomicCAS((int*)&ctl->cg_status, 0, -8);
           break;
         }
+        // another block gave up: stop waiting too
+        if ((spins & 1023) == 0 && *((volatile int*)&ctl->cg_status) == -8) break;
         __nanosleep(64);
       }
     }
@@ -221,44 +243,60 @@ __device__ __forceinline__ dd ldx(const dd* p) {
   return dd{v.x, v.y};
 }
 
-template <class T>
-__device__ __forceinline__ T stencil_val(const T* r, const T* pold, T beta, bool first, int64_t c) {
-  using A = CgA<T>;
-  const T rv = ldx(r + c);
-  if (first) return rv;
-  return A::add(rv, A::mul(beta, ldx(pold + c)));
-}
+// Cell coordinates and the six face neighbours (-1: zero-flux face).
+struct Stencil {
+  int32_t nb[6];
+};
 
-// y = A v at cell c; v(c') given by the functor.
-template <class T, class Get>
-__device__ __forceinline__ T apply_A(const SmoothArgs& a, const T* cf, int64_t c, Get get) {
-  using A = CgA<T>;
-  const int nx = a.nc[0], ny = a.nc[1], nz = a.nc[2];
-  const int ix = (int)(c % nx);
-  const int iy = (int)((c / nx) % ny);
-  const int iz = (int)(c / ((int64_t)nx * ny));
-  const T vc = get(c);
-  T lap = A::zero();
-  const int idx[3] = {ix, iy, iz};
-  const int n[3] = {nx, ny, nz};
-  const int64_t stride[3] = {1, nx, (int64_t)nx * ny};
+__device__ __forceinline__ Stencil stencil_of(const SmoothArgs& a, int64_t c) {
+  const uint32_t nx = a.nc[0], ny = a.nc[1], nz = a.nc[2];
+  const uint32_t cc = (uint32_t)c;
+  const uint32_t ix = cc % nx;
+  const uint32_t t = cc / nx;
+  const uint32_t iy = t % ny;
+  const uint32_t iz = t / ny;
+  const uint32_t idx[3] = {ix, iy, iz};
+  const uint32_t n[3] = {nx, ny, nz};
+  const int32_t stride[3] = {1, (int32_t)nx, (int32_t)(nx * ny)};
+  Stencil s;
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
+    const int32_t base = (int32_t)cc - (int32_t)idx[ax] * stride[ax];
+    // minus face
+    if (idx[ax] > 0) s.nb[2 * ax] = (int32_t)cc - stride[ax];
+    else s.nb[2 * ax] = a.per[ax] ? base + (int32_t)(n[ax] - 1) * stride[ax] : -1;
+    // plus face
+    if (idx[ax] + 1 < n[ax]) s.nb[2 * ax + 1] = (int32_t)cc + stride[ax];
+    else s.nb[2 * ax + 1] = a.per[ax] ? base : -1;
+  }
+  return s;
+}
+
+// (A v)(c) = v_c - sum_faces coef_a (v_nb - v_c) for one field
+template <class T>
+__device__ __forceinline__ T apply_A(const Stencil& st, const T* cf, const T* v, int64_t c) {
+  using A = CgA<T>;
+  const T vc = ldx(v + c);
+  T lap = A::zero();
 #pragma unroll
-    for (int s = -1; s <= 1; s += 2) {
-      int t = idx[ax] + s;
-      int64_t cn;
-      if (t < 0 || t >= n[ax]) {
-        if (!a.per[ax]) continue;
-        t = (t + n[ax]) % n[ax];
-      }
-      cn = c + (int64_t)(t - idx[ax]) * stride[ax];
-      lap = A::add(lap, A::mul(cf[ax], A::sub(get(cn), vc)));
-    }
+  for (int k = 0; k < 6; ++k) {
+    if (st.nb[k] < 0) continue;
+    lap = A::add(lap, A::mul(cf[k >> 1], A::sub(ldx(v + st.nb[k]), vc)));
   }
   return A::sub(vc, lap);
 }
 
+// Chebyshev semi-iteration for A x = b, spectrum of A in [1, lmax] (A = I - dtau L
+// with the zero-flux / periodic 7-point Laplacian: lambda_min = 1 exactly,
+// lambda_max <= 1 + 4 sum_a coef_a by Gershgorin).  Three-term recurrence:
+//   r0 = b - A x0, d0 = r0 / theta, rho0 = delta / theta
+//   x += d ; r -= A d ; rho' = 1 / (2 theta/delta - rho) ; d = rho' rho d + (2 rho'/delta) r
+// (theta, delta: centre and half-width of the spectrum).  The residual obeys
+// ||r_k|| <= 2 sigma^k ||r_0||, sigma = (sqrt(kappa)-1)/(sqrt(kappa)+1), so the
+// iteration count is fixed up front from ||r_0|| / ||b|| and confirmed by one
+// residual reduction; no dot product inside the loop, one grid barrier per
+// iteration.  With x0 = b (or a guess shifted to sum(b)), 1^T r = 0 and 1^T d = 0
+// throughout, so every iterate keeps sum(x) = sum(b).
 template <class T>
 __global__ void __launch_bounds__(kSmoothThreads) k_smooth(SmoothArgs a) {
   using A = CgA<T>;
@@ -271,17 +309,26 @@ __global__ void __launch_bounds__(kSmoothThreads) k_smooth(SmoothArgs a) {
   T* Bv = (T*)a.b;
   T* R = (T*)a.r;
   T* Q = (T*)a.q;
-  const T cf[3] = {A::from_d(a.coef[0]), A::from_d(a.coef[1]), A::from_d(a.coef[2])};
+  const T cf[3] = {coef_word<T>(a, 0), coef_word<T>(a, 1), coef_word<T>(a, 2)};
   __shared__ double s_bb[kMaxF], s_rr[kMaxF], s_tmp[kMaxF], s_tmp2[kMaxF];
+  __shared__ T s_word[kMaxF];
   __shared__ int s_active[kMaxF];
+  __shared__ T s_c1, s_c2, s_inv_theta;
+  __shared__ int s_kmin;
   int iters[kMaxF];
   for (int f = 0; f < kMaxF; ++f) iters[f] = 0;
   T acc[kMaxF], acc2[kMaxF];
   double* part0 = a.part;
   double* part1 = a.part + (int64_t)kMaxF * G;
+  const double theta = 0.5 * (a.lmax + 1.0), delta = 0.5 * (a.lmax - 1.0);
+  const double sigma1 = theta / delta;
+  const double kappa = a.lmax;
+  const double sq = sqrt(kappa);
+  const double sig = (sq - 1.0) / (sq + 1.0);
+  if (threadIdx.x == 0) s_inv_theta = A::from_d(1.0 / theta);
+  __syncthreads();
 
   for (int m = 0; m < a.n_tau; ++m) {
-    // b = x (and optional projected guess on the first pseudo-step)
     const bool use_guess = (m == 0 && a.guess != nullptr);
     for (int f = 0; f < nf; ++f) { acc[f] = A::zero(); acc2[f] = A::zero(); }
     for (int64_t c = tid; c < C; c += nthr)
@@ -299,116 +346,115 @@ __global__ void __launch_bounds__(kSmoothThreads) k_smooth(SmoothArgs a) {
       if (!grid_barrier(a.ctl, G)) return;
       grid_sums(part0, nf, G, s_tmp);
       grid_sums(part1, nf, G, s_tmp2);
-      for (int f = 0; f < nf; ++f) {
-        const T shift = A::from_d((s_tmp[f] - s_tmp2[f]) / (double)C);
-        for (int64_t c = tid; c < C; c += nthr)
-          X[f * C + c] = A::add(ldx((const T*)a.guess + f * C + c), shift);
-      }
+      if (threadIdx.x < nf)
+        s_word[threadIdx.x] = A::from_d((s_tmp[threadIdx.x] - s_tmp2[threadIdx.x]) / (double)C);
+      __syncthreads();
+      for (int64_t c = tid; c < C; c += nthr)
+        for (int f = 0; f < nf; ++f)
+          X[f * C + c] = A::add(ldx((const T*)a.guess + f * C + c), s_word[f]);
     }
     if (!grid_barrier(a.ctl, G)) return;
-    // r = b - A x ; partials b.b and r.r
+    // r = b - A x ; d = r / theta ; partials b.b and r.r
     for (int f = 0; f < nf; ++f) { acc[f] = A::zero(); acc2[f] = A::zero(); }
-    for (int64_t c = tid; c < C; c += nthr)
+    T* D0 = (T*)a.p[0];
+    for (int64_t c = tid; c < C; c += nthr) {
+      const Stencil sc = stencil_of(a, c);
       for (int f = 0; f < nf; ++f) {
-        const T* xf = X + f * C;
-        const T ax = apply_A<T>(a, cf, c, [&](int64_t k) { return ldx(xf + k); });
+        const T ax = apply_A<T>(sc, cf, X + f * C, c);
         const T bv = ldx(Bv + f * C + c);
         const T rv = A::sub(bv, ax);
         R[f * C + c] = rv;
+        D0[f * C + c] = A::mul(rv, s_inv_theta);
         acc[f] = A::add(acc[f], A::mul(bv, bv));
         acc2[f] = A::add(acc2[f], A::mul(rv, rv));
       }
+    }
     block_partials<T>(acc, nf, part0, G);
     block_partials<T>(acc2, nf, part1, G);
     if (!grid_barrier(a.ctl, G)) return;
     grid_sums(part0, nf, G, s_bb);
     grid_sums(part1, nf, G, s_rr);
-    if (threadIdx.x == 0)
-      for (int f = 0; f < nf; ++f)
+    if (threadIdx.x == 0) {
+      int kmin = 0;
+      for (int f = 0; f < nf; ++f) {
         s_active[f] = (s_bb[f] > 0.0) && (s_rr[f] > a.rtol2 * s_bb[f]);
+        if (s_active[f]) {
+          // ||r_k|| <= 2 sig^k ||r_0||  ->  k >= log(rtol ||b|| / (2 ||r_0||)) / log(sig)
+          const double need = 0.5 * sqrt(a.rtol2 * s_bb[f] / s_rr[f]);
+          int k = sig > 0.0 ? (int)ceil(log(need) / log(sig)) : 1;
+          if (k < 1) k = 1;
+          if (k > kmin) kmin = k;
+        }
+      }
+      s_kmin = kmin;
+    }
     __syncthreads();
-    // fields with b = 0 have x = 0
     for (int f = 0; f < nf; ++f)
       if (!(s_bb[f] > 0.0))
         for (int64_t c = tid; c < C; c += nthr) X[f * C + c] = A::zero();
-    double beta[kMaxF];
-    for (int f = 0; f < kMaxF; ++f) beta[f] = 0.0;
     int any = 0;
     for (int f = 0; f < nf; ++f) any |= s_active[f];
+    int kcheck = s_kmin;
+    double rho = 1.0 / sigma1;
     int it = 0;
     while (any && it < a.max_iter) {
       ++it;
-      const bool first = (it == 1);
-      const T* Pold = (const T*)a.p[it & 1];
-      T* Pnew = (T*)a.p[(it & 1) ^ 1];
-      // phase A: p = r + beta p_old ; q = A p ; p.q
-      for (int f = 0; f < nf; ++f) acc[f] = A::zero();
-      for (int f = 0; f < nf; ++f) {
-        if (!s_active[f]) continue;
-        const T bt = A::from_d(beta[f]);
-        const T* rf = R + f * C;
-        const T* pf = Pold + f * C;
-        for (int64_t c = tid; c < C; c += nthr) {
-          const T pc = stencil_val<T>(rf, pf, bt, first, c);
-          const T qv = apply_A<T>(a, cf, c, [&](int64_t k) { return stencil_val<T>(rf, pf, bt, first, k); });
-          Pnew[f * C + c] = pc;
-          Q[f * C + c] = qv;
-          acc[f] = A::add(acc[f], A::mul(pc, qv));
-        }
-      }
-      block_partials<T>(acc, nf, part0, G);
-      if (!grid_barrier(a.ctl, G)) return;
-      grid_sums(part0, nf, G, s_tmp);
-      // phase B: x += alpha p ; r -= alpha q ; r.r
-      for (int f = 0; f < nf; ++f) acc[f] = A::zero();
-      for (int f = 0; f < nf; ++f) {
-        if (!s_active[f]) continue;
-        const T al = A::from_d(s_rr[f] / s_tmp[f]);
-        for (int64_t c = tid; c < C; c += nthr) {
-          const int64_t k = f * C + c;
-          const T pv = ldx(Pnew + k);
-          const T qv = ldx(Q + k);
-          X[k] = A::add(ldx(X + k), A::mul(al, pv));
-          const T rv = A::sub(ldx(R + k), A::mul(al, qv));
-          R[k] = rv;
-          acc[f] = A::add(acc[f], A::mul(rv, rv));
-        }
-      }
-      block_partials<T>(acc, nf, part1, G);
-      if (!grid_barrier(a.ctl, G)) return;
-      grid_sums(part1, nf, G, s_tmp2);
-      int act[kMaxF];
-      for (int f = 0; f < nf; ++f) {
-        act[f] = s_active[f];
-        if (!act[f]) continue;
-        const double rr_new = s_tmp2[f];
-        if (rr_new <= a.rtol2 * s_bb[f]) {
-          iters[f] += it;
-          act[f] = 0;
-        } else {
-          beta[f] = rr_new / s_rr[f];
-        }
+      // scalars of this iteration (block thread 0, broadcast)
+      const double rho_new = 1.0 / (2.0 * sigma1 - rho);
+      if (threadIdx.x == 0) {
+        s_c1 = A::from_d(rho_new * rho);
+        s_c2 = A::from_d(2.0 * rho_new / delta);
       }
       __syncthreads();
-      if (threadIdx.x == 0)
+      rho = rho_new;
+      const T c1 = s_c1, c2 = s_c2;
+      const T* Dold = (const T*)a.p[(it - 1) & 1];
+      T* Dnew = (T*)a.p[it & 1];
+      const bool check = (it >= kcheck);
+      for (int f = 0; f < nf; ++f) acc[f] = A::zero();
+      for (int64_t c = tid; c < C; c += nthr) {
+        const Stencil sc = stencil_of(a, c);
         for (int f = 0; f < nf; ++f) {
-          if (s_active[f]) s_rr[f] = s_tmp2[f];
-          s_active[f] = act[f];
+          if (!s_active[f]) continue;
+          const int64_t k = f * C + c;
+          const T dv = ldx(Dold + k);
+          const T ad = apply_A<T>(sc, cf, Dold + f * C, c);
+          X[k] = A::add(ldx(X + k), dv);
+          const T rv = A::sub(ldx(R + k), ad);
+          R[k] = rv;
+          Dnew[k] = A::add(A::mul(c1, dv), A::mul(c2, rv));
+          if (check) acc[f] = A::add(acc[f], A::mul(rv, rv));
         }
-      __syncthreads();
-      any = 0;
-      for (int f = 0; f < nf; ++f) any |= act[f];
+      }
+      if (check) block_partials<T>(acc, nf, part0, G);
+      if (!grid_barrier(a.ctl, G)) return;
+      if (check) {
+        grid_sums(part0, nf, G, s_tmp);
+        if (threadIdx.x == 0)
+          for (int f = 0; f < nf; ++f)
+            if (s_active[f] && s_tmp[f] <= a.rtol2 * s_bb[f]) s_active[f] = -it;
+        __syncthreads();
+        any = 0;
+        for (int f = 0; f < nf; ++f) {
+          if (s_active[f] < 0) iters[f] += -s_active[f];
+          any |= s_active[f] > 0;
+        }
+        __syncthreads();
+        if (threadIdx.x < nf && s_active[threadIdx.x] < 0) s_active[threadIdx.x] = 0;
+        __syncthreads();
+        kcheck = it + 2;
+      }
     }
     for (int f = 0; f < nf; ++f)
       if (s_active[f]) {
         iters[f] += a.max_iter;
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS((int*)&a.ctl->cg_status, 0, -6);
       }
-    // x of this pseudo-step must be complete before the next copies it into b
     if (!grid_barrier(a.ctl, G)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0)
     for (int f = 0; f < nf; ++f) a.iters[f] += iters[f];
+  (void)Q;
 }
 
 __global__ void k_bar_reset(Ctl* ctl) {
@@ -418,34 +464,34 @@ __global__ void k_bar_reset(Ctl* ctl) {
 
 // ---------------------------------------------------------------- conversions
 template <class T>
-__device__ __forceinline__ T t_from_fixed(long long q, double scale);
+__device__ __forceinline__ T t_from_fixed(long long q, double scale, float scalef);
 template <>
-__device__ __forceinline__ double t_from_fixed<double>(long long q, double scale) {
+__device__ __forceinline__ double t_from_fixed<double>(long long q, double scale, float) {
   return (double)q * scale;
 }
 template <>
-__device__ __forceinline__ dd t_from_fixed<dd>(long long q, double scale) {
+__device__ __forceinline__ dd t_from_fixed<dd>(long long q, double, float s) {
   // exact split of the integer, then an exact power-of-two scaling of both words
   const float hi = __ll2float_rn(q);
   const long long rest = q - (long long)hi;
   const float lo = __ll2float_rn(rest);
-  const float s = (float)scale;
   return quick_two_sum(hi * s, lo * s);
 }
 template <>
-__device__ __forceinline__ float t_from_fixed<float>(long long q, double scale) {
-  return (float)((double)q * scale);
+__device__ __forceinline__ float t_from_fixed<float>(long long q, double, float s) {
+  return __ll2float_rn(q) * s;
 }
 
 template <class T>
 __global__ void k_from_fixed(const long long* q, T* phi, int64_t C, double s0, double s1,
-                             double s2, int nf) {
+                             double s2, float f0, float f1, float f2, int nf) {
   const int64_t n = (int64_t)nf * C;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int f = (int)(k / C);
     const double s = f == 0 ? s0 : (f < 4 ? s1 : s2);
-    phi[k] = t_from_fixed<T>(q[k], s);
+    const float sf = f == 0 ? f0 : (f < 4 ? f1 : f2);
+    phi[k] = t_from_fixed<T>(q[k], s, sf);
   }
 }
 
@@ -488,9 +534,24 @@ inline unsigned grid_for(int64_t n, int block) {
 }
 
 template <class T>
+int smooth_impl_sized(const DevParams& P, void* phi, const void* guess, int nf, void* work,
+                      size_t stride_bytes, const DevState& st, int* iters_dev, double rtol,
+                      int max_iter, int n_tau, const double coef[3], int max_blocks,
+                      cudaStream_t s);
+
+template <class T>
 int smooth_impl(const DevParams& P, void* phi, const void* guess, int nf, void* work,
                 const DevState& st, int* iters_dev, double rtol, int max_iter, int n_tau,
                 const double coef[3], cudaStream_t s) {
+  return smooth_impl_sized<T>(P, phi, guess, nf, work, (size_t)nf * P.C * sizeof(T), st, iters_dev,
+                              rtol, max_iter, n_tau, coef, 152 * 8, s);
+}
+
+template <class T>
+int smooth_impl_sized(const DevParams& P, void* phi, const void* guess, int nf, void* work,
+                      size_t stride_bytes, const DevState& st, int* iters_dev, double rtol,
+                      int max_iter, int n_tau, const double coef[3], int max_blocks,
+                      cudaStream_t s) {
   const int64_t C = P.C;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -500,10 +561,11 @@ int smooth_impl(const DevParams& P, void* phi, const void* guess, int nf, void* 
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smooth<T>, kSmoothThreads, 0);
   if (per_sm < 1) return -3;
   if (per_sm > 2) per_sm = 2;
-  const unsigned G = (unsigned)(nsm * per_sm);
+  unsigned G = (unsigned)(nsm * per_sm);
+  if ((int)G > max_blocks) G = (unsigned)max_blocks;
   SmoothArgs a{};
   char* w = (char*)work;
-  const size_t fb = (size_t)nf * C * sizeof(T);
+  const size_t fb = stride_bytes;
   a.x = phi;
   a.b = w;
   a.r = w + fb;
@@ -519,7 +581,11 @@ int smooth_impl(const DevParams& P, void* phi, const void* guess, int nf, void* 
     a.nc[k] = P.nc[k];
     a.per[k] = P.periodic[k];
     a.coef[k] = coef[k];
+    const float hi = (float)coef[k];
+    a.coef_dd[k] = dd{hi, (float)(coef[k] - (double)hi)};
   }
+  a.lmax = 1.0 + 4.0 * (coef[0] + coef[1] + coef[2]);
+  if (a.lmax < 1.0 + 1e-12) a.lmax = 1.0 + 1e-12;
   a.rtol2 = rtol * rtol;
   a.max_iter = max_iter;
   a.n_tau = n_tau;
@@ -551,11 +617,12 @@ void launch_deposit(int form, const DevState& st, const DevMesh& mesh, const Dev
 void launch_fields_from_fixed(int form, const void* q, const DevParams& P, void* phi, int nf,
                               cudaStream_t s) {
   const double s0 = 1.0 / P.two_shift[0], s1 = 1.0 / P.two_shift[1], s2 = 1.0 / P.two_shift[2];
+  const float f0 = (float)s0, f1 = (float)s1, f2 = (float)s2;  // exact powers of two
   const unsigned g = grid_for((int64_t)nf * P.C, 256);
   if (form == FORM_SPLIT)
-    k_from_fixed<dd><<<g, 256, 0, s>>>((const long long*)q, (dd*)phi, P.C, s0, s1, s2, nf);
+    k_from_fixed<dd><<<g, 256, 0, s>>>((const long long*)q, (dd*)phi, P.C, s0, s1, s2, f0, f1, f2, nf);
   else if (form == FORM_FP64)
-    k_from_fixed<double><<<g, 256, 0, s>>>((const long long*)q, (double*)phi, P.C, s0, s1, s2, nf);
+    k_from_fixed<double><<<g, 256, 0, s>>>((const long long*)q, (double*)phi, P.C, s0, s1, s2, f0, f1, f2, nf);
   // the plain form deposits floats straight into phi
 }
 
@@ -601,3 +668,4 @@ void launch_phi_from_double(int form, const double* in, void* phi, int64_t n, cu
 }
 
 }  // namespace sedi
+

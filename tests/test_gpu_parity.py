@@ -158,8 +158,9 @@ def test_smoothing_matches_oracle(small, form):
     phi[rng.random((7, C)) < 0.6] = 0.0
     sg, itg = g.smooth(phi)
     so, ito = o.smooth(phi)
+    # Chebyshev iterations on the GPU, CG in the oracle: same system, same tolerance
     assert np.all(itg > 0)
-    assert np.all(np.abs(itg - ito) <= 2 * prm["n_tau"])
+    assert np.all(itg <= 2 * ito + 4 * prm["n_tau"])
     for f in range(7):
         assert np.abs(sg[f] - so[f]).max() <= 1e-7 * np.abs(phi[f]).max()
         assert abs(sg[f].sum() - phi[f].sum()) <= 1e-9 * phi[f].sum()

@@ -103,6 +103,7 @@ def test_p10_lubrication_log_law(oracle_mod):
     mu = p["rho_f"] * p["nu_f"]
     k = 6 * math.pi * mu * r * r / m
     checked = 0
+    steps = 0
     for target in (h0 / 3, h0 / 10):
         while True:
             x, v, _, _ = o.get_particles()
@@ -110,6 +111,8 @@ def test_p10_lubrication_log_law(oracle_mod):
             if h <= target:
                 break
             o.step(10)
+            steps += 10
+            assert steps < 200000, "the sphere stopped short of the wall"
         o.step(1)
         x2, v2, _, _ = o.get_particles()
         # v is the half-step velocity between the two positions

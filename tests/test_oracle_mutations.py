@@ -1,0 +1,66 @@
+"""The pins catch plausible mistakes: each mutation below is planted in a copy of
+the oracle sources (CPU only), the copy is built, and at least one pin must fail.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# (file, original text, mutated text, pin tests that must catch it)
+MUTATIONS = [
+    ("orc_contact.cpp", "double la = ra - 0.5 * delta, lb = rb - 0.5 * delta;",
+     "double la = ra, lb = rb;", "test_p4"),
+    ("orc_contact.cpp", "V3 Fn = sub(scl(-kn * delta * std::sqrt(delta), n), scl(cn, vn));",
+     "V3 Fn = add(scl(-kn * delta * std::sqrt(delta), n), scl(cn, vn));", "test_p2"),
+    ("orc_contact.cpp", "double kn = (4.0 / 3.0) * mat.Es * std::sqrt(Rs);",
+     "double kn = (4.0 / 3.0) * mat.Es * Rs;", "test_p1"),
+    ("orc_contact.cpp", "out.Ta = cross(scl(la, n), Ft);", "out.Ta = cross(Ft, scl(la, n));", "test_p4"),
+    ("orc_contact.cpp", "out.Ta = cross(scl(l, n), Ft);", "out.Ta = cross(Ft, scl(l, n));", "test_p13"),
+    ("orc_contact.cpp", "  if (ft > p.friction * fn) {", "  if (false) {", "test_p13"),
+    ("orc_contact.cpp", "return scl(-6.0 * M_PI * mu * r * r * vn / hh, n);",
+     "return scl(-6.0 * M_PI * mu * r * vn / hh, n);", "test_p10"),
+    ("orc_fluid.cpp", "double c = 0.63 + 4.8 * std::sqrt(Vr / Re);\n  double Cd = c * c;",
+     "double c = 0.63 + 0.48 * std::sqrt(Vr / Re);\n  double Cd = c * c;", "test_p3"),
+    ("orc_fluid.cpp", "f = add(f, scl(p.c_add * p.rho_f * Vp, sub(Du, a_prev)));",
+     "f = add(f, scl(p.c_add * p.rho_f * Vp, sub(a_prev, Du)));", "added_mass_initial"),
+    ("orc_fluid.cpp", "double s = (x - p.lo[a]) * inv - 0.5;", "double s = (x - p.lo[a]) * inv;",
+     "test_trilinear"),
+    ("orc_average.cpp", "if (!p.periodic[a]) continue; /* no flux through this face */",
+     "if (!p.periodic[a]) { lap += coef[a] * (0.0 - x[c]); continue; }", "test_p6"),
+    ("orc_average.cpp", "double D = 0.25 * p.bandwidth[a] * p.bandwidth[a];",
+     "double D = 0.5 * p.bandwidth[a] * p.bandwidth[a];", "test_p7"),
+    ("orc_average.cpp", "*q = (int64_t)std::llrint(s);", "*q = (int64_t)s;", "test_p8"),
+    ("orc_neighbors.cpp", "  return d2 < rc * rc;", "  return d2 <= rc * rc * 0.999;", "test_p5"),
+    ("orc_step.cpp", "h->x[i] = xn;", "h->x[i] = orc::add(h->x[i], orc::scl(p.dt, orc::sub(h->v[i], orc::scl(p.dt, a))));",
+     "test_p1"),
+]
+
+
+@pytest.fixture(scope="module")
+def workdir(tmp_path_factory):
+    return tmp_path_factory.mktemp("mut")
+
+
+@pytest.mark.parametrize("k", range(len(MUTATIONS)))
+def test_pin_catches_mutation(workdir, k):
+    fname, orig, mut, pin = MUTATIONS[k]
+    d = workdir / f"m{k}"
+    pkg = d / "oracle"
+    shutil.copytree(os.path.join(ROOT, "oracle"), pkg,
+                    ignore=shutil.ignore_patterns("*.so", "__pycache__"))
+    src = (pkg / fname).read_text()
+    assert src.count(orig) == 1, f"mutation anchor not found: {orig!r}"
+    (pkg / fname).write_text(src.replace(orig, mut))
+    tests = d / "tests"
+    shutil.copytree(os.path.join(ROOT, "tests"), tests,
+                    ignore=shutil.ignore_patterns("__pycache__", "test_gpu*", "test_zz*",
+                                                  "test_abi.py", "test_oracle_mutations.py"))
+    env = dict(os.environ, PYTHONPATH=f"{d}:{ROOT}")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        "-k", pin, str(tests)], cwd=d, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 1, f"pin {pin} did not catch mutation {k}:\n{r.stdout[-2000:]}"
