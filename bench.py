@@ -112,6 +112,24 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def aggregate(total_ms_local, particles_local, steps, world, device="cpu"):
+    """Whole-job throughput over ranks: every rank ran its own bed for `steps`
+    steps; the job time is the slowest rank's (max over ranks)."""
+    total_ms = float(total_ms_local)
+    parts = float(particles_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        p = torch.tensor([parts], dtype=torch.float64, device=device)
+        dist.all_reduce(p, op=dist.ReduceOp.SUM)
+        parts = float(p.item())
+    value = parts * SUBSTEPS * steps / (total_ms / 1e3)
+    return value, total_ms
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -180,13 +198,7 @@ def gpu_arm(args):
 
     g = make("split", 1)
     ms, t0, t1, st0, st1, clocks = timed_steps(g, args.steps, args.warmup)
-    total_ms = float(np.sum(ms))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * n * SUBSTEPS * args.steps / (total_ms / 1e3)
+    value, total_ms = aggregate(float(np.sum(ms)), n, args.steps, world, device="cuda")
     ms_per_step = total_ms / args.steps
 
     # roofline of the dominant kernel (fused substep): algorithmic bytes per launch

@@ -33,7 +33,8 @@ struct Ctl {
   int32_t deposit_range;   // a deposited value overflowed the fixed-point format
   int32_t cg_status;       // 0 or SEDI_EDIVERGED / SEDI_ETIMEOUT from the smoother
   uint32_t bar_count, bar_gen;  // grid barrier of the persistent smoother
-  int32_t pad[3];
+  uint32_t blocks_done;    // completion counter of the substep kernel
+  int32_t pad[2];
 };
 
 // Constants of the force arithmetic, precomputed on the host in the force word
@@ -79,6 +80,8 @@ struct DevParams {
   // deposition
   int32_t shift[3];                // eps, momentum, force
   double two_shift[3];             // 2^shift
+  float two_shift_f;               // 2^shift[2] (exact in FP32)
+  float inv_vc_f;                  // 1 / V_c in FP32
 };
 
 template <class F>
@@ -124,6 +127,8 @@ struct Num<float> {
   __device__ static float fma_ff(float a, float b, float c) { return fmaf(b, c, a); }
   __device__ static bool lt(float a, float b) { return a < b; }
   __device__ static float dif(float a, float b) { return a - b; }
+  __device__ static float addq(float a, float b) { return a + b; }
+  __device__ static float subq(float a, float b) { return a - b; }
 };
 
 template <>
@@ -139,6 +144,8 @@ struct Num<double> {
   __device__ static double fma_ff(double a, double b, double c) { return a + b * c; }
   __device__ static bool lt(double a, double b) { return a < b; }
   __device__ static double dif(double a, double b) { return a - b; }
+  __device__ static double addq(double a, double b) { return a + b; }
+  __device__ static double subq(double a, double b) { return a - b; }
 };
 
 template <>
@@ -157,6 +164,9 @@ struct Num<dd> {
   __device__ static float dif(dd a, dd b) {
     return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo));
   }
+  // additions whose error is relative to the operands (see dd_add_fast)
+  __device__ static dd addq(dd a, dd b) { return dd_add_fast(a, b); }
+  __device__ static dd subq(dd a, dd b) { return dd_sub_fast(a, b); }
 };
 
 template <class S>
@@ -225,7 +235,7 @@ struct DevState {
   float4* xb[2];      // position at the last rebuild (pb parity)
   void* whist[2];     // S [6 walls][3][N] springs (pb parity)
   uint32_t* wmask[2]; // bit w: wall spring w in use (pb parity)
-  int32_t* nbr[2];    // [cap][N] neighbour index (nl parity)
+  int32_t* nbr[2];    // [cap][N] list entry: partner index | first-in-pair bit (nl parity)
   int32_t* nn[2];     // [N] list length (nl parity)
   void* hist[2];      // S [3][cap][N] pair springs (nl parity)
   uint32_t* cmask[2]; // bit k: slot k holds a spring (nl parity)
@@ -250,5 +260,11 @@ struct DevMesh {
 };
 
 constexpr int kWalls = 6;
+
+// A list entry holds the partner index in bits 0-30 and, in bit 31, whether the
+// owner comes first in canonical pair order (lower caller index).
+constexpr uint32_t kFirstBit = 0x80000000u;
+__host__ __device__ __forceinline__ int32_t nbr_index(int32_t e) { return e & 0x7fffffff; }
+__host__ __device__ __forceinline__ bool nbr_first(int32_t e) { return ((uint32_t)e & kFirstBit) != 0; }
 
 }  // namespace sedi

@@ -206,6 +206,8 @@ void fill_params(sedi_handle* h) {
   P.shift[1] = p.shift_mom;
   P.shift[2] = p.shift_force;
   for (int k = 0; k < 3; ++k) P.two_shift[k] = std::ldexp(1.0, P.shift[k]);
+  P.two_shift_f = (float)P.two_shift[2];
+  P.inv_vc_f = (float)(1.0 / P.vc);
   const double dtau = 1.0 / p.n_tau;
   const double hs[3] = {dx, dy, dz};
   for (int a = 0; a < 3; ++a) {
@@ -377,24 +379,27 @@ int build_graph(sedi_handle* h, int n, cudaGraphExec_t* out) {
       ev.c.push_back(new_event());
     }
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &g, &deps, nullptr, &nd));
+  // one IF node per substep: the first condition comes from a check kernel, every
+  // later one from the last block of the previous substep kernel
+  std::vector<cudaGraphConditionalHandle> ch(n);
+  for (int s = 0; s < n; ++s) CK(cudaGraphConditionalHandleCreate(&ch[s], g, 0, cudaGraphCondAssignDefault));
+  // inside a capture only the External flag makes an event-record node
+  if (h->prm.profile) CK(cudaEventRecordWithFlags(ev.a[0], h->stream, cudaEventRecordExternal));
+  launch_check(h->st, h->P, (unsigned long long)ch[0], 1, h->stream);
   for (int s = 0; s < n; ++s) {
-    // inside a capture only the External flag makes an event-record node
-    if (h->prm.profile) CK(cudaEventRecordWithFlags(ev.a[s], h->stream, cudaEventRecordExternal));
-    cudaStreamCaptureStatus cs;
-    cudaGraph_t g;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t nd = 0;
-    CK(cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &g, &deps, nullptr, &nd));
-    cudaGraphConditionalHandle ch;
-    CK(cudaGraphConditionalHandleCreate(&ch, g, 0, cudaGraphCondAssignDefault));
-    launch_check(h->st, h->P, (unsigned long long)ch, 1, h->stream);
+    if (h->prm.profile && s > 0) CK(cudaEventRecordWithFlags(ev.a[s], h->stream, cudaEventRecordExternal));
     CK(cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &g, &deps, nullptr, &nd));
     // the struct has a union of non-trivial members: zero raw storage instead
     alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
     std::memset(raw, 0, sizeof(raw));
     cudaGraphNodeParams* cp = reinterpret_cast<cudaGraphNodeParams*>(raw);
     cp->type = cudaGraphNodeTypeConditional;
-    cp->conditional.handle = ch;
+    cp->conditional.handle = ch[s];
     cp->conditional.type = cudaGraphCondTypeIf;
     cp->conditional.size = 1;
     cudaGraphNode_t node;
@@ -405,7 +410,9 @@ int build_graph(sedi_handle* h, int n, cudaGraphExec_t* out) {
     launch_rebuild(h->form, h->st, h->P, s, false, h->side);
     CK(cudaStreamEndCapture(h->side, &body));
     if (h->prm.profile) CK(cudaEventRecordWithFlags(ev.b[s], h->stream, cudaEventRecordExternal));
-    launch_substep(h->form, h->st, h->mesh, h->P, s, true, h->block, h->stream);
+    const bool more = s + 1 < n;
+    launch_substep(h->form, h->st, h->mesh, h->P, s, true, h->block,
+                   more ? (unsigned long long)ch[s + 1] : 0ull, more ? 1 : 0, h->stream);
     if (h->prm.profile) CK(cudaEventRecordWithFlags(ev.c[s], h->stream, cudaEventRecordExternal));
   }
   launch_advance_parity(h->st, n, h->stream);
@@ -690,10 +697,11 @@ int sedi_step(sedi_handle* h, int32_t n) {
     }
     for (int s = 0; s < n; ++s) {
       if (h->prm.profile) CK(cudaEventRecord(h->gev[-n].a[s], h->stream));
-      launch_check(h->st, h->P, 0ull, 0, h->stream);
+      // the substep kernel's last block sets need_rebuild for the next substep
+      if (s == 0) launch_check(h->st, h->P, 0ull, 0, h->stream);
       launch_rebuild(h->form, h->st, h->P, s, false, h->stream);
       if (h->prm.profile) CK(cudaEventRecord(h->gev[-n].b[s], h->stream));
-      launch_substep(h->form, h->st, h->mesh, h->P, s, true, h->block, h->stream);
+      launch_substep(h->form, h->st, h->mesh, h->P, s, true, h->block, 0ull, 0, h->stream);
       if (h->prm.profile) {
         CK(cudaEventRecord(h->gev[-n].c[s], h->stream));
         h->pending.push_back({0, {h->gev[-n].a[s], h->gev[-n].b[s]}});
@@ -884,7 +892,7 @@ int sedi_compute_forces(sedi_handle* h, int32_t bed, double* fc, double* fl, dou
   // lists must cover the current positions
   launch_check(h->st, h->P, 0ull, 0, h->stream);
   launch_rebuild(h->form, h->st, h->P, 0, false, h->stream);
-  launch_substep(h->form, h->st, h->mesh, h->P, 0, false, h->block, h->stream);
+  launch_substep(h->form, h->st, h->mesh, h->P, 0, false, h->block, 0ull, 0, h->stream);
   // fdbg is in sorted order: scatter to caller order through the host
   std::vector<double> dbg(12 * N);
   std::vector<int32_t> uid(N);

@@ -91,8 +91,8 @@ __device__ __forceinline__ void fluid_force(const DevParams& P, const ForceConst
     F w0 = U[0] - v[0], w1 = U[1] - v[1], w2 = U[2] - v[2];
     F wm = xsqrt(w0 * w0 + w1 * w1 + w2 * w2);
     F Re = d * wm / K.nu_f;
-    F A1 = xpow(ef, F(4.14));
-    F A2 = ef <= F(0.85) ? F(0.8) * xpow(ef, F(1.28)) : xpow(ef, F(2.65));
+    F A1 = xpow_drag(ef, F(4.14));
+    F A2 = ef <= F(0.85) ? F(0.8) * xpow_drag(ef, F(1.28)) : xpow_drag(ef, F(2.65));
     F t = F(0.06) * Re;
     F Vr = F(0.5) * (A1 - t + xsqrt(t * t + F(0.12) * Re * (F(2) * A2 - A1) + A1 * A1));
     F c = F(0.63) * xsqrt(wm) + F(4.8) * xsqrt(Vr * K.nu_f / d);

@@ -49,8 +49,18 @@ __global__ void k_deposit(DevState st, DevMesh mesh, DevParams P, void* qout) {
     int64_t cc[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      double s = __dmul_rn(__dsub_rn(NS::d(xs[a]), P.lo[a]), P.inv_h[a]);
-      int64_t k = (int64_t)floor(s);
+      // the cell must equal floor((x - lo) * n / L) in FP64; FP32 decides unless x
+      // lies within ~1e-4 of a cell face, where the FP64 product is formed
+      int64_t k;
+      const float sf = (float)NS::f(NS::sub(xs[a], sbox<S>(P).lo[a])) * P.cf.inv_h[a];
+      const float fl = floorf(sf);
+      const float fr = sf - fl;
+      if (FORM != FORM_FP64 && fr > 1e-4f && fr < 1.0f - 1e-4f) {
+        k = (int64_t)fl;
+      } else {
+        const double s = __dmul_rn(__dsub_rn(NS::d(xs[a]), P.lo[a]), P.inv_h[a]);
+        k = (int64_t)floor(s);
+      }
       if (k < 0) k = 0;
       if (k > P.nc[a] - 1) k = P.nc[a] - 1;
       cc[a] = k;
@@ -62,29 +72,53 @@ __global__ void k_deposit(DevState st, DevMesh mesh, DevParams P, void* qout) {
     fluid_force<S, F>(P, K, (const Quad<F>*)mesh.ufe, (const Quad<F>*)mesh.gfl, xs, NS::f(p.d), vf,
                       ap, ff);
     const double vfrac = st.vfrac[pb][i];
-    double val[7];
-    val[0] = vfrac;
-    val[1] = __dmul_rn(vfrac, NS::d(v.a));
-    val[2] = __dmul_rn(vfrac, NS::d(v.b));
-    val[3] = __dmul_rn(vfrac, NS::d(v.c));
-#pragma unroll
-    for (int a = 0; a < 3; ++a) val[4 + a] = __ddiv_rn(-(double)ff[a], P.vc);
     if (FORM == FORM_PLAIN) {
       float* q = (float*)qout;
+      const float vf32 = (float)vfrac;
+      const float inv_vc = P.cf.inv_h[0] * P.cf.inv_h[1] * P.cf.inv_h[2];
+      atomicAdd(q + cell, vf32);
+      atomicAdd(q + 1 * C + cell, vf32 * vf[0]);
+      atomicAdd(q + 2 * C + cell, vf32 * vf[1]);
+      atomicAdd(q + 3 * C + cell, vf32 * vf[2]);
 #pragma unroll
-      for (int f = 0; f < 7; ++f) atomicAdd(q + f * C + cell, (float)val[f]);
+      for (int a = 0; a < 3; ++a) atomicAdd(q + (4 + a) * C + cell, -(float)ff[a] * inv_vc);
     } else {
+      // eps and eps*U: exact FP64 products, scaled by 2^S (exact) and rounded to
+      // nearest, bit-identical to an FP64 evaluation
+      double val[4];
+      val[0] = vfrac;
+      val[1] = __dmul_rn(vfrac, NS::d(v.a));
+      val[2] = __dmul_rn(vfrac, NS::d(v.b));
+      val[3] = __dmul_rn(vfrac, NS::d(v.c));
       unsigned long long* q = (unsigned long long*)qout;
 #pragma unroll
-      for (int f = 0; f < 7; ++f) {
-        const double sc = P.two_shift[f == 0 ? 0 : (f < 4 ? 1 : 2)];
-        const double t = __dmul_rn(val[f], sc);
+      for (int f = 0; f < 4; ++f) {
+        const double t = __dmul_rn(val[f], P.two_shift[f == 0 ? 0 : 1]);
         if (!(fabs(t) < 4.0e18)) {
           atomicCAS((int*)&st.ctl->deposit_range, 0, 1);
           continue;
         }
-        const long long qi = __double2ll_rn(t);
-        atomicAdd(q + f * C + cell, (unsigned long long)qi);
+        atomicAdd(q + f * C + cell, (unsigned long long)__double2ll_rn(t));
+      }
+      // force density -f_fp / V_c in the force word, then to fixed point
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        long long qi;
+        bool ok;
+        if (FORM == FORM_FP64) {
+          const double t = __dmul_rn(__ddiv_rn(-(double)ff[a], P.vc), P.two_shift[2]);
+          ok = fabs(t) < 4.0e18;
+          qi = ok ? __double2ll_rn(t) : 0;
+        } else {
+          const float t = -(float)ff[a] * P.inv_vc_f * P.two_shift_f;
+          ok = fabsf(t) < 4.0e18f;
+          qi = ok ? __float2ll_rn(t) : 0;
+        }
+        if (!ok) {
+          atomicCAS((int*)&st.ctl->deposit_range, 0, 1);
+          continue;
+        }
+        atomicAdd(q + (4 + a) * C + cell, (unsigned long long)qi);
       }
     }
   }
@@ -102,6 +136,8 @@ struct CgA<double> {
   __device__ static double from_d(double a) { return a; }
   __device__ static double to_d(double a) { return a; }
   __device__ static double shfl_xor(double a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+  __device__ static double addq(double a, double b) { return a + b; }
+  __device__ static double subq(double a, double b) { return a - b; }
 };
 template <>
 struct CgA<float> {
@@ -112,6 +148,8 @@ struct CgA<float> {
   __device__ static float from_d(double a) { return __double2float_rn(a); }
   __device__ static double to_d(float a) { return (double)a; }
   __device__ static float shfl_xor(float a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+  __device__ static float addq(float a, float b) { return a + b; }
+  __device__ static float subq(float a, float b) { return a - b; }
 };
 template <>
 struct CgA<dd> {
@@ -124,6 +162,9 @@ struct CgA<dd> {
   __device__ static dd shfl_xor(dd a, int o) {
     return dd{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
   }
+  // additions with error ~2^-44 of the operands (see dd_add_fast)
+  __device__ static dd addq(dd a, dd b) { return dd_add_fast(a, b); }
+  __device__ static dd subq(dd a, dd b) { return dd_sub_fast(a, b); }
 };
 
 struct SmoothArgs;
@@ -279,11 +320,20 @@ __device__ __forceinline__ T apply_A(const Stencil& st, const T* cf, const T* v,
   const T vc = ldx(v + c);
   T lap = A::zero();
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    if (st.nb[k] < 0) continue;
-    lap = A::add(lap, A::mul(cf[k >> 1], A::sub(ldx(v + st.nb[k]), vc)));
+  for (int ax = 0; ax < 3; ++ax) {
+    // both faces of one axis share the coefficient: coef * ((v- - vc) + (v+ - vc))
+    T sa = A::zero();
+    bool any = false;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int32_t nb = st.nb[2 * ax + side];
+      if (nb < 0) continue;
+      sa = any ? A::addq(sa, A::subq(ldx(v + nb), vc)) : A::subq(ldx(v + nb), vc);
+      any = true;
+    }
+    if (any) lap = A::addq(lap, A::mul(cf[ax], sa));
   }
-  return A::sub(vc, lap);
+  return A::subq(vc, lap);
 }
 
 // Chebyshev semi-iteration for A x = b, spectrum of A in [1, lmax] (A = I - dtau L
@@ -419,10 +469,10 @@ __global__ void __launch_bounds__(kSmoothThreads) k_smooth(SmoothArgs a) {
           const int64_t k = f * C + c;
           const T dv = ldx(Dold + k);
           const T ad = apply_A<T>(sc, cf, Dold + f * C, c);
-          X[k] = A::add(ldx(X + k), dv);
-          const T rv = A::sub(ldx(R + k), ad);
+          X[k] = A::addq(ldx(X + k), dv);
+          const T rv = A::subq(ldx(R + k), ad);
           R[k] = rv;
-          Dnew[k] = A::add(A::mul(c1, dv), A::mul(c2, rv));
+          Dnew[k] = A::addq(A::mul(c1, dv), A::mul(c2, rv));
           if (check) acc[f] = A::add(acc[f], A::mul(rv, rv));
         }
       }

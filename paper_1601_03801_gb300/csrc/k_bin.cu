@@ -262,12 +262,14 @@ __global__ void k_build(DevState st, DevParams P, int sub_off, bool force) {
   const int64_t N = st.N;
   const Quad<S>* pos = (const Quad<S>*)st.pos[sb];
   const double* r64 = st.r64[qb];
+  const int32_t* uid = st.uid[qb];
   int32_t* nbr = st.nbr[ql];
   const float fr = (float)P.lub_out_frac, sk = (float)P.skin;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     const Quad<S> pi = ldq(pos + i);
     const double ri = r64[i];
+    const int32_t ui = uid[i];
     const float rif = (float)ri;
     int c[3] = {bin_axis<S>(pi.a, P, 0), bin_axis<S>(pi.b, P, 1), bin_axis<S>(pi.c, P, 2)};
     int n = 0;
@@ -309,7 +311,7 @@ __global__ void k_build(DevState st, DevParams P, int sub_off, bool force) {
               in = listed_exact(xi, xj, ri, rj, P);
             }
             if (in) {
-              if (n < P.cap) nbr[(int64_t)n * N + i] = j;
+              if (n < P.cap) nbr[(int64_t)n * N + i] = j | (ui < uid[j] ? (int32_t)kFirstBit : 0);
               ++n;
             }
           }
@@ -343,10 +345,10 @@ __global__ void k_remap(DevState st, DevParams P, bool force) {
       const int onn = st.nn[nl][o];
       const int nn = st.nn[ql][i];
       for (int k = 0; k < nn; ++k) {
-        const int32_t uj = st.uid[qb][st.nbr[ql][(int64_t)k * N + i]];
+        const int32_t uj = st.uid[qb][nbr_index(st.nbr[ql][(int64_t)k * N + i])];
         for (int kk = 0; kk < onn; ++kk) {
           if (!((omask >> kk) & 1u)) continue;
-          if (st.uid[pb][st.nbr[nl][(int64_t)kk * N + o]] != uj) continue;
+          if (st.uid[pb][nbr_index(st.nbr[nl][(int64_t)kk * N + o])] != uj) continue;
           for (int c = 0; c < 3; ++c)
             hnew[((int64_t)c * cap + k) * N + i] = hold[((int64_t)c * cap + kk) * N + o];
           nmask |= 1u << k;
@@ -505,7 +507,7 @@ __global__ void k_nbr_fill(DevState st, const int64_t* offsets, int64_t* out) {
     int64_t* o = out + offsets[u];
     const int n = st.nn[nl][i];
     for (int k = 0; k < n; ++k) {
-      int64_t v = st.uid[pb][st.nbr[nl][(int64_t)k * st.N + i]];
+      int64_t v = st.uid[pb][nbr_index(st.nbr[nl][(int64_t)k * st.N + i])];
       int c = k - 1;
       while (c >= 0 && o[c] > v) {
         o[c + 1] = o[c];
@@ -530,7 +532,7 @@ __global__ void k_contacts(DevState st, DevParams P, unsigned long long* count, 
     const int n = st.nn[nl][i];
     for (int k = 0; k < n; ++k) {
       if (!((m >> k) & 1u)) continue;
-      const int32_t uj = st.uid[pb][st.nbr[nl][(int64_t)k * st.N + i]];
+      const int32_t uj = st.uid[pb][nbr_index(st.nbr[nl][(int64_t)k * st.N + i])];
       if (uj < ui) continue;
       unsigned long long slot = atomicAdd(count, 1ull);
       if ((int64_t)slot >= cap) continue;

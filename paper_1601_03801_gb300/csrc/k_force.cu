@@ -98,8 +98,9 @@ __device__ __forceinline__ V3<F> cross(V3<F> a, V3<F> b) {
 }  // namespace
 
 template <int FORM, bool INTEGRATE>
-__global__ void __launch_bounds__(256) k_substep(DevState st, DevMesh mesh, DevParams P,
-                                                 int sub_off) {
+__global__ void __launch_bounds__(128, 6) k_substep(DevState st, DevMesh mesh, DevParams P,
+                                                    int sub_off, cudaGraphConditionalHandle next,
+                                                    int use_cond) {
   using S = typename Traits<FORM>::S;
   using F = typename Traits<FORM>::F;
   using NS = Num<S>;
@@ -116,14 +117,12 @@ __global__ void __launch_bounds__(256) k_substep(DevState st, DevMesh mesh, DevP
     const Quad<S>* pos = (const Quad<S>*)st.pos[sb];
     const Quad<S>* vel = (const Quad<S>*)st.vel[sb];
     const Quad<S>* omg = (const Quad<S>*)st.omg[sb];
-    const int32_t* uid = st.uid[pb];
     Quad<S> Pi = ldq(pos + i), Vi = ldq(vel + i), Wi = ldq(omg + i);
     Quad<F>* accp = (Quad<F>*)st.acc[pb];
     Quad<F> Ai = ldq(accp + i);
     const F ri = NS::f(Pi.d), mi = NS::f(Vi.d);
     const F vi[3] = {NS::f(Vi.a), NS::f(Vi.b), NS::f(Vi.c)};
     const F wi[3] = {NS::f(Wi.a), NS::f(Wi.b), NS::f(Wi.c)};
-    const int32_t ui = uid[i];
     V3<F> fc{0, 0, 0}, fl{0, 0, 0}, tq{0, 0, 0};
     const int32_t* nbr = st.nbr[nl];
     const int nn = st.nn[nl][i];
@@ -133,7 +132,8 @@ __global__ void __launch_bounds__(256) k_substep(DevState st, DevMesh mesh, DevP
     const int64_t cap = P.cap;
     const float lub_out_f = P.lub_out_f;
     for (int k = 0; k < nn; ++k) {
-      const int j = nbr[(int64_t)k * N + i];
+      const int32_t e = nbr[(int64_t)k * N + i];
+      const int j = nbr_index(e);
       const Quad<S> Pj = ldq(pos + j);
       // cheap FP32 cull with a relative margin (exact test follows)
       {
@@ -146,23 +146,22 @@ __global__ void __launch_bounds__(256) k_substep(DevState st, DevMesh mesh, DevP
         float cut = P.lubrication ? sr * (1.0f + lub_out_f) : sr;
         if (dx * dx + dy * dy + dz * dz > cut * cut * 1.0002f) continue;
       }
-      const int32_t uj = uid[j];
-      const bool i_lo = ui < uj;
+      const bool i_lo = nbr_first(e);
       const Quad<S>& A = i_lo ? Pi : Pj;
       const Quad<S>& Bq = i_lo ? Pj : Pi;
       // precise geometry in canonical order: dx = x_B - x_A (minimum image)
-      S dxs[3] = {NS::sub(Bq.a, A.a), NS::sub(Bq.b, A.b), NS::sub(Bq.c, A.c)};
+      S dxs[3] = {NS::subq(Bq.a, A.a), NS::subq(Bq.b, A.b), NS::subq(Bq.c, A.c)};
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         if (!P.periodic[a]) continue;
         F c = NS::f(dxs[a]);
-        if (c > K.halfL[a]) dxs[a] = NS::sub(dxs[a], B.L[a]);
-        else if (c < -K.halfL[a]) dxs[a] = NS::add(dxs[a], B.L[a]);
+        if (c > K.halfL[a]) dxs[a] = NS::subq(dxs[a], B.L[a]);
+        else if (c < -K.halfL[a]) dxs[a] = NS::addq(dxs[a], B.L[a]);
       }
-      S d2 = NS::add(NS::add(NS::mul(dxs[0], dxs[0]), NS::mul(dxs[1], dxs[1])),
-                     NS::mul(dxs[2], dxs[2]));
-      S ssum = NS::add(A.d, Bq.d);
-      S num = NS::sub(NS::mul(ssum, ssum), d2);
+      S d2 = NS::addq(NS::addq(NS::mul(dxs[0], dxs[0]), NS::mul(dxs[1], dxs[1])),
+                      NS::mul(dxs[2], dxs[2]));
+      S ssum = NS::addq(A.d, Bq.d);
+      S num = NS::subq(NS::mul(ssum, ssum), d2);
       const F dist = xsqrt(NS::f(d2));
       const F sF = NS::f(ssum);
       const F delta = NS::f(num) / (sF + dist);  // r_A + r_B - |dx|
@@ -348,26 +347,51 @@ __global__ void __launch_bounds__(256) k_substep(DevState st, DevMesh mesh, DevP
       for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
       if (lane == 0 && m > 0.0f) atomicMax(&st.ctl->disp_max_bits, __float_as_uint(m));
     }
+    // the last block to finish decides whether the lists must be rebuilt before the
+    // next substep (and sets the graph condition of that substep's rebuild node)
+    __shared__ bool last;
+    __threadfence();
+    if (threadIdx.x == 0) last = atomicAdd(&st.ctl->blocks_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+      __threadfence();
+      const float mx = __uint_as_float(atomicAdd(&st.ctl->disp_max_bits, 0u));
+      const int need = mx > P.half_skin_f * P.half_skin_f ? 1 : 0;
+      st.ctl->need_rebuild = need;
+      st.ctl->blocks_done = 0u;
+      if (use_cond) cudaGraphSetConditional(next, need ? 1u : 0u);
+    }
   }
 }
 
 template <int FORM>
 static void launch_one(const DevState& st, const DevMesh& mesh, const DevParams& P, int sub_off,
-                       bool integrate, int block, cudaStream_t s) {
-  const int64_t grid = (st.N + block - 1) / block;
+                       bool integrate, int block, unsigned long long next, int use_cond,
+                       cudaStream_t s) {
+  (void)block;
+  const int bs = 128;  // matches __launch_bounds__
+  const int64_t grid = (st.N + bs - 1) / bs;
+  const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)next;
   if (integrate)
-    k_substep<FORM, true><<<(unsigned)grid, block, 0, s>>>(st, mesh, P, sub_off);
+    k_substep<FORM, true><<<(unsigned)grid, bs, 0, s>>>(st, mesh, P, sub_off, h, use_cond);
   else
-    k_substep<FORM, false><<<(unsigned)grid, block, 0, s>>>(st, mesh, P, sub_off);
+    k_substep<FORM, false><<<(unsigned)grid, bs, 0, s>>>(st, mesh, P, sub_off, h, 0);
 }
 
 void launch_substep(int form, const DevState& st, const DevMesh& mesh, const DevParams& P,
-                    int sub_off, bool integrate, int block, cudaStream_t s) {
+                    int sub_off, bool integrate, int block, unsigned long long next_cond,
+                    int use_cond, cudaStream_t s) {
   if (st.N <= 0) return;
   switch (form) {
-    case FORM_SPLIT: launch_one<FORM_SPLIT>(st, mesh, P, sub_off, integrate, block, s); break;
-    case FORM_PLAIN: launch_one<FORM_PLAIN>(st, mesh, P, sub_off, integrate, block, s); break;
-    default: launch_one<FORM_FP64>(st, mesh, P, sub_off, integrate, block, s); break;
+    case FORM_SPLIT:
+      launch_one<FORM_SPLIT>(st, mesh, P, sub_off, integrate, block, next_cond, use_cond, s);
+      break;
+    case FORM_PLAIN:
+      launch_one<FORM_PLAIN>(st, mesh, P, sub_off, integrate, block, next_cond, use_cond, s);
+      break;
+    default:
+      launch_one<FORM_FP64>(st, mesh, P, sub_off, integrate, block, next_cond, use_cond, s);
+      break;
   }
 }
 

@@ -7,8 +7,11 @@
 namespace sedi {
 
 // k_force.cu: one fused substep (integrate = true) or forces only into st.fdbg.
+// The last block of an integrating launch sets ctl->need_rebuild and, when
+// use_cond, the graph condition next_cond of the following rebuild node.
 void launch_substep(int form, const DevState& st, const DevMesh& mesh, const DevParams& P,
-                    int sub_off, bool integrate, int block, cudaStream_t s);
+                    int sub_off, bool integrate, int block, unsigned long long next_cond,
+                    int use_cond, cudaStream_t s);
 
 // k_bin.cu: rebuild = bin, sort by (bin, caller index), gather into the other
 // buffers, build lists, carry springs over.  `conditional` kernels return at once
