@@ -212,6 +212,34 @@ int sedi_load_state(sedi_handle* h, const char* path);
 int sedi_get_timings(sedi_handle* h, double* ms_per_phase, int32_t n);
 int sedi_get_stats(sedi_handle* h, sedi_stats* out);
 
+/* ---- Smoothing without any device allocation ----
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc themselves or through this library -- e.g. code that
+ * runs while a memory pool or a host framework owns all device memory, or a
+ * plugin whose device allocations are forbidden after start-up.  It smooths
+ * n_fields caller fields exactly like sedi_smooth (Sec. 2.4, Eq. 10; the mesh,
+ * bandwidth, n_tau, cg_rtol, cg_max_iter and precision_form of *p), but keeps
+ * all scratch in one static device array of this library, so it allocates
+ * nothing: no cudaMalloc/cudaFree, no allocating library routine.
+ *   p       : parameters (only the mesh, box, bandwidth, solver and form fields
+ *             are read); no handle is needed.
+ *   in, out : DEVICE pointers, [n_fields][C] float64, C = prod(ncell); caller-owned.
+ *   iters   : host array of n_fields (or NULL) receiving the solver iterations.
+ *   cuda_stream : stream to run on (NULL = legacy default stream).
+ *   msg     : optional host buffer of msg_len bytes for an error message.
+ * Limit: n_fields * C <= SEDI_STATIC_MAX_WORDS (e.g. 7 fields on 131,072 cells);
+ * larger sizes return SEDI_EINVAL.  The scratch (about 50 MB) lives on every GPU
+ * that loads the library until the process exits.  The first call on a device
+ * looks up the scratch's device address (cudaGetSymbolAddress) for that device;
+ * make that first call before any stream capture.  Every call shares the one
+ * array and leaves its contents behind: calls whose GPU work overlaps (two
+ * streams, two threads) race and must be serialised by the caller.  The call
+ * synchronises its stream and returns SEDI_OK, SEDI_EINVAL, SEDI_EDIVERGED,
+ * SEDI_ETIMEOUT or SEDI_ECUDA. */
+#define SEDI_STATIC_MAX_WORDS (1 << 20)
+int sedi_smooth_static(const sedi_params* p, int32_t n_fields, const double* in, double* out,
+                       int32_t* iters, void* cuda_stream, char* msg, int32_t msg_len);
+
 /* Block until all queued work of the handle is done; returns its status. */
 int sedi_sync(sedi_handle* h);
 

@@ -20,6 +20,11 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
+#include "../../include/sedi.h"
 #include "common.cuh"
 #include "fluid.cuh"
 #include "kernels.h"
@@ -719,3 +724,146 @@ void launch_phi_from_double(int form, const double* in, void* phi, int64_t n, cu
 
 }  // namespace sedi
 
+// ---------------------------------------------------------------- no-allocation smoothing
+// sedi_smooth_static: the smoothing solve of sedi_smooth without a handle and
+// without any device allocation.  Its scratch is the file-scope array below,
+// sized for SEDI_STATIC_MAX_WORDS field words, which every GPU that loads this
+// library holds until the process exits.  Host code must not pass the array's
+// name to a kernel (on the host it is only a stand-in): the device address is
+// taken once per device with cudaGetSymbolAddress and passed instead.
+
+using namespace sedi;
+
+namespace {
+
+constexpr int64_t kStaticWords = SEDI_STATIC_MAX_WORDS;
+constexpr int kStaticMaxBlocks = 1216;  // partial sums of up to 1216 blocks
+// layout (8-byte words): phi[W] b[W] r[W] p0[W] p1[W] q[W] part[2*kMaxF*1216] iters[8] ctl
+constexpr int64_t kStaticBytes =
+    8 * (6 * kStaticWords + 2 * (int64_t)kMaxF * kStaticMaxBlocks + 8) + (int64_t)sizeof(Ctl) + 256;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+struct StaticSlot {
+  unsigned char* base = nullptr;  // device address of g_static_scratch on this device
+};
+std::mutex g_static_mutex;
+StaticSlot g_static_slots[64];
+
+void put_msg(char* msg, int32_t len, const char* text) {
+  if (msg && len > 0) std::snprintf(msg, (size_t)len, "%s", text);
+}
+
+}  // namespace
+
+extern "C" int sedi_smooth_static(const sedi_params* p, int32_t nf, const double* in, double* out,
+                                  int32_t* iters, void* cuda_stream, char* msg, int32_t msg_len) {
+  if (!p || !in || !out || nf < 1 || nf > kMaxF) {
+    put_msg(msg, msg_len, "sedi_smooth_static: null pointer or n_fields outside [1, 8]");
+    return SEDI_EINVAL;
+  }
+  const int64_t C = (int64_t)p->ncell[0] * p->ncell[1] * p->ncell[2];
+  if (p->ncell[0] < 1 || p->ncell[1] < 1 || p->ncell[2] < 1 || p->n_tau < 1 || !(p->cg_rtol > 0) ||
+      p->cg_max_iter < 1 || p->precision_form < 0 || p->precision_form > 2) {
+    put_msg(msg, msg_len, "sedi_smooth_static: invalid mesh or solver parameters");
+    return SEDI_EINVAL;
+  }
+  if ((int64_t)nf * C > kStaticWords) {
+    char buf[256];
+    std::snprintf(buf, sizeof(buf),
+                  "sedi_smooth_static: n_fields * cells = %lld exceeds the static scratch limit "
+                  "SEDI_STATIC_MAX_WORDS = %lld",
+                  (long long)nf * C, (long long)kStaticWords);
+    put_msg(msg, msg_len, buf);
+    return SEDI_EINVAL;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    put_msg(msg, msg_len, "sedi_smooth_static: no current CUDA device");
+    return SEDI_ECUDA;
+  }
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_slots[dev].base) {
+      void* ptr = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+      if (e != cudaSuccess || !ptr) {
+        put_msg(msg, msg_len, "sedi_smooth_static: cudaGetSymbolAddress of the scratch failed");
+        return SEDI_ECUDA;
+      }
+      g_static_slots[dev].base = (unsigned char*)ptr;
+    }
+    base = g_static_slots[dev].base;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int form = p->precision_form;
+  const size_t W = (size_t)kStaticWords * 8;
+  unsigned char* phi = base;
+  unsigned char* work = base + W;  // b, r, p0, p1, q, then the partial sums
+  int* iters_dev = (int*)(base + 6 * W + 8 * 2 * (size_t)kMaxF * kStaticMaxBlocks);
+  Ctl* ctl = (Ctl*)(base + 6 * W + 8 * (2 * (size_t)kMaxF * kStaticMaxBlocks + 8));
+  // what must start at zero: the counters, the barrier and the status word
+  if (cudaMemsetAsync(iters_dev, 0, 8 * sizeof(int), s) != cudaSuccess ||
+      cudaMemsetAsync(ctl, 0, sizeof(Ctl), s) != cudaSuccess) {
+    put_msg(msg, msg_len, "sedi_smooth_static: clearing the scratch failed");
+    return SEDI_ECUDA;
+  }
+  DevParams P{};
+  for (int a = 0; a < 3; ++a) {
+    P.nc[a] = p->ncell[a];
+    P.periodic[a] = p->periodic[a] ? 1 : 0;
+  }
+  P.C = C;
+  double coef[3];
+  const double dtau = 1.0 / p->n_tau;
+  for (int a = 0; a < 3; ++a) {
+    const double h = (p->hi[a] - p->lo[a]) / p->ncell[a];
+    coef[a] = dtau * 0.25 * p->bandwidth[a] * p->bandwidth[a] / (h * h);
+  }
+  DevState st{};
+  st.ctl = ctl;
+  const double rtol = form == FORM_PLAIN ? (p->cg_rtol > 2e-6 ? p->cg_rtol : 2e-6) : p->cg_rtol;
+  const int64_t n = (int64_t)nf * C;
+  launch_phi_from_double(form, in, phi, n, s);
+  int rc = -3;
+  switch (form) {
+    case FORM_SPLIT:
+      rc = smooth_impl_sized<dd>(P, phi, nullptr, nf, work, W, st, iters_dev, rtol, p->cg_max_iter,
+                                 p->n_tau, coef, kStaticMaxBlocks, s);
+      break;
+    case FORM_PLAIN:
+      rc = smooth_impl_sized<float>(P, phi, nullptr, nf, work, W, st, iters_dev, rtol,
+                                    p->cg_max_iter, p->n_tau, coef, kStaticMaxBlocks, s);
+      break;
+    default:
+      rc = smooth_impl_sized<double>(P, phi, nullptr, nf, work, W, st, iters_dev, rtol,
+                                     p->cg_max_iter, p->n_tau, coef, kStaticMaxBlocks, s);
+      break;
+  }
+  if (rc) {
+    put_msg(msg, msg_len, "sedi_smooth_static: cooperative launch of the smoother failed");
+    return SEDI_ECUDA;
+  }
+  launch_phi_convert(form, phi, out, n, 1, s);
+  int it[8] = {0};
+  Ctl c{};
+  if (cudaMemcpyAsync(it, iters_dev, 8 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&c, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    put_msg(msg, msg_len, "sedi_smooth_static: CUDA error while smoothing");
+    return SEDI_ECUDA;
+  }
+  if (iters)
+    for (int f = 0; f < nf; ++f) iters[f] = it[f];
+  if (c.cg_status == SEDI_ETIMEOUT) {
+    put_msg(msg, msg_len, "sedi_smooth_static: grid barrier timed out");
+    return SEDI_ETIMEOUT;
+  }
+  if (c.cg_status == SEDI_EDIVERGED) {
+    put_msg(msg, msg_len, "sedi_smooth_static: cg_max_iter reached before cg_rtol");
+    return SEDI_EDIVERGED;
+  }
+  put_msg(msg, msg_len, "");
+  return 0;
+}

@@ -32,7 +32,7 @@ EXPORTS = [
     "sedi_set_fluid", "sedi_set_eps", "sedi_step", "sedi_average", "sedi_deposit", "sedi_smooth",
     "sedi_get_particles", "sedi_compute_forces", "sedi_get_neighbors", "sedi_get_contacts",
     "sedi_save_state", "sedi_load_state", "sedi_get_timings", "sedi_get_stats", "sedi_sync",
-    "sedi_last_error",
+    "sedi_last_error", "sedi_smooth_static",
 ]
 
 
@@ -97,6 +97,7 @@ def lib():
             "sedi_get_stats": (C.c_int, [_P, C.POINTER(SediStats)]),
             "sedi_sync": (C.c_int, [_P]),
             "sedi_last_error": (C.c_char_p, [_P]),
+            "sedi_smooth_static": (C.c_int, [C.POINTER(SediParams), _I, _P, _P, _P, _P, C.c_char_p, _I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -127,6 +128,24 @@ def make_params(prm: dict) -> SediParams:
         t = fields[k]
         setattr(p, k, t(*v) if hasattr(t, "_length_") else v)
     return p
+
+
+STATIC_MAX_WORDS = 1 << 20  # SEDI_STATIC_MAX_WORDS of include/sedi.h
+
+
+def smooth_static(params: dict, phi, out, stream=None):
+    """sedi_smooth_static: smoothing with the library's static scratch (no device
+    allocation).  phi and out are CUDA tensors [n_fields, C] of float64."""
+    p = make_params(params)
+    nf = int(phi.shape[0])
+    iters = np.zeros(nf, dtype=np.int32)
+    msg = C.create_string_buffer(256)
+    sptr = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    rc = lib().sedi_smooth_static(C.byref(p), nf, phi.data_ptr(), out.data_ptr(), iters.ctypes.data,
+                                  sptr, msg, 256)
+    if rc:
+        raise SediError(rc, msg.value.decode())
+    return iters
 
 
 def _is_torch(a):

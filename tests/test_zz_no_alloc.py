@@ -1,0 +1,50 @@
+"""The allocation-free smoothing entry point (sedi_smooth_static).
+
+Some callers cannot allocate device memory (a framework or memory pool owns it,
+or allocations are forbidden after start-up).  sedi_smooth_static serves them
+from a static scratch array.  This file is collected last so a stop-at-first-
+failure run has already run every other test; it passes alone or after them.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1601_03801_gb300 import sedi  # noqa: E402
+from paper_1601_03801_gb300.workloads import default_params, random_fields  # noqa: E402
+
+
+def test_static_smoothing_matches_handle_path_twice():
+    prm = default_params(hi=(64e-3, 32e-3, 64e-3), ncell=(64, 32, 64), wall_hi=(0, 0, 0),
+                         bandwidth=(1.5e-3,) * 3)
+    C = int(np.prod(prm["ncell"]))
+    ref = sedi.Sedi(dict(prm, precision_form="split"))
+    stream = torch.cuda.Stream()
+    for call, seed in enumerate((21, 22)):
+        phi = random_fields(prm["ncell"], 7, seed=seed)
+        want, want_it = ref.smooth(phi)
+        dev_in = torch.as_tensor(phi, device="cuda")
+        dev_out = torch.full_like(dev_in, float("nan"))
+        torch.cuda.synchronize()
+        it = sedi.smooth_static(dict(prm, precision_form="split"), dev_in, dev_out, stream)
+        got = dev_out.cpu().numpy()
+        assert np.isfinite(got).all(), call
+        for f in range(7):
+            assert np.abs(got[f] - want[f]).max() <= 1e-7 * np.abs(phi[f]).max(), (call, f)
+        assert np.array_equal(it, want_it)
+        # the input is untouched (the scratch holds the working copy)
+        assert np.array_equal(dev_in.cpu().numpy(), phi)
+
+
+def test_static_smoothing_rejects_oversize():
+    prm = default_params(ncell=(128, 128, 64))  # 8 fields x 1,048,576 cells > limit
+    C = int(np.prod(prm["ncell"]))
+    assert 8 * C > sedi.STATIC_MAX_WORDS
+    dev = torch.zeros((8, C), dtype=torch.float64, device="cuda")
+    with pytest.raises(sedi.SediError) as e:
+        sedi.smooth_static(prm, dev, dev)
+    assert e.value.code == -1 and "SEDI_STATIC_MAX_WORDS" in str(e.value)
