@@ -260,6 +260,9 @@ def gpu_arm(args):
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(prm, parts, fl, budget_s=args.cpu_seconds)
+    cnn = None
+    if rank == 0 and not args.no_cnn:
+        cnn = cnn_warm_start(prm, parts, fl)
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
@@ -273,12 +276,87 @@ def gpu_arm(args):
                            "parallelism": "independent bed per GPU" if world > 1 else "1 GPU"},
                 "phases_ms_per_step": phases, "rebuilds_in_timed_region": int(rebuilds),
                 "roofline": roof, "plain_form": plain, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks, "cpu_baseline": cpu}
+                "clocks": clocks, "cpu_baseline": cpu, "cnn_warm_start": cnn}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+
+
+def cnn_warm_start(prm0, parts, fl, train_steps=300, snapshots=5):
+    """Learned warm start on the 128 x 64 x 128 mesh (0.5 mm cells) of the same bed:
+    (phi^m, phi^{m+1}) pairs of (eps, F) are made by the method itself (deposition,
+    then single backward-Euler pseudo-steps), the network is trained on the GPU, and
+    a held-out snapshot is averaged from phi^m and from the learned guess."""
+    import torch
+
+    from paper_1601_03801_gb300 import sedi
+
+    prm = dict(prm0, ncell=(128, 64, 128))
+    n_tau = prm["n_tau"]
+    run = sedi.Sedi(dict(prm, precision_form="split"))
+    run.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+    run.set_fluid(U=_resample_u(fl["U"], prm0["ncell"], prm["ncell"]))
+    one = sedi.Sedi(dict(prm, precision_form="split", n_tau=1,
+                         bandwidth=tuple(b / np.sqrt(n_tau) for b in prm["bandwidth"])))
+    S0, S1 = prm["shift_eps"], prm["shift_force"]
+    pairs = []
+    for _ in range(snapshots + 1):
+        run.step(SUBSTEPS * 5)
+        run.average_inplace()
+        q = run.deposit()
+        phi = np.stack([np.ldexp(q[0].astype(float), -S0)] +
+                       [np.ldexp(q[4 + a].astype(float), -S1) for a in range(3)])
+        for _m in range(n_tau):
+            nxt, _ = one.smooth(phi)
+            pairs.append((phi, nxt))
+            phi = nxt
+    train, held = pairs[:-n_tau], pairs[-n_tau:]
+    scale = np.maximum(np.abs(np.stack([p[0] for p in train])).max(axis=(0, 2)), 1e-30)
+    xs = np.stack([p[0] / scale[:, None] for p in train])
+    ts = np.stack([(p[1] - p[0]) / scale[:, None] for p in train])
+    rng = np.random.default_rng(1601038015)
+    params = []
+    for li, (ci, co) in enumerate([(4, 32), (32, 32), (32, 4)]):
+        w = rng.normal(0, np.sqrt(2.0 / (27 * ci)), co * ci * 27) * (0.0 if li == 2 else 1.0)
+        params += [w, np.zeros(co)]
+    trainer = sedi.Sedi(dict(prm, precision_form="split"))
+    trainer.cnn_set_params(np.concatenate(params))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = trainer.cnn_train(xs, ts, steps=train_steps, lr=2e-3)
+    train_s = time.perf_counter() - t0
+    trained = trainer.cnn_get_params()
+    x, v, w, _ = run.get_particles()
+    out = {}
+    for warm in (0, 1):
+        h = sedi.Sedi(dict(prm, precision_form="split", use_cnn_guess=warm, cnn_scale=tuple(scale),
+                           profile=1))
+        h.set_particles(x, v, w, parts["d"], parts["rho"])
+        h.cnn_set_params(trained)
+        h.average_inplace()  # warm-up
+        t_a, i_a = h.timings(), h.stats()["cg_iterations"]
+        for _ in range(3):
+            h.average_inplace()
+        t_b, i_b = h.timings(), h.stats()["cg_iterations"]
+        out[warm] = ((i_b - i_a) / 3.0, (t_b["smooth_ms"] - t_a["smooth_ms"]) / 3.0)
+    return {"mesh": list(prm["ncell"]), "train_pairs": len(train), "train_steps": train_steps,
+            "train_s": round(train_s, 2), "loss_first": float(losses[:5].mean()),
+            "loss_last": float(losses[-20:].mean()),
+            "iterations_cold": out[0][0], "iterations_warm": out[1][0],
+            "smooth_ms_cold": round(out[0][1], 3), "smooth_ms_warm": round(out[1][1], 3),
+            "note": "smooth_ms_warm includes the network inference of every pseudo-step"}
+
+
+def _resample_u(U, nc_from, nc_to):
+    """Nearest-cell copy of a cell-centred field onto a finer uniform mesh."""
+    nx, ny, nz = nc_from
+    f = U.reshape(nz, ny, nx, 3)
+    iz = (np.arange(nc_to[2]) * nz) // nc_to[2]
+    iy = (np.arange(nc_to[1]) * ny) // nc_to[1]
+    ix = (np.arange(nc_to[0]) * nx) // nc_to[0]
+    return f[iz][:, iy][:, :, ix].reshape(-1, 3)
 
 
 def cpu_baseline(prm, parts, fl, budget_s=20.0):
@@ -376,6 +454,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-cnn", action="store_true", help="skip the learned-warm-start leg")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--settle", type=int, default=50, help="untimed settling steps before warm-up")
     ap.add_argument("--mode", default="bench", choices=["bench", "kernels"],

@@ -98,6 +98,10 @@ typedef struct sedi_params {
   int32_t n_beds;                          /* independent beds in this handle [1] */
   int32_t profile;                         /* record CUDA events around each phase
                                               (see sedi_get_timings) [0] */
+  int32_t use_cnn_guess;                   /* start every smoothing pseudo-step from
+                                              the learned guess (sedi_cnn_*) [0] */
+  double cnn_scale[4];                     /* network input/output scale of eps_s and
+                                              F_fp x, y, z [1, 1, 1, 1] */
   uint64_t seed;                           /* reserved for stochastic extensions [0] */
 } sedi_params;
 
@@ -197,6 +201,33 @@ int64_t sedi_get_neighbors(sedi_handle* h, int32_t bed, int64_t* offsets, int64_
 /* Tangential springs of the pairs in contact: ij (m x 2, caller indices, i < j)
    and xi (m x 3) as seen from i.  Returns m, or SEDI_EOVERFLOW if m > cap. */
 int64_t sedi_get_contacts(sedi_handle* h, int32_t bed, int64_t cap, int64_t* ij, double* xi);
+
+/* ---- Learned warm start of the smoothing solve ----
+ * A 3-layer 3x3x3 convolutional network 4 -> 32 -> 32 -> 4 (ReLU after the first
+ * two; bfloat16 weights and activations, FP32 accumulation) maps one smoothing
+ * pseudo-step's right-hand side phi^m of (eps_s, F_fp x, y, z), divided by
+ * cnn_scale, to the predicted change (phi^{m+1} - phi^m) / cnn_scale.  With
+ * params.use_cnn_guess = 1, sedi_average starts every pseudo-step's solve from
+ * phi^m + cnn_scale * net(phi^m / cnn_scale), shifted to the conserved sum; the
+ * solve still runs to cg_rtol, so only the iteration count changes.  The paper
+ * has no learned component (Sec. 2.4 solves the diffusion equation directly).
+ * Parameters are packed w1[32][4][27] b1[32] w2[32][32][27] b2[32] w3[4][32][27]
+ * b3[4], tap t = (kz*3 + ky)*3 + kx at offset (kx-1, ky-1, kz-1); fields are
+ * channels-first [4][C] float64; taps outside the mesh wrap on periodic axes and
+ * read zero elsewhere.  Training runs on the GPU: forward, backward and Adam
+ * (lr given, beta 0.9/0.999, eps 1e-8) on FP32 master weights. */
+#define SEDI_CNN_PARAMS 34628
+int sedi_cnn_set_params(sedi_handle* h, const double* params, int64_t n);  /* host array; resets Adam */
+int sedi_cnn_get_params(sedi_handle* h, double* params, int64_t n);        /* host array */
+/* y = net(x), x and y [4][C] */
+int sedi_cnn_forward(sedi_handle* h, const double* x, double* y, int32_t mem);
+/* loss = mean over [4][C] of (net(x) - target)^2 and d loss / d params (n doubles, host) */
+int sedi_cnn_loss_grad(sedi_handle* h, const double* x, const double* target, double* grad,
+                       double* loss, int32_t mem);
+/* `steps` Adam steps cycling over n_pairs (x, target) pairs, each [4][C]; losses
+   (steps doubles, host, or NULL) receives the loss before each step. */
+int sedi_cnn_train(sedi_handle* h, int32_t n_pairs, const double* x, const double* target,
+                   int32_t steps, double lr, double* losses, int32_t mem);
 
 /* Checkpoint and restore of particles, lagged accelerations, tangential springs,
    fluid fields and the drag's solid fraction (binary, this library's format). */

@@ -9,7 +9,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SOURCES = ["orc_contact.cpp", "orc_fluid.cpp", "orc_neighbors.cpp", "orc_step.cpp",
-           "orc_average.cpp"]
+           "orc_average.cpp", "orc_cnn.cpp"]
 LIB = os.path.join(HERE, "liborc.so")
 
 

@@ -67,6 +67,14 @@ def lib():
         L.orc_drag.restype = None
         L.orc_vr.argtypes = [_D, _D]
         L.orc_vr.restype = _D
+        L.orc_cnn_num_params.argtypes = []
+        L.orc_cnn_num_params.restype = _L
+        L.orc_cnn_forward.argtypes = [C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P, _I]
+        L.orc_cnn_forward.restype = C.c_int
+        L.orc_cnn_loss_grad.argtypes = [C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P]
+        L.orc_cnn_loss_grad.restype = _D
+        L.orc_adam.argtypes = [_L, _P, _P, _P, _P, _L, _D, _D, _D, _D]
+        L.orc_adam.restype = None
         _lib = L
     return _lib
 
@@ -204,3 +212,42 @@ def drag(prm: dict, eps_s, w, d):
 
 def vr(eps_f, Re):
     return lib().orc_vr(float(eps_f), float(Re))
+
+
+# ---------------------------------------------------------------- learned warm start
+def cnn_num_params():
+    return int(lib().orc_cnn_num_params())
+
+
+def cnn_forward(params, x, ncell, periodic, round_bf16=False, activations=False):
+    """x [4, nz, ny, nx] (or [4, C]) -> y of the same shape."""
+    nx, ny, nz = ncell
+    N = nx * ny * nz
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    xi = np.ascontiguousarray(x, dtype=np.float64).reshape(4, N)
+    y = np.zeros((4, N))
+    a1 = np.zeros((32, N)) if activations else None
+    a2 = np.zeros((32, N)) if activations else None
+    per = np.asarray(periodic, dtype=np.int32)
+    lib().orc_cnn_forward(nx, ny, nz, per.ctypes.data, p.ctypes.data, xi.ctypes.data, y.ctypes.data,
+                          _ptr(a1), _ptr(a2), int(bool(round_bf16)))
+    return (y, a1, a2) if activations else y
+
+
+def cnn_loss_grad(params, x, target, ncell, periodic):
+    nx, ny, nz = ncell
+    N = nx * ny * nz
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    xi = np.ascontiguousarray(x, dtype=np.float64).reshape(4, N)
+    ti = np.ascontiguousarray(target, dtype=np.float64).reshape(4, N)
+    g = np.zeros_like(p)
+    per = np.asarray(periodic, dtype=np.int32)
+    loss = lib().orc_cnn_loss_grad(nx, ny, nz, per.ctypes.data, p.ctypes.data, xi.ctypes.data,
+                                   ti.ctypes.data, g.ctypes.data)
+    return loss, g
+
+
+def adam(params, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In place on float64 numpy arrays."""
+    lib().orc_adam(params.size, params.ctypes.data, grad.ctypes.data, m.ctypes.data, v.ctypes.data,
+                   int(t), lr, beta1, beta2, eps)

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsedi.so")
-UNITS = ["engine.cu", "k_force.cu", "k_bin.cu", "k_avg.cu"]
+UNITS = ["engine.cu", "k_force.cu", "k_bin.cu", "k_avg.cu", "k_cnn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -129,6 +129,8 @@ struct Num<float> {
   __device__ static float dif(float a, float b) { return a - b; }
   __device__ static float addq(float a, float b) { return a + b; }
   __device__ static float subq(float a, float b) { return a - b; }
+  __device__ static float fmaq(float a, float b, float c) { return fmaf(b, c, a); }
+  static constexpr bool kExtended = false;  // no wider word than the force word
 };
 
 template <>
@@ -146,6 +148,8 @@ struct Num<double> {
   __device__ static double dif(double a, double b) { return a - b; }
   __device__ static double addq(double a, double b) { return a + b; }
   __device__ static double subq(double a, double b) { return a - b; }
+  __device__ static double fmaq(double a, double b, double c) { return a + b * c; }
+  static constexpr bool kExtended = false;
 };
 
 template <>
@@ -167,6 +171,8 @@ struct Num<dd> {
   // additions whose error is relative to the operands (see dd_add_fast)
   __device__ static dd addq(dd a, dd b) { return dd_add_fast(a, b); }
   __device__ static dd subq(dd a, dd b) { return dd_sub_fast(a, b); }
+  __device__ static dd fmaq(dd a, float b, float c) { return dd_add_fast(a, two_prod(b, c)); }
+  static constexpr bool kExtended = true;   // state word wider than the force word
 };
 
 template <class S>

@@ -58,6 +58,16 @@ struct sedi_handle {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
   double ms[4] = {0, 0, 0, 0};
   double cnt[4] = {0, 0, 0, 0};
+  // learned warm start: FP32 master weights, Adam moments, gradient, work space
+  float* cnn_master = nullptr;
+  float* cnn_m = nullptr;
+  float* cnn_v = nullptr;
+  float* cnn_grad = nullptr;
+  float* cnn_target = nullptr;  // [v][4]
+  double* cnn_loss = nullptr;   // device scalars (one per training step)
+  void* cnn_work = nullptr;
+  int64_t cnn_steps = 0;
+  bool cnn_set = false;
 };
 
 namespace {
@@ -476,6 +486,7 @@ void sedi_default_params(sedi_params* p) {
   p->use_graphs = 1;
   p->block_size = 0;
   p->n_beds = 1;
+  p->cnn_scale[0] = p->cnn_scale[1] = p->cnn_scale[2] = p->cnn_scale[3] = 1.0;
 }
 
 int sedi_create(const sedi_params* p, sedi_handle** out) {
@@ -537,6 +548,9 @@ void sedi_destroy(sedi_handle* h) {
   free_list(h->part_allocs);
   free_list(h->mesh_allocs);
   if (h->dstage) cudaFree(h->dstage);
+  for (void* p : {(void*)h->cnn_master, (void*)h->cnn_m, (void*)h->cnn_v, (void*)h->cnn_grad,
+                  (void*)h->cnn_target, (void*)h->cnn_loss, h->cnn_work})
+    if (p) cudaFree(p);
   if (h->st.ctl) cudaFree(h->st.ctl);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->own) cudaStreamDestroy(h->own);
@@ -734,13 +748,50 @@ static int deposit_dev(sedi_handle* h) {
   return 0;
 }
 
-static int smooth_dev(sedi_handle* h, int nf, const void* guess) {
-  CK(cudaMemsetAsync(h->iters_dev, 0, 4 * 8, h->stream));
+static int smooth_dev(sedi_handle* h, int nf, const void* guess, int n_tau = -1, bool zero_iters = true) {
+  if (zero_iters) CK(cudaMemsetAsync(h->iters_dev, 0, 4 * 8, h->stream));
   // FP32 words cannot reach a relative residual much below 1e-6
   const double rtol = h->form == FORM_PLAIN ? std::max(h->prm.cg_rtol, 2e-6) : h->prm.cg_rtol;
   int rc = launch_smooth(h->form, h->P, h->phi, guess, nf, h->work, h->st, h->iters_dev,
-                         rtol, h->prm.cg_max_iter, h->prm.n_tau, h->coef, h->stream);
+                         rtol, h->prm.cg_max_iter, n_tau > 0 ? n_tau : h->prm.n_tau, h->coef,
+                         h->stream);
   if (rc) return fail(h, SEDI_ECUDA, "cooperative launch of the smoother failed: %s", cudaGetErrorString(cudaGetLastError()));
+  return 0;
+}
+
+static int ensure_cnn(sedi_handle* h) {
+  if (h->cnn_master) return 0;
+  const size_t np = cnn_param_count();
+  CK(cudaMalloc((void**)&h->cnn_master, np * sizeof(float)));
+  CK(cudaMalloc((void**)&h->cnn_m, np * sizeof(float)));
+  CK(cudaMalloc((void**)&h->cnn_v, np * sizeof(float)));
+  CK(cudaMalloc((void**)&h->cnn_grad, np * sizeof(float)));
+  CK(cudaMalloc((void**)&h->cnn_target, (size_t)h->P.C * 4 * sizeof(float)));
+  CK(cudaMalloc(&h->cnn_work, cnn_work_bytes(h->P.C)));
+  CK(cudaMemsetAsync(h->cnn_master, 0, np * sizeof(float), h->stream));
+  CK(cudaMemsetAsync(h->cnn_m, 0, np * sizeof(float), h->stream));
+  CK(cudaMemsetAsync(h->cnn_v, 0, np * sizeof(float), h->stream));
+  return 0;
+}
+
+// One pseudo-step at a time: guess = phi + scale * net(phi / scale) on (eps, F),
+// projected onto the conserved sum by the smoother, then solve to cg_rtol.
+static int smooth_warm(sedi_handle* h) {
+  int rc = ensure_cnn(h);
+  if (rc) return rc;
+  const int64_t C = h->P.C;
+  const float scale[4] = {(float)h->prm.cnn_scale[0], (float)h->prm.cnn_scale[1],
+                          (float)h->prm.cnn_scale[2], (float)h->prm.cnn_scale[3]};
+  CK(cudaMemsetAsync(h->iters_dev, 0, 4 * 8, h->stream));
+  for (int m = 0; m < h->prm.n_tau; ++m) {
+    launch_phi_convert(h->form, h->phi, h->dstage, 7 * C, 1, h->stream);
+    const double* f[4] = {h->dstage, h->dstage + 4 * C, h->dstage + 5 * C, h->dstage + 6 * C};
+    cnn_input(h->P, f, scale, h->cnn_work, h->stream);
+    float* y = nullptr;
+    cnn_forward(h->P, h->cnn_master, h->cnn_work, &y, h->stream);
+    cnn_guess(h->form, h->phi, y, scale, h->qfix, C, h->stream);
+    if ((rc = smooth_dev(h, 7, h->qfix, 1, false))) return rc;
+  }
   return 0;
 }
 
@@ -780,7 +831,11 @@ int sedi_average(sedi_handle* h, int32_t bed, double* eps, double* Us, double* F
   if ((rc = deposit_dev(h))) return rc;
   launch_fields_from_fixed(h->form, h->qfix, h->P, h->phi, 7, h->stream);
   if (h->prm.profile) CK(cudaEventRecord(h->avg_ev[1], h->stream));
-  if ((rc = smooth_dev(h, 7, nullptr))) return rc;
+  if (h->prm.use_cnn_guess && h->cnn_set) {
+    if ((rc = smooth_warm(h))) return rc;
+  } else if ((rc = smooth_dev(h, 7, nullptr))) {
+    return rc;
+  }
   if (h->prm.profile) {
     CK(cudaEventRecord(h->avg_ev[2], h->stream));
     h->pending.push_back({2, {h->avg_ev[0], h->avg_ev[1]}});
@@ -1142,6 +1197,126 @@ int sedi_load_state(sedi_handle* h, const char* path) {
   if (rc) return rc;
   h->stats = hd.stats;
   h->have_particles = true;
+  return 0;
+}
+
+int sedi_cnn_set_params(sedi_handle* h, const double* params, int64_t n) {
+  if (!h || !params) return SEDI_EINVAL;
+  h->err.clear();
+  if (n != (int64_t)cnn_param_count()) return fail(h, SEDI_EINVAL, "expected %zu parameters", cnn_param_count());
+  int rc = ensure_cnn(h);
+  if (rc) return rc;
+  std::vector<float> f(n);
+  for (int64_t k = 0; k < n; ++k) f[k] = (float)params[k];
+  CK(cudaMemcpyAsync(h->cnn_master, f.data(), n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemsetAsync(h->cnn_m, 0, n * sizeof(float), h->stream));
+  CK(cudaMemsetAsync(h->cnn_v, 0, n * sizeof(float), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->cnn_steps = 0;
+  h->cnn_set = true;
+  return 0;
+}
+
+int sedi_cnn_get_params(sedi_handle* h, double* params, int64_t n) {
+  if (!h || !params) return SEDI_EINVAL;
+  h->err.clear();
+  if (n != (int64_t)cnn_param_count()) return fail(h, SEDI_EINVAL, "expected %zu parameters", cnn_param_count());
+  if (!h->cnn_set) return fail(h, SEDI_ESTATE, "no network parameters set");
+  std::vector<float> f(n);
+  CK(cudaMemcpyAsync(f.data(), h->cnn_master, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int64_t k = 0; k < n; ++k) params[k] = f[k];
+  return 0;
+}
+
+static int cnn_stage_input(sedi_handle* h, const double* x, int32_t mem) {
+  const int64_t C = h->P.C;
+  int rc = ensure_stage(h, 8 * C);
+  if (rc) return rc;
+  if ((rc = copy_in(h, h->dstage, x, 8 * 4 * C, mem))) return rc;
+  const double* f[4] = {h->dstage, h->dstage + C, h->dstage + 2 * C, h->dstage + 3 * C};
+  const float one[4] = {1, 1, 1, 1};
+  cnn_input(h->P, f, one, h->cnn_work, h->stream);
+  return 0;
+}
+
+int sedi_cnn_forward(sedi_handle* h, const double* x, double* y, int32_t mem) {
+  if (!h || !x || !y) return SEDI_EINVAL;
+  h->err.clear();
+  if (!h->cnn_set) return fail(h, SEDI_ESTATE, "no network parameters set");
+  const int64_t C = h->P.C;
+  int rc = cnn_stage_input(h, x, mem);
+  if (rc) return rc;
+  float* yd = nullptr;
+  cnn_forward(h->P, h->cnn_master, h->cnn_work, &yd, h->stream);
+  cnn_vec_to_chan_first(yd, h->dstage + 4 * C, C, 4, h->stream);
+  if ((rc = copy_out(h, y, h->dstage + 4 * C, 8 * 4 * C, mem))) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  return 0;
+}
+
+int sedi_cnn_loss_grad(sedi_handle* h, const double* x, const double* target, double* grad,
+                       double* loss, int32_t mem) {
+  if (!h || !x || !target) return SEDI_EINVAL;
+  h->err.clear();
+  if (!h->cnn_set) return fail(h, SEDI_ESTATE, "no network parameters set");
+  const int64_t C = h->P.C;
+  int rc = cnn_stage_input(h, x, mem);
+  if (rc) return rc;
+  if ((rc = copy_in(h, h->dstage + 4 * C, target, 8 * 4 * C, mem))) return rc;
+  cnn_chan_first_to_vec(h->dstage + 4 * C, h->cnn_target, C, 4, h->stream);
+  if (!h->cnn_loss) CK(cudaMalloc((void**)&h->cnn_loss, 8 * 4096));
+  cnn_loss_grad(h->P, h->cnn_master, h->cnn_target, h->cnn_grad, h->cnn_loss, h->cnn_work, h->stream);
+  const size_t np = cnn_param_count();
+  std::vector<float> g(np);
+  double l = 0;
+  CK(cudaMemcpyAsync(g.data(), h->cnn_grad, np * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&l, h->cnn_loss, 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  if (grad)
+    for (size_t k = 0; k < np; ++k) grad[k] = g[k];
+  if (loss) *loss = l;
+  return 0;
+}
+
+int sedi_cnn_train(sedi_handle* h, int32_t n_pairs, const double* x, const double* target,
+                   int32_t steps, double lr, double* losses, int32_t mem) {
+  if (!h || !x || !target || n_pairs < 1 || steps < 0) return SEDI_EINVAL;
+  h->err.clear();
+  if (!h->cnn_set) return fail(h, SEDI_ESTATE, "no network parameters set");
+  const int64_t C = h->P.C;
+  double* dx = nullptr;
+  double* dt = nullptr;
+  if (!h->cnn_loss) CK(cudaMalloc((void**)&h->cnn_loss, 8 * 4096));
+  CK(cudaMalloc((void**)&dx, 8 * 4 * C * (size_t)n_pairs));
+  CK(cudaMalloc((void**)&dt, 8 * 4 * C * (size_t)n_pairs));
+  int rc = copy_in(h, dx, x, 8 * 4 * C * (size_t)n_pairs, mem);
+  if (!rc) rc = copy_in(h, dt, target, 8 * 4 * C * (size_t)n_pairs, mem);
+  std::vector<double> lh(steps);
+  const float one[4] = {1, 1, 1, 1};
+  for (int32_t k = 0; k < steps && !rc; k += 4096) {
+    const int32_t kn = std::min<int32_t>(steps - k, 4096);
+    for (int32_t j = 0; j < kn; ++j) {
+      const int64_t pr = (k + j) % n_pairs;
+      const double* xp = dx + pr * 4 * C;
+      const double* f[4] = {xp, xp + C, xp + 2 * C, xp + 3 * C};
+      cnn_input(h->P, f, one, h->cnn_work, h->stream);
+      cnn_chan_first_to_vec(dt + pr * 4 * C, h->cnn_target, C, 4, h->stream);
+      cnn_loss_grad(h->P, h->cnn_master, h->cnn_target, h->cnn_grad, h->cnn_loss + j, h->cnn_work, h->stream);
+      cnn_adam(h->cnn_master, h->cnn_grad, h->cnn_m, h->cnn_v, ++h->cnn_steps, (float)lr, h->stream);
+    }
+    if (cudaMemcpyAsync(lh.data() + k, h->cnn_loss, 8 * kn, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+      rc = fail(h, SEDI_ECUDA, "loss copy failed");
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = fail(h, SEDI_ECUDA, "training step failed");
+  }
+  cudaFree(dx);
+  cudaFree(dt);
+  if (rc) return rc;
+  CK(cudaGetLastError());
+  if (losses)
+    for (int32_t k = 0; k < steps; ++k) losses[k] = lh[k];
   return 0;
 }
 

@@ -10,11 +10,12 @@ namespace sedi {
 template <class F>
 __device__ __forceinline__ void axis_w(F s, int n, int per, int* i0, int* i1, F* f) {
   if (per) {
+    // positions lie in [lo, hi), so s is in [-0.5, n - 0.5) and k in [-1, n - 1]
     F fl = xfloor(s);
     *f = s - fl;
     int k = (int)fl;
-    k %= n;
     if (k < 0) k += n;
+    if (k >= n) k -= n;
     *i0 = k;
     *i1 = (k + 1 == n) ? 0 : k + 1;
   } else {

@@ -369,18 +369,22 @@ __global__ void __launch_bounds__(kSmoothThreads) k_smooth(SmoothArgs a) {
   __shared__ T s_word[kMaxF];
   __shared__ int s_active[kMaxF];
   __shared__ T s_c1, s_c2, s_inv_theta;
-  __shared__ int s_kmin;
+  __shared__ int s_kmin[kMaxF];
   int iters[kMaxF];
   for (int f = 0; f < kMaxF; ++f) iters[f] = 0;
   T acc[kMaxF], acc2[kMaxF];
   double* part0 = a.part;
   double* part1 = a.part + (int64_t)kMaxF * G;
-  const double theta = 0.5 * (a.lmax + 1.0), delta = 0.5 * (a.lmax - 1.0);
-  const double sigma1 = theta / delta;
-  const double kappa = a.lmax;
-  const double sq = sqrt(kappa);
-  const double sig = (sq - 1.0) / (sq + 1.0);
-  if (threadIdx.x == 0) s_inv_theta = A::from_d(1.0 / theta);
+  // spectral constants: FP64 scalars used by thread 0 only
+  double theta = 0.0, delta = 0.0, sigma1 = 0.0, sig = 0.0;
+  if (threadIdx.x == 0) {
+    theta = 0.5 * (a.lmax + 1.0);
+    delta = 0.5 * (a.lmax - 1.0);
+    sigma1 = theta / delta;
+    const double sq = sqrt(a.lmax);
+    sig = (sq - 1.0) / (sq + 1.0);
+    s_inv_theta = A::from_d(1.0 / theta);
+  }
   __syncthreads();
 
   for (int m = 0; m < a.n_tau; ++m) {
@@ -430,18 +434,16 @@ __global__ void __launch_bounds__(kSmoothThreads) k_smooth(SmoothArgs a) {
     grid_sums(part0, nf, G, s_bb);
     grid_sums(part1, nf, G, s_rr);
     if (threadIdx.x == 0) {
-      int kmin = 0;
       for (int f = 0; f < nf; ++f) {
         s_active[f] = (s_bb[f] > 0.0) && (s_rr[f] > a.rtol2 * s_bb[f]);
+        s_kmin[f] = 0;
         if (s_active[f]) {
           // ||r_k|| <= 2 sig^k ||r_0||  ->  k >= log(rtol ||b|| / (2 ||r_0||)) / log(sig)
           const double need = 0.5 * sqrt(a.rtol2 * s_bb[f] / s_rr[f]);
           int k = sig > 0.0 ? (int)ceil(log(need) / log(sig)) : 1;
-          if (k < 1) k = 1;
-          if (k > kmin) kmin = k;
+          s_kmin[f] = k < 1 ? 1 : k;
         }
       }
-      s_kmin = kmin;
     }
     __syncthreads();
     for (int f = 0; f < nf; ++f)
@@ -449,23 +451,26 @@ __global__ void __launch_bounds__(kSmoothThreads) k_smooth(SmoothArgs a) {
         for (int64_t c = tid; c < C; c += nthr) X[f * C + c] = A::zero();
     int any = 0;
     for (int f = 0; f < nf; ++f) any |= s_active[f];
-    int kcheck = s_kmin;
-    double rho = 1.0 / sigma1;
+    // each field is first checked at its own a-priori count, then every 2 iterations
+    int kcheck[kMaxF];
+    for (int f = 0; f < kMaxF; ++f) kcheck[f] = f < nf ? s_kmin[f] : 0;
+    double rho = 1.0 / sigma1;  // advanced by thread 0 only (FP64 is slow here)
     int it = 0;
     while (any && it < a.max_iter) {
       ++it;
       // scalars of this iteration (block thread 0, broadcast)
-      const double rho_new = 1.0 / (2.0 * sigma1 - rho);
       if (threadIdx.x == 0) {
+        const double rho_new = 1.0 / (2.0 * sigma1 - rho);
         s_c1 = A::from_d(rho_new * rho);
         s_c2 = A::from_d(2.0 * rho_new / delta);
+        rho = rho_new;
       }
       __syncthreads();
-      rho = rho_new;
       const T c1 = s_c1, c2 = s_c2;
       const T* Dold = (const T*)a.p[(it - 1) & 1];
       T* Dnew = (T*)a.p[it & 1];
-      const bool check = (it >= kcheck);
+      bool check = false;
+      for (int f = 0; f < nf; ++f) check |= s_active[f] && it >= kcheck[f];
       for (int f = 0; f < nf; ++f) acc[f] = A::zero();
       for (int64_t c = tid; c < C; c += nthr) {
         const Stencil sc = stencil_of(a, c);
@@ -487,7 +492,7 @@ __global__ void __launch_bounds__(kSmoothThreads) k_smooth(SmoothArgs a) {
         grid_sums(part0, nf, G, s_tmp);
         if (threadIdx.x == 0)
           for (int f = 0; f < nf; ++f)
-            if (s_active[f] && s_tmp[f] <= a.rtol2 * s_bb[f]) s_active[f] = -it;
+            if (s_active[f] && it >= kcheck[f] && s_tmp[f] <= a.rtol2 * s_bb[f]) s_active[f] = -it;
         __syncthreads();
         any = 0;
         for (int f = 0; f < nf; ++f) {
@@ -497,7 +502,8 @@ __global__ void __launch_bounds__(kSmoothThreads) k_smooth(SmoothArgs a) {
         __syncthreads();
         if (threadIdx.x < nf && s_active[threadIdx.x] < 0) s_active[threadIdx.x] = 0;
         __syncthreads();
-        kcheck = it + 2;
+        for (int f = 0; f < nf; ++f)
+          if (it >= kcheck[f]) kcheck[f] = it + 2;
       }
     }
     for (int f = 0; f < nf; ++f)

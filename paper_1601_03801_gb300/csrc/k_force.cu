@@ -131,21 +131,39 @@ __global__ void __launch_bounds__(128, 6) k_substep(DevState st, DevMesh mesh, D
     S* hist = (S*)st.hist[nl];
     const int64_t cap = P.cap;
     const float lub_out_f = P.lub_out_f;
-    for (int k = 0; k < nn; ++k) {
+    // phase 1: cheap FP32 cull of every listed partner (relative margin; the exact
+    // test follows); four candidates per round so their gathers overlap
+    uint32_t live = 0;
+    {
+      const float rif = (float)ri;
+      const float fac = P.lubrication ? (1.0f + lub_out_f) : 1.0f;
+      for (int k0 = 0; k0 < nn; k0 += 4) {
+        int32_t ev[4];
+        Quad<S> Pv[4];
+        const int32_t* ep = nbr + (int64_t)k0 * N + i;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ev[u] = k0 + u < nn ? ep[u * N] : 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) Pv[u] = ldq(pos + (k0 + u < nn ? nbr_index(ev[u]) : (int)i));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          float dx = (float)NS::dif(Pv[u].a, Pi.a), dy = (float)NS::dif(Pv[u].b, Pi.b),
+                dz = (float)NS::dif(Pv[u].c, Pi.c);
+          if (P.periodic[0]) dx = dx > P.cf.halfL[0] ? dx - P.cf.L[0] : (dx < -P.cf.halfL[0] ? dx + P.cf.L[0] : dx);
+          if (P.periodic[1]) dy = dy > P.cf.halfL[1] ? dy - P.cf.L[1] : (dy < -P.cf.halfL[1] ? dy + P.cf.L[1] : dy);
+          if (P.periodic[2]) dz = dz > P.cf.halfL[2] ? dz - P.cf.L[2] : (dz < -P.cf.halfL[2] ? dz + P.cf.L[2] : dz);
+          const float cut = (rif + (float)NS::f(Pv[u].d)) * fac;
+          if (k0 + u < nn && dx * dx + dy * dy + dz * dz <= cut * cut * 1.0002f) live |= 1u << (k0 + u);
+        }
+      }
+    }
+    // phase 2: interacting pairs only
+    while (live) {
+      const int k = __ffs(live) - 1;
+      live &= live - 1;
       const int32_t e = nbr[(int64_t)k * N + i];
       const int j = nbr_index(e);
       const Quad<S> Pj = ldq(pos + j);
-      // cheap FP32 cull with a relative margin (exact test follows)
-      {
-        float dx = (float)NS::dif(Pj.a, Pi.a), dy = (float)NS::dif(Pj.b, Pi.b),
-              dz = (float)NS::dif(Pj.c, Pi.c);
-        if (P.periodic[0]) dx = dx > P.cf.halfL[0] ? dx - P.cf.L[0] : (dx < -P.cf.halfL[0] ? dx + P.cf.L[0] : dx);
-        if (P.periodic[1]) dy = dy > P.cf.halfL[1] ? dy - P.cf.L[1] : (dy < -P.cf.halfL[1] ? dy + P.cf.L[1] : dy);
-        if (P.periodic[2]) dz = dz > P.cf.halfL[2] ? dz - P.cf.L[2] : (dz < -P.cf.halfL[2] ? dz + P.cf.L[2] : dz);
-        float sr = (float)ri + (float)NS::f(Pj.d);
-        float cut = P.lubrication ? sr * (1.0f + lub_out_f) : sr;
-        if (dx * dx + dy * dy + dz * dz > cut * cut * 1.0002f) continue;
-      }
       const bool i_lo = nbr_first(e);
       const Quad<S>& A = i_lo ? Pi : Pj;
       const Quad<S>& Bq = i_lo ? Pj : Pi;
@@ -164,12 +182,14 @@ __global__ void __launch_bounds__(128, 6) k_substep(DevState st, DevMesh mesh, D
       S num = NS::subq(NS::mul(ssum, ssum), d2);
       const F dist = xsqrt(NS::f(d2));
       const F sF = NS::f(ssum);
-      const F delta = NS::f(num) / (sF + dist);  // r_A + r_B - |dx|
+      // r_A + r_B - |dx| without cancellation: (s^2 - d^2) / (s + d)
+      const F delta = NS::kExtended ? NS::f(num) / (sF + dist) : sF - dist;
+      const F dxf[3] = {NS::f(dxs[0]), NS::f(dxs[1]), NS::f(dxs[2])};
       const bool contact = delta > F(0);
       const bool lub = P.lubrication && (-delta < K.lub_out * sF);
       if (!contact && !lub) continue;
       const F inv_d = F(1) / dist;
-      const V3<F> n{NS::f(dxs[0]) * inv_d, NS::f(dxs[1]) * inv_d, NS::f(dxs[2]) * inv_d};
+      const V3<F> n{dxf[0] * inv_d, dxf[1] * inv_d, dxf[2] * inv_d};
       const Quad<S> Vj = ldq(vel + j);
       const F vj[3] = {NS::f(Vj.a), NS::f(Vj.b), NS::f(Vj.c)};
       const F* vA = i_lo ? vi : vj;
@@ -294,14 +314,14 @@ __global__ void __launch_bounds__(128, 6) k_substep(DevState st, DevMesh mesh, D
                   (fc.z + fl.z + ff[2]) * inv_m + K.g[2]};
       const F inv_I = F(2.5) / (mi * ri * ri);
       F alp[3] = {tq.x * inv_I, tq.y * inv_I, tq.z * inv_I};
-      S vn[3] = {NS::fma_ff(Vi.a, K.dt, acc[0]), NS::fma_ff(Vi.b, K.dt, acc[1]),
-                 NS::fma_ff(Vi.c, K.dt, acc[2])};
-      S wn[3] = {NS::fma_ff(Wi.a, K.dt, alp[0]), NS::fma_ff(Wi.b, K.dt, alp[1]),
-                 NS::fma_ff(Wi.c, K.dt, alp[2])};
+      S vn[3] = {NS::fmaq(Vi.a, K.dt, acc[0]), NS::fmaq(Vi.b, K.dt, acc[1]),
+                 NS::fmaq(Vi.c, K.dt, acc[2])};
+      S wn[3] = {NS::fmaq(Wi.a, K.dt, alp[0]), NS::fmaq(Wi.b, K.dt, alp[1]),
+                 NS::fmaq(Wi.c, K.dt, alp[2])};
       S xn[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        S x = NS::add(xi_s[a], NS::mul_f(vn[a], K.dt));
+        S x = NS::addq(xi_s[a], NS::mul_f(vn[a], K.dt));
         if (P.periodic[a]) {
           if (NS::lt(x, B.lo[a])) x = NS::add(x, B.L[a]);
           else if (!NS::lt(x, B.hi[a])) x = NS::sub(x, B.L[a]);

@@ -52,4 +52,24 @@ void launch_phi_convert(int form, const void* phi, double* out, int64_t n, int t
                         cudaStream_t s);
 void launch_phi_from_double(int form, const double* in, void* phi, int64_t n, cudaStream_t s);
 
+// k_cnn.cu: learned warm start (3x3x3 CNN 4 -> 32 -> 32 -> 4, bf16 storage).
+size_t cnn_param_count();
+size_t cnn_work_bytes(int64_t n);
+// network input from four channel rows (FP64 device arrays) divided by scale
+void cnn_input(const DevParams& P, const double* const f[4], const float scale[4], void* work,
+               cudaStream_t s);
+// forward with the bf16-rounded copy of the FP32 master weights; *y_out: [v][4] FP32
+void cnn_forward(const DevParams& P, const float* master, void* work, float** y_out,
+                 cudaStream_t s);
+// loss = mean (y - target)^2 ([v][4] FP32 target) and its gradient (FP32, packed order)
+void cnn_loss_grad(const DevParams& P, const float* master, const float* target, float* grad,
+                   double* loss, void* work, cudaStream_t s);
+void cnn_adam(float* master, const float* grad, float* m, float* v, int64_t t, float lr,
+              cudaStream_t s);
+void cnn_chan_first_to_vec(const double* in, float* out, int64_t n, int nc, cudaStream_t s);
+void cnn_vec_to_chan_first(const float* in, double* out, int64_t n, int nc, cudaStream_t s);
+// guess = phi (+ scale * y on eps and F), in the smoothing word of the form
+void cnn_guess(int form, const void* phi, const float* y, const float scale[4], void* guess,
+               int64_t C, cudaStream_t s);
+
 }  // namespace sedi

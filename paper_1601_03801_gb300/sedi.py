@@ -32,7 +32,8 @@ EXPORTS = [
     "sedi_set_fluid", "sedi_set_eps", "sedi_step", "sedi_average", "sedi_deposit", "sedi_smooth",
     "sedi_get_particles", "sedi_compute_forces", "sedi_get_neighbors", "sedi_get_contacts",
     "sedi_save_state", "sedi_load_state", "sedi_get_timings", "sedi_get_stats", "sedi_sync",
-    "sedi_last_error", "sedi_smooth_static",
+    "sedi_last_error", "sedi_smooth_static", "sedi_cnn_set_params", "sedi_cnn_get_params",
+    "sedi_cnn_forward", "sedi_cnn_loss_grad", "sedi_cnn_train",
 ]
 
 
@@ -50,7 +51,8 @@ class SediParams(C.Structure):
         ("bandwidth", _D * 3), ("n_tau", _I), ("cg_rtol", _D), ("cg_max_iter", _I),
         ("shift_eps", _I), ("shift_mom", _I), ("shift_force", _I),
         ("precision_form", _I), ("nbr_capacity", _I), ("use_graphs", _I), ("block_size", _I),
-        ("n_beds", _I), ("profile", _I), ("seed", C.c_uint64),
+        ("n_beds", _I), ("profile", _I), ("use_cnn_guess", _I), ("cnn_scale", _D * 4),
+        ("seed", C.c_uint64),
     ]
 
 
@@ -98,6 +100,11 @@ def lib():
             "sedi_sync": (C.c_int, [_P]),
             "sedi_last_error": (C.c_char_p, [_P]),
             "sedi_smooth_static": (C.c_int, [C.POINTER(SediParams), _I, _P, _P, _P, _P, C.c_char_p, _I]),
+            "sedi_cnn_set_params": (C.c_int, [_P, _P, _L]),
+            "sedi_cnn_get_params": (C.c_int, [_P, _P, _L]),
+            "sedi_cnn_forward": (C.c_int, [_P, _P, _P, _I]),
+            "sedi_cnn_loss_grad": (C.c_int, [_P, _P, _P, _P, _P, _I]),
+            "sedi_cnn_train": (C.c_int, [_P, _I, _P, _P, _I, _D, _P, _I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -323,6 +330,41 @@ class Sedi:
 
     def load_state(self, path):
         self._check(lib().sedi_load_state(self.h, str(path).encode()))
+
+    # ---- learned warm start
+    CNN_PARAMS = 34628  # SEDI_CNN_PARAMS
+
+    def cnn_set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        self._check(lib().sedi_cnn_set_params(self.h, p.ctypes.data, p.size))
+
+    def cnn_get_params(self):
+        p = np.zeros(self.CNN_PARAMS)
+        self._check(lib().sedi_cnn_get_params(self.h, p.ctypes.data, p.size))
+        return p
+
+    def cnn_forward(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(4, self.C)
+        y = np.zeros_like(x)
+        self._check(lib().sedi_cnn_forward(self.h, x.ctypes.data, y.ctypes.data, MEM_HOST))
+        return y
+
+    def cnn_loss_grad(self, x, target):
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(4, self.C)
+        t = np.ascontiguousarray(target, dtype=np.float64).reshape(4, self.C)
+        g = np.zeros(self.CNN_PARAMS)
+        loss = C.c_double()
+        self._check(lib().sedi_cnn_loss_grad(self.h, x.ctypes.data, t.ctypes.data, g.ctypes.data,
+                                             C.byref(loss), MEM_HOST))
+        return loss.value, g
+
+    def cnn_train(self, x, target, steps, lr=1e-3):
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 4, self.C)
+        t = np.ascontiguousarray(target, dtype=np.float64).reshape(-1, 4, self.C)
+        losses = np.zeros(steps)
+        self._check(lib().sedi_cnn_train(self.h, x.shape[0], x.ctypes.data, t.ctypes.data, int(steps),
+                                         float(lr), losses.ctypes.data, MEM_HOST))
+        return losses
 
     def timings(self) -> dict:
         ms = (C.c_double * 8)()
