@@ -435,9 +435,15 @@ def kernels_only(args):
 
     torch.cuda.set_device(0)
     prm, parts, fl = bed_case()
-    g = sedi.Sedi(dict(prm, precision_form=args.form, use_graphs=int(args.graphs)))
+    extra = {}
+    if args.with_cnn:
+        extra = dict(use_cnn_guess=1, cnn_scale=(0.6, 1e4, 1e4, 1e4))
+    g = sedi.Sedi(dict(prm, precision_form=args.form, use_graphs=int(args.graphs), **extra))
     g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
     g.set_fluid(U=fl["U"])
+    if args.with_cnn:
+        rng = np.random.default_rng(7)
+        g.cnn_set_params(rng.normal(0, 0.05, g.CNN_PARAMS))
     g.average_inplace()
     for _ in range(args.settle + args.steps):
         g.step(SUBSTEPS)
@@ -460,6 +466,8 @@ def main():
     ap.add_argument("--mode", default="bench", choices=["bench", "kernels"],
                     help="kernels: run the workload untimed (profiling driver)")
     ap.add_argument("--form", default="split", choices=["split", "plain", "fp64"])
+    ap.add_argument("--with-cnn", action="store_true",
+                    help="kernels mode: average with the learned warm start (random weights)")
     ap.add_argument("--graphs", type=int, default=1,
                     help="kernels mode: 0 launches kernels one by one (profilers see them)")
     args = ap.parse_args()

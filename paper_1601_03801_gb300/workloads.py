@@ -195,7 +195,7 @@ def _cache_path(tag):
 
 def packed_bed(n_total, tiles, block_xy, dsample, seed, spacing):
     """Tile a relaxed periodic block of n_total / prod(tiles) spheres."""
-    tag = f"bedv2_{n_total}_{tiles[0]}x{tiles[1]}_{block_xy[0]:.4g}_{block_xy[1]:.4g}_{seed}"
+    tag = f"bedv3_{n_total}_{tiles[0]}x{tiles[1]}_{block_xy[0]:.4g}_{block_xy[1]:.4g}_{seed}"
     path = _cache_path(tag)
     if os.path.exists(path):
         z = np.load(path)
@@ -211,6 +211,11 @@ def packed_bed(n_total, tiles, block_xy, dsample, seed, spacing):
             xs.append(x + np.array([tx * block_xy[0], ty * block_xy[1], 0.0]))
             ds.append(d)
     X = np.concatenate(xs); D = np.concatenate(ds)
+    # the offsets can round a coordinate up to the periodic bound: keep [0, L)
+    for a in range(2):
+        L = tiles[a] * block_xy[a]
+        X[:, a] = np.where(X[:, a] >= L, X[:, a] - L, X[:, a])
+        X[:, a] = np.minimum(X[:, a], np.nextafter(L, 0.0))
     np.savez(path, x=X, d=D)
     return X, D
 

@@ -321,3 +321,58 @@ def test_full_size_bed_forces_and_lists():
     off_g, ids_g = g.neighbors()
     off_o, ids_o = o.neighbors(prm["skin"], brute=False)
     assert np.array_equal(off_g, off_o) and np.array_equal(ids_g, ids_o)
+
+
+@pytest.mark.skipif(os.environ.get("SEDI_SKIP_LARGE") == "1", reason="large case disabled")
+def test_large_bed_window_forces_and_lists():
+    """The 10M-sphere bed at full size, sampled: forces and lists come from the full
+    10M launch; the oracle gets a mesh-aligned window of the same state.  Spheres
+    deeper inside the window than the list cut-off (plus two cells) have all their
+    partners and interpolation cells inside it, so their forces (split form, 1e-5 of
+    the largest force of each kind) and lists (bit-exact) must agree."""
+    from paper_1601_03801_gb300.workloads import large_case
+
+    prm, parts, fl = large_case()
+    run = sedi.Sedi(dict(prm, precision_form="split"))
+    run.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+    run.set_fluid(U=fl["U"], DUDt=fl["DUDt"])
+    run.step(20)
+    eps, _, _ = run.average()
+    run.step(20)
+    x, v, w, _ = run.get_particles()
+    run.close()
+    # a fresh full-size handle at this state (springs and lagged acceleration zero)
+    full = sedi.Sedi(dict(prm, precision_form="split"))
+    full.set_particles(x, v, w, parts["d"], parts["rho"])
+    full.set_fluid(U=fl["U"], DUDt=fl["DUDt"])
+    full.set_eps(eps)
+    x, v, w, _ = full.get_particles()
+    fg = full.compute_forces()
+    nc = np.array(prm["ncell"])
+    h = (np.array(prm["hi"]) - np.array(prm["lo"])) / nc
+    c0 = np.array([120, 60, 0]); c1 = np.array([136, 76, nc[2]])  # window in cells
+    lo = c0 * h; hi = c1 * h
+    idx = np.nonzero(np.all((x >= lo) & (x < hi), axis=1))[0]
+    wprm = dict(prm, lo=tuple(lo), hi=tuple(hi), ncell=tuple(c1 - c0), periodic=(0, 0, 0),
+                wall_lo=(0, 0, 1), wall_hi=(0, 0, 0))
+
+    def sub(f, k):
+        return f.reshape(nc[2], nc[1], nc[0], k)[c0[2]:c1[2], c0[1]:c1[1], c0[0]:c1[0]].reshape(-1, k)
+
+    o = orc.Oracle(wprm)
+    o.set_particles(x[idx], v[idx], w[idx], parts["d"][idx], parts["rho"][idx])
+    o.set_fluid(U=sub(fl["U"], 3), DUDt=sub(fl["DUDt"], 3))
+    o.set_eps(sub(eps.reshape(-1, 1), 1)[:, 0])
+    fo = o.forces()
+    cut = 2 * parts["d"].max() * (1 + prm["lub_h_out_frac"]) + prm["skin"] + 2 * h.max()
+    xi = x[idx]
+    deep = np.all((xi[:, :2] >= lo[:2] + cut) & (xi[:, :2] < hi[:2] - cut), axis=1)
+    assert deep.sum() > 1000
+    for k in ("contact", "lub", "fluid", "torque"):
+        assert rel_err(fg[k][idx[deep]], fo[k][deep]) <= 1e-5, k
+    off_g, ids_g = full.neighbors()
+    off_o, ids_o = o.neighbors(prm["skin"], brute=False)
+    for li in np.nonzero(deep)[0][:3000]:
+        gi = idx[li]
+        want = np.sort(idx[ids_o[off_o[li]:off_o[li + 1]]])
+        assert np.array_equal(ids_g[off_g[gi]:off_g[gi + 1]], want)
