@@ -272,6 +272,8 @@ def gpu_arm(args):
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "particles_per_gpu": n, "substeps_per_step": SUBSTEPS,
                            "mesh_cells": C, "form": "split", "graphs": True,
+                           "substep_variant": {"variant": st1["substep_variant"],
+                                               "block": st1["substep_block"], "chosen_by": "autotuner"},
                            "l2": "flushed (256 MB write) between timed steps, outside the events",
                            "parallelism": "independent bed per GPU" if world > 1 else "1 GPU"},
                 "phases_ms_per_step": phases, "rebuilds_in_timed_region": int(rebuilds),

@@ -94,7 +94,12 @@ typedef struct sedi_params {
   int32_t precision_form;                  /* SEDI_FORM_* [SPLIT] */
   int32_t nbr_capacity;                    /* listed neighbours per particle, <= 32 [32] */
   int32_t use_graphs;                      /* capture substeps in CUDA graphs [1] */
-  int32_t block_size;                      /* force-kernel block size, 0 = tuned [0] */
+  int32_t substep_variant;                 /* launch shape of the fused substep kernel:
+                                              -1 = autotuned at the first sedi_step [-1];
+                                              0: 128 threads, 6 blocks/SM; 1: 64 x 12;
+                                              2: 256 x 3; 3: 128 x 8; 4: 128 x 5.  Results
+                                              are bit-identical across variants.  The
+                                              FP64 parity form always runs variant 0. */
   int32_t n_beds;                          /* independent beds in this handle [1] */
   int32_t profile;                         /* record CUDA events around each phase
                                               (see sedi_get_timings) [0] */
@@ -113,6 +118,8 @@ typedef struct sedi_stats {
   int64_t cg_iterations;  /* CG iterations summed over fields and pseudo-steps */
   int32_t max_neighbors;  /* largest list length at the last rebuild */
   int32_t nbr_capacity;   /* capacity in use */
+  int32_t substep_variant; /* launch variant of the substep kernel in use (-1: not yet tuned) */
+  int32_t substep_block;   /* its threads per block (0: not yet tuned) */
 } sedi_stats;
 
 /* Fill p with the defaults listed above (box 20 x 20 x 40 mm, periodic x/y,

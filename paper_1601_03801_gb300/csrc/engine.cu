@@ -9,7 +9,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -47,7 +49,8 @@ struct sedi_handle {
   double coef[3] = {0, 0, 0};
   std::map<int, cudaGraphExec_t> graphs;
   sedi_stats stats{};
-  int block = 128;
+  int variant = SUBSTEP_B128;  // substep launch variant in use
+  std::string tuned_key;       // workload the variant was tuned for (empty: not tuned)
   // profiling: events per captured substep (A: before check, B: before the
   // substep kernel, C: after it) and around deposition / smoothing
   struct GraphEv {
@@ -243,6 +246,8 @@ int check_params(sedi_handle* h, const sedi_params& p) {
   if (p.precision_form < 0 || p.precision_form > 2) return fail(h, SEDI_EINVAL, "unknown precision_form");
   if (p.nbr_capacity < 1 || p.nbr_capacity > 32) return fail(h, SEDI_EINVAL, "nbr_capacity must be in [1, 32]");
   if (p.n_beds != 1) return fail(h, SEDI_EINVAL, "n_beds: this build runs one bed per handle");
+  if (p.substep_variant < -1 || p.substep_variant >= kSubstepVariants)
+    return fail(h, SEDI_EINVAL, "substep_variant must be -1 (tuned) or in [0, %d]", kSubstepVariants - 1);
   for (int k = 0; k < 3; ++k) {
     int s = k == 0 ? p.shift_eps : (k == 1 ? p.shift_mom : p.shift_force);
     if (s < 0 || s > 60) return fail(h, SEDI_EINVAL, "fixed-point shifts must be in [0, 60]");
@@ -421,7 +426,7 @@ int build_graph(sedi_handle* h, int n, cudaGraphExec_t* out) {
     CK(cudaStreamEndCapture(h->side, &body));
     if (h->prm.profile) CK(cudaEventRecordWithFlags(ev.b[s], h->stream, cudaEventRecordExternal));
     const bool more = s + 1 < n;
-    launch_substep(h->form, h->st, h->mesh, h->P, s, true, h->block,
+    launch_substep(h->form, h->st, h->mesh, h->P, s, true, h->variant,
                    more ? (unsigned long long)ch[s + 1] : 0ull, more ? 1 : 0, h->stream);
     if (h->prm.profile) CK(cudaEventRecordWithFlags(ev.c[s], h->stream, cudaEventRecordExternal));
   }
@@ -443,6 +448,122 @@ int need_particles(sedi_handle* h) {
 int rebuild_now(sedi_handle* h) {
   launch_rebuild(h->form, h->st, h->P, 0, true, h->stream);
   return sync_status(h);
+}
+
+// ---------------------------------------------------------------- autotuner
+// The launch variant of the substep kernel (threads per block x resident blocks,
+// which sets the register budget) is picked per workload: forces-only launches of
+// every variant (they write only the force read-back buffer, so the state is
+// untouched) are timed with events in interleaved rounds, and the variant with
+// the lowest median wins.  Results are keyed by (GPU, N, diameter range, form),
+// kept for the process and, when the environment variable SEDI_AUTOTUNE_CACHE
+// names a file, in that file as one JSON object per line.
+
+constexpr int kTuneRounds = 5;
+
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune_cache;
+
+std::string tune_key(sedi_handle* h) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) std::snprintf(prop.name, sizeof(prop.name), "device%d", dev);
+  double dmin = 1e300, dmax = 0.0;
+  for (double d : h->d_host) {
+    dmin = std::min(dmin, d);
+    dmax = std::max(dmax, d);
+  }
+  char buf[512];
+  std::snprintf(buf, sizeof(buf), "%s sm%d|N=%lld|d=%.3e..%.3e|form=%d", prop.name,
+                prop.multiProcessorCount, (long long)h->N, dmin, dmax, h->form);
+  return buf;
+}
+
+int tune_file_lookup(const std::string& key) {
+  const char* path = std::getenv("SEDI_AUTOTUNE_CACHE");
+  if (!path || !*path) return -1;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return -1;
+  int found = -1;
+  char line[1024];
+  const std::string want = "\"key\": \"" + key + "\"";
+  while (std::fgets(line, sizeof(line), f)) {
+    const char* k = std::strstr(line, want.c_str());
+    const char* v = std::strstr(line, "\"variant\": ");
+    if (!k || !v) continue;
+    const int var = std::atoi(v + 11);
+    if (var >= 0 && var < kSubstepVariants) found = var;  // the last entry wins
+  }
+  std::fclose(f);
+  return found;
+}
+
+void tune_file_store(const std::string& key, int variant, const double* us) {
+  const char* path = std::getenv("SEDI_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "{\"key\": \"%s\", \"variant\": %d, \"block\": %d, \"median_us\": [", key.c_str(),
+               variant, substep_block(variant));
+  for (int v = 0; v < kSubstepVariants; ++v) std::fprintf(f, "%s%.3f", v ? ", " : "", us[v]);
+  std::fprintf(f, "]}\n");
+  std::fclose(f);
+}
+
+// Choose h->variant for the current particles (no-op when fixed or up to date).
+int autotune(sedi_handle* h) {
+  if (h->prm.substep_variant >= 0 || h->form == FORM_FP64) return 0;
+  const std::string key = tune_key(h);
+  if (key == h->tuned_key) return 0;
+  int best = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) best = it->second;
+  }
+  if (best < 0) best = tune_file_lookup(key);
+  if (best < 0) {
+    // lists must cover the current positions, exactly as the first substep would see them
+    launch_check(h->st, h->P, 0ull, 0, h->stream);
+    launch_rebuild(h->form, h->st, h->P, 0, false, h->stream);
+    std::vector<cudaEvent_t> ev(2 * kSubstepVariants * kTuneRounds, nullptr);
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    for (int v = 0; v < kSubstepVariants; ++v)  // warm-up: first launch of each variant
+      launch_substep(h->form, h->st, h->mesh, h->P, 0, false, v, 0ull, 0, h->stream);
+    for (int r = 0; r < kTuneRounds; ++r)
+      for (int v = 0; v < kSubstepVariants; ++v) {
+        cudaEvent_t* e = &ev[2 * (r * kSubstepVariants + v)];
+        CK(cudaEventRecord(e[0], h->stream));
+        launch_substep(h->form, h->st, h->mesh, h->P, 0, false, v, 0ull, 0, h->stream);
+        CK(cudaEventRecord(e[1], h->stream));
+      }
+    int rc = sync_status(h);
+    double med[kSubstepVariants];
+    for (int v = 0; v < kSubstepVariants && !rc; ++v) {
+      std::vector<double> t;
+      for (int r = 0; r < kTuneRounds; ++r) {
+        float ms = 0.0f;
+        cudaEvent_t* e = &ev[2 * (r * kSubstepVariants + v)];
+        if (cudaEventElapsedTime(&ms, e[0], e[1]) != cudaSuccess) ms = 1e30f;
+        t.push_back(1e3 * ms);
+      }
+      std::sort(t.begin(), t.end());
+      med[v] = t[kTuneRounds / 2];
+      if (best < 0 || med[v] < med[best]) best = v;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (rc) return rc;
+    tune_file_store(key, best, med);
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  if (best != h->variant) clear_graphs(h);  // graphs bake in the launch shape
+  h->variant = best;
+  h->tuned_key = key;
+  return 0;
 }
 
 }  // namespace
@@ -484,7 +605,7 @@ void sedi_default_params(sedi_params* p) {
   p->precision_form = SEDI_FORM_SPLIT;
   p->nbr_capacity = 32;
   p->use_graphs = 1;
-  p->block_size = 0;
+  p->substep_variant = -1;
   p->n_beds = 1;
   p->cnn_scale[0] = p->cnn_scale[1] = p->cnn_scale[2] = p->cnn_scale[3] = 1.0;
 }
@@ -502,7 +623,7 @@ int sedi_create(const sedi_params* p, sedi_handle** out) {
     return rc;
   }
   h->form = p->precision_form;
-  h->block = p->block_size > 0 ? p->block_size : 128;
+  h->variant = p->substep_variant >= 0 && h->form != FORM_FP64 ? p->substep_variant : SUBSTEP_B128;
   fill_params(h);
   const int64_t C = h->P.C;
   h->U.assign(3 * C, 0.0);
@@ -680,6 +801,7 @@ int sedi_step(sedi_handle* h, int32_t n) {
   h->err.clear();
   if (n < 0) return fail(h, SEDI_EINVAL, "n_substeps must be >= 0");
   if (n == 0) return 0;
+  if ((rc = autotune(h))) return rc;
   if (h->prm.profile) harvest(h);
   // stream capture needs a real stream: the legacy NULL stream runs without graphs
   if (h->prm.use_graphs && h->stream != nullptr) {
@@ -715,7 +837,7 @@ int sedi_step(sedi_handle* h, int32_t n) {
       if (s == 0) launch_check(h->st, h->P, 0ull, 0, h->stream);
       launch_rebuild(h->form, h->st, h->P, s, false, h->stream);
       if (h->prm.profile) CK(cudaEventRecord(h->gev[-n].b[s], h->stream));
-      launch_substep(h->form, h->st, h->mesh, h->P, s, true, h->block, 0ull, 0, h->stream);
+      launch_substep(h->form, h->st, h->mesh, h->P, s, true, h->variant, 0ull, 0, h->stream);
       if (h->prm.profile) {
         CK(cudaEventRecord(h->gev[-n].c[s], h->stream));
         h->pending.push_back({0, {h->gev[-n].a[s], h->gev[-n].b[s]}});
@@ -947,7 +1069,7 @@ int sedi_compute_forces(sedi_handle* h, int32_t bed, double* fc, double* fl, dou
   // lists must cover the current positions
   launch_check(h->st, h->P, 0ull, 0, h->stream);
   launch_rebuild(h->form, h->st, h->P, 0, false, h->stream);
-  launch_substep(h->form, h->st, h->mesh, h->P, 0, false, h->block, 0ull, 0, h->stream);
+  launch_substep(h->form, h->st, h->mesh, h->P, 0, false, h->variant, 0ull, 0, h->stream);
   // fdbg is in sorted order: scatter to caller order through the host
   std::vector<double> dbg(12 * N);
   std::vector<int32_t> uid(N);
@@ -1333,6 +1455,9 @@ int sedi_get_stats(sedi_handle* h, sedi_stats* out) {
   if (!h || !out) return SEDI_EINVAL;
   int rc = h->have_particles ? sync_status(h) : 0;
   h->stats.nbr_capacity = h->P.cap;
+  const bool tuned = h->prm.substep_variant >= 0 || h->form == FORM_FP64 || !h->tuned_key.empty();
+  h->stats.substep_variant = tuned ? h->variant : -1;
+  h->stats.substep_block = tuned ? substep_block(h->variant) : 0;
   *out = h->stats;
   return rc;
 }

@@ -14,6 +14,10 @@ __device__ __forceinline__ float xpow_drag(float a, float b) { return __powf(a, 
 __device__ __forceinline__ double xpow_drag(double a, double b) { return pow(a, b); }
 __device__ __forceinline__ float xfloor(float a) { return floorf(a); }
 __device__ __forceinline__ double xfloor(double a) { return floor(a); }
+// a * b + c with a single rounding, written out so that the result does not depend
+// on the compiler's contraction choices (which can change with register budgets)
+__device__ __forceinline__ float xfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double xfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float xabs(float a) { return fabsf(a); }
 __device__ __forceinline__ double xabs(double a) { return fabs(a); }
 __device__ __forceinline__ bool xisfinite(float a) { return isfinite(a); }

@@ -97,10 +97,13 @@ __device__ __forceinline__ V3<F> cross(V3<F> a, V3<F> b) {
 
 }  // namespace
 
-template <int FORM, bool INTEGRATE>
-__global__ void __launch_bounds__(128, 6) k_substep(DevState st, DevMesh mesh, DevParams P,
-                                                    int sub_off, cudaGraphConditionalHandle next,
-                                                    int use_cond) {
+// BS threads per block, at least MINB resident blocks per SM (which caps the
+// registers a thread may use); the variant is chosen per workload by the engine's
+// autotuner.
+template <int FORM, bool INTEGRATE, int BS, int MINB>
+__global__ void __launch_bounds__(BS, MINB) k_substep(DevState st, DevMesh mesh, DevParams P,
+                                                         int sub_off, cudaGraphConditionalHandle next,
+                                                         int use_cond) {
   using S = typename Traits<FORM>::S;
   using F = typename Traits<FORM>::F;
   using NS = Num<S>;
@@ -310,8 +313,8 @@ __global__ void __launch_bounds__(128, 6) k_substep(DevState st, DevMesh mesh, D
     } else {
       // leapfrog: v += dt a, w += dt T / I, x += dt v (state word)
       const F inv_m = F(1) / mi;
-      F acc[3] = {(fc.x + fl.x + ff[0]) * inv_m + K.g[0], (fc.y + fl.y + ff[1]) * inv_m + K.g[1],
-                  (fc.z + fl.z + ff[2]) * inv_m + K.g[2]};
+      F acc[3] = {xfma(fc.x + fl.x + ff[0], inv_m, K.g[0]), xfma(fc.y + fl.y + ff[1], inv_m, K.g[1]),
+                  xfma(fc.z + fl.z + ff[2], inv_m, K.g[2])};
       const F inv_I = F(2.5) / (mi * ri * ri);
       F alp[3] = {tq.x * inv_I, tq.y * inv_I, tq.z * inv_I};
       S vn[3] = {NS::fmaq(Vi.a, K.dt, acc[0]), NS::fmaq(Vi.b, K.dt, acc[1]),
@@ -357,7 +360,7 @@ __global__ void __launch_bounds__(128, 6) k_substep(DevState st, DevMesh mesh, D
     float m = my_disp2;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    __shared__ float wmax[8];
+    __shared__ float wmax[BS / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) wmax[wid] = m;
     __syncthreads();
@@ -384,33 +387,47 @@ __global__ void __launch_bounds__(128, 6) k_substep(DevState st, DevMesh mesh, D
   }
 }
 
-template <int FORM>
-static void launch_one(const DevState& st, const DevMesh& mesh, const DevParams& P, int sub_off,
-                       bool integrate, int block, unsigned long long next, int use_cond,
-                       cudaStream_t s) {
-  (void)block;
-  const int bs = 128;  // matches __launch_bounds__
-  const int64_t grid = (st.N + bs - 1) / bs;
+template <int FORM, int BS, int MINB>
+static void launch_bs(const DevState& st, const DevMesh& mesh, const DevParams& P, int sub_off,
+                      bool integrate, unsigned long long next, int use_cond, cudaStream_t s) {
+  const int64_t grid = (st.N + BS - 1) / BS;
   const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)next;
   if (integrate)
-    k_substep<FORM, true><<<(unsigned)grid, bs, 0, s>>>(st, mesh, P, sub_off, h, use_cond);
+    k_substep<FORM, true, BS, MINB><<<(unsigned)grid, BS, 0, s>>>(st, mesh, P, sub_off, h, use_cond);
   else
-    k_substep<FORM, false><<<(unsigned)grid, bs, 0, s>>>(st, mesh, P, sub_off, h, 0);
+    k_substep<FORM, false, BS, MINB><<<(unsigned)grid, BS, 0, s>>>(st, mesh, P, sub_off, h, 0);
+}
+
+template <int FORM>
+static void launch_one(const DevState& st, const DevMesh& mesh, const DevParams& P, int sub_off,
+                       bool integrate, int variant, unsigned long long next, int use_cond,
+                       cudaStream_t s) {
+  // the parity form has the 128-thread variant only
+  if constexpr (FORM != FORM_FP64) {
+    switch (variant) {
+      case SUBSTEP_B64: launch_bs<FORM, 64, 12>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
+      case SUBSTEP_B256: launch_bs<FORM, 256, 3>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
+      case SUBSTEP_B128_OCC8: launch_bs<FORM, 128, 8>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
+      case SUBSTEP_B128_OCC5: launch_bs<FORM, 128, 5>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
+      default: break;
+    }
+  }
+  launch_bs<FORM, 128, 6>(st, mesh, P, sub_off, integrate, next, use_cond, s);
 }
 
 void launch_substep(int form, const DevState& st, const DevMesh& mesh, const DevParams& P,
-                    int sub_off, bool integrate, int block, unsigned long long next_cond,
+                    int sub_off, bool integrate, int variant, unsigned long long next_cond,
                     int use_cond, cudaStream_t s) {
   if (st.N <= 0) return;
   switch (form) {
     case FORM_SPLIT:
-      launch_one<FORM_SPLIT>(st, mesh, P, sub_off, integrate, block, next_cond, use_cond, s);
+      launch_one<FORM_SPLIT>(st, mesh, P, sub_off, integrate, variant, next_cond, use_cond, s);
       break;
     case FORM_PLAIN:
-      launch_one<FORM_PLAIN>(st, mesh, P, sub_off, integrate, block, next_cond, use_cond, s);
+      launch_one<FORM_PLAIN>(st, mesh, P, sub_off, integrate, variant, next_cond, use_cond, s);
       break;
     default:
-      launch_one<FORM_FP64>(st, mesh, P, sub_off, integrate, block, next_cond, use_cond, s);
+      launch_one<FORM_FP64>(st, mesh, P, sub_off, integrate, variant, next_cond, use_cond, s);
       break;
   }
 }

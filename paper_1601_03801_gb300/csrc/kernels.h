@@ -6,11 +6,25 @@
 
 namespace sedi {
 
+// Launch variants of the substep kernel: threads per block and minimum resident
+// blocks per SM (128/6, 64/12, 256/3 cap registers at 80 a thread, 128/8 at 64,
+// 128/5 at 96).  The split and plain forms have all five; the FP64 parity form
+// runs 128/6.
+enum SubstepVariant {
+  SUBSTEP_B128 = 0,
+  SUBSTEP_B64 = 1,
+  SUBSTEP_B256 = 2,
+  SUBSTEP_B128_OCC8 = 3,
+  SUBSTEP_B128_OCC5 = 4
+};
+constexpr int kSubstepVariants = 5;
+inline int substep_block(int variant) { return variant == SUBSTEP_B64 ? 64 : variant == SUBSTEP_B256 ? 256 : 128; }
+
 // k_force.cu: one fused substep (integrate = true) or forces only into st.fdbg.
 // The last block of an integrating launch sets ctl->need_rebuild and, when
 // use_cond, the graph condition next_cond of the following rebuild node.
 void launch_substep(int form, const DevState& st, const DevMesh& mesh, const DevParams& P,
-                    int sub_off, bool integrate, int block, unsigned long long next_cond,
+                    int sub_off, bool integrate, int variant, unsigned long long next_cond,
                     int use_cond, cudaStream_t s);
 
 // k_bin.cu: rebuild = bin, sort by (bin, caller index), gather into the other

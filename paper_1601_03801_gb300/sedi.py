@@ -50,7 +50,7 @@ class SediParams(C.Structure):
         ("ncell", _I * 3),
         ("bandwidth", _D * 3), ("n_tau", _I), ("cg_rtol", _D), ("cg_max_iter", _I),
         ("shift_eps", _I), ("shift_mom", _I), ("shift_force", _I),
-        ("precision_form", _I), ("nbr_capacity", _I), ("use_graphs", _I), ("block_size", _I),
+        ("precision_form", _I), ("nbr_capacity", _I), ("use_graphs", _I), ("substep_variant", _I),
         ("n_beds", _I), ("profile", _I), ("use_cnn_guess", _I), ("cnn_scale", _D * 4),
         ("seed", C.c_uint64),
     ]
@@ -58,7 +58,8 @@ class SediParams(C.Structure):
 
 class SediStats(C.Structure):
     _fields_ = [("substeps", _L), ("rebuilds", _L), ("averages", _L), ("cg_iterations", _L),
-                ("max_neighbors", _I), ("nbr_capacity", _I)]
+                ("max_neighbors", _I), ("nbr_capacity", _I), ("substep_variant", _I),
+                ("substep_block", _I)]
 
 
 class SediError(RuntimeError):

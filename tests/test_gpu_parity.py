@@ -131,6 +131,57 @@ def test_deterministic_runs(small):
         assert np.array_equal(res[0][k], res[1][k])
 
 
+@pytest.mark.parametrize("form", ["split", "plain"])
+def test_substep_variants_bit_identical(small, form):
+    """Every launch variant of the substep kernel gives the same bits: each particle's
+    arithmetic does not depend on the block it runs in."""
+    prm, parts = small
+    ref = None
+    for variant in range(5):
+        g = sedi.Sedi(dict(prm, precision_form=form, substep_variant=variant))
+        g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+        g.step(40)
+        eps, _, F = g.average()
+        st = g.stats()
+        assert st["substep_variant"] == variant
+        assert st["substep_block"] == {0: 128, 1: 64, 2: 256, 3: 128, 4: 128}[variant]
+        got = (*g.get_particles(), eps, F)
+        if ref is None:
+            ref = got
+        else:
+            for a, b in zip(ref, got):
+                assert np.array_equal(a, b), variant
+
+
+def test_autotuner_chooses_and_caches(small, tmp_path, monkeypatch):
+    prm, parts = small
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("SEDI_AUTOTUNE_CACHE", str(cache))
+    # a particle count no other test uses, so the in-process cache is cold
+    n = len(parts["x"]) - 3
+    sub = {k: parts[k][:n] for k in ("x", "v", "w", "d", "rho")}
+    g = sedi.Sedi(dict(prm, precision_form="split"))
+    g.set_particles(sub["x"], sub["v"], sub["w"], sub["d"], sub["rho"])
+    assert g.stats()["substep_variant"] == -1
+    g.step(10)
+    st = g.stats()
+    assert 0 <= st["substep_variant"] < 5 and st["substep_block"] in (64, 128, 256)
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and f"N={n}|" in lines[0] and '"median_us"' in lines[0]
+    # a second handle on the same workload takes the cached choice without re-timing
+    h = sedi.Sedi(dict(prm, precision_form="split"))
+    h.set_particles(sub["x"], sub["v"], sub["w"], sub["d"], sub["rho"])
+    h.step(10)
+    assert h.stats()["substep_variant"] == st["substep_variant"]
+    assert len(cache.read_text().splitlines()) == 1
+    # the tuned run is the same trajectory as a fixed variant
+    f = sedi.Sedi(dict(prm, precision_form="split", substep_variant=0))
+    f.set_particles(sub["x"], sub["v"], sub["w"], sub["d"], sub["rho"])
+    f.step(10)
+    for a, b in zip(h.get_particles(), f.get_particles()):
+        assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("form", ["fp64", "split"])
 def test_deposition_bit_exact(small, form):
     prm, parts = small
@@ -259,6 +310,8 @@ def test_errors_are_reported(small):
     prm, parts = small
     with pytest.raises(sedi.SediError):
         sedi.Sedi(dict(prm, restitution=0.0))
+    with pytest.raises(sedi.SediError):
+        sedi.Sedi(dict(prm, substep_variant=5))
     g = sedi.Sedi(dict(prm, precision_form="split", nbr_capacity=2))
     with pytest.raises(sedi.SediError) as e:
         g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
