@@ -32,7 +32,8 @@ METRIC = "particle-steps/s (contact+coupling+averaging), % HBM roofline, vs plai
 UNIT = "particle-steps/s"
 SUBSTEPS = 20
 WORKLOAD = ("sheared sediment bed: 200,000 lognormal spheres (median 0.5 mm, sigma_ln 0.1) "
-            "packed in a periodic 64x32x64 mm channel, wall z=0, log-law flow u*=0.02 m/s, "
+            "packed in a periodic 64x32x64 mm channel, wall z=0, settled by a 40,000-substep "
+            "prep run of the method (untimed), log-law flow u*=0.02 m/s, "
             "64x32x64 mesh, Hertz-Mindlin + lubrication + drag + added mass, diffusion "
             "averaging b=3 d50; step = 20 substeps (dt=1e-6 s) + 1 averaging")
 PROFILE_FILE = os.path.join(ROOT, "profiles", "k_substep_bed200k.md")
@@ -148,7 +149,7 @@ def gpu_arm(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    prm, parts, fl = bed_case()
+    prm, parts, fl = bed_case(settled=True)
     n = len(parts["x"])
     stream = torch.cuda.Stream()
 
@@ -260,6 +261,9 @@ def gpu_arm(args):
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(prm, parts, fl, budget_s=args.cpu_seconds)
+    ens = None
+    if rank == 0 and not args.no_ensemble:
+        ens = ensemble_leg()
     cnn = None
     if rank == 0 and not args.no_cnn:
         cnn = cnn_warm_start(prm, parts, fl)
@@ -278,12 +282,82 @@ def gpu_arm(args):
                            "parallelism": "independent bed per GPU" if world > 1 else "1 GPU"},
                 "phases_ms_per_step": phases, "rebuilds_in_timed_region": int(rebuilds),
                 "roofline": roof, "plain_form": plain, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks, "cpu_baseline": cpu, "cnn_warm_start": cnn}
+                "clocks": clocks, "cpu_baseline": cpu, "ensemble": ens, "cnn_warm_start": cnn}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+
+
+def ensemble_leg(steps=3, warmup=2):
+    """256 independent beds of 2,000..50,000 spheres (log-uniform) on 16^3..48^3
+    meshes: one ensemble handle (one launch per phase over all beds, one CUDA graph
+    per fluid step, batched averaging) against the same beds in 256 single-bed
+    handles stepped one after the other.  A step = 20 substeps + 1 averaging of
+    every bed; particle-steps/s of all beds together."""
+    import torch
+
+    from paper_1601_03801_gb300 import sedi
+    from paper_1601_03801_gb300.workloads import ensemble_case
+
+    prm, beds = ensemble_case()
+    n_total = int(sum(len(b["parts"]["x"]) for b in beds))
+    stream = torch.cuda.Stream()
+
+    def load(g, b, bd, kw):
+        p = bd["parts"]
+        g.set_particles(p["x"], p["v"], p["w"], p["d"], p["rho"], **kw)
+        g.set_fluid(U=bd["U"], **kw)
+
+    E = sedi.Sedi(dict(prm, n_beds=len(beds), precision_form="split"), stream=stream)
+    for b, bd in enumerate(beds):
+        E.set_bed(b, bd["lo"], bd["hi"], bd["ncell"])
+        load(E, b, bd, {"bed": b})
+    singles = []
+    for bd in beds:
+        g = sedi.Sedi(dict(prm, lo=bd["lo"], hi=bd["hi"], ncell=bd["ncell"], precision_form="split"),
+                      stream=stream)
+        load(g, 0, bd, {})
+        singles.append(g)
+
+    def timed(step):
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def step_batched():
+        E.step(SUBSTEPS)
+        E.average_inplace()
+
+    def step_per_bed():
+        for g in singles:
+            g.step(SUBSTEPS)
+            g.average_inplace()
+
+    E.average_inplace()
+    for g in singles:
+        g.average_inplace()
+    ms_b = timed(step_batched)
+    ms_p = timed(step_per_bed)
+    rate = lambda ms: round(n_total * SUBSTEPS / (ms / 1e3), 1)
+    return {"workload": "256 beds, N_b = exp(U[ln 2000, ln 50000]) spheres of d = 0.5 mm on a jittered "
+                        "lattice, n_b mm cubic periodic-x/y wall-z boxes, n_b^3 meshes (n_b = 16..48), "
+                        "log-law flow; step = 20 substeps + 1 averaging of every bed",
+            "beds": len(beds), "particles": n_total, "steps": steps, "warmup": warmup,
+            "batched": {"value": rate(ms_b), "unit": UNIT, "ms_per_step": round(ms_b, 3)},
+            "per_bed_launches": {"value": rate(ms_p), "unit": UNIT, "ms_per_step": round(ms_p, 3)},
+            "speedup": round(ms_p / ms_b, 3),
+            "timing": "CUDA events on the launching stream around the steps (the averagings "
+                      "synchronise the host once per handle per step)"}
 
 
 def cnn_warm_start(prm0, parts, fl, train_steps=300, snapshots=5):
@@ -397,7 +471,7 @@ def reference_arm(args):
     from oracle import oracle as orc
     from paper_1601_03801_gb300.workloads import bed_case
 
-    prm, parts, fl = bed_case()
+    prm, parts, fl = bed_case(settled=True)
     n = len(parts["x"])
     o = orc.Oracle(prm)
     o.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
@@ -436,7 +510,7 @@ def kernels_only(args):
     from paper_1601_03801_gb300.workloads import bed_case
 
     torch.cuda.set_device(0)
-    prm, parts, fl = bed_case()
+    prm, parts, fl = bed_case(settled=True)
     extra = {}
     if args.with_cnn:
         extra = dict(use_cnn_guess=1, cnn_scale=(0.6, 1e4, 1e4, 1e4))
@@ -463,6 +537,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-cnn", action="store_true", help="skip the learned-warm-start leg")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 256-bed ensemble leg")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--settle", type=int, default=50, help="untimed settling steps before warm-up")
     ap.add_argument("--mode", default="bench", choices=["bench", "kernels"],

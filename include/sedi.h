@@ -53,6 +53,9 @@ enum {
 
 enum { SEDI_MEM_HOST = 0, SEDI_MEM_DEVICE = 1 };
 
+/* sedi_average's bed argument for "every bed of an ensemble, in place". */
+#define SEDI_ALL_BEDS (-1)
+
 /* Arithmetic of the hot path.
  * SEDI_FORM_SPLIT (default): forces in FP32; positions, velocities, spins and
  *   tangential springs carried in FP64-class double-float (two FP32 words,
@@ -97,10 +100,13 @@ typedef struct sedi_params {
   int32_t substep_variant;                 /* launch shape of the fused substep kernel:
                                               -1 = autotuned at the first sedi_step [-1];
                                               0: 128 threads, 6 blocks/SM; 1: 64 x 12;
-                                              2: 256 x 3; 3: 128 x 8; 4: 128 x 5.  Results
-                                              are bit-identical across variants.  The
-                                              FP64 parity form always runs variant 0. */
-  int32_t n_beds;                          /* independent beds in this handle [1] */
+                                              2: 256 x 3; 3: 128 x 8; 4: 128 x 5.  In the
+                                              split form results are bit-identical across
+                                              variants; in the plain form they agree to
+                                              FP32 rounding.  The FP64 parity form always
+                                              runs variant 0. */
+  int32_t n_beds;                          /* independent beds in this handle, 1..1024
+                                              (see "Ensembles" below) [1] */
   int32_t profile;                         /* record CUDA events around each phase
                                               (see sedi_get_timings) [0] */
   int32_t use_cnn_guess;                   /* start every smoothing pseudo-step from
@@ -140,6 +146,28 @@ void sedi_destroy(sedi_handle* h);
    The stream must outlive its use by the handle. */
 int sedi_set_stream(sedi_handle* h, void* cuda_stream);
 
+/* ---- Ensembles (params.n_beds > 1) ----
+ * The paper runs one bed per simulation; an ensemble holds n_beds independent
+ * beds of uneven size (Sec. 2's method applied to each) so that small beds fill
+ * the GPU together.  Each bed has its own particles, box and mesh (default: the
+ * box and mesh of the parameters; sedi_set_bed changes them) and its own fluid
+ * fields; the material, fluid, time step, bandwidth and solver parameters are
+ * shared.  Every call that takes `bed` addresses one bed.  sedi_step advances all
+ * beds with one launch per phase over all beds (one CUDA graph per fluid step);
+ * sedi_average(h, SEDI_ALL_BEDS, NULL, NULL, NULL, mem) averages every bed in
+ * batched launches and leaves the results on the device for the drag;
+ * sedi_average(h, bed, ...) returns one bed's averaged fields (averaging all beds
+ * first if a step happened since).  Every bed must have particles before the
+ * first step.  A bed's results are bit-identical to running it alone in a
+ * single-bed handle.  Not for ensembles: params.use_cnn_guess (learned warm
+ * start) and the substep autotuner (ensembles run 128-thread blocks). */
+
+/* Box [lo, hi) and mesh ncell of ensemble bed `bed`; resets that bed (its
+   particles must be set again).  Errors: EINVAL (not an ensemble, bed out of
+   range, bad box or mesh), ENOMEM. */
+int sedi_set_bed(sedi_handle* h, int32_t bed, const double lo[3], const double hi[3],
+                 const int32_t ncell[3]);
+
 /* Set n particles of bed `bed` (0 <= bed < n_beds): ids (may be NULL: 0..n-1),
    positions x, half-step velocities v (Sec. 2.1: leapfrog), angular velocities
    omega (NULL = 0), diameters d and densities rho.  Positions on periodic axes
@@ -169,9 +197,10 @@ int sedi_step(sedi_handle* h, int32_t n_substeps);
 
 /* Diffusion-based averaging of bed `bed` (Sec. 2.4, Eq. 9-10): PCM deposition of
    eps_s, eps_s U_s and the force density -f_fp / V_c on the fluid, then n_tau
-   implicit diffusion steps.  Outputs (any may be NULL): eps_s (C), U_s (C x 3),
-   F_fp (C x 3).  The smoothed eps_s becomes the one the drag law sees.  Errors:
-   ERANGE, EDIVERGED. */
+   implicit diffusion steps, each solved to ||b - A x|| <= cg_rtol ||b||.  Outputs
+   (any may be NULL): eps_s (C), U_s (C x 3), F_fp (C x 3).  The smoothed eps_s
+   becomes the one the drag law sees.  bed = SEDI_ALL_BEDS (ensembles): every
+   bed, outputs NULL.  Errors: ERANGE, EDIVERGED. */
 int sedi_average(sedi_handle* h, int32_t bed, double* eps_s, double* U_s, double* F_fp,
                  int32_t mem);
 
@@ -237,7 +266,9 @@ int sedi_cnn_train(sedi_handle* h, int32_t n_pairs, const double* x, const doubl
                    int32_t steps, double lr, double* losses, int32_t mem);
 
 /* Checkpoint and restore of particles, lagged accelerations, tangential springs,
-   fluid fields and the drag's solid fraction (binary, this library's format). */
+   fluid fields and the drag's solid fraction (binary, this library's format; an
+   ensemble writes every bed, and restores into a handle with as many beds of the
+   same meshes). */
 int sedi_save_state(sedi_handle* h, const char* path);
 int sedi_load_state(sedi_handle* h, const char* path);
 
@@ -265,8 +296,9 @@ int sedi_get_stats(sedi_handle* h, sedi_stats* out);
  *   iters   : host array of n_fields (or NULL) receiving the solver iterations.
  *   cuda_stream : stream to run on (NULL = legacy default stream).
  *   msg     : optional host buffer of msg_len bytes for an error message.
- * Limit: n_fields * C <= SEDI_STATIC_MAX_WORDS (e.g. 7 fields on 131,072 cells);
- * larger sizes return SEDI_EINVAL.  The scratch (about 50 MB) lives on every GPU
+ * Limit: 8 * C <= SEDI_STATIC_MAX_WORDS, i.e. up to 131,072 cells with any
+ * n_fields <= 8 (the solver keeps 8 words per cell); larger meshes return
+ * SEDI_EINVAL.  The scratch (about 42 MB) lives on every GPU
  * that loads the library until the process exits.  The first call on a device
  * looks up the scratch's device address (cudaGetSymbolAddress) for that device;
  * make that first call before any stream capture.  Every call shares the one

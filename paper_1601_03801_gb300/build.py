@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsedi.so")
-UNITS = ["engine.cu", "k_force.cu", "k_bin.cu", "k_avg.cu", "k_cnn.cu"]
+UNITS = ["engine.cu", "k_force.cu", "k_bin.cu", "k_avg.cu", "k_smooth.cu", "k_cnn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -30,7 +30,11 @@ def nvcc():
 def _compile(unit, extra):
     src = os.path.join(CSRC, unit)
     obj = os.path.join(BUILD, unit + ".o")
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+    # --fmad=false: a multiply-add is fused only where the source writes fmaf (or an
+    # FMA intrinsic), never by the compiler's choice, which can depend on the
+    # surrounding kernel; so a device function gives the same bits in every kernel
+    # and launch variant it is compiled into (single-bed and ensemble launches)
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
            "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-c", src, "-o", obj, *extra]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

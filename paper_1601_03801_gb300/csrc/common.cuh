@@ -267,6 +267,29 @@ struct DevMesh {
 
 constexpr int kWalls = 6;
 
+// One bed of an ensemble as the kernels see it: the single-bed views of its arrays
+// and parameters.  Batched launches take a device table of these and pick the bed
+// of a block from blockIdx.y.
+struct alignas(16) BedView {
+  DevState st;
+  DevMesh mesh;
+  DevParams P;
+  void* qfix;  // [7][C] fixed-point deposition (split/FP64 forms)
+  void* phi;   // [8][C] smoothing word (the plain form deposits here)
+};
+
+#ifdef __CUDACC__
+// Copy the view of this block's bed (blockIdx.y) into shared memory.
+__device__ __forceinline__ const BedView& bed_view(const BedView* views) {
+  __shared__ BedView s_view;
+  const int4* src = reinterpret_cast<const int4*>(views + blockIdx.y);
+  int4* dst = reinterpret_cast<int4*>(&s_view);
+  for (int k = threadIdx.x; k < (int)(sizeof(BedView) / 16); k += blockDim.x) dst[k] = src[k];
+  __syncthreads();
+  return s_view;
+}
+#endif
+
 // A list entry holds the partner index in bits 0-30 and, in bit 31, whether the
 // owner comes first in canonical pair order (lower caller index).
 constexpr uint32_t kFirstBit = 0x80000000u;

@@ -71,6 +71,17 @@ struct sedi_handle {
   void* cnn_work = nullptr;
   int64_t cnn_steps = 0;
   bool cnn_set = false;
+  // ensemble (n_beds > 1): one single-bed handle per bed, stepped and averaged by
+  // batched launches over all beds (grid.y = bed)
+  std::vector<sedi_handle*> beds;
+  BedView* ens_views = nullptr;   // device table of the beds' views
+  void* ens_smooth = nullptr;     // smoothing batch tables
+  int* ens_iters = nullptr;       // [B][8] smoother step counts
+  Ctl* ens_ctl = nullptr;         // [B] gathered control blocks
+  EnsLaunch ens{};
+  bool ens_dirty = true;          // a bed's buffers changed: rebuild the table
+  bool ens_fresh = false;         // the batched averaging is newer than the last step
+  bool eps_dev_newer = false;     // (bed handle) device eps newer than the host copy
 };
 
 namespace {
@@ -245,7 +256,7 @@ int check_params(sedi_handle* h, const sedi_params& p) {
   if (p.n_tau < 1 || !(p.cg_rtol > 0) || p.cg_max_iter < 1) return fail(h, SEDI_EINVAL, "n_tau, cg_rtol, cg_max_iter must be positive");
   if (p.precision_form < 0 || p.precision_form > 2) return fail(h, SEDI_EINVAL, "unknown precision_form");
   if (p.nbr_capacity < 1 || p.nbr_capacity > 32) return fail(h, SEDI_EINVAL, "nbr_capacity must be in [1, 32]");
-  if (p.n_beds != 1) return fail(h, SEDI_EINVAL, "n_beds: this build runs one bed per handle");
+  if (p.n_beds < 1 || p.n_beds > kMaxBeds) return fail(h, SEDI_EINVAL, "n_beds must be in [1, %d]", kMaxBeds);
   if (p.substep_variant < -1 || p.substep_variant >= kSubstepVariants)
     return fail(h, SEDI_EINVAL, "substep_variant must be -1 (tuned) or in [0, %d]", kSubstepVariants - 1);
   for (int k = 0; k < 3; ++k) {
@@ -442,6 +453,37 @@ int build_graph(sedi_handle* h, int n, cudaGraphExec_t* out) {
 int need_particles(sedi_handle* h) {
   if (!h) return SEDI_EINVAL;
   if (!h->have_particles) return fail(h, SEDI_ESTATE, "no particles set");
+  return 0;
+}
+
+
+// Ensembles: a per-bed call goes to that bed's single-bed handle.
+#define ENS_FORWARD(CALL)                                                                 \
+  do {                                                                                    \
+    if (!h->beds.empty()) {                                                               \
+      if (bed < 0 || bed >= (int32_t)h->beds.size())                                      \
+        return fail(h, SEDI_EINVAL, "bed %d out of range", bed);                          \
+      sedi_handle* sub = h->beds[bed];                                                    \
+      const auto rc_ = (CALL);                                                            \
+      if (rc_ < 0) h->err = sub->err;                                                     \
+      return rc_;                                                                         \
+    }                                                                                     \
+  } while (0)
+
+// The smoothed solid fraction of an ensemble bed lives on the device only: bring
+// the host copy (used when the mesh fields are uploaded again, and by checkpoints)
+// up to date.
+int refresh_eps_host(sedi_handle* h) {
+  if (!h->eps_dev_newer) return 0;
+  const int64_t C = h->P.C;
+  if (h->form == FORM_FP64) {
+    CK(cudaMemcpy2D(h->eps.data(), 8, (const char*)h->mesh.ufe + 24, 32, 8, C, cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<float> e(C);
+    CK(cudaMemcpy2D(e.data(), 4, (const char*)h->mesh.ufe + 12, 16, 4, C, cudaMemcpyDeviceToHost));
+    for (int64_t c = 0; c < C; ++c) h->eps[c] = e[c];
+  }
+  h->eps_dev_newer = false;
   return 0;
 }
 
@@ -657,6 +699,19 @@ int sedi_create(const sedi_params* p, sedi_handle** out) {
     sedi_destroy(h);
     return rc;
   }
+  if (p->n_beds > 1) {
+    // one single-bed handle per bed, all on this handle's stream
+    sedi_params q = *p;
+    q.n_beds = 1;
+    h->beds.assign(p->n_beds, nullptr);
+    for (int b = 0; b < p->n_beds; ++b) {
+      if ((rc = sedi_create(&q, &h->beds[b]))) {
+        sedi_destroy(h);
+        return rc;
+      }
+      h->beds[b]->stream = h->stream;
+    }
+  }
   *out = h;
   return 0;
 }
@@ -665,6 +720,14 @@ void sedi_destroy(sedi_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   clear_graphs(h);
+  for (sedi_handle* b : h->beds) {
+    if (!b) continue;
+    b->stream = b->own;  // the shared stream belongs to the ensemble handle
+    sedi_destroy(b);
+  }
+  h->beds.clear();
+  for (void* p : {(void*)h->ens_views, h->ens_smooth, (void*)h->ens_iters, (void*)h->ens_ctl})
+    if (p) cudaFree(p);
   for (cudaEvent_t e : h->avg_ev) cudaEventDestroy(e);
   free_list(h->part_allocs);
   free_list(h->mesh_allocs);
@@ -682,6 +745,35 @@ int sedi_set_stream(sedi_handle* h, void* s) {
   if (!h) return SEDI_EINVAL;
   if ((cudaStream_t)s != h->stream) clear_graphs(h);
   h->stream = (cudaStream_t)s;
+  for (sedi_handle* b : h->beds) sedi_set_stream(b, s);
+  return 0;
+}
+
+int sedi_set_bed(sedi_handle* h, int32_t bed, const double lo[3], const double hi[3],
+                 const int32_t ncell[3]) {
+  if (!h || !lo || !hi || !ncell) return SEDI_EINVAL;
+  h->err.clear();
+  if (h->beds.empty())
+    return fail(h, SEDI_EINVAL, "sedi_set_bed needs n_beds > 1 (one bed takes its box from the parameters)");
+  if (bed < 0 || bed >= (int32_t)h->beds.size()) return fail(h, SEDI_EINVAL, "bed %d out of range", bed);
+  sedi_params q = h->beds[bed]->prm;
+  for (int a = 0; a < 3; ++a) {
+    q.lo[a] = lo[a];
+    q.hi[a] = hi[a];
+    q.ncell[a] = ncell[a];
+  }
+  sedi_handle* nb = nullptr;
+  const int rc = sedi_create(&q, &nb);
+  if (rc) return fail(h, rc, "bed %d: invalid box or mesh", bed);
+  nb->stream = h->stream;
+  sedi_handle* old = h->beds[bed];
+  old->stream = old->own;
+  cudaStreamSynchronize(h->stream);
+  sedi_destroy(old);
+  h->beds[bed] = nb;
+  h->ens_dirty = true;
+  h->ens_fresh = false;
+  clear_graphs(h);
   return 0;
 }
 
@@ -690,6 +782,12 @@ int sedi_set_particles(sedi_handle* h, int32_t bed, int64_t n, const int64_t* id
                        int32_t mem) {
   if (!h) return SEDI_EINVAL;
   h->err.clear();
+  if (!h->beds.empty()) {
+    h->ens_dirty = true;
+    h->ens_fresh = false;
+    clear_graphs(h);
+  }
+  ENS_FORWARD(sedi_set_particles(sub, 0, n, id, x, v, omega, d, rho, mem));
   if (bed != 0) return fail(h, SEDI_EINVAL, "bed %d out of range", bed);
   if (n <= 0 || n > ((int64_t)1 << 31) - 1) return fail(h, SEDI_EINVAL, "n must be in [1, 2^31)");
   if (!x || !d || !rho) return fail(h, SEDI_EINVAL, "x, d and rho are required");
@@ -758,7 +856,9 @@ int sedi_set_fluid(sedi_handle* h, int32_t bed, const int32_t ncell[3], const do
                    const double* grad_p, const double* DUDt, int32_t mem) {
   if (!h) return SEDI_EINVAL;
   h->err.clear();
+  ENS_FORWARD(sedi_set_fluid(sub, 0, ncell, U, grad_p, DUDt, mem));
   if (bed != 0) return fail(h, SEDI_EINVAL, "bed %d out of range", bed);
+  if (int rc0 = refresh_eps_host(h)) return rc0;
   if (!ncell || ncell[0] != h->prm.ncell[0] || ncell[1] != h->prm.ncell[1] || ncell[2] != h->prm.ncell[2])
     return fail(h, SEDI_EINVAL, "ncell must equal params.ncell");
   const int64_t C = h->P.C;
@@ -785,7 +885,9 @@ int sedi_set_fluid(sedi_handle* h, int32_t bed, const int32_t ncell[3], const do
 int sedi_set_eps(sedi_handle* h, int32_t bed, const double* eps, int32_t mem) {
   if (!h || !eps) return SEDI_EINVAL;
   h->err.clear();
+  ENS_FORWARD(sedi_set_eps(sub, 0, eps, mem));
   if (bed != 0) return fail(h, SEDI_EINVAL, "bed %d out of range", bed);
+  h->eps_dev_newer = false;
   const int64_t C = h->P.C;
   if (mem == SEDI_MEM_DEVICE) {
     CK(cudaMemcpy(h->eps.data(), eps, 8 * C, cudaMemcpyDeviceToHost));
@@ -795,11 +897,16 @@ int sedi_set_eps(sedi_handle* h, int32_t bed, const double* eps, int32_t mem) {
   return upload_mesh(h);
 }
 
+static int ens_step(sedi_handle* h, int n);
+static int ens_status(sedi_handle* h);
+
 int sedi_step(sedi_handle* h, int32_t n) {
-  int rc = need_particles(h);
-  if (rc) return rc;
+  if (!h) return SEDI_EINVAL;
   h->err.clear();
   if (n < 0) return fail(h, SEDI_EINVAL, "n_substeps must be >= 0");
+  if (!h->beds.empty()) return n == 0 ? 0 : ens_step(h, n);
+  int rc = need_particles(h);
+  if (rc) return rc;
   if (n == 0) return 0;
   if ((rc = autotune(h))) return rc;
   if (h->prm.profile) harvest(h);
@@ -853,6 +960,7 @@ int sedi_step(sedi_handle* h, int32_t n) {
 
 int sedi_sync(sedi_handle* h) {
   if (!h) return SEDI_EINVAL;
+  if (!h->beds.empty()) return ens_status(h);
   return sync_status(h);
 }
 
@@ -938,10 +1046,266 @@ static int smooth_status(sedi_handle* h, int nf) {
   return 0;
 }
 
+
+// ---------------------------------------------------------------- ensembles
+// n_beds > 1: every bed is a single-bed handle (its own particles, box, mesh and
+// control block); a step and an averaging are batched launches over all beds, the
+// beds' views gathered in one device table.
+
+static int ens_finalize(sedi_handle* h) {
+  for (size_t b = 0; b < h->beds.size(); ++b)
+    if (!h->beds[b]->have_particles) return fail(h, SEDI_ESTATE, "bed %zu has no particles", b);
+  if (!h->ens_dirty) return 0;
+  const int B = (int)h->beds.size();
+  std::vector<BedView> v(B);
+  int64_t max_n = 0, max_bins = 0, max_c = 0, U = 0;
+  for (int b = 0; b < B; ++b) {
+    sedi_handle* sb = h->beds[b];
+    v[b].st = sb->st;
+    v[b].mesh = sb->mesh;
+    v[b].P = sb->P;
+    v[b].qfix = sb->qfix;
+    v[b].phi = sb->phi;
+    max_n = std::max(max_n, sb->N);
+    max_bins = std::max(max_bins, sb->P.nbins);
+    max_c = std::max(max_c, sb->P.C);
+    U += smooth_units(sb->P.C);
+  }
+  for (void* p : {(void*)h->ens_views, h->ens_smooth, (void*)h->ens_iters, (void*)h->ens_ctl})
+    if (p) cudaFree(p);
+  h->ens_views = nullptr;
+  h->ens_smooth = nullptr;
+  h->ens_iters = nullptr;
+  h->ens_ctl = nullptr;
+  CK(cudaMalloc((void**)&h->ens_views, sizeof(BedView) * B));
+  CK(cudaMalloc(&h->ens_smooth, smooth_batch_bytes(B, U)));
+  CK(cudaMalloc((void**)&h->ens_iters, sizeof(int) * 8 * B));
+  CK(cudaMalloc((void**)&h->ens_ctl, sizeof(Ctl) * B));
+  CK(cudaMemcpy(h->ens_views, v.data(), sizeof(BedView) * B, cudaMemcpyHostToDevice));
+  h->ens.views = h->ens_views;
+  h->ens.B = B;
+  h->ens.max_n = max_n;
+  h->ens.max_bins = max_bins;
+  h->ens.max_cells = max_c;
+  h->ens.ectl = h->st.ctl;
+  clear_graphs(h);
+  h->ens_dirty = false;
+  return 0;
+}
+
+// Synchronise; read every bed's control block; map device-side errors.
+static int ens_status(sedi_handle* h) {
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  if (h->ens_dirty) return 0;
+  const int B = h->ens.B;
+  std::vector<Ctl> c(B);
+  launch_ctl_gather_ens(h->ens, h->ens_ctl, h->stream);
+  CK(cudaMemcpyAsync(c.data(), h->ens_ctl, sizeof(Ctl) * B, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int b = 0; b < B; ++b) {
+    sedi_handle* sb = h->beds[b];
+    sb->stats.rebuilds = c[b].rebuilds;
+    sb->stats.max_neighbors = c[b].max_nn;
+    if (c[b].error == SEDI_EOVERFLOW)
+      return fail(h, SEDI_EOVERFLOW, "bed %d: a particle has %d listed neighbours > nbr_capacity %d", b,
+                  c[b].overflow_nn, sb->P.cap);
+    if (c[b].error == SEDI_ENONFINITE) return fail(h, SEDI_ENONFINITE, "bed %d: non-finite force or state", b);
+    if (c[b].error) return fail(h, c[b].error, "bed %d: device error %d", b, c[b].error);
+  }
+  return 0;
+}
+
+static int build_graph_ens(sedi_handle* h, int n, cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &g, &deps, nullptr, &nd));
+  // one IF node per substep: rebuild the beds that need it (any bed -> condition)
+  std::vector<cudaGraphConditionalHandle> ch(n);
+  for (int s = 0; s < n; ++s) CK(cudaGraphConditionalHandleCreate(&ch[s], g, 0, cudaGraphCondAssignDefault));
+  launch_check_ens(h->ens, (unsigned long long)ch[0], 1, h->stream);
+  for (int s = 0; s < n; ++s) {
+    CK(cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &g, &deps, nullptr, &nd));
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+    std::memset(raw, 0, sizeof(raw));
+    cudaGraphNodeParams* cp = reinterpret_cast<cudaGraphNodeParams*>(raw);
+    cp->type = cudaGraphNodeTypeConditional;
+    cp->conditional.handle = ch[s];
+    cp->conditional.type = cudaGraphCondTypeIf;
+    cp->conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, cp));
+    CK(cudaStreamUpdateCaptureDependencies(h->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t body = cp->conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(h->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    launch_rebuild_ens(h->form, h->ens, s, h->side);
+    CK(cudaStreamEndCapture(h->side, &body));
+    const bool more = s + 1 < n;
+    launch_substep_ens(h->form, h->ens, s, more ? (unsigned long long)ch[s + 1] : 0ull, more ? 1 : 0,
+                       h->stream);
+  }
+  launch_advance_ens(h->ens, n, h->stream);
+  CK(cudaStreamEndCapture(h->stream, &graph));
+  cudaError_t e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(h, SEDI_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  return 0;
+}
+
+static int ens_step(sedi_handle* h, int n) {
+  int rc = ens_finalize(h);
+  if (rc) return rc;
+  if (h->prm.profile) {
+    harvest(h);
+    if (h->avg_ev.empty())
+      for (int k = 0; k < 5; ++k) h->avg_ev.push_back(new_event());
+    CK(cudaEventRecord(h->avg_ev[3], h->stream));
+  }
+  if (h->prm.use_graphs && h->stream != nullptr) {
+    auto it = h->graphs.find(n);
+    cudaGraphExec_t ex;
+    if (it == h->graphs.end()) {
+      if ((rc = build_graph_ens(h, n, &ex))) return rc;
+      h->graphs[n] = ex;
+    } else {
+      ex = it->second;
+    }
+    CK(cudaGraphLaunch(ex, h->stream));
+  } else {
+    launch_check_ens(h->ens, 0ull, 0, h->stream);
+    for (int s = 0; s < n; ++s) {
+      launch_rebuild_ens(h->form, h->ens, s, h->stream);
+      launch_substep_ens(h->form, h->ens, s, 0ull, 0, h->stream);
+    }
+    launch_advance_ens(h->ens, n, h->stream);
+  }
+  if (h->prm.profile) {
+    CK(cudaEventRecord(h->avg_ev[4], h->stream));
+    h->pending.push_back({1, {h->avg_ev[3], h->avg_ev[4]}});
+  }
+  CK(cudaGetLastError());
+  h->stats.substeps += n;
+  for (sedi_handle* b : h->beds) b->stats.substeps += n;
+  h->ens_fresh = false;
+  return 0;
+}
+
+// Deposition and smoothing of every bed in batched launches; the smoothed eps
+// feeds each bed's drag.  Outputs stay on the device.
+static int ens_average(sedi_handle* h) {
+  int rc = ens_finalize(h);
+  if (rc) return rc;
+  const int B = h->ens.B;
+  if (h->prm.profile) {
+    harvest(h);
+    if (h->avg_ev.empty())
+      for (int k = 0; k < 5; ++k) h->avg_ev.push_back(new_event());
+    CK(cudaEventRecord(h->avg_ev[0], h->stream));
+  }
+  launch_deposit_ens(h->form, h->ens, h->stream);
+  if (h->prm.profile) CK(cudaEventRecord(h->avg_ev[1], h->stream));
+  std::vector<SmoothMesh> m(B);
+  for (int b = 0; b < B; ++b) {
+    sedi_handle* sb = h->beds[b];
+    SmoothMesh& x = m[b];
+    x.phi = sb->phi;
+    x.guess = nullptr;
+    x.work = sb->work;
+    x.iters = h->ens_iters + 8 * b;
+    x.C = sb->P.C;
+    x.nf = 7;
+    for (int a = 0; a < 3; ++a) {
+      x.nc[a] = sb->P.nc[a];
+      x.per[a] = sb->P.periodic[a];
+      x.coef[a] = sb->coef[a];
+    }
+  }
+  CK(cudaMemsetAsync(h->ens_iters, 0, sizeof(int) * 8 * B, h->stream));
+  const double rtol = h->form == FORM_PLAIN ? std::max(h->prm.cg_rtol, 2e-6) : h->prm.cg_rtol;
+  if (launch_smooth_batch(h->form, m.data(), B, 7, h->ens_smooth, rtol, h->prm.cg_max_iter,
+                          h->prm.n_tau, h->st.ctl, 1 << 30, h->stream))
+    return fail(h, SEDI_ECUDA, "cooperative launch of the batched smoother failed: %s",
+                cudaGetErrorString(cudaGetLastError()));
+  launch_eps_out_ens(h->form, h->ens, h->stream);
+  if (h->prm.profile) {
+    CK(cudaEventRecord(h->avg_ev[2], h->stream));
+    h->pending.push_back({2, {h->avg_ev[0], h->avg_ev[1]}});
+    h->pending.push_back({3, {h->avg_ev[1], h->avg_ev[2]}});
+  }
+  std::vector<int> it(8 * B);
+  CK(cudaMemcpyAsync(it.data(), h->ens_iters, sizeof(int) * 8 * B, cudaMemcpyDeviceToHost, h->stream));
+  if ((rc = ens_status(h))) return rc;
+  Ctl ec;
+  CK(cudaMemcpy(&ec, h->st.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  std::vector<Ctl> c(B);
+  CK(cudaMemcpy(c.data(), h->ens_ctl, sizeof(Ctl) * B, cudaMemcpyDeviceToHost));
+  int range_bed = -1;
+  for (int b = 0; b < B; ++b) {
+    sedi_handle* sb = h->beds[b];
+    int64_t sum = 0;
+    for (int f = 0; f < 7; ++f) sum += it[8 * b + f];
+    sb->stats.cg_iterations += sum;
+    h->stats.cg_iterations += sum;
+    sb->stats.averages += 1;
+    sb->eps_dev_newer = true;
+    if (c[b].deposit_range) {
+      range_bed = b;
+      int z = 0;
+      cudaMemcpy((char*)sb->st.ctl + offsetof(Ctl, deposit_range), &z, 4, cudaMemcpyHostToDevice);
+    }
+  }
+  h->stats.averages += 1;
+  if (ec.cg_status) {
+    int z = 0;
+    cudaMemcpy((char*)h->st.ctl + offsetof(Ctl, cg_status), &z, 4, cudaMemcpyHostToDevice);
+  }
+  if (range_bed >= 0) return fail(h, SEDI_ERANGE, "bed %d: a deposited value does not fit the fixed-point format", range_bed);
+  if (ec.cg_status == SEDI_ETIMEOUT) return fail(h, SEDI_ETIMEOUT, "smoother grid barrier timed out");
+  if (ec.cg_status == SEDI_EDIVERGED) return fail(h, SEDI_EDIVERGED, "smoothing reached cg_max_iter");
+  h->ens_fresh = true;
+  return 0;
+}
+
+// Outputs of the last averaging of a single-bed handle (smoothing word -> FP64).
+static int average_outputs(sedi_handle* h, double* eps, double* Us, double* F, int32_t mem) {
+  const int64_t C = h->P.C;
+  double* de = h->dstage;
+  double* du = h->dstage + C;
+  double* dF = h->dstage + 4 * C;
+  int rc;
+  launch_average_out(h->form, h->phi, h->P, h->mesh.ufe, de, du, dF, h->stream);
+  if (eps && (rc = copy_out(h, eps, de, 8 * C, mem))) return rc;
+  if (Us && (rc = copy_out(h, Us, du, 24 * C, mem))) return rc;
+  if (F && (rc = copy_out(h, F, dF, 24 * C, mem))) return rc;
+  if ((rc = sync_status(h))) return rc;
+  // keep the host copy of the drag's solid fraction in step (checkpoints)
+  CK(cudaMemcpy(h->eps.data(), de, 8 * C, cudaMemcpyDeviceToHost));
+  h->eps_dev_newer = false;
+  return 0;
+}
+
 int sedi_average(sedi_handle* h, int32_t bed, double* eps, double* Us, double* F, int32_t mem) {
+  if (!h) return SEDI_EINVAL;
+  h->err.clear();
+  if (!h->beds.empty()) {
+    if (bed == SEDI_ALL_BEDS) {
+      if (eps || Us || F) return fail(h, SEDI_EINVAL, "SEDI_ALL_BEDS averages in place: outputs must be NULL");
+      return ens_average(h);
+    }
+    if (bed < 0 || bed >= (int32_t)h->beds.size()) return fail(h, SEDI_EINVAL, "bed %d out of range", bed);
+    int rc = h->ens_fresh ? 0 : ens_average(h);
+    if (rc) return rc;
+    sedi_handle* sb = h->beds[bed];
+    rc = average_outputs(sb, eps, Us, F, mem);
+    if (rc) h->err = sb->err;
+    return rc;
+  }
   int rc = need_particles(h);
   if (rc) return rc;
-  h->err.clear();
   if (bed != 0) return fail(h, SEDI_EINVAL, "bed %d out of range", bed);
   const int64_t C = h->P.C;
   if (h->prm.profile) {
@@ -978,6 +1342,8 @@ int sedi_average(sedi_handle* h, int32_t bed, double* eps, double* Us, double* F
 }
 
 int sedi_deposit(sedi_handle* h, int32_t bed, int64_t* q, int32_t mem) {
+  if (!h) return SEDI_EINVAL;
+  ENS_FORWARD(sedi_deposit(sub, 0, q, mem));
   int rc = need_particles(h);
   if (rc) return rc;
   h->err.clear();
@@ -1016,6 +1382,8 @@ int sedi_deposit(sedi_handle* h, int32_t bed, int64_t* q, int32_t mem) {
 int sedi_smooth(sedi_handle* h, int32_t bed, int32_t nf, const double* in, double* out,
                 const double* guess, int32_t* iters, int32_t mem) {
   if (!h) return SEDI_EINVAL;
+  ENS_FORWARD(sedi_smooth(sub, 0, nf, in, out, guess, iters, mem));
+  if (!h) return SEDI_EINVAL;
   h->err.clear();
   if (bed != 0 || nf < 1 || nf > 8 || !in || !out) return fail(h, SEDI_EINVAL, "bad smoothing arguments (1 <= n_fields <= 8)");
   const int64_t C = h->P.C;
@@ -1045,6 +1413,8 @@ int sedi_smooth(sedi_handle* h, int32_t bed, int32_t nf, const double* in, doubl
 
 int sedi_get_particles(sedi_handle* h, int32_t bed, double* x, double* v, double* w, double* a,
                        int32_t mem) {
+  if (!h) return SEDI_EINVAL;
+  ENS_FORWARD(sedi_get_particles(sub, 0, x, v, w, a, mem));
   int rc = need_particles(h);
   if (rc) return rc;
   h->err.clear();
@@ -1061,6 +1431,8 @@ int sedi_get_particles(sedi_handle* h, int32_t bed, double* x, double* v, double
 
 int sedi_compute_forces(sedi_handle* h, int32_t bed, double* fc, double* fl, double* ff,
                         double* tq, int32_t mem) {
+  if (!h) return SEDI_EINVAL;
+  ENS_FORWARD(sedi_compute_forces(sub, 0, fc, fl, ff, tq, mem));
   int rc = need_particles(h);
   if (rc) return rc;
   h->err.clear();
@@ -1094,6 +1466,8 @@ int sedi_compute_forces(sedi_handle* h, int32_t bed, double* fc, double* fl, dou
 }
 
 int64_t sedi_get_neighbors(sedi_handle* h, int32_t bed, int64_t* offsets, int64_t* ids, int64_t cap) {
+  if (!h) return SEDI_EINVAL;
+  ENS_FORWARD(sedi_get_neighbors(sub, 0, offsets, ids, cap));
   int rc = need_particles(h);
   if (rc) return rc;
   h->err.clear();
@@ -1133,6 +1507,8 @@ int64_t sedi_get_neighbors(sedi_handle* h, int32_t bed, int64_t* offsets, int64_
 }
 
 int64_t sedi_get_contacts(sedi_handle* h, int32_t bed, int64_t cap, int64_t* ij, double* xi) {
+  if (!h) return SEDI_EINVAL;
+  ENS_FORWARD(sedi_get_contacts(sub, 0, cap, ij, xi));
   int rc = need_particles(h);
   if (rc) return rc;
   h->err.clear();
@@ -1237,13 +1613,10 @@ int state_io(sedi_handle* h, FILE* f, bool save) {
 }
 }  // namespace
 
-int sedi_save_state(sedi_handle* h, const char* path) {
+static int save_to(sedi_handle* h, FILE* f) {
   int rc = need_particles(h);
   if (rc) return rc;
-  h->err.clear();
-  if ((rc = sync_status(h))) return rc;
-  FILE* f = std::fopen(path, "wb");
-  if (!f) return fail(h, SEDI_EIO, "cannot open %s", path);
+  if ((rc = sync_status(h)) || (rc = refresh_eps_host(h))) return rc;
   CkHeader hd{};
   std::memcpy(hd.magic, "SEDICK01", 8);
   hd.version = 1;
@@ -1265,15 +1638,10 @@ int sedi_save_state(sedi_handle* h, const char* path) {
   int gpd = h->gp_default ? 1 : 0;
   if (!rc) rc = ck_write(f, &gpd, 4) ? fail(h, SEDI_EIO, "write failed") : 0;
   if (!rc) rc = state_io(h, f, true);
-  std::fclose(f);
   return rc;
 }
 
-int sedi_load_state(sedi_handle* h, const char* path) {
-  if (!h) return SEDI_EINVAL;
-  h->err.clear();
-  FILE* f = std::fopen(path, "rb");
-  if (!f) return fail(h, SEDI_EIO, "cannot open %s", path);
+static int load_from(sedi_handle* h, FILE* f) {
   CkHeader hd{};
   int rc = 0;
   if (ck_read(f, &hd, sizeof(hd)) || std::memcmp(hd.magic, "SEDICK01", 8) != 0) rc = fail(h, SEDI_EIO, "not a checkpoint of this library");
@@ -1299,6 +1667,7 @@ int sedi_load_state(sedi_handle* h, const char* path) {
     rc = fail(h, SEDI_EIO, "read failed");
   if (!rc) {
     h->gp_default = gpd != 0;
+    h->eps_dev_newer = false;
     double rmax = 0;
     for (double di : d) rmax = std::max(rmax, 0.5 * di);
     h->P.cap = hd.cap;
@@ -1315,11 +1684,64 @@ int sedi_load_state(sedi_handle* h, const char* path) {
     cudaMemcpy(h->st.ctl, &zero, sizeof(Ctl), cudaMemcpyHostToDevice);
     rc = state_io(h, f, false);
   }
-  std::fclose(f);
   if (rc) return rc;
   h->stats = hd.stats;
   h->have_particles = true;
   return 0;
+}
+
+// Ensemble checkpoints: a header with the bed count, then every bed's checkpoint.
+struct EnsHeader {
+  char magic[8];
+  int32_t beds, pad;
+  sedi_stats stats;
+};
+
+int sedi_save_state(sedi_handle* h, const char* path) {
+  if (!h || !path) return SEDI_EINVAL;
+  h->err.clear();
+  int rc = h->beds.empty() ? need_particles(h) : ens_status(h);
+  if (rc) return rc;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(h, SEDI_EIO, "cannot open %s", path);
+  if (h->beds.empty()) {
+    rc = save_to(h, f);
+  } else {
+    EnsHeader eh{};
+    std::memcpy(eh.magic, "SEDIEN01", 8);
+    eh.beds = (int32_t)h->beds.size();
+    eh.stats = h->stats;
+    rc = ck_write(f, &eh, sizeof(eh)) ? fail(h, SEDI_EIO, "write failed") : 0;
+    for (size_t b = 0; !rc && b < h->beds.size(); ++b)
+      if ((rc = save_to(h->beds[b], f))) h->err = h->beds[b]->err;
+  }
+  std::fclose(f);
+  return rc;
+}
+
+int sedi_load_state(sedi_handle* h, const char* path) {
+  if (!h || !path) return SEDI_EINVAL;
+  h->err.clear();
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(h, SEDI_EIO, "cannot open %s", path);
+  int rc = 0;
+  if (h->beds.empty()) {
+    rc = load_from(h, f);
+  } else {
+    EnsHeader eh{};
+    if (ck_read(f, &eh, sizeof(eh)) || std::memcmp(eh.magic, "SEDIEN01", 8) != 0)
+      rc = fail(h, SEDI_EIO, "not an ensemble checkpoint of this library");
+    else if (eh.beds != (int32_t)h->beds.size())
+      rc = fail(h, SEDI_EINVAL, "checkpoint has %d beds, this handle %zu", eh.beds, h->beds.size());
+    for (size_t b = 0; !rc && b < h->beds.size(); ++b)
+      if ((rc = load_from(h->beds[b], f))) h->err = h->beds[b]->err;
+    if (!rc) h->stats = eh.stats;
+    h->ens_dirty = true;
+    h->ens_fresh = false;
+    clear_graphs(h);
+  }
+  std::fclose(f);
+  return rc;
 }
 
 int sedi_cnn_set_params(sedi_handle* h, const double* params, int64_t n) {
@@ -1453,6 +1875,23 @@ int sedi_get_timings(sedi_handle* h, double* ms, int32_t n) {
 
 int sedi_get_stats(sedi_handle* h, sedi_stats* out) {
   if (!h || !out) return SEDI_EINVAL;
+  if (!h->beds.empty()) {
+    // ensemble: substeps, averages and smoother steps of the whole ensemble, list
+    // rebuilds summed and the longest list over the beds
+    const int rc = ens_status(h);
+    sedi_stats st = h->stats;
+    st.rebuilds = 0;
+    st.max_neighbors = 0;
+    for (sedi_handle* b : h->beds) {
+      st.rebuilds += b->stats.rebuilds;
+      st.max_neighbors = std::max(st.max_neighbors, b->stats.max_neighbors);
+    }
+    st.nbr_capacity = h->P.cap;
+    st.substep_variant = SUBSTEP_B128;
+    st.substep_block = 128;
+    *out = st;
+    return rc;
+  }
   int rc = h->have_particles ? sync_status(h) : 0;
   h->stats.nbr_capacity = h->P.cap;
   const bool tuned = h->prm.substep_variant >= 0 || h->form == FORM_FP64 || !h->tuned_key.empty();

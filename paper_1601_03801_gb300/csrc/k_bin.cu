@@ -43,7 +43,7 @@ __global__ void k_check(Ctl* ctl, float thresh2, cudaGraphConditionalHandle h, i
 
 __global__ void k_force_need(Ctl* ctl) { ctl->need_rebuild = 1; }
 
-__global__ void k_zero_bins(DevState st, int64_t nbins, bool force) {
+__device__ __forceinline__ void zero_bins_body(const DevState& st, int64_t nbins, bool force) {
   if (skip(st.ctl, force)) return;
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nbins;
        b += (int64_t)gridDim.x * blockDim.x) {
@@ -68,7 +68,8 @@ __device__ __forceinline__ int64_t bin_index(const Quad<S>& p, const DevParams& 
 }
 
 template <int FORM>
-__global__ void k_bin_count(DevState st, DevParams P, int sub_off, bool force) {
+__device__ __forceinline__ void bin_count_body(const DevState& st, const DevParams& P, int sub_off,
+                                               bool force) {
   if (skip(st.ctl, force)) return;
   using S = typename Traits<FORM>::S;
   const int sb = (st.ctl->st + sub_off) & 1;
@@ -113,7 +114,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int* total) {
   return r;
 }
 
-__global__ void k_scan1(DevState st, int64_t nbins, bool force) {
+__device__ __forceinline__ void scan1_body(const DevState& st, int64_t nbins, bool force) {
   if (skip(st.ctl, force)) return;
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
   int v[kScanItems];
@@ -135,7 +136,7 @@ __global__ void k_scan1(DevState st, int64_t nbins, bool force) {
   if (threadIdx.x == 0) st.scan_blk[blockIdx.x] = total;
 }
 
-__global__ void k_scan2(DevState st, int64_t nblk, int64_t nbins, bool force) {
+__device__ __forceinline__ void scan2_body(const DevState& st, int64_t nblk, int64_t nbins, bool force) {
   if (skip(st.ctl, force)) return;
   __shared__ int carry;
   if (threadIdx.x == 0) carry = 0;
@@ -153,7 +154,7 @@ __global__ void k_scan2(DevState st, int64_t nblk, int64_t nbins, bool force) {
   if (threadIdx.x == 0) st.bin_start[nbins] = carry;
 }
 
-__global__ void k_scan3(DevState st, int64_t nbins, bool force) {
+__device__ __forceinline__ void scan3_body(const DevState& st, int64_t nbins, bool force) {
   if (skip(st.ctl, force)) return;
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
   const int add = st.scan_blk[blockIdx.x];
@@ -163,7 +164,7 @@ __global__ void k_scan3(DevState st, int64_t nbins, bool force) {
   }
 }
 
-__global__ void k_scatter(DevState st, bool force) {
+__device__ __forceinline__ void scatter_body(const DevState& st, bool force) {
   if (skip(st.ctl, force)) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < st.N;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -174,7 +175,7 @@ __global__ void k_scatter(DevState st, bool force) {
 }
 
 // Insertion sort of each bin's entries by caller index (bins hold a few particles).
-__global__ void k_sort_bins(DevState st, int64_t nbins, bool force) {
+__device__ __forceinline__ void sort_bins_body(const DevState& st, int64_t nbins, bool force) {
   if (skip(st.ctl, force)) return;
   const int32_t* uid = st.uid[st.ctl->pb];
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nbins;
@@ -196,7 +197,7 @@ __global__ void k_sort_bins(DevState st, int64_t nbins, bool force) {
 }
 
 template <int FORM>
-__global__ void k_gather(DevState st, int sub_off, bool force) {
+__device__ __forceinline__ void gather_body(const DevState& st, int sub_off, bool force) {
   if (skip(st.ctl, force)) return;
   using S = typename Traits<FORM>::S;
   using F = typename Traits<FORM>::F;
@@ -251,7 +252,8 @@ __device__ __forceinline__ bool listed_exact(const double xi[3], const double xj
 }
 
 template <int FORM>
-__global__ void k_build(DevState st, DevParams P, int sub_off, bool force) {
+__device__ __forceinline__ void build_body(const DevState& st, const DevParams& P, int sub_off,
+                                           bool force) {
   if (skip(st.ctl, force)) return;
   using S = typename Traits<FORM>::S;
   using NS = Num<S>;
@@ -328,7 +330,7 @@ __global__ void k_build(DevState st, DevParams P, int sub_off, bool force) {
 }
 
 template <int FORM>
-__global__ void k_remap(DevState st, DevParams P, bool force) {
+__device__ __forceinline__ void remap_body(const DevState& st, const DevParams& P, bool force) {
   if (skip(st.ctl, force)) return;
   using S = typename Traits<FORM>::S;
   const int pb = st.ctl->pb, qb = pb ^ 1;
@@ -360,7 +362,7 @@ __global__ void k_remap(DevState st, DevParams P, bool force) {
   }
 }
 
-__global__ void k_flip(DevState st, bool force) {
+__device__ __forceinline__ void flip_body(const DevState& st, bool force) {
   if (skip(st.ctl, force)) return;
   Ctl* c = st.ctl;
   c->st ^= 1;
@@ -372,6 +374,127 @@ __global__ void k_flip(DevState st, bool force) {
 }
 
 __global__ void k_advance(Ctl* ctl, int n) { ctl->st = (ctl->st + n) & 1; }
+
+// ---------------------------------------------------------------- kernels
+// Single-bed kernels take the bed's views by value; the _e kernels of an ensemble
+// take blockIdx.y as the bed and return at once for a bed without a rebuild.
+
+__global__ void k_zero_bins(DevState st, int64_t nbins, bool force) { zero_bins_body(st, nbins, force); }
+template <int FORM>
+__global__ void k_bin_count(DevState st, DevParams P, int sub_off, bool force) {
+  bin_count_body<FORM>(st, P, sub_off, force);
+}
+__global__ void k_scan1(DevState st, int64_t nbins, bool force) { scan1_body(st, nbins, force); }
+__global__ void k_scan2(DevState st, int64_t nblk, int64_t nbins, bool force) {
+  scan2_body(st, nblk, nbins, force);
+}
+__global__ void k_scan3(DevState st, int64_t nbins, bool force) { scan3_body(st, nbins, force); }
+__global__ void k_scatter(DevState st, bool force) { scatter_body(st, force); }
+__global__ void k_sort_bins(DevState st, int64_t nbins, bool force) { sort_bins_body(st, nbins, force); }
+template <int FORM>
+__global__ void k_gather(DevState st, int sub_off, bool force) { gather_body<FORM>(st, sub_off, force); }
+template <int FORM>
+__global__ void k_build(DevState st, DevParams P, int sub_off, bool force) {
+  build_body<FORM>(st, P, sub_off, force);
+}
+template <int FORM>
+__global__ void k_remap(DevState st, DevParams P, bool force) { remap_body<FORM>(st, P, force); }
+__global__ void k_flip(DevState st, bool force) { flip_body(st, force); }
+
+// true when this block's bed has no rebuild pending (the whole block returns)
+__device__ __forceinline__ bool ens_idle(const BedView* v) {
+  return !v[blockIdx.y].st.ctl->need_rebuild;
+}
+
+__global__ void k_zero_bins_e(const BedView* v) {
+  if (ens_idle(v)) return;
+  const BedView& b = bed_view(v);
+  zero_bins_body(b.st, b.P.nbins, false);
+}
+template <int FORM>
+__global__ void k_bin_count_e(const BedView* v, int sub_off) {
+  if (ens_idle(v)) return;
+  const BedView& b = bed_view(v);
+  bin_count_body<FORM>(b.st, b.P, sub_off, false);
+}
+__global__ void k_scan1_e(const BedView* v) {
+  if (ens_idle(v)) return;
+  const BedView& b = bed_view(v);
+  if ((int64_t)blockIdx.x * kScanTile >= b.P.nbins) return;
+  scan1_body(b.st, b.P.nbins, false);
+}
+__global__ void k_scan2_e(const BedView* v) {
+  if (ens_idle(v)) return;
+  const BedView& b = bed_view(v);
+  scan2_body(b.st, (b.P.nbins + kScanTile - 1) / kScanTile, b.P.nbins, false);
+}
+__global__ void k_scan3_e(const BedView* v) {
+  if (ens_idle(v)) return;
+  const BedView& b = bed_view(v);
+  if ((int64_t)blockIdx.x * kScanTile >= b.P.nbins) return;
+  scan3_body(b.st, b.P.nbins, false);
+}
+__global__ void k_scatter_e(const BedView* v) {
+  if (ens_idle(v)) return;
+  const BedView& b = bed_view(v);
+  scatter_body(b.st, false);
+}
+__global__ void k_sort_bins_e(const BedView* v) {
+  if (ens_idle(v)) return;
+  const BedView& b = bed_view(v);
+  sort_bins_body(b.st, b.P.nbins, false);
+}
+template <int FORM>
+__global__ void k_gather_e(const BedView* v, int sub_off) {
+  if (ens_idle(v)) return;
+  const BedView& b = bed_view(v);
+  gather_body<FORM>(b.st, sub_off, false);
+}
+template <int FORM>
+__global__ void k_build_e(const BedView* v, int sub_off) {
+  if (ens_idle(v)) return;
+  const BedView& b = bed_view(v);
+  build_body<FORM>(b.st, b.P, sub_off, false);
+}
+template <int FORM>
+__global__ void k_remap_e(const BedView* v) {
+  if (ens_idle(v)) return;
+  const BedView& b = bed_view(v);
+  remap_body<FORM>(b.st, b.P, false);
+}
+// one thread per bed
+__global__ void k_flip_e(const BedView* v, int B) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x)
+    flip_body(v[b].st, false);
+}
+
+// Rebuild flags of every bed from its displacement; graph condition = any.
+__global__ void k_check_e(const BedView* v, int B, cudaGraphConditionalHandle h, int use_cond) {
+  int any = 0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    Ctl* c = v[b].st.ctl;
+    const float hs = v[b].P.half_skin_f;
+    const float m = __uint_as_float(c->disp_max_bits);
+    const int need = (m > hs * hs) ? 1 : 0;
+    c->need_rebuild = need;
+    any |= need;
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+// Copy every bed's control block into one array (one read-back for all beds).
+__global__ void k_ctl_gather_e(const BedView* v, int B, Ctl* out) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) out[b] = *v[b].st.ctl;
+}
+
+__global__ void k_advance_e(const BedView* v, int B, int n) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    Ctl* c = v[b].st.ctl;
+    c->st = (c->st + n) & 1;
+  }
+}
+
 
 inline unsigned grid_for(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
@@ -398,6 +521,31 @@ void rebuild_impl(const DevState& st, const DevParams& P, int sub_off, bool forc
   k_flip<<<1, 1, 0, s>>>(st, false);
 }
 
+template <int FORM>
+void rebuild_ens_impl(const EnsLaunch& e, int sub_off, cudaStream_t s) {
+  const int B = 256;
+  const unsigned gy = (unsigned)e.B;
+  auto per_bed = [](int64_t n, int block) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > 64) g = 64;  // grid-stride loops cover larger beds
+    return (unsigned)g;
+  };
+  const unsigned gn = per_bed(e.max_n, B), gb = per_bed(e.max_bins, B);
+  const unsigned tiles = (unsigned)((e.max_bins + kScanTile - 1) / kScanTile);
+  k_zero_bins_e<<<dim3(gb, gy), B, 0, s>>>(e.views);
+  k_bin_count_e<FORM><<<dim3(gn, gy), B, 0, s>>>(e.views, sub_off);
+  k_scan1_e<<<dim3(tiles, gy), kScanThreads, 0, s>>>(e.views);
+  k_scan2_e<<<dim3(1, gy), 1024, 0, s>>>(e.views);
+  k_scan3_e<<<dim3(tiles, gy), kScanThreads, 0, s>>>(e.views);
+  k_scatter_e<<<dim3(gn, gy), B, 0, s>>>(e.views);
+  k_sort_bins_e<<<dim3(gb, gy), B, 0, s>>>(e.views);
+  k_gather_e<FORM><<<dim3(gn, gy), B, 0, s>>>(e.views, sub_off);
+  k_build_e<FORM><<<dim3(per_bed(e.max_n, 128), gy), 128, 0, s>>>(e.views, sub_off);
+  k_remap_e<FORM><<<dim3(gn, gy), B, 0, s>>>(e.views);
+  k_flip_e<<<(e.B + 255) / 256, 256, 0, s>>>(e.views, e.B);
+}
+
 }  // namespace
 
 void launch_rebuild(int form, const DevState& st, const DevParams& P, int sub_off, bool force,
@@ -418,6 +566,28 @@ void launch_check(const DevState& st, const DevParams& P, unsigned long long con
 void launch_advance_parity(const DevState& st, int n, cudaStream_t s) {
   if (n & 1) k_advance<<<1, 1, 0, s>>>(st.ctl, n);
 }
+
+void launch_check_ens(const EnsLaunch& e, unsigned long long cond_handle, int use_cond,
+                      cudaStream_t s) {
+  k_check_e<<<1, 1024, 0, s>>>(e.views, e.B, (cudaGraphConditionalHandle)cond_handle, use_cond);
+}
+
+void launch_rebuild_ens(int form, const EnsLaunch& e, int sub_off, cudaStream_t s) {
+  switch (form) {
+    case FORM_SPLIT: rebuild_ens_impl<FORM_SPLIT>(e, sub_off, s); break;
+    case FORM_PLAIN: rebuild_ens_impl<FORM_PLAIN>(e, sub_off, s); break;
+    default: rebuild_ens_impl<FORM_FP64>(e, sub_off, s); break;
+  }
+}
+
+void launch_ctl_gather_ens(const EnsLaunch& e, Ctl* out, cudaStream_t s) {
+  k_ctl_gather_e<<<(e.B + 127) / 128, 128, 0, s>>>(e.views, e.B, out);
+}
+
+void launch_advance_ens(const EnsLaunch& e, int n, cudaStream_t s) {
+  if (n & 1) k_advance_e<<<(e.B + 255) / 256, 256, 0, s>>>(e.views, e.B, n);
+}
+
 
 // ---------------------------------------------------------------- import/export
 

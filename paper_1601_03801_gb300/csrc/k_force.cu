@@ -100,10 +100,14 @@ __device__ __forceinline__ V3<F> cross(V3<F> a, V3<F> b) {
 // BS threads per block, at least MINB resident blocks per SM (which caps the
 // registers a thread may use); the variant is chosen per workload by the engine's
 // autotuner.
-template <int FORM, bool INTEGRATE, int BS, int MINB>
-__global__ void __launch_bounds__(BS, MINB) k_substep(DevState st, DevMesh mesh, DevParams P,
-                                                         int sub_off, cudaGraphConditionalHandle next,
-                                                         int use_cond) {
+// Body of the fused substep for one bed: blk is the block's index within the bed,
+// nblk the bed's block count; ectl (ensembles only) collects the rebuild decision
+// of all nbeds beds for the graph condition of the next substep.
+template <int FORM, bool INTEGRATE, int BS>
+__device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& mesh,
+                                             const DevParams& P, int sub_off,
+                                             cudaGraphConditionalHandle next, int use_cond,
+                                             int64_t blk, unsigned nblk, Ctl* ectl, int nbeds) {
   using S = typename Traits<FORM>::S;
   using F = typename Traits<FORM>::F;
   using NS = Num<S>;
@@ -114,7 +118,7 @@ __global__ void __launch_bounds__(BS, MINB) k_substep(DevState st, DevMesh mesh,
   const int pb = ctl->pb;
   const int nl = ctl->nl;
   const int64_t N = st.N;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = blk * BS + threadIdx.x;
   float my_disp2 = 0.0f;
   if (i < N) {
     const Quad<S>* pos = (const Quad<S>*)st.pos[sb];
@@ -372,9 +376,13 @@ __global__ void __launch_bounds__(BS, MINB) k_substep(DevState st, DevMesh mesh,
     }
     // the last block to finish decides whether the lists must be rebuilt before the
     // next substep (and sets the graph condition of that substep's rebuild node)
+    // (thread 0 made this block's displacement atomic above; its fence orders it
+    // before the completion count)
     __shared__ bool last;
-    __threadfence();
-    if (threadIdx.x == 0) last = atomicAdd(&st.ctl->blocks_done, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      last = atomicAdd(&st.ctl->blocks_done, 1u) == nblk - 1;
+    }
     __syncthreads();
     if (last && threadIdx.x == 0) {
       __threadfence();
@@ -382,9 +390,43 @@ __global__ void __launch_bounds__(BS, MINB) k_substep(DevState st, DevMesh mesh,
       const int need = mx > P.half_skin_f * P.half_skin_f ? 1 : 0;
       st.ctl->need_rebuild = need;
       st.ctl->blocks_done = 0u;
-      if (use_cond) cudaGraphSetConditional(next, need ? 1u : 0u);
+      if (ectl) {
+        // the last bed to finish sets the condition: rebuild if any bed needs it
+        if (need) atomicOr(&ectl->need_rebuild, 1);
+        __threadfence();
+        if (atomicAdd(&ectl->blocks_done, 1u) == (unsigned)nbeds - 1) {
+          __threadfence();
+          const int any = atomicExch(&ectl->need_rebuild, 0);
+          ectl->blocks_done = 0u;
+          if (use_cond) cudaGraphSetConditional(next, any ? 1u : 0u);
+        }
+      } else if (use_cond) {
+        cudaGraphSetConditional(next, need ? 1u : 0u);
+      }
     }
   }
+}
+
+template <int FORM, bool INTEGRATE, int BS, int MINB>
+__global__ void __launch_bounds__(BS, MINB) k_substep(DevState st, DevMesh mesh, DevParams P,
+                                                         int sub_off, cudaGraphConditionalHandle next,
+                                                         int use_cond) {
+  substep_body<FORM, INTEGRATE, BS>(st, mesh, P, sub_off, next, use_cond, blockIdx.x, gridDim.x,
+                                    nullptr, 1);
+}
+
+// Ensemble: blockIdx.y is the bed, blockIdx.x the block within it (blocks past the
+// bed's particles return at once).
+template <int FORM, int BS, int MINB>
+__global__ void __launch_bounds__(BS, MINB) k_substep_e(const BedView* v, int nbeds, Ctl* ectl,
+                                                           int sub_off, cudaGraphConditionalHandle next,
+                                                           int use_cond) {
+  const int64_t N = v[blockIdx.y].st.N;
+  const unsigned nblk = (unsigned)((N + BS - 1) / BS);
+  if (blockIdx.x >= nblk) return;
+  const BedView& b = bed_view(v);
+  substep_body<FORM, true, BS>(b.st, b.mesh, b.P, sub_off, next, use_cond, blockIdx.x, nblk, ectl,
+                               nbeds);
 }
 
 template <int FORM, int BS, int MINB>
@@ -429,6 +471,18 @@ void launch_substep(int form, const DevState& st, const DevMesh& mesh, const Dev
     default:
       launch_one<FORM_FP64>(st, mesh, P, sub_off, integrate, variant, next_cond, use_cond, s);
       break;
+  }
+}
+
+
+void launch_substep_ens(int form, const EnsLaunch& e, int sub_off, unsigned long long next_cond,
+                        int use_cond, cudaStream_t s) {
+  const dim3 grid((unsigned)((e.max_n + 127) / 128), (unsigned)e.B);
+  const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)next_cond;
+  switch (form) {
+    case FORM_SPLIT: k_substep_e<FORM_SPLIT, 128, 6><<<grid, 128, 0, s>>>(e.views, e.B, e.ectl, sub_off, h, use_cond); break;
+    case FORM_PLAIN: k_substep_e<FORM_PLAIN, 128, 6><<<grid, 128, 0, s>>>(e.views, e.B, e.ectl, sub_off, h, use_cond); break;
+    default: k_substep_e<FORM_FP64, 128, 6><<<grid, 128, 0, s>>>(e.views, e.B, e.ectl, sub_off, h, use_cond); break;
   }
 }
 

@@ -1,0 +1,1023 @@
+// Diffusion smoothing of the averaged fields (Sec. 2.4, Eq. 10): n_tau
+// backward-Euler pseudo-steps (I - dtau div D grad) x = b of the 7-point
+// finite-volume Laplacian (zero flux through non-periodic faces), each solved to
+// ||b - A x|| <= rtol ||b|| for every field of every mesh of a batch, in ONE
+// persistent cooperative launch.
+//
+// Solver: Chebyshev semi-iteration on the known spectrum of A (lambda_min = 1 from
+// the constant mode, lambda_max <= 1 + 4 sum_a coef_a by Gershgorin), organised as
+// iterative refinement:
+//   round:  r = b - A x in the wide word (df64 in the split form), kept as a narrow
+//           copy, with the sums |r|^2, sum r (and |b|^2 in the first round)
+//           reduced per work unit;
+//           the constant shift s = sum(r) / C restores sum(x) = sum(b) (1^T A = 1^T,
+//           so A 1 = 1 and the shifted residual has |r - s|^2 = |r|^2 - (sum r)^2/C);
+//           if |r - s| <= rtol |b| the field is done, otherwise k Chebyshev steps
+//           follow, k fixed up front from |r_k| <= 2 sigma^k |r_0|,
+//           sigma = (sqrt(kappa) - 1) / (sqrt(kappa) + 1);
+//   steps:  d_0 = (r - s) / theta;  x += d;  q -= A d;  d = c1 d + c2 q
+//           with the direction d and the recursive residual q in the narrow word
+//           (FP32 in the split form, the 8 fields of a cell interleaved so they load
+//           as two 16-byte vectors) and x accumulated in the wide word;
+//           rho' = 1 / (2 theta/delta - rho), c1 = rho' rho, c2 = 2 rho'/delta.
+// A round that ends with the narrow recursion's rounding floor above the tolerance
+// is followed by another round from the true residual, so every field finishes
+// with a true df64 residual below rtol and sum(x) = sum(b) to df64 rounding.  The
+// narrow steps do about a sixth of the work of df64 steps.
+//
+// Work units: 256 consecutive cells of one mesh (one per thread).  Every reduction
+// is a per-unit partial sum followed by a per-mesh sum over its units in unit
+// order, so a mesh's result does not depend on the grid size or on the other
+// meshes of the batch: a batch of beds gives the same bits as each bed alone.
+// The grid barrier spins at most ~0.3 s, then records SEDI_ETIMEOUT and returns;
+// the other blocks see the record and return at their next barrier.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/sedi.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sedi {
+
+namespace {
+
+constexpr int kThreads = 256;  // threads per block = cells per work unit
+constexpr int kMaxF = 8;
+constexpr int kQ = 3;          // per-unit sums: |r|^2, sum r, |b|^2
+constexpr int kMaxRounds = 64;
+
+// ---------------------------------------------------------------- words
+// T: wide word (x, b, r); N: narrow word (d, q); Acc: unit sums.
+template <class T>
+struct Wide;
+template <>
+struct Wide<dd> {
+  using N = float;
+  using Acc = float;
+  static constexpr double kFloor = 1.0e-6;  // reduction one narrow round can reach
+  __device__ static dd zero() { return dd{0.0f, 0.0f}; }
+  __device__ static dd from_d(double a) { return dd_from_double(a); }
+  __device__ static float narrow(dd a) { return __fadd_rn(a.hi, a.lo); }
+  __device__ static dd add(dd a, dd b) { return dd_add(a, b); }
+  __device__ static dd addq(dd a, dd b) { return dd_add_fast(a, b); }
+  __device__ static dd subq(dd a, dd b) { return dd_sub_fast(a, b); }
+  __device__ static dd mul(dd a, dd b) { return dd_mul(a, b); }
+  __device__ static dd add_n(dd a, float b) { return dd_add_f(a, b); }
+  __device__ static dd ld(const dd* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return dd{v.x, v.y};
+  }
+};
+template <>
+struct Wide<float> {
+  using N = float;
+  using Acc = float;
+  static constexpr double kFloor = 1.0e-6;
+  __device__ static float zero() { return 0.0f; }
+  __device__ static float from_d(double a) { return __double2float_rn(a); }
+  __device__ static float narrow(float a) { return a; }
+  __device__ static float add(float a, float b) { return a + b; }
+  __device__ static float addq(float a, float b) { return a + b; }
+  __device__ static float subq(float a, float b) { return a - b; }
+  __device__ static float mul(float a, float b) { return a * b; }
+  __device__ static float add_n(float a, float b) { return a + b; }
+  __device__ static float ld(const float* p) { return __ldcg(p); }
+};
+template <>
+struct Wide<double> {
+  using N = double;
+  using Acc = double;
+  static constexpr double kFloor = 0.0;
+  __device__ static double zero() { return 0.0; }
+  __device__ static double from_d(double a) { return a; }
+  __device__ static double narrow(double a) { return a; }
+  __device__ static double add(double a, double b) { return a + b; }
+  __device__ static double addq(double a, double b) { return a + b; }
+  __device__ static double subq(double a, double b) { return a - b; }
+  __device__ static double mul(double a, double b) { return a * b; }
+  __device__ static double add_n(double a, double b) { return a + b; }
+  __device__ static double ld(const double* p) { return __ldcg(p); }
+};
+
+// Loads of words written by other blocks of the same launch go to L2 (ld.cg), so
+// no stale L1 line is read after a grid barrier.
+__device__ __forceinline__ int ldi(const int* p) { return __ldcg(p); }
+__device__ __forceinline__ double ldd(const double* p) { return __ldcg(p); }
+
+// Bounded grid barrier (co-residency guaranteed by the cooperative launch).
+__device__ bool grid_barrier(Ctl* ctl, unsigned nblocks) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = &ctl->bar_gen;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&ctl->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&ctl->bar_gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == g) {
+        if (++spins > (1ll << 22)) {  // ~0.3 s
+          atomicCAS((int*)&ctl->cg_status, 0, SEDI_ETIMEOUT);
+          break;
+        }
+        // another block gave up: stop waiting too
+        if ((spins & 1023) == 0 && *((volatile int*)&ctl->cg_status) == SEDI_ETIMEOUT) break;
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *((volatile int*)&ctl->cg_status) != SEDI_ETIMEOUT;
+}
+
+// Cell coordinates -> the six face neighbours (-1: zero-flux face).
+struct Stencil {
+  int32_t nb[6];
+};
+
+__device__ __forceinline__ Stencil stencil_of(const SmoothMeshDev& m, int64_t c) {
+  const uint32_t nx = m.nc[0], ny = m.nc[1], nz = m.nc[2];
+  const uint32_t cc = (uint32_t)c;
+  const uint32_t ix = cc % nx;
+  const uint32_t t = cc / nx;
+  const uint32_t iy = t % ny;
+  const uint32_t iz = t / ny;
+  const uint32_t idx[3] = {ix, iy, iz};
+  const uint32_t n[3] = {nx, ny, nz};
+  const int32_t stride[3] = {1, (int32_t)nx, (int32_t)(nx * ny)};
+  Stencil s;
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const int32_t base = (int32_t)cc - (int32_t)idx[ax] * stride[ax];
+    if (idx[ax] > 0) s.nb[2 * ax] = (int32_t)cc - stride[ax];
+    else s.nb[2 * ax] = m.per[ax] ? base + (int32_t)(n[ax] - 1) * stride[ax] : -1;
+    if (idx[ax] + 1 < n[ax]) s.nb[2 * ax + 1] = (int32_t)cc + stride[ax];
+    else s.nb[2 * ax + 1] = m.per[ax] ? base : -1;
+  }
+  return s;
+}
+
+// (A v)(c) = v_c - sum_axes coef_a ((v_- - v_c) + (v_+ - v_c)), faces that exist only.
+// V is the word of the operand, get(k) loads (or forms) its value at cell k.
+template <class V, class Sub, class Add, class Mul, class Get>
+__device__ __forceinline__ V apply_A(const Stencil& st, const V* cf, V vc, Sub sub, Add add,
+                                     Mul mul, Get get) {
+  V lap{};
+  bool any_axis = false;
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    V sa{};
+    bool any = false;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int32_t nb = st.nb[2 * ax + side];
+      if (nb < 0) continue;
+      const V t = sub(get(nb), vc);
+      sa = any ? add(sa, t) : t;
+      any = true;
+    }
+    if (any) {
+      const V t = mul(cf[ax], sa);
+      lap = any_axis ? add(lap, t) : t;
+      any_axis = true;
+    }
+  }
+  return any_axis ? sub(vc, lap) : vc;
+}
+
+// Eight narrow words of one cell (the fields of the narrow recursion are stored
+// interleaved, [C][8], so one cell's fields load as two 16-byte vectors).
+template <class N>
+struct V8 {
+  N v[8];
+};
+__device__ __forceinline__ V8<float> ld8(const float* p) {
+  const float4 a = __ldcg(reinterpret_cast<const float4*>(p));
+  const float4 b = __ldcg(reinterpret_cast<const float4*>(p) + 1);
+  return V8<float>{{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w}};
+}
+__device__ __forceinline__ void st8(float* p, const V8<float>& x) {
+  reinterpret_cast<float4*>(p)[0] = make_float4(x.v[0], x.v[1], x.v[2], x.v[3]);
+  reinterpret_cast<float4*>(p)[1] = make_float4(x.v[4], x.v[5], x.v[6], x.v[7]);
+}
+__device__ __forceinline__ V8<double> ld8(const double* p) {
+  V8<double> r;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double2 a = __ldcg(reinterpret_cast<const double2*>(p) + k);
+    r.v[2 * k] = a.x;
+    r.v[2 * k + 1] = a.y;
+  }
+  return r;
+}
+__device__ __forceinline__ void st8(double* p, const V8<double>& x) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) reinterpret_cast<double2*>(p)[k] = make_double2(x.v[2 * k], x.v[2 * k + 1]);
+}
+
+// Per-mesh solver state published by the owner block of each mesh.
+struct alignas(16) MeshState {
+  int32_t k[kMaxF];      // Chebyshev steps of the current round per field (0: none)
+  int32_t done[kMaxF];   // converged, zero or stopped
+  int32_t zero[kMaxF];   // b == 0: x = 0
+  int32_t total[kMaxF];  // steps taken in this pseudo-step
+  double shift[kMaxF];   // projection shift of the current round
+  double bb[kMaxF];      // |b|^2
+};
+
+// Per-block reduction of the kQ sums of nf fields for one unit (fixed order).
+template <class Acc>
+__device__ __forceinline__ void unit_sums(const Acc (&v)[kMaxF][kQ], int nf, double* out) {
+  __shared__ Acc red[kThreads / 32][kMaxF][kQ];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int f = 0; f < kMaxF; ++f)
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      if (f >= nf) continue;
+      Acc t = v[f][q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) red[wid][f][q] = t;
+    }
+  __syncthreads();
+  if (threadIdx.x < nf * kQ) {
+    const int f = threadIdx.x / kQ, q = threadIdx.x % kQ;
+    double s = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s += (double)red[w][f][q];
+    out[f * kQ + q] = s;
+  }
+  __syncthreads();
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
+  using W = Wide<T>;
+  using N = typename W::N;
+  using Acc = typename W::Acc;
+  const unsigned G = gridDim.x;
+  const int nf = a.nf;
+  const int64_t U = a.U;
+  const int64_t u_begin = (int64_t)blockIdx.x * U / G, u_end = (int64_t)(blockIdx.x + 1) * U / G;
+  MeshState* ms = (MeshState*)a.pairs;
+  __shared__ N s_c1[kMaxBeds], s_c2[kMaxBeds];
+  __shared__ double s_rho[kMaxBeds];
+  __shared__ double s_sums[kMaxF * kQ];
+  __shared__ int s_K;
+  int slot = 0;
+
+  for (int m = 0; m < a.n_tau; ++m) {
+    const bool use_guess = (m == 0);
+    // ---- b = x (the previous pseudo-step's result); x = guess on the first
+    for (int64_t u = u_begin; u < u_end; ++u) {
+      const SmoothMeshDev& md = a.mesh[a.unit_bed[u]];
+      const int64_t c = (u - md.u0) * kThreads + threadIdx.x;
+      if (c >= md.C) continue;
+      for (int f = 0; f < nf; ++f) {
+        const int64_t k = f * md.C + c;
+        ((T*)md.b)[k] = W::ld((const T*)md.x + k);
+        if (use_guess && md.guess) ((T*)md.x)[k] = W::ld((const T*)md.guess + k);
+      }
+    }
+    if (!grid_barrier(a.ctl, G)) return;
+    for (int round = 0; round < kMaxRounds; ++round) {
+      // ---- true residual r = b - A x (wide), its narrow copy (interleaved, in d[0])
+      //      and the unit sums |r|^2, sum r, |b|^2
+      for (int64_t u = u_begin; u < u_end; ++u) {
+        const int bi = a.unit_bed[u];
+        const SmoothMeshDev& md = a.mesh[bi];
+        const MeshState& st = ms[bi];
+        const int64_t c = (u - md.u0) * kThreads + threadIdx.x;
+        const bool in = c < md.C;
+        Acc v[kMaxF][kQ];
+        V8<N> rn;
+        const T cf[3] = {W::from_d(md.coef[0]), W::from_d(md.coef[1]), W::from_d(md.coef[2])};
+        const Stencil sc = stencil_of(md, in ? c : 0);
+#pragma unroll
+        for (int f = 0; f < kMaxF; ++f) {
+          v[f][0] = v[f][1] = v[f][2] = Acc(0);
+          rn.v[f] = N(0);
+          if (f >= nf || !in || (round > 0 && ldi(&st.done[f]))) continue;
+          const T* X = (const T*)md.x + f * md.C;
+          const T xc = W::ld(X + c);
+          const T ax = apply_A<T>(sc, cf, xc, [](T p, T q) { return W::subq(p, q); },
+                                  [](T p, T q) { return W::addq(p, q); },
+                                  [](T p, T q) { return W::mul(p, q); },
+                                  [&](int32_t k) { return W::ld(X + k); });
+          const T bv = W::ld((const T*)md.b + f * md.C + c);
+          const T rv = W::subq(bv, ax);
+          const N r_n = W::narrow(rv);
+          rn.v[f] = r_n;
+          v[f][0] = (Acc)r_n * (Acc)r_n;
+          v[f][1] = (Acc)r_n;
+          if (round == 0) {
+            const Acc bn = (Acc)W::narrow(bv);
+            v[f][2] = bn * bn;
+          }
+        }
+        if (in) st8((N*)md.d[0] + c * kMaxF, rn);
+        unit_sums<Acc>(v, nf, md.part + (u - md.u0) * (kMaxF * kQ));
+      }
+      if (!grid_barrier(a.ctl, G)) return;
+      // ---- owners: per-(mesh, field) sums over the mesh's units, decisions
+      for (int bi = blockIdx.x; bi < a.B; bi += G) {
+        const SmoothMeshDev& md = a.mesh[bi];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        for (int pq = wid; pq < nf * kQ; pq += kThreads / 32) {
+          const int f = pq / kQ, q = pq % kQ;
+          double s = 0.0;
+          for (int64_t u = lane; u < md.nu; u += 32) s += ldd(md.part + u * (kMaxF * kQ) + f * kQ + q);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          if (lane == 0) s_sums[f * kQ + q] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x < kMaxF) {
+          const int f = threadIdx.x;
+          MeshState& st = ms[bi];
+          int k = 0, done = 1, zero = 0, total = 0;
+          double shift = 0.0, bb = 0.0;
+          if (f < nf) {
+            done = round == 0 ? 0 : st.done[f];
+            zero = round == 0 ? 0 : st.zero[f];
+            total = round == 0 ? 0 : st.total[f];
+            bb = round == 0 ? s_sums[f * kQ + 2] : st.bb[f];
+            if (round == 0) zero = !(bb > 0.0);
+            if (!done) {
+              const double rr = s_sums[f * kQ + 0], sr = s_sums[f * kQ + 1];
+              const double Cd = (double)md.C;
+              if (zero) {
+                done = 1;
+              } else {
+                shift = sr / Cd;
+                const double rrp = fmax(rr - sr * sr / Cd, 0.0);
+                if (rrp <= a.rtol2 * bb) {
+                  done = 1;
+                } else {
+                  // |r_k| <= 2 sig^k |r_0|: enough steps for the tolerance, or for the
+                  // reduction the narrow word can deliver in one round
+                  const double need = fmax(0.5 * sqrt(a.rtol2 * bb / rrp), W::kFloor);
+                  k = md.sig > 0.0 ? (int)ceil(log(need) / log(md.sig)) : 1;
+                  if (k < 1) k = 1;
+                  if (total + k > a.max_iter) k = a.max_iter - total;
+                  if (k <= 0) {
+                    k = 0;
+                    done = 1;
+                    atomicCAS((int*)&a.ctl->cg_status, 0, SEDI_EDIVERGED);
+                  } else {
+                    total += k;
+                  }
+                }
+              }
+              if (done && md.iters) atomicAdd(md.iters + f, total);
+            }
+          }
+          st.k[f] = k;
+          st.done[f] = done;
+          st.zero[f] = zero;
+          st.total[f] = total;
+          st.shift[f] = shift;
+          st.bb[f] = bb;
+          if (k > 0) atomicMax(a.gflag + slot, k);
+        }
+        __syncthreads();
+      }
+      // the slot of the next round was last read before the previous barrier
+      if (blockIdx.x == 0 && threadIdx.x == 0) a.gflag[slot ^ 1] = 0;
+      if (!grid_barrier(a.ctl, G)) return;
+      if (threadIdx.x == 0) s_K = ldi(a.gflag + slot);
+      for (int b = threadIdx.x; b < a.B; b += kThreads) s_rho[b] = 1.0 / a.mesh[b].sigma1;
+      __syncthreads();
+      const int K = s_K;
+      slot ^= 1;
+      // ---- Chebyshev steps j = 1..K; step 1 also applies the shift (or zeroes x)
+      const int J = K > 0 ? K : 1;
+      for (int j = 1; j <= J; ++j) {
+        for (int b = threadIdx.x; b < a.B; b += kThreads) {
+          const SmoothMeshDev& md = a.mesh[b];
+          const double rho = s_rho[b];
+          const double rho_new = 1.0 / (2.0 * md.sigma1 - rho);
+          s_c1[b] = (N)(rho_new * rho);
+          s_c2[b] = (N)(2.0 * rho_new / md.delta);
+          s_rho[b] = rho_new;
+        }
+        __syncthreads();
+        for (int64_t u = u_begin; u < u_end; ++u) {
+          const int bi = a.unit_bed[u];
+          const SmoothMeshDev& md = a.mesh[bi];
+          const MeshState& st = ms[bi];
+          const int64_t c = (u - md.u0) * kThreads + threadIdx.x;
+          if (c >= md.C) continue;
+          int kf[kMaxF];
+          N sh[kMaxF];
+          bool any = false;
+#pragma unroll
+          for (int f = 0; f < kMaxF; ++f) sh[f] = N(0);
+#pragma unroll
+          for (int f = 0; f < kMaxF; ++f) {
+            kf[f] = f < nf ? ldi(&st.k[f]) : 0;
+            any |= kf[f] >= j;
+          }
+          if (j == 1) {
+            // projection shift (and zero fields) for every field, then the first step
+            T* X = (T*)md.x;
+#pragma unroll
+            for (int f = 0; f < kMaxF; ++f) {
+              if (f >= nf) continue;
+              const double s = ldd(&st.shift[f]);
+              sh[f] = (N)s;
+              if (kf[f] == 0) {
+                if (round == 0 && ldi(&st.zero[f])) X[f * md.C + c] = W::zero();
+                else if (s != 0.0) X[f * md.C + c] = W::add(W::ld(X + f * md.C + c), W::from_d(s));
+              }
+            }
+          }
+          if (!any) continue;
+          const N cfn[3] = {(N)md.coef[0], (N)md.coef[1], (N)md.coef[2]};
+          const N c1 = s_c1[bi], c2 = s_c2[bi];
+          const N inv_theta = (N)(1.0 / md.theta);
+          const Stencil sc = stencil_of(md, c);
+          // step 1 reads the narrow residual (d[0]) and forms d0 = (r - s) / theta at
+          // every stencil point; later steps read the previous direction
+          const N* Dold = (const N*)md.d[(j - 1) & 1];
+          N* Dnew = (N*)md.d[j & 1];
+          N* Q = (N*)md.q;
+          auto dir = [&](const V8<N>& raw) {
+            V8<N> d = raw;
+            if (j == 1) {
+#pragma unroll
+              for (int f = 0; f < kMaxF; ++f) d.v[f] = (raw.v[f] - sh[f]) * inv_theta;
+            }
+            return d;
+          };
+          const V8<N> dc = dir(ld8(Dold + c * kMaxF));
+          V8<N> lap;
+          bool any_axis = false;
+#pragma unroll
+          for (int ax = 0; ax < 3; ++ax) {
+            V8<N> sa;
+            bool any_side = false;
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+              const int32_t nb = sc.nb[2 * ax + side];
+              if (nb < 0) continue;
+              const V8<N> dn = dir(ld8(Dold + (int64_t)nb * kMaxF));
+#pragma unroll
+              for (int f = 0; f < kMaxF; ++f) {
+                const N t = dn.v[f] - dc.v[f];
+                sa.v[f] = any_side ? sa.v[f] + t : t;
+              }
+              any_side = true;
+            }
+            if (any_side) {
+#pragma unroll
+              for (int f = 0; f < kMaxF; ++f) {
+                const N t = cfn[ax] * sa.v[f];
+                lap.v[f] = any_axis ? lap.v[f] + t : t;
+              }
+              any_axis = true;
+            }
+          }
+          // q: the narrow residual r - s (step 1) or the recursive residual
+          V8<N> q = j == 1 ? ld8(Dold + c * kMaxF) : ld8(Q + c * kMaxF);
+          V8<N> dn;
+          T* X = (T*)md.x;
+#pragma unroll
+          for (int f = 0; f < kMaxF; ++f) {
+            dn.v[f] = N(0);
+            if (kf[f] < j) continue;
+            const N ad = any_axis ? dc.v[f] - lap.v[f] : dc.v[f];
+            const int64_t k = f * md.C + c;
+            T xv = W::ld(X + k);
+            if (j == 1) {
+              xv = W::add(xv, W::from_d(ldd(&st.shift[f])));  // projection shift
+              q.v[f] = q.v[f] - sh[f];                         // narrow r - s
+            }
+            q.v[f] = q.v[f] - ad;
+            dn.v[f] = c1 * dc.v[f] + c2 * q.v[f];
+            X[k] = W::add_n(xv, dc.v[f]);
+          }
+          st8(Q + c * kMaxF, q);
+          st8(Dnew + c * kMaxF, dn);
+        }
+        if (!grid_barrier(a.ctl, G)) return;
+      }
+      if (K == 0) break;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- cluster solver
+// Meshes whose z-planes fit 8192 cells per CTA on at most 16 CTAs (split and plain
+// forms): a thread-block cluster solves one (mesh, field) pair at a time.  CTA r
+// holds whole z-planes [r P, (r + 1) P) of the field and its narrow recursion in
+// shared memory (x in the wide word, the narrow residual and two directions), so a
+// step touches no global memory; the z-neighbours of a CTA's first and last plane
+// are read from the adjacent CTAs through distributed shared memory.  Pairs are
+// independent, so there is no grid-wide barrier: each step ends with the hardware
+// cluster barrier and each field runs its own step count.  Same iteration as the
+// grid solver (rounds of a wide true residual, then narrow Chebyshev steps); the
+// sums of a round are reduced per CTA, then over the CTAs in rank order.  The
+// cluster shape is a function of the mesh alone, so a bed smooths the same way in
+// any batch.
+namespace cg = cooperative_groups;
+constexpr int kClThreads = 1024;
+constexpr int kClCells = 8192;   // cells per CTA at most
+constexpr int kClMaxCta = 16;
+constexpr int kClMaxSteps = 64;  // Chebyshev steps of one round at most (more: next round)
+
+// A stencil neighbour: index in the owning CTA's arrays, and that CTA (-1: this one).
+struct Nb {
+  int32_t l;
+  int32_t r;
+};
+
+template <class T>
+__global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
+  using W = Wide<T>;
+  using N = typename W::N;
+  using Acc = typename W::Acc;
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  __shared__ double s_part[kQ];
+  __shared__ double s_red[kClThreads / 32][kQ];
+  __shared__ N s_c1[kClMaxSteps], s_c2[kClMaxSteps];
+  cg::cluster_group cl = cg::this_cluster();
+  const int csize = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int64_t ncl = gridDim.x / csize, cid = blockIdx.x / csize;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t items = (int64_t)a.B * a.nf;
+  for (int64_t w = cid; w < items; w += ncl) {
+    const int bi = (int)(w / a.nf), f = (int)(w % a.nf);
+    const SmoothMeshDev& md = a.mesh[bi];
+    const int64_t C = md.C;
+    const int nx = md.nc[0], ny = md.nc[1], nz = md.nc[2], nxy = nx * ny;
+    const int P = md.cl_planes;                                  // planes of a full CTA
+    const int z0 = rank * P;
+    const int planes = z0 + P <= nz ? P : nz - z0;               // this CTA's planes
+    const int last_planes = nz - (csize - 1) * P;
+    const int ncell = planes * nxy;
+    const int64_t c0 = (int64_t)z0 * nxy;
+    T* Xs = (T*)s_dyn;                      // [P nxy] x
+    N* dA = (N*)(Xs + P * nxy);             // narrow true residual, then even directions
+    N* dB = dA + P * nxy;                   // odd directions
+    N* Qs = dB + P * nxy;                   // recursive residual
+    T* Xg = (T*)md.x + f * C;
+    T* Bg = (T*)md.b + f * C;
+    const T cf[3] = {W::from_d(md.coef[0]), W::from_d(md.coef[1]), W::from_d(md.coef[2])};
+    const N cfn[3] = {(N)md.coef[0], (N)md.coef[1], (N)md.coef[2]};
+    const N inv_theta = (N)(1.0 / md.theta);
+    // Work layout: thread t owns the (x, y) sites t, t + kClThreads, ... of a plane and
+    // all of this CTA's planes at those sites, so the in-plane neighbours are fixed
+    // offsets per site and only the z-neighbours change from plane to plane.
+    struct Site {
+      int32_t s;        // site index in the plane
+      int32_t off[4];   // in-plane neighbour offsets (x-, x+, y-, y+); INT32_MIN: none
+    };
+    auto site_of = [&](int sidx) {
+      Site st;
+      st.s = sidx;
+      const int ix = sidx % nx, iy = sidx / nx;
+      st.off[0] = ix > 0 ? -1 : (md.per[0] ? nx - 1 : INT32_MIN);
+      st.off[1] = ix < nx - 1 ? 1 : (md.per[0] ? -(nx - 1) : INT32_MIN);
+      st.off[2] = iy > 0 ? -nx : (md.per[1] ? (ny - 1) * nx : INT32_MIN);
+      st.off[3] = iy < ny - 1 ? nx : (md.per[1] ? -(ny - 1) * nx : INT32_MIN);
+      return st;
+    };
+    // the six face neighbours of local cell l = izl nxy + site (r = -2: zero-flux face)
+    auto stencil = [&](const Site& st, int izl, Nb* nb) {
+      const int l = izl * nxy + st.s;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) nb[k] = st.off[k] != INT32_MIN ? Nb{l + st.off[k], -1} : Nb{0, -2};
+      if (izl > 0) nb[4] = Nb{l - nxy, -1};
+      else if (z0 > 0) nb[4] = Nb{(P - 1) * nxy + st.s, rank - 1};
+      else if (md.per[2]) nb[4] = csize > 1 ? Nb{(last_planes - 1) * nxy + st.s, csize - 1} : Nb{(planes - 1) * nxy + st.s, -1};
+      else nb[4] = Nb{0, -2};
+      if (izl < planes - 1) nb[5] = Nb{l + nxy, -1};
+      else if (z0 + planes < nz) nb[5] = Nb{st.s, rank + 1};
+      else if (md.per[2]) nb[5] = csize > 1 ? Nb{st.s, 0} : Nb{st.s, -1};
+      else nb[5] = Nb{0, -2};
+    };
+    // (A v) at a cell from its value vc and its neighbours' values, axis by axis:
+    // vc - sum_a coef_a ((v_- - vc) + (v_+ - vc)) over the faces that exist
+    auto lap_apply = [&](auto vc, const Nb* nb, auto get, auto sub, auto add, auto mul, const auto* cfa) {
+      decltype(vc) lap{};
+      bool any_axis = false;
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        decltype(vc) sa{};
+        bool any = false;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          const Nb& n = nb[2 * ax + side];
+          if (n.r == -2) continue;
+          const auto t = sub(get(n), vc);
+          sa = any ? add(sa, t) : t;
+          any = true;
+        }
+        if (any) {
+          const auto t = mul(cfa[ax], sa);
+          lap = any_axis ? add(lap, t) : t;
+          any_axis = true;
+        }
+      }
+      return any_axis ? sub(vc, lap) : vc;
+    };
+    auto wsub = [](T p, T q) { return W::subq(p, q); };
+    auto wadd = [](T p, T q) { return W::addq(p, q); };
+    auto wmul = [](T p, T q) { return W::mul(p, q); };
+    auto nsub = [](N p, N q) { return p - q; };
+    auto nadd = [](N p, N q) { return p + q; };
+    auto nmul = [](N p, N q) { return p * q; };
+    for (int m = 0; m < a.n_tau; ++m) {
+      // ---- b = x (global); x (or the guess) into shared memory
+      for (int l = threadIdx.x; l < ncell; l += kClThreads) {
+        const T xv = W::ld(Xg + c0 + l);
+        Bg[c0 + l] = xv;
+        Xs[l] = (m == 0 && md.guess) ? W::ld((const T*)md.guess + f * C + c0 + l) : xv;
+      }
+      cl.sync();
+      int total = 0, zero = 0;
+      double bb = 0.0;
+      for (int round = 0; round < kMaxRounds; ++round) {
+        // ---- true residual (wide), its narrow copy in dA, sums
+        Acc v[kQ] = {Acc(0), Acc(0), Acc(0)};
+        for (int sidx = threadIdx.x; sidx < nxy; sidx += kClThreads)
+        for (int izl = 0; izl < planes; ++izl) {
+          const Site st = site_of(sidx);
+          const int l = izl * nxy + sidx;
+          Nb nb[6];
+          stencil(st, izl, nb);
+          auto getx = [&](const Nb& n) {
+            const T* base = n.r < 0 ? Xs : cl.map_shared_rank(Xs, (unsigned)n.r);
+            return base[n.l];
+          };
+          const T ax = lap_apply(Xs[l], nb, getx, wsub, wadd, wmul, cf);
+          const T bv = W::ld(Bg + c0 + l);
+          const N rn = W::narrow(W::subq(bv, ax));
+          dA[l] = rn;
+          v[0] += (Acc)rn * (Acc)rn;
+          v[1] += (Acc)rn;
+          if (round == 0) {
+            const Acc bn = (Acc)W::narrow(bv);
+            v[2] += bn * bn;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+          double t = (double)v[q];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+          if (lane == 0) s_red[wid][q] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x < kQ) {
+          double t = 0.0;
+          for (int k = 0; k < kClThreads / 32; ++k) t += s_red[k][threadIdx.x];
+          s_part[threadIdx.x] = t;
+        }
+        cl.sync();
+        // every CTA sums the CTAs' parts in rank order: identical decisions
+        double tot[kQ] = {0.0, 0.0, 0.0};
+        for (int r = 0; r < csize; ++r) {
+          const double* p = cl.map_shared_rank(s_part, (unsigned)r);
+#pragma unroll
+          for (int q = 0; q < kQ; ++q) tot[q] += p[q];
+        }
+        if (round == 0) {
+          bb = tot[2];
+          zero = !(bb > 0.0);
+        }
+        const double Cd = (double)C;
+        const double shift = zero ? 0.0 : tot[1] / Cd;
+        const double rrp = fmax(tot[0] - tot[1] * tot[1] / Cd, 0.0);
+        int k = 0;
+        if (!zero && !(rrp <= a.rtol2 * bb)) {
+          const double need = fmax(0.5 * sqrt(a.rtol2 * bb / rrp), W::kFloor);
+          k = md.sig > 0.0 ? (int)ceil(log(need) / log(md.sig)) : 1;
+          if (k < 1) k = 1;
+          if (k > kClMaxSteps) k = kClMaxSteps;
+          if (total + k > a.max_iter) k = a.max_iter - total;
+          if (k <= 0) {
+            k = 0;
+            if (rank == 0 && threadIdx.x == 0) atomicCAS((int*)&a.ctl->cg_status, 0, SEDI_EDIVERGED);
+          }
+        }
+        total += k;
+        if (k == 0) {
+          // converged (or zero, or stopped): apply the projection shift, write x back
+          const T sw = W::from_d(shift);
+          for (int l = threadIdx.x; l < ncell; l += kClThreads) {
+            T xv = Xs[l];
+            if (zero) xv = W::zero();
+            else if (shift != 0.0) xv = W::add(xv, sw);
+            Xg[c0 + l] = xv;
+          }
+          break;
+        }
+        if (threadIdx.x == 0) {
+          double rho = 1.0 / md.sigma1;
+          for (int j = 0; j < k; ++j) {
+            const double rho_new = 1.0 / (2.0 * md.sigma1 - rho);
+            s_c1[j] = (N)(rho_new * rho);
+            s_c2[j] = (N)(2.0 * rho_new / md.delta);
+            rho = rho_new;
+          }
+        }
+        __syncthreads();
+        const N shn = (N)shift;
+        const T sw = W::from_d(shift);
+        // ---- Chebyshev steps (step 1 applies the shift and forms d0 = (r - s) / theta)
+        for (int j = 1; j <= k; ++j) {
+          N* Dold = (j & 1) ? dA : dB;
+          N* Dnew = (j & 1) ? dB : dA;
+          const N c1s = s_c1[j - 1], c2s = s_c2[j - 1];
+          for (int sidx = threadIdx.x; sidx < nxy; sidx += kClThreads) {
+            const Site st = site_of(sidx);
+            for (int izl = 0; izl < planes; ++izl) {
+            const int l = izl * nxy + sidx;
+            Nb nb[6];
+            stencil(st, izl, nb);
+            auto dir = [&](const Nb& n) {
+              const N* base = n.r < 0 ? Dold : cl.map_shared_rank(Dold, (unsigned)n.r);
+              const N raw = base[n.l];
+              return j == 1 ? (raw - shn) * inv_theta : raw;
+            };
+            const N dc = dir(Nb{l, -1});
+            const N ad = lap_apply(dc, nb, dir, nsub, nadd, nmul, cfn);
+            T xv = Xs[l];
+            N q;
+            if (j == 1) {
+              xv = W::add(xv, sw);
+              q = Dold[l] - shn;
+            } else {
+              q = Qs[l];
+            }
+            q = q - ad;
+            Qs[l] = q;
+            Dnew[l] = c1s * dc + c2s * q;
+            Xs[l] = W::add_n(xv, dc);
+            }
+          }
+          cl.sync();
+        }
+      }
+      if (rank == 0 && threadIdx.x == 0 && md.iters) atomicAdd(md.iters + f, total);
+    }
+  }
+}
+
+__global__ void k_bar_reset(Ctl* ctl) {
+  ctl->bar_count = 0u;
+  ctl->bar_gen = 0u;
+}
+
+template <class T>
+size_t word() {
+  return sizeof(T);
+}
+
+template <class T>
+int launch_impl(const SmoothBatchDev& a, int max_blocks, cudaStream_t s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smooth<T>, kThreads, 0);
+  if (per_sm < 1) return -3;
+  if (per_sm > 2) per_sm = 2;
+  int G = nsm * per_sm;
+  if (G > max_blocks) G = max_blocks;
+  if (G < 1) G = 1;
+  k_bar_reset<<<1, 1, 0, s>>>(a.ctl);
+  SmoothBatchDev args = a;
+  void* p[] = {&args};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_smooth<T>, dim3(G), dim3(kThreads), p, 0, s);
+  return e == cudaSuccess ? 0 : -3;
+}
+
+size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+}  // namespace
+
+int64_t smooth_units(int64_t C) { return (C + kThreads - 1) / kThreads; }
+
+size_t smooth_mesh_bytes(int form, int64_t C, int nf) {
+  const size_t w = form == FORM_PLAIN ? 4 : 8;             // wide word
+  const size_t n = form == FORM_FP64 ? 8 : 4;              // narrow word
+  return align256((size_t)nf * C * w) + 3 * align256((size_t)kMaxF * C * n) +
+         align256((size_t)smooth_units(C) * kMaxF * kQ * 8) + 256;
+}
+
+size_t smooth_work_bytes(int form, int64_t C, int nf) {
+  return align256(smooth_mesh_bytes(form, C, nf)) + smooth_batch_bytes(1, smooth_units(C));
+}
+
+int launch_smooth(int form, const DevParams& P, void* phi, const void* guess, int nf, void* work,
+                  const DevState& st, int* iters_dev, double rtol, int max_iter, int n_tau,
+                  const double coef[3], cudaStream_t s) {
+  SmoothMesh m{};
+  m.phi = phi;
+  m.guess = guess;
+  m.work = work;
+  m.iters = iters_dev;
+  m.C = P.C;
+  m.nf = nf;
+  for (int k = 0; k < 3; ++k) {
+    m.nc[k] = P.nc[k];
+    m.per[k] = P.periodic[k];
+    m.coef[k] = coef[k];
+  }
+  void* batch = (char*)work + align256(smooth_mesh_bytes(form, P.C, nf));
+  return launch_smooth_batch(form, &m, 1, nf, batch, rtol, max_iter, n_tau, st.ctl, 1 << 30, s);
+}
+
+size_t smooth_batch_bytes(int64_t B, int64_t U) {
+  return 2 * align256((size_t)B * sizeof(SmoothMeshDev)) + align256((size_t)U * 4) +
+         align256((size_t)B * sizeof(MeshState)) + 256;
+}
+
+void smooth_mesh_layout(int form, const SmoothMesh& in, SmoothMeshDev* out) {
+  const size_t w = form == FORM_PLAIN ? 4 : 8;
+  const size_t n = form == FORM_FP64 ? 8 : 4;
+  char* p = (char*)in.work;
+  SmoothMeshDev& m = *out;
+  std::memset(&m, 0, sizeof(m));
+  m.x = in.phi;
+  m.guess = in.guess;
+  m.b = p;  // [nf][C] wide
+  p += align256((size_t)in.nf * in.C * w);
+  const size_t nar = align256((size_t)kMaxF * in.C * n);  // [C][8] narrow
+  m.q = p;
+  m.d[0] = p + nar;
+  m.d[1] = p + 2 * nar;
+  p += 3 * nar;
+  m.part = (double*)p;
+  m.iters = in.iters;
+  m.C = in.C;
+  m.nu = smooth_units(in.C);
+  for (int k = 0; k < 3; ++k) {
+    m.nc[k] = in.nc[k];
+    m.per[k] = in.per[k];
+    m.coef[k] = in.coef[k];
+  }
+  double lmax = 1.0 + 4.0 * (in.coef[0] + in.coef[1] + in.coef[2]);
+  if (lmax < 1.0 + 1e-12) lmax = 1.0 + 1e-12;
+  m.theta = 0.5 * (lmax + 1.0);
+  m.delta = 0.5 * (lmax - 1.0);
+  m.sigma1 = m.theta / m.delta;
+  const double sq = std::sqrt(lmax);
+  m.sig = (sq - 1.0) / (sq + 1.0);
+}
+
+namespace {
+
+template <class T>
+int launch_cluster(const SmoothBatchDev& a, int csize, cudaStream_t s) {
+  using N = typename Wide<T>::N;
+  const size_t smem = (size_t)kClCells * (sizeof(T) + 3 * sizeof(N));
+  if (cudaFuncSetAttribute(k_smooth_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return -3;
+  if (csize > 8 && cudaFuncSetAttribute(k_smooth_cl<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return -3;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kClThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(csize * 64);
+  int ncl = 0;
+  if (cudaOccupancyMaxActiveClusters(&ncl, (void*)k_smooth_cl<T>, &cfg) != cudaSuccess || ncl < 1) return -3;
+  const int64_t items = (int64_t)a.B * a.nf;
+  if (ncl > items) ncl = (int)items;
+  cfg.gridDim = dim3(csize * ncl);
+  return cudaLaunchKernelEx(&cfg, k_smooth_cl<T>, a) == cudaSuccess ? 0 : -3;
+}
+
+// Cluster plan of a mesh (whole z-planes per CTA, <= kClCells cells each), or
+// csize 0 when the mesh does not fit the cluster solver.
+void cluster_plan(int form, const SmoothMeshDev& m, int* csize, int* planes) {
+  *csize = 0;
+  *planes = 0;
+  if (form == FORM_FP64) return;
+  const int64_t nxy = (int64_t)m.nc[0] * m.nc[1];
+  if (nxy > kClCells) return;
+  const int pmax = (int)(kClCells / nxy);
+  const int nz = m.nc[2];
+  int cs = (nz + pmax - 1) / pmax;
+  if (cs > kClMaxCta) return;
+  const int p = (nz + cs - 1) / cs;
+  cs = (nz + p - 1) / p;  // every CTA gets at least one plane
+  *csize = cs;
+  *planes = p;
+}
+
+}  // namespace
+
+int launch_smooth_batch(int form, const SmoothMesh* meshes, int B, int nf, void* batch_work,
+                        double rtol, int max_iter, int n_tau, Ctl* ctl, int max_blocks,
+                        cudaStream_t s) {
+  if (B < 1 || B > kMaxBeds || nf < 1 || nf > kMaxF) return -1;
+  // meshes that fit the cluster solver take it; the rest take the grid solver.  The
+  // choice depends on the mesh alone, so a bed smooths the same way in any batch.
+  std::vector<SmoothMeshDev> mg, mc;
+  int64_t U = 0;
+  for (int b = 0; b < B; ++b) {
+    SmoothMeshDev m;
+    smooth_mesh_layout(form, meshes[b], &m);
+    int cs, pl;
+    cluster_plan(form, m, &cs, &pl);
+    if (cs > 0) {
+      m.cl_size = cs;
+      m.cl_planes = pl;
+      mc.push_back(m);
+    } else {
+      m.u0 = U;
+      U += m.nu;
+      mg.push_back(m);
+    }
+  }
+  // cluster meshes grouped by cluster size (one launch per size)
+  std::stable_sort(mc.begin(), mc.end(),
+                   [](const SmoothMeshDev& x, const SmoothMeshDev& y) { return x.cl_size < y.cl_size; });
+  char* p = (char*)batch_work;
+  SmoothBatchDev a{};
+  a.nf = nf;
+  a.rtol2 = rtol * rtol;
+  a.max_iter = max_iter;
+  a.n_tau = n_tau;
+  a.ctl = ctl;
+  SmoothMeshDev* tab_g = (SmoothMeshDev*)p;
+  p += align256((size_t)B * sizeof(SmoothMeshDev));
+  SmoothMeshDev* tab_c = (SmoothMeshDev*)p;
+  p += align256((size_t)B * sizeof(SmoothMeshDev));
+  int rc = 0;
+  if (!mc.empty()) {
+    if (cudaMemcpyAsync(tab_c, mc.data(), mc.size() * sizeof(SmoothMeshDev), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return -3;
+    for (size_t i0 = 0; i0 < mc.size();) {
+      size_t i1 = i0;
+      while (i1 < mc.size() && mc[i1].cl_size == mc[i0].cl_size) ++i1;
+      SmoothBatchDev c = a;
+      c.mesh = tab_c + i0;
+      c.B = (int32_t)(i1 - i0);
+      rc = form == FORM_SPLIT ? launch_cluster<dd>(c, mc[i0].cl_size, s)
+                              : launch_cluster<float>(c, mc[i0].cl_size, s);
+      if (rc) {
+        // a device without this cluster shape: these meshes take the grid solver
+        cudaGetLastError();
+        for (size_t i = i0; i < i1; ++i) {
+          SmoothMeshDev m = mc[i];
+          m.cl_size = m.cl_planes = 0;
+          m.u0 = U;
+          U += m.nu;
+          mg.push_back(m);
+        }
+        rc = 0;
+      }
+      i0 = i1;
+    }
+  }
+  if (!mg.empty()) {
+    std::vector<int32_t> ub(U);
+    for (size_t b = 0; b < mg.size(); ++b)
+      for (int64_t u = 0; u < mg[b].nu; ++u) ub[mg[b].u0 + u] = (int32_t)b;
+    a.mesh = tab_g;
+    a.unit_bed = (int32_t*)p;
+    p += align256((size_t)U * 4);
+    a.pairs = p;
+    p += align256((size_t)mg.size() * sizeof(MeshState));
+    a.gflag = (int32_t*)p;
+    a.B = (int32_t)mg.size();
+    a.U = U;
+    if (cudaMemcpyAsync(tab_g, mg.data(), mg.size() * sizeof(SmoothMeshDev), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync((void*)a.unit_bed, ub.data(), U * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(a.gflag, 0, 2 * sizeof(int32_t), s) != cudaSuccess)
+      return -3;
+    switch (form) {
+      case FORM_SPLIT: rc = launch_impl<dd>(a, max_blocks, s); break;
+      case FORM_PLAIN: rc = launch_impl<float>(a, max_blocks, s); break;
+      default: rc = launch_impl<double>(a, max_blocks, s); break;
+    }
+  }
+  return rc;
+}
+
+}  // namespace sedi

@@ -38,6 +38,27 @@ void launch_check(const DevState& st, const DevParams& P, unsigned long long con
 // ctl->st = (ctl->st + n) & 1 after n substeps.
 void launch_advance_parity(const DevState& st, int n, cudaStream_t s);
 
+// Ensembles: one launch per phase over every bed (grid.y = bed).
+struct EnsLaunch {
+  const BedView* views;  // [B] device table
+  int32_t B;
+  int64_t max_n;         // largest bed (particles)
+  int64_t max_bins;      // largest bin grid
+  int64_t max_cells;     // largest mesh
+  Ctl* ectl;             // ensemble control: completion counter, rebuild flag
+};
+void launch_check_ens(const EnsLaunch& e, unsigned long long cond_handle, int use_cond,
+                      cudaStream_t s);
+void launch_rebuild_ens(int form, const EnsLaunch& e, int sub_off, cudaStream_t s);
+void launch_advance_ens(const EnsLaunch& e, int n, cudaStream_t s);
+void launch_ctl_gather_ens(const EnsLaunch& e, Ctl* out, cudaStream_t s);
+void launch_substep_ens(int form, const EnsLaunch& e, int sub_off, unsigned long long next_cond,
+                        int use_cond, cudaStream_t s);
+// deposition of every bed (cleared first), fixed point -> smoothing word
+void launch_deposit_ens(int form, const EnsLaunch& e, cudaStream_t s);
+// smoothed eps of every bed -> the drag's mesh word
+void launch_eps_out_ens(int form, const EnsLaunch& e, cudaStream_t s);
+
 // Scatter/gather between the sorted device state and caller order.
 void launch_export(int form, const DevState& st, int what, double* out, cudaStream_t s);
 void launch_import(int form, const DevState& st, const double* x, const double* v,
@@ -50,16 +71,68 @@ void launch_contacts_export(int form, const DevState& st, const DevParams& P,
                             unsigned long long* count, int64_t cap, int64_t* ij, double* xi,
                             cudaStream_t s);
 
-// k_avg.cu: deposition, field conversion, persistent CG smoother, outputs.
+// k_avg.cu: deposition, field conversion, outputs.
 void launch_deposit(int form, const DevState& st, const DevMesh& mesh, const DevParams& P,
                     void* qfields, cudaStream_t s);
 void launch_fields_from_fixed(int form, const void* q, const DevParams& P, void* phi,
                               int nf, cudaStream_t s);
-// Smooth nf fields [nf][C] in place (type by form).  guess may be null.
+// k_smooth.cu: the smoothing solve of a batch of meshes in one persistent launch.
+constexpr int kMaxBeds = 1024;  // meshes in one smoothing launch
+
+// One mesh of a smoothing batch, as the caller describes it.
+struct SmoothMesh {
+  void* phi;          // [nf][C] fields in the smoothing word of the form, in place
+  const void* guess;  // [nf][C] initial guess of the first pseudo-step, or null
+  void* work;         // smooth_mesh_bytes(form, C, nf) bytes of device scratch
+  int* iters;         // [nf] device counters, incremented by the steps taken (or null)
+  int64_t C;
+  int32_t nc[3], per[3];
+  int32_t nf;
+  double coef[3];     // dtau * D_a / h_a^2
+};
+
+// The same, as the kernel sees it (device table, built by launch_smooth_batch).
+struct SmoothMeshDev {
+  void* x;
+  const void* guess;
+  void* b;           // [nf][C] right-hand side (wide word)
+  void* q;           // [C][8] recursive residual (narrow word, fields interleaved)
+  void* d[2];        // [C][8] directions; d[0] also holds the narrow true residual
+  double* part;       // [units][8][3] per-unit sums
+  int* iters;
+  int64_t C, u0, nu;  // cells, first unit, units
+  int32_t nc[3], per[3];
+  double coef[3];
+  double theta, delta, sigma1, sig;  // spectrum [1, lmax]: centre, half width, ratio, rate
+  int32_t cl_size, cl_planes;        // cluster solver: CTAs, z-planes per CTA (0: grid solver)
+};
+
+struct SmoothBatchDev {
+  const SmoothMeshDev* mesh;  // [B]
+  const int32_t* unit_bed;    // [U] mesh of each unit
+  void* pairs;                // [B] per-mesh solver state
+  int32_t* gflag;             // [2] largest step count of a round (alternating slots)
+  int64_t U;
+  int32_t B, nf;
+  double rtol2;
+  int32_t max_iter, n_tau;
+  Ctl* ctl;                   // grid barrier and cg_status
+};
+
+int64_t smooth_units(int64_t C);
+// scratch of one mesh, and of the batch tables
+size_t smooth_mesh_bytes(int form, int64_t C, int nf);
+size_t smooth_batch_bytes(int64_t B, int64_t U);
+// Smooth every mesh's nf fields in place; batch_work: smooth_batch_bytes(B, sum of
+// units) bytes.  Returns 0, -1 (bad sizes) or -3 (launch failed).
+int launch_smooth_batch(int form, const SmoothMesh* meshes, int B, int nf, void* batch_work,
+                        double rtol, int max_iter, int n_tau, Ctl* ctl, int max_blocks,
+                        cudaStream_t s);
+// Single mesh: work holds smooth_work_bytes(form, C, nf) = mesh + batch scratch.
+size_t smooth_work_bytes(int form, int64_t C, int nf);
 int launch_smooth(int form, const DevParams& P, void* phi, const void* guess, int nf,
                   void* work, const DevState& st, int* iters_dev, double rtol, int max_iter,
                   int n_tau, const double coef[3], cudaStream_t s);
-size_t smooth_work_bytes(int form, int64_t C, int nf);
 void launch_average_out(int form, const void* phi, const DevParams& P, void* ufe, double* eps,
                         double* Us, double* F, cudaStream_t s);
 void launch_phi_convert(int form, const void* phi, double* out, int64_t n, int to_double,

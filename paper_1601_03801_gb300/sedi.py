@@ -33,8 +33,9 @@ EXPORTS = [
     "sedi_get_particles", "sedi_compute_forces", "sedi_get_neighbors", "sedi_get_contacts",
     "sedi_save_state", "sedi_load_state", "sedi_get_timings", "sedi_get_stats", "sedi_sync",
     "sedi_last_error", "sedi_smooth_static", "sedi_cnn_set_params", "sedi_cnn_get_params",
-    "sedi_cnn_forward", "sedi_cnn_loss_grad", "sedi_cnn_train",
+    "sedi_cnn_forward", "sedi_cnn_loss_grad", "sedi_cnn_train", "sedi_set_bed",
 ]
+ALL_BEDS = -1  # SEDI_ALL_BEDS
 
 
 class SediParams(C.Structure):
@@ -106,6 +107,7 @@ def lib():
             "sedi_cnn_forward": (C.c_int, [_P, _P, _P, _I]),
             "sedi_cnn_loss_grad": (C.c_int, [_P, _P, _P, _P, _P, _I]),
             "sedi_cnn_train": (C.c_int, [_P, _I, _P, _P, _I, _D, _P, _I]),
+            "sedi_set_bed": (C.c_int, [_P, _I, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -201,7 +203,8 @@ def _mem(*args):
 
 
 class Sedi:
-    """One handle of the library (see include/sedi.h for the semantics)."""
+    """One handle of the library (see include/sedi.h for the semantics).  With
+    params["n_beds"] > 1 it is an ensemble: the per-bed methods take `bed`."""
 
     def __init__(self, params: dict, stream=None):
         self._p = make_params(params)
@@ -210,10 +213,26 @@ class Sedi:
         if rc:
             raise SediError(rc, "sedi_create rejected the parameters")
         self.h = h
-        self.C = int(np.prod(list(self._p.ncell)))
-        self.n = 0
+        self.n_beds = int(self._p.n_beds)
+        c0 = int(np.prod(list(self._p.ncell)))
+        self._C = {b: c0 for b in range(self.n_beds)}
+        self._nc = {b: tuple(self._p.ncell) for b in range(self.n_beds)}
+        self._n = {b: 0 for b in range(self.n_beds)}
         if stream is not None:
             self.set_stream(stream)
+
+    # bed 0 (single-bed handles)
+    @property
+    def n(self):
+        return self._n[0]
+
+    @n.setter
+    def n(self, value):  # after load_state, which restores a particle count the binding cannot see
+        self._n[0] = int(value)
+
+    @property
+    def C(self):
+        return self._C[0]
 
     def close(self):
         if getattr(self, "h", None):
@@ -235,25 +254,35 @@ class Sedi:
         ptr = stream if isinstance(stream, int) else stream.cuda_stream
         self._check(lib().sedi_set_stream(self.h, ptr))
 
-    def set_particles(self, x, v=None, w=None, d=None, rho=None, ids=None):
+    def set_bed(self, bed, lo, hi, ncell):
+        """Box and mesh of ensemble bed `bed` (resets its particles)."""
+        lo_a = (C.c_double * 3)(*lo); hi_a = (C.c_double * 3)(*hi)
+        nc = (C.c_int32 * 3)(*[int(v) for v in ncell])
+        self._check(lib().sedi_set_bed(self.h, int(bed), lo_a, hi_a, nc))
+        self._C[bed] = int(np.prod(ncell))
+        self._nc[bed] = tuple(int(v) for v in ncell)
+        self._n[bed] = 0
+
+    def set_particles(self, x, v=None, w=None, d=None, rho=None, ids=None, bed=0):
         n = (x.shape[0] if hasattr(x, "shape") else len(x))
         ax = _Arg(x, np.float64, (n, 3)); av = _Arg(v, np.float64, (n, 3))
         aw = _Arg(w, np.float64, (n, 3)); ad = _Arg(d, np.float64, (n,))
         ar = _Arg(rho, np.float64, (n,)); ai = _Arg(ids, np.int64, (n,))
         mem = _mem(ax, av, aw, ad, ar, ai)
-        self._check(lib().sedi_set_particles(self.h, 0, n, ai.ptr, ax.ptr, av.ptr, aw.ptr, ad.ptr,
-                                             ar.ptr, mem))
-        self.n = n
+        self._check(lib().sedi_set_particles(self.h, int(bed), n, ai.ptr, ax.ptr, av.ptr, aw.ptr,
+                                             ad.ptr, ar.ptr, mem))
+        self._n[bed] = n
 
-    def set_fluid(self, U=None, grad_p=None, DUDt=None):
-        nc = (C.c_int32 * 3)(*self._p.ncell)
-        au = _Arg(U, np.float64, (self.C, 3)); ag = _Arg(grad_p, np.float64, (self.C, 3))
-        ad = _Arg(DUDt, np.float64, (self.C, 3))
-        self._check(lib().sedi_set_fluid(self.h, 0, nc, au.ptr, ag.ptr, ad.ptr, _mem(au, ag, ad)))
+    def set_fluid(self, U=None, grad_p=None, DUDt=None, bed=0):
+        Cb = self._C[bed]
+        nc = (C.c_int32 * 3)(*self._nc[bed])
+        au = _Arg(U, np.float64, (Cb, 3)); ag = _Arg(grad_p, np.float64, (Cb, 3))
+        ad = _Arg(DUDt, np.float64, (Cb, 3))
+        self._check(lib().sedi_set_fluid(self.h, int(bed), nc, au.ptr, ag.ptr, ad.ptr, _mem(au, ag, ad)))
 
-    def set_eps(self, eps):
-        a = _Arg(eps, np.float64, (self.C,))
-        self._check(lib().sedi_set_eps(self.h, 0, a.ptr, a.mem))
+    def set_eps(self, eps, bed=0):
+        a = _Arg(eps, np.float64, (self._C[bed],))
+        self._check(lib().sedi_set_eps(self.h, int(bed), a.ptr, a.mem))
 
     def step(self, n_substeps=1):
         self._check(lib().sedi_step(self.h, int(n_substeps)))
@@ -261,65 +290,71 @@ class Sedi:
     def sync(self):
         self._check(lib().sedi_sync(self.h))
 
-    def average(self, eps=None, Us=None, F=None):
+    def average(self, eps=None, Us=None, F=None, bed=0):
         """Into given outputs (numpy or CUDA tensors), else new numpy arrays."""
+        Cb = self._C[bed]
         if eps is None and Us is None and F is None:
-            eps = np.zeros(self.C); Us = np.zeros((self.C, 3)); F = np.zeros((self.C, 3))
+            eps = np.zeros(Cb); Us = np.zeros((Cb, 3)); F = np.zeros((Cb, 3))
         a = [_Arg(o, np.float64, s, writable=True) for o, s in
-             ((eps, (self.C,)), (Us, (self.C, 3)), (F, (self.C, 3)))]
-        self._check(lib().sedi_average(self.h, 0, a[0].ptr, a[1].ptr, a[2].ptr, _mem(*a)))
+             ((eps, (Cb,)), (Us, (Cb, 3)), (F, (Cb, 3)))]
+        self._check(lib().sedi_average(self.h, int(bed), a[0].ptr, a[1].ptr, a[2].ptr, _mem(*a)))
         return eps, Us, F
 
     def average_inplace(self):
-        """Averaging whose only output is the drag's solid fraction on the device."""
-        self._check(lib().sedi_average(self.h, 0, None, None, None, MEM_HOST))
+        """Averaging whose only output is the drag's solid fraction on the device
+        (every bed of an ensemble)."""
+        bed = ALL_BEDS if self.n_beds > 1 else 0
+        self._check(lib().sedi_average(self.h, bed, None, None, None, MEM_HOST))
 
-    def deposit(self):
-        q = np.zeros((7, self.C), dtype=np.int64)
-        self._check(lib().sedi_deposit(self.h, 0, q.ctypes.data, MEM_HOST))
+    def deposit(self, bed=0):
+        q = np.zeros((7, self._C[bed]), dtype=np.int64)
+        self._check(lib().sedi_deposit(self.h, int(bed), q.ctypes.data, MEM_HOST))
         return q
 
-    def smooth(self, phi, guess=None):
-        phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(-1, self.C)
+    def smooth(self, phi, guess=None, bed=0):
+        Cb = self._C[bed]
+        phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(-1, Cb)
         nf = phi.shape[0]
         out = np.zeros_like(phi)
-        g = None if guess is None else np.ascontiguousarray(guess, dtype=np.float64).reshape(nf, self.C)
+        g = None if guess is None else np.ascontiguousarray(guess, dtype=np.float64).reshape(nf, Cb)
         iters = np.zeros(nf, dtype=np.int32)
-        self._check(lib().sedi_smooth(self.h, 0, nf, phi.ctypes.data, out.ctypes.data,
+        self._check(lib().sedi_smooth(self.h, int(bed), nf, phi.ctypes.data, out.ctypes.data,
                                       None if g is None else g.ctypes.data, iters.ctypes.data,
                                       MEM_HOST))
         return out, iters
 
-    def get_particles(self):
-        x, v, w, a = (np.zeros((self.n, 3)) for _ in range(4))
-        self._check(lib().sedi_get_particles(self.h, 0, x.ctypes.data, v.ctypes.data,
+    def get_particles(self, bed=0):
+        n = self._n[bed]
+        x, v, w, a = (np.zeros((n, 3)) for _ in range(4))
+        self._check(lib().sedi_get_particles(self.h, int(bed), x.ctypes.data, v.ctypes.data,
                                              w.ctypes.data, a.ctypes.data, MEM_HOST))
         return x, v, w, a
 
-    def get_positions(self, out):
-        a = _Arg(out, np.float64, (self.n, 3), writable=True)
-        self._check(lib().sedi_get_particles(self.h, 0, a.ptr, None, None, None, a.mem))
+    def get_positions(self, out, bed=0):
+        a = _Arg(out, np.float64, (self._n[bed], 3), writable=True)
+        self._check(lib().sedi_get_particles(self.h, int(bed), a.ptr, None, None, None, a.mem))
         return out
 
-    def compute_forces(self):
-        out = {k: np.zeros((self.n, 3)) for k in ("contact", "lub", "fluid", "torque")}
-        self._check(lib().sedi_compute_forces(self.h, 0, out["contact"].ctypes.data,
+    def compute_forces(self, bed=0):
+        n = self._n[bed]
+        out = {k: np.zeros((n, 3)) for k in ("contact", "lub", "fluid", "torque")}
+        self._check(lib().sedi_compute_forces(self.h, int(bed), out["contact"].ctypes.data,
                                               out["lub"].ctypes.data, out["fluid"].ctypes.data,
                                               out["torque"].ctypes.data, MEM_HOST))
         return out
 
-    def neighbors(self):
-        off = np.zeros(self.n + 1, dtype=np.int64)
-        tot = self._check(lib().sedi_get_neighbors(self.h, 0, off.ctypes.data, None, 0))
+    def neighbors(self, bed=0):
+        off = np.zeros(self._n[bed] + 1, dtype=np.int64)
+        tot = self._check(lib().sedi_get_neighbors(self.h, int(bed), off.ctypes.data, None, 0))
         ids = np.zeros(max(tot, 1), dtype=np.int64)
-        tot = self._check(lib().sedi_get_neighbors(self.h, 0, off.ctypes.data, ids.ctypes.data, tot))
+        tot = self._check(lib().sedi_get_neighbors(self.h, int(bed), off.ctypes.data, ids.ctypes.data, tot))
         return off, ids[:tot]
 
-    def contacts(self):
-        cap = max(16, 8 * self.n)
+    def contacts(self, bed=0):
+        cap = max(16, 8 * self._n[bed])
         while True:
             ij = np.zeros((cap, 2), dtype=np.int64); xi = np.zeros((cap, 3))
-            rc = lib().sedi_get_contacts(self.h, 0, cap, ij.ctypes.data, xi.ctypes.data)
+            rc = lib().sedi_get_contacts(self.h, int(bed), cap, ij.ctypes.data, xi.ctypes.data)
             if rc == -4:
                 cap *= 4
                 continue

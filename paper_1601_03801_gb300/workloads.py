@@ -282,7 +282,7 @@ def _library_tag():
     return h.hexdigest()[:12]
 
 
-def settle_bed(prm, parts, substeps=20_000, chunk=1000, log=None):
+def settle_bed(prm, parts, substeps=40_000, chunk=2000, log=None):
     """Settling prep run of the method itself (on the GPU, not timed): the packed bed
     falls into load-bearing contact under gravity in quiescent water, with
     lubrication off and a low restitution so the run dissipates quickly.  Returns
@@ -318,6 +318,54 @@ def hashlib_of(*arrays):
     for a in arrays:
         h.update(np.ascontiguousarray(a).tobytes())
     return h.hexdigest()[:12]
+
+
+def lattice_bed(n, L, d, seed, jitter=0.01, spacing=1.05):
+    """n spheres of diameter d on a square lattice filling a periodic L x L footprint
+    layer by layer from the wall z = 0 (spacing >= `spacing` d in every direction),
+    each moved by a uniform jitter of at most `jitter` d per axis (no overlaps while
+    spacing - 2 sqrt(3) jitter > 1)."""
+    rng = _rng(seed)
+    m = int(np.floor(L / (spacing * d)))
+    a = L / m                    # in-plane spacing (>= 1.05 d, periodic-consistent)
+    per_layer = m * m
+    k = np.arange(n)
+    layer, r = k // per_layer, k % per_layer
+    ix, iy = r % m, r // m
+    x = np.stack([(ix + 0.5) * a, (iy + 0.5) * a, 0.5 * d + 0.05 * d + layer * spacing * d], axis=1)
+    x += rng.uniform(-jitter * d, jitter * d, size=x.shape)
+    x[:, 0] = np.mod(x[:, 0], L)
+    x[:, 1] = np.mod(x[:, 1], L)
+    x[:, :2] = np.where(x[:, :2] >= L, x[:, :2] - L, x[:, :2])
+    return x
+
+
+def ensemble_case(n_beds=256, seed=1601038014, n_min=2000, n_max=50000, d=0.5e-3, spacing=1.05,
+                  jitter=0.01):
+    """Ensemble of independent beds of uneven size: N_b = round(exp(U[ln n_min,
+    ln n_max])), monodisperse d, a cubic periodic-x/y, wall-z box of n_b mm with an
+    n_b^3 mesh (1 mm cells), n_b = 16 + round(32 (ln N_b - ln n_min) / (ln n_max -
+    ln n_min)); the bed is a jittered lattice from the wall (height proportional
+    to N_b / n_b^2) under the log-law flow of the 200k bed (u* = 0.02 m/s).
+    Returns the shared parameters and a list of beds (box, mesh, parts, U)."""
+    rng = _rng(seed)
+    lnmin, lnmax = np.log(n_min), np.log(n_max)
+    prm = default_params(wall_hi=(0, 0, 0), bandwidth=(3 * d,) * 3)
+    beds = []
+    for b in range(n_beds):
+        t = rng.uniform(lnmin, lnmax)
+        nb = int(round(np.exp(t)))
+        side = 16 + int(round(32 * (t - lnmin) / (lnmax - lnmin)))
+        L = side * 1e-3
+        x = lattice_bed(nb, L, d, seed + 1 + b, jitter=jitter, spacing=spacing)
+        lo, hi = (0.0, 0.0, 0.0), (L, L, L)
+        ncell = (side, side, side)
+        z_bed = float(x[:, 2].max() + 0.5 * d)
+        U = log_law(ncell, lo, hi, z_bed, 0.02, d / 30.0)
+        parts = dict(x=x, v=np.zeros((nb, 3)), w=np.zeros((nb, 3)), d=np.full(nb, d),
+                     rho=np.full(nb, 2500.0))
+        beds.append(dict(lo=lo, hi=hi, ncell=ncell, parts=parts, U=U, z_bed=z_bed))
+    return prm, beds
 
 
 def _gauss_filter_periodic(f, sigma_cells):

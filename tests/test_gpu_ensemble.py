@@ -1,0 +1,120 @@
+"""Ensembles of independent beds (n_beds > 1): one launch per phase over all beds
+must give every bed exactly the bits it gets when run alone in a single-bed
+handle (whose parity with the oracle the other GPU tests establish)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1601_03801_gb300 import sedi  # noqa: E402
+from paper_1601_03801_gb300.workloads import ensemble_case  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ens():
+    # five beds of 300..3000 spheres on 16..48 mm meshes; a tight jittered lattice
+    # so pairs are in contact from the first substep
+    prm, beds = ensemble_case(n_beds=5, seed=77, n_min=300, n_max=3000, spacing=1.002, jitter=0.02)
+    rng = np.random.default_rng(5)
+    for bd in beds:
+        bd["parts"]["v"] = rng.normal(0.0, 0.05, bd["parts"]["x"].shape)
+    return prm, beds
+
+
+def make_ensemble(prm, beds, **extra):
+    g = sedi.Sedi(dict(prm, n_beds=len(beds), precision_form="split", **extra))
+    for b, bd in enumerate(beds):
+        g.set_bed(b, bd["lo"], bd["hi"], bd["ncell"])
+        p = bd["parts"]
+        g.set_particles(p["x"], p["v"], p["w"], p["d"], p["rho"], bed=b)
+        g.set_fluid(U=bd["U"], bed=b)
+    return g
+
+
+def make_single(prm, bd, **extra):
+    g = sedi.Sedi(dict(prm, lo=bd["lo"], hi=bd["hi"], ncell=bd["ncell"], precision_form="split", **extra))
+    p = bd["parts"]
+    g.set_particles(p["x"], p["v"], p["w"], p["d"], p["rho"])
+    g.set_fluid(U=bd["U"])
+    return g
+
+
+def run(g, beds_idx, single):
+    g.average_inplace()
+    for _ in range(3):
+        g.step(20)
+        g.average_inplace()
+    g.step(20)
+    out = []
+    for b in beds_idx:
+        kw = {} if single else {"bed": b}
+        x, v, w, a = g.get_particles(**kw)
+        eps, Us, F = g.average(**kw)
+        out.append((x, v, w, a, eps, Us, F))
+    return out
+
+
+def test_ensemble_bit_identical_to_single_beds(ens):
+    prm, beds = ens
+    E = make_ensemble(prm, beds)
+    got = run(E, range(len(beds)), single=False)
+    st = E.stats()
+    assert st["substeps"] == 80 and st["averages"] >= 4 and st["cg_iterations"] > 0
+    contacts = 0
+    for b, bd in enumerate(beds):
+        S = make_single(prm, bd)
+        want = run(S, [0], single=True)[0]
+        for k, (p, q) in enumerate(zip(got[b], want)):
+            assert np.array_equal(p, q), (b, k)
+        contacts += len(E.contacts(bed=b)[0])
+    assert contacts > 0
+
+
+def test_ensemble_graphs_equal_plain_launches(ens):
+    prm, beds = ens
+    res = []
+    for graphs in (1, 0):
+        E = make_ensemble(prm, beds, use_graphs=graphs)
+        res.append(run(E, range(len(beds)), single=False))
+    for a, b in zip(res[0], res[1]):
+        for p, q in zip(a, b):
+            assert np.array_equal(p, q)
+
+
+def test_ensemble_checkpoint_resume(ens, tmp_path):
+    prm, beds = ens
+    E = make_ensemble(prm, beds)
+    E.average_inplace()
+    E.step(30)
+    E.save_state(tmp_path / "ens.ck")
+    E.step(25)
+    want = [E.get_particles(bed=b) for b in range(len(beds))]
+    R = make_ensemble(prm, beds)
+    R.load_state(tmp_path / "ens.ck")
+    R.step(25)
+    for b in range(len(beds)):
+        for p, q in zip(want[b], R.get_particles(bed=b)):
+            assert np.array_equal(p, q), b
+
+
+def test_ensemble_errors(ens):
+    prm, beds = ens
+    E = sedi.Sedi(dict(prm, n_beds=3, precision_form="split"))
+    p = beds[0]["parts"]
+    E.set_bed(0, beds[0]["lo"], beds[0]["hi"], beds[0]["ncell"])
+    E.set_particles(p["x"], p["v"], p["w"], p["d"], p["rho"], bed=0)
+    with pytest.raises(sedi.SediError) as e:
+        E.step(1)  # beds 1 and 2 have no particles
+    assert e.value.code == -9
+    with pytest.raises(sedi.SediError) as e:
+        E.set_particles(p["x"], p["v"], p["w"], p["d"], p["rho"], bed=3)
+    assert e.value.code == -1
+    single = sedi.Sedi(dict(prm, precision_form="split"))
+    with pytest.raises(sedi.SediError):
+        single.set_bed(0, beds[0]["lo"], beds[0]["hi"], beds[0]["ncell"])
+    with pytest.raises(sedi.SediError):
+        sedi.Sedi(dict(prm, n_beds=2000))
