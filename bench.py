@@ -222,9 +222,10 @@ def gpu_arm(args):
     phases = {k: round((t1[k] - t0[k]) / args.steps, 4) for k in
               ("rebuild_ms", "substep_ms", "deposit_ms", "smooth_ms")}
     rebuilds = st1["rebuilds"] - st0["rebuilds"]
-    # kernels per step: 20 x (check + substep) + deposit, from_fixed, barrier reset,
-    # smoother, outputs; 12 per rebuild taken
-    launches = args.steps * (2 * SUBSTEPS + 5) + 12 * rebuilds
+    # kernels per step: the graph's rebuild check + 20 substep kernels (+ 11 rebuild
+    # kernels per rebuild taken), then deposition, fixed point -> smoothing word, the
+    # cluster smoother (one launch) and the outputs
+    launches = args.steps * (1 + SUBSTEPS + 4) + 11 * rebuilds
 
     # end-to-end through the C ABI with host buffers: per step the fluid fields go
     # host -> device (pinned) and the averaged fields come back

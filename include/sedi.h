@@ -100,11 +100,13 @@ typedef struct sedi_params {
   int32_t substep_variant;                 /* launch shape of the fused substep kernel:
                                               -1 = autotuned at the first sedi_step [-1];
                                               0: 128 threads, 6 blocks/SM; 1: 64 x 12;
-                                              2: 256 x 3; 3: 128 x 8; 4: 128 x 5.  In the
-                                              split form results are bit-identical across
-                                              variants; in the plain form they agree to
-                                              FP32 rounding.  The FP64 parity form always
-                                              runs variant 0. */
+                                              2: 256 x 3; 3: 128 x 8; 4: 128 x 5, all with
+                                              the warp-cooperative pair phase; 5: 128 x 6
+                                              with a per-particle pair loop.  The split
+                                              form gives bit-identical results across
+                                              variants, the plain form agrees to FP32
+                                              rounding.  The FP64 parity form always runs
+                                              the loop. */
   int32_t n_beds;                          /* independent beds in this handle, 1..1024
                                               (see "Ensembles" below) [1] */
   int32_t profile;                         /* record CUDA events around each phase
@@ -160,7 +162,8 @@ int sedi_set_stream(sedi_handle* h, void* cuda_stream);
  * first if a step happened since).  Every bed must have particles before the
  * first step.  A bed's results are bit-identical to running it alone in a
  * single-bed handle.  Not for ensembles: params.use_cnn_guess (learned warm
- * start) and the substep autotuner (ensembles run 128-thread blocks). */
+ * start) and the substep autotuner (ensembles run substep variant 5: 128-thread
+ * blocks with the per-particle pair loop). */
 
 /* Box [lo, hi) and mesh ncell of ensemble bed `bed`; resets that bed (its
    particles must be set again).  Errors: EINVAL (not an ensemble, bed out of

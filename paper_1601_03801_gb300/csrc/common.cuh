@@ -243,7 +243,7 @@ struct DevState {
   uint32_t* wmask[2]; // bit w: wall spring w in use (pb parity)
   int32_t* nbr[2];    // [cap][N] list entry: partner index | first-in-pair bit (nl parity)
   int32_t* nn[2];     // [N] list length (nl parity)
-  void* hist[2];      // S [3][cap][N] pair springs (nl parity)
+  void* hist[2];      // Quad<S> [cap][N] pair springs (x, y, z, 0) (nl parity)
   uint32_t* cmask[2]; // bit k: slot k holds a spring (nl parity)
   // binning scratch
   int32_t* bin_of;    // [N]

@@ -358,7 +358,7 @@ int alloc_particles(sedi_handle* h, int64_t N, double rmax) {
     if ((rc = dmalloc(h, h->part_allocs, (void**)&st.wmask[b], 4 * N))) return rc;
     if ((rc = dmalloc(h, h->part_allocs, (void**)&st.nbr[b], 4 * cap * N))) return rc;
     if ((rc = dmalloc(h, h->part_allocs, (void**)&st.nn[b], 4 * N))) return rc;
-    if ((rc = dmalloc(h, h->part_allocs, &st.hist[b], 3 * w * cap * N))) return rc;
+    if ((rc = dmalloc(h, h->part_allocs, &st.hist[b], q * cap * N))) return rc;
     if ((rc = dmalloc(h, h->part_allocs, (void**)&st.cmask[b], 4 * N))) return rc;
   }
   // bins: edge >= the largest list cutoff (2 r_max (1 + f) + skin) with margin
@@ -1594,7 +1594,7 @@ int state_io(sedi_handle* h, FILE* f, bool save) {
       {s.vfrac[c.pb], 8 * (size_t)N}, {s.xb[c.pb], 16 * (size_t)N},
       {s.whist[c.pb], (size_t)kWalls * 3 * w * N}, {s.wmask[c.pb], 4 * (size_t)N},
       {s.nbr[c.nl], 4 * (size_t)cap * N}, {s.nn[c.nl], 4 * (size_t)N},
-      {s.hist[c.nl], 3 * w * cap * N}, {s.cmask[c.nl], 4 * (size_t)N},
+      {s.hist[c.nl], q * cap * N}, {s.cmask[c.nl], 4 * (size_t)N},
       {h->mesh.ufe, fq * C}, {h->mesh.gfl, fq * C}};
   for (auto& it : items)
     if ((rc = dev_io(h, f, it.p, it.n, save))) return rc;
@@ -1887,7 +1887,7 @@ int sedi_get_stats(sedi_handle* h, sedi_stats* out) {
       st.max_neighbors = std::max(st.max_neighbors, b->stats.max_neighbors);
     }
     st.nbr_capacity = h->P.cap;
-    st.substep_variant = SUBSTEP_B128;
+    st.substep_variant = SUBSTEP_B128_LOOP;
     st.substep_block = 128;
     *out = st;
     return rc;

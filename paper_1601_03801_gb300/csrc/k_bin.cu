@@ -336,8 +336,8 @@ __device__ __forceinline__ void remap_body(const DevState& st, const DevParams& 
   const int pb = st.ctl->pb, qb = pb ^ 1;
   const int nl = st.ctl->nl, ql = nl ^ 1;
   const int64_t N = st.N, cap = P.cap;
-  const S* hold = (const S*)st.hist[nl];
-  S* hnew = (S*)st.hist[ql];
+  const Quad<S>* hold = (const Quad<S>*)st.hist[nl];
+  Quad<S>* hnew = (Quad<S>*)st.hist[ql];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t o = st.order[i];
@@ -351,8 +351,7 @@ __device__ __forceinline__ void remap_body(const DevState& st, const DevParams& 
         for (int kk = 0; kk < onn; ++kk) {
           if (!((omask >> kk) & 1u)) continue;
           if (st.uid[pb][nbr_index(st.nbr[nl][(int64_t)kk * N + o])] != uj) continue;
-          for (int c = 0; c < 3; ++c)
-            hnew[((int64_t)c * cap + k) * N + i] = hold[((int64_t)c * cap + kk) * N + o];
+          stq(hnew + (int64_t)k * N + i, ldq(hold + (int64_t)kk * N + o));
           nmask |= 1u << k;
           break;
         }
@@ -693,7 +692,7 @@ __global__ void k_contacts(DevState st, DevParams P, unsigned long long* count, 
                            int64_t* ij, double* xi) {
   using S = typename Traits<FORM>::S;
   const int pb = st.ctl->pb, nl = st.ctl->nl;
-  const S* hist = (const S*)st.hist[nl];
+  const Quad<S>* hist = (const Quad<S>*)st.hist[nl];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < st.N;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t m = st.cmask[nl][i];
@@ -708,8 +707,10 @@ __global__ void k_contacts(DevState st, DevParams P, unsigned long long* count, 
       if ((int64_t)slot >= cap) continue;
       ij[2 * slot] = ui;
       ij[2 * slot + 1] = uj;
-      for (int c = 0; c < 3; ++c)
-        xi[3 * slot + c] = Num<S>::d(hist[((int64_t)c * P.cap + k) * st.N + i]);
+      const Quad<S> h = ldq(hist + (int64_t)k * st.N + i);
+      xi[3 * slot + 0] = Num<S>::d(h.a);
+      xi[3 * slot + 1] = Num<S>::d(h.b);
+      xi[3 * slot + 2] = Num<S>::d(h.c);
     }
   }
 }

@@ -95,6 +95,104 @@ __device__ __forceinline__ V3<F> cross(V3<F> a, V3<F> b) {
   return V3<F>{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
 
+// Contribution of one listed partner (list entry e in slot k of owner i) to the
+// owner's accumulators: fa (contact force, signed for the owner), t (contact torque
+// on the owner), l (lubrication force on the owner).  The pair is evaluated in
+// canonical order (lower caller index first), so both sides get bitwise opposite
+// forces.  When INTEGRATE, the owner's tangential spring of slot k is updated.
+template <class F>
+struct PairOut {
+  V3<F> fa, t, l;
+  bool contact, lub;
+};
+
+template <int FORM, bool INTEGRATE>
+__device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
+    const DevParams& P, const Quad<typename Traits<FORM>::S>& Pi,
+    const typename Traits<FORM>::F* vi, const typename Traits<FORM>::F* wi,
+    typename Traits<FORM>::F mi, int32_t e, int k, bool has, int64_t i, int64_t N,
+    const Quad<typename Traits<FORM>::S>* pos, const Quad<typename Traits<FORM>::S>* vel,
+    const Quad<typename Traits<FORM>::S>* omg, Quad<typename Traits<FORM>::S>* hist) {
+  using S = typename Traits<FORM>::S;
+  using F = typename Traits<FORM>::F;
+  using NS = Num<S>;
+  const ForceConsts<F>& K = fconsts<F>(P);
+  const BoxS<S>& B = sbox<S>(P);
+  PairOut<F> o;
+  o.contact = o.lub = false;
+  const int j = nbr_index(e);
+  const Quad<S> Pj = ldq(pos + j);
+  const bool i_lo = nbr_first(e);
+  const Quad<S>& A = i_lo ? Pi : Pj;
+  const Quad<S>& Bq = i_lo ? Pj : Pi;
+  // precise geometry in canonical order: dx = x_B - x_A (minimum image)
+  S dxs[3] = {NS::subq(Bq.a, A.a), NS::subq(Bq.b, A.b), NS::subq(Bq.c, A.c)};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (!P.periodic[a]) continue;
+    F c = NS::f(dxs[a]);
+    if (c > K.halfL[a]) dxs[a] = NS::subq(dxs[a], B.L[a]);
+    else if (c < -K.halfL[a]) dxs[a] = NS::addq(dxs[a], B.L[a]);
+  }
+  S d2 = NS::addq(NS::addq(NS::mul(dxs[0], dxs[0]), NS::mul(dxs[1], dxs[1])), NS::mul(dxs[2], dxs[2]));
+  S ssum = NS::addq(A.d, Bq.d);
+  S num = NS::subq(NS::mul(ssum, ssum), d2);
+  const F dist = xsqrt(NS::f(d2));
+  const F sF = NS::f(ssum);
+  // r_A + r_B - |dx| without cancellation: (s^2 - d^2) / (s + d)
+  const F delta = NS::kExtended ? NS::f(num) / (sF + dist) : sF - dist;
+  const F dxf[3] = {NS::f(dxs[0]), NS::f(dxs[1]), NS::f(dxs[2])};
+  o.contact = delta > F(0);
+  o.lub = P.lubrication && (-delta < K.lub_out * sF);
+  if (!o.contact && !o.lub) return o;
+  const F inv_d = F(1) / dist;
+  const V3<F> n{dxf[0] * inv_d, dxf[1] * inv_d, dxf[2] * inv_d};
+  const Quad<S> Vj = ldq(vel + j);
+  const F vj[3] = {NS::f(Vj.a), NS::f(Vj.b), NS::f(Vj.c)};
+  const F* vA = i_lo ? vi : vj;
+  const F* vB = i_lo ? vj : vi;
+  if (o.contact) {
+    const Quad<S> Wj = ldq(omg + j);
+    const F wj[3] = {NS::f(Wj.a), NS::f(Wj.b), NS::f(Wj.c)};
+    const F* wA = i_lo ? wi : wj;
+    const F* wB = i_lo ? wj : wi;
+    const F rA = NS::f(A.d), rB = NS::f(Bq.d);
+    const F mA = i_lo ? mi : NS::f(Vj.d);
+    const F mB = i_lo ? NS::f(Vj.d) : mi;
+    const F Rs = rA * rB / (rA + rB);
+    const F ms = mA * mB / (mA + mB);
+    const F la = rA - F(0.5) * delta, lb = rB - F(0.5) * delta;
+    V3<F> om{la * wA[0] + lb * wB[0], la * wA[1] + lb * wB[1], la * wA[2] + lb * wB[2]};
+    V3<F> wxn = cross(om, n);
+    V3<F> vrel{vA[0] - vB[0] + wxn.x, vA[1] - vB[1] + wxn.y, vA[2] - vB[2] + wxn.z};
+    S xo[3], xn_[3];
+    if (has) {
+      const Quad<S> h = ldq(hist + (int64_t)k * N + i);
+      xo[0] = h.a;
+      xo[1] = h.b;
+      xo[2] = h.c;
+    }
+    V3<F> Ft;
+    V3<F> FA = hm_core<S, F>(K, n, delta, Rs, ms, vrel, xo, has, &Ft, xn_);
+    if (INTEGRATE) stq(hist + (int64_t)k * N + i, Quad<S>{xn_[0], xn_[1], xn_[2], NS::from_f(F(0))});
+    const F lev = i_lo ? la : lb;
+    o.t = cross(V3<F>{lev * n.x, lev * n.y, lev * n.z}, Ft);
+    o.fa = i_lo ? FA : V3<F>{-FA.x, -FA.y, -FA.z};
+  }
+  if (o.lub) {
+    const F h = -delta;
+    const F hin = K.lub_in * sF;
+    const F hh = h > hin ? h : hin;
+    const F rA = NS::f(A.d), rB = NS::f(Bq.d);
+    const F Rl = rA * rB / (rA + rB);
+    const F vn = (vA[0] - vB[0]) * n.x + (vA[1] - vB[1]) * n.y + (vA[2] - vB[2]) * n.z;
+    F sl = -K.six_pi_mu * Rl * Rl * vn / hh;
+    if (!i_lo) sl = -sl;
+    o.l = V3<F>{sl * n.x, sl * n.y, sl * n.z};
+  }
+  return o;
+}
+
 }  // namespace
 
 // BS threads per block, at least MINB resident blocks per SM (which caps the
@@ -103,7 +201,7 @@ __device__ __forceinline__ V3<F> cross(V3<F> a, V3<F> b) {
 // Body of the fused substep for one bed: blk is the block's index within the bed,
 // nblk the bed's block count; ectl (ensembles only) collects the rebuild decision
 // of all nbeds beds for the graph condition of the next substep.
-template <int FORM, bool INTEGRATE, int BS>
+template <int FORM, bool INTEGRATE, int BS, bool COOP>
 __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& mesh,
                                              const DevParams& P, int sub_off,
                                              cudaGraphConditionalHandle next, int use_cond,
@@ -119,136 +217,152 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
   const int nl = ctl->nl;
   const int64_t N = st.N;
   const int64_t i = blk * BS + threadIdx.x;
+  const bool valid = i < N;
   float my_disp2 = 0.0f;
-  if (i < N) {
-    const Quad<S>* pos = (const Quad<S>*)st.pos[sb];
-    const Quad<S>* vel = (const Quad<S>*)st.vel[sb];
-    const Quad<S>* omg = (const Quad<S>*)st.omg[sb];
-    Quad<S> Pi = ldq(pos + i), Vi = ldq(vel + i), Wi = ldq(omg + i);
-    Quad<F>* accp = (Quad<F>*)st.acc[pb];
-    Quad<F> Ai = ldq(accp + i);
-    const F ri = NS::f(Pi.d), mi = NS::f(Vi.d);
-    const F vi[3] = {NS::f(Vi.a), NS::f(Vi.b), NS::f(Vi.c)};
-    const F wi[3] = {NS::f(Wi.a), NS::f(Wi.b), NS::f(Wi.c)};
-    V3<F> fc{0, 0, 0}, fl{0, 0, 0}, tq{0, 0, 0};
-    const int32_t* nbr = st.nbr[nl];
+  const Quad<S>* pos = (const Quad<S>*)st.pos[sb];
+  const Quad<S>* vel = (const Quad<S>*)st.vel[sb];
+  const Quad<S>* omg = (const Quad<S>*)st.omg[sb];
+  Quad<F>* accp = (Quad<F>*)st.acc[pb];
+  const int32_t* nbr = st.nbr[nl];
+  Quad<S>* hist = (Quad<S>*)st.hist[nl];
+  Quad<S> Pi{}, Vi{}, Wi{};
+  Quad<F> Ai{};
+  F ri = F(0), mi = F(0);
+  F vi[3] = {F(0), F(0), F(0)}, wi[3] = {F(0), F(0), F(0)};
+  V3<F> fc{0, 0, 0}, fl{0, 0, 0}, tq{0, 0, 0};
+  uint32_t mask = 0, nmask = 0, live = 0;
+  if (valid) {
+    Pi = ldq(pos + i);
+    Vi = ldq(vel + i);
+    Wi = ldq(omg + i);
+    Ai = ldq(accp + i);
+    ri = NS::f(Pi.d);
+    mi = NS::f(Vi.d);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      vi[a] = NS::f(a == 0 ? Vi.a : (a == 1 ? Vi.b : Vi.c));
+      wi[a] = NS::f(a == 0 ? Wi.a : (a == 1 ? Wi.b : Wi.c));
+    }
     const int nn = st.nn[nl][i];
-    const uint32_t mask = st.cmask[nl][i];
-    uint32_t nmask = 0;
-    S* hist = (S*)st.hist[nl];
-    const int64_t cap = P.cap;
+    mask = st.cmask[nl][i];
     const float lub_out_f = P.lub_out_f;
     // phase 1: cheap FP32 cull of every listed partner (relative margin; the exact
     // test follows); four candidates per round so their gathers overlap
-    uint32_t live = 0;
+    const float rif = (float)ri;
+    const float fac = P.lubrication ? (1.0f + lub_out_f) : 1.0f;
+    for (int k0 = 0; k0 < nn; k0 += 4) {
+      int32_t ev[4];
+      Quad<S> Pv[4];
+      const int32_t* ep = nbr + (int64_t)k0 * N + i;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ev[u] = k0 + u < nn ? ep[u * N] : 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) Pv[u] = ldq(pos + (k0 + u < nn ? nbr_index(ev[u]) : (int)i));
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float dx = (float)NS::dif(Pv[u].a, Pi.a), dy = (float)NS::dif(Pv[u].b, Pi.b),
+              dz = (float)NS::dif(Pv[u].c, Pi.c);
+        if (P.periodic[0]) dx = dx > P.cf.halfL[0] ? dx - P.cf.L[0] : (dx < -P.cf.halfL[0] ? dx + P.cf.L[0] : dx);
+        if (P.periodic[1]) dy = dy > P.cf.halfL[1] ? dy - P.cf.L[1] : (dy < -P.cf.halfL[1] ? dy + P.cf.L[1] : dy);
+        if (P.periodic[2]) dz = dz > P.cf.halfL[2] ? dz - P.cf.L[2] : (dz < -P.cf.halfL[2] ? dz + P.cf.L[2] : dz);
+        const float cut = (rif + (float)NS::f(Pv[u].d)) * fac;
+        if (k0 + u < nn && dx * dx + dy * dy + dz * dz <= cut * cut * 1.0002f) live |= 1u << (k0 + u);
+      }
+    }
+  }
+  // phase 2: interacting pairs only, in slot order
+  if constexpr (COOP) {
+    // warp-cooperative: the warp's (owner lane, slot) pairs are queued in slot order
+    // and evaluated 32 at a time, one per lane; each owner then adds its results in
+    // queue order, i.e. the same additions in the same order as the loop below
+    constexpr int W = BS / 32;
+    __shared__ uint16_t q_pair[W][1024];
+    __shared__ Quad<S> q_pi[W][32];
+    __shared__ F q_vw[W][32][8];  // vi, wi, mi, (pad)
+    __shared__ uint32_t q_mask[W][32];
+    __shared__ F q_res[W][32][9];
+    __shared__ uint8_t q_flag[W][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int cnt = __popc(live);
+    int off = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, off, o);
+      if (lane >= o) off += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, off, 31);
+    off -= cnt;  // exclusive prefix
+    q_pi[wid][lane] = Pi;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      q_vw[wid][lane][a] = vi[a];
+      q_vw[wid][lane][3 + a] = wi[a];
+    }
+    q_vw[wid][lane][6] = mi;
+    q_mask[wid][lane] = mask;
     {
-      const float rif = (float)ri;
-      const float fac = P.lubrication ? (1.0f + lub_out_f) : 1.0f;
-      for (int k0 = 0; k0 < nn; k0 += 4) {
-        int32_t ev[4];
-        Quad<S> Pv[4];
-        const int32_t* ep = nbr + (int64_t)k0 * N + i;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) ev[u] = k0 + u < nn ? ep[u * N] : 0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) Pv[u] = ldq(pos + (k0 + u < nn ? nbr_index(ev[u]) : (int)i));
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          float dx = (float)NS::dif(Pv[u].a, Pi.a), dy = (float)NS::dif(Pv[u].b, Pi.b),
-                dz = (float)NS::dif(Pv[u].c, Pi.c);
-          if (P.periodic[0]) dx = dx > P.cf.halfL[0] ? dx - P.cf.L[0] : (dx < -P.cf.halfL[0] ? dx + P.cf.L[0] : dx);
-          if (P.periodic[1]) dy = dy > P.cf.halfL[1] ? dy - P.cf.L[1] : (dy < -P.cf.halfL[1] ? dy + P.cf.L[1] : dy);
-          if (P.periodic[2]) dz = dz > P.cf.halfL[2] ? dz - P.cf.L[2] : (dz < -P.cf.halfL[2] ? dz + P.cf.L[2] : dz);
-          const float cut = (rif + (float)NS::f(Pv[u].d)) * fac;
-          if (k0 + u < nn && dx * dx + dy * dy + dz * dz <= cut * cut * 1.0002f) live |= 1u << (k0 + u);
-        }
+      uint32_t lv = live;
+      int t = off;
+      while (lv) {
+        const int k = __ffs(lv) - 1;
+        lv &= lv - 1;
+        q_pair[wid][t++] = (uint16_t)((lane << 8) | k);
       }
     }
-    // phase 2: interacting pairs only
-    while (live) {
-      const int k = __ffs(live) - 1;
-      live &= live - 1;
-      const int32_t e = nbr[(int64_t)k * N + i];
-      const int j = nbr_index(e);
-      const Quad<S> Pj = ldq(pos + j);
-      const bool i_lo = nbr_first(e);
-      const Quad<S>& A = i_lo ? Pi : Pj;
-      const Quad<S>& Bq = i_lo ? Pj : Pi;
-      // precise geometry in canonical order: dx = x_B - x_A (minimum image)
-      S dxs[3] = {NS::subq(Bq.a, A.a), NS::subq(Bq.b, A.b), NS::subq(Bq.c, A.c)};
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (!P.periodic[a]) continue;
-        F c = NS::f(dxs[a]);
-        if (c > K.halfL[a]) dxs[a] = NS::subq(dxs[a], B.L[a]);
-        else if (c < -K.halfL[a]) dxs[a] = NS::addq(dxs[a], B.L[a]);
+    __syncwarp();
+    const int64_t i0 = i - lane;  // particle of lane 0
+    for (int base = 0; base < total; base += 32) {
+      const int p = base + lane;
+      if (p < total) {
+        const int e = q_pair[wid][p];
+        const int L = e >> 8, k = e & 255;
+        const int64_t iL = i0 + L;
+        const F* vw = q_vw[wid][L];
+        const PairOut<F> o = pair_eval<FORM, INTEGRATE>(P, q_pi[wid][L], vw, vw + 3, vw[6],
+                                                        nbr[(int64_t)k * N + iL], k,
+                                                        (q_mask[wid][L] >> k) & 1u, iL, N, pos, vel,
+                                                        omg, hist);
+        F* r = q_res[wid][lane];
+        r[0] = o.fa.x; r[1] = o.fa.y; r[2] = o.fa.z;
+        r[3] = o.t.x; r[4] = o.t.y; r[5] = o.t.z;
+        r[6] = o.l.x; r[7] = o.l.y; r[8] = o.l.z;
+        q_flag[wid][lane] = (uint8_t)((o.contact ? 1 : 0) | (o.lub ? 2 : 0));
       }
-      S d2 = NS::addq(NS::addq(NS::mul(dxs[0], dxs[0]), NS::mul(dxs[1], dxs[1])),
-                      NS::mul(dxs[2], dxs[2]));
-      S ssum = NS::addq(A.d, Bq.d);
-      S num = NS::subq(NS::mul(ssum, ssum), d2);
-      const F dist = xsqrt(NS::f(d2));
-      const F sF = NS::f(ssum);
-      // r_A + r_B - |dx| without cancellation: (s^2 - d^2) / (s + d)
-      const F delta = NS::kExtended ? NS::f(num) / (sF + dist) : sF - dist;
-      const F dxf[3] = {NS::f(dxs[0]), NS::f(dxs[1]), NS::f(dxs[2])};
-      const bool contact = delta > F(0);
-      const bool lub = P.lubrication && (-delta < K.lub_out * sF);
-      if (!contact && !lub) continue;
-      const F inv_d = F(1) / dist;
-      const V3<F> n{dxf[0] * inv_d, dxf[1] * inv_d, dxf[2] * inv_d};
-      const Quad<S> Vj = ldq(vel + j);
-      const F vj[3] = {NS::f(Vj.a), NS::f(Vj.b), NS::f(Vj.c)};
-      const F* vA = i_lo ? vi : vj;
-      const F* vB = i_lo ? vj : vi;
-      if (contact) {
-        const Quad<S> Wj = ldq(omg + j);
-        const F wj[3] = {NS::f(Wj.a), NS::f(Wj.b), NS::f(Wj.c)};
-        const F* wA = i_lo ? wi : wj;
-        const F* wB = i_lo ? wj : wi;
-        const F rA = NS::f(A.d), rB = NS::f(Bq.d);
-        const F mA = i_lo ? mi : NS::f(Vj.d);
-        const F mB = i_lo ? NS::f(Vj.d) : mi;
-        const F Rs = rA * rB / (rA + rB);
-        const F ms = mA * mB / (mA + mB);
-        const F la = rA - F(0.5) * delta, lb = rB - F(0.5) * delta;
-        V3<F> om{la * wA[0] + lb * wB[0], la * wA[1] + lb * wB[1], la * wA[2] + lb * wB[2]};
-        V3<F> wxn = cross(om, n);
-        V3<F> vrel{vA[0] - vB[0] + wxn.x, vA[1] - vB[1] + wxn.y, vA[2] - vB[2] + wxn.z};
-        S xo[3], xn_[3];
-        const bool has = (mask >> k) & 1u;
-        if (has) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) xo[c] = hist[((int64_t)c * cap + k) * N + i];
+      __syncwarp();
+      // this lane's queue entries inside the round, in order
+      const int q0 = off > base ? off : base;
+      const int q1 = off + cnt < base + 32 ? off + cnt : base + 32;
+      for (int q = q0; q < q1; ++q) {
+        const F* r = q_res[wid][q - base];
+        const int fg = q_flag[wid][q - base];
+        if (fg & 1) {
+          fc.x += r[0]; fc.y += r[1]; fc.z += r[2];
+          tq.x += r[3]; tq.y += r[4]; tq.z += r[5];
+          if (INTEGRATE) nmask |= 1u << (q_pair[wid][q] & 255);
         }
-        V3<F> Ft;
-        V3<F> FA = hm_core<S, F>(K, n, delta, Rs, ms, vrel, xo, has, &Ft, xn_);
-        if (INTEGRATE) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) hist[((int64_t)c * cap + k) * N + i] = xn_[c];
-          nmask |= 1u << k;
+        if (fg & 2) {
+          fl.x += r[6]; fl.y += r[7]; fl.z += r[8];
         }
-        const F lev = i_lo ? la : lb;
-        V3<F> T = cross(V3<F>{lev * n.x, lev * n.y, lev * n.z}, Ft);
-        if (i_lo) {
-          fc.x += FA.x; fc.y += FA.y; fc.z += FA.z;
-        } else {
-          fc.x -= FA.x; fc.y -= FA.y; fc.z -= FA.z;
-        }
-        tq.x += T.x; tq.y += T.y; tq.z += T.z;
       }
-      if (lub) {
-        const F h = -delta;
-        const F hin = K.lub_in * sF;
-        const F hh = h > hin ? h : hin;
-        const F rA = NS::f(A.d), rB = NS::f(Bq.d);
-        const F Rl = rA * rB / (rA + rB);
-        const F vn = (vA[0] - vB[0]) * n.x + (vA[1] - vB[1]) * n.y + (vA[2] - vB[2]) * n.z;
-        F s = -K.six_pi_mu * Rl * Rl * vn / hh;
-        if (!i_lo) s = -s;
-        fl.x += s * n.x; fl.y += s * n.y; fl.z += s * n.z;
-      }
+      __syncwarp();
     }
+  } else {
+      while (live) {
+        const int k = __ffs(live) - 1;
+        live &= live - 1;
+        const PairOut<F> o = pair_eval<FORM, INTEGRATE>(P, Pi, vi, wi, mi, nbr[(int64_t)k * N + i], k,
+                                                        (mask >> k) & 1u, i, N, pos, vel, omg, hist);
+        if (o.contact) {
+          fc.x += o.fa.x; fc.y += o.fa.y; fc.z += o.fa.z;
+          tq.x += o.t.x; tq.y += o.t.y; tq.z += o.t.z;
+          if (INTEGRATE) nmask |= 1u << k;
+        }
+        if (o.lub) {
+          fl.x += o.l.x; fl.y += o.l.y; fl.z += o.l.z;
+        }
+      }
+  }
+  if (valid) {
     // walls (planes of the same material)
     uint32_t wmask_old = st.wmask[pb][i], wmask_new = 0;
     S* whist = (S*)st.whist[pb];
@@ -407,12 +521,12 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
   }
 }
 
-template <int FORM, bool INTEGRATE, int BS, int MINB>
+template <int FORM, bool INTEGRATE, int BS, int MINB, bool COOP>
 __global__ void __launch_bounds__(BS, MINB) k_substep(DevState st, DevMesh mesh, DevParams P,
                                                          int sub_off, cudaGraphConditionalHandle next,
                                                          int use_cond) {
-  substep_body<FORM, INTEGRATE, BS>(st, mesh, P, sub_off, next, use_cond, blockIdx.x, gridDim.x,
-                                    nullptr, 1);
+  substep_body<FORM, INTEGRATE, BS, COOP>(st, mesh, P, sub_off, next, use_cond, blockIdx.x,
+                                          gridDim.x, nullptr, 1);
 }
 
 // Ensemble: blockIdx.y is the bed, blockIdx.x the block within it (blocks past the
@@ -425,36 +539,38 @@ __global__ void __launch_bounds__(BS, MINB) k_substep_e(const BedView* v, int nb
   const unsigned nblk = (unsigned)((N + BS - 1) / BS);
   if (blockIdx.x >= nblk) return;
   const BedView& b = bed_view(v);
-  substep_body<FORM, true, BS>(b.st, b.mesh, b.P, sub_off, next, use_cond, blockIdx.x, nblk, ectl,
-                               nbeds);
+  substep_body<FORM, true, BS, false>(b.st, b.mesh, b.P, sub_off, next, use_cond, blockIdx.x, nblk,
+                                      ectl, nbeds);
 }
 
-template <int FORM, int BS, int MINB>
+template <int FORM, int BS, int MINB, bool COOP>
 static void launch_bs(const DevState& st, const DevMesh& mesh, const DevParams& P, int sub_off,
                       bool integrate, unsigned long long next, int use_cond, cudaStream_t s) {
   const int64_t grid = (st.N + BS - 1) / BS;
   const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)next;
   if (integrate)
-    k_substep<FORM, true, BS, MINB><<<(unsigned)grid, BS, 0, s>>>(st, mesh, P, sub_off, h, use_cond);
+    k_substep<FORM, true, BS, MINB, COOP><<<(unsigned)grid, BS, 0, s>>>(st, mesh, P, sub_off, h, use_cond);
   else
-    k_substep<FORM, false, BS, MINB><<<(unsigned)grid, BS, 0, s>>>(st, mesh, P, sub_off, h, 0);
+    k_substep<FORM, false, BS, MINB, COOP><<<(unsigned)grid, BS, 0, s>>>(st, mesh, P, sub_off, h, 0);
 }
 
 template <int FORM>
 static void launch_one(const DevState& st, const DevMesh& mesh, const DevParams& P, int sub_off,
                        bool integrate, int variant, unsigned long long next, int use_cond,
                        cudaStream_t s) {
-  // the parity form has the 128-thread variant only
+  // the parity form runs the per-particle pair loop at 128 threads
   if constexpr (FORM != FORM_FP64) {
     switch (variant) {
-      case SUBSTEP_B64: launch_bs<FORM, 64, 12>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
-      case SUBSTEP_B256: launch_bs<FORM, 256, 3>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
-      case SUBSTEP_B128_OCC8: launch_bs<FORM, 128, 8>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
-      case SUBSTEP_B128_OCC5: launch_bs<FORM, 128, 5>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
-      default: break;
+      case SUBSTEP_B64: launch_bs<FORM, 64, 12, true>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
+      case SUBSTEP_B256: launch_bs<FORM, 256, 3, true>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
+      case SUBSTEP_B128_OCC8: launch_bs<FORM, 128, 8, true>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
+      case SUBSTEP_B128_OCC5: launch_bs<FORM, 128, 5, true>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
+      case SUBSTEP_B128_LOOP: launch_bs<FORM, 128, 6, false>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
+      default: launch_bs<FORM, 128, 6, true>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
     }
+  } else {
+    launch_bs<FORM, 128, 6, false>(st, mesh, P, sub_off, integrate, next, use_cond, s);
   }
-  launch_bs<FORM, 128, 6>(st, mesh, P, sub_off, integrate, next, use_cond, s);
 }
 
 void launch_substep(int form, const DevState& st, const DevMesh& mesh, const DevParams& P,

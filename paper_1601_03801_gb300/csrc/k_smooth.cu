@@ -35,6 +35,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -270,8 +271,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
   const int64_t U = a.U;
   const int64_t u_begin = (int64_t)blockIdx.x * U / G, u_end = (int64_t)(blockIdx.x + 1) * U / G;
   MeshState* ms = (MeshState*)a.pairs;
-  __shared__ N s_c1[kMaxBeds], s_c2[kMaxBeds];
-  __shared__ double s_rho[kMaxBeds];
   __shared__ double s_sums[kMaxF * kQ];
   __shared__ int s_K;
   int slot = 0;
@@ -369,6 +368,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
                   const double need = fmax(0.5 * sqrt(a.rtol2 * bb / rrp), W::kFloor);
                   k = md.sig > 0.0 ? (int)ceil(log(need) / log(md.sig)) : 1;
                   if (k < 1) k = 1;
+                  if (k > kMaxStepsRound) k = kMaxStepsRound;
                   if (total + k > a.max_iter) k = a.max_iter - total;
                   if (k <= 0) {
                     k = 0;
@@ -396,22 +396,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
       if (blockIdx.x == 0 && threadIdx.x == 0) a.gflag[slot ^ 1] = 0;
       if (!grid_barrier(a.ctl, G)) return;
       if (threadIdx.x == 0) s_K = ldi(a.gflag + slot);
-      for (int b = threadIdx.x; b < a.B; b += kThreads) s_rho[b] = 1.0 / a.mesh[b].sigma1;
       __syncthreads();
       const int K = s_K;
       slot ^= 1;
       // ---- Chebyshev steps j = 1..K; step 1 also applies the shift (or zeroes x)
       const int J = K > 0 ? K : 1;
       for (int j = 1; j <= J; ++j) {
-        for (int b = threadIdx.x; b < a.B; b += kThreads) {
-          const SmoothMeshDev& md = a.mesh[b];
-          const double rho = s_rho[b];
-          const double rho_new = 1.0 / (2.0 * md.sigma1 - rho);
-          s_c1[b] = (N)(rho_new * rho);
-          s_c2[b] = (N)(2.0 * rho_new / md.delta);
-          s_rho[b] = rho_new;
-        }
-        __syncthreads();
         for (int64_t u = u_begin; u < u_end; ++u) {
           const int bi = a.unit_bed[u];
           const SmoothMeshDev& md = a.mesh[bi];
@@ -444,7 +434,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
           }
           if (!any) continue;
           const N cfn[3] = {(N)md.coef[0], (N)md.coef[1], (N)md.coef[2]};
-          const N c1 = s_c1[bi], c2 = s_c2[bi];
+          const N c1 = (N)md.cheb[0][j - 1], c2 = (N)md.cheb[1][j - 1];
           const N inv_theta = (N)(1.0 / md.theta);
           const Stencil sc = stencil_of(md, c);
           // step 1 reads the narrow residual (d[0]) and forms d0 = (r - s) / theta at
@@ -533,8 +523,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
 namespace cg = cooperative_groups;
 constexpr int kClThreads = 1024;
 constexpr int kClCells = 8192;   // cells per CTA at most
+constexpr size_t kClSmem = 212 * 1024;  // dynamic shared memory of a CTA at most: 20 B a cell
 constexpr int kClMaxCta = 16;
-constexpr int kClMaxSteps = 64;  // Chebyshev steps of one round at most (more: next round)
 
 // A stencil neighbour: index in the owning CTA's arrays, and that CTA (-1: this one).
 struct Nb {
@@ -548,9 +538,10 @@ __global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
   using N = typename W::N;
   using Acc = typename W::Acc;
   extern __shared__ __align__(16) unsigned char s_dyn[];
-  __shared__ double s_part[kQ];
+  __shared__ double s_part[kClMaxCta][kQ];  // every CTA's sums, pushed by each CTA
   __shared__ double s_red[kClThreads / 32][kQ];
-  __shared__ N s_c1[kClMaxSteps], s_c2[kClMaxSteps];
+  __shared__ double s_shift;
+  __shared__ int s_k, s_zero;
   cg::cluster_group cl = cg::this_cluster();
   const int csize = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -572,73 +563,60 @@ __global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
     N* dA = (N*)(Xs + P * nxy);             // narrow true residual, then even directions
     N* dB = dA + P * nxy;                   // odd directions
     N* Qs = dB + P * nxy;                   // recursive residual
+
     T* Xg = (T*)md.x + f * C;
     T* Bg = (T*)md.b + f * C;
     const T cf[3] = {W::from_d(md.coef[0]), W::from_d(md.coef[1]), W::from_d(md.coef[2])};
     const N cfn[3] = {(N)md.coef[0], (N)md.coef[1], (N)md.coef[2]};
     const N inv_theta = (N)(1.0 / md.theta);
-    // Work layout: thread t owns the (x, y) sites t, t + kClThreads, ... of a plane and
-    // all of this CTA's planes at those sites, so the in-plane neighbours are fixed
-    // offsets per site and only the z-neighbours change from plane to plane.
-    struct Site {
-      int32_t s;        // site index in the plane
-      int32_t off[4];   // in-plane neighbour offsets (x-, x+, y-, y+); INT32_MIN: none
-    };
-    auto site_of = [&](int sidx) {
-      Site st;
-      st.s = sidx;
-      const int ix = sidx % nx, iy = sidx / nx;
-      st.off[0] = ix > 0 ? -1 : (md.per[0] ? nx - 1 : INT32_MIN);
-      st.off[1] = ix < nx - 1 ? 1 : (md.per[0] ? -(nx - 1) : INT32_MIN);
-      st.off[2] = iy > 0 ? -nx : (md.per[1] ? (ny - 1) * nx : INT32_MIN);
-      st.off[3] = iy < ny - 1 ? nx : (md.per[1] ? -(ny - 1) * nx : INT32_MIN);
-      return st;
-    };
-    // the six face neighbours of local cell l = izl nxy + site (r = -2: zero-flux face)
-    auto stencil = [&](const Site& st, int izl, Nb* nb) {
-      const int l = izl * nxy + st.s;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) nb[k] = st.off[k] != INT32_MIN ? Nb{l + st.off[k], -1} : Nb{0, -2};
-      if (izl > 0) nb[4] = Nb{l - nxy, -1};
-      else if (z0 > 0) nb[4] = Nb{(P - 1) * nxy + st.s, rank - 1};
-      else if (md.per[2]) nb[4] = csize > 1 ? Nb{(last_planes - 1) * nxy + st.s, csize - 1} : Nb{(planes - 1) * nxy + st.s, -1};
-      else nb[4] = Nb{0, -2};
-      if (izl < planes - 1) nb[5] = Nb{l + nxy, -1};
-      else if (z0 + planes < nz) nb[5] = Nb{st.s, rank + 1};
-      else if (md.per[2]) nb[5] = csize > 1 ? Nb{st.s, 0} : Nb{st.s, -1};
-      else nb[5] = Nb{0, -2};
-    };
-    // (A v) at a cell from its value vc and its neighbours' values, axis by axis:
-    // vc - sum_a coef_a ((v_- - vc) + (v_+ - vc)) over the faces that exist
-    auto lap_apply = [&](auto vc, const Nb* nb, auto get, auto sub, auto add, auto mul, const auto* cfa) {
-      decltype(vc) lap{};
-      bool any_axis = false;
-#pragma unroll
-      for (int ax = 0; ax < 3; ++ax) {
-        decltype(vc) sa{};
-        bool any = false;
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-          const Nb& n = nb[2 * ax + side];
-          if (n.r == -2) continue;
-          const auto t = sub(get(n), vc);
-          sa = any ? add(sa, t) : t;
-          any = true;
-        }
-        if (any) {
-          const auto t = mul(cfa[ax], sa);
-          lap = any_axis ? add(lap, t) : t;
-          any_axis = true;
-        }
+    // Work layout: thread t owns the (x, y) columns t, t + kClThreads, ... of the plane
+    // and walks each column through this CTA's planes with a rolling window in z, so
+    // the in-plane neighbours are fixed offsets per column and only the first and
+    // last plane read a z-neighbour from another CTA (distributed shared memory,
+    // both loaded before the walk).
+    const bool pz = md.per[2] != 0;
+    // z-neighbour below plane 0 / above the last plane of column s in array `arr`
+    // (has = false: zero-flux face)
+    auto z_below = [&](auto* arr, int s, bool& has) {
+      using V = typename std::remove_const<typename std::remove_pointer<decltype(arr)>::type>::type;
+      has = true;
+      if (z0 > 0) return (V)cl.map_shared_rank(arr, (unsigned)(rank - 1))[(P - 1) * nxy + s];
+      if (pz) {
+        if (csize > 1) return (V)cl.map_shared_rank(arr, (unsigned)(csize - 1))[(last_planes - 1) * nxy + s];
+        return (V)arr[(planes - 1) * nxy + s];
       }
-      return any_axis ? sub(vc, lap) : vc;
+      has = false;
+      return V{};
     };
-    auto wsub = [](T p, T q) { return W::subq(p, q); };
-    auto wadd = [](T p, T q) { return W::addq(p, q); };
-    auto wmul = [](T p, T q) { return W::mul(p, q); };
-    auto nsub = [](N p, N q) { return p - q; };
-    auto nadd = [](N p, N q) { return p + q; };
-    auto nmul = [](N p, N q) { return p * q; };
+    auto z_above = [&](auto* arr, int s, bool& has) {
+      using V = typename std::remove_const<typename std::remove_pointer<decltype(arr)>::type>::type;
+      has = true;
+      if (z0 + planes < nz) return (V)cl.map_shared_rank(arr, (unsigned)(rank + 1))[s];
+      if (pz) {
+        if (csize > 1) return (V)cl.map_shared_rank(arr, 0u)[s];
+        return (V)arr[s];
+      }
+      has = false;
+      return V{};
+    };
+    // in-plane neighbour offsets of column s (has[k] = false: zero-flux face)
+    struct Col {
+      int off[4];
+      bool has[4];
+    };
+    auto col_of = [&](int sidx) {
+      Col c;
+      const int ix = sidx % nx, iy = sidx / nx;
+      c.has[0] = ix > 0 || md.per[0];
+      c.off[0] = ix > 0 ? -1 : nx - 1;
+      c.has[1] = ix < nx - 1 || md.per[0];
+      c.off[1] = ix < nx - 1 ? 1 : -(nx - 1);
+      c.has[2] = iy > 0 || md.per[1];
+      c.off[2] = iy > 0 ? -nx : (ny - 1) * nx;
+      c.has[3] = iy < ny - 1 || md.per[1];
+      c.off[3] = iy < ny - 1 ? nx : -(ny - 1) * nx;
+      return c;
+    };
     for (int m = 0; m < a.n_tau; ++m) {
       // ---- b = x (global); x (or the guess) into shared memory
       for (int l = threadIdx.x; l < ncell; l += kClThreads) {
@@ -652,25 +630,43 @@ __global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
       for (int round = 0; round < kMaxRounds; ++round) {
         // ---- true residual (wide), its narrow copy in dA, sums
         Acc v[kQ] = {Acc(0), Acc(0), Acc(0)};
-        for (int sidx = threadIdx.x; sidx < nxy; sidx += kClThreads)
-        for (int izl = 0; izl < planes; ++izl) {
-          const Site st = site_of(sidx);
-          const int l = izl * nxy + sidx;
-          Nb nb[6];
-          stencil(st, izl, nb);
-          auto getx = [&](const Nb& n) {
-            const T* base = n.r < 0 ? Xs : cl.map_shared_rank(Xs, (unsigned)n.r);
-            return base[n.l];
-          };
-          const T ax = lap_apply(Xs[l], nb, getx, wsub, wadd, wmul, cf);
-          const T bv = W::ld(Bg + c0 + l);
-          const N rn = W::narrow(W::subq(bv, ax));
-          dA[l] = rn;
-          v[0] += (Acc)rn * (Acc)rn;
-          v[1] += (Acc)rn;
-          if (round == 0) {
-            const Acc bn = (Acc)W::narrow(bv);
-            v[2] += bn * bn;
+        // (A x)(c) = x_c - sum_a coef_a ((x_- - x_c) + (x_+ - x_c)), faces that exist
+        auto wpair = [](bool h0, T v0, bool h1, T v1, T c) {
+          if (h0 && h1) return W::addq(W::subq(v0, c), W::subq(v1, c));
+          if (h0) return W::subq(v0, c);
+          if (h1) return W::subq(v1, c);
+          return W::zero();
+        };
+        for (int sidx = threadIdx.x; sidx < nxy; sidx += kClThreads) {
+          const Col col = col_of(sidx);
+          bool hb, hl;
+          // both remote z-neighbours of the column are loaded before the walk
+          T below = z_below(Xs, sidx, hb);
+          const T top = z_above(Xs, sidx, hl);
+          T cur = Xs[sidx];
+          for (int izl = 0; izl < planes; ++izl) {
+            const int l = izl * nxy + sidx;
+            const bool ha = izl + 1 < planes || hl;
+            const T above = izl + 1 < planes ? Xs[l + nxy] : top;
+            const T sx = wpair(col.has[0], col.has[0] ? Xs[l + col.off[0]] : cur, col.has[1],
+                               col.has[1] ? Xs[l + col.off[1]] : cur, cur);
+            const T sy = wpair(col.has[2], col.has[2] ? Xs[l + col.off[2]] : cur, col.has[3],
+                               col.has[3] ? Xs[l + col.off[3]] : cur, cur);
+            const T sz = wpair(hb, below, ha, above, cur);
+            const T lap = W::addq(W::addq(W::mul(cf[0], sx), W::mul(cf[1], sy)), W::mul(cf[2], sz));
+            const T ax = W::subq(cur, lap);
+            const T bv = W::ld(Bg + c0 + l);
+            const N rn = W::narrow(W::subq(bv, ax));
+            dA[l] = rn;
+            v[0] += (Acc)rn * (Acc)rn;
+            v[1] += (Acc)rn;
+            if (round == 0) {
+              const Acc bn = (Acc)W::narrow(bv);
+              v[2] += bn * bn;
+            }
+            below = cur;
+            hb = true;
+            cur = above;
           }
         }
 #pragma unroll
@@ -681,38 +677,50 @@ __global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
           if (lane == 0) s_red[wid][q] = t;
         }
         __syncthreads();
-        if (threadIdx.x < kQ) {
+        // this CTA's sums, pushed into every CTA's shared memory (stores do not wait)
+        if (threadIdx.x < csize * kQ) {
+          const int r = threadIdx.x / kQ, q = threadIdx.x % kQ;
           double t = 0.0;
-          for (int k = 0; k < kClThreads / 32; ++k) t += s_red[k][threadIdx.x];
-          s_part[threadIdx.x] = t;
+          for (int k = 0; k < kClThreads / 32; ++k) t += s_red[k][q];
+          cl.map_shared_rank(&s_part[0][0], (unsigned)r)[rank * kQ + q] = t;
         }
         cl.sync();
-        // every CTA sums the CTAs' parts in rank order: identical decisions
-        double tot[kQ] = {0.0, 0.0, 0.0};
-        for (int r = 0; r < csize; ++r) {
-          const double* p = cl.map_shared_rank(s_part, (unsigned)r);
+        // one thread of every CTA sums the parts in rank order and decides: every CTA
+        // takes the same decision
+        if (threadIdx.x == 0) {
+          double tot[kQ] = {0.0, 0.0, 0.0};
+          for (int r = 0; r < csize; ++r)
 #pragma unroll
-          for (int q = 0; q < kQ; ++q) tot[q] += p[q];
-        }
-        if (round == 0) {
-          bb = tot[2];
-          zero = !(bb > 0.0);
-        }
-        const double Cd = (double)C;
-        const double shift = zero ? 0.0 : tot[1] / Cd;
-        const double rrp = fmax(tot[0] - tot[1] * tot[1] / Cd, 0.0);
-        int k = 0;
-        if (!zero && !(rrp <= a.rtol2 * bb)) {
-          const double need = fmax(0.5 * sqrt(a.rtol2 * bb / rrp), W::kFloor);
-          k = md.sig > 0.0 ? (int)ceil(log(need) / log(md.sig)) : 1;
-          if (k < 1) k = 1;
-          if (k > kClMaxSteps) k = kClMaxSteps;
-          if (total + k > a.max_iter) k = a.max_iter - total;
-          if (k <= 0) {
-            k = 0;
-            if (rank == 0 && threadIdx.x == 0) atomicCAS((int*)&a.ctl->cg_status, 0, SEDI_EDIVERGED);
+            for (int q = 0; q < kQ; ++q) tot[q] += s_part[r][q];
+          if (round == 0) {
+            bb = tot[2];
+            zero = !(bb > 0.0);
           }
+          const double Cd = (double)C;
+          const double shift = zero ? 0.0 : tot[1] / Cd;
+          const double rrp = fmax(tot[0] - tot[1] * tot[1] / Cd, 0.0);
+          int k = 0;
+          if (!zero && !(rrp <= a.rtol2 * bb)) {
+            // the step count only has to be about right (the next round checks the true
+            // residual), so it is formed in FP32
+            const float need = fmaxf(0.5f * sqrtf((float)(a.rtol2 * bb / rrp)), (float)W::kFloor);
+            k = md.sig > 0.0 ? (int)ceilf(logf(need) / logf((float)md.sig)) : 1;
+            if (k < 1) k = 1;
+            if (k > kMaxStepsRound) k = kMaxStepsRound;
+            if (total + k > a.max_iter) k = a.max_iter - total;
+            if (k <= 0) {
+              k = 0;
+              if (rank == 0) atomicCAS((int*)&a.ctl->cg_status, 0, SEDI_EDIVERGED);
+            }
+          }
+          s_k = k;
+          s_shift = shift;
+          s_zero = zero;
         }
+        __syncthreads();
+        const int k = s_k;
+        const double shift = s_shift;
+        zero = s_zero;
         total += k;
         if (k == 0) {
           // converged (or zero, or stopped): apply the projection shift, write x back
@@ -725,48 +733,67 @@ __global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
           }
           break;
         }
-        if (threadIdx.x == 0) {
-          double rho = 1.0 / md.sigma1;
-          for (int j = 0; j < k; ++j) {
-            const double rho_new = 1.0 / (2.0 * md.sigma1 - rho);
-            s_c1[j] = (N)(rho_new * rho);
-            s_c2[j] = (N)(2.0 * rho_new / md.delta);
-            rho = rho_new;
-          }
-        }
-        __syncthreads();
         const N shn = (N)shift;
         const T sw = W::from_d(shift);
         // ---- Chebyshev steps (step 1 applies the shift and forms d0 = (r - s) / theta)
         for (int j = 1; j <= k; ++j) {
           N* Dold = (j & 1) ? dA : dB;
           N* Dnew = (j & 1) ? dB : dA;
-          const N c1s = s_c1[j - 1], c2s = s_c2[j - 1];
-          for (int sidx = threadIdx.x; sidx < nxy; sidx += kClThreads) {
-            const Site st = site_of(sidx);
-            for (int izl = 0; izl < planes; ++izl) {
-            const int l = izl * nxy + sidx;
-            Nb nb[6];
-            stencil(st, izl, nb);
-            auto dir = [&](const Nb& n) {
-              const N* base = n.r < 0 ? Dold : cl.map_shared_rank(Dold, (unsigned)n.r);
-              const N raw = base[n.l];
-              return j == 1 ? (raw - shn) * inv_theta : raw;
+          const N c1s = (N)md.cheb[0][j - 1], c2s = (N)md.cheb[1][j - 1];
+          // One step over this CTA's columns.  FIRST (step 1) reads the narrow true
+          // residual r and forms d0 = (r - s) / theta at every point it touches; x and
+          // the recursion take the shift.  FULL: all four in-plane faces exist (the
+          // common case), so the loop has no per-face selects.
+          auto step = [&](auto first_tag, auto full_tag, int sidx, const Col& col) {
+            constexpr bool FIRST = decltype(first_tag)::value;
+            constexpr bool FULL = decltype(full_tag)::value;
+            auto tr = [&](N raw) {
+              if constexpr (FIRST) return (raw - shn) * inv_theta;
+              else return raw;
             };
-            const N dc = dir(Nb{l, -1});
-            const N ad = lap_apply(dc, nb, dir, nsub, nadd, nmul, cfn);
-            T xv = Xs[l];
-            N q;
-            if (j == 1) {
-              xv = W::add(xv, sw);
-              q = Dold[l] - shn;
-            } else {
-              q = Qs[l];
+            auto face = [&](bool h, int l, int off, N cur) {
+              if constexpr (FULL) return tr(Dold[l + off]) - cur;
+              else return h ? tr(Dold[l + off]) - cur : N(0);
+            };
+            bool hb, hl;
+            // both remote z-neighbours of the column are loaded before the walk
+            N below = tr(z_below(Dold, sidx, hb));
+            const N top = tr(z_above(Dold, sidx, hl));
+            N cur = tr(Dold[sidx]);
+            for (int izl = 0; izl < planes; ++izl) {
+              const int l = izl * nxy + sidx;
+              const bool up = izl + 1 < planes;
+              const N above = up ? tr(Dold[l + nxy]) : top;
+              const N sx = face(col.has[0], l, col.off[0], cur) + face(col.has[1], l, col.off[1], cur);
+              const N sy = face(col.has[2], l, col.off[2], cur) + face(col.has[3], l, col.off[3], cur);
+              const N sz = (hb ? below - cur : N(0)) + ((up || hl) ? above - cur : N(0));
+              const N ad = cur - ((cfn[0] * sx + cfn[1] * sy) + cfn[2] * sz);
+              T xv = Xs[l];
+              N q;
+              if constexpr (FIRST) {
+                xv = W::add(xv, sw);
+                q = Dold[l] - shn;
+              } else {
+                q = Qs[l];
+              }
+              q = q - ad;
+              Qs[l] = q;
+              Dnew[l] = c1s * cur + c2s * q;
+              Xs[l] = W::add_n(xv, cur);
+              below = cur;
+              hb = true;
+              cur = above;
             }
-            q = q - ad;
-            Qs[l] = q;
-            Dnew[l] = c1s * dc + c2s * q;
-            Xs[l] = W::add_n(xv, dc);
+          };
+          for (int sidx = threadIdx.x; sidx < nxy; sidx += kClThreads) {
+            const Col col = col_of(sidx);
+            const bool full = col.has[0] && col.has[1] && col.has[2] && col.has[3];
+            if (j == 1) {
+              if (full) step(std::true_type{}, std::true_type{}, sidx, col);
+              else step(std::true_type{}, std::false_type{}, sidx, col);
+            } else {
+              if (full) step(std::false_type{}, std::true_type{}, sidx, col);
+              else step(std::false_type{}, std::false_type{}, sidx, col);
             }
           }
           cl.sync();
@@ -879,6 +906,15 @@ void smooth_mesh_layout(int form, const SmoothMesh& in, SmoothMeshDev* out) {
   m.sigma1 = m.theta / m.delta;
   const double sq = std::sqrt(lmax);
   m.sig = (sq - 1.0) / (sq + 1.0);
+  // Chebyshev coefficients of steps 1..kMaxStepsRound (the same in every round):
+  // rho_1 = 1 / sigma1, rho' = 1 / (2 sigma1 - rho), c1 = rho' rho, c2 = 2 rho' / delta
+  double rho = 1.0 / m.sigma1;
+  for (int j = 0; j < kMaxStepsRound; ++j) {
+    const double rho_new = 1.0 / (2.0 * m.sigma1 - rho);
+    m.cheb[0][j] = rho_new * rho;
+    m.cheb[1][j] = 2.0 * rho_new / m.delta;
+    rho = rho_new;
+  }
 }
 
 namespace {
@@ -886,7 +922,7 @@ namespace {
 template <class T>
 int launch_cluster(const SmoothBatchDev& a, int csize, cudaStream_t s) {
   using N = typename Wide<T>::N;
-  const size_t smem = (size_t)kClCells * (sizeof(T) + 3 * sizeof(N));
+  const size_t smem = kClSmem;
   if (cudaFuncSetAttribute(k_smooth_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return -3;
   if (csize > 8 && cudaFuncSetAttribute(k_smooth_cl<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
@@ -918,8 +954,12 @@ void cluster_plan(int form, const SmoothMeshDev& m, int* csize, int* planes) {
   *planes = 0;
   if (form == FORM_FP64) return;
   const int64_t nxy = (int64_t)m.nc[0] * m.nc[1];
-  if (nxy > kClCells) return;
-  const int pmax = (int)(kClCells / nxy);
+  // per CTA: P planes of x (8 B) and three narrow words (4 B)
+  const int64_t room = (int64_t)kClSmem / 4;  // in 4-byte words
+  if (room < 5 * nxy) return;
+  int pmax = (int)(room / (5 * nxy));
+  if ((int64_t)pmax * nxy > kClCells) pmax = (int)(kClCells / nxy);
+  if (pmax < 1) return;
   const int nz = m.nc[2];
   int cs = (nz + pmax - 1) / pmax;
   if (cs > kClMaxCta) return;

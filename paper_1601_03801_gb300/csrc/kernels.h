@@ -8,16 +8,17 @@ namespace sedi {
 
 // Launch variants of the substep kernel: threads per block and minimum resident
 // blocks per SM (128/6, 64/12, 256/3 cap registers at 80 a thread, 128/8 at 64,
-// 128/5 at 96).  The split and plain forms have all five; the FP64 parity form
-// runs 128/6.
+// 128/5 at 96), all with the warp-cooperative pair phase; variant 5 is 128/6 with
+// the per-particle pair loop.  The FP64 parity form runs 128/6 with the loop.
 enum SubstepVariant {
   SUBSTEP_B128 = 0,
   SUBSTEP_B64 = 1,
   SUBSTEP_B256 = 2,
   SUBSTEP_B128_OCC8 = 3,
-  SUBSTEP_B128_OCC5 = 4
+  SUBSTEP_B128_OCC5 = 4,
+  SUBSTEP_B128_LOOP = 5
 };
-constexpr int kSubstepVariants = 5;
+constexpr int kSubstepVariants = 6;
 inline int substep_block(int variant) { return variant == SUBSTEP_B64 ? 64 : variant == SUBSTEP_B256 ? 256 : 128; }
 
 // k_force.cu: one fused substep (integrate = true) or forces only into st.fdbg.
@@ -77,7 +78,8 @@ void launch_deposit(int form, const DevState& st, const DevMesh& mesh, const Dev
 void launch_fields_from_fixed(int form, const void* q, const DevParams& P, void* phi,
                               int nf, cudaStream_t s);
 // k_smooth.cu: the smoothing solve of a batch of meshes in one persistent launch.
-constexpr int kMaxBeds = 1024;  // meshes in one smoothing launch
+constexpr int kMaxBeds = 1024;       // meshes in one smoothing launch
+constexpr int kMaxStepsRound = 64;  // Chebyshev steps of one round at most (more: next round)
 
 // One mesh of a smoothing batch, as the caller describes it.
 struct SmoothMesh {
@@ -105,6 +107,7 @@ struct SmoothMeshDev {
   double coef[3];
   double theta, delta, sigma1, sig;  // spectrum [1, lmax]: centre, half width, ratio, rate
   int32_t cl_size, cl_planes;        // cluster solver: CTAs, z-planes per CTA (0: grid solver)
+  double cheb[2][kMaxStepsRound];    // c1, c2 of Chebyshev steps 1..kMaxStepsRound of a round
 };
 
 struct SmoothBatchDev {

@@ -134,19 +134,19 @@ def test_deterministic_runs(small):
 @pytest.mark.parametrize("form", ["split", "plain"])
 def test_substep_variants_bit_identical(small, form):
     """Every launch variant of the substep kernel gives the same bits in the split
-    form: each particle's arithmetic does not depend on the block it runs in.  The
-    plain FP32 form leaves mul/add fusion to the code generator, whose choices may
-    differ with the register budget: there the variants agree to FP32 rounding."""
+    form: each particle's arithmetic does not depend on the block it runs in, and
+    the warp-cooperative pair phase adds the same terms in the same order as the
+    per-particle loop (variant 5).  The plain FP32 form agrees to FP32 rounding."""
     prm, parts = small
     ref = None
-    for variant in range(5):
+    for variant in range(6):
         g = sedi.Sedi(dict(prm, precision_form=form, substep_variant=variant))
         g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
         g.step(40)
         eps, _, F = g.average()
         st = g.stats()
         assert st["substep_variant"] == variant
-        assert st["substep_block"] == {0: 128, 1: 64, 2: 256, 3: 128, 4: 128}[variant]
+        assert st["substep_block"] == {0: 128, 1: 64, 2: 256, 3: 128, 4: 128, 5: 128}[variant]
         got = (*g.get_particles(), eps, F)
         if ref is None:
             ref = got
@@ -154,10 +154,12 @@ def test_substep_variants_bit_identical(small, form):
             for a, b in zip(ref, got):
                 assert np.array_equal(a, b), variant
         else:
-            x0, x1 = ref[0], got[0]
-            assert (np.abs(min_image(x1 - x0, prm)).max(axis=1) / parts["d"]).max() <= 1e-4, variant
-            for a, b in zip(ref[1:], got[1:]):
-                assert np.abs(a - b).max() <= 1e-3 * max(np.abs(a).max(), 1e-30), variant
+            # plain FP32: positions and velocities identical; the stored acceleration
+            # may differ in its last bits between launch shapes
+            for a, b in zip(ref[:3], got[:3]):
+                assert np.array_equal(a, b), variant
+            for a, b in zip(ref[3:], got[3:]):
+                assert np.abs(a - b).max() <= 1e-5 * max(np.abs(a).max(), 1e-30), variant
 
 
 def test_autotuner_chooses_and_caches(small, tmp_path, monkeypatch):
@@ -172,7 +174,7 @@ def test_autotuner_chooses_and_caches(small, tmp_path, monkeypatch):
     assert g.stats()["substep_variant"] == -1
     g.step(10)
     st = g.stats()
-    assert 0 <= st["substep_variant"] < 5 and st["substep_block"] in (64, 128, 256)
+    assert 0 <= st["substep_variant"] < 6 and st["substep_block"] in (64, 128, 256)
     lines = cache.read_text().splitlines()
     assert len(lines) == 1 and f"N={n}|" in lines[0] and '"median_us"' in lines[0]
     # a second handle on the same workload takes the cached choice without re-timing
@@ -318,7 +320,7 @@ def test_errors_are_reported(small):
     with pytest.raises(sedi.SediError):
         sedi.Sedi(dict(prm, restitution=0.0))
     with pytest.raises(sedi.SediError):
-        sedi.Sedi(dict(prm, substep_variant=5))
+        sedi.Sedi(dict(prm, substep_variant=6))
     g = sedi.Sedi(dict(prm, precision_form="split", nbr_capacity=2))
     with pytest.raises(sedi.SediError) as e:
         g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
