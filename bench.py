@@ -265,6 +265,9 @@ def gpu_arm(args):
     ens = None
     if rank == 0 and not args.no_ensemble:
         ens = ensemble_leg()
+    large = None
+    if rank == 0 and not args.no_large:
+        large = large_leg(peaks()[0])
     cnn = None
     if rank == 0 and not args.no_cnn:
         cnn = cnn_warm_start(prm, parts, fl)
@@ -283,12 +286,67 @@ def gpu_arm(args):
                            "parallelism": "independent bed per GPU" if world > 1 else "1 GPU"},
                 "phases_ms_per_step": phases, "rebuilds_in_timed_region": int(rebuilds),
                 "roofline": roof, "plain_form": plain, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks, "cpu_baseline": cpu, "ensemble": ens, "cnn_warm_start": cnn}
+                "clocks": clocks, "cpu_baseline": cpu, "ensemble": ens, "large": large,
+                "cnn_warm_start": cnn}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+
+
+def large_leg(peak_gbs, steps=3, warmup=2):
+    """10,000,000 spheres (d ~ U[0.4, 0.6] mm) in a periodic 400 x 200 x 100 mm box on a
+    256 x 128 x 64 mesh with a turbulent-like flow: throughput of the split form (step =
+    20 substeps + 1 averaging) and the substep kernel's HBM roofline fraction."""
+    import torch
+
+    from paper_1601_03801_gb300 import sedi
+    from paper_1601_03801_gb300.workloads import large_case
+
+    prm, parts, fl = large_case()
+    n = len(parts["x"])
+    stream = torch.cuda.Stream()
+    g = sedi.Sedi(dict(prm, precision_form="split", profile=1), stream=stream)
+    g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+    g.set_fluid(U=fl["U"], DUDt=fl["DUDt"])
+    g.average_inplace()
+    for _ in range(warmup):
+        g.step(SUBSTEPS)
+        g.average_inplace()
+    g.sync()
+    t0 = g.timings()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        g.step(SUBSTEPS)
+        g.average_inplace()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t1 = g.timings()
+    ms = e0.elapsed_time(e1) / steps
+    off, _ = g.neighbors()
+    kbar = float(off[-1]) / n
+    ij, _ = g.contacts()
+    cbar = 2.0 * len(ij) / n
+    C = int(np.prod(prm["ncell"]))
+    per_particle = 144 + 120 + 4 * kbar + 48 * cbar + 32.0 * C / n
+    sub_ms = (t1["substep_ms"] - t0["substep_ms"]) / max(1.0, t1["substep_n"] - t0["substep_n"])
+    achieved = per_particle * n / (sub_ms / 1e3) / 1e9
+    phases = {k: round((t1[k] - t0[k]) / steps, 3) for k in ("rebuild_ms", "substep_ms", "deposit_ms", "smooth_ms")}
+    return {"workload": "10,000,000 spheres, d ~ U[0.4, 0.6] mm, tiled relaxed packing in a periodic "
+                        "400 x 200 x 100 mm box (wall z = 0), 256 x 128 x 64 mesh, mean flow 0.3 m/s "
+                        "+ Gaussian-filtered noise (rms 0.03 m/s); step = 20 substeps + 1 averaging",
+            "particles": n, "steps": steps, "warmup": warmup,
+            "value": round(n * SUBSTEPS / (ms / 1e3), 1), "unit": UNIT, "ms_per_step": round(ms, 3),
+            "phases_ms_per_step": phases,
+            "roofline": {"bound": "hbm", "kernel": "k_substep<split>", "achieved": round(achieved, 1),
+                         "peak": peak_gbs, "unit": "GB/s", "frac": round(achieved / peak_gbs, 4),
+                         "algorithmic_bytes_per_particle": round(per_particle, 1),
+                         "launch_ms": round(sub_ms, 4), "kbar": round(kbar, 2), "cbar": round(cbar, 2)},
+            "substep_variant": g.stats()["substep_variant"]}
 
 
 def ensemble_leg(steps=3, warmup=2):
@@ -539,6 +597,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-cnn", action="store_true", help="skip the learned-warm-start leg")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 256-bed ensemble leg")
+    ap.add_argument("--no-large", action="store_true", help="skip the 10M-sphere leg")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--settle", type=int, default=50, help="untimed settling steps before warm-up")
     ap.add_argument("--mode", default="bench", choices=["bench", "kernels"],

@@ -68,14 +68,28 @@ enum { SEDI_MEM_HOST = 0, SEDI_MEM_DEVICE = 1 };
  *   reference (slow on GB300: FP64 runs at a small fraction of the FP32 rate). */
 enum { SEDI_FORM_SPLIT = 0, SEDI_FORM_PLAIN_FP32 = 1, SEDI_FORM_FP64 = 2 };
 
-enum { SEDI_HERTZ_MINDLIN = 0 };
+/* Contact laws.  SEDI_HERTZ_MINDLIN: Hertz normal force and Mindlin tangential
+ * spring with Tsuji-type damping (E, poisson, restitution).  SEDI_LINEAR_SPRING: the
+ * paper's linear spring-dashpot (Sec. 2.5, Table 1): normal stiffness kn_linear,
+ * tangential stiffness kt_ratio * kn_linear, damping set by the restitution
+ * coefficient (exactly e for a head-on collision). */
+enum { SEDI_HERTZ_MINDLIN = 0, SEDI_LINEAR_SPRING = 1 };
+
+/* Pseudo-time schemes of the diffusion smoothing (Sec. 2.4), n_tau steps of
+ * dtau = 1 / n_tau.  SEDI_TAU_EULER: (I - dtau D L) phi^{m+1} = phi^m.  SEDI_TAU_BDF2:
+ * the second-order implicit scheme, read as the two-step backward difference
+ * (I - (2/3) dtau D L) phi^{m+1} = (4/3) phi^m - (1/3) phi^{m-1}, its first step
+ * backward Euler.  Both keep sum(phi). */
+enum { SEDI_TAU_EULER = 0, SEDI_TAU_BDF2 = 1 };
 
 typedef struct sedi_handle sedi_handle; /* opaque, owned by the library */
 
 /* All SI units.  Defaults from sedi_default_params() in brackets. */
 typedef struct sedi_params {
-  int32_t contact_law;                     /* SEDI_HERTZ_MINDLIN */
+  int32_t contact_law;                     /* SEDI_HERTZ_MINDLIN | SEDI_LINEAR_SPRING [Hertz] */
   double E, poisson, restitution, friction;/* particles and walls [1e7, 0.3, 0.9, 0.3] */
+  double kn_linear, kt_ratio;              /* linear law: normal stiffness (N/m), tangential
+                                              / normal stiffness [800 (Table 1), 2/7] */
   double rho_f, nu_f, g[3];                /* fluid density, kinematic viscosity, gravity
                                               [1000, 1e-6, (0, 0, -9.81)] */
   double lo[3], hi[3];                     /* box; axis a spans [lo, hi) */
@@ -84,13 +98,25 @@ typedef struct sedi_params {
   double dt;                               /* DEM substep [1e-6] */
   double skin;                             /* neighbour-list skin [5e-5] */
   int32_t lubrication, drag, pressure_grad, added_mass; /* force switches [1, 1, 1, 1] */
+  int32_t lift;                            /* Saffman lift (Sec. 2.3, Eq. 7), read as
+                                              c_lift rho_f nu^0.5 d^2 |omega|^-0.5
+                                              (w x omega), w = U_f - u_p, omega = curl U_f
+                                              (central differences of U at the cell
+                                              centres, interpolated trilinearly) [0] */
+  int32_t lub_tangential;                  /* tangential (shear) lubrication terms of the
+                                              Ball-Melrose model, with their torques
+                                              (Sec. 2.5): leading log-gap term of the
+                                              two-sphere resistance; needs lubrication [0] */
   double lub_h_in_frac, lub_h_out_frac;    /* lubrication gap limits as fractions of the
                                               pair-mean diameter [1e-3, 0.1] */
   double c_add;                            /* added-mass coefficient, Eq. 8 [0.5] */
+  double c_lift;                           /* lift coefficient C_l, Eq. 7 [1.6] */
   double eps_max;                          /* clamp of eps_s in the drag law [0.9] */
   int32_t ncell[3];                        /* Eulerian mesh */
   double bandwidth[3];                     /* Gaussian bandwidth b per axis (Sec. 2.4) */
-  int32_t n_tau;                           /* backward-Euler pseudo-time steps [4] */
+  int32_t n_tau;                           /* implicit pseudo-time steps [4] */
+  int32_t tau_scheme;                      /* SEDI_TAU_EULER | SEDI_TAU_BDF2 [EULER];
+                                              BDF2 excludes use_cnn_guess */
   double cg_rtol;                          /* ||r|| <= rtol ||b|| per pseudo-step [1e-8] */
   int32_t cg_max_iter;                     /* [500] */
   int32_t shift_eps, shift_mom, shift_force; /* fixed-point exponents [40, 40, 32] */
@@ -290,7 +316,7 @@ int sedi_get_stats(sedi_handle* h, sedi_stats* out);
  * runs while a memory pool or a host framework owns all device memory, or a
  * plugin whose device allocations are forbidden after start-up.  It smooths
  * n_fields caller fields exactly like sedi_smooth (Sec. 2.4, Eq. 10; the mesh,
- * bandwidth, n_tau, cg_rtol, cg_max_iter and precision_form of *p), but keeps
+ * bandwidth, n_tau, tau_scheme, cg_rtol, cg_max_iter and precision_form of *p), but keeps
  * all scratch in one static device array of this library, so it allocates
  * nothing: no cudaMalloc/cudaFree, no allocating library routine.
  *   p       : parameters (only the mesh, box, bandwidth, solver and form fields
@@ -301,7 +327,7 @@ int sedi_get_stats(sedi_handle* h, sedi_stats* out);
  *   msg     : optional host buffer of msg_len bytes for an error message.
  * Limit: 8 * C <= SEDI_STATIC_MAX_WORDS, i.e. up to 131,072 cells with any
  * n_fields <= 8 (the solver keeps 8 words per cell); larger meshes return
- * SEDI_EINVAL.  The scratch (about 42 MB) lives on every GPU
+ * SEDI_EINVAL.  The scratch (about 50 MB) lives on every GPU
  * that loads the library until the process exits.  The first call on a device
  * looks up the scratch's device address (cudaGetSymbolAddress) for that device;
  * make that first call before any stream capture.  Every call shares the one

@@ -28,6 +28,8 @@ class OrcParams(C.Structure):
         ("ncell", _I * 3),
         ("bandwidth", _D * 3), ("n_tau", _I), ("cg_rtol", _D), ("cg_max_iter", _I),
         ("shift_eps", _I), ("shift_mom", _I), ("shift_force", _I),
+        ("contact_law", _I), ("kn_linear", _D), ("kt_ratio", _D), ("tau_scheme", _I),
+        ("lift", _I), ("c_lift", _D), ("lub_tangential", _I),
     ]
 
 
@@ -67,6 +69,14 @@ def lib():
         L.orc_drag.restype = None
         L.orc_vr.argtypes = [_D, _D]
         L.orc_vr.restype = _D
+        L.orc_curl.argtypes = [C.POINTER(OrcParams), _P, _P]
+        L.orc_curl.restype = None
+        L.orc_lift.argtypes = [C.POINTER(OrcParams), _P, _P, _D, _P]
+        L.orc_lift.restype = None
+        L.orc_lub_pair.argtypes = [C.POINTER(OrcParams), _P, _D, _D, _P, _P, _P, _P, _P, _P, _P]
+        L.orc_lub_pair.restype = None
+        L.orc_lub_wall.argtypes = [C.POINTER(OrcParams), _P, _D, _D, _P, _P, _P, _P]
+        L.orc_lub_wall.restype = None
         L.orc_cnn_num_params.argtypes = []
         L.orc_cnn_num_params.restype = _L
         L.orc_cnn_forward.argtypes = [C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P, _I]
@@ -82,10 +92,13 @@ def lib():
 def make_params(prm: dict) -> OrcParams:
     """Fill the oracle's own parameter struct from a plain dict of physical inputs."""
     p = OrcParams()
+    # the contact law defaults to Hertz-Mindlin (the linear law's inputs then unused)
+    optional = {"contact_law": 0, "kn_linear": 800.0, "kt_ratio": 2.0 / 7.0, "tau_scheme": 0,
+                "lift": 0, "c_lift": 1.6, "lub_tangential": 0}
     for name, ctype in OrcParams._fields_:
-        if name not in prm:
+        if name not in prm and name not in optional:
             raise KeyError(f"oracle parameter {name!r} missing")
-        val = prm[name]
+        val = prm.get(name, optional.get(name))
         if hasattr(ctype, "_length_"):
             setattr(p, name, ctype(*val))
         else:
@@ -212,6 +225,45 @@ def drag(prm: dict, eps_s, w, d):
 
 def vr(eps_f, Re):
     return lib().orc_vr(float(eps_f), float(Re))
+
+
+def curl(prm: dict, U):
+    """Cell-centred vorticity of the oracle from U [C, 3]."""
+    p = make_params(prm)
+    U = np.ascontiguousarray(U, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros_like(U)
+    lib().orc_curl(C.byref(p), _ptr(U), _ptr(out))
+    return out
+
+
+def lift(prm: dict, w, omega, d):
+    """Single-particle lift of the oracle for slip w = U_f - u_p and vorticity omega."""
+    p = make_params(prm)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    f = np.zeros(3)
+    lib().orc_lift(C.byref(p), _ptr(w), _ptr(om), float(d), _ptr(f))
+    return f
+
+
+def lub_pair(prm: dict, dx, ra, rb, va, vb, wa, wb):
+    """Lubrication of the pair (a, b), dx = x_b - x_a: (force on a, torque on a, torque on b)."""
+    p = make_params(prm)
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (dx, va, vb, wa, wb)]
+    F, Ta, Tb = np.zeros(3), np.zeros(3), np.zeros(3)
+    lib().orc_lub_pair(C.byref(p), _ptr(a[0]), float(ra), float(rb), _ptr(a[1]), _ptr(a[2]),
+                       _ptr(a[3]), _ptr(a[4]), _ptr(F), _ptr(Ta), _ptr(Tb))
+    return F, Ta, Tb
+
+
+def lub_wall(prm: dict, n, dist, r, v, w):
+    """Lubrication of a sphere against a wall (n towards the wall): (force, torque)."""
+    p = make_params(prm)
+    a = [np.ascontiguousarray(x, dtype=np.float64) for x in (n, v, w)]
+    F, T = np.zeros(3), np.zeros(3)
+    lib().orc_lub_wall(C.byref(p), _ptr(a[0]), float(dist), float(r), _ptr(a[1]), _ptr(a[2]),
+                       _ptr(F), _ptr(T))
+    return F, T
 
 
 # ---------------------------------------------------------------- learned warm start

@@ -51,6 +51,18 @@ typedef struct {
   /* fixed-point exponents of the deposited fields: solid fraction,
      momentum (eps*U) and force density */
   int32_t shift_eps, shift_mom, shift_force;
+  /* contact law: 0 Hertz-Mindlin, 1 linear spring-dashpot (Sec. 2.5, Table 1) with
+     normal stiffness kn_linear (N/m) and tangential stiffness kt_ratio * kn_linear */
+  int32_t contact_law;
+  double kn_linear, kt_ratio;
+  /* pseudo-time scheme of the smoothing: 0 backward Euler, 1 second-order BDF
+     (its first step backward Euler) */
+  int32_t tau_scheme;
+  /* Saffman lift (Sec. 2.3, Eq. 7) with coefficient c_lift (1.6), and the
+     tangential (shear) lubrication terms of the Ball-Melrose model (Sec. 2.5) */
+  int32_t lift;
+  double c_lift;
+  int32_t lub_tangential;
 } orc_params;
 
 typedef struct orc_handle orc_handle;
@@ -103,5 +115,18 @@ int orc_average(orc_handle* h, double* eps, double* Us, double* Ffp);
 void orc_drag(const orc_params* p, double eps_s, const double w[3], double d,
               double out_f[3], double* Vr, double* Cd_times_w);
 double orc_vr(double eps_f, double Re);
+/* Vorticity curl U of a cell-centred field U (C*3) into omega (C*3). */
+void orc_curl(const orc_params* p, const double* U, double* omega);
+/* Lift force on a sphere of diameter d with slip w = U_f - u_p in vorticity omega. */
+void orc_lift(const orc_params* p, const double w[3], const double omega[3], double d,
+              double out_f[3]);
+/* Lubrication on a for the pair (a, b), dx = x_b - x_a: force on a, torques on a
+   and b (b receives -F). */
+void orc_lub_pair(const orc_params* p, const double dx[3], double ra, double rb,
+                  const double va[3], const double vb[3], const double wa[3],
+                  const double wb[3], double F[3], double Ta[3], double Tb[3]);
+/* Lubrication against a wall: n unit normal towards the wall, dist centre-to-plane. */
+void orc_lub_wall(const orc_params* p, const double n[3], double dist, double r,
+                  const double v[3], const double w[3], double F[3], double T[3]);
 
 }  /* extern "C" */

@@ -15,8 +15,11 @@
  *
  * Smoothing, Eq. (10): d(phi)/d(tau) = div(D grad phi) up to unit pseudo-time,
  * D_a = b_a^2 / 4 per axis, which equals Gaussian-kernel averaging with
- * bandwidth b (kernel exp(-r^2/b^2)).  Readings: n_tau backward-Euler steps of
- * size 1/n_tau (the paper's OpenFOAM run uses a second-order implicit scheme),
+ * bandwidth b (kernel exp(-r^2/b^2)).  Readings: n_tau implicit steps of size
+ * dtau = 1/n_tau, backward Euler  (I - dtau L) phi^{m+1} = phi^m  by default, or the
+ * second-order implicit scheme the paper's OpenFOAM run uses (Sec. 2.4), read as
+ * BDF2:  (I - (2/3) dtau L) phi^{m+1} = (4/3) phi^m - (1/3) phi^{m-1}, its first step
+ * backward Euler (both keep sum(phi) since (4/3) - (1/3) = 1),
  * the 7-point finite-volume Laplacian with zero flux through non-periodic faces
  * (Sec. 2.4: "no-flux boundary condition ... conservative"), each step solved by
  * plain unpreconditioned conjugate gradients to ||r|| <= rtol ||b|| from
@@ -163,12 +166,18 @@ int orc_smooth(orc_handle* h, int32_t nf, double* phi, const double* guess, int3
     double D = 0.25 * p.bandwidth[a] * p.bandwidth[a];
     coef[a] = dtau * D / (dxs[a] * dxs[a]);
   }
+  const double coef2[3] = {2.0 / 3.0 * coef[0], 2.0 / 3.0 * coef[1], 2.0 / 3.0 * coef[2]};
   int status = 0;
   for (int32_t f = 0; f < nf; ++f) {
     std::vector<double> x(phi + f * C, phi + (f + 1) * C);
+    std::vector<double> x_prev;
     int32_t total = 0;
     for (int32_t m = 0; m < p.n_tau; ++m) {
+      const bool bdf2 = p.tau_scheme == 1 && m > 0;
       std::vector<double> b = x;
+      if (bdf2)
+        for (int64_t c = 0; c < C; ++c) b[c] = 4.0 / 3.0 * x[c] - 1.0 / 3.0 * x_prev[c];
+      x_prev = x;
       if (m == 0 && guess) {
         x.assign(guess + f * C, guess + (f + 1) * C);
         double sb = 0.0, sx = 0.0;
@@ -179,7 +188,7 @@ int orc_smooth(orc_handle* h, int32_t nf, double* phi, const double* guess, int3
         double shift = (sb - sx) / (double)C;
         for (int64_t c = 0; c < C; ++c) x[c] += shift;
       }
-      int it = cg(p, coef, b, x);
+      int it = cg(p, bdf2 ? coef2 : coef, b, x);
       if (it < 0) {
         status = -6;
         it = p.cg_max_iter;

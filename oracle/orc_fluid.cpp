@@ -20,6 +20,19 @@
  *   f_add = C_add rho_f V_p (DU_f/Dt - a_prev),
  * where a_prev is the particle's acceleration of the previous substep (the paper
  * uses the particle velocity of the previous time).
+ * Lift, Eq. (7) (lift = 1), printed as C_l rho_f nu^0.5 D^2 (u_p - U_f) x grad U_f,
+ * which is not a force dimensionally and whose sign would push a particle that lags
+ * the flow towards slower fluid.  Reading: Saffman's (1965) shear lift, of which the
+ * print is the scalar shear-flow form,
+ *   f_lift = C_l rho_f nu^0.5 d^2 |omega|^(-1/2) (w x omega),  w = U_f - u_p,
+ *   omega = curl U_f at the particle, C_l = 1.6,
+ * so a sphere at rest in the shear flow U = (G z, 0, 0) feels
+ * C_l rho_f nu^0.5 d^2 G^0.5 U_x along +z (towards the faster fluid); f_lift = 0
+ * where omega = 0.  omega is the trilinear interpolant of the cell-centred vorticity
+ * of U_f (the paper takes grad U_f from the fluid solver): second-order central
+ * differences, wrapped on periodic axes, one-sided in the first and last cell of
+ * other axes, zero along an axis of one cell.  The lift is part of f_fp, so the
+ * fluid also receives it through the deposition.
  */
 #include "orc_internal.h"
 
@@ -108,9 +121,63 @@ V3 drag_force(const orc_params& p, double eps_s, V3 w, double d, double* Vr_out,
   return scl(0.75 * Cd * p.rho_f * wmag * Vp / (Vr * Vr * d), w);
 }
 
+void curl_cells(const orc_params& p, const std::vector<double>& U, std::vector<double>& out) {
+  const int64_t n[3] = {p.ncell[0], p.ncell[1], p.ncell[2]};
+  const int64_t C = n[0] * n[1] * n[2];
+  out.assign(3 * C, 0.0);
+  for (int64_t iz = 0; iz < n[2]; ++iz)
+    for (int64_t iy = 0; iy < n[1]; ++iy)
+      for (int64_t ix = 0; ix < n[0]; ++ix) {
+        const int64_t idx[3] = {ix, iy, iz};
+        /* g[a][b] = dU_b / dx_a at this cell */
+        double g[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int a = 0; a < 3; ++a) {
+          if (n[a] < 2) continue;
+          const double h = (p.hi[a] - p.lo[a]) / (double)n[a];
+          int64_t ip[3] = {ix, iy, iz}, im[3] = {ix, iy, iz};
+          double den;
+          if (p.periodic[a]) {
+            ip[a] = (idx[a] + 1) % n[a];
+            im[a] = (idx[a] + n[a] - 1) % n[a];
+            den = 2.0 * h;
+          } else if (idx[a] == 0) {
+            ip[a] = 1;
+            den = h;
+          } else if (idx[a] == n[a] - 1) {
+            im[a] = n[a] - 2;
+            den = h;
+          } else {
+            ip[a] = idx[a] + 1;
+            im[a] = idx[a] - 1;
+            den = 2.0 * h;
+          }
+          const int64_t cp = (ip[2] * n[1] + ip[1]) * n[0] + ip[0];
+          const int64_t cm = (im[2] * n[1] + im[1]) * n[0] + im[0];
+          for (int b = 0; b < 3; ++b) g[a][b] = (U[3 * cp + b] - U[3 * cm + b]) / den;
+        }
+        const int64_t c = (iz * n[1] + iy) * n[0] + ix;
+        out[3 * c + 0] = g[1][2] - g[2][1];
+        out[3 * c + 1] = g[2][0] - g[0][2];
+        out[3 * c + 2] = g[0][1] - g[1][0];
+      }
+}
+
+V3 lift_force(const orc_params& p, V3 w, V3 omega, double d) {
+  double om = norm(omega);
+  if (!(om > 0.0)) return V3{0, 0, 0};
+  return scl(p.c_lift * p.rho_f * std::sqrt(p.nu_f) * d * d / std::sqrt(om), cross(w, omega));
+}
+
 V3 fluid_force(const orc_params& p, const FluidFields& ff, V3 x, V3 u, V3 a_prev, double d) {
   double Vp = M_PI / 6.0 * d * d * d;
   V3 f{0, 0, 0};
+  if (p.lift) {
+    V3 U{interp_scalar(p, *ff.U, 3, 0, x), interp_scalar(p, *ff.U, 3, 1, x),
+         interp_scalar(p, *ff.U, 3, 2, x)};
+    V3 om{interp_scalar(p, *ff.curlU, 3, 0, x), interp_scalar(p, *ff.curlU, 3, 1, x),
+          interp_scalar(p, *ff.curlU, 3, 2, x)};
+    f = add(f, lift_force(p, sub(U, u), om, d));
+  }
   if (p.drag) {
     V3 U{interp_scalar(p, *ff.U, 3, 0, x), interp_scalar(p, *ff.U, 3, 1, x),
          interp_scalar(p, *ff.U, 3, 2, x)};
@@ -143,5 +210,18 @@ void orc_drag(const orc_params* p, double eps_s, const double w[3], double d, do
 }
 
 double orc_vr(double eps_f, double Re) { return orc::vr_of(eps_f, Re); }
+
+void orc_curl(const orc_params* p, const double* U, double* omega) {
+  const int64_t C = (int64_t)p->ncell[0] * p->ncell[1] * p->ncell[2];
+  std::vector<double> u(U, U + 3 * C), out;
+  orc::curl_cells(*p, u, out);
+  for (int64_t k = 0; k < 3 * C; ++k) omega[k] = out[k];
+}
+
+void orc_lift(const orc_params* p, const double w[3], const double omega[3], double d,
+              double out_f[3]) {
+  orc::V3 f = orc::lift_force(*p, orc::load(w, 0), orc::load(omega, 0), d);
+  orc::store(out_f, 0, f);
+}
 
 }  // extern "C"

@@ -50,9 +50,13 @@ ContactOut hm_pair(const orc_params& p, V3 dx, double ra, double rb, double ma, 
    wall, dist the centre-to-plane distance. */
 ContactOut hm_wall(const orc_params& p, V3 n, double dist, double r, double m, V3 v, V3 w,
                    V3 xi_old);
-/* Ball-Melrose normal lubrication on a for the pair (a, b). */
-V3 lub_pair(const orc_params& p, V3 dx, double ra, double rb, V3 va, V3 vb);
-V3 lub_wall(const orc_params& p, V3 n, double dist, double r, V3 v);
+/* Ball-Melrose lubrication on a for the pair (a, b): force on a, torques on a
+   and on b (b receives -F). */
+struct LubOut {
+  V3 F, Ta, Tb;
+};
+LubOut lub_pair(const orc_params& p, V3 dx, double ra, double rb, V3 va, V3 vb, V3 wa, V3 wb);
+LubOut lub_wall(const orc_params& p, V3 n, double dist, double r, V3 v, V3 w);
 
 /* Fluid-particle force at one particle (Sec. 2.3). */
 struct FluidFields {
@@ -60,7 +64,11 @@ struct FluidFields {
   const std::vector<double>* gradp; /* C*3 */
   const std::vector<double>* DUDt;  /* C*3 */
   const std::vector<double>* eps;   /* C */
+  const std::vector<double>* curlU; /* C*3, vorticity of U */
 };
+/* Vorticity of a cell-centred velocity field (C*3 in, C*3 out). */
+void curl_cells(const orc_params& p, const std::vector<double>& U, std::vector<double>& out);
+V3 lift_force(const orc_params& p, V3 w, V3 omega, double d);
 double interp_scalar(const orc_params& p, const std::vector<double>& f, int ncomp, int comp,
                      V3 x);
 V3 fluid_force(const orc_params& p, const FluidFields& ff, V3 x, V3 u, V3 a_prev, double d);
@@ -84,5 +92,6 @@ struct orc_handle {
   /* tangential spring of each particle against each of the six walls */
   std::vector<orc::V3> whist; /* n*6 */
   std::vector<double> U, gradp, DUDt, eps;
+  std::vector<double> curlU; /* C*3, curl of U (lift force) */
   int64_t ncells() const { return (int64_t)p.ncell[0] * p.ncell[1] * p.ncell[2]; }
 };

@@ -58,13 +58,15 @@ void evaluate(orc_handle* h, Forces& out,
       if (new_hist) (*new_hist)[pr] = c.xi;
     }
     if (p.lubrication) {
-      V3 fl = orc::lub_pair(p, dx, r[i], r[j], h->v[i], h->v[j]);
-      out.fl[i] = orc::add(out.fl[i], fl);
-      out.fl[j] = orc::sub(out.fl[j], fl);
+      orc::LubOut l = orc::lub_pair(p, dx, r[i], r[j], h->v[i], h->v[j], h->w[i], h->w[j]);
+      out.fl[i] = orc::add(out.fl[i], l.F);
+      out.fl[j] = orc::sub(out.fl[j], l.F);
+      out.tq[i] = orc::add(out.tq[i], l.Ta);
+      out.tq[j] = orc::add(out.tq[j], l.Tb);
     }
   }
   if (new_whist) new_whist->assign(n * 6, V3{0, 0, 0});
-  orc::FluidFields ff{&h->U, &h->gradp, &h->DUDt, &h->eps};
+  orc::FluidFields ff{&h->U, &h->gradp, &h->DUDt, &h->eps, &h->curlU};
   for (int64_t i = 0; i < n; ++i) {
     for (int a = 0; a < 3; ++a) {
       if (p.periodic[a]) continue;
@@ -83,7 +85,11 @@ void evaluate(orc_handle* h, Forces& out,
           out.tq[i] = orc::add(out.tq[i], c.Ta);
           if (new_whist) (*new_whist)[i * 6 + slot] = c.xi;
         }
-        if (p.lubrication) out.fl[i] = orc::add(out.fl[i], orc::lub_wall(p, nrm, dist, r[i], h->v[i]));
+        if (p.lubrication) {
+          orc::LubOut l = orc::lub_wall(p, nrm, dist, r[i], h->v[i], h->w[i]);
+          out.fl[i] = orc::add(out.fl[i], l.F);
+          out.tq[i] = orc::add(out.tq[i], l.Ta);
+        }
       }
     }
     out.ff[i] = orc::fluid_force(p, ff, h->x[i], h->v[i], h->a_prev[i], h->d[i]);
@@ -104,6 +110,7 @@ orc_handle* orc_create(const orc_params* p) {
     for (int a = 0; a < 3; ++a) h->gradp[3 * c + a] = p->rho_f * p->g[a];
   h->DUDt.assign(C * 3, 0.0);
   h->eps.assign(C, 0.0);
+  h->curlU.assign(C * 3, 0.0);
   return h;
 }
 
@@ -135,7 +142,10 @@ int orc_set_accel(orc_handle* h, const double* a) {
 
 int orc_set_fluid(orc_handle* h, const double* U, const double* gp, const double* Du) {
   int64_t C = h->ncells();
-  if (U) h->U.assign(U, U + 3 * C);
+  if (U) {
+    h->U.assign(U, U + 3 * C);
+    orc::curl_cells(h->p, h->U, h->curlU);
+  }
   if (gp) h->gradp.assign(gp, gp + 3 * C);
   if (Du) h->DUDt.assign(Du, Du + 3 * C);
   return 0;

@@ -42,7 +42,10 @@ struct Ctl {
 template <class F>
 struct ForceConsts {
   F Es, Gs, cdamp, kn_fac, mu, dt;     // contact: E*, G*, -2 sqrt(5/6) beta, (4/3)E*, friction
+  int32_t law;                         // 0 Hertz-Mindlin, 1 linear spring-dashpot
+  F kn_lin, kt_lin, cdamp_lin;         // linear law: k_n, k_t, -2 beta
   F lub_in, lub_out, six_pi_mu;        // lubrication limits (fractions of mean diameter), 6 pi mu_f
+  F lift_c;                            // lift: C_l rho_f sqrt(nu_f)
   F rho_f, nu_f, c_add_rho_f, eps_max; // fluid
   F g[3];
   F lo[3], L[3], halfL[3], inv_h[3];   // box and mesh spacing (1/h = ncell/L)
@@ -59,6 +62,7 @@ struct DevParams {
   double lo[3], hi[3], L[3];
   int32_t periodic[3], wall_lo[3], wall_hi[3];
   int32_t lubrication, drag, pressure_grad, added_mass;
+  int32_t lift, lub_tangential;
   ForceConsts<float> cf;
   ForceConsts<double> cd;
   BoxS<float> bf;
@@ -258,10 +262,12 @@ struct DevState {
 };
 
 // Mesh arrays (type-erased Quad<F>): ufe = (Ux, Uy, Uz, eps_s), gfl = G where
-// the pressure-gradient + fluid-acceleration part of f_fp is V_p * G.
+// the pressure-gradient + fluid-acceleration part of f_fp is V_p * G, wfl =
+// (curl U, 0) for the lift force.
 struct DevMesh {
   void* ufe;
   void* gfl;
+  void* wfl;
   int64_t C;
 };
 

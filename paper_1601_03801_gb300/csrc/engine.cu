@@ -169,11 +169,16 @@ void fill_consts(const sedi_params& p, ForceConsts<F>& K) {
   K.Gs = (F)Gs;
   K.cdamp = (F)(-2.0 * std::sqrt(5.0 / 6.0) * beta);
   K.kn_fac = (F)(4.0 / 3.0 * Es);
+  K.law = p.contact_law;
+  K.kn_lin = (F)p.kn_linear;
+  K.kt_lin = (F)(p.kt_ratio * p.kn_linear);
+  K.cdamp_lin = (F)(-2.0 * beta);
   K.mu = (F)p.friction;
   K.dt = (F)p.dt;
   K.lub_in = (F)p.lub_h_in_frac;
   K.lub_out = (F)p.lub_h_out_frac;
   K.six_pi_mu = (F)(6.0 * M_PI * p.rho_f * p.nu_f);
+  K.lift_c = (F)(p.c_lift * p.rho_f * std::sqrt(p.nu_f));
   K.rho_f = (F)p.rho_f;
   K.nu_f = (F)p.nu_f;
   K.c_add_rho_f = (F)(p.c_add * p.rho_f);
@@ -214,6 +219,8 @@ void fill_params(sedi_handle* h) {
   P.drag = p.drag ? 1 : 0;
   P.pressure_grad = p.pressure_grad ? 1 : 0;
   P.added_mass = p.added_mass ? 1 : 0;
+  P.lift = p.lift ? 1 : 0;
+  P.lub_tangential = (p.lubrication && p.lub_tangential) ? 1 : 0;
   fill_consts<float>(p, P.cf);
   fill_consts<double>(p, P.cd);
   P.C = (int64_t)p.ncell[0] * p.ncell[1] * p.ncell[2];
@@ -241,10 +248,14 @@ void fill_params(sedi_handle* h) {
 }
 
 int check_params(sedi_handle* h, const sedi_params& p) {
-  if (p.contact_law != SEDI_HERTZ_MINDLIN) return fail(h, SEDI_EINVAL, "contact_law: only SEDI_HERTZ_MINDLIN");
+  if (p.contact_law != SEDI_HERTZ_MINDLIN && p.contact_law != SEDI_LINEAR_SPRING)
+    return fail(h, SEDI_EINVAL, "contact_law must be SEDI_HERTZ_MINDLIN or SEDI_LINEAR_SPRING");
+  if (p.contact_law == SEDI_LINEAR_SPRING && (!(p.kn_linear > 0) || !(p.kt_ratio >= 0)))
+    return fail(h, SEDI_EINVAL, "linear contact law needs kn_linear > 0 and kt_ratio >= 0");
   if (!(p.E > 0) || !(p.poisson >= 0 && p.poisson < 0.5)) return fail(h, SEDI_EINVAL, "E > 0 and 0 <= poisson < 0.5 required");
   if (!(p.restitution > 0 && p.restitution <= 1)) return fail(h, SEDI_EINVAL, "restitution must be in (0, 1]");
   if (!(p.friction >= 0)) return fail(h, SEDI_EINVAL, "friction must be >= 0");
+  if (!(p.c_lift >= 0)) return fail(h, SEDI_EINVAL, "c_lift must be >= 0");
   if (!(p.rho_f > 0) || !(p.nu_f > 0)) return fail(h, SEDI_EINVAL, "rho_f, nu_f must be > 0");
   if (!(p.dt > 0) || !(p.skin >= 0)) return fail(h, SEDI_EINVAL, "dt > 0 and skin >= 0 required");
   for (int a = 0; a < 3; ++a) {
@@ -254,6 +265,10 @@ int check_params(sedi_handle* h, const sedi_params& p) {
   }
   if (!(p.lub_h_in_frac > 0) || !(p.lub_h_out_frac > p.lub_h_in_frac)) return fail(h, SEDI_EINVAL, "need 0 < lub_h_in_frac < lub_h_out_frac");
   if (p.n_tau < 1 || !(p.cg_rtol > 0) || p.cg_max_iter < 1) return fail(h, SEDI_EINVAL, "n_tau, cg_rtol, cg_max_iter must be positive");
+  if (p.tau_scheme != SEDI_TAU_EULER && p.tau_scheme != SEDI_TAU_BDF2)
+    return fail(h, SEDI_EINVAL, "tau_scheme must be SEDI_TAU_EULER or SEDI_TAU_BDF2");
+  if (p.tau_scheme == SEDI_TAU_BDF2 && p.use_cnn_guess)
+    return fail(h, SEDI_EINVAL, "the learned warm start runs backward-Euler pseudo-steps only");
   if (p.precision_form < 0 || p.precision_form > 2) return fail(h, SEDI_EINVAL, "unknown precision_form");
   if (p.nbr_capacity < 1 || p.nbr_capacity > 32) return fail(h, SEDI_EINVAL, "nbr_capacity must be in [1, 32]");
   if (p.n_beds < 1 || p.n_beds > kMaxBeds) return fail(h, SEDI_EINVAL, "n_beds must be in [1, %d]", kMaxBeds);
@@ -302,7 +317,7 @@ int sync_status(sedi_handle* h) {
   return 0;
 }
 
-int upload_mesh(sedi_handle* h) {
+int upload_mesh(sedi_handle* h, bool velocity = true) {
   const int64_t C = h->P.C;
   const int form = h->form;
   const sedi_params& p = h->prm;
@@ -329,7 +344,21 @@ int upload_mesh(sedi_handle* h) {
     CK(cudaMemcpyAsync(h->mesh.ufe, uf.data(), 16 * C, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->mesh.gfl, gf.data(), 16 * C, cudaMemcpyHostToDevice, h->stream));
   }
-  CK(cudaStreamSynchronize(h->stream));
+  if (!velocity) {
+    CK(cudaStreamSynchronize(h->stream));
+    return 0;
+  }
+  // vorticity of U for the lift force, from the FP64 velocities
+  double* Ud = nullptr;
+  CK(cudaMalloc((void**)&Ud, 24 * C));
+  cudaError_t e = cudaMemcpyAsync(Ud, h->U.data(), 24 * C, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) {
+    launch_curl(form, Ud, h->P, h->mesh.wfl, h->stream);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(Ud);
+  if (e != cudaSuccess) return fail(h, SEDI_ECUDA, "vorticity of the fluid velocity: %s", cudaGetErrorString(e));
   return 0;
 }
 
@@ -619,6 +648,8 @@ void sedi_default_params(sedi_params* p) {
   p->poisson = 0.3;
   p->restitution = 0.9;
   p->friction = 0.3;
+  p->kn_linear = 800.0;
+  p->kt_ratio = 2.0 / 7.0;
   p->rho_f = 1000.0;
   p->nu_f = 1.0e-6;
   p->g[2] = -9.81;
@@ -633,12 +664,14 @@ void sedi_default_params(sedi_params* p) {
   p->lub_h_in_frac = 1.0e-3;
   p->lub_h_out_frac = 0.1;
   p->c_add = 0.5;
+  p->c_lift = 1.6;
   p->eps_max = 0.9;
   p->ncell[0] = 10;
   p->ncell[1] = 10;
   p->ncell[2] = 20;
   p->bandwidth[0] = p->bandwidth[1] = p->bandwidth[2] = 3e-3;
   p->n_tau = 4;
+  p->tau_scheme = SEDI_TAU_EULER;
   p->cg_rtol = 1e-8;
   p->cg_max_iter = 500;
   p->shift_eps = 40;
@@ -684,13 +717,14 @@ int sedi_create(const sedi_params* p, sedi_handle** out) {
   const size_t fq = fquad_bytes(h->form);
   if ((rc = dmalloc(h, h->mesh_allocs, &h->mesh.ufe, fq * C)) ||
       (rc = dmalloc(h, h->mesh_allocs, &h->mesh.gfl, fq * C)) ||
+      (rc = dmalloc(h, h->mesh_allocs, &h->mesh.wfl, fq * C)) ||
       (rc = dmalloc(h, h->mesh_allocs, &h->qfix, 8 * 7 * C)) ||
       (rc = dmalloc(h, h->mesh_allocs, &h->phi, 8 * 8 * C)) ||
       (rc = dmalloc(h, h->mesh_allocs, (void**)&h->iters_dev, 4 * 8))) {
     sedi_destroy(h);
     return rc;
   }
-  h->work_bytes = smooth_work_bytes(h->form, C, 8);
+  h->work_bytes = smooth_work_bytes(h->form, C, 8, h->prm.tau_scheme);
   if ((rc = dmalloc(h, h->mesh_allocs, &h->work, h->work_bytes))) {
     sedi_destroy(h);
     return rc;
@@ -894,7 +928,7 @@ int sedi_set_eps(sedi_handle* h, int32_t bed, const double* eps, int32_t mem) {
   } else {
     std::memcpy(h->eps.data(), eps, 8 * C);
   }
-  return upload_mesh(h);
+  return upload_mesh(h, false);
 }
 
 static int ens_step(sedi_handle* h, int n);
@@ -983,7 +1017,8 @@ static int smooth_dev(sedi_handle* h, int nf, const void* guess, int n_tau = -1,
   // FP32 words cannot reach a relative residual much below 1e-6
   const double rtol = h->form == FORM_PLAIN ? std::max(h->prm.cg_rtol, 2e-6) : h->prm.cg_rtol;
   int rc = launch_smooth(h->form, h->P, h->phi, guess, nf, h->work, h->st, h->iters_dev,
-                         rtol, h->prm.cg_max_iter, n_tau > 0 ? n_tau : h->prm.n_tau, h->coef,
+                         rtol, h->prm.cg_max_iter, n_tau > 0 ? n_tau : h->prm.n_tau,
+                         h->prm.tau_scheme, h->coef,
                          h->stream);
   if (rc) return fail(h, SEDI_ECUDA, "cooperative launch of the smoother failed: %s", cudaGetErrorString(cudaGetLastError()));
   return 0;
@@ -1227,7 +1262,7 @@ static int ens_average(sedi_handle* h) {
   CK(cudaMemsetAsync(h->ens_iters, 0, sizeof(int) * 8 * B, h->stream));
   const double rtol = h->form == FORM_PLAIN ? std::max(h->prm.cg_rtol, 2e-6) : h->prm.cg_rtol;
   if (launch_smooth_batch(h->form, m.data(), B, 7, h->ens_smooth, rtol, h->prm.cg_max_iter,
-                          h->prm.n_tau, h->st.ctl, 1 << 30, h->stream))
+                          h->prm.n_tau, h->prm.tau_scheme, h->st.ctl, 1 << 30, h->stream))
     return fail(h, SEDI_ECUDA, "cooperative launch of the batched smoother failed: %s",
                 cudaGetErrorString(cudaGetLastError()));
   launch_eps_out_ens(h->form, h->ens, h->stream);
@@ -1595,7 +1630,7 @@ int state_io(sedi_handle* h, FILE* f, bool save) {
       {s.whist[c.pb], (size_t)kWalls * 3 * w * N}, {s.wmask[c.pb], 4 * (size_t)N},
       {s.nbr[c.nl], 4 * (size_t)cap * N}, {s.nn[c.nl], 4 * (size_t)N},
       {s.hist[c.nl], q * cap * N}, {s.cmask[c.nl], 4 * (size_t)N},
-      {h->mesh.ufe, fq * C}, {h->mesh.gfl, fq * C}};
+      {h->mesh.ufe, fq * C}, {h->mesh.gfl, fq * C}, {h->mesh.wfl, fq * C}};
   for (auto& it : items)
     if ((rc = dev_io(h, f, it.p, it.n, save))) return rc;
   if (save) {

@@ -31,14 +31,17 @@ __device__ __forceinline__ void axis_w(F s, int n, int per, int* i0, int* i1, F*
 }
 
 // Fluid force on one particle (Sec. 2.3): drag (Eq. 3-6, Syamlal-O'Brien), the
-// pressure-gradient force and added mass (Eq. 8).  The mesh carries
-// G = -grad p + C_add rho_f DU/Dt so both linear terms come from one
-// interpolation.  Drag is written in a form without 1/Re:
+// pressure-gradient force, added mass (Eq. 8) and, when switched on, Saffman lift
+// (Eq. 7, read as C_l rho_f nu^0.5 d^2 |omega|^-0.5 (w x omega), w = U_f - u_p).
+// The mesh carries G = -grad p + C_add rho_f DU/Dt so both linear terms come from
+// one interpolation, and the cell vorticity omega = curl U_f for the lift.  Drag is
+// written in a form without 1/Re:
 //   C_d |w| = (0.63 sqrt|w| + 4.8 sqrt(V_r nu / d))^2.
 template <class S, class F>
 __device__ __forceinline__ void fluid_force(const DevParams& P, const ForceConsts<F>& K,
-                                            const Quad<F>* ufe, const Quad<F>* gfl, const S* x,
-                                            F r, const F v[3], const F a_prev[3], F out[3]) {
+                                            const Quad<F>* ufe, const Quad<F>* gfl,
+                                            const Quad<F>* wfl, const S* x, F r, const F v[3],
+                                            const F a_prev[3], F out[3]) {
   using NS = Num<S>;
   const BoxS<S>& B = sbox<S>(P);
   int i0[3], i1[3];
@@ -48,7 +51,7 @@ __device__ __forceinline__ void fluid_force(const DevParams& P, const ForceConst
     F s = rel * K.inv_h[a] - F(0.5);
     axis_w<F>(s, P.nc[a], P.periodic[a], &i0[a], &i1[a], &fr[a]);
   }
-  F U[3] = {0, 0, 0}, G[3] = {0, 0, 0}, eps = 0;
+  F U[3] = {0, 0, 0}, G[3] = {0, 0, 0}, Om[3] = {0, 0, 0}, eps = 0;
   const int64_t nx = P.nc[0], ny = P.nc[1];
   for (int kz = 0; kz < 2; ++kz) {
     int iz = kz ? i1[2] : i0[2];
@@ -71,6 +74,12 @@ __device__ __forceinline__ void fluid_force(const DevParams& P, const ForceConst
           G[0] += w * g.a;
           G[1] += w * g.b;
           G[2] += w * g.c;
+        }
+        if (P.lift) {
+          Quad<F> o = ldq(wfl + c);
+          Om[0] += w * o.a;
+          Om[1] += w * o.b;
+          Om[2] += w * o.c;
         }
       }
     }
@@ -101,6 +110,16 @@ __device__ __forceinline__ void fluid_force(const DevParams& P, const ForceConst
     out[0] += coef * w0;
     out[1] += coef * w1;
     out[2] += coef * w2;
+  }
+  if (P.lift) {
+    const F om = xsqrt(Om[0] * Om[0] + Om[1] * Om[1] + Om[2] * Om[2]);
+    if (om > F(0)) {
+      const F s = K.lift_c * d * d / xsqrt(om);
+      const F w0 = U[0] - v[0], w1 = U[1] - v[1], w2 = U[2] - v[2];
+      out[0] += s * (w1 * Om[2] - w2 * Om[1]);
+      out[1] += s * (w2 * Om[0] - w0 * Om[2]);
+      out[2] += s * (w0 * Om[1] - w1 * Om[0]);
+    }
   }
 }
 

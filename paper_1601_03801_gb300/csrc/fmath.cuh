@@ -12,6 +12,8 @@ __device__ __forceinline__ double xpow(double a, double b) { return pow(a, b); }
 // hardware approximations; relative error ~1e-6 for a in [0.1, 1], b <= 4.14).
 __device__ __forceinline__ float xpow_drag(float a, float b) { return __powf(a, b); }
 __device__ __forceinline__ double xpow_drag(double a, double b) { return pow(a, b); }
+__device__ __forceinline__ float xlog(float a) { return logf(a); }
+__device__ __forceinline__ double xlog(double a) { return log(a); }
 __device__ __forceinline__ float xfloor(float a) { return floorf(a); }
 __device__ __forceinline__ double xfloor(double a) { return floor(a); }
 // a * b + c with a single rounding, written out so that the result does not depend

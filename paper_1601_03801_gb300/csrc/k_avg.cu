@@ -66,7 +66,8 @@ __device__ __forceinline__ void deposit_body(const DevState& st, const DevMesh& 
     const F vf[3] = {NS::f(v.a), NS::f(v.b), NS::f(v.c)};
     const F ap[3] = {acc.a, acc.b, acc.c};
     F ff[3];
-    fluid_force<S, F>(P, K, (const Quad<F>*)mesh.ufe, (const Quad<F>*)mesh.gfl, xs, NS::f(p.d), vf,
+    fluid_force<S, F>(P, K, (const Quad<F>*)mesh.ufe, (const Quad<F>*)mesh.gfl,
+                      (const Quad<F>*)mesh.wfl, xs, NS::f(p.d), vf,
                       ap, ff);
     const double vfrac = st.vfrac[pb][i];
     if (FORM == FORM_PLAIN) {
@@ -282,6 +283,46 @@ __global__ void k_eps_out_e(const BedView* v) {
     ufe[c].d = (F)CgA<T>::to_d(phi[c]);
 }
 
+// Cell vorticity omega = curl U of the cell-centred fluid velocity U (FP64, C x 3),
+// for the lift force (Sec. 2.3, Eq. 7): central differences, wrapped on periodic
+// axes, one-sided in the first and last cell of other axes, zero along an axis of
+// one cell; stored as (omega, 0) in the form's word.
+template <class F>
+__global__ void k_curl(const double* __restrict__ U, DevParams P, Quad<F>* __restrict__ wfl) {
+  const int64_t nx = P.nc[0], ny = P.nc[1], nz = P.nc[2];
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < P.C;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t idx[3] = {c % nx, (c / nx) % ny, c / (nx * ny)};
+    const int64_t n[3] = {nx, ny, nz};
+    double g[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // g[a][b] = dU_b / dx_a
+    for (int a = 0; a < 3; ++a) {
+      if (n[a] < 2) continue;
+      const double h = (P.hi[a] - P.lo[a]) / (double)n[a];
+      int64_t ip[3] = {idx[0], idx[1], idx[2]}, im[3] = {idx[0], idx[1], idx[2]};
+      double den;
+      if (P.periodic[a]) {
+        ip[a] = (idx[a] + 1) % n[a];
+        im[a] = (idx[a] + n[a] - 1) % n[a];
+        den = 2.0 * h;
+      } else if (idx[a] == 0) {
+        ip[a] = 1;
+        den = h;
+      } else if (idx[a] == n[a] - 1) {
+        im[a] = n[a] - 2;
+        den = h;
+      } else {
+        ip[a] = idx[a] + 1;
+        im[a] = idx[a] - 1;
+        den = 2.0 * h;
+      }
+      const int64_t cp = (ip[2] * ny + ip[1]) * nx + ip[0];
+      const int64_t cm = (im[2] * ny + im[1]) * nx + im[0];
+      for (int b = 0; b < 3; ++b) g[a][b] = (U[3 * cp + b] - U[3 * cm + b]) / den;
+    }
+    wfl[c] = Quad<F>{(F)(g[1][2] - g[2][1]), (F)(g[2][0] - g[0][2]), (F)(g[0][1] - g[1][0]), F(0)};
+  }
+}
+
 inline unsigned grid_for(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
   if (g < 1) g = 1;
@@ -299,6 +340,12 @@ void launch_deposit(int form, const DevState& st, const DevMesh& mesh, const Dev
     case FORM_PLAIN: k_deposit<FORM_PLAIN><<<g, 256, 0, s>>>(st, mesh, P, q); break;
     default: k_deposit<FORM_FP64><<<g, 256, 0, s>>>(st, mesh, P, q); break;
   }
+}
+
+void launch_curl(int form, const double* U, const DevParams& P, void* wfl, cudaStream_t s) {
+  const unsigned g = grid_for(P.C, 256);
+  if (form == FORM_FP64) k_curl<double><<<g, 256, 0, s>>>(U, P, (Quad<double>*)wfl);
+  else k_curl<float><<<g, 256, 0, s>>>(U, P, (Quad<float>*)wfl);
 }
 
 void launch_fields_from_fixed(int form, const void* q, const DevParams& P, void* phi, int nf,
@@ -389,12 +436,13 @@ namespace {
 constexpr int64_t kStaticWords = SEDI_STATIC_MAX_WORDS;
 // The solver keeps 8 narrow words per cell whatever n_fields is, so the limit is
 // 8 * cells <= kStaticWords (n_fields <= 8).  Upper bound of the solver scratch then:
-// the wide right-hand side (n_fields * cells <= kStaticWords words), three narrow
-// [cells][8] arrays (8-byte words at most), per-unit sums of up to
-// kStaticWords / 2048 + 1 units of 256 cells, and the batch tables of one mesh.
+// the wide right-hand side and the BDF2 previous step (n_fields * cells <=
+// kStaticWords words each), three narrow [cells][8] arrays (8-byte words at most),
+// per-unit sums of up to kStaticWords / 2048 + 1 units of 256 cells, and the batch
+// tables of one mesh.
 constexpr int64_t kStaticUnits = kStaticWords / 2048 + 1;
 constexpr int64_t kStaticWork =
-    ((8 * 4 * kStaticWords + kStaticUnits * 8 * 3 * 8 + 4 * kStaticUnits + 64 * 1024) + 255) / 256 * 256;
+    ((8 * 5 * kStaticWords + kStaticUnits * 8 * 3 * 8 + 4 * kStaticUnits + 64 * 1024) + 255) / 256 * 256;
 // layout: phi [W words] | solver scratch | iters[8] | ctl, every part 256-byte aligned
 // (the control block holds 8-byte words that the compiler may access in pairs)
 constexpr int64_t kStaticBytes = 8 * kStaticWords + kStaticWork + 256 + (int64_t)sizeof(Ctl) + 256;
@@ -423,7 +471,8 @@ extern "C" int sedi_smooth_static(const sedi_params* p, int32_t nf, const double
   }
   const int64_t C = (int64_t)p->ncell[0] * p->ncell[1] * p->ncell[2];
   if (p->ncell[0] < 1 || p->ncell[1] < 1 || p->ncell[2] < 1 || p->n_tau < 1 || !(p->cg_rtol > 0) ||
-      p->cg_max_iter < 1 || p->precision_form < 0 || p->precision_form > 2) {
+      p->cg_max_iter < 1 || p->precision_form < 0 || p->precision_form > 2 ||
+      (p->tau_scheme != SEDI_TAU_EULER && p->tau_scheme != SEDI_TAU_BDF2)) {
     put_msg(msg, msg_len, "sedi_smooth_static: invalid mesh or solver parameters");
     return SEDI_EINVAL;
   }
@@ -462,7 +511,7 @@ extern "C" int sedi_smooth_static(const sedi_params* p, int32_t nf, const double
   unsigned char* work = base + W;  // solver scratch
   int* iters_dev = (int*)(base + W + kStaticWork);
   Ctl* ctl = (Ctl*)(base + W + kStaticWork + 256);
-  if (smooth_work_bytes(p->precision_form, C, nf) > (size_t)kStaticWork) {
+  if (smooth_work_bytes(p->precision_form, C, nf, p->tau_scheme) > (size_t)kStaticWork) {
     put_msg(msg, msg_len, "sedi_smooth_static: internal scratch bound exceeded");
     return SEDI_EINVAL;
   }
@@ -490,7 +539,7 @@ extern "C" int sedi_smooth_static(const sedi_params* p, int32_t nf, const double
   const int64_t n = (int64_t)nf * C;
   launch_phi_from_double(form, in, phi, n, s);
   const int rc = launch_smooth(form, P, phi, nullptr, nf, work, st, iters_dev, rtol,
-                               p->cg_max_iter, p->n_tau, coef, s);
+                               p->cg_max_iter, p->n_tau, p->tau_scheme, coef, s);
   if (rc) {
     put_msg(msg, msg_len, "sedi_smooth_static: cooperative launch of the smoother failed");
     return SEDI_ECUDA;

@@ -23,7 +23,8 @@ struct V3 {
   F x, y, z;
 };
 
-// Hertz-Mindlin contact on body "a" (Sec. 2.5 soft spheres; Tsuji-type damping).
+// Contact on body "a" (Sec. 2.5 soft spheres): Hertz-Mindlin with Tsuji-type damping,
+// or the linear spring-dashpot of Sec. 2.5 / Table 1 (K.law == 1).
 // n: unit normal a -> b; delta > 0 overlap; vrel: contact-point velocity of a
 // relative to b; xi_old: spring (valid if has_old).  Returns the force on a and
 // writes the tangential part and the updated spring.
@@ -32,15 +33,26 @@ __device__ __forceinline__ V3<F> hm_core(const ForceConsts<F>& K, V3<F> n, F del
                                          V3<F> vrel, const S* xi_old, bool has_old, V3<F>* Ft_out,
                                          S* xi_new) {
   using NS = Num<S>;
-  F sq = xsqrt(Rs * delta);
-  F Sn = F(2) * K.Es * sq;
-  F St = F(8) * K.Gs * sq;
-  F cn = K.cdamp * xsqrt(Sn * ms);
-  F ct = K.cdamp * xsqrt(St * ms);
+  F Sn, St, cn, ct, fel;  // stiffnesses, damping coefficients, elastic normal force
+  if (K.law == 1) {
+    // linear spring-dashpot (Sec. 2.5, Table 1)
+    Sn = K.kn_lin;
+    St = K.kt_lin;
+    cn = K.cdamp_lin * xsqrt(Sn * ms);
+    ct = K.cdamp_lin * xsqrt(St * ms);
+    fel = K.kn_lin * delta;
+  } else {
+    F sq = xsqrt(Rs * delta);
+    Sn = F(2) * K.Es * sq;
+    St = F(8) * K.Gs * sq;
+    cn = K.cdamp * xsqrt(Sn * ms);
+    ct = K.cdamp * xsqrt(St * ms);
+    F kn = K.kn_fac * xsqrt(Rs);
+    fel = kn * delta * xsqrt(delta);
+  }
   F vn = vrel.x * n.x + vrel.y * n.y + vrel.z * n.z;
   V3<F> vt{vrel.x - vn * n.x, vrel.y - vn * n.y, vrel.z - vn * n.z};
-  F kn = K.kn_fac * xsqrt(Rs);
-  F fn_s = -kn * delta * xsqrt(delta) - cn * vn;  // F_n = fn_s * n
+  F fn_s = -fel - cn * vn;  // F_n = fn_s * n
   // spring: rotate onto the tangent plane, keep the length, add v_t dt
   S xi[3];
   if (has_old) {
@@ -102,7 +114,7 @@ __device__ __forceinline__ V3<F> cross(V3<F> a, V3<F> b) {
 // forces.  When INTEGRATE, the owner's tangential spring of slot k is updated.
 template <class F>
 struct PairOut {
-  V3<F> fa, t, l;
+  V3<F> fa, t, l, lt;  // contact force (on i), contact torque, lubrication force and torque
   bool contact, lub;
 };
 
@@ -119,6 +131,7 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
   const ForceConsts<F>& K = fconsts<F>(P);
   const BoxS<S>& B = sbox<S>(P);
   PairOut<F> o;
+  o.lt = V3<F>{F(0), F(0), F(0)};
   o.contact = o.lub = false;
   const int j = nbr_index(e);
   const Quad<S> Pj = ldq(pos + j);
@@ -151,11 +164,16 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
   const F vj[3] = {NS::f(Vj.a), NS::f(Vj.b), NS::f(Vj.c)};
   const F* vA = i_lo ? vi : vj;
   const F* vB = i_lo ? vj : vi;
-  if (o.contact) {
+  F wj[3] = {F(0), F(0), F(0)};
+  if (o.contact || (o.lub && P.lub_tangential)) {
     const Quad<S> Wj = ldq(omg + j);
-    const F wj[3] = {NS::f(Wj.a), NS::f(Wj.b), NS::f(Wj.c)};
-    const F* wA = i_lo ? wi : wj;
-    const F* wB = i_lo ? wj : wi;
+    wj[0] = NS::f(Wj.a);
+    wj[1] = NS::f(Wj.b);
+    wj[2] = NS::f(Wj.c);
+  }
+  const F* wA = i_lo ? wi : wj;
+  const F* wB = i_lo ? wj : wi;
+  if (o.contact) {
     const F rA = NS::f(A.d), rB = NS::f(Bq.d);
     const F mA = i_lo ? mi : NS::f(Vj.d);
     const F mB = i_lo ? NS::f(Vj.d) : mi;
@@ -189,6 +207,29 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
     F sl = -K.six_pi_mu * Rl * Rl * vn / hh;
     if (!i_lo) sl = -sl;
     o.l = V3<F>{sl * n.x, sl * n.y, sl * n.z};
+    if (P.lub_tangential) {
+      // shear term: -6 pi mu R_l (4/15) (2 + b + 2 b^2)/(1 + b)^2 ln((r_A + r_B) / 2h) v_t,
+      // b = r_B / r_A, v_t the tangential surface velocity of A relative to B at the
+      // gap midpoint (lever arms r + h/2); torque l n x F on both spheres
+      const F la = rA + F(0.5) * h, lb = rB + F(0.5) * h;
+      const V3<F> om{la * wA[0] + lb * wB[0], la * wA[1] + lb * wB[1], la * wA[2] + lb * wB[2]};
+      const V3<F> wxn = cross(om, n);
+      const V3<F> vr{vA[0] - vB[0] + wxn.x, vA[1] - vB[1] + wxn.y, vA[2] - vB[2] + wxn.z};
+      const F vrn = vr.x * n.x + vr.y * n.y + vr.z * n.z;
+      const F b = rB / rA;
+      const F shape = (F(2) + b + F(2) * b * b) / ((F(1) + b) * (F(1) + b));
+      F lg = xlog(sF / (F(2) * hh));
+      if (lg < F(0)) lg = F(0);
+      const F ct = -K.six_pi_mu * Rl * F(4.0 / 15.0) * shape * lg;
+      const V3<F> Ft{ct * (vr.x - vrn * n.x), ct * (vr.y - vrn * n.y), ct * (vr.z - vrn * n.z)};
+      const F lev = i_lo ? la : lb;
+      o.lt = cross(V3<F>{lev * n.x, lev * n.y, lev * n.z}, Ft);
+      if (i_lo) {
+        o.l.x += Ft.x; o.l.y += Ft.y; o.l.z += Ft.z;
+      } else {
+        o.l.x -= Ft.x; o.l.y -= Ft.y; o.l.z -= Ft.z;
+      }
+    }
   }
   return o;
 }
@@ -280,7 +321,7 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
     __shared__ Quad<S> q_pi[W][32];
     __shared__ F q_vw[W][32][8];  // vi, wi, mi, (pad)
     __shared__ uint32_t q_mask[W][32];
-    __shared__ F q_res[W][32][9];
+    __shared__ F q_res[W][32][12];
     __shared__ uint8_t q_flag[W][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int cnt = __popc(live);
@@ -326,6 +367,7 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
         r[0] = o.fa.x; r[1] = o.fa.y; r[2] = o.fa.z;
         r[3] = o.t.x; r[4] = o.t.y; r[5] = o.t.z;
         r[6] = o.l.x; r[7] = o.l.y; r[8] = o.l.z;
+        r[9] = o.lt.x; r[10] = o.lt.y; r[11] = o.lt.z;
         q_flag[wid][lane] = (uint8_t)((o.contact ? 1 : 0) | (o.lub ? 2 : 0));
       }
       __syncwarp();
@@ -342,6 +384,9 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
         }
         if (fg & 2) {
           fl.x += r[6]; fl.y += r[7]; fl.z += r[8];
+          if (P.lub_tangential) {
+            tq.x += r[9]; tq.y += r[10]; tq.z += r[11];
+          }
         }
       }
       __syncwarp();
@@ -359,6 +404,9 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
         }
         if (o.lub) {
           fl.x += o.l.x; fl.y += o.l.y; fl.z += o.l.z;
+          if (P.lub_tangential) {
+            tq.x += o.lt.x; tq.y += o.lt.y; tq.z += o.lt.z;
+          }
         }
       }
   }
@@ -410,6 +458,20 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
             const F vn = vi[0] * n.x + vi[1] * n.y + vi[2] * n.z;
             const F s = -K.six_pi_mu * ri * ri * vn / hh;
             fl.x += s * n.x; fl.y += s * n.y; fl.z += s * n.z;
+            if (P.lub_tangential) {
+              // shear term against the plane: -6 pi mu r (8/15) ln(r / h) v_t
+              const F l = ri + F(0.5) * h;
+              const V3<F> wxn = cross(V3<F>{l * wi[0], l * wi[1], l * wi[2]}, n);
+              const V3<F> vr{vi[0] + wxn.x, vi[1] + wxn.y, vi[2] + wxn.z};
+              const F vrn = vr.x * n.x + vr.y * n.y + vr.z * n.z;
+              F lg = xlog(ri / hh);
+              if (lg < F(0)) lg = F(0);
+              const F ct = -K.six_pi_mu * ri * F(8.0 / 15.0) * lg;
+              const V3<F> Ft{ct * (vr.x - vrn * n.x), ct * (vr.y - vrn * n.y), ct * (vr.z - vrn * n.z)};
+              const V3<F> T = cross(V3<F>{l * n.x, l * n.y, l * n.z}, Ft);
+              fl.x += Ft.x; fl.y += Ft.y; fl.z += Ft.z;
+              tq.x += T.x; tq.y += T.y; tq.z += T.z;
+            }
           }
         }
       }
@@ -417,8 +479,8 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
     // fluid forces at the particle
     F ff[3];
     const F ap[3] = {Ai.a, Ai.b, Ai.c};
-    fluid_force<S, F>(P, K, (const Quad<F>*)mesh.ufe, (const Quad<F>*)mesh.gfl, xi_s, ri, vi, ap,
-                      ff);
+    fluid_force<S, F>(P, K, (const Quad<F>*)mesh.ufe, (const Quad<F>*)mesh.gfl,
+                      (const Quad<F>*)mesh.wfl, xi_s, ri, vi, ap, ff);
     if (!INTEGRATE) {
       double* o = st.fdbg;
       o[3 * i + 0] = (double)fc.x; o[3 * i + 1] = (double)fc.y; o[3 * i + 2] = (double)fc.z;

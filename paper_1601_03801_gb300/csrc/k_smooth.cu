@@ -1,8 +1,11 @@
-// Diffusion smoothing of the averaged fields (Sec. 2.4, Eq. 10): n_tau
-// backward-Euler pseudo-steps (I - dtau div D grad) x = b of the 7-point
-// finite-volume Laplacian (zero flux through non-periodic faces), each solved to
-// ||b - A x|| <= rtol ||b|| for every field of every mesh of a batch, in ONE
-// persistent cooperative launch.
+// Diffusion smoothing of the averaged fields (Sec. 2.4, Eq. 10): n_tau implicit
+// pseudo-steps A x = b of the 7-point finite-volume Laplacian L (zero flux through
+// non-periodic faces), each solved to ||b - A x|| <= rtol ||b|| for every field of
+// every mesh of a batch, in ONE persistent launch.  Backward Euler:
+// A = I - dtau D L, b = x^m.  BDF2 (the paper's second-order implicit scheme, read
+// as the two-step backward difference): A = I - (2/3) dtau D L,
+// b = (4/3) x^m - (1/3) x^{m-1} = x^m + (x^m - x^{m-1}) / 3, its first step backward
+// Euler; x^{m-1} is kept in the wide word.
 //
 // Solver: Chebyshev semi-iteration on the known spectrum of A (lambda_min = 1 from
 // the constant mode, lambda_max <= 1 + 4 sum_a coef_a by Gershgorin), organised as
@@ -261,6 +264,19 @@ __device__ __forceinline__ void unit_sums(const Acc (&v)[kMaxF][kQ], int nf, dou
   __syncthreads();
 }
 
+// Right-hand side of pseudo-step m from x^m (xv): x^m itself (backward Euler, and
+// the first BDF2 step), or x^m + (x^m - x^{m-1}) / 3 with x^{m-1} read from *xp.
+// BDF2 also stores x^m in *xp for the next step.
+template <class T>
+__device__ __forceinline__ T rhs_of(int scheme, int m, T xv, T* xp) {
+  using W = Wide<T>;
+  if (scheme != TAU_BDF2) return xv;
+  T bv = xv;
+  if (m > 0) bv = W::add(xv, W::mul(W::from_d(1.0 / 3.0), W::subq(xv, W::ld(xp))));
+  *xp = xv;
+  return bv;
+}
+
 template <class T>
 __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
   using W = Wide<T>;
@@ -277,14 +293,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
 
   for (int m = 0; m < a.n_tau; ++m) {
     const bool use_guess = (m == 0);
-    // ---- b = x (the previous pseudo-step's result); x = guess on the first
+    const int ph = (a.scheme == TAU_BDF2 && m > 0) ? 1 : 0;  // operator of this step
+    // ---- b from the previous pseudo-step's result; x = guess on the first
     for (int64_t u = u_begin; u < u_end; ++u) {
       const SmoothMeshDev& md = a.mesh[a.unit_bed[u]];
       const int64_t c = (u - md.u0) * kThreads + threadIdx.x;
       if (c >= md.C) continue;
       for (int f = 0; f < nf; ++f) {
         const int64_t k = f * md.C + c;
-        ((T*)md.b)[k] = W::ld((const T*)md.x + k);
+        const T xv = W::ld((const T*)md.x + k);
+        ((T*)md.b)[k] = rhs_of<T>(a.scheme, m, xv, (T*)md.xp + (md.xp ? k : 0));
         if (use_guess && md.guess) ((T*)md.x)[k] = W::ld((const T*)md.guess + k);
       }
     }
@@ -300,7 +318,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
         const bool in = c < md.C;
         Acc v[kMaxF][kQ];
         V8<N> rn;
-        const T cf[3] = {W::from_d(md.coef[0]), W::from_d(md.coef[1]), W::from_d(md.coef[2])};
+        const SmoothSpec& sp = md.sp[ph];
+        const T cf[3] = {W::from_d(sp.coef[0]), W::from_d(sp.coef[1]), W::from_d(sp.coef[2])};
         const Stencil sc = stencil_of(md, in ? c : 0);
 #pragma unroll
         for (int f = 0; f < kMaxF; ++f) {
@@ -366,7 +385,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
                   // |r_k| <= 2 sig^k |r_0|: enough steps for the tolerance, or for the
                   // reduction the narrow word can deliver in one round
                   const double need = fmax(0.5 * sqrt(a.rtol2 * bb / rrp), W::kFloor);
-                  k = md.sig > 0.0 ? (int)ceil(log(need) / log(md.sig)) : 1;
+                  const double sig = md.sp[ph].sig;
+                  k = sig > 0.0 ? (int)ceil(log(need) / log(sig)) : 1;
                   if (k < 1) k = 1;
                   if (k > kMaxStepsRound) k = kMaxStepsRound;
                   if (total + k > a.max_iter) k = a.max_iter - total;
@@ -433,9 +453,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
             }
           }
           if (!any) continue;
-          const N cfn[3] = {(N)md.coef[0], (N)md.coef[1], (N)md.coef[2]};
-          const N c1 = (N)md.cheb[0][j - 1], c2 = (N)md.cheb[1][j - 1];
-          const N inv_theta = (N)(1.0 / md.theta);
+          const SmoothSpec& sp = md.sp[ph];
+          const N cfn[3] = {(N)sp.coef[0], (N)sp.coef[1], (N)sp.coef[2]};
+          const N c1 = (N)sp.cheb[0][j - 1], c2 = (N)sp.cheb[1][j - 1];
+          const N inv_theta = (N)(1.0 / sp.theta);
           const Stencil sc = stencil_of(md, c);
           // step 1 reads the narrow residual (d[0]) and forms d0 = (r - s) / theta at
           // every stencil point; later steps read the previous direction
@@ -566,9 +587,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
 
     T* Xg = (T*)md.x + f * C;
     T* Bg = (T*)md.b + f * C;
-    const T cf[3] = {W::from_d(md.coef[0]), W::from_d(md.coef[1]), W::from_d(md.coef[2])};
-    const N cfn[3] = {(N)md.coef[0], (N)md.coef[1], (N)md.coef[2]};
-    const N inv_theta = (N)(1.0 / md.theta);
+    T* XPg = md.xp ? (T*)md.xp + f * C : nullptr;
     // Work layout: thread t owns the (x, y) columns t, t + kClThreads, ... of the plane
     // and walks each column through this CTA's planes with a rolling window in z, so
     // the in-plane neighbours are fixed offsets per column and only the first and
@@ -618,10 +637,15 @@ __global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
       return c;
     };
     for (int m = 0; m < a.n_tau; ++m) {
-      // ---- b = x (global); x (or the guess) into shared memory
+      const SmoothSpec& sp = md.sp[(a.scheme == TAU_BDF2 && m > 0) ? 1 : 0];
+      const T cf[3] = {W::from_d(sp.coef[0]), W::from_d(sp.coef[1]), W::from_d(sp.coef[2])};
+      const N cfn[3] = {(N)sp.coef[0], (N)sp.coef[1], (N)sp.coef[2]};
+      const N inv_theta = (N)(1.0 / sp.theta);
+      // ---- b (global) from the previous pseudo-step's result; x (or the guess)
+      //      into shared memory
       for (int l = threadIdx.x; l < ncell; l += kClThreads) {
         const T xv = W::ld(Xg + c0 + l);
-        Bg[c0 + l] = xv;
+        Bg[c0 + l] = rhs_of<T>(a.scheme, m, xv, XPg ? XPg + c0 + l : nullptr);
         Xs[l] = (m == 0 && md.guess) ? W::ld((const T*)md.guess + f * C + c0 + l) : xv;
       }
       cl.sync();
@@ -704,7 +728,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
             // the step count only has to be about right (the next round checks the true
             // residual), so it is formed in FP32
             const float need = fmaxf(0.5f * sqrtf((float)(a.rtol2 * bb / rrp)), (float)W::kFloor);
-            k = md.sig > 0.0 ? (int)ceilf(logf(need) / logf((float)md.sig)) : 1;
+            k = sp.sig > 0.0 ? (int)ceilf(logf(need) / logf((float)sp.sig)) : 1;
             if (k < 1) k = 1;
             if (k > kMaxStepsRound) k = kMaxStepsRound;
             if (total + k > a.max_iter) k = a.max_iter - total;
@@ -739,7 +763,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
         for (int j = 1; j <= k; ++j) {
           N* Dold = (j & 1) ? dA : dB;
           N* Dnew = (j & 1) ? dB : dA;
-          const N c1s = (N)md.cheb[0][j - 1], c2s = (N)md.cheb[1][j - 1];
+          const N c1s = (N)sp.cheb[0][j - 1], c2s = (N)sp.cheb[1][j - 1];
           // One step over this CTA's columns.  FIRST (step 1) reads the narrow true
           // residual r and forms d0 = (r - s) / theta at every point it touches; x and
           // the recursion take the shift.  FULL: all four in-plane faces exist (the
@@ -840,20 +864,21 @@ size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
 
 int64_t smooth_units(int64_t C) { return (C + kThreads - 1) / kThreads; }
 
-size_t smooth_mesh_bytes(int form, int64_t C, int nf) {
+size_t smooth_mesh_bytes(int form, int64_t C, int nf, int scheme) {
   const size_t w = form == FORM_PLAIN ? 4 : 8;             // wide word
   const size_t n = form == FORM_FP64 ? 8 : 4;              // narrow word
-  return align256((size_t)nf * C * w) + 3 * align256((size_t)kMaxF * C * n) +
+  const size_t wide = align256((size_t)nf * C * w);        // b, and x^{m-1} for BDF2
+  return (scheme == TAU_BDF2 ? 2 : 1) * wide + 3 * align256((size_t)kMaxF * C * n) +
          align256((size_t)smooth_units(C) * kMaxF * kQ * 8) + 256;
 }
 
-size_t smooth_work_bytes(int form, int64_t C, int nf) {
-  return align256(smooth_mesh_bytes(form, C, nf)) + smooth_batch_bytes(1, smooth_units(C));
+size_t smooth_work_bytes(int form, int64_t C, int nf, int scheme) {
+  return align256(smooth_mesh_bytes(form, C, nf, scheme)) + smooth_batch_bytes(1, smooth_units(C));
 }
 
 int launch_smooth(int form, const DevParams& P, void* phi, const void* guess, int nf, void* work,
                   const DevState& st, int* iters_dev, double rtol, int max_iter, int n_tau,
-                  const double coef[3], cudaStream_t s) {
+                  int scheme, const double coef[3], cudaStream_t s) {
   SmoothMesh m{};
   m.phi = phi;
   m.guess = guess;
@@ -866,8 +891,9 @@ int launch_smooth(int form, const DevParams& P, void* phi, const void* guess, in
     m.per[k] = P.periodic[k];
     m.coef[k] = coef[k];
   }
-  void* batch = (char*)work + align256(smooth_mesh_bytes(form, P.C, nf));
-  return launch_smooth_batch(form, &m, 1, nf, batch, rtol, max_iter, n_tau, st.ctl, 1 << 30, s);
+  void* batch = (char*)work + align256(smooth_mesh_bytes(form, P.C, nf, scheme));
+  return launch_smooth_batch(form, &m, 1, nf, batch, rtol, max_iter, n_tau, scheme, st.ctl,
+                             1 << 30, s);
 }
 
 size_t smooth_batch_bytes(int64_t B, int64_t U) {
@@ -875,7 +901,29 @@ size_t smooth_batch_bytes(int64_t B, int64_t U) {
          align256((size_t)B * sizeof(MeshState)) + 256;
 }
 
-void smooth_mesh_layout(int form, const SmoothMesh& in, SmoothMeshDev* out) {
+// Spectrum [1, lmax] of A = I - sum_a coef_a L_a (lmax <= 1 + 4 sum_a coef_a by
+// Gershgorin) and the Chebyshev coefficients of steps 1..kMaxStepsRound (the same
+// in every round): rho_1 = 1 / sigma1, rho' = 1 / (2 sigma1 - rho), c1 = rho' rho,
+// c2 = 2 rho' / delta.
+static void smooth_spec(const double coef[3], double scale, SmoothSpec* sp) {
+  for (int k = 0; k < 3; ++k) sp->coef[k] = scale * coef[k];
+  double lmax = 1.0 + 4.0 * (sp->coef[0] + sp->coef[1] + sp->coef[2]);
+  if (lmax < 1.0 + 1e-12) lmax = 1.0 + 1e-12;
+  sp->theta = 0.5 * (lmax + 1.0);
+  sp->delta = 0.5 * (lmax - 1.0);
+  sp->sigma1 = sp->theta / sp->delta;
+  const double sq = std::sqrt(lmax);
+  sp->sig = (sq - 1.0) / (sq + 1.0);
+  double rho = 1.0 / sp->sigma1;
+  for (int j = 0; j < kMaxStepsRound; ++j) {
+    const double rho_new = 1.0 / (2.0 * sp->sigma1 - rho);
+    sp->cheb[0][j] = rho_new * rho;
+    sp->cheb[1][j] = 2.0 * rho_new / sp->delta;
+    rho = rho_new;
+  }
+}
+
+static void smooth_mesh_layout(int form, int scheme, const SmoothMesh& in, SmoothMeshDev* out) {
   const size_t w = form == FORM_PLAIN ? 4 : 8;
   const size_t n = form == FORM_FP64 ? 8 : 4;
   char* p = (char*)in.work;
@@ -885,6 +933,10 @@ void smooth_mesh_layout(int form, const SmoothMesh& in, SmoothMeshDev* out) {
   m.guess = in.guess;
   m.b = p;  // [nf][C] wide
   p += align256((size_t)in.nf * in.C * w);
+  if (scheme == TAU_BDF2) {
+    m.xp = p;  // [nf][C] wide
+    p += align256((size_t)in.nf * in.C * w);
+  }
   const size_t nar = align256((size_t)kMaxF * in.C * n);  // [C][8] narrow
   m.q = p;
   m.d[0] = p + nar;
@@ -897,24 +949,9 @@ void smooth_mesh_layout(int form, const SmoothMesh& in, SmoothMeshDev* out) {
   for (int k = 0; k < 3; ++k) {
     m.nc[k] = in.nc[k];
     m.per[k] = in.per[k];
-    m.coef[k] = in.coef[k];
   }
-  double lmax = 1.0 + 4.0 * (in.coef[0] + in.coef[1] + in.coef[2]);
-  if (lmax < 1.0 + 1e-12) lmax = 1.0 + 1e-12;
-  m.theta = 0.5 * (lmax + 1.0);
-  m.delta = 0.5 * (lmax - 1.0);
-  m.sigma1 = m.theta / m.delta;
-  const double sq = std::sqrt(lmax);
-  m.sig = (sq - 1.0) / (sq + 1.0);
-  // Chebyshev coefficients of steps 1..kMaxStepsRound (the same in every round):
-  // rho_1 = 1 / sigma1, rho' = 1 / (2 sigma1 - rho), c1 = rho' rho, c2 = 2 rho' / delta
-  double rho = 1.0 / m.sigma1;
-  for (int j = 0; j < kMaxStepsRound; ++j) {
-    const double rho_new = 1.0 / (2.0 * m.sigma1 - rho);
-    m.cheb[0][j] = rho_new * rho;
-    m.cheb[1][j] = 2.0 * rho_new / m.delta;
-    rho = rho_new;
-  }
+  smooth_spec(in.coef, 1.0, &m.sp[0]);
+  smooth_spec(in.coef, scheme == TAU_BDF2 ? 2.0 / 3.0 : 1.0, &m.sp[1]);
 }
 
 namespace {
@@ -972,16 +1009,17 @@ void cluster_plan(int form, const SmoothMeshDev& m, int* csize, int* planes) {
 }  // namespace
 
 int launch_smooth_batch(int form, const SmoothMesh* meshes, int B, int nf, void* batch_work,
-                        double rtol, int max_iter, int n_tau, Ctl* ctl, int max_blocks,
-                        cudaStream_t s) {
-  if (B < 1 || B > kMaxBeds || nf < 1 || nf > kMaxF) return -1;
+                        double rtol, int max_iter, int n_tau, int scheme, Ctl* ctl,
+                        int max_blocks, cudaStream_t s) {
+  if (B < 1 || B > kMaxBeds || nf < 1 || nf > kMaxF || (scheme != TAU_EULER && scheme != TAU_BDF2))
+    return -1;
   // meshes that fit the cluster solver take it; the rest take the grid solver.  The
   // choice depends on the mesh alone, so a bed smooths the same way in any batch.
   std::vector<SmoothMeshDev> mg, mc;
   int64_t U = 0;
   for (int b = 0; b < B; ++b) {
     SmoothMeshDev m;
-    smooth_mesh_layout(form, meshes[b], &m);
+    smooth_mesh_layout(form, scheme, meshes[b], &m);
     int cs, pl;
     cluster_plan(form, m, &cs, &pl);
     if (cs > 0) {
@@ -1003,6 +1041,7 @@ int launch_smooth_batch(int form, const SmoothMesh* meshes, int B, int nf, void*
   a.rtol2 = rtol * rtol;
   a.max_iter = max_iter;
   a.n_tau = n_tau;
+  a.scheme = scheme;
   a.ctl = ctl;
   SmoothMeshDev* tab_g = (SmoothMeshDev*)p;
   p += align256((size_t)B * sizeof(SmoothMeshDev));

@@ -77,15 +77,21 @@ void launch_deposit(int form, const DevState& st, const DevMesh& mesh, const Dev
                     void* qfields, cudaStream_t s);
 void launch_fields_from_fixed(int form, const void* q, const DevParams& P, void* phi,
                               int nf, cudaStream_t s);
+// cell vorticity (curl U, 0) of the FP64 velocity U [C][3] into the mesh's wfl
+void launch_curl(int form, const double* U, const DevParams& P, void* wfl, cudaStream_t s);
 // k_smooth.cu: the smoothing solve of a batch of meshes in one persistent launch.
 constexpr int kMaxBeds = 1024;       // meshes in one smoothing launch
 constexpr int kMaxStepsRound = 64;  // Chebyshev steps of one round at most (more: next round)
+
+// Pseudo-time schemes of the smoothing (Sec. 2.4): backward Euler, or BDF2 whose
+// first step is backward Euler.
+enum { TAU_EULER = 0, TAU_BDF2 = 1 };
 
 // One mesh of a smoothing batch, as the caller describes it.
 struct SmoothMesh {
   void* phi;          // [nf][C] fields in the smoothing word of the form, in place
   const void* guess;  // [nf][C] initial guess of the first pseudo-step, or null
-  void* work;         // smooth_mesh_bytes(form, C, nf) bytes of device scratch
+  void* work;         // smooth_mesh_bytes(form, C, nf, scheme) bytes of device scratch
   int* iters;         // [nf] device counters, incremented by the steps taken (or null)
   int64_t C;
   int32_t nc[3], per[3];
@@ -93,21 +99,28 @@ struct SmoothMesh {
   double coef[3];     // dtau * D_a / h_a^2
 };
 
+// The operator of one kind of pseudo-step, A = I - sum_a coef_a L_a, and the
+// Chebyshev constants of its spectrum.
+struct SmoothSpec {
+  double coef[3];
+  double theta, delta, sigma1, sig;  // spectrum [1, lmax]: centre, half width, ratio, rate
+  double cheb[2][kMaxStepsRound];    // c1, c2 of Chebyshev steps 1..kMaxStepsRound of a round
+};
+
 // The same, as the kernel sees it (device table, built by launch_smooth_batch).
 struct SmoothMeshDev {
   void* x;
   const void* guess;
   void* b;           // [nf][C] right-hand side (wide word)
+  void* xp;          // [nf][C] previous pseudo-step (wide word; BDF2 only, else null)
   void* q;           // [C][8] recursive residual (narrow word, fields interleaved)
   void* d[2];        // [C][8] directions; d[0] also holds the narrow true residual
   double* part;       // [units][8][3] per-unit sums
   int* iters;
   int64_t C, u0, nu;  // cells, first unit, units
   int32_t nc[3], per[3];
-  double coef[3];
-  double theta, delta, sigma1, sig;  // spectrum [1, lmax]: centre, half width, ratio, rate
   int32_t cl_size, cl_planes;        // cluster solver: CTAs, z-planes per CTA (0: grid solver)
-  double cheb[2][kMaxStepsRound];    // c1, c2 of Chebyshev steps 1..kMaxStepsRound of a round
+  SmoothSpec sp[2];  // [0]: backward-Euler steps (coef); [1]: BDF2 steps (2/3 coef)
 };
 
 struct SmoothBatchDev {
@@ -118,24 +131,25 @@ struct SmoothBatchDev {
   int64_t U;
   int32_t B, nf;
   double rtol2;
-  int32_t max_iter, n_tau;
+  int32_t max_iter, n_tau, scheme;
   Ctl* ctl;                   // grid barrier and cg_status
 };
 
 int64_t smooth_units(int64_t C);
 // scratch of one mesh, and of the batch tables
-size_t smooth_mesh_bytes(int form, int64_t C, int nf);
+size_t smooth_mesh_bytes(int form, int64_t C, int nf, int scheme);
 size_t smooth_batch_bytes(int64_t B, int64_t U);
-// Smooth every mesh's nf fields in place; batch_work: smooth_batch_bytes(B, sum of
-// units) bytes.  Returns 0, -1 (bad sizes) or -3 (launch failed).
+// Smooth every mesh's nf fields in place by n_tau pseudo-steps of the scheme;
+// batch_work: smooth_batch_bytes(B, sum of units) bytes.  Returns 0, -1 (bad sizes)
+// or -3 (launch failed).
 int launch_smooth_batch(int form, const SmoothMesh* meshes, int B, int nf, void* batch_work,
-                        double rtol, int max_iter, int n_tau, Ctl* ctl, int max_blocks,
-                        cudaStream_t s);
-// Single mesh: work holds smooth_work_bytes(form, C, nf) = mesh + batch scratch.
-size_t smooth_work_bytes(int form, int64_t C, int nf);
+                        double rtol, int max_iter, int n_tau, int scheme, Ctl* ctl,
+                        int max_blocks, cudaStream_t s);
+// Single mesh: work holds smooth_work_bytes(form, C, nf, scheme) = mesh + batch scratch.
+size_t smooth_work_bytes(int form, int64_t C, int nf, int scheme);
 int launch_smooth(int form, const DevParams& P, void* phi, const void* guess, int nf,
                   void* work, const DevState& st, int* iters_dev, double rtol, int max_iter,
-                  int n_tau, const double coef[3], cudaStream_t s);
+                  int n_tau, int scheme, const double coef[3], cudaStream_t s);
 void launch_average_out(int form, const void* phi, const DevParams& P, void* ufe, double* eps,
                         double* Us, double* F, cudaStream_t s);
 void launch_phi_convert(int form, const void* phi, double* out, int64_t n, int to_double,

@@ -42,14 +42,16 @@ class SediParams(C.Structure):
     _fields_ = [
         ("contact_law", _I),
         ("E", _D), ("poisson", _D), ("restitution", _D), ("friction", _D),
+        ("kn_linear", _D), ("kt_ratio", _D),
         ("rho_f", _D), ("nu_f", _D), ("g", _D * 3),
         ("lo", _D * 3), ("hi", _D * 3),
         ("periodic", _I * 3), ("wall_lo", _I * 3), ("wall_hi", _I * 3),
         ("dt", _D), ("skin", _D),
         ("lubrication", _I), ("drag", _I), ("pressure_grad", _I), ("added_mass", _I),
-        ("lub_h_in_frac", _D), ("lub_h_out_frac", _D), ("c_add", _D), ("eps_max", _D),
+        ("lift", _I), ("lub_tangential", _I),
+        ("lub_h_in_frac", _D), ("lub_h_out_frac", _D), ("c_add", _D), ("c_lift", _D), ("eps_max", _D),
         ("ncell", _I * 3),
-        ("bandwidth", _D * 3), ("n_tau", _I), ("cg_rtol", _D), ("cg_max_iter", _I),
+        ("bandwidth", _D * 3), ("n_tau", _I), ("tau_scheme", _I), ("cg_rtol", _D), ("cg_max_iter", _I),
         ("shift_eps", _I), ("shift_mom", _I), ("shift_force", _I),
         ("precision_form", _I), ("nbr_capacity", _I), ("use_graphs", _I), ("substep_variant", _I),
         ("n_beds", _I), ("profile", _I), ("use_cnn_guess", _I), ("cnn_scale", _D * 4),

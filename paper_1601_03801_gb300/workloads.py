@@ -34,15 +34,17 @@ G = 9.81
 def default_params(**over) -> dict:
     """Physical inputs shared by the CUDA library binding and the oracle."""
     p = dict(
-        E=1.0e7, poisson=0.3, restitution=0.9, friction=0.3,
+        contact_law=0, E=1.0e7, poisson=0.3, restitution=0.9, friction=0.3,
+        kn_linear=800.0, kt_ratio=2.0 / 7.0,
         rho_f=1000.0, nu_f=1.0e-6, g=(0.0, 0.0, -G),
         lo=(0.0, 0.0, 0.0), hi=(20e-3, 20e-3, 40e-3),
         periodic=(1, 1, 0), wall_lo=(0, 0, 1), wall_hi=(0, 0, 1),
         dt=1.0e-6,
         lubrication=1, drag=1, pressure_grad=1, added_mass=1,
         lub_h_in_frac=1.0e-3, lub_h_out_frac=0.1, c_add=0.5, eps_max=0.9,
+        lift=0, c_lift=1.6, lub_tangential=0,
         ncell=(10, 10, 20),
-        bandwidth=(3e-3, 3e-3, 3e-3), n_tau=4, cg_rtol=1e-8, cg_max_iter=500,
+        bandwidth=(3e-3, 3e-3, 3e-3), n_tau=4, tau_scheme=0, cg_rtol=1e-8, cg_max_iter=500,
         shift_eps=40, shift_mom=40, shift_force=32,
         skin=0.05e-3,
     )

@@ -58,8 +58,10 @@ def run(g, beds_idx, single):
     return out
 
 
-def test_ensemble_bit_identical_to_single_beds(ens):
+@pytest.mark.parametrize("extra", [{}, {"lift": 1, "lub_tangential": 1}])
+def test_ensemble_bit_identical_to_single_beds(ens, extra):
     prm, beds = ens
+    prm = dict(prm, **extra)
     E = make_ensemble(prm, beds)
     got = run(E, range(len(beds)), single=False)
     st = E.stats()
@@ -72,6 +74,18 @@ def test_ensemble_bit_identical_to_single_beds(ens):
             assert np.array_equal(p, q), (b, k)
         contacts += len(E.contacts(bed=b)[0])
     assert contacts > 0
+
+
+def test_ensemble_bdf2_bit_identical_to_single_beds(ens):
+    # the BDF2 pseudo-time scheme through the batched smoothing launch
+    prm, beds = ens
+    prm = dict(prm, tau_scheme=1)
+    E = make_ensemble(prm, beds[:3])
+    got = run(E, range(3), single=False)
+    for b, bd in enumerate(beds[:3]):
+        want = run(make_single(prm, bd), [0], single=True)[0]
+        for k, (p, q) in enumerate(zip(got[b], want)):
+            assert np.array_equal(p, q), (b, k)
 
 
 def test_ensemble_graphs_equal_plain_launches(ens):

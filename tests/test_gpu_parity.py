@@ -78,6 +78,83 @@ def test_forces_identical_state(small, form):
         assert err <= FORCE_TOL[form], f"{form} {k}: {err:.3e}"
 
 
+# the paper's own contact law (Sec. 2.5, Table 1): linear spring-dashpot, k_n = 800 N/m,
+# e = 0.97, mu = 0.1
+LINEAR = dict(contact_law=1, kn_linear=800.0, kt_ratio=2.0 / 7.0, restitution=0.97, friction=0.1)
+
+
+@pytest.mark.parametrize("form", ["fp64", "split"])
+def test_linear_law_forces_and_trajectory(small, form):
+    prm, parts = small
+    prm = dict(prm, **LINEAR)
+    g, o = make_pair(prm, parts, form)
+    fg, fo = g.compute_forces(), o.forces()
+    for k in ("contact", "torque"):
+        assert np.abs(fo[k]).max() > 0, k
+        err = rel_err(fg[k], fo[k])
+        assert err <= FORCE_TOL[form], f"{form} {k}: {err:.3e}"
+    g.step(100)
+    o.step(100)
+    xg, _, _, _ = g.get_particles()
+    xo, _, _, _ = o.get_particles()
+    err = np.abs(min_image(xg - xo, prm)).max(axis=1) / parts["d"]
+    assert err.max() <= (1e-10 if form == "fp64" else 1e-4), f"{form}: {err.max():.3e}"
+    # the softer spring leaves fewer pairs touching than the Hertz law; the run still
+    # carries tangential springs through the 100 steps
+    ij, xi = o.contacts()
+    assert len(ij) >= 4 and np.abs(xi).max() > 0
+
+
+def shear_flow(prm, seed, G=5.0, noise=0.02):
+    """Shear U_x = G z plus a random perturbation: vorticity of every orientation."""
+    n = prm["ncell"]
+    hz = (prm["hi"][2] - prm["lo"][2]) / n[2]
+    zc = prm["lo"][2] + (np.arange(n[2]) + 0.5) * hz
+    rng = np.random.default_rng(seed)
+    C = int(np.prod(n))
+    U = rng.normal(0, noise, (C, 3))
+    U[:, 0] += G * np.repeat(zc, n[0] * n[1])
+    return U, rng.uniform(0.0, 0.4, C)
+
+
+@pytest.mark.parametrize("form", ["fp64", "split"])
+def test_lift_and_tangential_lubrication(small, form):
+    # Saffman lift (Sec. 2.3, Eq. 7) and the shear lubrication terms with their
+    # torques (Sec. 2.5), against the oracle at the same state, then 100 steps
+    prm, parts = small
+    prm = dict(prm, lift=1, lub_tangential=1)
+    g, o = make_pair(prm, parts, form)
+    U, eps = shear_flow(prm, 12)
+    for h in (g, o):
+        h.set_fluid(U=U)
+        h.set_eps(eps)
+    fg, fo = g.compute_forces(), o.forces()
+    for k in ("contact", "lub", "fluid", "torque"):
+        err = rel_err(fg[k], fo[k])
+        assert err <= FORCE_TOL[form], f"{form} {k}: {err:.3e}"
+    # the lift is part of f_fp, so the fluid receives it through the deposition
+    _, _, Fg = g.average()
+    _, _, Fo = o.average()
+    assert rel_err(Fg, Fo) <= 1e-4
+    # the terms are there: the same state without them differs well beyond tolerance
+    x, v, w, _ = g.get_particles()
+    o0 = orc.Oracle(dict(prm, lift=0, lub_tangential=0))
+    o0.set_particles(x, v, w, parts["d"], parts["rho"])
+    o0.set_fluid(U=U)
+    o0.set_eps(eps)
+    f0 = o0.forces()
+    assert rel_err(f0["fluid"], fo["fluid"]) > 1e-3
+    assert rel_err(f0["lub"], fo["lub"]) > 1e-3
+    assert rel_err(f0["torque"], fo["torque"]) > 1e-6
+    g.step(100)
+    o.step(100)
+    xg, _, wg, _ = g.get_particles()
+    xo, _, wo, _ = o.get_particles()
+    err = np.abs(min_image(xg - xo, prm)).max(axis=1) / parts["d"]
+    assert err.max() <= (1e-10 if form == "fp64" else 1e-4), f"{form}: {err.max():.3e}"
+    assert rel_err(wg, wo) <= (1e-8 if form == "fp64" else 1e-3)
+
+
 @pytest.mark.parametrize("form,steps,tol", [("fp64", 200, 1e-10), ("split", 200, 1e-4)])
 def test_trajectory_200_steps(small, form, steps, tol):
     prm, parts = small
@@ -224,6 +301,73 @@ def test_smoothing_matches_oracle(small, form):
     for f in range(7):
         assert np.abs(sg[f] - so[f]).max() <= 1e-7 * np.abs(phi[f]).max()
         assert abs(sg[f].sum() - phi[f].sum()) <= 1e-9 * phi[f].sum()
+
+
+@pytest.mark.parametrize("form", ["fp64", "split"])
+def test_bdf2_smoothing_matches_oracle(small, form):
+    # BDF2 pseudo-time (second-order implicit scheme of Sec. 2.4): operator
+    # I - (2/3) dtau D L after a backward-Euler first step, right-hand side
+    # (4/3) phi^m - (1/3) phi^{m-1}
+    prm, _ = small
+    prm = dict(prm, tau_scheme=1)
+    g = sedi.Sedi(dict(prm, precision_form=form))
+    o = orc.Oracle(prm)
+    rng = np.random.default_rng(6)
+    C = int(np.prod(prm["ncell"]))
+    phi = rng.random((7, C))
+    phi[rng.random((7, C)) < 0.6] = 0.0
+    sg, itg = g.smooth(phi)
+    so, _ = o.smooth(phi)
+    se, _ = orc.Oracle(dict(prm, tau_scheme=0)).smooth(phi)
+    assert np.all(itg > 0)
+    for f in range(7):
+        scale = np.abs(phi[f]).max()
+        assert np.abs(sg[f] - so[f]).max() <= 1e-7 * scale
+        assert abs(sg[f].sum() - phi[f].sum()) <= 1e-9 * phi[f].sum()
+        # a different scheme: the result moves well beyond the tolerance
+        assert np.abs(so[f] - se[f]).max() > 1e-4 * scale
+
+
+def test_bdf2_grid_solver_mesh():
+    # 96 x 96 planes hold more cells than one CTA of the cluster solver, so this mesh
+    # takes the grid solver in the split form
+    prm = default_params(hi=(96e-3, 96e-3, 24e-3), ncell=(96, 96, 24), wall_hi=(0, 0, 0),
+                         bandwidth=(2e-3, 2e-3, 1.5e-3), tau_scheme=1)
+    g = sedi.Sedi(dict(prm, precision_form="split"))
+    o = orc.Oracle(prm)
+    rng = np.random.default_rng(9)
+    C = int(np.prod(prm["ncell"]))
+    phi = rng.random((2, C)) * (rng.random((2, C)) < 0.3)
+    sg, _ = g.smooth(phi)
+    so, _ = o.smooth(phi)
+    assert np.abs(sg - so).max() <= 1e-7 * np.abs(phi).max()
+
+
+def test_anisotropic_bandwidth_matches_oracle():
+    # Case-3 bandwidths of Sec. 3: 4 d horizontally, 2 d vertically (d = 0.5 mm), on
+    # the benchmark's 64 x 32 x 64 mesh of 1 mm cells
+    d = 0.5e-3
+    prm = default_params(hi=(64e-3, 32e-3, 64e-3), ncell=(64, 32, 64), wall_hi=(0, 0, 0),
+                         bandwidth=(4 * d, 4 * d, 2 * d))
+    g = sedi.Sedi(dict(prm, precision_form="split"))
+    o = orc.Oracle(prm)
+    rng = np.random.default_rng(10)
+    C = int(np.prod(prm["ncell"]))
+    phi = rng.random((3, C)) * (rng.random((3, C)) < 0.3)
+    sg, _ = g.smooth(phi)
+    so, _ = o.smooth(phi)
+    si, _ = orc.Oracle(dict(prm, bandwidth=(4 * d,) * 3)).smooth(phi)
+    scale = np.abs(phi).max()
+    assert np.abs(sg - so).max() <= 1e-7 * scale
+    assert np.abs(so - si).max() > 1e-3 * scale
+
+
+def test_bdf2_rejects_learned_guess(small):
+    prm, _ = small
+    with pytest.raises(sedi.SediError):
+        sedi.Sedi(dict(prm, tau_scheme=1, use_cnn_guess=1))
+    with pytest.raises(sedi.SediError):
+        sedi.Sedi(dict(prm, tau_scheme=2))
 
 
 def test_smoothing_guess_and_large_mesh():

@@ -10,9 +10,12 @@ from paper_1601_03801_gb300.workloads import default_params, random_fields, smal
 RHO = 2500.0
 
 
-def exact_smooth(prm, phi):
-    """Exact discrete answer of n_tau backward-Euler steps of the 7-point
-    Laplacian: periodic axes diagonalised by the DFT, zero-flux axes by the DCT-II."""
+def exact_smooth(prm, phi, mode="scheme"):
+    """Exact discrete answer of n_tau implicit steps of the 7-point Laplacian:
+    periodic axes diagonalised by the DFT, zero-flux axes by the DCT-II.  Per mode:
+    backward Euler y' = y / (1 + lam); BDF2 (tau_scheme 1, first step backward Euler)
+    y'' = ((4/3) y' - (1/3) y) / (1 + (2/3) lam).  mode="exact": the continuous
+    pseudo-time solution exp(-n_tau lam) of the discrete Laplacian."""
     nx, ny, nz = prm["ncell"]
     f = phi.reshape(nz, ny, nx).astype(float)
     axes = {0: 2, 1: 1, 2: 0}  # physical axis -> array axis
@@ -36,7 +39,15 @@ def exact_smooth(prm, phi):
             g = sfft.fft(g, axis=ax)
         else:
             g = sfft.dct(g.real, type=2, norm="ortho", axis=ax) + 1j * sfft.dct(g.imag, type=2, norm="ortho", axis=ax)
-    g = g / (1 + lam) ** prm["n_tau"]
+    if mode == "exact":
+        g = g * np.exp(-prm["n_tau"] * lam)
+    elif prm.get("tau_scheme", 0) == 1:
+        prev, cur = g, g / (1 + lam)
+        for _ in range(prm["n_tau"] - 1):
+            prev, cur = cur, (4.0 / 3.0 * cur - 1.0 / 3.0 * prev) / (1 + 2.0 / 3.0 * lam)
+        g = cur
+    else:
+        g = g / (1 + lam) ** prm["n_tau"]
     for a in range(3):
         ax = axes[a]
         if prm["periodic"][a]:
@@ -61,6 +72,42 @@ def test_p7_smoothing_equals_spectral_solution(oracle_mod, periodic, walls, n_ta
         ref = exact_smooth(prm, phi[f])
         assert np.abs(out[f] - ref).max() <= 1e-11 * np.abs(phi[f]).max()
         assert iters[f] > 0
+
+
+@pytest.mark.parametrize("periodic,walls", [((1, 1, 1), (0, 0, 0)), ((1, 0, 0), (0, 1, 1))])
+def test_bdf2_smoothing_equals_spectral_recurrence(oracle_mod, periodic, walls):
+    """Second-order implicit pseudo-time (Sec. 2.4, read as BDF2): the oracle equals
+    the per-mode BDF2 recurrence and keeps sum(phi)."""
+    prm = default_params(periodic=periodic, wall_lo=walls, wall_hi=walls, ncell=(12, 10, 8),
+                         hi=(12e-3, 10e-3, 16e-3), bandwidth=(3e-3, 2e-3, 4e-3), n_tau=5,
+                         tau_scheme=1, cg_rtol=1e-14, cg_max_iter=2000)
+    o = oracle_mod.Oracle(prm)
+    phi = random_fields(prm["ncell"], 2, seed=12)
+    out, _ = o.smooth(phi)
+    for f in range(2):
+        ref = exact_smooth(prm, phi[f])
+        assert np.abs(out[f] - ref).max() <= 1e-11 * np.abs(phi[f]).max()
+        assert abs(out[f].sum() - phi[f].sum()) <= 1e-12 * np.abs(phi[f]).sum()
+
+
+def test_bdf2_second_order_backward_euler_first_order(oracle_mod):
+    """Against the continuous pseudo-time solution exp(-L) of the same discrete
+    Laplacian, halving dtau cuts the BDF2 error about fourfold and the backward-Euler
+    error about twofold."""
+    ratios = {}
+    for scheme in (0, 1):
+        errs = []
+        for n_tau in (32, 64):
+            prm = default_params(periodic=(1, 1, 1), wall_lo=(0, 0, 0), wall_hi=(0, 0, 0),
+                                 ncell=(12, 10, 8), hi=(12e-3, 10e-3, 16e-3),
+                                 bandwidth=(3e-3, 2e-3, 4e-3), n_tau=n_tau, tau_scheme=scheme,
+                                 cg_rtol=1e-14, cg_max_iter=2000)
+            phi = random_fields(prm["ncell"], 1, seed=13)
+            out, _ = oracle_mod.Oracle(prm).smooth(phi)
+            errs.append(np.abs(out[0] - exact_smooth(prm, phi[0], mode="exact")).max())
+        ratios[scheme] = errs[0] / errs[1]
+    assert 1.8 < ratios[0] < 2.2, ratios   # measured 2.05
+    assert 3.6 < ratios[1] < 4.6, ratios   # measured 4.25 (4.6, 5.9 at coarser steps)
 
 
 def test_p7_lone_particle_tends_to_gaussian(oracle_mod):

@@ -131,12 +131,15 @@ def test_p2_restitution_matches_ode(oracle_mod):
         assert abs(e_dem - e_ode[0]) < 2e-3
 
 
-def test_p4_momentum_and_angular_momentum(oracle_mod):
-    """P4: pair forces cancel (sum F = 0) and, with lever arms r - delta/2, the
-    pair torques close the angular-momentum balance sum(x x F + T) = 0."""
+@pytest.mark.parametrize("lub_t", [0, 1])
+def test_p4_momentum_and_angular_momentum(oracle_mod, lub_t):
+    """P4: pair forces cancel (sum F = 0) and, with lever arms r - delta/2 (r + h/2
+    across a lubrication gap), the pair torques close the angular-momentum balance
+    sum(x x F + T) = 0, with and without the tangential lubrication terms."""
     rng = np.random.default_rng(4)
     n = 60
-    p = dry(lubrication=1, periodic=(0, 0, 0), hi=(0.05, 0.05, 0.05), ncell=(4, 4, 4))
+    p = dry(lubrication=1, periodic=(0, 0, 0), hi=(0.05, 0.05, 0.05), ncell=(4, 4, 4),
+            lub_tangential=lub_t)
     x = 0.025 + rng.uniform(-1.6e-3, 1.6e-3, (n, 3))
     d = rng.uniform(0.8e-3, 1.2e-3, n)
     v = rng.normal(0, 0.2, (n, 3))
@@ -218,3 +221,52 @@ def test_timestep_rule_config_small():
     tc, _ = hertz_tc(p, 0.134)
     assert 1.2e-4 < tc < 1.8e-4
     assert p["dt"] <= tc / 50
+
+
+def linear_closed_form(p, d=D):
+    """Damped linear oscillator of the relative normal motion (equal spheres):
+    omega_0 = sqrt(k_n / m*), zeta = -ln e / sqrt(pi^2 + ln^2 e); contact ends at zero
+    overlap after half a damped period, with exactly the speed ratio e."""
+    ms = mass(d) / 2
+    w0 = math.sqrt(p["kn_linear"] / ms)
+    le = math.log(p["restitution"])
+    zeta = -le / math.sqrt(math.pi ** 2 + le * le)
+    return math.pi / (w0 * math.sqrt(1 - zeta * zeta)), w0
+
+
+@pytest.mark.parametrize("e,vrel", [(0.97, 0.1), (0.97, 1.0), (0.5, 0.1)])
+def test_linear_spring_dashpot_restitution_and_duration(oracle_mod, e, vrel):
+    """Linear spring-dashpot of Sec. 2.5 / Table 1 (k_n = 800 N/m): the head-on
+    collision lasts pi / omega_d whatever the impact speed, rebounds with exactly
+    the restitution coefficient e, and reaches the undamped peak overlap
+    v0 / omega_0 when e = 1; the DEM converges to these at first order or better."""
+    p0 = dry(contact_law=1, restitution=e)
+    tc, w0 = linear_closed_form(p0)
+    errs = []
+    for nper in (400, 800):
+        dt = tc / nper
+        p = dry(contact_law=1, restitution=e, dt=dt)
+        delta, vh = head_on(oracle_mod, p, vrel, int(1.3 * nper))
+        t0, t1, k1 = crossing_times(delta, dt)
+        e_dem = -vh[k1 + 2] / vh[0]
+        errs.append((abs((t1 - t0) - tc) / tc, abs(e_dem - e)))
+    # errors fall with dt and are small at the finer step
+    assert errs[1][0] < 2e-3 and errs[1][1] < 2e-3, errs
+    assert errs[1][0] <= errs[0][0] + 1e-12 and errs[1][1] <= errs[0][1] + 1e-12, errs
+    # elastic case: peak overlap of the undamped oscillator
+    pe = dry(contact_law=1, restitution=1.0, dt=tc / 800)
+    delta, _ = head_on(oracle_mod, pe, vrel, 1100)
+    assert abs(delta.max() - vrel / w0) / (vrel / w0) < 2e-3
+
+
+def test_linear_law_differs_from_hertz_at_same_state(oracle_mod):
+    """The law switch changes the force (guards against the flag being ignored)."""
+    x = np.array([[0.01 - 0.4999e-3, 0.01, 0.01], [0.01 + 0.4999e-3, 0.01, 0.01]])
+    f = []
+    for law in (0, 1):
+        o = oracle_mod.Oracle(dry(contact_law=law))
+        o.set_particles(x, np.zeros((2, 3)), np.zeros((2, 3)), np.full(2, D), np.full(2, RHO))
+        f.append(o.forces()["contact"][0, 0])
+    delta = D - 2 * 0.4999e-3
+    assert abs(f[1] + 800.0 * delta) < 1e-12 * 800.0 * D  # F = -k_n delta on the left sphere
+    assert abs(f[0] - f[1]) > 1e-3 * abs(f[1])

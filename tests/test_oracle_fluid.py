@@ -158,3 +158,141 @@ def test_trilinear_interpolation_of_linear_field(oracle_mod):
     fr = s - math.floor(s)
     expect = (1 - fr) * (7.0 + 3e4 * xc[-1]) + fr * (7.0 + 3e4 * xc[0])
     assert abs(-f[2, 0] / Vp - expect) < 1e-9
+
+
+def cell_centres(p):
+    n = p["ncell"]
+    c = [p["lo"][a] + (np.arange(n[a]) + 0.5) * (p["hi"][a] - p["lo"][a]) / n[a] for a in range(3)]
+    Z, Y, X = np.meshgrid(c[2], c[1], c[0], indexing="ij")
+    return X.ravel(), Y.ravel(), Z.ravel()
+
+
+def test_p15_vorticity_closed_forms(oracle_mod):
+    """P15: the cell vorticity is exact for linear fields (central and one-sided
+    differences alike): simple shear U = (G z, 0, 0) gives omega = (0, G, 0) in every
+    cell, rigid rotation U = W x (x - x0) gives 2 W; a periodic sine U_x = sin(k z)
+    gives the central-difference closed form k cos(k z) sin(k h) / (k h)."""
+    p = default_params(periodic=(0, 0, 0), wall_lo=(1, 1, 1), wall_hi=(1, 1, 1), ncell=(5, 4, 6))
+    X, Y, Z = cell_centres(p)
+    G = 37.0
+    U = np.stack([G * Z, 0 * Z, 0 * Z], 1)
+    om = oracle_mod.curl(p, U)
+    np.testing.assert_allclose(om, np.tile([0.0, G, 0.0], (len(X), 1)), rtol=0, atol=1e-10 * G)
+    W = np.array([3.0, -2.0, 5.0])
+    r = np.stack([X - 0.004, Y - 0.013, Z + 0.002], 1)
+    U = np.cross(W, r)
+    om = oracle_mod.curl(p, U)
+    np.testing.assert_allclose(om, np.tile(2 * W, (len(X), 1)), rtol=0, atol=1e-10)
+    q = default_params(periodic=(1, 1, 1), wall_lo=(0, 0, 0), wall_hi=(0, 0, 0), ncell=(3, 2, 16))
+    X, Y, Z = cell_centres(q)
+    L = q["hi"][2] - q["lo"][2]
+    h = L / q["ncell"][2]
+    k = 2 * np.pi / L
+    U = np.stack([np.sin(k * Z), 0 * Z, 0 * Z], 1)
+    om = oracle_mod.curl(q, U)
+    expect = k * np.cos(k * Z) * np.sin(k * h) / (k * h)
+    np.testing.assert_allclose(om[:, 1], expect, rtol=0, atol=1e-12 * k)
+    assert np.abs(om[:, [0, 2]]).max() < 1e-12 * k
+
+
+def test_p16_saffman_lift_in_simple_shear(oracle_mod):
+    """P16: a sphere at rest in the simple shear U = (G z, 0, 0) feels Saffman's lift
+    C_l rho_f nu^0.5 d^2 G^0.5 U_x towards the faster fluid (+z); a sphere leading
+    the flow is pushed down; one moving with the fluid feels none; the force is
+    perpendicular to the slip and to the vorticity."""
+    d, G = 0.5e-3, 40.0
+    p = default_params(drag=0, pressure_grad=0, added_mass=0, lubrication=0, lift=1,
+                       periodic=(1, 1, 0), ncell=(4, 4, 8))
+    X, Y, Z = cell_centres(p)
+    o = oracle_mod.Oracle(p)
+    z0 = 0.0137
+    Ux = G * z0
+    for vx, sign in ((0.0, 1.0), (2 * Ux, -1.0), (Ux, 0.0)):
+        o.set_particles(np.array([[0.011, 0.009, z0]]), np.array([[vx, 0.0, 0.0]]),
+                        np.zeros((1, 3)), np.array([d]), np.array([RHO]))
+        o.set_fluid(U=np.stack([G * Z, 0 * Z, 0 * Z], 1))
+        f = o.forces()["fluid"][0]
+        expect = p["c_lift"] * p["rho_f"] * math.sqrt(p["nu_f"]) * d * d * math.sqrt(G) * abs(Ux - vx)
+        assert abs(f[2] - sign * expect) <= 1e-9 * max(expect, 1e-30) + 1e-30
+        assert abs(f[0]) <= 1e-12 * expect + 1e-30 and abs(f[1]) <= 1e-12 * expect + 1e-30
+    # general orientation: perpendicular to w and omega, magnitude |w x omega| / |omega|^0.5 scale
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        w, om = rng.normal(size=3), rng.normal(size=3) * 20
+        f = oracle_mod.lift(p, w, om, d)
+        assert abs(f @ w) < 1e-12 * np.linalg.norm(f) * np.linalg.norm(w)
+        assert abs(f @ om) < 1e-12 * np.linalg.norm(f) * np.linalg.norm(om)
+        mag = p["c_lift"] * p["rho_f"] * math.sqrt(p["nu_f"]) * d * d * np.linalg.norm(np.cross(w, om))
+        assert abs(np.linalg.norm(f) - mag / math.sqrt(np.linalg.norm(om))) < 1e-12 * mag
+    assert np.all(oracle_mod.lift(p, [0.1, 0, 0], [0, 0, 0], d) == 0)
+
+
+def test_p17_tangential_lubrication_limits(oracle_mod):
+    """P17: the shear lubrication term has the published leading terms: equal
+    spheres 6 pi mu a (1/6) ln(a/h) (Jeffrey & Onishi), sphere-wall
+    6 pi mu a (8/15) ln(a/h) (Goldman, Cox & Brenner); its prefactor tends to the
+    wall's as one sphere grows; the pair is antisymmetric, conserves angular
+    momentum, and a sphere rolling without slip on a wall feels none of it."""
+    p = default_params(lub_tangential=1)
+    mu = p["rho_f"] * p["nu_f"]
+    a = 0.5e-3
+    h = 0.02 * a
+    v = np.array([0.0, 0.013, 0.0])
+    z = np.zeros(3)
+    F, Ta, Tb = oracle_mod.lub_pair(p, [2 * a + h, 0, 0], a, a, v, z, z, z)
+    expect = -np.pi * mu * a * math.log(a / h) * v
+    np.testing.assert_allclose(F, expect, rtol=1e-12, atol=0)
+    n = np.array([0.0, 0.0, -1.0])
+    Fw, Tw = oracle_mod.lub_wall(p, n, a + h, a, v, z)
+    np.testing.assert_allclose(Fw, -6 * np.pi * mu * a * (8 / 15) * math.log(a / h) * v, rtol=1e-12)
+    np.testing.assert_allclose(Tw, np.cross((a + h / 2) * n, Fw), rtol=1e-12)
+    # prefactor -> the wall's as r_b grows (the logarithm is the pair's own)
+    for beta in (1e3, 1e5):
+        rb = beta * a
+        # h_in scales with the pair-mean diameter: keep it below h
+        F, _, _ = oracle_mod.lub_pair(dict(p, lub_h_in_frac=1e-12), [a + rb + h, 0, 0], a, rb,
+                                      v, z, z, z)
+        pref = -F[1] / (v[1] * math.log((a + rb) / (2 * h)))
+        assert abs(pref / (6 * np.pi * mu * a * 8 / 15) - 1) < 3 / beta
+    # antisymmetry and angular momentum for an unequal pair with spins
+    rng = np.random.default_rng(2)
+    ra, rb = 0.3e-3, 0.45e-3
+    e = rng.normal(size=3)
+    e /= np.linalg.norm(e)
+    dx = (ra + rb + 0.03e-3) * e
+    va, vb, wa, wb = (rng.normal(size=3) * s for s in (0.01, 0.01, 30, 30))
+    F, Ta, Tb = oracle_mod.lub_pair(p, dx, ra, rb, va, vb, wa, wb)
+    G, Ua, Ub = oracle_mod.lub_pair(p, -dx, rb, ra, vb, va, wb, wa)
+    np.testing.assert_allclose(G, -F, rtol=1e-12, atol=1e-24)
+    np.testing.assert_allclose(Ua, Tb, rtol=1e-12, atol=1e-28)
+    np.testing.assert_allclose(Ub, Ta, rtol=1e-12, atol=1e-28)
+    L = Ta + Tb - np.cross(dx, F)
+    assert np.abs(L).max() <= 1e-12 * np.abs(Ta).max()
+    # rolling without slip: surface velocity at the gap midpoint is zero
+    w = np.array([0.0, 80.0, 0.0])
+    l = a + h / 2
+    vroll = -np.cross(l * w, n)
+    Fr, Tr = oracle_mod.lub_wall(p, n, a + h, a, vroll, w)
+    assert np.abs(Fr).max() <= 1e-12 * 6 * np.pi * mu * a * np.abs(vroll).max()
+    # switched off: the normal squeeze alone, no torque
+    F0, Ta0, _ = oracle_mod.lub_pair(dict(p, lub_tangential=0), dx, ra, rb, va, vb, wa, wb)
+    assert np.all(Ta0 == 0) and abs(F0 @ np.cross(e, [1.0, 0, 0])) <= 1e-12 * np.linalg.norm(F0)
+
+
+def test_p17_sliding_sphere_spins_up_above_wall(oracle_mod):
+    """P17 through the stepping oracle: a sphere sliding parallel to a wall at a
+    lubrication gap starts to spin in the rolling sense (w_y > 0 for v_x > 0 above
+    a floor) and slows; without the tangential term neither happens."""
+    d = 1e-3
+    r = d / 2
+    out = []
+    for lt in (1, 0):
+        p = default_params(drag=0, pressure_grad=0, added_mass=0, g=(0, 0, 0), wall_hi=(0, 0, 0),
+                           lub_tangential=lt)
+        o = single(oracle_mod, p, [0.01, 0.01, r + 0.01 * d], [0.02, 0, 0], d)
+        o.step(50)
+        x, v, w, _ = o.get_particles()
+        out.append((v[0], w[0]))
+    (v1, w1), (v0, w0) = out
+    assert w1[1] > 0 and v1[0] < 0.02 and abs(w1[0]) < 1e-12 * abs(w1[1]) + 1e-30
+    assert np.all(w0 == 0) and v0[0] == 0.02

@@ -14,15 +14,38 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 MUTATIONS = [
     ("orc_contact.cpp", "double la = ra - 0.5 * delta, lb = rb - 0.5 * delta;",
      "double la = ra, lb = rb;", "test_p4"),
-    ("orc_contact.cpp", "V3 Fn = sub(scl(-kn * delta * std::sqrt(delta), n), scl(cn, vn));",
-     "V3 Fn = add(scl(-kn * delta * std::sqrt(delta), n), scl(cn, vn));", "test_p2"),
+    ("orc_contact.cpp", "V3 Fn = sub(scl(-fel, n), scl(cn, vn));",
+     "V3 Fn = add(scl(-fel, n), scl(cn, vn));", "test_p2"),
+    ("orc_contact.cpp", "cn = -2.0 * mat.beta * std::sqrt(Sn * ms);",
+     "cn = -2.0 * std::sqrt(5.0 / 6.0) * mat.beta * std::sqrt(Sn * ms);", "test_linear_spring"),
+    ("orc_contact.cpp", "fel = p.kn_linear * delta;", "fel = p.kn_linear * delta * std::sqrt(delta / 1e-6);",
+     "test_linear_spring"),
     ("orc_contact.cpp", "double kn = (4.0 / 3.0) * mat.Es * std::sqrt(Rs);",
      "double kn = (4.0 / 3.0) * mat.Es * Rs;", "test_p1"),
     ("orc_contact.cpp", "out.Ta = cross(scl(la, n), Ft);", "out.Ta = cross(Ft, scl(la, n));", "test_p4"),
     ("orc_contact.cpp", "out.Ta = cross(scl(l, n), Ft);", "out.Ta = cross(Ft, scl(l, n));", "test_p13"),
     ("orc_contact.cpp", "  if (ft > p.friction * fn) {", "  if (false) {", "test_p13"),
-    ("orc_contact.cpp", "return scl(-6.0 * M_PI * mu * r * r * vn / hh, n);",
-     "return scl(-6.0 * M_PI * mu * r * vn / hh, n);", "test_p10"),
+    ("orc_contact.cpp", "out.F = scl(-6.0 * M_PI * mu * r * r * vn / hh, n);",
+     "out.F = scl(-6.0 * M_PI * mu * r * vn / hh, n);", "test_p10"),
+    ("orc_contact.cpp", "double shape = (2.0 + beta + 2.0 * beta * beta) / ((1.0 + beta) * (1.0 + beta));",
+     "double shape = (2.0 + beta + beta * beta) / ((1.0 + beta) * (1.0 + beta));", "test_p17"),
+    ("orc_contact.cpp", "double la = ra + 0.5 * h, lb = rb + 0.5 * h;", "double la = ra, lb = rb;",
+     "test_p17"),
+    ("orc_contact.cpp", "double lg = std::log(dbar / (2.0 * hh));", "double lg = std::log(dbar / hh);",
+     "test_p17"),
+    ("orc_contact.cpp", "V3 Fs = scl(-6.0 * M_PI * mu * r * (8.0 / 15.0) * lg, vt);",
+     "V3 Fs = scl(-6.0 * M_PI * mu * r * (4.0 / 15.0) * lg, vt);", "test_p17"),
+    ("orc_step.cpp", "out.tq[j] = orc::add(out.tq[j], l.Tb);", "", "test_p4"),
+    ("orc_fluid.cpp", "d * d / std::sqrt(om), cross(w, omega));", "d * d / std::sqrt(om), cross(omega, w));",
+     "test_p16"),
+    ("orc_fluid.cpp", "d * d / std::sqrt(om), cross(w, omega));", "d * d / om, cross(w, omega));",
+     "test_p16"),
+    ("orc_fluid.cpp", "f = add(f, lift_force(p, sub(U, u), om, d));",
+     "f = add(f, lift_force(p, sub(u, U), om, d));", "test_p16"),
+    ("orc_fluid.cpp", "out[3 * c + 1] = g[2][0] - g[0][2];", "out[3 * c + 1] = g[0][2] - g[2][0];",
+     "test_p15"),
+    ("orc_fluid.cpp", "ip[a] = 1;\n            den = h;", "ip[a] = 1;\n            den = 2.0 * h;",
+     "test_p15"),
     ("orc_fluid.cpp", "double c = 0.63 + 4.8 * std::sqrt(Vr / Re);\n  double Cd = c * c;",
      "double c = 0.63 + 0.48 * std::sqrt(Vr / Re);\n  double Cd = c * c;", "test_p3"),
     ("orc_fluid.cpp", "f = add(f, scl(p.c_add * p.rho_f * Vp, sub(Du, a_prev)));",

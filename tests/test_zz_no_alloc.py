@@ -40,6 +40,23 @@ def test_static_smoothing_matches_handle_path_twice():
         assert np.array_equal(dev_in.cpu().numpy(), phi)
 
 
+def test_static_smoothing_bdf2():
+    # the BDF2 pseudo-time scheme keeps the previous step in the same static scratch
+    prm = default_params(hi=(64e-3, 32e-3, 64e-3), ncell=(64, 32, 64), wall_hi=(0, 0, 0),
+                         bandwidth=(1.5e-3,) * 3, tau_scheme=1, precision_form="split")
+    ref = sedi.Sedi(prm)
+    phi = random_fields(prm["ncell"], 7, seed=23)
+    want, want_it = ref.smooth(phi)
+    dev_in = torch.as_tensor(phi, device="cuda")
+    dev_out = torch.full_like(dev_in, float("nan"))
+    torch.cuda.synchronize()
+    it = sedi.smooth_static(prm, dev_in, dev_out)
+    got = dev_out.cpu().numpy()
+    for f in range(7):
+        assert np.abs(got[f] - want[f]).max() <= 1e-7 * np.abs(phi[f]).max(), f
+    assert np.array_equal(it, want_it)
+
+
 def test_static_smoothing_rejects_oversize():
     prm = default_params(ncell=(128, 128, 64))  # 8 fields x 1,048,576 cells > limit
     C = int(np.prod(prm["ncell"]))
