@@ -271,6 +271,9 @@ def gpu_arm(args):
     cnn = None
     if rank == 0 and not args.no_cnn:
         cnn = cnn_warm_start(prm, parts, fl)
+    bounce = None
+    if rank == 0 and not args.no_bounce:
+        bounce = bounce_leg()
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
@@ -287,12 +290,41 @@ def gpu_arm(args):
                 "phases_ms_per_step": phases, "rebuilds_in_timed_region": int(rebuilds),
                 "roofline": roof, "plain_form": plain, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks, "cpu_baseline": cpu, "ensemble": ens, "large": large,
-                "cnn_warm_start": cnn}
+                "cnn_warm_start": cnn, "case1_bounce": bounce}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+
+
+def bounce_leg():
+    """Case 1 (Sec. 3.1): a 6 mm sphere falls onto the floor through quiescent fluid;
+    the effective restitution e = e_water / e_air (e_air = 0.97, the dry coefficient of
+    the linear contact law) over Stokes numbers set by density and viscosity, with
+    lubrication and added mass and without them.  Qualitative: the paper compares with
+    experimental data that are not available here."""
+    from paper_1601_03801_gb300 import diagnostics as dg
+    from paper_1601_03801_gb300 import sedi
+    from paper_1601_03801_gb300.workloads import bounce_case
+    d, out = 6e-3, []
+    t0 = time.time()
+    for rho_p, nu in ((7800, 1e-6), (2500, 1e-6), (7800, 1e-5), (2500, 1e-5), (7800, 3e-5), (7800, 1e-4)):
+        dt = dg.linear_contact_time(800.0, rho_p * math.pi / 6 * d ** 3, 0.97) / 50
+        row = {"rho_p": rho_p, "nu_f": nu, "dt": dt}
+        for key, on in (("e_eff", 1), ("e_eff_without_lub_added_mass", 0)):
+            prm, parts = bounce_case(rho_p, nu, dt, d=d, lubrication=on, added_mass=on)
+            g = sedi.Sedi(dict(prm, precision_form="split"))
+            g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+            v_in, v_out, _ = dg.bounce_velocities(g, chunk=10)
+            row[key] = round(v_out / abs(v_in) / 0.97, 4)
+            if on:
+                row["impact_speed"] = round(-v_in, 4)
+                row["St"] = round(dg.stokes_number(rho_p, d, v_in, nu, 1000.0), 1)
+        out.append(row)
+    return {"workload": "Case 1: 6 mm sphere, 100 x 100 x 500 mm box of quiescent fluid, k_n = 800 N/m, "
+                        "e = 0.97, mu = 0.1, dt = t_c / 50", "sweep": out,
+            "wall_s": round(time.time() - t0, 2)}
 
 
 def large_leg(peak_gbs, steps=3, warmup=2):
@@ -598,6 +630,7 @@ def main():
     ap.add_argument("--no-cnn", action="store_true", help="skip the learned-warm-start leg")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 256-bed ensemble leg")
     ap.add_argument("--no-large", action="store_true", help="skip the 10M-sphere leg")
+    ap.add_argument("--no-bounce", action="store_true", help="skip the Case-1 bounce sweep")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--settle", type=int, default=50, help="untimed settling steps before warm-up")
     ap.add_argument("--mode", default="bench", choices=["bench", "kernels"],

@@ -127,8 +127,10 @@ typedef struct sedi_params {
                                               -1 = autotuned at the first sedi_step [-1];
                                               0: 128 threads, 6 blocks/SM; 1: 64 x 12;
                                               2: 256 x 3; 3: 128 x 8; 4: 128 x 5, all with
-                                              the warp-cooperative pair phase; 5: 128 x 6
-                                              with a per-particle pair loop.  The split
+                                              the warp-cooperative pair phase; 5: 128 x 6,
+                                              6: 128 x 8, 7: 64 x 12 with a per-particle
+                                              pair loop.  With lift or lub_tangential on
+                                              the loop at 128 x 6 runs.  The split
                                               form gives bit-identical results across
                                               variants, the plain form agrees to FP32
                                               rounding.  The FP64 parity form always runs

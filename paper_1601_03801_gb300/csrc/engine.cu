@@ -585,6 +585,11 @@ void tune_file_store(const std::string& key, int variant, const double* us) {
 // Choose h->variant for the current particles (no-op when fixed or up to date).
 int autotune(sedi_handle* h) {
   if (h->prm.substep_variant >= 0 || h->form == FORM_FP64) return 0;
+  if (h->P.lift || h->P.lub_tangential) {
+    // the optional terms run one launch shape (the per-particle loop at 128 x 6)
+    h->variant = SUBSTEP_B128_LOOP;
+    return 0;
+  }
   const std::string key = tune_key(h);
   if (key == h->tuned_key) return 0;
   int best = -1;
@@ -1087,6 +1092,9 @@ static int smooth_status(sedi_handle* h, int nf) {
 // control block); a step and an averaging are batched launches over all beds, the
 // beds' views gathered in one device table.
 
+// every bed shares the physics switches of the ensemble's parameters
+static bool ens_ext(const sedi_handle* h) { return h->P.lift || h->P.lub_tangential; }
+
 static int ens_finalize(sedi_handle* h) {
   for (size_t b = 0; b < h->beds.size(); ++b)
     if (!h->beds[b]->have_particles) return fail(h, SEDI_ESTATE, "bed %zu has no particles", b);
@@ -1180,7 +1188,7 @@ static int build_graph_ens(sedi_handle* h, int n, cudaGraphExec_t* out) {
     launch_rebuild_ens(h->form, h->ens, s, h->side);
     CK(cudaStreamEndCapture(h->side, &body));
     const bool more = s + 1 < n;
-    launch_substep_ens(h->form, h->ens, s, more ? (unsigned long long)ch[s + 1] : 0ull, more ? 1 : 0,
+    launch_substep_ens(h->form, h->ens, ens_ext(h), s, more ? (unsigned long long)ch[s + 1] : 0ull, more ? 1 : 0,
                        h->stream);
   }
   launch_advance_ens(h->ens, n, h->stream);
@@ -1214,7 +1222,7 @@ static int ens_step(sedi_handle* h, int n) {
     launch_check_ens(h->ens, 0ull, 0, h->stream);
     for (int s = 0; s < n; ++s) {
       launch_rebuild_ens(h->form, h->ens, s, h->stream);
-      launch_substep_ens(h->form, h->ens, s, 0ull, 0, h->stream);
+      launch_substep_ens(h->form, h->ens, ens_ext(h), s, 0ull, 0, h->stream);
     }
     launch_advance_ens(h->ens, n, h->stream);
   }

@@ -37,7 +37,7 @@ __device__ __forceinline__ void axis_w(F s, int n, int per, int* i0, int* i1, F*
 // one interpolation, and the cell vorticity omega = curl U_f for the lift.  Drag is
 // written in a form without 1/Re:
 //   C_d |w| = (0.63 sqrt|w| + 4.8 sqrt(V_r nu / d))^2.
-template <class S, class F>
+template <class S, class F, bool LIFT = true>
 __device__ __forceinline__ void fluid_force(const DevParams& P, const ForceConsts<F>& K,
                                             const Quad<F>* ufe, const Quad<F>* gfl,
                                             const Quad<F>* wfl, const S* x, F r, const F v[3],
@@ -75,7 +75,7 @@ __device__ __forceinline__ void fluid_force(const DevParams& P, const ForceConst
           G[1] += w * g.b;
           G[2] += w * g.c;
         }
-        if (P.lift) {
+        if (LIFT && P.lift) {
           Quad<F> o = ldq(wfl + c);
           Om[0] += w * o.a;
           Om[1] += w * o.b;
@@ -111,7 +111,7 @@ __device__ __forceinline__ void fluid_force(const DevParams& P, const ForceConst
     out[1] += coef * w1;
     out[2] += coef * w2;
   }
-  if (P.lift) {
+  if (LIFT && P.lift) {
     const F om = xsqrt(Om[0] * Om[0] + Om[1] * Om[1] + Om[2] * Om[2]);
     if (om > F(0)) {
       const F s = K.lift_c * d * d / xsqrt(om);

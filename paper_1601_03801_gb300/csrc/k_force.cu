@@ -118,7 +118,9 @@ struct PairOut {
   bool contact, lub;
 };
 
-template <int FORM, bool INTEGRATE>
+// EXT: the optional terms (tangential lubrication here, lift in the fluid force)
+// are compiled in; without it the kernel carries none of their registers.
+template <int FORM, bool INTEGRATE, bool EXT>
 __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
     const DevParams& P, const Quad<typename Traits<FORM>::S>& Pi,
     const typename Traits<FORM>::F* vi, const typename Traits<FORM>::F* wi,
@@ -165,7 +167,7 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
   const F* vA = i_lo ? vi : vj;
   const F* vB = i_lo ? vj : vi;
   F wj[3] = {F(0), F(0), F(0)};
-  if (o.contact || (o.lub && P.lub_tangential)) {
+  if (o.contact || (EXT && o.lub && P.lub_tangential)) {
     const Quad<S> Wj = ldq(omg + j);
     wj[0] = NS::f(Wj.a);
     wj[1] = NS::f(Wj.b);
@@ -207,7 +209,7 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
     F sl = -K.six_pi_mu * Rl * Rl * vn / hh;
     if (!i_lo) sl = -sl;
     o.l = V3<F>{sl * n.x, sl * n.y, sl * n.z};
-    if (P.lub_tangential) {
+    if (EXT && P.lub_tangential) {
       // shear term: -6 pi mu R_l (4/15) (2 + b + 2 b^2)/(1 + b)^2 ln((r_A + r_B) / 2h) v_t,
       // b = r_B / r_A, v_t the tangential surface velocity of A relative to B at the
       // gap midpoint (lever arms r + h/2); torque l n x F on both spheres
@@ -242,7 +244,7 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
 // Body of the fused substep for one bed: blk is the block's index within the bed,
 // nblk the bed's block count; ectl (ensembles only) collects the rebuild decision
 // of all nbeds beds for the graph condition of the next substep.
-template <int FORM, bool INTEGRATE, int BS, bool COOP>
+template <int FORM, bool INTEGRATE, int BS, bool COOP, bool EXT>
 __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& mesh,
                                              const DevParams& P, int sub_off,
                                              cudaGraphConditionalHandle next, int use_cond,
@@ -321,7 +323,7 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
     __shared__ Quad<S> q_pi[W][32];
     __shared__ F q_vw[W][32][8];  // vi, wi, mi, (pad)
     __shared__ uint32_t q_mask[W][32];
-    __shared__ F q_res[W][32][12];
+    __shared__ F q_res[W][32][EXT ? 12 : 9];
     __shared__ uint8_t q_flag[W][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int cnt = __popc(live);
@@ -359,7 +361,7 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
         const int L = e >> 8, k = e & 255;
         const int64_t iL = i0 + L;
         const F* vw = q_vw[wid][L];
-        const PairOut<F> o = pair_eval<FORM, INTEGRATE>(P, q_pi[wid][L], vw, vw + 3, vw[6],
+        const PairOut<F> o = pair_eval<FORM, INTEGRATE, EXT>(P, q_pi[wid][L], vw, vw + 3, vw[6],
                                                         nbr[(int64_t)k * N + iL], k,
                                                         (q_mask[wid][L] >> k) & 1u, iL, N, pos, vel,
                                                         omg, hist);
@@ -367,7 +369,9 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
         r[0] = o.fa.x; r[1] = o.fa.y; r[2] = o.fa.z;
         r[3] = o.t.x; r[4] = o.t.y; r[5] = o.t.z;
         r[6] = o.l.x; r[7] = o.l.y; r[8] = o.l.z;
-        r[9] = o.lt.x; r[10] = o.lt.y; r[11] = o.lt.z;
+        if constexpr (EXT) {
+          r[9] = o.lt.x; r[10] = o.lt.y; r[11] = o.lt.z;
+        }
         q_flag[wid][lane] = (uint8_t)((o.contact ? 1 : 0) | (o.lub ? 2 : 0));
       }
       __syncwarp();
@@ -384,8 +388,10 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
         }
         if (fg & 2) {
           fl.x += r[6]; fl.y += r[7]; fl.z += r[8];
-          if (P.lub_tangential) {
-            tq.x += r[9]; tq.y += r[10]; tq.z += r[11];
+          if constexpr (EXT) {
+            if (P.lub_tangential) {
+              tq.x += r[9]; tq.y += r[10]; tq.z += r[11];
+            }
           }
         }
       }
@@ -395,7 +401,7 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
       while (live) {
         const int k = __ffs(live) - 1;
         live &= live - 1;
-        const PairOut<F> o = pair_eval<FORM, INTEGRATE>(P, Pi, vi, wi, mi, nbr[(int64_t)k * N + i], k,
+        const PairOut<F> o = pair_eval<FORM, INTEGRATE, EXT>(P, Pi, vi, wi, mi, nbr[(int64_t)k * N + i], k,
                                                         (mask >> k) & 1u, i, N, pos, vel, omg, hist);
         if (o.contact) {
           fc.x += o.fa.x; fc.y += o.fa.y; fc.z += o.fa.z;
@@ -404,7 +410,7 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
         }
         if (o.lub) {
           fl.x += o.l.x; fl.y += o.l.y; fl.z += o.l.z;
-          if (P.lub_tangential) {
+          if (EXT && P.lub_tangential) {
             tq.x += o.lt.x; tq.y += o.lt.y; tq.z += o.lt.z;
           }
         }
@@ -458,7 +464,7 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
             const F vn = vi[0] * n.x + vi[1] * n.y + vi[2] * n.z;
             const F s = -K.six_pi_mu * ri * ri * vn / hh;
             fl.x += s * n.x; fl.y += s * n.y; fl.z += s * n.z;
-            if (P.lub_tangential) {
+            if (EXT && P.lub_tangential) {
               // shear term against the plane: -6 pi mu r (8/15) ln(r / h) v_t
               const F l = ri + F(0.5) * h;
               const V3<F> wxn = cross(V3<F>{l * wi[0], l * wi[1], l * wi[2]}, n);
@@ -479,8 +485,8 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
     // fluid forces at the particle
     F ff[3];
     const F ap[3] = {Ai.a, Ai.b, Ai.c};
-    fluid_force<S, F>(P, K, (const Quad<F>*)mesh.ufe, (const Quad<F>*)mesh.gfl,
-                      (const Quad<F>*)mesh.wfl, xi_s, ri, vi, ap, ff);
+    fluid_force<S, F, EXT>(P, K, (const Quad<F>*)mesh.ufe, (const Quad<F>*)mesh.gfl,
+                           (const Quad<F>*)mesh.wfl, xi_s, ri, vi, ap, ff);
     if (!INTEGRATE) {
       double* o = st.fdbg;
       o[3 * i + 0] = (double)fc.x; o[3 * i + 1] = (double)fc.y; o[3 * i + 2] = (double)fc.z;
@@ -583,17 +589,17 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
   }
 }
 
-template <int FORM, bool INTEGRATE, int BS, int MINB, bool COOP>
+template <int FORM, bool INTEGRATE, int BS, int MINB, bool COOP, bool EXT>
 __global__ void __launch_bounds__(BS, MINB) k_substep(DevState st, DevMesh mesh, DevParams P,
                                                          int sub_off, cudaGraphConditionalHandle next,
                                                          int use_cond) {
-  substep_body<FORM, INTEGRATE, BS, COOP>(st, mesh, P, sub_off, next, use_cond, blockIdx.x,
-                                          gridDim.x, nullptr, 1);
+  substep_body<FORM, INTEGRATE, BS, COOP, EXT>(st, mesh, P, sub_off, next, use_cond, blockIdx.x,
+                                               gridDim.x, nullptr, 1);
 }
 
 // Ensemble: blockIdx.y is the bed, blockIdx.x the block within it (blocks past the
 // bed's particles return at once).
-template <int FORM, int BS, int MINB>
+template <int FORM, int BS, int MINB, bool EXT>
 __global__ void __launch_bounds__(BS, MINB) k_substep_e(const BedView* v, int nbeds, Ctl* ectl,
                                                            int sub_off, cudaGraphConditionalHandle next,
                                                            int use_cond) {
@@ -601,26 +607,31 @@ __global__ void __launch_bounds__(BS, MINB) k_substep_e(const BedView* v, int nb
   const unsigned nblk = (unsigned)((N + BS - 1) / BS);
   if (blockIdx.x >= nblk) return;
   const BedView& b = bed_view(v);
-  substep_body<FORM, true, BS, false>(b.st, b.mesh, b.P, sub_off, next, use_cond, blockIdx.x, nblk,
-                                      ectl, nbeds);
+  substep_body<FORM, true, BS, false, EXT>(b.st, b.mesh, b.P, sub_off, next, use_cond, blockIdx.x,
+                                           nblk, ectl, nbeds);
 }
 
-template <int FORM, int BS, int MINB, bool COOP>
+template <int FORM, int BS, int MINB, bool COOP, bool EXT = false>
 static void launch_bs(const DevState& st, const DevMesh& mesh, const DevParams& P, int sub_off,
                       bool integrate, unsigned long long next, int use_cond, cudaStream_t s) {
   const int64_t grid = (st.N + BS - 1) / BS;
   const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)next;
   if (integrate)
-    k_substep<FORM, true, BS, MINB, COOP><<<(unsigned)grid, BS, 0, s>>>(st, mesh, P, sub_off, h, use_cond);
+    k_substep<FORM, true, BS, MINB, COOP, EXT><<<(unsigned)grid, BS, 0, s>>>(st, mesh, P, sub_off, h, use_cond);
   else
-    k_substep<FORM, false, BS, MINB, COOP><<<(unsigned)grid, BS, 0, s>>>(st, mesh, P, sub_off, h, 0);
+    k_substep<FORM, false, BS, MINB, COOP, EXT><<<(unsigned)grid, BS, 0, s>>>(st, mesh, P, sub_off, h, 0);
 }
 
 template <int FORM>
 static void launch_one(const DevState& st, const DevMesh& mesh, const DevParams& P, int sub_off,
                        bool integrate, int variant, unsigned long long next, int use_cond,
                        cudaStream_t s) {
-  // the parity form runs the per-particle pair loop at 128 threads
+  // the optional terms (lift, tangential lubrication) and the parity form run the
+  // per-particle pair loop at 128 threads
+  if (P.lift || P.lub_tangential) {
+    launch_bs<FORM, 128, 6, false, true>(st, mesh, P, sub_off, integrate, next, use_cond, s);
+    return;
+  }
   if constexpr (FORM != FORM_FP64) {
     switch (variant) {
       case SUBSTEP_B64: launch_bs<FORM, 64, 12, true>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
@@ -628,6 +639,8 @@ static void launch_one(const DevState& st, const DevMesh& mesh, const DevParams&
       case SUBSTEP_B128_OCC8: launch_bs<FORM, 128, 8, true>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
       case SUBSTEP_B128_OCC5: launch_bs<FORM, 128, 5, true>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
       case SUBSTEP_B128_LOOP: launch_bs<FORM, 128, 6, false>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
+      case SUBSTEP_B128_OCC8_LOOP: launch_bs<FORM, 128, 8, false>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
+      case SUBSTEP_B64_LOOP: launch_bs<FORM, 64, 12, false>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
       default: launch_bs<FORM, 128, 6, true>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
     }
   } else {
@@ -653,15 +666,22 @@ void launch_substep(int form, const DevState& st, const DevMesh& mesh, const Dev
 }
 
 
-void launch_substep_ens(int form, const EnsLaunch& e, int sub_off, unsigned long long next_cond,
-                        int use_cond, cudaStream_t s) {
+template <bool EXT>
+static void launch_ens(int form, const EnsLaunch& e, int sub_off, unsigned long long next_cond,
+                       int use_cond, cudaStream_t s) {
   const dim3 grid((unsigned)((e.max_n + 127) / 128), (unsigned)e.B);
   const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)next_cond;
   switch (form) {
-    case FORM_SPLIT: k_substep_e<FORM_SPLIT, 128, 6><<<grid, 128, 0, s>>>(e.views, e.B, e.ectl, sub_off, h, use_cond); break;
-    case FORM_PLAIN: k_substep_e<FORM_PLAIN, 128, 6><<<grid, 128, 0, s>>>(e.views, e.B, e.ectl, sub_off, h, use_cond); break;
-    default: k_substep_e<FORM_FP64, 128, 6><<<grid, 128, 0, s>>>(e.views, e.B, e.ectl, sub_off, h, use_cond); break;
+    case FORM_SPLIT: k_substep_e<FORM_SPLIT, 128, 6, EXT><<<grid, 128, 0, s>>>(e.views, e.B, e.ectl, sub_off, h, use_cond); break;
+    case FORM_PLAIN: k_substep_e<FORM_PLAIN, 128, 6, EXT><<<grid, 128, 0, s>>>(e.views, e.B, e.ectl, sub_off, h, use_cond); break;
+    default: k_substep_e<FORM_FP64, 128, 6, EXT><<<grid, 128, 0, s>>>(e.views, e.B, e.ectl, sub_off, h, use_cond); break;
   }
+}
+
+void launch_substep_ens(int form, const EnsLaunch& e, bool ext, int sub_off,
+                        unsigned long long next_cond, int use_cond, cudaStream_t s) {
+  if (ext) launch_ens<true>(form, e, sub_off, next_cond, use_cond, s);
+  else launch_ens<false>(form, e, sub_off, next_cond, use_cond, s);
 }
 
 }  // namespace sedi

@@ -8,18 +8,23 @@ namespace sedi {
 
 // Launch variants of the substep kernel: threads per block and minimum resident
 // blocks per SM (128/6, 64/12, 256/3 cap registers at 80 a thread, 128/8 at 64,
-// 128/5 at 96), all with the warp-cooperative pair phase; variant 5 is 128/6 with
-// the per-particle pair loop.  The FP64 parity form runs 128/6 with the loop.
+// 128/5 at 96), all with the warp-cooperative pair phase; variants 5-7 run the
+// per-particle pair loop at 128/6, 128/8 and 64/12.  The FP64 parity form runs
+// 128/6 with the loop.
 enum SubstepVariant {
   SUBSTEP_B128 = 0,
   SUBSTEP_B64 = 1,
   SUBSTEP_B256 = 2,
   SUBSTEP_B128_OCC8 = 3,
   SUBSTEP_B128_OCC5 = 4,
-  SUBSTEP_B128_LOOP = 5
+  SUBSTEP_B128_LOOP = 5,
+  SUBSTEP_B128_OCC8_LOOP = 6,
+  SUBSTEP_B64_LOOP = 7
 };
-constexpr int kSubstepVariants = 6;
-inline int substep_block(int variant) { return variant == SUBSTEP_B64 ? 64 : variant == SUBSTEP_B256 ? 256 : 128; }
+constexpr int kSubstepVariants = 8;
+inline int substep_block(int variant) {
+  return (variant == SUBSTEP_B64 || variant == SUBSTEP_B64_LOOP) ? 64 : variant == SUBSTEP_B256 ? 256 : 128;
+}
 
 // k_force.cu: one fused substep (integrate = true) or forces only into st.fdbg.
 // The last block of an integrating launch sets ctl->need_rebuild and, when
@@ -53,8 +58,9 @@ void launch_check_ens(const EnsLaunch& e, unsigned long long cond_handle, int us
 void launch_rebuild_ens(int form, const EnsLaunch& e, int sub_off, cudaStream_t s);
 void launch_advance_ens(const EnsLaunch& e, int n, cudaStream_t s);
 void launch_ctl_gather_ens(const EnsLaunch& e, Ctl* out, cudaStream_t s);
-void launch_substep_ens(int form, const EnsLaunch& e, int sub_off, unsigned long long next_cond,
-                        int use_cond, cudaStream_t s);
+// ext: the beds run the optional terms (lift, tangential lubrication)
+void launch_substep_ens(int form, const EnsLaunch& e, bool ext, int sub_off,
+                        unsigned long long next_cond, int use_cond, cudaStream_t s);
 // deposition of every bed (cleared first), fixed point -> smoothing word
 void launch_deposit_ens(int form, const EnsLaunch& e, cudaStream_t s);
 // smoothed eps of every bed -> the drag's mesh word

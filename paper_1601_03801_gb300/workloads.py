@@ -15,6 +15,9 @@ Sec. 3.1, 3.3 and 4.2, Table 1; every one is synthetic):
   at z = 0, log-law flow u* = 0.02 m/s, 64 x 32 x 64 mesh.
 * ``large``  : 10,000,000 spheres, d ~ U[0.4, 0.6] mm, 400 x 200 x 100 mm,
   256 x 128 x 64 mesh, mean flow 0.3 m/s plus filtered noise of rms 0.03 m/s.
+* ``bounce`` : Case 1, one 6 mm sphere (sand or steel) released above the floor
+  of a 100 x 100 x H mm box of quiescent fluid, the paper's linear contact
+  (k_n = 800 N/m, e = 0.97, mu = 0.1); the viscosity sets the Stokes number.
 
 Beds are made without any dynamics: a periodic block is seeded on an FCC
 lattice of spacing ~1.1 median diameters (packing fraction ~0.58), overlaps are
@@ -420,3 +423,22 @@ def random_fields(ncell, nf, seed, scale=1.0):
     f = rng.random((nf, C)) * scale
     f[rng.random((nf, C)) < 0.5] = 0.0
     return f
+
+
+def bounce_case(rho_p, nu_f, dt, d=6e-3, height=0.5, drop=0.45, lubrication=1, added_mass=1):
+    """Case 1 of Sec. 3.1 (Table 1): one sphere of diameter d and density rho_p
+    released at rest at z = drop in quiescent fluid (rho_f = 1000, viscosity nu_f)
+    in a 100 x 100 x height mm box, periodic in x and y, floor and lid walls, 10 x
+    10 x (height / 10 mm) mesh; the paper's linear spring-dashpot contact
+    (k_n = 800 N/m, e = 0.97, mu = 0.1).  The box is taller than the paper's 200 mm
+    so the sphere nears its settling speed before the impact."""
+    prm = default_params(
+        contact_law=1, kn_linear=800.0, kt_ratio=2.0 / 7.0, restitution=0.97, friction=0.1,
+        rho_f=1000.0, nu_f=nu_f, lo=(0.0, 0.0, 0.0), hi=(0.1, 0.1, height),
+        periodic=(1, 1, 0), wall_lo=(0, 0, 1), wall_hi=(0, 0, 1), dt=dt, skin=1e-3,
+        lubrication=lubrication, added_mass=added_mass, drag=1, pressure_grad=1,
+        ncell=(10, 10, int(round(height / 0.01))), bandwidth=(0.0, 0.0, 0.0))
+    parts = dict(x=np.array([[0.05, 0.05, drop]]), v=np.zeros((1, 3)), w=np.zeros((1, 3)),
+                 d=np.array([d]), rho=np.array([rho_p]))
+    return prm, parts
+

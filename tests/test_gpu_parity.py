@@ -155,6 +155,29 @@ def test_lift_and_tangential_lubrication(small, form):
     assert rel_err(wg, wo) <= (1e-8 if form == "fp64" else 1e-3)
 
 
+@pytest.mark.parametrize("form", ["fp64", "split"])
+def test_case1_bounce_matches_oracle(form):
+    # Case 1 (Sec. 3.1): a 6 mm steel sphere falls onto the floor under the paper's
+    # linear contact, with lubrication and added mass; impact and rebound speeds of
+    # the library against the oracle sampled every 10 substeps
+    import math
+    from paper_1601_03801_gb300 import diagnostics as dg
+    from paper_1601_03801_gb300.workloads import bounce_case
+    d, rho = 6e-3, 7800.0
+    dt = dg.linear_contact_time(800.0, rho * math.pi / 6 * d ** 3, 0.97) / 50
+    for nu in (1e-5, 1e-4):
+        prm, parts = bounce_case(rho, nu, dt, d=d)
+        g = sedi.Sedi(dict(prm, precision_form=form))
+        g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+        o = orc.Oracle(prm)
+        o.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+        vg, vo = dg.bounce_velocities(g, chunk=10), dg.bounce_velocities(o, chunk=10)
+        assert vg[2] == vo[2], (vg, vo)
+        tol = 1e-9 if form == "fp64" else 2e-4
+        assert abs(vg[0] - vo[0]) <= tol * abs(vo[0]) and abs(vg[1] - vo[1]) <= tol * abs(vo[0]), (vg, vo)
+        assert vo[1] > 0.0
+
+
 @pytest.mark.parametrize("form,steps,tol", [("fp64", 200, 1e-10), ("split", 200, 1e-4)])
 def test_trajectory_200_steps(small, form, steps, tol):
     prm, parts = small
@@ -216,14 +239,15 @@ def test_substep_variants_bit_identical(small, form):
     per-particle loop (variant 5).  The plain FP32 form agrees to FP32 rounding."""
     prm, parts = small
     ref = None
-    for variant in range(6):
+    for variant in range(8):
         g = sedi.Sedi(dict(prm, precision_form=form, substep_variant=variant))
         g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
         g.step(40)
         eps, _, F = g.average()
         st = g.stats()
         assert st["substep_variant"] == variant
-        assert st["substep_block"] == {0: 128, 1: 64, 2: 256, 3: 128, 4: 128, 5: 128}[variant]
+        assert st["substep_block"] == {0: 128, 1: 64, 2: 256, 3: 128, 4: 128, 5: 128, 6: 128,
+                                       7: 64}[variant]
         got = (*g.get_particles(), eps, F)
         if ref is None:
             ref = got
@@ -251,7 +275,7 @@ def test_autotuner_chooses_and_caches(small, tmp_path, monkeypatch):
     assert g.stats()["substep_variant"] == -1
     g.step(10)
     st = g.stats()
-    assert 0 <= st["substep_variant"] < 6 and st["substep_block"] in (64, 128, 256)
+    assert 0 <= st["substep_variant"] < 8 and st["substep_block"] in (64, 128, 256)
     lines = cache.read_text().splitlines()
     assert len(lines) == 1 and f"N={n}|" in lines[0] and '"median_us"' in lines[0]
     # a second handle on the same workload takes the cached choice without re-timing
@@ -464,7 +488,7 @@ def test_errors_are_reported(small):
     with pytest.raises(sedi.SediError):
         sedi.Sedi(dict(prm, restitution=0.0))
     with pytest.raises(sedi.SediError):
-        sedi.Sedi(dict(prm, substep_variant=6))
+        sedi.Sedi(dict(prm, substep_variant=8))
     g = sedi.Sedi(dict(prm, precision_form="split", nbr_capacity=2))
     with pytest.raises(sedi.SediError) as e:
         g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])

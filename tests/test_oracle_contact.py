@@ -270,3 +270,26 @@ def test_linear_law_differs_from_hertz_at_same_state(oracle_mod):
     delta = D - 2 * 0.4999e-3
     assert abs(f[1] + 800.0 * delta) < 1e-12 * 800.0 * D  # F = -k_n delta on the left sphere
     assert abs(f[0] - f[1]) > 1e-3 * abs(f[1])
+
+
+def test_case1_bounce_effective_restitution(oracle_mod):
+    """Case 1 (Sec. 3.1) on the oracle: with lubrication and added mass the effective
+    restitution e_water / e_air falls with the Stokes number (small at St ~ 25, near 1
+    at St ~ 5000); without them the sphere keeps nearly its dry coefficient."""
+    from paper_1601_03801_gb300 import diagnostics as dg
+    from paper_1601_03801_gb300.workloads import bounce_case
+    d, rho = 6e-3, 7800.0
+    dt = dg.linear_contact_time(800.0, rho * math.pi / 6 * d ** 3, 0.97) / 50
+    e_lub, e_dry, st = [], [], []
+    for nu in (1e-6, 1e-5, 1e-4):
+        for on, out in ((1, e_lub), (0, e_dry)):
+            prm, parts = bounce_case(rho, nu, dt, d=d, lubrication=on, added_mass=on)
+            o = oracle_mod.Oracle(prm)
+            o.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+            v_in, v_out, _ = dg.bounce_velocities(o, chunk=10)
+            out.append(v_out / abs(v_in) / 0.97)
+            if on:
+                st.append(dg.stokes_number(rho, d, v_in, nu, 1000.0))
+    assert st[0] > st[1] > st[2] and st[2] < 40 and st[0] > 3000
+    assert e_lub[0] > e_lub[1] > e_lub[2] and e_lub[2] < 0.2 and e_lub[0] > 0.85
+    assert all(e > 0.95 for e in e_dry) and all(a < b for a, b in zip(e_lub, e_dry))

@@ -42,8 +42,8 @@ def test_static_smoothing_matches_handle_path_twice():
 
 def test_static_smoothing_bdf2():
     # the BDF2 pseudo-time scheme keeps the previous step in the same static scratch
-    prm = default_params(hi=(64e-3, 32e-3, 64e-3), ncell=(64, 32, 64), wall_hi=(0, 0, 0),
-                         bandwidth=(1.5e-3,) * 3, tau_scheme=1, precision_form="split")
+    prm = dict(default_params(hi=(64e-3, 32e-3, 64e-3), ncell=(64, 32, 64), wall_hi=(0, 0, 0),
+                              bandwidth=(1.5e-3,) * 3, tau_scheme=1), precision_form="split")
     ref = sedi.Sedi(prm)
     phi = random_fields(prm["ncell"], 7, seed=23)
     want, want_it = ref.smooth(phi)
