@@ -113,6 +113,11 @@ typedef struct sedi_params {
   double c_lift;                           /* lift coefficient C_l, Eq. 7 [1.6] */
   double eps_max;                          /* clamp of eps_s in the drag law [0.9] */
   int32_t ncell[3];                        /* Eulerian mesh */
+  double z_grading;                        /* graded mesh along z (Sec. 3.2: refined
+                                              towards the bottom): cell heights grow
+                                              geometrically from lo[2], top cell / bottom
+                                              cell = z_grading; 1 = uniform.  Needs a
+                                              non-periodic z axis with ncell[2] >= 2 [1] */
   double bandwidth[3];                     /* Gaussian bandwidth b per axis (Sec. 2.4) */
   int32_t n_tau;                           /* implicit pseudo-time steps [4] */
   int32_t tau_scheme;                      /* SEDI_TAU_EULER | SEDI_TAU_BDF2 [EULER];

@@ -29,7 +29,7 @@ class OrcParams(C.Structure):
         ("bandwidth", _D * 3), ("n_tau", _I), ("cg_rtol", _D), ("cg_max_iter", _I),
         ("shift_eps", _I), ("shift_mom", _I), ("shift_force", _I),
         ("contact_law", _I), ("kn_linear", _D), ("kt_ratio", _D), ("tau_scheme", _I),
-        ("lift", _I), ("c_lift", _D), ("lub_tangential", _I),
+        ("lift", _I), ("c_lift", _D), ("lub_tangential", _I), ("z_grading", _D),
     ]
 
 
@@ -69,6 +69,10 @@ def lib():
         L.orc_drag.restype = None
         L.orc_vr.argtypes = [_D, _D]
         L.orc_vr.restype = _D
+        L.orc_z_faces.argtypes = [C.POINTER(OrcParams), _P]
+        L.orc_z_faces.restype = None
+        L.orc_smooth_operator.argtypes = [C.POINTER(OrcParams), _P, _P]
+        L.orc_smooth_operator.restype = None
         L.orc_curl.argtypes = [C.POINTER(OrcParams), _P, _P]
         L.orc_curl.restype = None
         L.orc_lift.argtypes = [C.POINTER(OrcParams), _P, _P, _D, _P]
@@ -94,7 +98,7 @@ def make_params(prm: dict) -> OrcParams:
     p = OrcParams()
     # the contact law defaults to Hertz-Mindlin (the linear law's inputs then unused)
     optional = {"contact_law": 0, "kn_linear": 800.0, "kt_ratio": 2.0 / 7.0, "tau_scheme": 0,
-                "lift": 0, "c_lift": 1.6, "lub_tangential": 0}
+                "lift": 0, "c_lift": 1.6, "lub_tangential": 0, "z_grading": 1.0}
     for name, ctype in OrcParams._fields_:
         if name not in prm and name not in optional:
             raise KeyError(f"oracle parameter {name!r} missing")
@@ -225,6 +229,23 @@ def drag(prm: dict, eps_s, w, d):
 
 def vr(eps_f, Re):
     return lib().orc_vr(float(eps_f), float(Re))
+
+
+def z_faces(prm: dict):
+    """Faces of the oracle's z mesh (n_z + 1 values)."""
+    p = make_params(prm)
+    out = np.zeros(prm["ncell"][2] + 1)
+    lib().orc_z_faces(C.byref(p), _ptr(out))
+    return out
+
+
+def smooth_operator(prm: dict, x):
+    """y = A x, the operator of one backward-Euler smoothing step, on one field [C]."""
+    p = make_params(prm)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros_like(x)
+    lib().orc_smooth_operator(C.byref(p), _ptr(x), _ptr(y))
+    return y
 
 
 def curl(prm: dict, U):

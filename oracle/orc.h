@@ -63,6 +63,9 @@ typedef struct {
   int32_t lift;
   double c_lift;
   int32_t lub_tangential;
+  /* graded mesh along z (Sec. 3.2: refined towards the bottom): ratio of the top
+     cell's height to the bottom cell's; 1 = uniform */
+  double z_grading;
 } orc_params;
 
 typedef struct orc_handle orc_handle;
@@ -115,6 +118,10 @@ int orc_average(orc_handle* h, double* eps, double* Us, double* Ffp);
 void orc_drag(const orc_params* p, double eps_s, const double w[3], double d,
               double out_f[3], double* Vr, double* Cd_times_w);
 double orc_vr(double eps_f, double Re);
+/* Faces of the z mesh (n_z + 1 values). */
+void orc_z_faces(const orc_params* p, double* faces);
+/* y = (I - dtau div(D grad)) x on one field (the operator of a smoothing step). */
+void orc_smooth_operator(const orc_params* p, const double* x, double* y);
 /* Vorticity curl U of a cell-centred field U (C*3) into omega (C*3). */
 void orc_curl(const orc_params* p, const double* U, double* omega);
 /* Lift force on a sphere of diameter d with slip w = U_f - u_p in vorticity omega. */

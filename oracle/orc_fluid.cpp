@@ -4,7 +4,8 @@
  * Interpolation (Sec. 2.3 says only that U_f is "interpolated to the center of
  * particle i"; Sec. 2.2 says fluid fields are not smoothed before use).  Reading:
  * trilinear interpolation of the cell-centred fields; periodic axes wrap, other
- * axes clamp to the first/last cell centre.
+ * axes clamp to the first/last cell centre.  On a graded z mesh (Sec. 3.2) the z
+ * weight is the linear one between the two enclosing cell centres.
  *
  * Drag, Eq. (3)-(6), the Syamlal-O'Brien correlation of the MFIX documentation.
  * Readings of the garbled print:
@@ -31,12 +32,40 @@
  * where omega = 0.  omega is the trilinear interpolant of the cell-centred vorticity
  * of U_f (the paper takes grad U_f from the fluid solver): second-order central
  * differences, wrapped on periodic axes, one-sided in the first and last cell of
- * other axes, zero along an axis of one cell.  The lift is part of f_fp, so the
+ * other axes, zero along an axis of one cell; on a graded z mesh the z differences
+ * divide by the distance between the centres used.  The lift is part of f_fp, so the
  * fluid also receives it through the deposition.
  */
+#include <algorithm>
+
 #include "orc_internal.h"
 
 namespace orc {
+
+ZGrid zgrid(const orc_params& p) {
+  ZGrid g;
+  const int64_t n = p.ncell[2];
+  const double L = p.hi[2] - p.lo[2];
+  g.graded = p.z_grading != 1.0 && n >= 2;
+  g.zf.resize(n + 1);
+  for (int64_t k = 0; k <= n; ++k) {
+    if (g.graded) {
+      const double lr = std::log(p.z_grading) / (double)(n - 1);  /* ln r */
+      g.zf[k] = p.lo[2] + L * (std::expm1((double)k * lr) / std::expm1((double)n * lr));
+    } else {
+      g.zf[k] = p.lo[2] + L * (double)k / (double)n;
+    }
+  }
+  g.zf[0] = p.lo[2];
+  g.zf[n] = p.hi[2];
+  g.zc.resize(n);
+  g.hz.resize(n);
+  for (int64_t k = 0; k < n; ++k) {
+    g.zc[k] = 0.5 * (g.zf[k] + g.zf[k + 1]);
+    g.hz[k] = g.zf[k + 1] - g.zf[k];
+  }
+  return g;
+}
 
 namespace {
 
@@ -47,6 +76,26 @@ struct Axis {
 
 Axis axis_weights(const orc_params& p, int a, double x) {
   int n = p.ncell[a];
+  if (a == 2 && p.z_grading != 1.0 && n >= 2) {
+    /* graded z: linear weight between the enclosing centres, clamped outside */
+    const ZGrid g = zgrid(p);
+    Axis ax;
+    if (!(x > g.zc[0])) {
+      ax.i0 = 0;
+      ax.i1 = 1;
+      ax.f = 0.0;
+    } else if (!(x < g.zc[n - 1])) {
+      ax.i0 = n - 2;
+      ax.i1 = n - 1;
+      ax.f = 1.0;
+    } else {
+      int64_t k = (int64_t)(std::upper_bound(g.zc.begin(), g.zc.end(), x) - g.zc.begin()) - 1;
+      ax.i0 = k;
+      ax.i1 = k + 1;
+      ax.f = (x - g.zc[k]) / (g.zc[k + 1] - g.zc[k]);
+    }
+    return ax;
+  }
   double inv = (double)n / (p.hi[a] - p.lo[a]);
   double s = (x - p.lo[a]) * inv - 0.5;
   Axis ax;
@@ -125,6 +174,7 @@ void curl_cells(const orc_params& p, const std::vector<double>& U, std::vector<d
   const int64_t n[3] = {p.ncell[0], p.ncell[1], p.ncell[2]};
   const int64_t C = n[0] * n[1] * n[2];
   out.assign(3 * C, 0.0);
+  const ZGrid zg = zgrid(p);
   for (int64_t iz = 0; iz < n[2]; ++iz)
     for (int64_t iy = 0; iy < n[1]; ++iy)
       for (int64_t ix = 0; ix < n[0]; ++ix) {
@@ -151,6 +201,7 @@ void curl_cells(const orc_params& p, const std::vector<double>& U, std::vector<d
             im[a] = idx[a] - 1;
             den = 2.0 * h;
           }
+          if (a == 2 && zg.graded) den = zg.zc[ip[2]] - zg.zc[im[2]];
           const int64_t cp = (ip[2] * n[1] + ip[1]) * n[0] + ip[0];
           const int64_t cm = (im[2] * n[1] + im[1]) * n[0] + im[0];
           for (int b = 0; b < 3; ++b) g[a][b] = (U[3 * cp + b] - U[3 * cm + b]) / den;

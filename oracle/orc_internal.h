@@ -66,6 +66,17 @@ struct FluidFields {
   const std::vector<double>* eps;   /* C */
   const std::vector<double>* curlU; /* C*3, vorticity of U */
 };
+/* The z mesh.  Uniform unless z_grading != 1: then cell heights grow geometrically
+   from the floor, h_k = h_0 r^k, r = z_grading^(1/(n_z - 1)) (z_grading is the ratio
+   of the top cell's height to the bottom cell's), faces
+   z_k = lo + L (r^k - 1) / (r^n - 1), written with expm1 so a ratio near 1 keeps
+   its accuracy. */
+struct ZGrid {
+  bool graded;
+  std::vector<double> zf, zc, hz; /* faces (n + 1), centres, heights (n) */
+};
+ZGrid zgrid(const orc_params& p);
+
 /* Vorticity of a cell-centred velocity field (C*3 in, C*3 out). */
 void curl_cells(const orc_params& p, const std::vector<double>& U, std::vector<double>& out);
 V3 lift_force(const orc_params& p, V3 w, V3 omega, double d);

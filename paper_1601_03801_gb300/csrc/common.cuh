@@ -63,6 +63,7 @@ struct DevParams {
   int32_t periodic[3], wall_lo[3], wall_hi[3];
   int32_t lubrication, drag, pressure_grad, added_mass;
   int32_t lift, lub_tangential;
+  int32_t graded;                  // graded z mesh (tables in DevMesh)
   ForceConsts<float> cf;
   ForceConsts<double> cd;
   BoxS<float> bf;
@@ -263,11 +264,16 @@ struct DevState {
 
 // Mesh arrays (type-erased Quad<F>): ufe = (Ux, Uy, Uz, eps_s), gfl = G where
 // the pressure-gradient + fluid-acceleration part of f_fp is V_p * G, wfl =
-// (curl U, 0) for the lift force.
+// (curl U, 0) for the lift force.  Graded z mesh only (null otherwise): faces
+// zf [nz + 1], centres zc [nz] (FP64) and zcf (FP32), cell volumes vcz [nz].
 struct DevMesh {
   void* ufe;
   void* gfl;
   void* wfl;
+  const double* zf;
+  const double* zc;
+  const float* zcf;
+  const double* vcz;
   int64_t C;
 };
 

@@ -39,6 +39,7 @@ struct sedi_handle {
   DevMesh mesh{};
   std::vector<void*> part_allocs;  // per-particle buffers
   std::vector<void*> mesh_allocs;
+  SmoothZ zs{};                        // graded z mesh: smoothing tables (device) and bounds
   void* qfix = nullptr;   // [7][C] int64 (plain: float phi)
   void* phi = nullptr;    // [8][C] smoothing word
   void* work = nullptr;
@@ -221,6 +222,7 @@ void fill_params(sedi_handle* h) {
   P.added_mass = p.added_mass ? 1 : 0;
   P.lift = p.lift ? 1 : 0;
   P.lub_tangential = (p.lubrication && p.lub_tangential) ? 1 : 0;
+  P.graded = p.z_grading != 1.0 ? 1 : 0;
   fill_consts<float>(p, P.cf);
   fill_consts<double>(p, P.cd);
   P.C = (int64_t)p.ncell[0] * p.ncell[1] * p.ncell[2];
@@ -256,6 +258,9 @@ int check_params(sedi_handle* h, const sedi_params& p) {
   if (!(p.restitution > 0 && p.restitution <= 1)) return fail(h, SEDI_EINVAL, "restitution must be in (0, 1]");
   if (!(p.friction >= 0)) return fail(h, SEDI_EINVAL, "friction must be >= 0");
   if (!(p.c_lift >= 0)) return fail(h, SEDI_EINVAL, "c_lift must be >= 0");
+  if (!(p.z_grading > 0) || !std::isfinite(p.z_grading)) return fail(h, SEDI_EINVAL, "z_grading must be > 0");
+  if (p.z_grading != 1.0 && (p.periodic[2] || p.ncell[2] < 2))
+    return fail(h, SEDI_EINVAL, "a graded z mesh needs a non-periodic z axis with ncell[2] >= 2");
   if (!(p.rho_f > 0) || !(p.nu_f > 0)) return fail(h, SEDI_EINVAL, "rho_f, nu_f must be > 0");
   if (!(p.dt > 0) || !(p.skin >= 0)) return fail(h, SEDI_EINVAL, "dt > 0 and skin >= 0 required");
   for (int a = 0; a < 3; ++a) {
@@ -317,6 +322,84 @@ int sync_status(sedi_handle* h) {
   return 0;
 }
 
+// Graded z mesh (Sec. 3.2): cell heights h_k = h_0 r^k from the floor,
+// r = z_grading^(1/(nz - 1)), faces z_k = lo + L (r^k - 1) / (r^nz - 1) (expm1 keeps a
+// ratio near 1 accurate); centres, cell volumes h_x h_y h_k, and per plane the
+// finite-volume z-face coefficients of one smoothing step,
+// c-_k = dtau D_z / (h_k (zc_k - zc_{k-1})), c+_k = dtau D_z / (h_k (zc_{k+1} - zc_k))
+// (0 at the floor and lid), times 2/3 for BDF2 steps; plane weights h_k / mean h.
+// One device buffer; nothing on a uniform mesh.
+int build_zgrid(sedi_handle* h) {
+  const sedi_params& p = h->prm;
+  if (!h->P.graded) return 0;
+  const int64_t n = p.ncell[2], nxy = (int64_t)p.ncell[0] * p.ncell[1];
+  const double L = p.hi[2] - p.lo[2];
+  const double lr = std::log(p.z_grading) / (double)(n - 1);
+  std::vector<double> zf(n + 1), zc(n), hz(n);
+  for (int64_t k = 0; k <= n; ++k) zf[k] = p.lo[2] + L * (std::expm1((double)k * lr) / std::expm1((double)n * lr));
+  zf[0] = p.lo[2];
+  zf[n] = p.hi[2];
+  for (int64_t k = 0; k < n; ++k) {
+    zc[k] = 0.5 * (zf[k] + zf[k + 1]);
+    hz[k] = zf[k + 1] - zf[k];
+  }
+  const double dx = (p.hi[0] - p.lo[0]) / p.ncell[0], dy = (p.hi[1] - p.lo[1]) / p.ncell[1];
+  const double dtau = 1.0 / p.n_tau, Dz = 0.25 * p.bandwidth[2] * p.bandwidth[2], hmean = L / (double)n;
+  // doubles: zf, zc, vc, cz[0], cz[1], w; floats: zcf, czf[0], czf[1]
+  const size_t nd = (n + 1) + n + n + 2 * n + 2 * n + n, nfl = n + 2 * n + 2 * n;
+  std::vector<double> dv(nd, 0.0);
+  std::vector<float> fv(nfl, 0.0f);
+  double* d_zf = dv.data();
+  double* d_zc = d_zf + (n + 1);
+  double* d_vc = d_zc + n;
+  double* d_cz0 = d_vc + n;
+  double* d_cz1 = d_cz0 + 2 * n;
+  double* d_w = d_cz1 + 2 * n;
+  float* f_zc = fv.data();
+  float* f_cz0 = f_zc + n;
+  float* f_cz1 = f_cz0 + 2 * n;
+  double zmax[2] = {0.0, 0.0}, wsum = 0.0;
+  for (int64_t k = 0; k <= n; ++k) d_zf[k] = zf[k];
+  for (int64_t k = 0; k < n; ++k) {
+    d_zc[k] = zc[k];
+    f_zc[k] = (float)zc[k];
+    d_vc[k] = dx * dy * hz[k];
+    d_w[k] = hz[k] / hmean;
+    wsum += d_w[k] * (double)nxy;
+    for (int s = 0; s < 2; ++s) {
+      const double scale = s == 0 ? 1.0 : 2.0 / 3.0;
+      double* cz = s == 0 ? d_cz0 : d_cz1;
+      float* czf = s == 0 ? f_cz0 : f_cz1;
+      cz[2 * k] = k > 0 ? scale * dtau * Dz / (hz[k] * (zc[k] - zc[k - 1])) : 0.0;
+      cz[2 * k + 1] = k < n - 1 ? scale * dtau * Dz / (hz[k] * (zc[k + 1] - zc[k])) : 0.0;
+      czf[2 * k] = (float)cz[2 * k];
+      czf[2 * k + 1] = (float)cz[2 * k + 1];
+      zmax[s] = std::max(zmax[s], cz[2 * k] + cz[2 * k + 1]);
+    }
+  }
+  void* buf = nullptr;
+  const size_t dbytes = (nd * 8 + 255) & ~(size_t)255;
+  int rc = dmalloc(h, h->mesh_allocs, &buf, dbytes + nfl * 4);
+  if (rc) return rc;
+  CK(cudaMemcpy(buf, dv.data(), nd * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy((char*)buf + dbytes, fv.data(), nfl * 4, cudaMemcpyHostToDevice));
+  const double* bd = (const double*)buf;
+  const float* bf = (const float*)((char*)buf + dbytes);
+  h->mesh.zf = bd;
+  h->mesh.zc = bd + (n + 1);
+  h->mesh.vcz = bd + (n + 1) + n;
+  h->mesh.zcf = bf;
+  h->zs.cz[0] = bd + (n + 1) + 2 * n;
+  h->zs.cz[1] = bd + (n + 1) + 4 * n;
+  h->zs.w = bd + (n + 1) + 6 * n;
+  h->zs.czf[0] = bf + n;
+  h->zs.czf[1] = bf + 3 * n;
+  h->zs.wsum = wsum;
+  h->zs.zmax[0] = zmax[0];
+  h->zs.zmax[1] = zmax[1];
+  return 0;
+}
+
 int upload_mesh(sedi_handle* h, bool velocity = true) {
   const int64_t C = h->P.C;
   const int form = h->form;
@@ -353,7 +436,7 @@ int upload_mesh(sedi_handle* h, bool velocity = true) {
   CK(cudaMalloc((void**)&Ud, 24 * C));
   cudaError_t e = cudaMemcpyAsync(Ud, h->U.data(), 24 * C, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) {
-    launch_curl(form, Ud, h->P, h->mesh.wfl, h->stream);
+    launch_curl(form, Ud, h->P, h->mesh, h->stream);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -670,6 +753,7 @@ void sedi_default_params(sedi_params* p) {
   p->lub_h_out_frac = 0.1;
   p->c_add = 0.5;
   p->c_lift = 1.6;
+  p->z_grading = 1.0;
   p->eps_max = 0.9;
   p->ncell[0] = 10;
   p->ncell[1] = 10;
@@ -726,6 +810,10 @@ int sedi_create(const sedi_params* p, sedi_handle** out) {
       (rc = dmalloc(h, h->mesh_allocs, &h->qfix, 8 * 7 * C)) ||
       (rc = dmalloc(h, h->mesh_allocs, &h->phi, 8 * 8 * C)) ||
       (rc = dmalloc(h, h->mesh_allocs, (void**)&h->iters_dev, 4 * 8))) {
+    sedi_destroy(h);
+    return rc;
+  }
+  if ((rc = build_zgrid(h))) {
     sedi_destroy(h);
     return rc;
   }
@@ -1023,7 +1111,7 @@ static int smooth_dev(sedi_handle* h, int nf, const void* guess, int n_tau = -1,
   const double rtol = h->form == FORM_PLAIN ? std::max(h->prm.cg_rtol, 2e-6) : h->prm.cg_rtol;
   int rc = launch_smooth(h->form, h->P, h->phi, guess, nf, h->work, h->st, h->iters_dev,
                          rtol, h->prm.cg_max_iter, n_tau > 0 ? n_tau : h->prm.n_tau,
-                         h->prm.tau_scheme, h->coef,
+                         h->prm.tau_scheme, h->coef, h->P.graded ? &h->zs : nullptr,
                          h->stream);
   if (rc) return fail(h, SEDI_ECUDA, "cooperative launch of the smoother failed: %s", cudaGetErrorString(cudaGetLastError()));
   return 0;
@@ -1266,6 +1354,7 @@ static int ens_average(sedi_handle* h) {
       x.per[a] = sb->P.periodic[a];
       x.coef[a] = sb->coef[a];
     }
+    x.z = sb->zs;
   }
   CK(cudaMemsetAsync(h->ens_iters, 0, sizeof(int) * 8 * B, h->stream));
   const double rtol = h->form == FORM_PLAIN ? std::max(h->prm.cg_rtol, 2e-6) : h->prm.cg_rtol;

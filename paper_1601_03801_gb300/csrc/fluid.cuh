@@ -37,16 +37,47 @@ __device__ __forceinline__ void axis_w(F s, int n, int per, int* i0, int* i1, F*
 // one interpolation, and the cell vorticity omega = curl U_f for the lift.  Drag is
 // written in a form without 1/Re:
 //   C_d |w| = (0.63 sqrt|w| + 4.8 sqrt(V_r nu / d))^2.
+// z centres of a graded mesh in the force word
+template <class F>
+__device__ __forceinline__ const F* zcent(const DevMesh& m);
+template <>
+__device__ __forceinline__ const float* zcent<float>(const DevMesh& m) {
+  return m.zcf;
+}
+template <>
+__device__ __forceinline__ const double* zcent<double>(const DevMesh& m) {
+  return m.zc;
+}
+
 template <class S, class F, bool LIFT = true>
 __device__ __forceinline__ void fluid_force(const DevParams& P, const ForceConsts<F>& K,
                                             const Quad<F>* ufe, const Quad<F>* gfl,
-                                            const Quad<F>* wfl, const S* x, F r, const F v[3],
-                                            const F a_prev[3], F out[3]) {
+                                            const Quad<F>* wfl, const F* zc, const S* x, F r,
+                                            const F v[3], const F a_prev[3], F out[3]) {
   using NS = Num<S>;
   const BoxS<S>& B = sbox<S>(P);
   int i0[3], i1[3];
   F fr[3];
   for (int a = 0; a < 3; ++a) {
+    if (a == 2 && P.graded) {
+      // graded z: linear weight between the enclosing cell centres, clamped outside
+      const F z = NS::f(x[2]);
+      const int n = P.nc[2];
+      if (!(z > zc[0])) {
+        i0[2] = 0, i1[2] = 1, fr[2] = F(0);
+      } else if (!(z < zc[n - 1])) {
+        i0[2] = n - 2, i1[2] = n - 1, fr[2] = F(1);
+      } else {
+        int lo = 0, hi = n - 1;  // zc[lo] < z < zc[hi]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (zc[mid] <= z) lo = mid;
+          else hi = mid;
+        }
+        i0[2] = lo, i1[2] = lo + 1, fr[2] = (z - zc[lo]) / (zc[lo + 1] - zc[lo]);
+      }
+      continue;
+    }
     F rel = NS::f(NS::sub(x[a], B.lo[a]));
     F s = rel * K.inv_h[a] - F(0.5);
     axis_w<F>(s, P.nc[a], P.periodic[a], &i0[a], &i1[a], &fr[a]);

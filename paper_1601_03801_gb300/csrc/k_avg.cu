@@ -46,6 +46,18 @@ __device__ __forceinline__ void deposit_body(const DevState& st, const DevMesh& 
     int64_t cc[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
+      if (a == 2 && P.graded) {
+        // graded z: the cell whose FP64 faces enclose z (the last face <= z)
+        const double z = NS::d(xs[2]);
+        int lo = 0, hi = P.nc[2];  // faces zf[lo] <= z < zf[hi] once clamped
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (mesh.zf[mid] <= z) lo = mid;
+          else hi = mid;
+        }
+        cc[2] = lo;
+        continue;
+      }
       // the cell must equal floor((x - lo) * n / L) in FP64; FP32 decides unless x
       // lies within ~1e-4 of a cell face, where the FP64 product is formed
       int64_t k;
@@ -67,13 +79,15 @@ __device__ __forceinline__ void deposit_body(const DevState& st, const DevMesh& 
     const F ap[3] = {acc.a, acc.b, acc.c};
     F ff[3];
     fluid_force<S, F>(P, K, (const Quad<F>*)mesh.ufe, (const Quad<F>*)mesh.gfl,
-                      (const Quad<F>*)mesh.wfl, xs, NS::f(p.d), vf,
+                      (const Quad<F>*)mesh.wfl, zcent<F>(mesh), xs, NS::f(p.d), vf,
                       ap, ff);
-    const double vfrac = st.vfrac[pb][i];
+    // graded mesh: the stored value is V_p, divided here by the volume of the cell
+    const double vfrac = P.graded ? __ddiv_rn(st.vfrac[pb][i], mesh.vcz[cc[2]]) : st.vfrac[pb][i];
     if (FORM == FORM_PLAIN) {
       float* q = (float*)qout;
       const float vf32 = (float)vfrac;
-      const float inv_vc = P.cf.inv_h[0] * P.cf.inv_h[1] * P.cf.inv_h[2];
+      const float inv_vc = P.graded ? (float)(1.0 / mesh.vcz[cc[2]])
+                                    : P.cf.inv_h[0] * P.cf.inv_h[1] * P.cf.inv_h[2];
       atomicAdd(q + cell, vf32);
       atomicAdd(q + 1 * C + cell, vf32 * vf[0]);
       atomicAdd(q + 2 * C + cell, vf32 * vf[1]);
@@ -104,11 +118,13 @@ __device__ __forceinline__ void deposit_body(const DevState& st, const DevMesh& 
         long long qi;
         bool ok;
         if (FORM == FORM_FP64) {
-          const double t = __dmul_rn(__ddiv_rn(-(double)ff[a], P.vc), P.two_shift[2]);
+          const double t = __dmul_rn(__ddiv_rn(-(double)ff[a], P.graded ? mesh.vcz[cc[2]] : P.vc),
+                                     P.two_shift[2]);
           ok = fabs(t) < 4.0e18;
           qi = ok ? __double2ll_rn(t) : 0;
         } else {
-          const float t = -(float)ff[a] * P.inv_vc_f * P.two_shift_f;
+          const float inv_vc = P.graded ? (float)(1.0 / mesh.vcz[cc[2]]) : P.inv_vc_f;
+          const float t = -(float)ff[a] * inv_vc * P.two_shift_f;
           ok = fabsf(t) < 4.0e18f;
           qi = ok ? __float2ll_rn(t) : 0;
         }
@@ -286,9 +302,11 @@ __global__ void k_eps_out_e(const BedView* v) {
 // Cell vorticity omega = curl U of the cell-centred fluid velocity U (FP64, C x 3),
 // for the lift force (Sec. 2.3, Eq. 7): central differences, wrapped on periodic
 // axes, one-sided in the first and last cell of other axes, zero along an axis of
-// one cell; stored as (omega, 0) in the form's word.
+// one cell (on a graded z mesh the z differences divide by the distance between
+// the centres used); stored as (omega, 0) in the form's word.
 template <class F>
-__global__ void k_curl(const double* __restrict__ U, DevParams P, Quad<F>* __restrict__ wfl) {
+__global__ void k_curl(const double* __restrict__ U, DevParams P, const double* __restrict__ zc,
+                       Quad<F>* __restrict__ wfl) {
   const int64_t nx = P.nc[0], ny = P.nc[1], nz = P.nc[2];
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < P.C;
        c += (int64_t)gridDim.x * blockDim.x) {
@@ -315,6 +333,7 @@ __global__ void k_curl(const double* __restrict__ U, DevParams P, Quad<F>* __res
         im[a] = idx[a] - 1;
         den = 2.0 * h;
       }
+      if (a == 2 && P.graded) den = zc[ip[2]] - zc[im[2]];
       const int64_t cp = (ip[2] * ny + ip[1]) * nx + ip[0];
       const int64_t cm = (im[2] * ny + im[1]) * nx + im[0];
       for (int b = 0; b < 3; ++b) g[a][b] = (U[3 * cp + b] - U[3 * cm + b]) / den;
@@ -342,10 +361,11 @@ void launch_deposit(int form, const DevState& st, const DevMesh& mesh, const Dev
   }
 }
 
-void launch_curl(int form, const double* U, const DevParams& P, void* wfl, cudaStream_t s) {
+void launch_curl(int form, const double* U, const DevParams& P, const DevMesh& mesh,
+                 cudaStream_t s) {
   const unsigned g = grid_for(P.C, 256);
-  if (form == FORM_FP64) k_curl<double><<<g, 256, 0, s>>>(U, P, (Quad<double>*)wfl);
-  else k_curl<float><<<g, 256, 0, s>>>(U, P, (Quad<float>*)wfl);
+  if (form == FORM_FP64) k_curl<double><<<g, 256, 0, s>>>(U, P, mesh.zc, (Quad<double>*)mesh.wfl);
+  else k_curl<float><<<g, 256, 0, s>>>(U, P, mesh.zc, (Quad<float>*)mesh.wfl);
 }
 
 void launch_fields_from_fixed(int form, const void* q, const DevParams& P, void* phi, int nf,
@@ -511,6 +531,10 @@ extern "C" int sedi_smooth_static(const sedi_params* p, int32_t nf, const double
   unsigned char* work = base + W;  // solver scratch
   int* iters_dev = (int*)(base + W + kStaticWork);
   Ctl* ctl = (Ctl*)(base + W + kStaticWork + 256);
+  if (p->z_grading != 1.0) {
+    put_msg(msg, msg_len, "sedi_smooth_static: a graded z mesh needs a handle (sedi_smooth)");
+    return SEDI_EINVAL;
+  }
   if (smooth_work_bytes(p->precision_form, C, nf, p->tau_scheme) > (size_t)kStaticWork) {
     put_msg(msg, msg_len, "sedi_smooth_static: internal scratch bound exceeded");
     return SEDI_EINVAL;
@@ -539,7 +563,7 @@ extern "C" int sedi_smooth_static(const sedi_params* p, int32_t nf, const double
   const int64_t n = (int64_t)nf * C;
   launch_phi_from_double(form, in, phi, n, s);
   const int rc = launch_smooth(form, P, phi, nullptr, nf, work, st, iters_dev, rtol,
-                               p->cg_max_iter, p->n_tau, p->tau_scheme, coef, s);
+                               p->cg_max_iter, p->n_tau, p->tau_scheme, coef, nullptr, s);
   if (rc) {
     put_msg(msg, msg_len, "sedi_smooth_static: cooperative launch of the smoother failed");
     return SEDI_ECUDA;

@@ -721,10 +721,12 @@ void launch_import(int form, const DevState& st, const double* x, const double* 
                    const double* d, const double* rho, const DevParams& P, cudaStream_t s) {
   const double pi6 = 3.14159265358979323846 / 6.0;
   unsigned g = grid_for(st.N, 256);
+  // a graded mesh keeps V_p itself (the deposition divides by the cell's volume)
+  const double vc = P.graded ? 1.0 : P.vc;
   switch (form) {
-    case FORM_SPLIT: k_import<FORM_SPLIT><<<g, 256, 0, s>>>(st, x, v, w, d, rho, pi6, P.vc); break;
-    case FORM_PLAIN: k_import<FORM_PLAIN><<<g, 256, 0, s>>>(st, x, v, w, d, rho, pi6, P.vc); break;
-    default: k_import<FORM_FP64><<<g, 256, 0, s>>>(st, x, v, w, d, rho, pi6, P.vc); break;
+    case FORM_SPLIT: k_import<FORM_SPLIT><<<g, 256, 0, s>>>(st, x, v, w, d, rho, pi6, vc); break;
+    case FORM_PLAIN: k_import<FORM_PLAIN><<<g, 256, 0, s>>>(st, x, v, w, d, rho, pi6, vc); break;
+    default: k_import<FORM_FP64><<<g, 256, 0, s>>>(st, x, v, w, d, rho, pi6, vc); break;
   }
 }
 

@@ -486,7 +486,7 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
     F ff[3];
     const F ap[3] = {Ai.a, Ai.b, Ai.c};
     fluid_force<S, F, EXT>(P, K, (const Quad<F>*)mesh.ufe, (const Quad<F>*)mesh.gfl,
-                           (const Quad<F>*)mesh.wfl, xi_s, ri, vi, ap, ff);
+                           (const Quad<F>*)mesh.wfl, zcent<F>(mesh), xi_s, ri, vi, ap, ff);
     if (!INTEGRATE) {
       double* o = st.fdbg;
       o[3 * i + 0] = (double)fc.x; o[3 * i + 1] = (double)fc.y; o[3 * i + 2] = (double)fc.z;

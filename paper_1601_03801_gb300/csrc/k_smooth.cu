@@ -53,7 +53,7 @@ namespace {
 
 constexpr int kThreads = 256;  // threads per block = cells per work unit
 constexpr int kMaxF = 8;
-constexpr int kQ = 3;          // per-unit sums: |r|^2, sum r, |b|^2
+constexpr int kQ = 4;          // per-unit sums: |r|^2, sum r, |b|^2, sum w r (graded mesh)
 constexpr int kMaxRounds = 64;
 
 // ---------------------------------------------------------------- words
@@ -199,6 +199,42 @@ __device__ __forceinline__ V apply_A(const Stencil& st, const V* cf, V vc, Sub s
   return any_axis ? sub(vc, lap) : vc;
 }
 
+// Graded z mesh: as apply_A, the z faces with their own coefficients (cz_m towards
+// the plane below, cz_p towards the plane above).
+template <class V, class Sub, class Add, class Mul, class Get>
+__device__ __forceinline__ V apply_A_graded(const Stencil& st, const V* cf, V czm, V czp, V vc,
+                                            Sub sub, Add add, Mul mul, Get get) {
+  V lap{};
+  bool any_axis = false;
+#pragma unroll
+  for (int ax = 0; ax < 2; ++ax) {
+    V sa{};
+    bool any = false;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int32_t nb = st.nb[2 * ax + side];
+      if (nb < 0) continue;
+      const V t = sub(get(nb), vc);
+      sa = any ? add(sa, t) : t;
+      any = true;
+    }
+    if (any) {
+      const V t = mul(cf[ax], sa);
+      lap = any_axis ? add(lap, t) : t;
+      any_axis = true;
+    }
+  }
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const int32_t nb = st.nb[4 + side];
+    if (nb < 0) continue;
+    const V t = mul(side ? czp : czm, sub(get(nb), vc));
+    lap = any_axis ? add(lap, t) : t;
+    any_axis = true;
+  }
+  return any_axis ? sub(vc, lap) : vc;
+}
+
 // Eight narrow words of one cell (the fields of the narrow recursion are stored
 // interleaved, [C][8], so one cell's fields load as two 16-byte vectors).
 template <class N>
@@ -277,7 +313,8 @@ __device__ __forceinline__ T rhs_of(int scheme, int m, T xv, T* xp) {
   return bv;
 }
 
-template <class T>
+// GR: graded z mesh (per-plane z coefficients, volume-weighted projection shift).
+template <class T, bool GR>
 __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
   using W = Wide<T>;
   using N = typename W::N;
@@ -321,23 +358,35 @@ __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
         const SmoothSpec& sp = md.sp[ph];
         const T cf[3] = {W::from_d(sp.coef[0]), W::from_d(sp.coef[1]), W::from_d(sp.coef[2])};
         const Stencil sc = stencil_of(md, in ? c : 0);
+        T czm{}, czp{};
+        Acc wz = Acc(1);
+        if constexpr (GR) {
+          const int kz = (int)((uint32_t)(in ? c : 0) / (uint32_t)(md.nc[0] * md.nc[1]));
+          czm = W::from_d(md.z.cz[ph][2 * kz]);
+          czp = W::from_d(md.z.cz[ph][2 * kz + 1]);
+          wz = (Acc)md.z.w[kz];
+        }
 #pragma unroll
         for (int f = 0; f < kMaxF; ++f) {
-          v[f][0] = v[f][1] = v[f][2] = Acc(0);
+          v[f][0] = v[f][1] = v[f][2] = v[f][3] = Acc(0);
           rn.v[f] = N(0);
           if (f >= nf || !in || (round > 0 && ldi(&st.done[f]))) continue;
           const T* X = (const T*)md.x + f * md.C;
           const T xc = W::ld(X + c);
-          const T ax = apply_A<T>(sc, cf, xc, [](T p, T q) { return W::subq(p, q); },
-                                  [](T p, T q) { return W::addq(p, q); },
-                                  [](T p, T q) { return W::mul(p, q); },
-                                  [&](int32_t k) { return W::ld(X + k); });
+          auto subq = [](T p, T q) { return W::subq(p, q); };
+          auto addq = [](T p, T q) { return W::addq(p, q); };
+          auto mul = [](T p, T q) { return W::mul(p, q); };
+          auto get = [&](int32_t k) { return W::ld(X + k); };
+          T ax;
+          if constexpr (GR) ax = apply_A_graded<T>(sc, cf, czm, czp, xc, subq, addq, mul, get);
+          else ax = apply_A<T>(sc, cf, xc, subq, addq, mul, get);
           const T bv = W::ld((const T*)md.b + f * md.C + c);
           const T rv = W::subq(bv, ax);
           const N r_n = W::narrow(rv);
           rn.v[f] = r_n;
           v[f][0] = (Acc)r_n * (Acc)r_n;
           v[f][1] = (Acc)r_n;
+          if constexpr (GR) v[f][3] = wz * (Acc)r_n;
           if (round == 0) {
             const Acc bn = (Acc)W::narrow(bv);
             v[f][2] = bn * bn;
@@ -377,8 +426,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
               if (zero) {
                 done = 1;
               } else {
-                shift = sr / Cd;
-                const double rrp = fmax(rr - sr * sr / Cd, 0.0);
+                double rrp;
+                if (GR) {
+                  // the shift keeps sum(w x) = sum(w b); |r - s|^2 = |r|^2 - 2 s sum r + C s^2
+                  shift = s_sums[f * kQ + 3] / md.z.wsum;
+                  rrp = fmax(rr - 2.0 * shift * sr + Cd * shift * shift, 0.0);
+                } else {
+                  shift = sr / Cd;
+                  rrp = fmax(rr - sr * sr / Cd, 0.0);
+                }
                 if (rrp <= a.rtol2 * bb) {
                   done = 1;
                 } else {
@@ -474,8 +530,35 @@ __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
           const V8<N> dc = dir(ld8(Dold + c * kMaxF));
           V8<N> lap;
           bool any_axis = false;
+          N czn[2] = {N(0), N(0)};
+          if constexpr (GR) {
+            const int kz = (int)((uint32_t)c / (uint32_t)(md.nc[0] * md.nc[1]));
+            if constexpr (sizeof(N) == 4) {
+              czn[0] = md.z.czf[ph][2 * kz];
+              czn[1] = md.z.czf[ph][2 * kz + 1];
+            } else {
+              czn[0] = (N)md.z.cz[ph][2 * kz];
+              czn[1] = (N)md.z.cz[ph][2 * kz + 1];
+            }
+          }
 #pragma unroll
           for (int ax = 0; ax < 3; ++ax) {
+            if (GR && ax == 2) {
+              // graded z: each face with its own coefficient
+#pragma unroll
+              for (int side = 0; side < 2; ++side) {
+                const int32_t nb = sc.nb[4 + side];
+                if (nb < 0) continue;
+                const V8<N> dn = dir(ld8(Dold + (int64_t)nb * kMaxF));
+#pragma unroll
+                for (int f = 0; f < kMaxF; ++f) {
+                  const N t = czn[side] * (dn.v[f] - dc.v[f]);
+                  lap.v[f] = any_axis ? lap.v[f] + t : t;
+                }
+                any_axis = true;
+              }
+              continue;
+            }
             V8<N> sa;
             bool any_side = false;
 #pragma unroll
@@ -553,7 +636,7 @@ struct Nb {
   int32_t r;
 };
 
-template <class T>
+template <class T, bool GR>
 __global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
   using W = Wide<T>;
   using N = typename W::N;
@@ -637,7 +720,8 @@ __global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
       return c;
     };
     for (int m = 0; m < a.n_tau; ++m) {
-      const SmoothSpec& sp = md.sp[(a.scheme == TAU_BDF2 && m > 0) ? 1 : 0];
+      const int ph = (a.scheme == TAU_BDF2 && m > 0) ? 1 : 0;
+      const SmoothSpec& sp = md.sp[ph];
       const T cf[3] = {W::from_d(sp.coef[0]), W::from_d(sp.coef[1]), W::from_d(sp.coef[2])};
       const N cfn[3] = {(N)sp.coef[0], (N)sp.coef[1], (N)sp.coef[2]};
       const N inv_theta = (N)(1.0 / sp.theta);
@@ -653,7 +737,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
       double bb = 0.0;
       for (int round = 0; round < kMaxRounds; ++round) {
         // ---- true residual (wide), its narrow copy in dA, sums
-        Acc v[kQ] = {Acc(0), Acc(0), Acc(0)};
+        Acc v[kQ] = {Acc(0), Acc(0), Acc(0), Acc(0)};
         // (A x)(c) = x_c - sum_a coef_a ((x_- - x_c) + (x_+ - x_c)), faces that exist
         auto wpair = [](bool h0, T v0, bool h1, T v1, T c) {
           if (h0 && h1) return W::addq(W::subq(v0, c), W::subq(v1, c));
@@ -676,14 +760,24 @@ __global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
                                col.has[1] ? Xs[l + col.off[1]] : cur, cur);
             const T sy = wpair(col.has[2], col.has[2] ? Xs[l + col.off[2]] : cur, col.has[3],
                                col.has[3] ? Xs[l + col.off[3]] : cur, cur);
-            const T sz = wpair(hb, below, ha, above, cur);
-            const T lap = W::addq(W::addq(W::mul(cf[0], sx), W::mul(cf[1], sy)), W::mul(cf[2], sz));
+            T zt;
+            if constexpr (GR) {
+              // graded z: each face with its plane's own coefficient
+              const double* cz = md.z.cz[ph] + 2 * (z0 + izl);
+              zt = W::zero();
+              if (hb) zt = W::mul(W::from_d(cz[0]), W::subq(below, cur));
+              if (ha) zt = W::addq(zt, W::mul(W::from_d(cz[1]), W::subq(above, cur)));
+            } else {
+              zt = W::mul(cf[2], wpair(hb, below, ha, above, cur));
+            }
+            const T lap = W::addq(W::addq(W::mul(cf[0], sx), W::mul(cf[1], sy)), zt);
             const T ax = W::subq(cur, lap);
             const T bv = W::ld(Bg + c0 + l);
             const N rn = W::narrow(W::subq(bv, ax));
             dA[l] = rn;
             v[0] += (Acc)rn * (Acc)rn;
             v[1] += (Acc)rn;
+            if constexpr (GR) v[3] += (Acc)md.z.w[z0 + izl] * (Acc)rn;
             if (round == 0) {
               const Acc bn = (Acc)W::narrow(bv);
               v[2] += bn * bn;
@@ -712,7 +806,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
         // one thread of every CTA sums the parts in rank order and decides: every CTA
         // takes the same decision
         if (threadIdx.x == 0) {
-          double tot[kQ] = {0.0, 0.0, 0.0};
+          double tot[kQ] = {0.0, 0.0, 0.0, 0.0};
           for (int r = 0; r < csize; ++r)
 #pragma unroll
             for (int q = 0; q < kQ; ++q) tot[q] += s_part[r][q];
@@ -721,8 +815,15 @@ __global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
             zero = !(bb > 0.0);
           }
           const double Cd = (double)C;
-          const double shift = zero ? 0.0 : tot[1] / Cd;
-          const double rrp = fmax(tot[0] - tot[1] * tot[1] / Cd, 0.0);
+          double shift, rrp;
+          if (GR) {
+            // the shift keeps sum(w x) = sum(w b); |r - s|^2 = |r|^2 - 2 s sum r + C s^2
+            shift = zero ? 0.0 : tot[3] / md.z.wsum;
+            rrp = fmax(tot[0] - 2.0 * shift * tot[1] + Cd * shift * shift, 0.0);
+          } else {
+            shift = zero ? 0.0 : tot[1] / Cd;
+            rrp = fmax(tot[0] - tot[1] * tot[1] / Cd, 0.0);
+          }
           int k = 0;
           if (!zero && !(rrp <= a.rtol2 * bb)) {
             // the step count only has to be about right (the next round checks the true
@@ -790,8 +891,14 @@ __global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
               const N above = up ? tr(Dold[l + nxy]) : top;
               const N sx = face(col.has[0], l, col.off[0], cur) + face(col.has[1], l, col.off[1], cur);
               const N sy = face(col.has[2], l, col.off[2], cur) + face(col.has[3], l, col.off[3], cur);
-              const N sz = (hb ? below - cur : N(0)) + ((up || hl) ? above - cur : N(0));
-              const N ad = cur - ((cfn[0] * sx + cfn[1] * sy) + cfn[2] * sz);
+              N zt;
+              if constexpr (GR) {
+                const float* cz = md.z.czf[ph] + 2 * (z0 + izl);
+                zt = (hb ? (N)cz[0] * (below - cur) : N(0)) + ((up || hl) ? (N)cz[1] * (above - cur) : N(0));
+              } else {
+                zt = cfn[2] * ((hb ? below - cur : N(0)) + ((up || hl) ? above - cur : N(0)));
+              }
+              const N ad = cur - ((cfn[0] * sx + cfn[1] * sy) + zt);
               T xv = Xs[l];
               N q;
               if constexpr (FIRST) {
@@ -838,14 +945,14 @@ size_t word() {
   return sizeof(T);
 }
 
-template <class T>
+template <class T, bool GR>
 int launch_impl(const SmoothBatchDev& a, int max_blocks, cudaStream_t s) {
   int dev = 0;
   cudaGetDevice(&dev);
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smooth<T>, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smooth<T, GR>, kThreads, 0);
   if (per_sm < 1) return -3;
   if (per_sm > 2) per_sm = 2;
   int G = nsm * per_sm;
@@ -854,7 +961,7 @@ int launch_impl(const SmoothBatchDev& a, int max_blocks, cudaStream_t s) {
   k_bar_reset<<<1, 1, 0, s>>>(a.ctl);
   SmoothBatchDev args = a;
   void* p[] = {&args};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_smooth<T>, dim3(G), dim3(kThreads), p, 0, s);
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_smooth<T, GR>, dim3(G), dim3(kThreads), p, 0, s);
   return e == cudaSuccess ? 0 : -3;
 }
 
@@ -878,7 +985,7 @@ size_t smooth_work_bytes(int form, int64_t C, int nf, int scheme) {
 
 int launch_smooth(int form, const DevParams& P, void* phi, const void* guess, int nf, void* work,
                   const DevState& st, int* iters_dev, double rtol, int max_iter, int n_tau,
-                  int scheme, const double coef[3], cudaStream_t s) {
+                  int scheme, const double coef[3], const SmoothZ* z, cudaStream_t s) {
   SmoothMesh m{};
   m.phi = phi;
   m.guess = guess;
@@ -891,6 +998,7 @@ int launch_smooth(int form, const DevParams& P, void* phi, const void* guess, in
     m.per[k] = P.periodic[k];
     m.coef[k] = coef[k];
   }
+  if (z) m.z = *z;
   void* batch = (char*)work + align256(smooth_mesh_bytes(form, P.C, nf, scheme));
   return launch_smooth_batch(form, &m, 1, nf, batch, rtol, max_iter, n_tau, scheme, st.ctl,
                              1 << 30, s);
@@ -902,12 +1010,13 @@ size_t smooth_batch_bytes(int64_t B, int64_t U) {
 }
 
 // Spectrum [1, lmax] of A = I - sum_a coef_a L_a (lmax <= 1 + 4 sum_a coef_a by
-// Gershgorin) and the Chebyshev coefficients of steps 1..kMaxStepsRound (the same
-// in every round): rho_1 = 1 / sigma1, rho' = 1 / (2 sigma1 - rho), c1 = rho' rho,
-// c2 = 2 rho' / delta.
-static void smooth_spec(const double coef[3], double scale, SmoothSpec* sp) {
+// Gershgorin; on a graded z mesh the z term is 2 max_k (c-_k + c+_k), zmax > 0) and
+// the Chebyshev coefficients of steps 1..kMaxStepsRound (the same in every round):
+// rho_1 = 1 / sigma1, rho' = 1 / (2 sigma1 - rho), c1 = rho' rho, c2 = 2 rho' / delta.
+static void smooth_spec(const double coef[3], double scale, double zmax, SmoothSpec* sp) {
   for (int k = 0; k < 3; ++k) sp->coef[k] = scale * coef[k];
-  double lmax = 1.0 + 4.0 * (sp->coef[0] + sp->coef[1] + sp->coef[2]);
+  double lmax = zmax > 0.0 ? 1.0 + 4.0 * (sp->coef[0] + sp->coef[1]) + 2.0 * zmax
+                           : 1.0 + 4.0 * (sp->coef[0] + sp->coef[1] + sp->coef[2]);
   if (lmax < 1.0 + 1e-12) lmax = 1.0 + 1e-12;
   sp->theta = 0.5 * (lmax + 1.0);
   sp->delta = 0.5 * (lmax - 1.0);
@@ -950,19 +1059,22 @@ static void smooth_mesh_layout(int form, int scheme, const SmoothMesh& in, Smoot
     m.nc[k] = in.nc[k];
     m.per[k] = in.per[k];
   }
-  smooth_spec(in.coef, 1.0, &m.sp[0]);
-  smooth_spec(in.coef, scheme == TAU_BDF2 ? 2.0 / 3.0 : 1.0, &m.sp[1]);
+  m.z = in.z;
+  const bool gr = in.z.cz[0] != nullptr;
+  smooth_spec(in.coef, 1.0, gr ? in.z.zmax[0] : 0.0, &m.sp[0]);
+  smooth_spec(in.coef, scheme == TAU_BDF2 ? 2.0 / 3.0 : 1.0, gr ? in.z.zmax[scheme == TAU_BDF2 ? 1 : 0] : 0.0,
+              &m.sp[1]);
 }
 
 namespace {
 
-template <class T>
+template <class T, bool GR>
 int launch_cluster(const SmoothBatchDev& a, int csize, cudaStream_t s) {
   using N = typename Wide<T>::N;
   const size_t smem = kClSmem;
-  if (cudaFuncSetAttribute(k_smooth_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_smooth_cl<T, GR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return -3;
-  if (csize > 8 && cudaFuncSetAttribute(k_smooth_cl<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+  if (csize > 8 && cudaFuncSetAttribute(k_smooth_cl<T, GR>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
     return -3;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -977,11 +1089,11 @@ int launch_cluster(const SmoothBatchDev& a, int csize, cudaStream_t s) {
   cfg.numAttrs = 1;
   cfg.gridDim = dim3(csize * 64);
   int ncl = 0;
-  if (cudaOccupancyMaxActiveClusters(&ncl, (void*)k_smooth_cl<T>, &cfg) != cudaSuccess || ncl < 1) return -3;
+  if (cudaOccupancyMaxActiveClusters(&ncl, (void*)k_smooth_cl<T, GR>, &cfg) != cudaSuccess || ncl < 1) return -3;
   const int64_t items = (int64_t)a.B * a.nf;
   if (ncl > items) ncl = (int)items;
   cfg.gridDim = dim3(csize * ncl);
-  return cudaLaunchKernelEx(&cfg, k_smooth_cl<T>, a) == cudaSuccess ? 0 : -3;
+  return cudaLaunchKernelEx(&cfg, k_smooth_cl<T, GR>, a) == cudaSuccess ? 0 : -3;
 }
 
 // Cluster plan of a mesh (whole z-planes per CTA, <= kClCells cells each), or
@@ -1013,6 +1125,10 @@ int launch_smooth_batch(int form, const SmoothMesh* meshes, int B, int nf, void*
                         int max_blocks, cudaStream_t s) {
   if (B < 1 || B > kMaxBeds || nf < 1 || nf > kMaxF || (scheme != TAU_EULER && scheme != TAU_BDF2))
     return -1;
+  // every mesh of a batch is graded or none is (one kernel instantiation per launch)
+  const bool gr = meshes[0].z.cz[0] != nullptr;
+  for (int b = 1; b < B; ++b)
+    if ((meshes[b].z.cz[0] != nullptr) != gr) return -1;
   // meshes that fit the cluster solver take it; the rest take the grid solver.  The
   // choice depends on the mesh alone, so a bed smooths the same way in any batch.
   std::vector<SmoothMeshDev> mg, mc;
@@ -1057,8 +1173,12 @@ int launch_smooth_batch(int form, const SmoothMesh* meshes, int B, int nf, void*
       SmoothBatchDev c = a;
       c.mesh = tab_c + i0;
       c.B = (int32_t)(i1 - i0);
-      rc = form == FORM_SPLIT ? launch_cluster<dd>(c, mc[i0].cl_size, s)
-                              : launch_cluster<float>(c, mc[i0].cl_size, s);
+      if (gr)
+        rc = form == FORM_SPLIT ? launch_cluster<dd, true>(c, mc[i0].cl_size, s)
+                                : launch_cluster<float, true>(c, mc[i0].cl_size, s);
+      else
+        rc = form == FORM_SPLIT ? launch_cluster<dd, false>(c, mc[i0].cl_size, s)
+                                : launch_cluster<float, false>(c, mc[i0].cl_size, s);
       if (rc) {
         // a device without this cluster shape: these meshes take the grid solver
         cudaGetLastError();
@@ -1091,9 +1211,9 @@ int launch_smooth_batch(int form, const SmoothMesh* meshes, int B, int nf, void*
         cudaMemsetAsync(a.gflag, 0, 2 * sizeof(int32_t), s) != cudaSuccess)
       return -3;
     switch (form) {
-      case FORM_SPLIT: rc = launch_impl<dd>(a, max_blocks, s); break;
-      case FORM_PLAIN: rc = launch_impl<float>(a, max_blocks, s); break;
-      default: rc = launch_impl<double>(a, max_blocks, s); break;
+      case FORM_SPLIT: rc = gr ? launch_impl<dd, true>(a, max_blocks, s) : launch_impl<dd, false>(a, max_blocks, s); break;
+      case FORM_PLAIN: rc = gr ? launch_impl<float, true>(a, max_blocks, s) : launch_impl<float, false>(a, max_blocks, s); break;
+      default: rc = gr ? launch_impl<double, true>(a, max_blocks, s) : launch_impl<double, false>(a, max_blocks, s); break;
     }
   }
   return rc;

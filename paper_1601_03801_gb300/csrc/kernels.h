@@ -84,7 +84,8 @@ void launch_deposit(int form, const DevState& st, const DevMesh& mesh, const Dev
 void launch_fields_from_fixed(int form, const void* q, const DevParams& P, void* phi,
                               int nf, cudaStream_t s);
 // cell vorticity (curl U, 0) of the FP64 velocity U [C][3] into the mesh's wfl
-void launch_curl(int form, const double* U, const DevParams& P, void* wfl, cudaStream_t s);
+void launch_curl(int form, const double* U, const DevParams& P, const DevMesh& mesh,
+                 cudaStream_t s);
 // k_smooth.cu: the smoothing solve of a batch of meshes in one persistent launch.
 constexpr int kMaxBeds = 1024;       // meshes in one smoothing launch
 constexpr int kMaxStepsRound = 64;  // Chebyshev steps of one round at most (more: next round)
@@ -92,6 +93,19 @@ constexpr int kMaxStepsRound = 64;  // Chebyshev steps of one round at most (mor
 // Pseudo-time schemes of the smoothing (Sec. 2.4): backward Euler, or BDF2 whose
 // first step is backward Euler.
 enum { TAU_EULER = 0, TAU_BDF2 = 1 };
+
+// Graded z mesh of a smoothing (all null / 0 on a uniform mesh): the z-face
+// coefficients of every plane, [nz][2] (towards k - 1, towards k + 1), for the
+// backward-Euler (0) and BDF2 (1) operators in FP64 and FP32; the plane weights
+// h_k / mean h, their sum over the cells, and per operator the largest sum of a
+// plane's two coefficients (for the Gershgorin bound of the spectrum).
+struct SmoothZ {
+  const double* cz[2];
+  const float* czf[2];
+  const double* w;
+  double wsum;
+  double zmax[2];
+};
 
 // One mesh of a smoothing batch, as the caller describes it.
 struct SmoothMesh {
@@ -102,7 +116,8 @@ struct SmoothMesh {
   int64_t C;
   int32_t nc[3], per[3];
   int32_t nf;
-  double coef[3];     // dtau * D_a / h_a^2
+  double coef[3];     // dtau * D_a / h_a^2 (z: unused on a graded mesh)
+  SmoothZ z;
 };
 
 // The operator of one kind of pseudo-step, A = I - sum_a coef_a L_a, and the
@@ -127,6 +142,7 @@ struct SmoothMeshDev {
   int32_t nc[3], per[3];
   int32_t cl_size, cl_planes;        // cluster solver: CTAs, z-planes per CTA (0: grid solver)
   SmoothSpec sp[2];  // [0]: backward-Euler steps (coef); [1]: BDF2 steps (2/3 coef)
+  SmoothZ z;         // graded z mesh (null: uniform)
 };
 
 struct SmoothBatchDev {
@@ -155,7 +171,8 @@ int launch_smooth_batch(int form, const SmoothMesh* meshes, int B, int nf, void*
 size_t smooth_work_bytes(int form, int64_t C, int nf, int scheme);
 int launch_smooth(int form, const DevParams& P, void* phi, const void* guess, int nf,
                   void* work, const DevState& st, int* iters_dev, double rtol, int max_iter,
-                  int n_tau, int scheme, const double coef[3], cudaStream_t s);
+                  int n_tau, int scheme, const double coef[3], const SmoothZ* z,
+                  cudaStream_t s);
 void launch_average_out(int form, const void* phi, const DevParams& P, void* ufe, double* eps,
                         double* Us, double* F, cudaStream_t s);
 void launch_phi_convert(int form, const void* phi, double* out, int64_t n, int to_double,

@@ -50,7 +50,7 @@ class SediParams(C.Structure):
         ("lubrication", _I), ("drag", _I), ("pressure_grad", _I), ("added_mass", _I),
         ("lift", _I), ("lub_tangential", _I),
         ("lub_h_in_frac", _D), ("lub_h_out_frac", _D), ("c_add", _D), ("c_lift", _D), ("eps_max", _D),
-        ("ncell", _I * 3),
+        ("ncell", _I * 3), ("z_grading", _D),
         ("bandwidth", _D * 3), ("n_tau", _I), ("tau_scheme", _I), ("cg_rtol", _D), ("cg_max_iter", _I),
         ("shift_eps", _I), ("shift_mom", _I), ("shift_force", _I),
         ("precision_form", _I), ("nbr_capacity", _I), ("use_graphs", _I), ("substep_variant", _I),

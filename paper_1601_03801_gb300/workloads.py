@@ -45,7 +45,7 @@ def default_params(**over) -> dict:
         dt=1.0e-6,
         lubrication=1, drag=1, pressure_grad=1, added_mass=1,
         lub_h_in_frac=1.0e-3, lub_h_out_frac=0.1, c_add=0.5, eps_max=0.9,
-        lift=0, c_lift=1.6, lub_tangential=0,
+        lift=0, c_lift=1.6, lub_tangential=0, z_grading=1.0,
         ncell=(10, 10, 20),
         bandwidth=(3e-3, 3e-3, 3e-3), n_tau=4, tau_scheme=0, cg_rtol=1e-8, cg_max_iter=500,
         shift_eps=40, shift_mom=40, shift_force=32,

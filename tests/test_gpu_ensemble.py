@@ -58,7 +58,7 @@ def run(g, beds_idx, single):
     return out
 
 
-@pytest.mark.parametrize("extra", [{}, {"lift": 1, "lub_tangential": 1}])
+@pytest.mark.parametrize("extra", [{}, {"lift": 1, "lub_tangential": 1}, {"z_grading": 3.0}])
 def test_ensemble_bit_identical_to_single_beds(ens, extra):
     prm, beds = ens
     prm = dict(prm, **extra)

@@ -225,3 +225,103 @@ def test_p5_neighbor_lists_cell_equals_brute(oracle_mod, periodic, skin):
         ref.append(np.nonzero(m)[0])
     assert np.array_equal(np.concatenate(ref), ib)
     assert ib.size > n  # non-trivial lists
+
+
+# ---------------------------------------------------------------- graded z mesh
+def graded_params(g=4.0, **over):
+    p = default_params(hi=(8e-3, 6e-3, 16e-3), ncell=(4, 3, 12), bandwidth=(2e-3, 1.5e-3, 2.5e-3),
+                       z_grading=g, cg_rtol=1e-12, cg_max_iter=5000)
+    p.update(over)
+    return p
+
+
+def test_p18_graded_faces(oracle_mod):
+    """P18: geometric cell heights from the floor, top / bottom = z_grading, summing to
+    the box height; z_grading = 1 gives the uniform faces."""
+    p = graded_params(4.0)
+    f = oracle_mod.z_faces(p)
+    h = np.diff(f)
+    assert f[0] == p["lo"][2] and f[-1] == p["hi"][2]
+    assert abs(h[-1] / h[0] - 4.0) < 1e-12
+    np.testing.assert_allclose(h[1:] / h[:-1], 4.0 ** (1 / 11), rtol=1e-12)
+    u = oracle_mod.z_faces(dict(p, z_grading=1.0))
+    np.testing.assert_allclose(u, np.linspace(0, 16e-3, 13), rtol=0, atol=1e-17)
+
+
+def test_p18_graded_operator(oracle_mod):
+    """P18: the graded diffusion operator keeps the constant mode (A 1 = 1), is
+    symmetric in the cell-volume inner product (so it keeps sum V_c x), and leaves a
+    field linear in z unchanged in interior cells (a linear profile is steady)."""
+    p = graded_params(5.0, periodic=(1, 0, 0), wall_lo=(0, 1, 1), wall_hi=(0, 1, 1))
+    nx, ny, nz = p["ncell"]
+    C = nx * ny * nz
+    f = oracle_mod.z_faces(p)
+    w = np.repeat(np.diff(f), nx * ny)
+    np.testing.assert_allclose(oracle_mod.smooth_operator(p, np.ones(C)), 1.0, rtol=0, atol=1e-13)
+    rng = np.random.default_rng(3)
+    x, y = rng.normal(size=C), rng.normal(size=C)
+    Ax, Ay = oracle_mod.smooth_operator(p, x), oracle_mod.smooth_operator(p, y)
+    assert abs(x @ (w * Ay) - y @ (w * Ax)) < 1e-12 * np.abs(x).sum() * np.abs(w * Ay).max()
+    assert abs((w * Ax).sum() - (w * x).sum()) < 1e-12 * np.abs(w * x).sum()
+    zc = 0.5 * (f[1:] + f[:-1])
+    lin = np.repeat(3.0 + 250.0 * zc, nx * ny)
+    r = (oracle_mod.smooth_operator(p, lin) - lin).reshape(nz, ny, nx)
+    assert np.abs(r[1:-1]).max() < 1e-12 * np.abs(lin).max()
+    assert np.abs(r[0]).max() > 1e-3  # the zero-flux floor is not a linear profile's face
+
+
+def test_p18_graded_smoothing_limit_and_conservation(oracle_mod):
+    """P18: a grading ratio a hair from 1 gives the uniform result; a real grading
+    keeps sum V_c phi (not sum phi) through the smoothing, with both schemes."""
+    p = graded_params(1.0)
+    C = int(np.prod(p["ncell"]))
+    phi = np.abs(np.random.default_rng(4).normal(size=(2, C)))
+    su, _ = oracle_mod.Oracle(p).smooth(phi)
+    sg, _ = oracle_mod.Oracle(dict(p, z_grading=1.0 + 1e-9)).smooth(phi)
+    assert np.abs(sg - su).max() < 1e-7 * np.abs(su).max()
+    for scheme in (0, 1):
+        q = graded_params(6.0, tau_scheme=scheme)
+        w = np.repeat(np.diff(oracle_mod.z_faces(q)), q["ncell"][0] * q["ncell"][1])
+        s, _ = oracle_mod.Oracle(q).smooth(phi)
+        for k in range(2):
+            assert abs((w * s[k]).sum() / (w * phi[k]).sum() - 1) < 1e-10
+            assert abs(s[k].sum() / phi[k].sum() - 1) > 1e-4
+        assert np.abs(s - phi).max() > 1e-2 * phi.max()
+
+
+def test_p18_graded_deposition_interpolation_curl(oracle_mod):
+    """P18: on a graded mesh a particle lands in the cell whose faces enclose it and
+    deposits V_p / V_c of that cell (so sum eps_c V_c = sum V_p); interpolation is
+    exact for a field linear in z between centres; the vorticity of a linear shear is
+    exact."""
+    p = graded_params(8.0, periodic=(1, 1, 0), ncell=(4, 4, 12), hi=(8e-3, 8e-3, 16e-3),
+                      drag=0, pressure_grad=1, added_mass=0, lubrication=0)
+    nx, ny, nz = p["ncell"]
+    f = oracle_mod.z_faces(p)
+    zc = 0.5 * (f[1:] + f[:-1])
+    rng = np.random.default_rng(5)
+    n = 40
+    x = np.stack([rng.uniform(0, 8e-3, n), rng.uniform(0, 8e-3, n), rng.uniform(0.6e-3, 15.4e-3, n)], 1)
+    d = np.full(n, 0.4e-3)
+    o = oracle_mod.Oracle(p)
+    o.set_particles(x, np.zeros((n, 3)), np.zeros((n, 3)), d, np.full(n, RHO))
+    q = o.deposit()
+    eps = np.ldexp(q[0].astype(float), -p["shift_eps"]).reshape(nz, ny, nx)
+    vc = (8e-3 / nx) * (8e-3 / ny) * np.diff(f)
+    vp = np.pi / 6 * d ** 3
+    assert abs((eps.sum(axis=(1, 2)) * vc).sum() / vp.sum() - 1) < 1e-9
+    kz = np.searchsorted(f, x[:, 2], side="right") - 1
+    per_plane = np.bincount(kz, weights=vp, minlength=nz)
+    np.testing.assert_allclose(eps.sum(axis=(1, 2)) * vc, per_plane, rtol=1e-9, atol=1e-30)
+    # interpolation: grad p linear in z -> -f_pg / V_p linear at interior points
+    gp = np.zeros((nz, ny, nx, 3))
+    gp[..., 2] = 100.0 + 4e4 * zc[:, None, None]
+    o.set_fluid(grad_p=gp.reshape(-1, 3))
+    fz = -o.forces()["fluid"][:, 2] / vp
+    inside = (x[:, 2] > zc[0]) & (x[:, 2] < zc[-1])
+    np.testing.assert_allclose(fz[inside], 100.0 + 4e4 * x[inside, 2], rtol=1e-12)
+    # vorticity of U = (G z, 0, 0)
+    U = np.zeros((nz, ny, nx, 3))
+    U[..., 0] = 30.0 * zc[:, None, None]
+    om = oracle_mod.curl(p, U.reshape(-1, 3))
+    np.testing.assert_allclose(om[:, 1], 30.0, rtol=1e-12)

@@ -42,6 +42,15 @@ MUTATIONS = [
      "test_p16"),
     ("orc_fluid.cpp", "f = add(f, lift_force(p, sub(U, u), om, d));",
      "f = add(f, lift_force(p, sub(u, U), om, d));", "test_p16"),
+    ("orc_average.cpp", "if (k > 0) op.czm[k] = scale * dtau * D[2] / (zg.hz[k] * (zg.zc[k] - zg.zc[k - 1]));",
+     "if (k > 0) op.czm[k] = scale * dtau * D[2] / (zg.hz[k - 1] * (zg.zc[k] - zg.zc[k - 1]));", "test_p18"),
+    ("orc_average.cpp", "double dz = zg.graded ? zg.hz[kz] : (p.hi[2] - p.lo[2]) / p.ncell[2];",
+     "double dz = zg.graded ? zg.hz[0] : (p.hi[2] - p.lo[2]) / p.ncell[2];", "test_p18"),
+    ("orc_fluid.cpp", "ax.f = (x - g.zc[k]) / (g.zc[k + 1] - g.zc[k]);",
+     "ax.f = (x - g.zc[k]) / (g.zf[k + 1] - g.zf[k]);", "test_p18"),
+    ("orc_fluid.cpp", "if (a == 2 && zg.graded) den = zg.zc[ip[2]] - zg.zc[im[2]];", "", "test_p18"),
+    ("orc_fluid.cpp", "std::expm1((double)k * lr) / std::expm1((double)n * lr)", "(double)k / (double)n",
+     "test_p18"),
     ("orc_fluid.cpp", "out[3 * c + 1] = g[2][0] - g[0][2];", "out[3 * c + 1] = g[0][2] - g[2][0];",
      "test_p15"),
     ("orc_fluid.cpp", "ip[a] = 1;\n            den = h;", "ip[a] = 1;\n            den = 2.0 * h;",
