@@ -299,7 +299,7 @@ def gpu_arm(args):
 
 
 def bounce_leg():
-    """Case 1 (Sec. 3.1): a 6 mm sphere falls onto the floor through quiescent fluid;
+    """Case 1 (Sec. 4.1): a 6 mm sphere falls onto the floor through quiescent fluid;
     the effective restitution e = e_water / e_air (e_air = 0.97, the dry coefficient of
     the linear contact law) over Stokes numbers set by density and viscosity, with
     lubrication and added mass and without them.  Qualitative: the paper compares with

@@ -113,7 +113,7 @@ typedef struct sedi_params {
   double c_lift;                           /* lift coefficient C_l, Eq. 7 [1.6] */
   double eps_max;                          /* clamp of eps_s in the drag law [0.9] */
   int32_t ncell[3];                        /* Eulerian mesh */
-  double z_grading;                        /* graded mesh along z (Sec. 3.2: refined
+  double z_grading;                        /* graded mesh along z (Sec. 4.2: refined
                                               towards the bottom): cell heights grow
                                               geometrically from lo[2], top cell / bottom
                                               cell = z_grading; 1 = uniform.  Needs a

@@ -63,7 +63,7 @@ typedef struct {
   int32_t lift;
   double c_lift;
   int32_t lub_tangential;
-  /* graded mesh along z (Sec. 3.2: refined towards the bottom): ratio of the top
+  /* graded mesh along z (Sec. 4.2: refined towards the bottom): ratio of the top
      cell's height to the bottom cell's; 1 = uniform */
   double z_grading;
 } orc_params;

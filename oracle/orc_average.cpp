@@ -26,7 +26,7 @@
  * x0 = phi^m.  An initial guess is first shifted so its sum equals sum(b).
  * U_s = (eps_s U_s) / max(eps_s, 1e-12) after smoothing.
  *
- * Graded z mesh (z_grading != 1; Sec. 3.2 refines the mesh towards the bottom).
+ * Graded z mesh (z_grading != 1; Sec. 4.2 refines the mesh towards the bottom).
  * Reading: cell heights h_k grow geometrically from the floor (faces in
  * orc_internal.h); a particle's cell is the one whose faces enclose its centre;
  * V_c = h_x h_y h_k.  The finite-volume diffusion step on the graded mesh:

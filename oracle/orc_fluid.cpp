@@ -4,7 +4,7 @@
  * Interpolation (Sec. 2.3 says only that U_f is "interpolated to the center of
  * particle i"; Sec. 2.2 says fluid fields are not smoothed before use).  Reading:
  * trilinear interpolation of the cell-centred fields; periodic axes wrap, other
- * axes clamp to the first/last cell centre.  On a graded z mesh (Sec. 3.2) the z
+ * axes clamp to the first/last cell centre.  On a graded z mesh (Sec. 4.2) the z
  * weight is the linear one between the two enclosing cell centres.
  *
  * Drag, Eq. (3)-(6), the Syamlal-O'Brien correlation of the MFIX documentation.

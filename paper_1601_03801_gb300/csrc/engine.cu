@@ -322,7 +322,7 @@ int sync_status(sedi_handle* h) {
   return 0;
 }
 
-// Graded z mesh (Sec. 3.2): cell heights h_k = h_0 r^k from the floor,
+// Graded z mesh (Sec. 4.2): cell heights h_k = h_0 r^k from the floor,
 // r = z_grading^(1/(nz - 1)), faces z_k = lo + L (r^k - 1) / (r^nz - 1) (expm1 keeps a
 // ratio near 1 accurate); centres, cell volumes h_x h_y h_k, and per plane the
 // finite-volume z-face coefficients of one smoothing step,

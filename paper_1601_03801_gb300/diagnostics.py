@@ -1,4 +1,4 @@
-"""Diagnostics of Case 1 (Sec. 3.1): the particle Stokes number, the time-step rule
+"""Diagnostics of Case 1 (Sec. 4.1): the particle Stokes number, the time-step rule
 of Sec. 2.5 for the linear contact law, and the impact and rebound speeds of a
 sphere bouncing on a wall, from which the effective restitution coefficient
 e = e_water / e_air of the particle-wall collision test is formed.
@@ -13,7 +13,7 @@ import math
 
 
 def stokes_number(rho_p, d, u, nu_f, rho_f):
-    """St = rho_p d u / (9 nu_f rho_f) (Sec. 3.1, Eq. 11)."""
+    """St = rho_p d u / (9 nu_f rho_f) (Sec. 4.1, Eq. 11)."""
     return rho_p * d * abs(u) / (9.0 * nu_f * rho_f)
 
 

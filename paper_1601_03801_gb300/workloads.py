@@ -6,7 +6,7 @@ deposition or smoothing).  The CUDA library and the FP64 oracle both consume
 what it returns.
 
 Workloads (the paper's Case 1 and Case 3 / sediment-transport scaling shapes,
-Sec. 3.1, 3.3 and 4.2, Table 1; every one is synthetic):
+Sec. 4.1, 4.3 and 5.2, Table 1; every one is synthetic):
 
 * ``small``  : 1,000 glass spheres, d = 1 mm, in a 20 x 20 x 40 mm box, periodic
   in x and y, walls at z = 0 and z = 40 mm, quiescent water, 10 x 10 x 20 mesh.
@@ -426,7 +426,7 @@ def random_fields(ncell, nf, seed, scale=1.0):
 
 
 def bounce_case(rho_p, nu_f, dt, d=6e-3, height=0.5, drop=0.45, lubrication=1, added_mass=1):
-    """Case 1 of Sec. 3.1 (Table 1): one sphere of diameter d and density rho_p
+    """Case 1 of Sec. 4.1 (Table 1): one sphere of diameter d and density rho_p
     released at rest at z = drop in quiescent fluid (rho_f = 1000, viscosity nu_f)
     in a 100 x 100 x height mm box, periodic in x and y, floor and lid walls, 10 x
     10 x (height / 10 mm) mesh; the paper's linear spring-dashpot contact

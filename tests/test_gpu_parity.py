@@ -157,7 +157,7 @@ def test_lift_and_tangential_lubrication(small, form):
 
 @pytest.mark.parametrize("form", ["fp64", "split"])
 def test_graded_mesh_matches_oracle(small, form):
-    # graded z mesh (Sec. 3.2: refined towards the floor, top cell 4x the bottom one):
+    # graded z mesh (Sec. 4.2: refined towards the floor, top cell 4x the bottom one):
     # deposition cells and volumes, smoothing with both schemes, interpolation of the
     # fluid fields, vorticity for the lift, averaging, 100 steps
     prm, parts = small
@@ -217,7 +217,7 @@ def test_graded_mesh_grid_solver():
 
 @pytest.mark.parametrize("form", ["fp64", "split"])
 def test_case1_bounce_matches_oracle(form):
-    # Case 1 (Sec. 3.1): a 6 mm steel sphere falls onto the floor under the paper's
+    # Case 1 (Sec. 4.1): a 6 mm steel sphere falls onto the floor under the paper's
     # linear contact, with lubrication and added mass; impact and rebound speeds of
     # the library against the oracle sampled every 10 substeps
     import math
@@ -428,7 +428,7 @@ def test_bdf2_grid_solver_mesh():
 
 
 def test_anisotropic_bandwidth_matches_oracle():
-    # Case-3 bandwidths of Sec. 3: 4 d horizontally, 2 d vertically (d = 0.5 mm), on
+    # Case-3 bandwidths of Sec. 4.3: 4 d horizontally, 2 d vertically (d = 0.5 mm), on
     # the benchmark's 64 x 32 x 64 mesh of 1 mm cells
     d = 0.5e-3
     prm = default_params(hi=(64e-3, 32e-3, 64e-3), ncell=(64, 32, 64), wall_hi=(0, 0, 0),

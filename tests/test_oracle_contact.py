@@ -273,7 +273,7 @@ def test_linear_law_differs_from_hertz_at_same_state(oracle_mod):
 
 
 def test_case1_bounce_effective_restitution(oracle_mod):
-    """Case 1 (Sec. 3.1) on the oracle: with lubrication and added mass the effective
+    """Case 1 (Sec. 4.1) on the oracle: with lubrication and added mass the effective
     restitution e_water / e_air falls with the Stokes number (small at St ~ 25, near 1
     at St ~ 5000); without them the sphere keeps nearly its dry coefficient."""
     from paper_1601_03801_gb300 import diagnostics as dg
