@@ -41,6 +41,16 @@ KERNEL_SOURCES = ["paper_1601_03801_gb300/csrc/k_force.cu", "paper_1601_03801_gb
                   "paper_1601_03801_gb300/csrc/common.cuh", "paper_1601_03801_gb300/csrc/dd.cuh"]
 
 
+PAIRS_VARIANT = 8  # substep variant of the pair list (two kernels per substep)
+
+
+def substep_kernel_name(variant):
+    """The kernel(s) the roofline line measures for a substep launch variant."""
+    if variant == PAIRS_VARIANT:
+        return "k_pair_forces<split> + k_substep<split, gather>"
+    return "k_substep<split>"
+
+
 def kernel_hash():
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
@@ -217,15 +227,19 @@ def gpu_arm(args):
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_source": peak_kind,
             "traffic": None if traffic_pp is None else round(traffic_pp * n),
-            "kernel": "k_substep<split>", "algorithmic_bytes_per_particle": round(per_particle, 1),
+            "kernel": substep_kernel_name(st1["substep_variant"]),
+            "algorithmic_bytes_per_particle": round(per_particle, 1),
             "launch_ms": round(sub_ms, 5), "kbar": round(kbar, 2), "cbar": round(cbar, 2)}
     phases = {k: round((t1[k] - t0[k]) / args.steps, 4) for k in
               ("rebuild_ms", "substep_ms", "deposit_ms", "smooth_ms")}
     rebuilds = st1["rebuilds"] - st0["rebuilds"]
-    # kernels per step: the graph's rebuild check + 20 substep kernels (+ 11 rebuild
-    # kernels per rebuild taken), then deposition, fixed point -> smoothing word, the
-    # cluster smoother (one launch) and the outputs
-    launches = args.steps * (1 + SUBSTEPS + 4) + 11 * rebuilds
+    # kernels per step: the graph's rebuild check + 20 substeps of one kernel (two with
+    # the pair list: pair forces, then the per-particle gather) (+ 13 rebuild kernels per
+    # rebuild taken: binning, lists, spring carry-over, pair list, flip), then
+    # deposition, fixed point -> smoothing word, the cluster smoother (one launch) and
+    # the outputs
+    per_sub = 2 if st1["substep_variant"] == PAIRS_VARIANT else 1
+    launches = args.steps * (1 + per_sub * SUBSTEPS + 4) + 13 * rebuilds
 
     # end-to-end through the C ABI with host buffers: per step the fluid fields go
     # host -> device (pinned) and the averaged fields come back
@@ -327,7 +341,7 @@ def bounce_leg():
             "wall_s": round(time.time() - t0, 2)}
 
 
-def large_leg(peak_gbs, steps=3, warmup=2):
+def large_leg(peak_gbs, steps=3, warmup=11):
     """10,000,000 spheres (d ~ U[0.4, 0.6] mm) in a periodic 400 x 200 x 100 mm box on a
     256 x 128 x 64 mesh with a turbulent-like flow: throughput of the split form (step =
     20 substeps + 1 averaging) and the substep kernel's HBM roofline fraction."""
@@ -374,7 +388,8 @@ def large_leg(peak_gbs, steps=3, warmup=2):
             "particles": n, "steps": steps, "warmup": warmup,
             "value": round(n * SUBSTEPS / (ms / 1e3), 1), "unit": UNIT, "ms_per_step": round(ms, 3),
             "phases_ms_per_step": phases,
-            "roofline": {"bound": "hbm", "kernel": "k_substep<split>", "achieved": round(achieved, 1),
+            "roofline": {"bound": "hbm", "kernel": substep_kernel_name(g.stats()["substep_variant"]),
+                         "achieved": round(achieved, 1),
                          "peak": peak_gbs, "unit": "GB/s", "frac": round(achieved / peak_gbs, 4),
                          "algorithmic_bytes_per_particle": round(per_particle, 1),
                          "launch_ms": round(sub_ms, 4), "kbar": round(kbar, 2), "cbar": round(cbar, 2)},
@@ -605,7 +620,8 @@ def kernels_only(args):
     extra = {}
     if args.with_cnn:
         extra = dict(use_cnn_guess=1, cnn_scale=(0.6, 1e4, 1e4, 1e4))
-    g = sedi.Sedi(dict(prm, precision_form=args.form, use_graphs=int(args.graphs), **extra))
+    g = sedi.Sedi(dict(prm, precision_form=args.form, use_graphs=int(args.graphs),
+                       substep_variant=args.variant, **extra))
     g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
     g.set_fluid(U=fl["U"])
     if args.with_cnn:
@@ -638,6 +654,8 @@ def main():
     ap.add_argument("--form", default="split", choices=["split", "plain", "fp64"])
     ap.add_argument("--with-cnn", action="store_true",
                     help="kernels mode: average with the learned warm start (random weights)")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="kernels mode: substep launch variant (-1: autotuned)")
     ap.add_argument("--graphs", type=int, default=1,
                     help="kernels mode: 0 launches kernels one by one (profilers see them)")
     args = ap.parse_args()

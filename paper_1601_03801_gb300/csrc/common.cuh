@@ -34,7 +34,8 @@ struct Ctl {
   int32_t cg_status;       // 0 or SEDI_EDIVERGED / SEDI_ETIMEOUT from the smoother
   uint32_t bar_count, bar_gen;  // grid barrier of the persistent smoother
   uint32_t blocks_done;    // completion counter of the substep kernel
-  int32_t pad[2];
+  uint32_t npair;          // interaction pairs of the current lists (pair list)
+  int32_t pad;
 };
 
 // Constants of the force arithmetic, precomputed on the host in the force word
@@ -250,6 +251,16 @@ struct DevState {
   int32_t* nn[2];     // [N] list length (nl parity)
   void* hist[2];      // Quad<S> [cap][N] pair springs (x, y, z, 0) (nl parity)
   uint32_t* cmask[2]; // bit k: slot k holds a spring (nl parity)
+  // pair list of the current lists (null: not kept): every listed pair once, from the
+  // particle that comes first in it, with the pair's record of the current substep.
+  // In the pair mode only the first particle's slot holds the pair's spring (see
+  // launch_spring_sync).
+  int4* pairs;        // [cap N / 2] (i, slot of j in i's list, j, slot of i in j's list)
+  int32_t* pid;       // [N][cap] pair of each list slot (particle-major)
+  uint32_t* fmask;    // [N] slots of the pairs the particle comes first in
+  uint32_t* amask;    // [2][N] slots of this substep's contact / lubrication pairs
+  void* prec;         // Quad<F> [cap N / 2][3] the pair's forces and torques
+  int64_t pcap;       // capacity of the pair arrays (cap N / 2)
   // binning scratch
   int32_t* bin_of;    // [N]
   int32_t* bin_count; // [nbins]

@@ -39,6 +39,7 @@ struct sedi_handle {
   DevMesh mesh{};
   std::vector<void*> part_allocs;  // per-particle buffers
   std::vector<void*> mesh_allocs;
+  int64_t since_set = 0;               // substeps since the particles were set
   SmoothZ zs{};                        // graded z mesh: smoothing tables (device) and bounds
   void* qfix = nullptr;   // [7][C] int64 (plain: float phi)
   void* phi = nullptr;    // [8][C] smoothing word
@@ -473,6 +474,20 @@ int alloc_particles(sedi_handle* h, int64_t N, double rmax) {
     if ((rc = dmalloc(h, h->part_allocs, &st.hist[b], q * cap * N))) return rc;
     if ((rc = dmalloc(h, h->part_allocs, (void**)&st.cmask[b], 4 * N))) return rc;
   }
+  if (form != FORM_FP64) {
+    // pair list (substep variant SUBSTEP_PAIRS): every listed pair once, cap N / 2 at most
+    st.pcap = cap * N / 2 + 1;
+    if ((rc = dmalloc(h, h->part_allocs, (void**)&st.pairs, 16 * st.pcap)) ||
+        (rc = dmalloc(h, h->part_allocs, (void**)&st.pid, 4 * cap * N)) ||
+        (rc = dmalloc(h, h->part_allocs, (void**)&st.fmask, 4 * N)) ||
+        (rc = dmalloc(h, h->part_allocs, (void**)&st.amask, 8 * N)) ||
+        (rc = dmalloc(h, h->part_allocs, &st.prec, 3 * fq * st.pcap)))
+      return rc;
+    CK(cudaMemset(st.pairs, 0, 16 * st.pcap));
+    CK(cudaMemset(st.amask, 0, 8 * N));
+    CK(cudaMemset(st.pid, 0, 4 * cap * N));
+    CK(cudaMemset(st.fmask, 0, 4 * N));
+  }
   // bins: edge >= the largest list cutoff (2 r_max (1 + f) + skin) with margin
   const sedi_params& p = h->prm;
   const double rc_max = (2.0 * rmax) * (1.0 + p.lub_h_out_frac) + p.skin;
@@ -606,14 +621,22 @@ int rebuild_now(sedi_handle* h) {
 
 // ---------------------------------------------------------------- autotuner
 // The launch variant of the substep kernel (threads per block x resident blocks,
-// which sets the register budget) is picked per workload: forces-only launches of
-// every variant (they write only the force read-back buffer, so the state is
-// untouched) are timed with events in interleaved rounds, and the variant with
-// the lowest median wins.  Results are keyed by (GPU, N, diameter range, form),
-// kept for the process and, when the environment variable SEDI_AUTOTUNE_CACHE
-// names a file, in that file as one JSON object per line.
+// which sets the register budget, the pair phase, or the pair list) is picked per
+// workload: one integrating substep of every variant is timed with events in
+// interleaved rounds, and the variant with the lowest median wins.  A substep
+// reads the state buffer the step starts from and writes the other one, so only
+// the arrays it updates in place (springs and their masks, wall springs, lagged
+// accelerations, the control block) are copied aside first and put back after
+// every timed launch: tuning leaves the state as it found it.  Results are keyed
+// by (GPU, N, diameter range, form), kept for the process and, when the
+// environment variable SEDI_AUTOTUNE_CACHE names a file, in that file as one JSON
+// object per line.
 
 constexpr int kTuneRounds = 5;
+// Springs and lubrication gaps form over the first substeps after the particles are
+// set (a fresh state has no tangential history); the launch shapes are compared on
+// a state that has them.  Until then the per-particle loop at 128 x 6 runs.
+constexpr int64_t kTuneAfter = 200;
 
 std::mutex g_tune_mu;
 std::map<std::string, int> g_tune_cache;
@@ -673,6 +696,7 @@ int autotune(sedi_handle* h) {
     h->variant = SUBSTEP_B128_LOOP;
     return 0;
   }
+  if (h->since_set < kTuneAfter) return 0;
   const std::string key = tune_key(h);
   if (key == h->tuned_key) return 0;
   int best = -1;
@@ -686,18 +710,46 @@ int autotune(sedi_handle* h) {
     // lists must cover the current positions, exactly as the first substep would see them
     launch_check(h->st, h->P, 0ull, 0, h->stream);
     launch_rebuild(h->form, h->st, h->P, 0, false, h->stream);
+    CK(cudaStreamSynchronize(h->stream));
+    // the arrays an integrating substep updates in place, and their saved copies
+    Ctl c;
+    CK(cudaMemcpy(&c, h->st.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    const int64_t N = h->N, cap = h->P.cap;
+    const size_t q = quad_bytes(h->form), fq = fquad_bytes(h->form), w = word_bytes(h->form);
+    struct Item { void* p; size_t n; };
+    const std::vector<Item> live = {
+        {h->st.hist[c.nl], q * cap * N}, {h->st.cmask[c.nl], 4 * (size_t)N},
+        {h->st.acc[c.pb], fq * N}, {h->st.whist[c.pb], (size_t)kWalls * 3 * w * N},
+        {h->st.wmask[c.pb], 4 * (size_t)N}, {h->st.ctl, sizeof(Ctl)}};
+    size_t total = 0;
+    for (const auto& it : live) total += (it.n + 255) & ~(size_t)255;
+    char* save = nullptr;
+    CK(cudaMalloc((void**)&save, total));
+    auto copy_all = [&](bool to_save) {
+      size_t off = 0;
+      for (const auto& it : live) {
+        if (to_save) cudaMemcpyAsync(save + off, it.p, it.n, cudaMemcpyDeviceToDevice, h->stream);
+        else cudaMemcpyAsync(it.p, save + off, it.n, cudaMemcpyDeviceToDevice, h->stream);
+        off += (it.n + 255) & ~(size_t)255;
+      }
+    };
+    copy_all(true);
     std::vector<cudaEvent_t> ev(2 * kSubstepVariants * kTuneRounds, nullptr);
     for (auto& e : ev) CK(cudaEventCreate(&e));
-    for (int v = 0; v < kSubstepVariants; ++v)  // warm-up: first launch of each variant
-      launch_substep(h->form, h->st, h->mesh, h->P, 0, false, v, 0ull, 0, h->stream);
+    for (int v = 0; v < kSubstepVariants; ++v) {  // warm-up: first launch of each variant
+      launch_substep(h->form, h->st, h->mesh, h->P, 0, true, v, 0ull, 0, h->stream);
+      copy_all(false);
+    }
     for (int r = 0; r < kTuneRounds; ++r)
       for (int v = 0; v < kSubstepVariants; ++v) {
         cudaEvent_t* e = &ev[2 * (r * kSubstepVariants + v)];
         CK(cudaEventRecord(e[0], h->stream));
-        launch_substep(h->form, h->st, h->mesh, h->P, 0, false, v, 0ull, 0, h->stream);
+        launch_substep(h->form, h->st, h->mesh, h->P, 0, true, v, 0ull, 0, h->stream);
         CK(cudaEventRecord(e[1], h->stream));
+        copy_all(false);
       }
     int rc = sync_status(h);
+    cudaFree(save);
     double med[kSubstepVariants];
     for (int v = 0; v < kSubstepVariants && !rc; ++v) {
       std::vector<double> t;
@@ -720,6 +772,8 @@ int autotune(sedi_handle* h) {
     g_tune_cache[key] = best;
   }
   if (best != h->variant) clear_graphs(h);  // graphs bake in the launch shape
+  // leaving the pair mode: the other variants read the partner copies of the springs
+  if (h->variant == SUBSTEP_PAIRS && best != SUBSTEP_PAIRS) launch_spring_sync(h->form, h->st, h->stream);
   h->variant = best;
   h->tuned_key = key;
   return 0;
@@ -787,7 +841,7 @@ int sedi_create(const sedi_params* p, sedi_handle** out) {
     return rc;
   }
   h->form = p->precision_form;
-  h->variant = p->substep_variant >= 0 && h->form != FORM_FP64 ? p->substep_variant : SUBSTEP_B128;
+  h->variant = p->substep_variant >= 0 && h->form != FORM_FP64 ? p->substep_variant : SUBSTEP_B128_LOOP;
   fill_params(h);
   const int64_t C = h->P.C;
   h->U.assign(3 * C, 0.0);
@@ -976,6 +1030,7 @@ int sedi_set_particles(sedi_handle* h, int32_t bed, int64_t n, const int64_t* id
   cudaFree(tmp);
   if (rc) return rc;
   h->have_particles = true;
+  h->since_set = 0;
   return 0;
 }
 
@@ -1082,6 +1137,7 @@ int sedi_step(sedi_handle* h, int32_t n) {
   }
   CK(cudaGetLastError());
   h->stats.substeps += n;
+  h->since_set += n;
   return 0;
 }
 
@@ -1653,6 +1709,7 @@ int64_t sedi_get_contacts(sedi_handle* h, int32_t bed, int64_t cap, int64_t* ij,
   CK(cudaMalloc((void**)&dij, 16 * c2));
   CK(cudaMalloc((void**)&dxi, 24 * c2));
   cudaMemsetAsync(dc, 0, 8, h->stream);
+  launch_spring_sync(h->form, h->st, h->stream);  // pair-mode springs to both slots
   launch_contacts_export(h->form, h->st, h->P, dc, cap, dij, dxi, h->stream);
   unsigned long long m = 0;
   cudaMemcpyAsync(&m, dc, 8, cudaMemcpyDeviceToHost, h->stream);
@@ -1748,6 +1805,7 @@ int state_io(sedi_handle* h, FILE* f, bool save) {
 static int save_to(sedi_handle* h, FILE* f) {
   int rc = need_particles(h);
   if (rc) return rc;
+  launch_spring_sync(h->form, h->st, h->stream);  // pair-mode springs to both slots
   if ((rc = sync_status(h)) || (rc = refresh_eps_host(h))) return rc;
   CkHeader hd{};
   std::memcpy(hd.magic, "SEDICK01", 8);
@@ -1817,6 +1875,9 @@ static int load_from(sedi_handle* h, FILE* f) {
     rc = state_io(h, f, false);
   }
   if (rc) return rc;
+  // the pair list follows the loaded neighbour lists
+  launch_pair_list(h->st, h->P, h->stream);
+  CK(cudaStreamSynchronize(h->stream));
   h->stats = hd.stats;
   h->have_particles = true;
   return 0;

@@ -372,6 +372,67 @@ __device__ __forceinline__ void flip_body(const DevState& st, bool force) {
   c->rebuilds += 1;
 }
 
+// Pair list of the lists just built (before the flip): every particle appends the
+// pairs it comes first in (list bit) in slot order, a warp's particles contiguously
+// (one atomic per warp), and records the pair in both particles' slots.  The order
+// of the pairs in the list depends on scheduling; nothing computed from a pair does.
+__device__ __forceinline__ void pair_fill_body(const DevState& st, bool force, bool current,
+                                               int P_CAP) {
+  if (skip(st.ctl, force)) return;
+  const int ql = current ? st.ctl->nl : st.ctl->nl ^ 1;  // the new lists, or the current ones
+  const int64_t N = st.N;
+  const int32_t* nbr = st.nbr[ql];
+  const int32_t* nn = st.nn[ql];
+  const int lane = threadIdx.x & 31;
+  // whole warps iterate together (the shuffles below need every lane)
+  const int64_t n_pad = (N + 31) & ~(int64_t)31;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const bool valid = i < N;
+    const int ni = valid ? nn[i] : 0;
+    uint32_t own = 0;
+    for (int k = 0; k < ni; ++k)
+      if (nbr_first(nbr[(int64_t)k * N + i])) own |= 1u << k;
+    if (valid) st.fmask[i] = own;
+    const int cnt = __popc(own);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    uint32_t base = 0;
+    if (lane == 31) base = atomicAdd(&st.ctl->npair, (uint32_t)incl);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    uint32_t m = base + (uint32_t)(incl - cnt);
+    while (own) {
+      const int k = __ffs(own) - 1;
+      own &= own - 1;
+      const int32_t j = nbr_index(nbr[(int64_t)k * N + i]);
+      int k2 = -1;
+      const int nj = nn[j];
+      for (int kk = 0; kk < nj; ++kk)
+        if (nbr_index(nbr[(int64_t)kk * N + j]) == (int32_t)i) {
+          k2 = kk;
+          break;
+        }
+      if (k2 < 0) {
+        // lists are symmetric by construction; an unmatched pair is an internal error
+        atomicCAS(&st.ctl->error, 0, -9);
+        k2 = 0;
+      }
+      if ((int64_t)m >= st.pcap) {
+        atomicCAS(&st.ctl->error, 0, -9);
+        break;
+      }
+      st.pairs[m] = make_int4((int)i, k, j, k2);
+      st.pid[(int64_t)i * P_CAP + k] = (int32_t)m;
+      st.pid[(int64_t)j * P_CAP + k2] = (int32_t)m;
+      ++m;
+    }
+  }
+}
+
 __global__ void k_advance(Ctl* ctl, int n) { ctl->st = (ctl->st + n) & 1; }
 
 // ---------------------------------------------------------------- kernels
@@ -399,6 +460,31 @@ __global__ void k_build(DevState st, DevParams P, int sub_off, bool force) {
 template <int FORM>
 __global__ void k_remap(DevState st, DevParams P, bool force) { remap_body<FORM>(st, P, force); }
 __global__ void k_flip(DevState st, bool force) { flip_body(st, force); }
+__global__ void k_pair_reset(DevState st, bool force) {
+  if (!skip(st.ctl, force)) st.ctl->npair = 0u;
+}
+__global__ void k_pair_fill(DevState st, bool force, bool current, int cap) {
+  pair_fill_body(st, force, current, cap);
+}
+
+// Pair mode keeps a pair's spring in the first particle's slot only; this copies it
+// to the partner's slot, as the per-particle loop keeps it (before the lists are
+// read slot by slot: another launch variant, a checkpoint, the contact export).
+template <int FORM>
+__global__ void k_spring_sync(DevState st) {
+  using S = typename Traits<FORM>::S;
+  const int nl = st.ctl->nl;
+  const int64_t N = st.N;
+  const int64_t M = (int64_t)st.ctl->npair < st.pcap ? (int64_t)st.ctl->npair : st.pcap;
+  Quad<S>* hist = (Quad<S>*)st.hist[nl];
+  const uint32_t* cmask = st.cmask[nl];
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
+       m += (int64_t)gridDim.x * blockDim.x) {
+    const int4 pr = st.pairs[m];
+    if ((cmask[pr.x] >> pr.y) & 1u)
+      stq(hist + (int64_t)pr.w * N + pr.z, ldq(hist + (int64_t)pr.y * N + pr.x));
+  }
+}
 
 // true when this block's bed has no rebuild pending (the whole block returns)
 __device__ __forceinline__ bool ens_idle(const BedView* v) {
@@ -517,6 +603,10 @@ void rebuild_impl(const DevState& st, const DevParams& P, int sub_off, bool forc
   k_gather<FORM><<<grid_for(st.N, B), B, 0, s>>>(st, sub_off, false);
   k_build<FORM><<<grid_for(st.N, 128), 128, 0, s>>>(st, P, sub_off, false);
   k_remap<FORM><<<grid_for(st.N, B), B, 0, s>>>(st, P, force);
+  if (st.pairs) {
+    k_pair_reset<<<1, 1, 0, s>>>(st, false);
+    k_pair_fill<<<grid_for(st.N, B), B, 0, s>>>(st, false, false, (int)P.cap);
+  }
   k_flip<<<1, 1, 0, s>>>(st, false);
 }
 
@@ -554,6 +644,19 @@ void launch_rebuild(int form, const DevState& st, const DevParams& P, int sub_of
     case FORM_PLAIN: rebuild_impl<FORM_PLAIN>(st, P, sub_off, force, s); break;
     default: rebuild_impl<FORM_FP64>(st, P, sub_off, force, s); break;
   }
+}
+
+void launch_pair_list(const DevState& st, const DevParams& P, cudaStream_t s) {
+  if (!st.pairs) return;
+  k_pair_reset<<<1, 1, 0, s>>>(st, true);
+  k_pair_fill<<<grid_for(st.N, 256), 256, 0, s>>>(st, true, true, (int)P.cap);
+}
+
+void launch_spring_sync(int form, const DevState& st, cudaStream_t s) {
+  if (!st.pairs) return;
+  const unsigned g = grid_for(st.pcap, 256);
+  if (form == FORM_SPLIT) k_spring_sync<FORM_SPLIT><<<g, 256, 0, s>>>(st);
+  else if (form == FORM_PLAIN) k_spring_sync<FORM_PLAIN><<<g, 256, 0, s>>>(st);
 }
 
 void launch_check(const DevState& st, const DevParams& P, unsigned long long cond_handle,

@@ -115,18 +115,21 @@ __device__ __forceinline__ V3<F> cross(V3<F> a, V3<F> b) {
 template <class F>
 struct PairOut {
   V3<F> fa, t, l, lt;  // contact force (on i), contact torque, lubrication force and torque
+  V3<F> tb;            // contact torque on the partner (BOTH only)
   bool contact, lub;
 };
 
 // EXT: the optional terms (tangential lubrication here, lift in the fluid force)
 // are compiled in; without it the kernel carries none of their registers.
-template <int FORM, bool INTEGRATE, bool EXT>
+// BOTH (pair list, i first in the pair): also the partner's contact torque, and the
+// spring stored in the partner's slot k2 as well.
+template <int FORM, bool INTEGRATE, bool EXT, bool BOTH = false>
 __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
     const DevParams& P, const Quad<typename Traits<FORM>::S>& Pi,
     const typename Traits<FORM>::F* vi, const typename Traits<FORM>::F* wi,
     typename Traits<FORM>::F mi, int32_t e, int k, bool has, int64_t i, int64_t N,
     const Quad<typename Traits<FORM>::S>* pos, const Quad<typename Traits<FORM>::S>* vel,
-    const Quad<typename Traits<FORM>::S>* omg, Quad<typename Traits<FORM>::S>* hist) {
+    const Quad<typename Traits<FORM>::S>* omg, Quad<typename Traits<FORM>::S>* hist, int k2 = 0) {
   using S = typename Traits<FORM>::S;
   using F = typename Traits<FORM>::F;
   using NS = Num<S>;
@@ -197,6 +200,7 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
     if (INTEGRATE) stq(hist + (int64_t)k * N + i, Quad<S>{xn_[0], xn_[1], xn_[2], NS::from_f(F(0))});
     const F lev = i_lo ? la : lb;
     o.t = cross(V3<F>{lev * n.x, lev * n.y, lev * n.z}, Ft);
+    if (BOTH) o.tb = cross(V3<F>{lb * n.x, lb * n.y, lb * n.z}, Ft);
     o.fa = i_lo ? FA : V3<F>{-FA.x, -FA.y, -FA.z};
   }
   if (o.lub) {
@@ -238,13 +242,80 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
 
 }  // namespace
 
+// Pair forces from the pair list: one thread per listed pair, from the particle
+// that comes first in it.  The same FP32 cull and the same pair evaluation as the
+// per-particle loop; the pair's flags and its forces and torques on both particles
+// go to the pair record, the spring to both particles' slots.  The pairs run
+// independently, so the grid-stride order does not change any result.
+template <int FORM, bool INTEGRATE>
+__global__ void __launch_bounds__(128, 6) k_pair_forces(DevState st, DevParams P, int sub_off) {
+  using S = typename Traits<FORM>::S;
+  using F = typename Traits<FORM>::F;
+  using NS = Num<S>;
+  const Ctl* ctl = st.ctl;
+  const int sb = (ctl->st + sub_off) & 1;
+  const int nl = ctl->nl;
+  const int64_t N = st.N;
+  const Quad<S>* pos = (const Quad<S>*)st.pos[sb];
+  const Quad<S>* vel = (const Quad<S>*)st.vel[sb];
+  const Quad<S>* omg = (const Quad<S>*)st.omg[sb];
+  const int32_t* nbr = st.nbr[nl];
+  const uint32_t* cmask = st.cmask[nl];
+  Quad<S>* hist = (Quad<S>*)st.hist[nl];
+  Quad<F>* prec = (Quad<F>*)st.prec;
+  const int64_t M = (int64_t)ctl->npair < st.pcap ? (int64_t)ctl->npair : st.pcap;
+  const float fac = P.lubrication ? (1.0f + P.lub_out_f) : 1.0f;
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
+       m += (int64_t)gridDim.x * blockDim.x) {
+    const int4 pr = st.pairs[m];
+    const int64_t i = pr.x;
+    const Quad<S> Pi = ldq(pos + i);
+    const Quad<S> Pv = ldq(pos + pr.z);
+    float dx = (float)NS::dif(Pv.a, Pi.a), dy = (float)NS::dif(Pv.b, Pi.b), dz = (float)NS::dif(Pv.c, Pi.c);
+    if (P.periodic[0]) dx = dx > P.cf.halfL[0] ? dx - P.cf.L[0] : (dx < -P.cf.halfL[0] ? dx + P.cf.L[0] : dx);
+    if (P.periodic[1]) dy = dy > P.cf.halfL[1] ? dy - P.cf.L[1] : (dy < -P.cf.halfL[1] ? dy + P.cf.L[1] : dy);
+    if (P.periodic[2]) dz = dz > P.cf.halfL[2] ? dz - P.cf.L[2] : (dz < -P.cf.halfL[2] ? dz + P.cf.L[2] : dz);
+    const float cut = ((float)NS::f(Pi.d) + (float)NS::f(Pv.d)) * fac;
+    if (!(dx * dx + dy * dy + dz * dz <= cut * cut * 1.0002f)) continue;
+    const Quad<S> Vi = ldq(vel + i), Wi = ldq(omg + i);
+    const F vi[3] = {NS::f(Vi.a), NS::f(Vi.b), NS::f(Vi.c)};
+    const F wi[3] = {NS::f(Wi.a), NS::f(Wi.b), NS::f(Wi.c)};
+    const int k = pr.y;
+    const PairOut<F> o = pair_eval<FORM, INTEGRATE, false, true>(
+        P, Pi, vi, wi, NS::f(Vi.d), nbr[(int64_t)k * N + i], k, (cmask[i] >> k) & 1u, i, N, pos,
+        vel, omg, hist, pr.w);
+    // the pair's record; the slot masks tell the gather which slots hold this
+    // substep's records (OR is order-free)
+    if (o.contact) {
+      atomicOr(st.amask + i, 1u << k);
+      atomicOr(st.amask + pr.z, 1u << pr.w);
+    }
+    if (o.lub) {
+      atomicOr(st.amask + N + i, 1u << k);
+      atomicOr(st.amask + N + pr.z, 1u << pr.w);
+    }
+    if (o.contact || o.lub) {
+      const V3<F> z{F(0), F(0), F(0)};
+      const V3<F> fa = o.contact ? o.fa : z, ta = o.contact ? o.t : z, tb = o.contact ? o.tb : z;
+      const V3<F> l = o.lub ? o.l : z;
+      Quad<F>* r = prec + 3 * m;
+      stq(r, Quad<F>{fa.x, fa.y, fa.z, ta.x});
+      stq(r + 1, Quad<F>{ta.y, ta.z, tb.x, tb.y});
+      stq(r + 2, Quad<F>{tb.z, l.x, l.y, l.z});
+    }
+  }
+}
+
 // BS threads per block, at least MINB resident blocks per SM (which caps the
 // registers a thread may use); the variant is chosen per workload by the engine's
 // autotuner.
 // Body of the fused substep for one bed: blk is the block's index within the bed,
 // nblk the bed's block count; ectl (ensembles only) collects the rebuild decision
 // of all nbeds beds for the graph condition of the next substep.
-template <int FORM, bool INTEGRATE, int BS, bool COOP, bool EXT>
+// GATHER: the pair forces come from the pair list (k_pair_forces ran before); each
+// particle adds its pairs' records in slot order, the same additions in the same
+// order as the per-particle loop.
+template <int FORM, bool INTEGRATE, int BS, bool COOP, bool EXT, bool GATHER = false>
 __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& mesh,
                                              const DevParams& P, int sub_off,
                                              cudaGraphConditionalHandle next, int use_cond,
@@ -288,6 +359,9 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
     }
     const int nn = st.nn[nl][i];
     mask = st.cmask[nl][i];
+    if constexpr (GATHER) {
+      (void)nn;  // the slots come from the pair kernel's masks
+    } else {
     const float lub_out_f = P.lub_out_f;
     // phase 1: cheap FP32 cull of every listed partner (relative margin; the exact
     // test follows); four candidates per round so their gathers overlap
@@ -312,9 +386,52 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
         if (k0 + u < nn && dx * dx + dy * dy + dz * dz <= cut * cut * 1.0002f) live |= 1u << (k0 + u);
       }
     }
+    }
   }
   // phase 2: interacting pairs only, in slot order
-  if constexpr (COOP) {
+  if constexpr (GATHER) {
+    const Quad<F>* prec = (const Quad<F>*)st.prec;
+    const int32_t* pid = st.pid + i * P.cap;
+    uint32_t mc = 0, ml = 0, first = 0;
+    if (valid) {
+      first = st.fmask[i];
+      // this substep's contact and lubrication slots, cleared for the next substep
+      mc = st.amask[i];
+      ml = st.amask[N + i];
+      st.amask[i] = 0u;
+      st.amask[N + i] = 0u;
+    }
+    live = mc | ml;
+    while (live) {
+      const int k = __ffs(live) - 1;
+      live &= live - 1;
+      const int32_t m = pid[k];
+      if ((uint64_t)(uint32_t)m >= (uint64_t)st.pcap) continue;
+      const Quad<F>* r = prec + 3 * (int64_t)m;
+      const bool fi = (first >> k) & 1u;
+      if ((mc >> k) & 1u) {
+        // the force on the partner is minus the force on the first particle
+        const Quad<F> q0 = ldq(r), q1 = ldq(r + 1);
+        if (fi) {
+          fc.x += q0.a; fc.y += q0.b; fc.z += q0.c;
+          tq.x += q0.d; tq.y += q1.a; tq.z += q1.b;
+        } else {
+          const Quad<F> q2 = ldq(r + 2);
+          fc.x += -q0.a; fc.y += -q0.b; fc.z += -q0.c;
+          tq.x += q1.c; tq.y += q1.d; tq.z += q2.a;
+        }
+        if (INTEGRATE) nmask |= 1u << k;
+      }
+      if ((ml >> k) & 1u) {
+        const Quad<F> q2 = ldq(r + 2);
+        if (fi) {
+          fl.x += q2.b; fl.y += q2.c; fl.z += q2.d;
+        } else {
+          fl.x += -q2.b; fl.y += -q2.c; fl.z += -q2.d;
+        }
+      }
+    }
+  } else if constexpr (COOP) {
     // warp-cooperative: the warp's (owner lane, slot) pairs are queued in slot order
     // and evaluated 32 at a time, one per lane; each owner then adds its results in
     // queue order, i.e. the same additions in the same order as the loop below
@@ -589,12 +706,12 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
   }
 }
 
-template <int FORM, bool INTEGRATE, int BS, int MINB, bool COOP, bool EXT>
+template <int FORM, bool INTEGRATE, int BS, int MINB, bool COOP, bool EXT, bool GATHER = false>
 __global__ void __launch_bounds__(BS, MINB) k_substep(DevState st, DevMesh mesh, DevParams P,
                                                          int sub_off, cudaGraphConditionalHandle next,
                                                          int use_cond) {
-  substep_body<FORM, INTEGRATE, BS, COOP, EXT>(st, mesh, P, sub_off, next, use_cond, blockIdx.x,
-                                               gridDim.x, nullptr, 1);
+  substep_body<FORM, INTEGRATE, BS, COOP, EXT, GATHER>(st, mesh, P, sub_off, next, use_cond,
+                                                       blockIdx.x, gridDim.x, nullptr, 1);
 }
 
 // Ensemble: blockIdx.y is the bed, blockIdx.x the block within it (blocks past the
@@ -622,6 +739,29 @@ static void launch_bs(const DevState& st, const DevMesh& mesh, const DevParams& 
     k_substep<FORM, false, BS, MINB, COOP, EXT><<<(unsigned)grid, BS, 0, s>>>(st, mesh, P, sub_off, h, 0);
 }
 
+// Pair list: the pair forces (grid-stride over the pairs on a fixed grid, the pair
+// count lives on the device), then the per-particle kernel gathering the records.
+template <int FORM>
+static void launch_pairs(const DevState& st, const DevMesh& mesh, const DevParams& P, int sub_off,
+                         bool integrate, unsigned long long next, int use_cond, cudaStream_t s) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int64_t g = (st.pcap + 127) / 128;
+  const int64_t gmax = (int64_t)nsm * 6 * 4;
+  if (g > gmax) g = gmax;
+  if (g < 1) g = 1;
+  const int64_t grid = (st.N + 127) / 128;
+  const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)next;
+  if (integrate) {
+    k_pair_forces<FORM, true><<<(unsigned)g, 128, 0, s>>>(st, P, sub_off);
+    k_substep<FORM, true, 128, 6, false, false, true><<<(unsigned)grid, 128, 0, s>>>(st, mesh, P, sub_off, h, use_cond);
+  } else {
+    k_pair_forces<FORM, false><<<(unsigned)g, 128, 0, s>>>(st, P, sub_off);
+    k_substep<FORM, false, 128, 6, false, false, true><<<(unsigned)grid, 128, 0, s>>>(st, mesh, P, sub_off, h, 0);
+  }
+}
+
 template <int FORM>
 static void launch_one(const DevState& st, const DevMesh& mesh, const DevParams& P, int sub_off,
                        bool integrate, int variant, unsigned long long next, int use_cond,
@@ -641,6 +781,10 @@ static void launch_one(const DevState& st, const DevMesh& mesh, const DevParams&
       case SUBSTEP_B128_LOOP: launch_bs<FORM, 128, 6, false>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
       case SUBSTEP_B128_OCC8_LOOP: launch_bs<FORM, 128, 8, false>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
       case SUBSTEP_B64_LOOP: launch_bs<FORM, 64, 12, false>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
+      case SUBSTEP_PAIRS:
+        if (st.pairs) launch_pairs<FORM>(st, mesh, P, sub_off, integrate, next, use_cond, s);
+        else launch_bs<FORM, 128, 6, false>(st, mesh, P, sub_off, integrate, next, use_cond, s);
+        return;
       default: launch_bs<FORM, 128, 6, true>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
     }
   } else {

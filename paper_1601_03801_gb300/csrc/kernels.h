@@ -9,8 +9,10 @@ namespace sedi {
 // Launch variants of the substep kernel: threads per block and minimum resident
 // blocks per SM (128/6, 64/12, 256/3 cap registers at 80 a thread, 128/8 at 64,
 // 128/5 at 96), all with the warp-cooperative pair phase; variants 5-7 run the
-// per-particle pair loop at 128/6, 128/8 and 64/12.  The FP64 parity form runs
-// 128/6 with the loop.
+// per-particle pair loop at 128/6, 128/8 and 64/12; variant 8 evaluates each listed
+// pair once from a pair list (one thread per pair) and gathers the pair records per
+// particle in slot order (two launches).  The FP64 parity form runs 128/6 with the
+// loop.
 enum SubstepVariant {
   SUBSTEP_B128 = 0,
   SUBSTEP_B64 = 1,
@@ -19,9 +21,10 @@ enum SubstepVariant {
   SUBSTEP_B128_OCC5 = 4,
   SUBSTEP_B128_LOOP = 5,
   SUBSTEP_B128_OCC8_LOOP = 6,
-  SUBSTEP_B64_LOOP = 7
+  SUBSTEP_B64_LOOP = 7,
+  SUBSTEP_PAIRS = 8
 };
-constexpr int kSubstepVariants = 8;
+constexpr int kSubstepVariants = 9;
 inline int substep_block(int variant) {
   return (variant == SUBSTEP_B64 || variant == SUBSTEP_B64_LOOP) ? 64 : variant == SUBSTEP_B256 ? 256 : 128;
 }
@@ -77,6 +80,11 @@ void launch_neighbors_fill(const DevState& st, const int64_t* offsets, int64_t* 
 void launch_contacts_export(int form, const DevState& st, const DevParams& P,
                             unsigned long long* count, int64_t cap, int64_t* ij, double* xi,
                             cudaStream_t s);
+
+// k_bin.cu: pair list of the current neighbour lists (after a checkpoint load), and
+// the partner copies of the pair-mode springs (before the slots are read elsewhere).
+void launch_pair_list(const DevState& st, const DevParams& P, cudaStream_t s);
+void launch_spring_sync(int form, const DevState& st, cudaStream_t s);
 
 // k_avg.cu: deposition, field conversion, outputs.
 void launch_deposit(int form, const DevState& st, const DevMesh& mesh, const DevParams& P,
