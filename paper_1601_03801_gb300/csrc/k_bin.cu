@@ -372,9 +372,10 @@ __device__ __forceinline__ void flip_body(const DevState& st, bool force) {
   c->rebuilds += 1;
 }
 
-// Pair list of the lists just built (before the flip): every particle appends the
-// pairs it comes first in (list bit) in slot order, a warp's particles contiguously
-// (one atomic per warp), and records the pair in both particles' slots.  The order
+// Pair list of the lists just built (before the flip): every particle appends, in
+// slot order, its pairs with partners of higher index (a warp's particles
+// contiguously, one atomic per warp), each stored from the particle that comes first
+// in it (list bit), and records the pair in both particles' slots.  The order
 // of the pairs in the list depends on scheduling; nothing computed from a pair does.
 __device__ __forceinline__ void pair_fill_body(const DevState& st, bool force, bool current,
                                                int P_CAP) {
@@ -390,10 +391,16 @@ __device__ __forceinline__ void pair_fill_body(const DevState& st, bool force, b
        i += (int64_t)gridDim.x * blockDim.x) {
     const bool valid = i < N;
     const int ni = valid ? nn[i] : 0;
-    uint32_t own = 0;
-    for (int k = 0; k < ni; ++k)
-      if (nbr_first(nbr[(int64_t)k * N + i])) own |= 1u << k;
-    if (valid) st.fmask[i] = own;
+    // first: the pairs this particle comes first in (evaluation order); own: the
+    // pairs it appends, those with a partner of higher index, so each particle's
+    // pairs sit next to those of its neighbours in the (cell-sorted) order
+    uint32_t own = 0, first = 0;
+    for (int k = 0; k < ni; ++k) {
+      const int32_t e = nbr[(int64_t)k * N + i];
+      if (nbr_first(e)) first |= 1u << k;
+      if (nbr_index(e) > (int32_t)i) own |= 1u << k;
+    }
+    if (valid) st.fmask[i] = first;
     const int cnt = __popc(own);
     int incl = cnt;
 #pragma unroll
@@ -425,7 +432,8 @@ __device__ __forceinline__ void pair_fill_body(const DevState& st, bool force, b
         atomicCAS(&st.ctl->error, 0, -9);
         break;
       }
-      st.pairs[m] = make_int4((int)i, k, j, k2);
+      // the pair from the particle that comes first in it
+      st.pairs[m] = ((first >> k) & 1u) ? make_int4((int)i, k, j, k2) : make_int4(j, k2, (int)i, k);
       st.pid[(int64_t)i * P_CAP + k] = (int32_t)m;
       st.pid[(int64_t)j * P_CAP + k2] = (int32_t)m;
       ++m;

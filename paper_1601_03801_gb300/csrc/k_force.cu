@@ -402,32 +402,56 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
       st.amask[N + i] = 0u;
     }
     live = mc | ml;
+    // two slots per round: their record loads are issued together, then added in
+    // slot order
     while (live) {
-      const int k = __ffs(live) - 1;
-      live &= live - 1;
-      const int32_t m = pid[k];
-      if ((uint64_t)(uint32_t)m >= (uint64_t)st.pcap) continue;
-      const Quad<F>* r = prec + 3 * (int64_t)m;
-      const bool fi = (first >> k) & 1u;
-      if ((mc >> k) & 1u) {
-        // the force on the partner is minus the force on the first particle
-        const Quad<F> q0 = ldq(r), q1 = ldq(r + 1);
-        if (fi) {
-          fc.x += q0.a; fc.y += q0.b; fc.z += q0.c;
-          tq.x += q0.d; tq.y += q1.a; tq.z += q1.b;
-        } else {
-          const Quad<F> q2 = ldq(r + 2);
-          fc.x += -q0.a; fc.y += -q0.b; fc.z += -q0.c;
-          tq.x += q1.c; tq.y += q1.d; tq.z += q2.a;
+      int ks[2];
+      int cnt = 0;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        ks[u] = 0;
+        if (live) {
+          ks[u] = __ffs(live) - 1;
+          live &= live - 1;
+          cnt = u + 1;
         }
-        if (INTEGRATE) nmask |= 1u << k;
       }
-      if ((ml >> k) & 1u) {
-        const Quad<F> q2 = ldq(r + 2);
-        if (fi) {
-          fl.x += q2.b; fl.y += q2.c; fl.z += q2.d;
-        } else {
-          fl.x += -q2.b; fl.y += -q2.c; fl.z += -q2.d;
+      Quad<F> q[2][3];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int32_t m = u < cnt ? pid[ks[u]] : 0;
+        const bool ok = u < cnt && (uint64_t)(uint32_t)m < (uint64_t)st.pcap;
+        const Quad<F>* r = prec + 3 * (int64_t)(ok ? m : 0);
+        q[u][0] = ldq(r);
+        q[u][1] = ldq(r + 1);
+        q[u][2] = ldq(r + 2);
+        if (!ok) ks[u] = -1;
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (u >= cnt || ks[u] < 0) continue;
+        const int k = ks[u];
+        const bool fi = (first >> k) & 1u;
+        const Quad<F>& q0 = q[u][0];
+        const Quad<F>& q1 = q[u][1];
+        const Quad<F>& q2 = q[u][2];
+        if ((mc >> k) & 1u) {
+          // the force on the partner is minus the force on the first particle
+          if (fi) {
+            fc.x += q0.a; fc.y += q0.b; fc.z += q0.c;
+            tq.x += q0.d; tq.y += q1.a; tq.z += q1.b;
+          } else {
+            fc.x += -q0.a; fc.y += -q0.b; fc.z += -q0.c;
+            tq.x += q1.c; tq.y += q1.d; tq.z += q2.a;
+          }
+          if (INTEGRATE) nmask |= 1u << k;
+        }
+        if ((ml >> k) & 1u) {
+          if (fi) {
+            fl.x += q2.b; fl.y += q2.c; fl.z += q2.d;
+          } else {
+            fl.x += -q2.b; fl.y += -q2.c; fl.z += -q2.d;
+          }
         }
       }
     }
