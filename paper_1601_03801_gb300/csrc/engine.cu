@@ -40,6 +40,7 @@ struct sedi_handle {
   std::vector<void*> part_allocs;  // per-particle buffers
   std::vector<void*> mesh_allocs;
   int64_t since_set = 0;               // substeps since the particles were set
+  bool is_bed = false;                 // a bed of an ensemble (stepped by the ensemble)
   SmoothZ zs{};                        // graded z mesh: smoothing tables (device) and bounds
   void* qfix = nullptr;   // [7][C] int64 (plain: float phi)
   void* phi = nullptr;    // [8][C] smoothing word
@@ -474,8 +475,9 @@ int alloc_particles(sedi_handle* h, int64_t N, double rmax) {
     if ((rc = dmalloc(h, h->part_allocs, &st.hist[b], q * cap * N))) return rc;
     if ((rc = dmalloc(h, h->part_allocs, (void**)&st.cmask[b], 4 * N))) return rc;
   }
-  if (form != FORM_FP64) {
-    // pair list (substep variant SUBSTEP_PAIRS): every listed pair once, cap N / 2 at most
+  if (form != FORM_FP64 && !h->is_bed) {
+    // pair list (substep variant SUBSTEP_PAIRS; not for ensemble beds, which the
+    // ensemble steps with the per-particle loop): every listed pair once, cap N / 2 at most
     st.pcap = cap * N / 2 + 1;
     if ((rc = dmalloc(h, h->part_allocs, (void**)&st.pairs, 16 * st.pcap)) ||
         (rc = dmalloc(h, h->part_allocs, (void**)&st.pid, 4 * cap * N)) ||
@@ -651,9 +653,11 @@ std::string tune_key(sedi_handle* h) {
     dmin = std::min(dmin, d);
     dmax = std::max(dmax, d);
   }
+  // the force terms that change a pair's cost belong to the workload too
   char buf[512];
-  std::snprintf(buf, sizeof(buf), "%s sm%d|N=%lld|d=%.3e..%.3e|form=%d", prop.name,
-                prop.multiProcessorCount, (long long)h->N, dmin, dmax, h->form);
+  std::snprintf(buf, sizeof(buf), "%s sm%d|N=%lld|d=%.3e..%.3e|form=%d|law=%d|lub=%d|fluid=%d%d%d",
+                prop.name, prop.multiProcessorCount, (long long)h->N, dmin, dmax, h->form,
+                h->prm.contact_law, h->P.lubrication, h->P.drag, h->P.pressure_grad, h->P.added_mass);
   return buf;
 }
 
@@ -891,6 +895,7 @@ int sedi_create(const sedi_params* p, sedi_handle** out) {
         return rc;
       }
       h->beds[b]->stream = h->stream;
+      h->beds[b]->is_bed = true;
     }
   }
   *out = h;
@@ -947,6 +952,7 @@ int sedi_set_bed(sedi_handle* h, int32_t bed, const double lo[3], const double h
   const int rc = sedi_create(&q, &nb);
   if (rc) return fail(h, rc, "bed %d: invalid box or mesh", bed);
   nb->stream = h->stream;
+  nb->is_bed = true;
   sedi_handle* old = h->beds[bed];
   old->stream = old->own;
   cudaStreamSynchronize(h->stream);
@@ -1629,6 +1635,8 @@ int sedi_compute_forces(sedi_handle* h, int32_t bed, double* fc, double* fl, dou
   // lists must cover the current positions
   launch_check(h->st, h->P, 0ull, 0, h->stream);
   launch_rebuild(h->form, h->st, h->P, 0, false, h->stream);
+  // pair-mode springs (ensembles, variant 8) to both slots: any variant may evaluate
+  launch_spring_sync(h->form, h->st, h->stream);
   launch_substep(h->form, h->st, h->mesh, h->P, 0, false, h->variant, 0ull, 0, h->stream);
   // fdbg is in sorted order: scatter to caller order through the host
   std::vector<double> dbg(12 * N);

@@ -248,7 +248,7 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
 // go to the pair record, the spring to both particles' slots.  The pairs run
 // independently, so the grid-stride order does not change any result.
 template <int FORM, bool INTEGRATE>
-__global__ void __launch_bounds__(128, 6) k_pair_forces(DevState st, DevParams P, int sub_off) {
+__device__ __forceinline__ void pair_forces_body(const DevState& st, const DevParams& P, int sub_off) {
   using S = typename Traits<FORM>::S;
   using F = typename Traits<FORM>::F;
   using NS = Num<S>;
@@ -304,6 +304,11 @@ __global__ void __launch_bounds__(128, 6) k_pair_forces(DevState st, DevParams P
       stq(r + 2, Quad<F>{tb.z, l.x, l.y, l.z});
     }
   }
+}
+
+template <int FORM, bool INTEGRATE>
+__global__ void __launch_bounds__(128, 6) k_pair_forces(DevState st, DevParams P, int sub_off) {
+  pair_forces_body<FORM, INTEGRATE>(st, P, sub_off);
 }
 
 // BS threads per block, at least MINB resident blocks per SM (which caps the

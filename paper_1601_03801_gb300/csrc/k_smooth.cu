@@ -109,6 +109,23 @@ struct Wide<double> {
   __device__ static double ld(const double* p) { return __ldcg(p); }
 };
 
+// The operator coefficients in the wide and the narrow word (converted on the host,
+// so the kernels run no FP64 conversion per cell).
+template <class T>
+__device__ __forceinline__ T coef_w(const SmoothSpec& sp, int a);
+template <>
+__device__ __forceinline__ dd coef_w<dd>(const SmoothSpec& sp, int a) {
+  return dd{sp.coef_hi[a], sp.coef_lo[a]};
+}
+template <>
+__device__ __forceinline__ float coef_w<float>(const SmoothSpec& sp, int a) {
+  return sp.coef_hi[a];
+}
+template <>
+__device__ __forceinline__ double coef_w<double>(const SmoothSpec& sp, int a) {
+  return sp.coef[a];
+}
+
 // Loads of words written by other blocks of the same launch go to L2 (ld.cg), so
 // no stale L1 line is read after a grid barrier.
 __device__ __forceinline__ int ldi(const int* p) { return __ldcg(p); }
@@ -356,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
         Acc v[kMaxF][kQ];
         V8<N> rn;
         const SmoothSpec& sp = md.sp[ph];
-        const T cf[3] = {W::from_d(sp.coef[0]), W::from_d(sp.coef[1]), W::from_d(sp.coef[2])};
+        const T cf[3] = {coef_w<T>(sp, 0), coef_w<T>(sp, 1), coef_w<T>(sp, 2)};
         const Stencil sc = stencil_of(md, in ? c : 0);
         T czm{}, czp{};
         Acc wz = Acc(1);
@@ -510,9 +527,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
           }
           if (!any) continue;
           const SmoothSpec& sp = md.sp[ph];
-          const N cfn[3] = {(N)sp.coef[0], (N)sp.coef[1], (N)sp.coef[2]};
-          const N c1 = (N)sp.cheb[0][j - 1], c2 = (N)sp.cheb[1][j - 1];
-          const N inv_theta = (N)(1.0 / sp.theta);
+          const N cfn[3] = {coef_w<N>(sp, 0), coef_w<N>(sp, 1), coef_w<N>(sp, 2)};
+          N c1, c2, inv_theta;
+          if constexpr (sizeof(N) == 4) {
+            c1 = sp.chebf[0][j - 1];
+            c2 = sp.chebf[1][j - 1];
+            inv_theta = sp.inv_theta_f;
+          } else {
+            c1 = (N)sp.cheb[0][j - 1];
+            c2 = (N)sp.cheb[1][j - 1];
+            inv_theta = (N)(1.0 / sp.theta);
+          }
           const Stencil sc = stencil_of(md, c);
           // step 1 reads the narrow residual (d[0]) and forms d0 = (r - s) / theta at
           // every stencil point; later steps read the previous direction
@@ -722,9 +747,11 @@ __global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
     for (int m = 0; m < a.n_tau; ++m) {
       const int ph = (a.scheme == TAU_BDF2 && m > 0) ? 1 : 0;
       const SmoothSpec& sp = md.sp[ph];
-      const T cf[3] = {W::from_d(sp.coef[0]), W::from_d(sp.coef[1]), W::from_d(sp.coef[2])};
-      const N cfn[3] = {(N)sp.coef[0], (N)sp.coef[1], (N)sp.coef[2]};
-      const N inv_theta = (N)(1.0 / sp.theta);
+      const T cf[3] = {coef_w<T>(sp, 0), coef_w<T>(sp, 1), coef_w<T>(sp, 2)};
+      const N cfn[3] = {coef_w<N>(sp, 0), coef_w<N>(sp, 1), coef_w<N>(sp, 2)};
+      N inv_theta;
+      if constexpr (sizeof(N) == 4) inv_theta = sp.inv_theta_f;
+      else inv_theta = (N)(1.0 / sp.theta);
       // ---- b (global) from the previous pseudo-step's result; x (or the guess)
       //      into shared memory
       for (int l = threadIdx.x; l < ncell; l += kClThreads) {
@@ -789,10 +816,12 @@ __global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
         }
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
-          double t = (double)v[q];
+          // warp sums in the accumulation word (as the grid solver's units), the
+          // CTA's sum of the 32 warp sums in FP64
+          Acc t = v[q];
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-          if (lane == 0) s_red[wid][q] = t;
+          if (lane == 0) s_red[wid][q] = (double)t;
         }
         __syncthreads();
         // this CTA's sums, pushed into every CTA's shared memory (stores do not wait)
@@ -864,7 +893,14 @@ __global__ void __launch_bounds__(kClThreads, 1) k_smooth_cl(SmoothBatchDev a) {
         for (int j = 1; j <= k; ++j) {
           N* Dold = (j & 1) ? dA : dB;
           N* Dnew = (j & 1) ? dB : dA;
-          const N c1s = (N)sp.cheb[0][j - 1], c2s = (N)sp.cheb[1][j - 1];
+          N c1s, c2s;
+          if constexpr (sizeof(N) == 4) {
+            c1s = sp.chebf[0][j - 1];
+            c2s = sp.chebf[1][j - 1];
+          } else {
+            c1s = (N)sp.cheb[0][j - 1];
+            c2s = (N)sp.cheb[1][j - 1];
+          }
           // One step over this CTA's columns.  FIRST (step 1) reads the narrow true
           // residual r and forms d0 = (r - s) / theta at every point it touches; x and
           // the recursion take the shift.  FULL: all four in-plane faces exist (the
@@ -1014,13 +1050,18 @@ size_t smooth_batch_bytes(int64_t B, int64_t U) {
 // the Chebyshev coefficients of steps 1..kMaxStepsRound (the same in every round):
 // rho_1 = 1 / sigma1, rho' = 1 / (2 sigma1 - rho), c1 = rho' rho, c2 = 2 rho' / delta.
 static void smooth_spec(const double coef[3], double scale, double zmax, SmoothSpec* sp) {
-  for (int k = 0; k < 3; ++k) sp->coef[k] = scale * coef[k];
+  for (int k = 0; k < 3; ++k) {
+    sp->coef[k] = scale * coef[k];
+    sp->coef_hi[k] = (float)sp->coef[k];
+    sp->coef_lo[k] = (float)(sp->coef[k] - (double)sp->coef_hi[k]);
+  }
   double lmax = zmax > 0.0 ? 1.0 + 4.0 * (sp->coef[0] + sp->coef[1]) + 2.0 * zmax
                            : 1.0 + 4.0 * (sp->coef[0] + sp->coef[1] + sp->coef[2]);
   if (lmax < 1.0 + 1e-12) lmax = 1.0 + 1e-12;
   sp->theta = 0.5 * (lmax + 1.0);
   sp->delta = 0.5 * (lmax - 1.0);
   sp->sigma1 = sp->theta / sp->delta;
+  sp->inv_theta_f = (float)(1.0 / sp->theta);
   const double sq = std::sqrt(lmax);
   sp->sig = (sq - 1.0) / (sq + 1.0);
   double rho = 1.0 / sp->sigma1;
@@ -1028,6 +1069,8 @@ static void smooth_spec(const double coef[3], double scale, double zmax, SmoothS
     const double rho_new = 1.0 / (2.0 * sp->sigma1 - rho);
     sp->cheb[0][j] = rho_new * rho;
     sp->cheb[1][j] = 2.0 * rho_new / sp->delta;
+    sp->chebf[0][j] = (float)sp->cheb[0][j];
+    sp->chebf[1][j] = (float)sp->cheb[1][j];
     rho = rho_new;
   }
 }

@@ -134,6 +134,9 @@ struct SmoothSpec {
   double coef[3];
   double theta, delta, sigma1, sig;  // spectrum [1, lmax]: centre, half width, ratio, rate
   double cheb[2][kMaxStepsRound];    // c1, c2 of Chebyshev steps 1..kMaxStepsRound of a round
+  float chebf[2][kMaxStepsRound];    // the same rounded to FP32 (narrow recursion)
+  float inv_theta_f;                 // 1 / theta in FP32
+  float coef_hi[3], coef_lo[3];      // coef as an FP32 pair: hi = fl32(c), lo = fl32(c - hi)
 };
 
 // The same, as the kernel sees it (device table, built by launch_smooth_batch).

@@ -301,7 +301,10 @@ def settle_bed(prm, parts, substeps=40_000, chunk=2000, log=None):
     if os.path.exists(path):
         z = np.load(path)
         return dict(parts, x=z["x"], v=np.zeros_like(z["x"]), w=np.zeros_like(z["x"]))
-    g = sedi.Sedi(dict(prm, precision_form="split", lubrication=0, added_mass=0, restitution=0.3))
+    # a fixed launch shape: the prep run's early, loose state is not the workload the
+    # autotuner should rank the shapes on
+    g = sedi.Sedi(dict(prm, precision_form="split", lubrication=0, added_mass=0, restitution=0.3,
+                       substep_variant=5))
     g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
     done = 0
     while done < substeps:
