@@ -37,6 +37,7 @@ WORKLOAD = ("sheared sediment bed: 200,000 lognormal spheres (median 0.5 mm, sig
             "64x32x64 mesh, Hertz-Mindlin + lubrication + drag + added mass, diffusion "
             "averaging b=3 d50; step = 20 substeps (dt=1e-6 s) + 1 averaging")
 PROFILE_FILE = os.path.join(ROOT, "profiles", "k_substep_bed200k.md")
+PAIRS_PROFILE_FILE = os.path.join(ROOT, "profiles", "k_pair_forces_gather_bed200k.md")
 KERNEL_SOURCES = ["paper_1601_03801_gb300/csrc/k_force.cu", "paper_1601_03801_gb300/csrc/fluid.cuh",
                   "paper_1601_03801_gb300/csrc/common.cuh", "paper_1601_03801_gb300/csrc/dd.cuh"]
 
@@ -59,12 +60,14 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic():
-    """DRAM bytes per particle-substep of the fused substep kernel from the committed
-    ncu summary, if it was taken on the current kernel source."""
-    if not os.path.exists(PROFILE_FILE):
+def measured_traffic(variant=None):
+    """DRAM bytes per particle-substep of the substep launch (the fused kernel, or the
+    pair-force and gather kernels of the pair list) from the committed ncu summary, if
+    it was taken on the current kernel source."""
+    path = PAIRS_PROFILE_FILE if variant == PAIRS_VARIANT else PROFILE_FILE
+    if not os.path.exists(path):
         return None, None
-    txt = open(PROFILE_FILE).read()
+    txt = open(path).read()
     m = re.search(r"dram_bytes_per_particle_substep:\s*([0-9.eE+-]+)", txt)
     k = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
     if not m or not k or k.group(1) != kernel_hash():
@@ -223,7 +226,7 @@ def gpu_arm(args):
     sub_ms = (t1["substep_ms"] - t0["substep_ms"]) / max(1.0, t1["substep_n"] - t0["substep_n"])
     achieved = per_particle * n / (sub_ms / 1e3) / 1e9
     peak, peak_kind = peaks()
-    traffic_pp, _ = measured_traffic()
+    traffic_pp, _ = measured_traffic(st1["substep_variant"])
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_source": peak_kind,
             "traffic": None if traffic_pp is None else round(traffic_pp * n),

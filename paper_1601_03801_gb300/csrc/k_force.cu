@@ -307,7 +307,7 @@ __device__ __forceinline__ void pair_forces_body(const DevState& st, const DevPa
 }
 
 template <int FORM, bool INTEGRATE>
-__global__ void __launch_bounds__(128, 6) k_pair_forces(DevState st, DevParams P, int sub_off) {
+__global__ void __launch_bounds__(128, 8) k_pair_forces(DevState st, DevParams P, int sub_off) {
   pair_forces_body<FORM, INTEGRATE>(st, P, sub_off);
 }
 
@@ -777,7 +777,7 @@ static void launch_pairs(const DevState& st, const DevMesh& mesh, const DevParam
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int64_t g = (st.pcap + 127) / 128;
-  const int64_t gmax = (int64_t)nsm * 6 * 4;
+  const int64_t gmax = (int64_t)nsm * 8 * 4;
   if (g > gmax) g = gmax;
   if (g < 1) g = 1;
   const int64_t grid = (st.N + 127) / 128;
