@@ -128,18 +128,24 @@ typedef struct sedi_params {
   int32_t precision_form;                  /* SEDI_FORM_* [SPLIT] */
   int32_t nbr_capacity;                    /* listed neighbours per particle, <= 32 [32] */
   int32_t use_graphs;                      /* capture substeps in CUDA graphs [1] */
-  int32_t substep_variant;                 /* launch shape of the fused substep kernel:
-                                              -1 = autotuned at the first sedi_step [-1];
+  int32_t substep_variant;                 /* launch shape of the substep:
+                                              -1 = autotuned [-1]: the per-particle loop
+                                              (5) runs until 200 substeps after the
+                                              particles were set, then every shape is
+                                              timed on integrating substeps (state
+                                              restored) and the fastest kept;
                                               0: 128 threads, 6 blocks/SM; 1: 64 x 12;
                                               2: 256 x 3; 3: 128 x 8; 4: 128 x 5, all with
                                               the warp-cooperative pair phase; 5: 128 x 6,
                                               6: 128 x 8, 7: 64 x 12 with a per-particle
-                                              pair loop.  With lift or lub_tangential on
-                                              the loop at 128 x 6 runs.  The split
-                                              form gives bit-identical results across
-                                              variants, the plain form agrees to FP32
-                                              rounding.  The FP64 parity form always runs
-                                              the loop. */
+                                              pair loop; 8: the pair list (each listed
+                                              pair evaluated once by one thread, then a
+                                              per-particle gather; two launches).  With
+                                              lift or lub_tangential on the loop at
+                                              128 x 6 runs.  The split form gives
+                                              bit-identical results across variants, the
+                                              plain form agrees to FP32 rounding.  The
+                                              FP64 parity form always runs the loop. */
   int32_t n_beds;                          /* independent beds in this handle, 1..1024
                                               (see "Ensembles" below) [1] */
   int32_t profile;                         /* record CUDA events around each phase
