@@ -41,6 +41,7 @@ struct sedi_handle {
   std::vector<void*> mesh_allocs;
   int64_t since_set = 0;               // substeps since the particles were set
   bool is_bed = false;                 // a bed of an ensemble (stepped by the ensemble)
+  double* u_stage = nullptr;           // FP64 fluid velocity on the device (vorticity)
   SmoothZ zs{};                        // graded z mesh: smoothing tables (device) and bounds
   void* qfix = nullptr;   // [7][C] int64 (plain: float phi)
   void* phi = nullptr;    // [8][C] smoothing word
@@ -429,20 +430,23 @@ int upload_mesh(sedi_handle* h, bool velocity = true) {
     CK(cudaMemcpyAsync(h->mesh.ufe, uf.data(), 16 * C, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->mesh.gfl, gf.data(), 16 * C, cudaMemcpyHostToDevice, h->stream));
   }
-  if (!velocity) {
+  if (!velocity || !h->P.lift) {
+    // the vorticity feeds the lift force only
     CK(cudaStreamSynchronize(h->stream));
     return 0;
   }
-  // vorticity of U for the lift force, from the FP64 velocities
-  double* Ud = nullptr;
-  CK(cudaMalloc((void**)&Ud, 24 * C));
-  cudaError_t e = cudaMemcpyAsync(Ud, h->U.data(), 24 * C, cudaMemcpyHostToDevice, h->stream);
+  // vorticity of U for the lift force, from the FP64 velocities (staged in a buffer
+  // kept with the mesh)
+  if (!h->u_stage) {
+    int rc = dmalloc(h, h->mesh_allocs, (void**)&h->u_stage, 24 * C);
+    if (rc) return rc;
+  }
+  cudaError_t e = cudaMemcpyAsync(h->u_stage, h->U.data(), 24 * C, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) {
-    launch_curl(form, Ud, h->P, h->mesh, h->stream);
+    launch_curl(form, h->u_stage, h->P, h->mesh, h->stream);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  cudaFree(Ud);
   if (e != cudaSuccess) return fail(h, SEDI_ECUDA, "vorticity of the fluid velocity: %s", cudaGetErrorString(e));
   return 0;
 }
@@ -871,6 +875,7 @@ int sedi_create(const sedi_params* p, sedi_handle** out) {
     sedi_destroy(h);
     return rc;
   }
+  cudaMemset(h->mesh.wfl, 0, fq * C);  // no vorticity until a velocity field with lift
   if ((rc = build_zgrid(h))) {
     sedi_destroy(h);
     return rc;
