@@ -41,7 +41,9 @@ struct sedi_handle {
   std::vector<void*> mesh_allocs;
   int64_t since_set = 0;               // substeps since the particles were set
   bool is_bed = false;                 // a bed of an ensemble (stepped by the ensemble)
-  double* u_stage = nullptr;           // FP64 fluid velocity on the device (vorticity)
+  double* fdev = nullptr;              // FP64 U, grad p, DU/Dt [3][C][3] on the device
+  double* edev = nullptr;              // FP64 staging of eps_s [C]
+  bool fluid_host_stale = false;       // host copies (U, gp, du, eps) behind the device
   SmoothZ zs{};                        // graded z mesh: smoothing tables (device) and bounds
   void* qfix = nullptr;   // [7][C] int64 (plain: float phi)
   void* phi = nullptr;    // [8][C] smoothing word
@@ -85,7 +87,6 @@ struct sedi_handle {
   EnsLaunch ens{};
   bool ens_dirty = true;          // a bed's buffers changed: rebuild the table
   bool ens_fresh = false;         // the batched averaging is newer than the last step
-  bool eps_dev_newer = false;     // (bed handle) device eps newer than the host copy
 };
 
 namespace {
@@ -403,51 +404,17 @@ int build_zgrid(sedi_handle* h) {
   return 0;
 }
 
+// Mesh words of the fluid fields from the FP64 fields kept on the device (fdev:
+// U, grad p, DU/Dt); the vorticity too when the lift is on and U changed.
 int upload_mesh(sedi_handle* h, bool velocity = true) {
   const int64_t C = h->P.C;
-  const int form = h->form;
   const sedi_params& p = h->prm;
-  std::vector<double> ufe(4 * C), gfl(4 * C, 0.0);
-  for (int64_t c = 0; c < C; ++c) {
-    for (int a = 0; a < 3; ++a) {
-      ufe[4 * c + a] = h->U[3 * c + a];
-      double g = 0.0;
-      if (p.pressure_grad) g -= h->gp_default ? p.rho_f * p.g[a] : h->gp[3 * c + a];
-      if (p.added_mass) g += p.c_add * p.rho_f * h->du[3 * c + a];
-      gfl[4 * c + a] = g;
-    }
-    ufe[4 * c + 3] = h->eps[c];
-  }
-  if (form == FORM_FP64) {
-    CK(cudaMemcpyAsync(h->mesh.ufe, ufe.data(), 32 * C, cudaMemcpyHostToDevice, h->stream));
-    CK(cudaMemcpyAsync(h->mesh.gfl, gfl.data(), 32 * C, cudaMemcpyHostToDevice, h->stream));
-  } else {
-    std::vector<float> uf(4 * C), gf(4 * C);
-    for (int64_t k = 0; k < 4 * C; ++k) {
-      uf[k] = (float)ufe[k];
-      gf[k] = (float)gfl[k];
-    }
-    CK(cudaMemcpyAsync(h->mesh.ufe, uf.data(), 16 * C, cudaMemcpyHostToDevice, h->stream));
-    CK(cudaMemcpyAsync(h->mesh.gfl, gf.data(), 16 * C, cudaMemcpyHostToDevice, h->stream));
-  }
-  if (!velocity || !h->P.lift) {
-    // the vorticity feeds the lift force only
-    CK(cudaStreamSynchronize(h->stream));
-    return 0;
-  }
-  // vorticity of U for the lift force, from the FP64 velocities (staged in a buffer
-  // kept with the mesh)
-  if (!h->u_stage) {
-    int rc = dmalloc(h, h->mesh_allocs, (void**)&h->u_stage, 24 * C);
-    if (rc) return rc;
-  }
-  cudaError_t e = cudaMemcpyAsync(h->u_stage, h->U.data(), 24 * C, cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) {
-    launch_curl(form, h->u_stage, h->P, h->mesh, h->stream);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (e != cudaSuccess) return fail(h, SEDI_ECUDA, "vorticity of the fluid velocity: %s", cudaGetErrorString(e));
+  const double rho_g[3] = {p.rho_f * p.g[0], p.rho_f * p.g[1], p.rho_f * p.g[2]};
+  launch_fluid_prep(h->form, h->fdev, h->fdev + 3 * C, h->fdev + 6 * C, h->gp_default ? 1 : 0,
+                    p.c_add * p.rho_f, rho_g, h->P, h->mesh, h->stream);
+  if (velocity && h->P.lift) launch_curl(h->form, h->fdev, h->P, h->mesh, h->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
   return 0;
 }
 
@@ -603,20 +570,18 @@ int need_particles(sedi_handle* h) {
     }                                                                                     \
   } while (0)
 
-// The smoothed solid fraction of an ensemble bed lives on the device only: bring
-// the host copy (used when the mesh fields are uploaded again, and by checkpoints)
-// up to date.
-int refresh_eps_host(sedi_handle* h) {
-  if (!h->eps_dev_newer) return 0;
+// The fluid fields and the drag's solid fraction live on the device; the host
+// copies serve checkpoints only and are brought up to date here.
+int refresh_fluid_host(sedi_handle* h) {
+  if (!h->fluid_host_stale) return 0;
   const int64_t C = h->P.C;
-  if (h->form == FORM_FP64) {
-    CK(cudaMemcpy2D(h->eps.data(), 8, (const char*)h->mesh.ufe + 24, 32, 8, C, cudaMemcpyDeviceToHost));
-  } else {
-    std::vector<float> e(C);
-    CK(cudaMemcpy2D(e.data(), 4, (const char*)h->mesh.ufe + 12, 16, 4, C, cudaMemcpyDeviceToHost));
-    for (int64_t c = 0; c < C; ++c) h->eps[c] = e[c];
-  }
-  h->eps_dev_newer = false;
+  launch_eps_io(h->form, h->edev, h->mesh, C, 0, h->stream);
+  CK(cudaMemcpyAsync(h->U.data(), h->fdev, 24 * C, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->gp.data(), h->fdev + 3 * C, 24 * C, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->du.data(), h->fdev + 6 * C, 24 * C, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->eps.data(), h->edev, 8 * C, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->fluid_host_stale = false;
   return 0;
 }
 
@@ -869,6 +834,8 @@ int sedi_create(const sedi_params* p, sedi_handle** out) {
   if ((rc = dmalloc(h, h->mesh_allocs, &h->mesh.ufe, fq * C)) ||
       (rc = dmalloc(h, h->mesh_allocs, &h->mesh.gfl, fq * C)) ||
       (rc = dmalloc(h, h->mesh_allocs, &h->mesh.wfl, fq * C)) ||
+      (rc = dmalloc(h, h->mesh_allocs, (void**)&h->fdev, 72 * C)) ||
+      (rc = dmalloc(h, h->mesh_allocs, (void**)&h->edev, 8 * C)) ||
       (rc = dmalloc(h, h->mesh_allocs, &h->qfix, 8 * 7 * C)) ||
       (rc = dmalloc(h, h->mesh_allocs, &h->phi, 8 * 8 * C)) ||
       (rc = dmalloc(h, h->mesh_allocs, (void**)&h->iters_dev, 4 * 8))) {
@@ -876,6 +843,8 @@ int sedi_create(const sedi_params* p, sedi_handle** out) {
     return rc;
   }
   cudaMemset(h->mesh.wfl, 0, fq * C);  // no vorticity until a velocity field with lift
+  cudaMemset(h->mesh.ufe, 0, fq * C);  // U = 0, eps_s = 0
+  cudaMemset(h->fdev, 0, 72 * C);
   if ((rc = build_zgrid(h))) {
     sedi_destroy(h);
     return rc;
@@ -1051,27 +1020,18 @@ int sedi_set_fluid(sedi_handle* h, int32_t bed, const int32_t ncell[3], const do
   h->err.clear();
   ENS_FORWARD(sedi_set_fluid(sub, 0, ncell, U, grad_p, DUDt, mem));
   if (bed != 0) return fail(h, SEDI_EINVAL, "bed %d out of range", bed);
-  if (int rc0 = refresh_eps_host(h)) return rc0;
   if (!ncell || ncell[0] != h->prm.ncell[0] || ncell[1] != h->prm.ncell[1] || ncell[2] != h->prm.ncell[2])
     return fail(h, SEDI_EINVAL, "ncell must equal params.ncell");
   const int64_t C = h->P.C;
-  auto get = [&](const double* src, std::vector<double>& dst) -> int {
-    if (mem == SEDI_MEM_DEVICE) {
-      CK(cudaMemcpy(dst.data(), src, 24 * C, cudaMemcpyDeviceToHost));
-    } else {
-      std::memcpy(dst.data(), src, 24 * C);
-    }
-    return 0;
-  };
-  int rc = 0;
-  if (U) rc = get(U, h->U);
-  else std::fill(h->U.begin(), h->U.end(), 0.0);
-  if (rc) return rc;
+  // the caller's fields straight to the device (a pinned host buffer copies by DMA)
+  const cudaMemcpyKind kind = mem == SEDI_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (U) CK(cudaMemcpyAsync(h->fdev, U, 24 * C, kind, h->stream));
+  else CK(cudaMemsetAsync(h->fdev, 0, 24 * C, h->stream));
   h->gp_default = grad_p == nullptr;
-  if (grad_p && (rc = get(grad_p, h->gp))) return rc;
-  if (DUDt) rc = get(DUDt, h->du);
-  else std::fill(h->du.begin(), h->du.end(), 0.0);
-  if (rc) return rc;
+  if (grad_p) CK(cudaMemcpyAsync(h->fdev + 3 * C, grad_p, 24 * C, kind, h->stream));
+  if (DUDt) CK(cudaMemcpyAsync(h->fdev + 6 * C, DUDt, 24 * C, kind, h->stream));
+  else CK(cudaMemsetAsync(h->fdev + 6 * C, 0, 24 * C, h->stream));
+  h->fluid_host_stale = true;
   return upload_mesh(h);
 }
 
@@ -1080,14 +1040,14 @@ int sedi_set_eps(sedi_handle* h, int32_t bed, const double* eps, int32_t mem) {
   h->err.clear();
   ENS_FORWARD(sedi_set_eps(sub, 0, eps, mem));
   if (bed != 0) return fail(h, SEDI_EINVAL, "bed %d out of range", bed);
-  h->eps_dev_newer = false;
   const int64_t C = h->P.C;
-  if (mem == SEDI_MEM_DEVICE) {
-    CK(cudaMemcpy(h->eps.data(), eps, 8 * C, cudaMemcpyDeviceToHost));
-  } else {
-    std::memcpy(h->eps.data(), eps, 8 * C);
-  }
-  return upload_mesh(h, false);
+  const cudaMemcpyKind kind = mem == SEDI_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(h->edev, eps, 8 * C, kind, h->stream));
+  launch_eps_io(h->form, h->edev, h->mesh, C, 1, h->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  h->fluid_host_stale = true;
+  return 0;
 }
 
 static int ens_step(sedi_handle* h, int n);
@@ -1450,7 +1410,7 @@ static int ens_average(sedi_handle* h) {
     sb->stats.cg_iterations += sum;
     h->stats.cg_iterations += sum;
     sb->stats.averages += 1;
-    sb->eps_dev_newer = true;
+    sb->fluid_host_stale = true;
     if (c[b].deposit_range) {
       range_bed = b;
       int z = 0;
@@ -1481,9 +1441,7 @@ static int average_outputs(sedi_handle* h, double* eps, double* Us, double* F, i
   if (Us && (rc = copy_out(h, Us, du, 24 * C, mem))) return rc;
   if (F && (rc = copy_out(h, F, dF, 24 * C, mem))) return rc;
   if ((rc = sync_status(h))) return rc;
-  // keep the host copy of the drag's solid fraction in step (checkpoints)
-  CK(cudaMemcpy(h->eps.data(), de, 8 * C, cudaMemcpyDeviceToHost));
-  h->eps_dev_newer = false;
+  h->fluid_host_stale = true;
   return 0;
 }
 
@@ -1535,8 +1493,7 @@ int sedi_average(sedi_handle* h, int32_t bed, double* eps, double* Us, double* F
   if (F && (rc = copy_out(h, F, dF, 24 * C, mem))) return rc;
   h->stats.averages += 1;
   rc = smooth_status(h, 7);
-  // keep the host copy of the drag's solid fraction in step (checkpoints)
-  if (!rc) cudaMemcpy(h->eps.data(), de, 8 * C, cudaMemcpyDeviceToHost);
+  h->fluid_host_stale = true;
   return rc;
 }
 
@@ -1819,7 +1776,7 @@ static int save_to(sedi_handle* h, FILE* f) {
   int rc = need_particles(h);
   if (rc) return rc;
   launch_spring_sync(h->form, h->st, h->stream);  // pair-mode springs to both slots
-  if ((rc = sync_status(h)) || (rc = refresh_eps_host(h))) return rc;
+  if ((rc = sync_status(h)) || (rc = refresh_fluid_host(h))) return rc;
   CkHeader hd{};
   std::memcpy(hd.magic, "SEDICK01", 8);
   hd.version = 1;
@@ -1870,7 +1827,11 @@ static int load_from(sedi_handle* h, FILE* f) {
     rc = fail(h, SEDI_EIO, "read failed");
   if (!rc) {
     h->gp_default = gpd != 0;
-    h->eps_dev_newer = false;
+    // the fluid fields back on the device (the mesh words come with the state below)
+    CK(cudaMemcpy(h->fdev, h->U.data(), 24 * C, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->fdev + 3 * C, h->gp.data(), 24 * C, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->fdev + 6 * C, h->du.data(), 24 * C, cudaMemcpyHostToDevice));
+    h->fluid_host_stale = false;
     double rmax = 0;
     for (double di : d) rmax = std::max(rmax, 0.5 * di);
     h->P.cap = hd.cap;

@@ -342,6 +342,51 @@ __global__ void k_curl(const double* __restrict__ U, DevParams P, const double* 
   }
 }
 
+// Mesh words of the fluid fields (Sec. 2.3): ufe = (U, eps_s) keeps its eps_s, gfl =
+// G = -grad p + C_add rho_f DU/Dt (grad p = rho_f g when none is given), from the FP64
+// fields [C][3] on the device.
+template <class F>
+__global__ void k_fluid_prep(const double* __restrict__ U, const double* __restrict__ gp,
+                             const double* __restrict__ du, int64_t C, int pressure_grad,
+                             int added_mass, int gp_default, double c_add_rho_f, double rgx,
+                             double rgy, double rgz, Quad<F>* __restrict__ ufe,
+                             Quad<F>* __restrict__ gfl) {
+  const double rg[3] = {rgx, rgy, rgz};
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    double g[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double v = 0.0;
+      if (pressure_grad) v -= gp_default ? rg[a] : gp[3 * c + a];
+      if (added_mass) v += c_add_rho_f * du[3 * c + a];
+      g[a] = v;
+    }
+    Quad<F> u = ufe[c];
+    u.a = (F)U[3 * c];
+    u.b = (F)U[3 * c + 1];
+    u.c = (F)U[3 * c + 2];
+    ufe[c] = u;
+    gfl[c] = Quad<F>{(F)g[0], (F)g[1], (F)g[2], F(0)};
+  }
+}
+
+// eps_s of the drag law from FP64 cell values.
+template <class F>
+__global__ void k_eps_in(const double* __restrict__ eps, int64_t C, Quad<F>* __restrict__ ufe) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+       c += (int64_t)gridDim.x * blockDim.x)
+    ufe[c].d = (F)eps[c];
+}
+
+// eps_s of the drag law as FP64 cell values (checkpoints).
+template <class F>
+__global__ void k_eps_out(const Quad<F>* __restrict__ ufe, int64_t C, double* __restrict__ eps) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+       c += (int64_t)gridDim.x * blockDim.x)
+    eps[c] = (double)ufe[c].d;
+}
+
 inline unsigned grid_for(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
   if (g < 1) g = 1;
@@ -358,6 +403,31 @@ void launch_deposit(int form, const DevState& st, const DevMesh& mesh, const Dev
     case FORM_SPLIT: k_deposit<FORM_SPLIT><<<g, 256, 0, s>>>(st, mesh, P, q); break;
     case FORM_PLAIN: k_deposit<FORM_PLAIN><<<g, 256, 0, s>>>(st, mesh, P, q); break;
     default: k_deposit<FORM_FP64><<<g, 256, 0, s>>>(st, mesh, P, q); break;
+  }
+}
+
+void launch_fluid_prep(int form, const double* U, const double* gp, const double* du, int gp_default,
+                       double c_add_rho_f, const double rho_g[3], const DevParams& P,
+                       const DevMesh& mesh, cudaStream_t s) {
+  const unsigned g = grid_for(P.C, 256);
+  if (form == FORM_FP64)
+    k_fluid_prep<double><<<g, 256, 0, s>>>(U, gp, du, P.C, P.pressure_grad, P.added_mass, gp_default,
+                                           c_add_rho_f, rho_g[0], rho_g[1], rho_g[2],
+                                           (Quad<double>*)mesh.ufe, (Quad<double>*)mesh.gfl);
+  else
+    k_fluid_prep<float><<<g, 256, 0, s>>>(U, gp, du, P.C, P.pressure_grad, P.added_mass, gp_default,
+                                          c_add_rho_f, rho_g[0], rho_g[1], rho_g[2],
+                                          (Quad<float>*)mesh.ufe, (Quad<float>*)mesh.gfl);
+}
+
+void launch_eps_io(int form, double* eps, const DevMesh& mesh, int64_t C, int to_mesh, cudaStream_t s) {
+  const unsigned g = grid_for(C, 256);
+  if (form == FORM_FP64) {
+    if (to_mesh) k_eps_in<double><<<g, 256, 0, s>>>(eps, C, (Quad<double>*)mesh.ufe);
+    else k_eps_out<double><<<g, 256, 0, s>>>((const Quad<double>*)mesh.ufe, C, eps);
+  } else {
+    if (to_mesh) k_eps_in<float><<<g, 256, 0, s>>>(eps, C, (Quad<float>*)mesh.ufe);
+    else k_eps_out<float><<<g, 256, 0, s>>>((const Quad<float>*)mesh.ufe, C, eps);
   }
 }
 

@@ -91,6 +91,12 @@ void launch_deposit(int form, const DevState& st, const DevMesh& mesh, const Dev
                     void* qfields, cudaStream_t s);
 void launch_fields_from_fixed(int form, const void* q, const DevParams& P, void* phi,
                               int nf, cudaStream_t s);
+// mesh words ufe (U; eps_s kept) and gfl (G) from the FP64 fields [C][3] on the device
+void launch_fluid_prep(int form, const double* U, const double* gp, const double* du, int gp_default,
+                       double c_add_rho_f, const double rho_g[3], const DevParams& P,
+                       const DevMesh& mesh, cudaStream_t s);
+// eps_s of the mesh from (to_mesh = 1) or to (0) FP64 cell values
+void launch_eps_io(int form, double* eps, const DevMesh& mesh, int64_t C, int to_mesh, cudaStream_t s);
 // cell vorticity (curl U, 0) of the FP64 velocity U [C][3] into the mesh's wfl
 void launch_curl(int form, const double* U, const DevParams& P, const DevMesh& mesh,
                  cudaStream_t s);
