@@ -697,7 +697,12 @@ int autotune(sedi_handle* h) {
     size_t total = 0;
     for (const auto& it : live) total += (it.n + 255) & ~(size_t)255;
     char* save = nullptr;
-    CK(cudaMalloc((void**)&save, total));
+    if (cudaMalloc((void**)&save, total) != cudaSuccess) {
+      // no room for the saved copies: keep the current launch shape, do not retry
+      cudaGetLastError();
+      h->tuned_key = key;
+      return 0;
+    }
     auto copy_all = [&](bool to_save) {
       size_t off = 0;
       for (const auto& it : live) {
