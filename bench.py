@@ -282,6 +282,27 @@ def gpu_arm(args):
     msp, _, _, _, _, _ = timed_steps(gp, max(2, args.steps // 2), 2)
     plain = {"value": round(n * SUBSTEPS * len(msp) / (np.sum(msp) / 1e3), 1),
              "ms_per_step": round(float(np.mean(msp)), 4)}
+    del gp
+    # each form's force error at one identical state (the headline bed's positions and
+    # velocities after its timed steps, no tangential history, one averaging), against
+    # the FP64 form, which matches the oracle to 1e-12: max |F - F_fp64| / max |F_fp64|
+    # per kind of force
+    xs, vs, ws, _ = g.get_particles()
+    frc = {}
+    for form in ("fp64", "split", "plain"):
+        h = sedi.Sedi(dict(prm, precision_form=form, use_graphs=0), stream=stream)
+        h.set_particles(xs, vs, ws, parts["d"], parts["rho"])
+        h.set_fluid(U=fl["U"])
+        h.average_inplace()
+        frc[form] = h.compute_forces()
+        del h
+    plain["force_error_vs_fp64"] = {}
+    for form in ("split", "plain"):
+        e = {}
+        for k in ("contact", "lub", "fluid", "torque"):
+            ref = np.abs(frc["fp64"][k]).max()
+            e[k] = float(f"{np.abs(frc[form][k] - frc['fp64'][k]).max() / ref:.3e}") if ref > 0 else None
+        plain["force_error_vs_fp64"][form] = e
 
     cpu = None
     if rank == 0 and not args.no_cpu:

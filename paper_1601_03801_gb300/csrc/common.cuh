@@ -123,6 +123,7 @@ struct Num;
 template <>
 struct Num<float> {
   __device__ static float f(float a) { return a; }
+  __device__ static float lo(float) { return 0.0f; }
   __device__ static double d(float a) { return (double)a; }
   __device__ static float from_f(float a) { return a; }
   __device__ static float add(float a, float b) { return a + b; }
@@ -142,6 +143,7 @@ struct Num<float> {
 template <>
 struct Num<double> {
   __device__ static double f(double a) { return a; }
+  __device__ static double lo(double) { return 0.0; }
   __device__ static double d(double a) { return a; }
   __device__ static double from_f(double a) { return a; }
   __device__ static double add(double a, double b) { return a + b; }
@@ -161,6 +163,7 @@ struct Num<double> {
 template <>
 struct Num<dd> {
   __device__ static float f(dd a) { return a.hi; }
+  __device__ static float lo(dd a) { return a.lo; }  // the low word (f() is the high one)
   __device__ static double d(dd a) { return dd_to_double(a); }
   __device__ static dd from_f(float a) { return dd{a, 0.0f}; }
   __device__ static dd add(dd a, dd b) { return dd_add(a, b); }

@@ -126,8 +126,9 @@ struct PairOut {
 template <int FORM, bool INTEGRATE, bool EXT, bool BOTH = false>
 __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
     const DevParams& P, const Quad<typename Traits<FORM>::S>& Pi,
-    const typename Traits<FORM>::F* vi, const typename Traits<FORM>::F* wi,
-    typename Traits<FORM>::F mi, int32_t e, int k, bool has, int64_t i, int64_t N,
+    const typename Traits<FORM>::F* vi, const typename Traits<FORM>::F* vil,
+    const typename Traits<FORM>::F* wi, typename Traits<FORM>::F mi, int32_t e, int k, bool has,
+    int64_t i, int64_t N,
     const Quad<typename Traits<FORM>::S>* pos, const Quad<typename Traits<FORM>::S>* vel,
     const Quad<typename Traits<FORM>::S>* omg, Quad<typename Traits<FORM>::S>* hist, int k2 = 0) {
   using S = typename Traits<FORM>::S;
@@ -167,8 +168,17 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
   const V3<F> n{dxf[0] * inv_d, dxf[1] * inv_d, dxf[2] * inv_d};
   const Quad<S> Vj = ldq(vel + j);
   const F vj[3] = {NS::f(Vj.a), NS::f(Vj.b), NS::f(Vj.c)};
-  const F* vA = i_lo ? vi : vj;
-  const F* vB = i_lo ? vj : vi;
+  const F vjl[3] = {NS::lo(Vj.a), NS::lo(Vj.b), NS::lo(Vj.c)};
+  // velocity of A relative to B from both words of each velocity: neighbours in a
+  // moving bed differ by far less than their speed, so rounding each velocity to one
+  // word first would cost the difference most of its digits.  Formed as i minus j and
+  // negated when j comes first (exact: rounding is symmetric under negation).
+  F dv[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const F d = (vi[a] - vj[a]) + (vil[a] - vjl[a]);
+    dv[a] = i_lo ? d : -d;
+  }
   F wj[3] = {F(0), F(0), F(0)};
   if (o.contact || (EXT && o.lub && P.lub_tangential)) {
     const Quad<S> Wj = ldq(omg + j);
@@ -187,7 +197,7 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
     const F la = rA - F(0.5) * delta, lb = rB - F(0.5) * delta;
     V3<F> om{la * wA[0] + lb * wB[0], la * wA[1] + lb * wB[1], la * wA[2] + lb * wB[2]};
     V3<F> wxn = cross(om, n);
-    V3<F> vrel{vA[0] - vB[0] + wxn.x, vA[1] - vB[1] + wxn.y, vA[2] - vB[2] + wxn.z};
+    V3<F> vrel{dv[0] + wxn.x, dv[1] + wxn.y, dv[2] + wxn.z};
     S xo[3], xn_[3];
     if (has) {
       const Quad<S> h = ldq(hist + (int64_t)k * N + i);
@@ -209,7 +219,7 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
     const F hh = h > hin ? h : hin;
     const F rA = NS::f(A.d), rB = NS::f(Bq.d);
     const F Rl = rA * rB / (rA + rB);
-    const F vn = (vA[0] - vB[0]) * n.x + (vA[1] - vB[1]) * n.y + (vA[2] - vB[2]) * n.z;
+    const F vn = dv[0] * n.x + dv[1] * n.y + dv[2] * n.z;
     F sl = -K.six_pi_mu * Rl * Rl * vn / hh;
     if (!i_lo) sl = -sl;
     o.l = V3<F>{sl * n.x, sl * n.y, sl * n.z};
@@ -220,7 +230,7 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
       const F la = rA + F(0.5) * h, lb = rB + F(0.5) * h;
       const V3<F> om{la * wA[0] + lb * wB[0], la * wA[1] + lb * wB[1], la * wA[2] + lb * wB[2]};
       const V3<F> wxn = cross(om, n);
-      const V3<F> vr{vA[0] - vB[0] + wxn.x, vA[1] - vB[1] + wxn.y, vA[2] - vB[2] + wxn.z};
+      const V3<F> vr{dv[0] + wxn.x, dv[1] + wxn.y, dv[2] + wxn.z};
       const F vrn = vr.x * n.x + vr.y * n.y + vr.z * n.z;
       const F b = rB / rA;
       const F shape = (F(2) + b + F(2) * b * b) / ((F(1) + b) * (F(1) + b));
@@ -279,10 +289,11 @@ __device__ __forceinline__ void pair_forces_body(const DevState& st, const DevPa
     if (!(dx * dx + dy * dy + dz * dz <= cut * cut * 1.0002f)) continue;
     const Quad<S> Vi = ldq(vel + i), Wi = ldq(omg + i);
     const F vi[3] = {NS::f(Vi.a), NS::f(Vi.b), NS::f(Vi.c)};
+    const F vil[3] = {NS::lo(Vi.a), NS::lo(Vi.b), NS::lo(Vi.c)};
     const F wi[3] = {NS::f(Wi.a), NS::f(Wi.b), NS::f(Wi.c)};
     const int k = pr.y;
     const PairOut<F> o = pair_eval<FORM, INTEGRATE, false, true>(
-        P, Pi, vi, wi, NS::f(Vi.d), nbr[(int64_t)k * N + i], k, (cmask[i] >> k) & 1u, i, N, pos,
+        P, Pi, vi, vil, wi, NS::f(Vi.d), nbr[(int64_t)k * N + i], k, (cmask[i] >> k) & 1u, i, N, pos,
         vel, omg, hist, pr.w);
     // the pair's record; the slot masks tell the gather which slots hold this
     // substep's records (OR is order-free)
@@ -307,7 +318,7 @@ __device__ __forceinline__ void pair_forces_body(const DevState& st, const DevPa
 }
 
 template <int FORM, bool INTEGRATE>
-__global__ void __launch_bounds__(128, 8) k_pair_forces(DevState st, DevParams P, int sub_off) {
+__global__ void __launch_bounds__(128, 6) k_pair_forces(DevState st, DevParams P, int sub_off) {
   pair_forces_body<FORM, INTEGRATE>(st, P, sub_off);
 }
 
@@ -347,7 +358,7 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
   Quad<S> Pi{}, Vi{}, Wi{};
   Quad<F> Ai{};
   F ri = F(0), mi = F(0);
-  F vi[3] = {F(0), F(0), F(0)}, wi[3] = {F(0), F(0), F(0)};
+  F vi[3] = {F(0), F(0), F(0)}, wi[3] = {F(0), F(0), F(0)}, vil[3] = {F(0), F(0), F(0)};
   V3<F> fc{0, 0, 0}, fl{0, 0, 0}, tq{0, 0, 0};
   uint32_t mask = 0, nmask = 0, live = 0;
   if (valid) {
@@ -360,6 +371,7 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       vi[a] = NS::f(a == 0 ? Vi.a : (a == 1 ? Vi.b : Vi.c));
+      vil[a] = NS::lo(a == 0 ? Vi.a : (a == 1 ? Vi.b : Vi.c));
       wi[a] = NS::f(a == 0 ? Wi.a : (a == 1 ? Wi.b : Wi.c));
     }
     const int nn = st.nn[nl][i];
@@ -467,7 +479,7 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
     constexpr int W = BS / 32;
     __shared__ uint16_t q_pair[W][1024];
     __shared__ Quad<S> q_pi[W][32];
-    __shared__ F q_vw[W][32][8];  // vi, wi, mi, (pad)
+    __shared__ F q_vw[W][32][12];  // vi, wi, mi, (pad), low words of vi, (pad)
     __shared__ uint32_t q_mask[W][32];
     __shared__ F q_res[W][32][EXT ? 12 : 9];
     __shared__ uint8_t q_flag[W][32];
@@ -486,6 +498,7 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
     for (int a = 0; a < 3; ++a) {
       q_vw[wid][lane][a] = vi[a];
       q_vw[wid][lane][3 + a] = wi[a];
+      q_vw[wid][lane][8 + a] = vil[a];
     }
     q_vw[wid][lane][6] = mi;
     q_mask[wid][lane] = mask;
@@ -507,7 +520,7 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
         const int L = e >> 8, k = e & 255;
         const int64_t iL = i0 + L;
         const F* vw = q_vw[wid][L];
-        const PairOut<F> o = pair_eval<FORM, INTEGRATE, EXT>(P, q_pi[wid][L], vw, vw + 3, vw[6],
+        const PairOut<F> o = pair_eval<FORM, INTEGRATE, EXT>(P, q_pi[wid][L], vw, vw + 8, vw + 3, vw[6],
                                                         nbr[(int64_t)k * N + iL], k,
                                                         (q_mask[wid][L] >> k) & 1u, iL, N, pos, vel,
                                                         omg, hist);
@@ -547,7 +560,7 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
       while (live) {
         const int k = __ffs(live) - 1;
         live &= live - 1;
-        const PairOut<F> o = pair_eval<FORM, INTEGRATE, EXT>(P, Pi, vi, wi, mi, nbr[(int64_t)k * N + i], k,
+        const PairOut<F> o = pair_eval<FORM, INTEGRATE, EXT>(P, Pi, vi, vil, wi, mi, nbr[(int64_t)k * N + i], k,
                                                         (mask >> k) & 1u, i, N, pos, vel, omg, hist);
         if (o.contact) {
           fc.x += o.fa.x; fc.y += o.fa.y; fc.z += o.fa.z;

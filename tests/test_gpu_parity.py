@@ -79,6 +79,24 @@ def test_forces_identical_state(small, form):
         assert err <= FORCE_TOL[form], f"{form} {k}: {err:.3e}"
 
 
+@pytest.mark.parametrize("form", ["fp64", "split"])
+def test_forces_bed_moving_as_a_whole(small, form):
+    # every sphere carries the same 2.4 m/s drift plus relative velocities four thousand
+    # times smaller: the pair forces depend on the relative velocity only, so its
+    # digits must survive the drift (the split form forms it from both words)
+    prm, parts = small
+    rng = np.random.default_rng(5)
+    n = len(parts["x"])
+    moving = dict(parts, v=np.array([2.0, -1.2, 0.4]) + rng.normal(0, 5e-4, (n, 3)),
+                  w=rng.normal(0, 1.0, (n, 3)))
+    g, o = make_pair(prm, moving, form)
+    fg, fo = g.compute_forces(), o.forces()
+    for k in ("contact", "lub", "torque"):
+        assert np.abs(fo[k]).max() > 0, k
+        err = rel_err(fg[k], fo[k])
+        assert err <= FORCE_TOL[form], f"{form} {k}: {err:.3e}"
+
+
 # the paper's own contact law (Sec. 2.5, Table 1): linear spring-dashpot, k_n = 800 N/m,
 # e = 0.97, mu = 0.1
 LINEAR = dict(contact_law=1, kn_linear=800.0, kt_ratio=2.0 / 7.0, restitution=0.97, friction=0.1)
