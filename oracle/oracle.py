@@ -79,6 +79,9 @@ def lib():
         L.orc_lift.restype = None
         L.orc_lub_pair.argtypes = [C.POINTER(OrcParams), _P, _D, _D, _P, _P, _P, _P, _P, _P, _P]
         L.orc_lub_pair.restype = None
+        L.orc_hm_pair.argtypes = [C.POINTER(OrcParams), _P, _D, _D, _D, _D, _P, _P, _P, _P, _P,
+                                  _P, _P, _P, _P]
+        L.orc_hm_pair.restype = C.c_int
         L.orc_lub_wall.argtypes = [C.POINTER(OrcParams), _P, _D, _D, _P, _P, _P, _P]
         L.orc_lub_wall.restype = None
         L.orc_cnn_num_params.argtypes = []
@@ -275,6 +278,18 @@ def lub_pair(prm: dict, dx, ra, rb, va, vb, wa, wb):
     lib().orc_lub_pair(C.byref(p), _ptr(a[0]), float(ra), float(rb), _ptr(a[1]), _ptr(a[2]),
                        _ptr(a[3]), _ptr(a[4]), _ptr(F), _ptr(Ta), _ptr(Tb))
     return F, Ta, Tb
+
+
+def hm_pair(prm: dict, dx, ra, rb, ma, mb, va, vb, wa, wb, xi_old):
+    """Contact of the pair (a, b), dx = x_b - x_a, with spring xi_old: (active, force on a,
+    torque on a, torque on b, updated spring)."""
+    p = make_params(prm)
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (dx, va, vb, wa, wb, xi_old)]
+    F, Ta, Tb, xi = np.zeros(3), np.zeros(3), np.zeros(3), np.zeros(3)
+    act = lib().orc_hm_pair(C.byref(p), _ptr(a[0]), float(ra), float(rb), float(ma), float(mb),
+                            _ptr(a[1]), _ptr(a[2]), _ptr(a[3]), _ptr(a[4]), _ptr(a[5]),
+                            _ptr(F), _ptr(Ta), _ptr(Tb), _ptr(xi))
+    return bool(act), F, Ta, Tb, xi
 
 
 def lub_wall(prm: dict, n, dist, r, v, w):

@@ -132,6 +132,13 @@ void orc_lift(const orc_params* p, const double w[3], const double omega[3], dou
 void orc_lub_pair(const orc_params* p, const double dx[3], double ra, double rb,
                   const double va[3], const double vb[3], const double wa[3],
                   const double wb[3], double F[3], double Ta[3], double Tb[3]);
+/* Contact of the pair (a, b) with spring xi_old, dx = x_b - x_a: force on a, torques
+   on a and b, updated spring.  Returns 1 if the spheres overlap, else 0 (outputs
+   untouched). */
+int orc_hm_pair(const orc_params* p, const double dx[3], double ra, double rb, double ma,
+                double mb, const double va[3], const double vb[3], const double wa[3],
+                const double wb[3], const double xi_old[3], double F[3], double Ta[3],
+                double Tb[3], double xi_new[3]);
 /* Lubrication against a wall: n unit normal towards the wall, dist centre-to-plane. */
 void orc_lub_wall(const orc_params* p, const double n[3], double dist, double r,
                   const double v[3], const double w[3], double F[3], double T[3]);

@@ -238,6 +238,21 @@ void orc_lub_pair(const orc_params* p, const double dx[3], double ra, double rb,
   orc::store(Tb, 0, o.Tb);
 }
 
+int orc_hm_pair(const orc_params* p, const double dx[3], double ra, double rb, double ma,
+                double mb, const double va[3], const double vb[3], const double wa[3],
+                const double wb[3], const double xi_old[3], double F[3], double Ta[3],
+                double Tb[3], double xi_new[3]) {
+  orc::ContactOut o = orc::hm_pair(*p, orc::load(dx, 0), ra, rb, ma, mb, orc::load(va, 0),
+                                   orc::load(vb, 0), orc::load(wa, 0), orc::load(wb, 0),
+                                   orc::load(xi_old, 0));
+  if (!o.active) return 0;
+  orc::store(F, 0, o.F);
+  orc::store(Ta, 0, o.Ta);
+  orc::store(Tb, 0, o.Tb);
+  orc::store(xi_new, 0, o.xi);
+  return 1;
+}
+
 void orc_lub_wall(const orc_params* p, const double n[3], double dist, double r,
                   const double v[3], const double w[3], double F[3], double T[3]) {
   orc::LubOut o = orc::lub_wall(*p, orc::load(n, 0), dist, r, orc::load(v, 0), orc::load(w, 0));

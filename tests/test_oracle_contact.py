@@ -293,3 +293,60 @@ def test_case1_bounce_effective_restitution(oracle_mod):
     assert st[0] > st[1] > st[2] and st[2] < 40 and st[0] > 3000
     assert e_lub[0] > e_lub[1] > e_lub[2] and e_lub[2] < 0.2 and e_lub[0] > 0.85
     assert all(e > 0.95 for e in e_dry) and all(a < b for a, b in zip(e_lub, e_dry))
+
+
+def _rot_z(th, v):
+    c, s = math.cos(th), math.sin(th)
+    return np.array([c * v[0] - s * v[1], s * v[0] + c * v[1], v[2]])
+
+
+def _rigid_rotation(oracle_mod, xi0, steps, omega=100.0, p=None):
+    """Two touching spheres turning rigidly about their common centre (axis z, rate
+    omega) with no surface slip: positions, velocities and spins prescribed in closed
+    form, the spring fed from one substep to the next through the contact law."""
+    p = p or dry(friction=10.0)
+    dt = p["dt"]
+    m = mass()
+    delta = 2e-6
+    dist = D - delta
+    xi = np.array(xi0, float)
+    W = np.array([0.0, 0.0, omega])
+    forces = []
+    for k in range(steps + 1):
+        th = omega * dt * k
+        n = _rot_z(th, [1.0, 0.0, 0.0])
+        xa, xb = -0.5 * dist * n, 0.5 * dist * n
+        act, F, _, _, xi_new = oracle_mod.hm_pair(p, xb - xa, D / 2, D / 2, m, m, np.cross(W, xa),
+                                                  np.cross(W, xb), W, W, xi)
+        assert act
+        forces.append((th, F))
+        xi = xi_new  # tangent to n of substep k
+    return xi, forces, p
+
+
+def test_p19_spring_turns_with_rigidly_rotating_contact(oracle_mod):
+    """P19 (Sec. 2.5, endured contacts): a contact that turns rigidly carries its
+    tangential spring with it.  Relative surface velocity is zero, so each substep only
+    rotates the spring onto the new tangent plane and restores its length: a spring in
+    the plane of rotation after angle theta is R(theta) xi0 (exact up to rounding), the
+    contact force is constant in the co-rotating frame, and a spring with a component
+    along the axis keeps its length and converges to R(theta) xi0 at first order in the
+    step angle."""
+    xi0 = np.array([0.0, 2e-7, 0.0])  # tangent at n = x, in the plane of rotation
+    steps = 10000                      # 1 rad at 100 rad/s and dt = 1e-6 s
+    xi, forces, p = _rigid_rotation(oracle_mod, xi0, steps)
+    th = 100.0 * p["dt"] * steps
+    assert np.abs(xi - _rot_z(th, xi0)).max() < 1e-12 * np.linalg.norm(xi0)
+    # force in the co-rotating frame (n, t, z): constant along the whole rotation
+    fr = np.array([[F @ _rot_z(t, [1, 0, 0]), F @ _rot_z(t, [0, 1, 0]), F[2]] for t, F in forces[1:]])
+    assert np.abs(fr - fr[0]).max() < 1e-10 * np.abs(fr[0]).max()
+    assert fr[0][1] < 0 and abs(fr[0][2]) < 1e-12 * abs(fr[0][1])  # F_t = -S_t xi, along -t
+    # with a component along the rotation axis: length kept, first-order convergence
+    xi0 = np.array([0.0, 2e-7, 1e-7])
+    errs = []
+    for steps in (2500, 5000):
+        p2 = dry(friction=10.0, dt=1e-6 * 10000 / steps)
+        xi, _, _ = _rigid_rotation(oracle_mod, xi0, steps, p=p2)
+        assert abs(np.linalg.norm(xi) / np.linalg.norm(xi0) - 1) < 1e-12
+        errs.append(np.abs(xi - _rot_z(1.0, xi0)).max())
+    assert 1.8 < errs[0] / errs[1] < 2.2 and errs[1] < 1e-3 * np.linalg.norm(xi0)

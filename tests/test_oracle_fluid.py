@@ -89,6 +89,42 @@ def test_p9_drag_identities(oracle_mod):
     assert vr1 < vr0 and f1[2] > f0[2] > 0
 
 
+# Eq. 6 limits at eps_f < 1, computed by hand (30-digit arithmetic) from the printed
+# exponents: A1 = eps_f^4.14; A2 = 0.8 eps_f^1.28 for eps_f <= 0.85, else eps_f^2.65.
+VR_LIMITS = {  # eps_f: (A1, A2)
+    0.4: (0.022517924781948604002, 0.24758639476830814702),
+    0.7: (0.22840514666231898778, 0.50677534527606156953),
+    0.85: (0.51026332237862154106, 0.64974988589687697339),
+    0.9: (0.64649324148994868621, 0.7563845512207213536),
+}
+
+
+@pytest.mark.parametrize("eps_f", sorted(VR_LIMITS))
+def test_p9b_vr_limits_below_unit_fluid_fraction(oracle_mod, eps_f):
+    """P9b (Sec. 2.3, Eq. 6): the terminal-velocity ratio V_r tends to A1 = eps_f^4.14 as
+    Re -> 0 and to A2 as Re -> infinity (the square root grows like 0.06 Re + 2 A2 - A1),
+    on both sides of the switch of A2 at eps_f = 0.85; in between it is monotone.  The
+    Re -> infinity side is taken at Re = 1e8, where the O(1/Re) remainder (~4e-8) and the
+    FP64 cancellation of 0.06 Re against the square root (~1e-9) both stay below 2e-7."""
+    A1, A2 = VR_LIMITS[eps_f]
+    assert abs(oracle_mod.vr(eps_f, 1e-14) - A1) < 1e-10 * A1
+    assert abs(oracle_mod.vr(eps_f, 1e8) - A2) < 2e-7 * A2
+    vals = [oracle_mod.vr(eps_f, Re) for Re in np.logspace(-6, 8, 57)]
+    assert np.all(np.diff(vals) > 0) and A1 < vals[0] < vals[-1] < A2
+
+
+def test_p9c_hindered_stokes_limit(oracle_mod):
+    """P9c: at a small slip in a suspension of solid fraction eps_s, C_d -> 23.04 V_r / Re
+    and the drag tends to (23.04 / 24) x Stokes / eps_f^4.14 (Eq. 3-6 combined)."""
+    p = default_params()
+    d, wz = 1e-3, 1e-12
+    stokes = 3 * math.pi * p["rho_f"] * p["nu_f"] * d * wz
+    for eps_s, (eps_f, A1) in ((0.3, (0.7, VR_LIMITS[0.7][0])), (0.6, (0.4, VR_LIMITS[0.4][0]))):
+        f, vr, _ = oracle_mod.drag(p, eps_s, np.array([0.0, 0.0, wz]), d)
+        assert abs(vr / A1 - 1) < 1e-6
+        assert abs(f[2] / stokes / (0.96 / A1) - 1) < 1e-4
+
+
 def test_p10_lubrication_log_law(oracle_mod):
     """P10: lubrication alone slows a sphere approaching a wall as
     v(h) = v0 + (6 pi mu r^2 / m) ln(h0 / h) (v < 0 towards the wall)."""

@@ -67,6 +67,12 @@ MUTATIONS = [
      "double D = 0.5 * p.bandwidth[a] * p.bandwidth[a];", "test_p7"),
     ("orc_average.cpp", "*q = (int64_t)std::llrint(s);", "*q = (int64_t)s;", "test_p8"),
     ("orc_neighbors.cpp", "  return d2 < rc * rc;", "  return d2 <= rc * rc * 0.999;", "test_p5"),
+    ("orc_fluid.cpp", "double A1 = std::pow(eps_f, 4.14);", "double A1 = std::pow(eps_f, 4.41);",
+     "test_p9b"),
+    ("orc_fluid.cpp", "0.8 * std::pow(eps_f, 1.28)", "0.8 * std::pow(eps_f, 1.82)", "test_p9b"),
+    ("orc_fluid.cpp", ": std::pow(eps_f, 2.65);", ": std::pow(eps_f, 2.56);", "test_p9b"),
+    ("orc_contact.cpp", "V3 xi = sub(xi_old, scl(dot(xi_old, n), n));", "V3 xi = xi_old;", "test_p19"),
+    ("orc_contact.cpp", "if (new_len > 0.0) xi = scl(old_len / new_len, xi);", "", "test_p19"),
     ("orc_step.cpp", "h->x[i] = xn;", "h->x[i] = orc::add(h->x[i], orc::scl(p.dt, orc::sub(h->v[i], orc::scl(p.dt, a))));",
      "test_p1"),
 ]
