@@ -4,14 +4,15 @@ One step = one fluid step of the coupled loop: 20 DEM substeps (binning and
 lists when due, Hertz-Mindlin contact with springs, lubrication, drag /
 pressure-gradient / added-mass forces, leapfrog update) followed by one
 diffusion-based averaging (fixed-point PCM deposition + implicit smoothing by
-CG), on the 200,000-sphere sheared sediment bed (64 x 32 x 64 mm, log-law flow,
-64 x 32 x 64 mesh).  Metric: particle-steps/s = N x substeps / device seconds.
+Chebyshev iterative refinement), on the large settled bed: 10,000,000 spheres in
+a periodic 400 x 200 x 100 mm box on a 256 x 128 x 64 mesh.  Metric:
+particle-steps/s = N x substeps / device seconds.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 N > 1 (torchrun, one rank per GPU) runs one independent bed per rank (weak
 scaling, no collective on the data path).  --impl reference times the FP64 CPU
-oracle on this host's cores on a bounded sample of the same workload.
+oracle on this host's cores on a bounded sample of the same workload (no GPU).
 """
 import argparse
 import hashlib
@@ -31,11 +32,17 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-steps/s (contact+coupling+averaging), % HBM roofline, vs plain form"
 UNIT = "particle-steps/s"
 SUBSTEPS = 20
-WORKLOAD = ("sheared sediment bed: 200,000 lognormal spheres (median 0.5 mm, sigma_ln 0.1) "
-            "packed in a periodic 64x32x64 mm channel, wall z=0, settled by a 40,000-substep "
-            "prep run of the method (untimed), log-law flow u*=0.02 m/s, "
-            "64x32x64 mesh, Hertz-Mindlin + lubrication + drag + added mass, diffusion "
-            "averaging b=3 d50; step = 20 substeps (dt=1e-6 s) + 1 averaging")
+WORKLOAD = ("large settled bed: 10,000,000 spheres, d ~ U[0.4, 0.6] mm, rho 2500, settled into a "
+            "~14 mm deep bed (FIRE energy-minimised 4 x 4 mm periodic block of 2,000 spheres tiled "
+            "100 x 50: ~5 contacts per sphere, packing fraction ~0.6) in a periodic 400x200x100 mm "
+            "box, wall z=0, water, 256x128x64 mesh, mean flow 0.3 m/s + Gaussian-filtered noise "
+            "(rms 0.03 m/s), DU/Dt = U.grad U; Hertz-Mindlin + lubrication + drag + pressure "
+            "gradient + added mass, diffusion averaging b=1.5 mm; step = 20 substeps "
+            "(dt=1e-6 s) + 1 averaging")
+WORKLOAD_200K = ("sheared sediment bed: 200,000 lognormal spheres (median 0.5 mm, sigma_ln 0.1) "
+                 "settled (FIRE energy-minimised 8 x 4 mm block tiled 8 x 8) in a periodic "
+                 "64x32x64 mm channel, wall z=0, log-law flow u*=0.02 m/s, 64x32x64 mesh; "
+                 "step = 20 substeps + 1 averaging")
 PROFILE_FILE = os.path.join(ROOT, "profiles", "k_substep_bed200k.md")
 PAIRS_PROFILE_FILE = os.path.join(ROOT, "profiles", "k_pair_forces_gather_bed200k.md")
 KERNEL_SOURCES = ["paper_1601_03801_gb300/csrc/k_force.cu", "paper_1601_03801_gb300/csrc/fluid.cuh",
@@ -151,196 +158,327 @@ def dist_setup(args):
     return world, rank, local
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def algorithmic_bytes(kbar, cbar, cells, n, form="split"):
+    """Algorithmic DRAM bytes of one particle-substep (contact + coupling + update):
+    own state x, v, omega read and written (FP64: 3 x 24 x 2 = 144 B), radius and
+    lagged acceleration read (16 B), acceleration written (12 B), 4 B per listed
+    neighbour index, 24 B per contact spring read plus 12 B owner write, and ~40 B of
+    mesh fields per cell shared by C/N spheres.  The plain FP32 form carries FP32
+    state and springs: 72 + 16 + 12 + 4 kbar + 18 cbar + 40 C/N."""
+    if form == "plain":
+        return 72 + 16 + 12 + 4 * kbar + 18 * cbar + 40.0 * cells / n
+    return 144 + 16 + 12 + 4 * kbar + 36 * cbar + 40.0 * cells / n
+
+
+def implementation_bytes(kbar, cbar, cells, n):
+    """Bytes the split form's layout moves per particle-substep: 32-byte double-float
+    records (position + radius, velocity + mass, spin) read and written (96 + 96),
+    acceleration and build position (16 + 16), wall mask and list count (8), 4 B per
+    listed index, a 32-byte spring record read and written per contact side (64 per
+    contact, i.e. 48 per contact and particle with the pair list's single store), and
+    two 16-byte mesh words per cell."""
+    return 264 + 4 * kbar + 48 * cbar + 32.0 * cells / n
+
+
+def list_stats(g, n):
+    off, _ = g.neighbors()
+    ij, _ = g.contacts()
+    return float(off[-1]) / n, 2.0 * len(ij) / n
+
+
+def measure(prm, parts, fl, form, steps, warmup, settle, stream, flush=None, profile=0,
+            world=1, local=0, clocks=False):
+    """One handle on the workload: untimed settling, W warm-up steps, then K timed
+    steps (20 substeps + 1 averaging each) with CUDA events on the launching stream.
+    Returns the handle and the measurements."""
+    import torch
+
+    from paper_1601_03801_gb300 import sedi
+
+    g = sedi.Sedi(dict(prm, precision_form=form, use_graphs=1, profile=profile), stream=stream)
+    g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+    g.set_fluid(U=fl["U"], DUDt=fl.get("DUDt"))
+    g.average_inplace()  # the drag sees a smoothed solid fraction from the start
+    for _ in range(settle):
+        g.step(SUBSTEPS)
+        g.average_inplace()
+    for _ in range(warmup):
+        g.step(SUBSTEPS)
+        g.average_inplace()
+    g.sync()
+    t0 = g.timings() if profile else None
+    st0 = g.stats()
+    evs = []
+    clk = Clocks(local) if clocks else None
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if clk:
+        clk.start()
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            if flush is not None:
+                flush.zero_()  # L2 flushed between timed steps, outside the events
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        g.step(SUBSTEPS)
+        g.average_inplace()
+        with torch.cuda.stream(stream):
+            e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    out = {"clocks": clk.stop() if clk else None,
+           "ms": [a.elapsed_time(b) for a, b in evs],
+           "stats0": st0, "stats1": g.stats()}
+    if profile:
+        t1 = g.timings()
+        out["phases"] = {k: round((t1[k] - t0[k]) / steps, 4) for k in
+                         ("rebuild_ms", "substep_ms", "deposit_ms", "smooth_ms")}
+        out["substep_launch_ms"] = ((t1["substep_ms"] - t0["substep_ms"]) /
+                                    max(1.0, t1["substep_n"] - t0["substep_n"]))
+    return g, out
+
+
+def roofline(prm, n, g, launch_ms, variant, form="split", traffic_scale=None):
+    """Roofline of the substep launch: algorithmic bytes (algorithmic_bytes) of every
+    particle-substep of one launch / the launch's mean duration (CUDA events inside
+    the graph), against the measured HBM copy bandwidth."""
+    kbar, cbar = list_stats(g, n)
+    C = int(np.prod(prm["ncell"]))
+    alg = algorithmic_bytes(kbar, cbar, C, n, form)
+    achieved = alg * n / (launch_ms / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    traffic_pp, _ = measured_traffic(variant) if form == "split" else (None, None)
+    out = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+           "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+           "traffic": None if traffic_pp is None else round(traffic_pp * n),
+           "kernel": substep_kernel_name(variant),
+           "algorithmic_bytes_per_particle_substep": round(alg, 1),
+           "particles_per_launch": n, "launch_ms": round(launch_ms, 5),
+           "kbar": round(kbar, 2), "cbar": round(cbar, 2), "cells": C}
+    if form == "split":
+        out["implementation_bytes_per_particle_substep"] = round(implementation_bytes(kbar, cbar, C, n), 1)
+        if traffic_pp is not None:
+            out["traffic_bytes_per_particle_substep"] = traffic_pp
+            out["traffic_note"] = ("DRAM bytes per particle-substep from the ncu capture of the "
+                                   "200,000-sphere bed (caches flushed before the launch), times the "
+                                   "particles of this launch")
+    return out
+
+
+def launches_per_step(variant, rebuilds, steps, cells):
+    """Kernels of one step: the graph's rebuild check, 20 substeps of one kernel (two
+    with the pair list), 13 per list rebuild taken, then deposition, fixed point ->
+    smoothing word, the smoother (the cluster solver: one launch; the grid solver:
+    barrier reset + cooperative launch) and the outputs."""
+    per_sub = 2 if variant == PAIRS_VARIANT else 1
+    per_avg = 4 if cells <= 131072 else 5
+    return steps * (1 + per_sub * SUBSTEPS + per_avg) + 13 * rebuilds
+
+
 def gpu_arm(args):
     import torch
 
     from paper_1601_03801_gb300 import sedi
-    from paper_1601_03801_gb300.workloads import bed_case
+    from paper_1601_03801_gb300.workloads import large_case
 
     world, rank, local = dist_setup(args)
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    prm, parts, fl = bed_case(settled=True)
+    prm, parts, fl = large_case()
     n = len(parts["x"])
+    C = int(np.prod(prm["ncell"]))
     stream = torch.cuda.Stream()
-
-    def make(form, profile):
-        g = sedi.Sedi(dict(prm, precision_form=form, use_graphs=1, profile=profile), stream=stream)
-        g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
-        g.set_fluid(U=fl["U"])
-        g.average_inplace()  # the drag sees a smoothed solid fraction from the start
-        # untimed settling so contacts carry load before the warm-up steps
-        for _ in range(args.settle):
-            g.step(SUBSTEPS)
-        g.average_inplace()
-        return g
-
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
-
-    def timed_steps(g, K, W):
-        for _ in range(W):
-            g.step(SUBSTEPS)
-            g.average_inplace()
-        g.sync()
-        t0 = g.timings() if g._p.profile else None
-        st0 = g.stats()
-        evs = []
-        clk = Clocks(local)
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        clk.start()
-        for _ in range(K):
-            with torch.cuda.stream(stream):
-                flush.zero_()  # L2 flushed between timed steps, outside the events
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-            g.step(SUBSTEPS)
-            g.average_inplace()
-            with torch.cuda.stream(stream):
-                e1.record(stream)
-            evs.append((e0, e1))
-        torch.cuda.synchronize()
-        clocks = clk.stop()
-        ms = [a.elapsed_time(b) for a, b in evs]
-        t1 = g.timings() if g._p.profile else None
-        st1 = g.stats()
-        return ms, t0, t1, st0, st1, clocks
-
-    # the headline handle runs without the per-phase event nodes in its graph
-    g = make("split", 0)
-    ms, _, _, st0, st1, clocks = timed_steps(g, args.steps, args.warmup)
-    value, total_ms = aggregate(float(np.sum(ms)), n, args.steps, world, device="cuda")
-    ms_per_step = total_ms / args.steps
+    # the headline handle runs without per-phase event nodes in its graph; the state
+    # (~2 GB) is far larger than L2, so no flush is needed between timed steps
+    g, m = measure(prm, parts, fl, "split", args.steps, args.warmup, args.settle, stream,
+                   world=world, local=local, clocks=True)
+    value, total_ms = aggregate(float(np.sum(m["ms"])), n, args.steps, world, device="cuda")
+    st0, st1 = m["stats0"], m["stats1"]
+    variant = st1["substep_variant"]
+    rebuilds = st1["rebuilds"] - st0["rebuilds"]
+    roof = None
+    phases = None
+    del g
+    torch.cuda.empty_cache()
     # phase breakdown and the substep launch time from a second, profiled handle (CUDA
     # events recorded inside the graph around every phase)
-    gprof = make("split", 1)
-    prof_steps = max(3, min(args.steps, 10))
-    _, t0, t1, _, _, _ = timed_steps(gprof, prof_steps, args.warmup)
-    gprof.close()
-
-    # roofline of the dominant kernel (fused substep): algorithmic bytes per launch
-    off, _ = g.neighbors()
-    kbar = float(off[-1]) / n
-    ij, _ = g.contacts()
-    cbar = 2.0 * len(ij) / n
-    C = int(np.prod(prm["ncell"]))
-    own_rw = 144 + 120          # own records read + written (see DESIGN: algorithmic bytes)
-    per_particle = own_rw + 4 * kbar + 48 * cbar + 32.0 * C / n
-    sub_ms = (t1["substep_ms"] - t0["substep_ms"]) / max(1.0, t1["substep_n"] - t0["substep_n"])
-    achieved = per_particle * n / (sub_ms / 1e3) / 1e9
-    peak, peak_kind = peaks()
-    traffic_pp, _ = measured_traffic(st1["substep_variant"])
-    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-            "traffic": None if traffic_pp is None else round(traffic_pp * n),
-            "kernel": substep_kernel_name(st1["substep_variant"]),
-            "algorithmic_bytes_per_particle": round(per_particle, 1),
-            "launch_ms": round(sub_ms, 5), "kbar": round(kbar, 2), "cbar": round(cbar, 2)}
-    phases = {k: round((t1[k] - t0[k]) / prof_steps, 4) for k in
-              ("rebuild_ms", "substep_ms", "deposit_ms", "smooth_ms")}
-    rebuilds = st1["rebuilds"] - st0["rebuilds"]
-    # kernels per step: the graph's rebuild check + 20 substeps of one kernel (two with
-    # the pair list: pair forces, then the per-particle gather) (+ 13 rebuild kernels per
-    # rebuild taken: binning, lists, spring carry-over, pair list, flip), then
-    # deposition, fixed point -> smoothing word, the cluster smoother (one launch) and
-    # the outputs
-    per_sub = 2 if st1["substep_variant"] == PAIRS_VARIANT else 1
-    launches = args.steps * (1 + per_sub * SUBSTEPS + 4) + 13 * rebuilds
-
-    # end-to-end through the C ABI with host buffers: per step the fluid fields go
-    # host -> device (pinned) and the averaged fields come back
-    import torch as _t
-    Uh = _t.from_numpy(np.ascontiguousarray(fl["U"])).pin_memory()
-    gph = _t.from_numpy(np.tile(np.array([0.0, 0.0, -9.81 * 1000.0]), (C, 1))).pin_memory()
-    duh = _t.zeros((C, 3), dtype=_t.float64).pin_memory()
-    eps_h = _t.zeros(C, dtype=_t.float64).pin_memory()
-    us_h = _t.zeros((C, 3), dtype=_t.float64).pin_memory()
-    F_h = _t.zeros((C, 3), dtype=_t.float64).pin_memory()
-    ge = make("split", 0)
-    K2 = max(2, min(args.steps, 10))
-    for _ in range(2):
-        ge.set_fluid(U=Uh.numpy(), grad_p=gph.numpy(), DUDt=duh.numpy())
-        ge.step(SUBSTEPS)
-        ge.average(eps_h.numpy(), us_h.numpy(), F_h.numpy())
-    torch.cuda.synchronize()
-    t_start = time.perf_counter()
-    for _ in range(K2):
-        ge.set_fluid(U=Uh.numpy(), grad_p=gph.numpy(), DUDt=duh.numpy())
-        ge.step(SUBSTEPS)
-        ge.average(eps_h.numpy(), us_h.numpy(), F_h.numpy())
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t_start
-    e2e = {"value": round(world * n * SUBSTEPS * K2 / e2e_s, 1), "unit": UNIT,
-           "h2d_bytes_per_step": 3 * C * 3 * 8, "d2h_bytes_per_step": 7 * C * 8, "steps": K2}
-
-    # the plain FP32 form on the same GPU (comparison baseline)
-    gp = make("plain", 0)
-    msp, _, _, _, _, _ = timed_steps(gp, max(2, args.steps // 2), 2)
-    plain = {"value": round(n * SUBSTEPS * len(msp) / (np.sum(msp) / 1e3), 1),
-             "ms_per_step": round(float(np.mean(msp)), 4)}
+    gp, mp = measure(prm, parts, fl, "split", max(3, min(args.steps, 10)), args.warmup, args.settle,
+                     stream, profile=1)
+    roof = roofline(prm, n, gp, mp["substep_launch_ms"], gp.stats()["substep_variant"])
+    phases = mp["phases"]
+    gp.close()
     del gp
-    # each form's force error at one identical state (the headline bed's positions and
-    # velocities after its timed steps, no tangential history, one averaging), against
-    # the FP64 form, which matches the oracle to 1e-12: max |F - F_fp64| / max |F_fp64|
-    # per kind of force
-    xs, vs, ws, _ = g.get_particles()
-    frc = {}
-    for form in ("fp64", "split", "plain"):
-        h = sedi.Sedi(dict(prm, precision_form=form, use_graphs=0), stream=stream)
-        h.set_particles(xs, vs, ws, parts["d"], parts["rho"])
-        h.set_fluid(U=fl["U"])
-        h.average_inplace()
-        frc[form] = h.compute_forces()
-        del h
-    plain["force_error_vs_fp64"] = {}
-    for form in ("split", "plain"):
-        e = {}
-        for k in ("contact", "lub", "fluid", "torque"):
-            ref = np.abs(frc["fp64"][k]).max()
-            e[k] = float(f"{np.abs(frc[form][k] - frc['fp64'][k]).max() / ref:.3e}") if ref > 0 else None
-        plain["force_error_vs_fp64"][form] = e
+    torch.cuda.empty_cache()
+    e2e = end_to_end(prm, parts, fl, stream, args, world)
+    plain = plain_form_leg(prm, parts, fl, stream, args) if rank == 0 and not args.no_plain else None
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(prm, parts, fl, budget_s=args.cpu_seconds)
-    ens = None
-    if rank == 0 and not args.no_ensemble:
-        ens = ensemble_leg()
-    large = None
-    if rank == 0 and not args.no_large:
-        large = large_leg(peaks()[0])
-    cnn = None
-    if rank == 0 and not args.no_cnn:
-        cnn = cnn_warm_start(prm, parts, fl)
-    bounce = None
-    if rank == 0 and not args.no_bounce:
-        bounce = bounce_leg()
+        cpu = cpu_baseline(prm, parts, fl)
+    extra = {}
+    if rank == 0:
+        if not args.no_bed200k:
+            extra["bed200k"] = bed200k_leg(args)
+        if not args.no_ensemble:
+            extra["ensemble"] = ensemble_leg()
+        if not args.no_cnn:
+            from paper_1601_03801_gb300.workloads import bed_case
+            extra["cnn_warm_start"] = cnn_warm_start(*bed_case())
+        if not args.no_bounce:
+            extra["case1_bounce"] = bounce_leg()
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(total_ms / args.steps, 4),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32 forces, df64 (FP32-pair) state, int64 deposition",
+                "dtype": "f32 forces; df64 (FP32-pair, 48-bit) state and springs; int64 deposition",
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "particles_per_gpu": n, "substeps_per_step": SUBSTEPS,
                            "mesh_cells": C, "form": "split", "graphs": True,
-                           "substep_variant": {"variant": st1["substep_variant"],
-                                               "block": st1["substep_block"], "chosen_by": "autotuner"},
-                           "l2": "flushed (256 MB write) between timed steps, outside the events",
+                           "settle_steps_untimed": args.settle,
+                           "substep_variant": {"variant": variant, "block": st1["substep_block"],
+                                               "chosen_by": "autotuner"},
+                           "l2": "not flushed: the particle state (~2 GB) is larger than L2",
                            "parallelism": "independent bed per GPU" if world > 1 else "1 GPU"},
                 "phases_ms_per_step": phases, "rebuilds_in_timed_region": int(rebuilds),
-                "roofline": roof, "plain_form": plain, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks, "cpu_baseline": cpu, "ensemble": ens, "large": large,
-                "cnn_warm_start": cnn, "case1_bounce": bounce}
+                "roofline": roof, "e2e": e2e,
+                "gpu_launches": int(launches_per_step(variant, rebuilds, args.steps, C)),
+                "clocks": m["clocks"], "cpu_baseline": cpu, "plain_form": plain, **extra}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+
+
+def end_to_end(prm, parts, fl, stream, args, world):
+    """The metric through the C ABI with host buffers: every step copies the fluid
+    fields (U, grad p, DU/Dt) from pinned host memory to the library, runs 20
+    substeps, and averages into pinned host buffers (eps_s, U_s, F_fp), wall clock
+    around the steps with the device synchronised on both sides."""
+    import torch
+
+    from paper_1601_03801_gb300 import sedi
+
+    n = len(parts["x"])
+    C = int(np.prod(prm["ncell"]))
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    Uh = pin(fl["U"])
+    gph = pin(np.tile(np.array([0.0, 0.0, -9.81 * 1000.0]), (C, 1)))
+    duh = pin(fl["DUDt"] if fl.get("DUDt") is not None else np.zeros((C, 3)))
+    eps_h = torch.zeros(C, dtype=torch.float64).pin_memory()
+    us_h = torch.zeros((C, 3), dtype=torch.float64).pin_memory()
+    F_h = torch.zeros((C, 3), dtype=torch.float64).pin_memory()
+    ge = sedi.Sedi(dict(prm, precision_form="split", use_graphs=1), stream=stream)
+    ge.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+
+    def step():
+        ge.set_fluid(U=Uh.numpy(), grad_p=gph.numpy(), DUDt=duh.numpy())
+        ge.step(SUBSTEPS)
+        ge.average(eps_h.numpy(), us_h.numpy(), F_h.numpy())
+
+    for _ in range(args.settle + args.warmup):
+        step()
+    torch.cuda.synchronize()
+    K2 = max(3, min(args.steps, 10))
+    t_start = time.perf_counter()
+    for _ in range(K2):
+        step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t_start
+    ge.close()
+    return {"value": round(world * n * SUBSTEPS * K2 / e2e_s, 1), "unit": UNIT,
+            "h2d_bytes_per_step": 3 * C * 3 * 8, "d2h_bytes_per_step": 7 * C * 8, "steps": K2}
+
+
+def plain_form_leg(prm, parts, fl, stream, args):
+    """The plain FP32 form on the same workload and GPU (comparison baseline of the
+    precision pattern): throughput and its substep roofline; plus, on the 200,000-
+    sphere bed, each form's force error at one identical state and its position error
+    after 100 substeps against the FP64 form (which matches the oracle to 1e-12)."""
+    import torch
+
+    n = len(parts["x"])
+    gp, mp = measure(prm, parts, fl, "plain", max(3, args.steps // 2), args.warmup, args.settle,
+                     stream, profile=1)
+    out = {"value": round(n * SUBSTEPS * len(mp["ms"]) / (np.sum(mp["ms"]) / 1e3), 1), "unit": UNIT,
+           "ms_per_step": round(float(np.mean(mp["ms"])), 4),
+           "roofline": roofline(prm, n, gp, mp["substep_launch_ms"], gp.stats()["substep_variant"],
+                                form="plain")}
+    gp.close()
+    del gp
+    torch.cuda.empty_cache()
+    out["errors_vs_fp64_on_bed200k"] = form_errors(stream)
+    return out
+
+
+def form_errors(stream, substeps=100):
+    from paper_1601_03801_gb300 import sedi
+    from paper_1601_03801_gb300.workloads import bed_case
+
+    prm, parts, fl = bed_case()
+    rng = np.random.default_rng(29)
+    n = len(parts["x"])
+    parts = dict(parts, v=rng.normal(0, 0.01, (n, 3)), w=rng.normal(0, 20.0, (n, 3)))
+    res = {}
+    for form in ("fp64", "split", "plain"):
+        h = sedi.Sedi(dict(prm, precision_form=form, use_graphs=0), stream=stream)
+        h.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+        h.set_fluid(U=fl["U"])
+        h.average_inplace()
+        f = h.compute_forces()
+        h.step(substeps)
+        res[form] = (f, h.get_particles()[0])
+        h.close()
+    L = np.array(prm["hi"]) - np.array(prm["lo"])
+    out = {}
+    for form in ("split", "plain"):
+        e = {}
+        for k in ("contact", "lub", "fluid", "torque"):
+            ref = np.abs(res["fp64"][0][k]).max()
+            e[k] = float(f"{np.abs(res[form][0][k] - res['fp64'][0][k]).max() / ref:.3e}")
+        dx = res[form][1] - res["fp64"][1]
+        dx -= L * np.round(dx / L) * np.array(prm["periodic"])
+        e[f"position_after_{substeps}_substeps_over_d"] = float(
+            f"{(np.abs(dx).max(axis=1) / parts['d']).max():.3e}")
+        out[form] = e
+    return out
+
+
+def bed200k_leg(args):
+    """The sheared 200,000-sphere bed (64 x 32 x 64 mm channel, 64 x 32 x 64 mesh):
+    throughput with the L2 flushed between steps (the state fits L2), and the
+    substep launch's roofline (the case the ncu captures in profiles/ are taken on)."""
+    import torch
+
+    from paper_1601_03801_gb300.workloads import bed_case
+
+    prm, parts, fl = bed_case()
+    n = len(parts["x"])
+    stream = torch.cuda.Stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    g, m = measure(prm, parts, fl, "split", max(args.steps, 20), args.warmup, args.settle, stream,
+                   flush=flush, profile=1)
+    out = {"workload": WORKLOAD_200K, "particles": n,
+           "value": round(n * SUBSTEPS * len(m["ms"]) / (np.sum(m["ms"]) / 1e3), 1), "unit": UNIT,
+           "ms_per_step": round(float(np.mean(m["ms"])), 4),
+           "l2": "flushed (256 MB write) between timed steps, outside the events",
+           "phases_ms_per_step": m["phases"],
+           "roofline": roofline(prm, n, g, m["substep_launch_ms"], g.stats()["substep_variant"])}
+    g.close()
+    return out
 
 
 def bounce_leg():
@@ -370,61 +508,6 @@ def bounce_leg():
     return {"workload": "Case 1: 6 mm sphere, 100 x 100 x 500 mm box of quiescent fluid, k_n = 800 N/m, "
                         "e = 0.97, mu = 0.1, dt = t_c / 50", "sweep": out,
             "wall_s": round(time.time() - t0, 2)}
-
-
-def large_leg(peak_gbs, steps=3, warmup=11):
-    """10,000,000 spheres (d ~ U[0.4, 0.6] mm) in a periodic 400 x 200 x 100 mm box on a
-    256 x 128 x 64 mesh with a turbulent-like flow: throughput of the split form (step =
-    20 substeps + 1 averaging) and the substep kernel's HBM roofline fraction."""
-    import torch
-
-    from paper_1601_03801_gb300 import sedi
-    from paper_1601_03801_gb300.workloads import large_case
-
-    prm, parts, fl = large_case()
-    n = len(parts["x"])
-    stream = torch.cuda.Stream()
-    g = sedi.Sedi(dict(prm, precision_form="split", profile=1), stream=stream)
-    g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
-    g.set_fluid(U=fl["U"], DUDt=fl["DUDt"])
-    g.average_inplace()
-    for _ in range(warmup):
-        g.step(SUBSTEPS)
-        g.average_inplace()
-    g.sync()
-    t0 = g.timings()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        g.step(SUBSTEPS)
-        g.average_inplace()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t1 = g.timings()
-    ms = e0.elapsed_time(e1) / steps
-    off, _ = g.neighbors()
-    kbar = float(off[-1]) / n
-    ij, _ = g.contacts()
-    cbar = 2.0 * len(ij) / n
-    C = int(np.prod(prm["ncell"]))
-    per_particle = 144 + 120 + 4 * kbar + 48 * cbar + 32.0 * C / n
-    sub_ms = (t1["substep_ms"] - t0["substep_ms"]) / max(1.0, t1["substep_n"] - t0["substep_n"])
-    achieved = per_particle * n / (sub_ms / 1e3) / 1e9
-    phases = {k: round((t1[k] - t0[k]) / steps, 3) for k in ("rebuild_ms", "substep_ms", "deposit_ms", "smooth_ms")}
-    return {"workload": "10,000,000 spheres, d ~ U[0.4, 0.6] mm, tiled relaxed packing in a periodic "
-                        "400 x 200 x 100 mm box (wall z = 0), 256 x 128 x 64 mesh, mean flow 0.3 m/s "
-                        "+ Gaussian-filtered noise (rms 0.03 m/s); step = 20 substeps + 1 averaging",
-            "particles": n, "steps": steps, "warmup": warmup,
-            "value": round(n * SUBSTEPS / (ms / 1e3), 1), "unit": UNIT, "ms_per_step": round(ms, 3),
-            "phases_ms_per_step": phases,
-            "roofline": {"bound": "hbm", "kernel": substep_kernel_name(g.stats()["substep_variant"]),
-                         "achieved": round(achieved, 1),
-                         "peak": peak_gbs, "unit": "GB/s", "frac": round(achieved / peak_gbs, 4),
-                         "algorithmic_bytes_per_particle": round(per_particle, 1),
-                         "launch_ms": round(sub_ms, 4), "kbar": round(kbar, 2), "cbar": round(cbar, 2)},
-            "substep_variant": g.stats()["substep_variant"]}
 
 
 def ensemble_leg(steps=3, warmup=2):
@@ -572,66 +655,88 @@ def _resample_u(U, nc_from, nc_to):
     return f[iz][:, iy][:, :, ix].reshape(-1, 3)
 
 
-def cpu_baseline(prm, parts, fl, budget_s=20.0):
-    """FP64 oracle on this host on a bounded sample of the same workload: a few
-    substeps of the full bed plus one averaging, combined at the 20:1 cadence."""
+def oracle_sample(prm, parts, fl, threads, substeps, with_average=True):
+    """Time the FP64 oracle on a bounded sample of the large bed: the 100 x 100 mm
+    patch (large_patch: 1/8 of the spheres and cells, the same bed) for `substeps`
+    substeps and one averaging, on `threads` host threads.  Returns (spheres,
+    seconds per substep, seconds per averaging)."""
     from oracle import oracle as orc
+    from paper_1601_03801_gb300.workloads import large_patch
 
-    o = orc.Oracle(prm)
-    o.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
-    o.set_fluid(U=fl["U"])
-    n = len(parts["x"])
+    pprm, pparts, pfl = large_patch(prm, parts, fl)
+    o = orc.Oracle(pprm, threads=threads)
+    o.set_particles(pparts["x"], pparts["v"], pparts["w"], pparts["d"], pparts["rho"])
+    o.set_fluid(U=pfl["U"], DUDt=pfl["DUDt"])
     t0 = time.perf_counter()
-    o.average()
+    if with_average:
+        o.average()
     t_avg = time.perf_counter() - t0
-    subs = 0
     t0 = time.perf_counter()
-    while True:
-        o.step(1)
-        subs += 1
-        el = time.perf_counter() - t0
-        if el > budget_s or subs >= 20:
-            break
-    t_sub = el / subs
-    step_s = SUBSTEPS * t_sub + t_avg
-    return {"value": round(n * SUBSTEPS / step_s, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{subs} oracle substeps + 1 averaging of the full 200k bed on 1 host core, "
-                      f"combined as 20 substeps + 1 averaging per step "
-                      f"(substep {t_sub:.3f} s, averaging {t_avg:.3f} s)"}
+    o.step(substeps)
+    t_sub = (time.perf_counter() - t0) / substeps
+    return len(pparts["x"]), t_sub, t_avg
+
+
+def cpu_baseline(prm, parts, fl):
+    """The FP64 oracle on this host on a bounded sample of the headline workload
+    (oracle_sample): all host cores (3 substeps + 1 averaging) and one core (1 substep
+    + 1 averaging), each combined as 20 substeps + 1 averaging per step."""
+    cores = host_cores()
+    n_all, sub_all, avg_all = oracle_sample(prm, parts, fl, cores, 3)
+    n_one, sub_one, avg_one = oracle_sample(prm, parts, fl, 1, 1)
+    rate = lambda n, sub, avg: round(n * SUBSTEPS / (SUBSTEPS * sub + avg), 1)
+    return {"value": rate(n_all, sub_all, avg_all), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"100 x 100 mm patch of the large bed ({n_all} spheres, 64x64x64 cells, the same "
+                       f"tiled bed): 3 oracle substeps ({sub_all:.3f} s each) + 1 averaging "
+                       f"({avg_all:.3f} s) on {cores} threads, combined as 20 substeps + 1 averaging"),
+            "single_core": {"value": rate(n_one, sub_one, avg_one), "cores": 1,
+                            "sample": f"same patch: 1 substep ({sub_one:.3f} s) + 1 averaging "
+                                      f"({avg_one:.3f} s) on 1 thread"},
+            "nproc": os.cpu_count()}
 
 
 def reference_arm(args):
-    """--impl reference: the FP64 oracle as it stands, on this host's cores."""
+    """--impl reference: the FP64 oracle as it stands, on this host's cores, with no
+    GPU and without the CUDA library.  Each step is a bounded sample of the headline
+    workload: one oracle substep of the 100 x 100 mm patch of the large bed (1/8 of it,
+    the same tiled bed, oracle_sample), with the averaging after every 20th step, so
+    20 steps are one fluid step of the patch."""
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return
     from oracle import oracle as orc
-    from paper_1601_03801_gb300.workloads import bed_case
+    from paper_1601_03801_gb300.workloads import large_case, large_patch
 
-    prm, parts, fl = bed_case(settled=True)
-    n = len(parts["x"])
-    o = orc.Oracle(prm)
-    o.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
-    o.set_fluid(U=fl["U"])
-    t0 = time.perf_counter()
-    o.average()
-    t_avg = time.perf_counter() - t0
+    prm, parts, fl = large_case()
+    pprm, pparts, pfl = large_patch(prm, parts, fl)
+    n = len(pparts["x"])
+    cores = host_cores()
+    o = orc.Oracle(pprm, threads=cores)
+    o.set_particles(pparts["x"], pparts["v"], pparts["w"], pparts["d"], pparts["rho"])
+    o.set_fluid(U=pfl["U"], DUDt=pfl["DUDt"])
+    o.average()  # untimed: the drag sees a smoothed solid fraction
     for _ in range(args.warmup):
         o.step(1)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    n_avg = 0
+    for s in range(args.steps):
         o.step(1)
-    t_sub = (time.perf_counter() - t0) / max(1, args.steps)
-    step_s = SUBSTEPS * t_sub + t_avg
-    value = n * SUBSTEPS / step_s
-    sample = (f"each step: 1 oracle substep of the full 200k bed; one averaging timed once "
-              f"({t_avg:.3f} s); value combines 20 substeps + 1 averaging per fluid step")
+        if (s + 1) % SUBSTEPS == 0:
+            o.average()
+            n_avg += 1
+    total = time.perf_counter() - t0
+    value = n * args.steps / total
+    sample = (f"each step: 1 oracle substep of the 100 x 100 mm patch of the large bed ({n} spheres, "
+              f"64x64x64 cells, 1/8 of the bed), averaging after every 20th step ({n_avg} in the "
+              f"timed region), {cores} host threads")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(step_s * 1e3, 2), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "particles_per_gpu": n, "substeps_per_step": SUBSTEPS},
-            "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "ms_per_step": round(total / max(1, args.steps) * 1e3, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "particles_per_gpu": len(parts["x"]),
+                       "substeps_per_step": SUBSTEPS, "sample_particles": n,
+                       "step": "one substep of the sample; averaging every 20th step"},
+            "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -639,22 +744,28 @@ def reference_arm(args):
 
 
 def kernels_only(args):
-    """Run the benchmark workload for a few steps without timing (profiling driver:
-    the command an ncu capture wraps)."""
+    """Run a workload for a few steps without timing (profiling driver: the command
+    an ncu capture wraps).  --case bed200k (default), large, or small."""
     import torch
 
     from paper_1601_03801_gb300 import sedi
-    from paper_1601_03801_gb300.workloads import bed_case
+    from paper_1601_03801_gb300.workloads import bed_case, large_case, small_case
 
     torch.cuda.set_device(0)
-    prm, parts, fl = bed_case(settled=True)
+    if args.case == "large":
+        prm, parts, fl = large_case()
+    elif args.case == "small":
+        prm, parts = small_case(parity_addon=True)
+        fl = {"U": None}
+    else:
+        prm, parts, fl = bed_case()
     extra = {}
     if args.with_cnn:
         extra = dict(use_cnn_guess=1, cnn_scale=(0.6, 1e4, 1e4, 1e4))
     g = sedi.Sedi(dict(prm, precision_form=args.form, use_graphs=int(args.graphs),
                        substep_variant=args.variant, **extra))
     g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
-    g.set_fluid(U=fl["U"])
+    g.set_fluid(U=fl["U"], DUDt=fl.get("DUDt"))
     if args.with_cnn:
         rng = np.random.default_rng(7)
         g.cnn_set_params(rng.normal(0, 0.05, g.CNN_PARAMS))
@@ -663,26 +774,29 @@ def kernels_only(args):
         g.step(SUBSTEPS)
         g.average_inplace()
     g.sync()
-    print(json.dumps({"mode": "kernels", "form": args.form, "steps": args.settle + args.steps,
-                      "stats": g.stats()}))
+    print(json.dumps({"mode": "kernels", "case": args.case, "form": args.form,
+                      "steps": args.settle + args.steps, "stats": g.stats()}))
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    # 200 fluid steps: about 0.6 s of timed work, long enough for several clock samples
-    ap.add_argument("--steps", type=int, default=200)
+    # 20 fluid steps of the 10M bed: a few seconds of timed work, several clock samples
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-cnn", action="store_true", help="skip the learned-warm-start leg")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 256-bed ensemble leg")
-    ap.add_argument("--no-large", action="store_true", help="skip the 10M-sphere leg")
+    ap.add_argument("--no-bed200k", action="store_true", help="skip the 200,000-sphere leg")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 form leg")
     ap.add_argument("--no-bounce", action="store_true", help="skip the Case-1 bounce sweep")
-    ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--settle", type=int, default=50, help="untimed settling steps before warm-up")
+    ap.add_argument("--settle", type=int, default=10,
+                    help="untimed steps before the warm-up (the method settles the bed further)")
     ap.add_argument("--mode", default="bench", choices=["bench", "kernels"],
-                    help="kernels: run the workload untimed (profiling driver)")
+                    help="kernels: run a workload untimed (profiling driver)")
+    ap.add_argument("--case", default="bed200k", choices=["bed200k", "large", "small"],
+                    help="kernels mode: workload")
     ap.add_argument("--form", default="split", choices=["split", "plain", "fp64"])
     ap.add_argument("--with-cnn", action="store_true",
                     help="kernels mode: average with the learned warm start (random weights)")

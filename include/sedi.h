@@ -9,7 +9,10 @@
  * pressure-gradient and added-mass forces (Sec. 2.3, Eq. 3-8) and a leapfrog
  * velocity-Verlet update (Sec. 2.1, Eq. 1).  sedi_average does the diffusion-based
  * averaging (Sec. 2.4, Eq. 9-10): PCM deposition, then implicit diffusion
- * smoothing solved by conjugate gradients.
+ * smoothing, each implicit step solved to a relative residual by Chebyshev
+ * semi-iteration on the operator's known spectrum, organised as iterative
+ * refinement (the linear systems and the stopping test are those of plain
+ * conjugate gradients; the iteration differs, see sedi_average).
  *
  * Conventions for every call:
  *   - Return 0 on success or a negative SEDI_E* code; sedi_last_error() then
@@ -44,7 +47,7 @@ enum {
   SEDI_ECUDA = -3,     /* a CUDA runtime call failed */
   SEDI_EOVERFLOW = -4, /* a particle has more listed neighbours than nbr_capacity */
   SEDI_ERANGE = -5,    /* a deposited value does not fit the fixed-point format */
-  SEDI_EDIVERGED = -6, /* smoothing CG hit cg_max_iter before cg_rtol */
+  SEDI_EDIVERGED = -6, /* smoothing solver hit cg_max_iter steps before cg_rtol */
   SEDI_ENONFINITE = -7,/* a force or position became NaN/Inf */
   SEDI_ETIMEOUT = -8,  /* a bounded device-side wait gave up */
   SEDI_ESTATE = -9,    /* calls in the wrong order (e.g. step before particles) */
@@ -60,8 +63,9 @@ enum { SEDI_MEM_HOST = 0, SEDI_MEM_DEVICE = 1 };
  * SEDI_FORM_SPLIT (default): forces in FP32; positions, velocities, spins and
  *   tangential springs carried in FP64-class double-float (two FP32 words,
  *   48-bit significand) so every update runs on the FP32 pipes; contact overlap
- *   and gap evaluated in double-float; fixed-point deposition; double-float CG.
- * SEDI_FORM_PLAIN_FP32: everything FP32 (absolute FP32 positions, FP32 CG with
+ *   and gap evaluated in double-float; fixed-point deposition; smoothing with a
+ *   double-float true residual and an FP32 Chebyshev recursion.
+ * SEDI_FORM_PLAIN_FP32: everything FP32 (absolute FP32 positions, FP32 smoothing with
  *   its tolerance raised to at least 2e-6, float atomics for deposition) -- the
  *   comparison baseline.
  * SEDI_FORM_FP64: everything IEEE FP64, for parity checks against an FP64
@@ -122,8 +126,11 @@ typedef struct sedi_params {
   int32_t n_tau;                           /* implicit pseudo-time steps [4] */
   int32_t tau_scheme;                      /* SEDI_TAU_EULER | SEDI_TAU_BDF2 [EULER];
                                               BDF2 excludes use_cnn_guess */
-  double cg_rtol;                          /* ||r|| <= rtol ||b|| per pseudo-step [1e-8] */
-  int32_t cg_max_iter;                     /* [500] */
+  double cg_rtol;                          /* ||r|| <= rtol ||b|| per pseudo-step [1e-8]
+                                              (the names keep the usual CG vocabulary:
+                                              the stopping test is the same) */
+  int32_t cg_max_iter;                     /* most solver steps per field and pseudo-step
+                                              [500] */
   int32_t shift_eps, shift_mom, shift_force; /* fixed-point exponents [40, 40, 32] */
   int32_t precision_form;                  /* SEDI_FORM_* [SPLIT] */
   int32_t nbr_capacity;                    /* listed neighbours per particle, <= 32 [32] */
@@ -162,7 +169,9 @@ typedef struct sedi_stats {
   int64_t substeps;       /* substeps advanced */
   int64_t rebuilds;       /* neighbour-list rebuilds */
   int64_t averages;       /* sedi_average calls */
-  int64_t cg_iterations;  /* CG iterations summed over fields and pseudo-steps */
+  int64_t cg_iterations;  /* smoothing solver steps (Chebyshev steps plus one true-
+                             residual evaluation per refinement round) summed over
+                             fields and pseudo-steps */
   int32_t max_neighbors;  /* largest list length at the last rebuild */
   int32_t nbr_capacity;   /* capacity in use */
   int32_t substep_variant; /* launch variant of the substep kernel in use (-1: not yet tuned) */
@@ -177,7 +186,11 @@ void sedi_default_params(sedi_params* p);
    allocates the mesh fields and smoothing work space; particle buffers are
    allocated by sedi_set_particles.  (Sec. 2.5 advises dt <= t_c / 50 of the
    Hertz contact time; the caller chooses dt.)  *out is owned by the caller and
-   released with sedi_destroy.  Errors: EINVAL, ENOMEM, ECUDA. */
+   released with sedi_destroy.  Errors: EINVAL, ENOMEM, ECUDA.  The environment
+   variable SEDI_BARRIER_SPIN_LIMIT, read here, lowers the number of polls after
+   which a wait at the grid-wide barrier of the smoother (meshes too large for one
+   thread-block cluster) gives up and the averaging returns SEDI_ETIMEOUT (default
+   2^22, about 0.3 s); it exists so tests can make that wait run out. */
 int sedi_create(const sedi_params* p, sedi_handle** out);
 void sedi_destroy(sedi_handle* h);
 
@@ -239,7 +252,12 @@ int sedi_step(sedi_handle* h, int32_t n_substeps);
 
 /* Diffusion-based averaging of bed `bed` (Sec. 2.4, Eq. 9-10): PCM deposition of
    eps_s, eps_s U_s and the force density -f_fp / V_c on the fluid, then n_tau
-   implicit diffusion steps, each solved to ||b - A x|| <= cg_rtol ||b||.  Outputs
+   implicit diffusion steps, each solved to ||b - A x|| <= cg_rtol ||b||.  The
+   solver: A = I - dtau div(D grad) has its spectrum in [1, 1 + 4 sum_a dtau D_a /
+   dx_a^2], so Chebyshev semi-iteration needs no inner products; each refinement
+   round forms the true residual in double-float (FP64 in SEDI_FORM_FP64), stops
+   when it meets the tolerance, else runs a fixed number of Chebyshev steps on the
+   correction in FP32.  The conserved sum of each field is kept as CG keeps it.  Outputs
    (any may be NULL): eps_s (C), U_s (C x 3), F_fp (C x 3).  The smoothed eps_s
    becomes the one the drag law sees.  bed = SEDI_ALL_BEDS (ensembles): every
    bed, outputs NULL.  Errors: ERANGE, EDIVERGED. */
@@ -255,7 +273,7 @@ int sedi_deposit(sedi_handle* h, int32_t bed, int64_t* fixed_fields, int32_t mem
 /* Smooth n_fields caller fields [n_fields][C] with the averaging operator
    (Sec. 2.4, Eq. 10); guess (same shape or NULL) is projected onto the conserved
    sum and used as the first pseudo-step's initial iterate; iters (n_fields or
-   NULL) receives the CG iterations per field summed over pseudo-steps. */
+   NULL) receives the solver steps per field summed over pseudo-steps. */
 int sedi_smooth(sedi_handle* h, int32_t bed, int32_t n_fields, const double* in, double* out,
                 const double* guess, int32_t* iters, int32_t mem);
 
@@ -328,26 +346,29 @@ int sedi_get_stats(sedi_handle* h, sedi_stats* out);
  * cannot call cudaMalloc themselves or through this library -- e.g. code that
  * runs while a memory pool or a host framework owns all device memory, or a
  * plugin whose device allocations are forbidden after start-up.  It smooths
- * n_fields caller fields exactly like sedi_smooth (Sec. 2.4, Eq. 10; the mesh,
- * bandwidth, n_tau, tau_scheme, cg_rtol, cg_max_iter and precision_form of *p), but keeps
- * all scratch in one static device array of this library, so it allocates
- * nothing: no cudaMalloc/cudaFree, no allocating library routine.
+ * n_fields caller fields exactly like sedi_smooth (same operator, solver and
+ * stopping test; the mesh, bandwidth, n_tau, tau_scheme, cg_rtol, cg_max_iter and
+ * precision_form of *p), but keeps all scratch in one static device array of this
+ * library, so it allocates nothing: no cudaMalloc/cudaFree, no allocating library
+ * routine.
  *   p       : parameters (only the mesh, box, bandwidth, solver and form fields
- *             are read); no handle is needed.
- *   in, out : DEVICE pointers, [n_fields][C] float64, C = prod(ncell); caller-owned.
- *   iters   : host array of n_fields (or NULL) receiving the solver iterations.
+ *             are read); no handle is needed.  A graded z mesh is rejected.
+ *   in, out : DEVICE pointers (checked with cudaPointerGetAttributes; host memory
+ *             is rejected), [n_fields][C] float64, C = prod(ncell); caller-owned.
+ *   iters   : host array of n_fields (or NULL) receiving the solver steps.
  *   cuda_stream : stream to run on (NULL = legacy default stream).
  *   msg     : optional host buffer of msg_len bytes for an error message.
  * Limit: 8 * C <= SEDI_STATIC_MAX_WORDS, i.e. up to 131,072 cells with any
  * n_fields <= 8 (the solver keeps 8 words per cell); larger meshes return
- * SEDI_EINVAL.  The scratch (about 50 MB) lives on every GPU
- * that loads the library until the process exits.  The first call on a device
- * looks up the scratch's device address (cudaGetSymbolAddress) for that device;
- * make that first call before any stream capture.  Every call shares the one
- * array and leaves its contents behind: calls whose GPU work overlaps (two
- * streams, two threads) race and must be serialised by the caller.  The call
- * synchronises its stream and returns SEDI_OK, SEDI_EINVAL, SEDI_EDIVERGED,
- * SEDI_ETIMEOUT or SEDI_ECUDA. */
+ * SEDI_EINVAL.  The scratch (about 50 MB) lives on every GPU that loads the
+ * library until the process exits.  The first call on a device looks up the
+ * scratch's device address (cudaGetSymbolAddress) for that device and keeps it;
+ * that first call should come before any stream capture, and the library must not
+ * be used across a cudaDeviceReset (the kept address would be stale).  Every call
+ * shares the one array and leaves its contents behind: calls whose GPU work
+ * overlaps (two streams, two threads) race and must be serialised by the caller.
+ * Each call ends by synchronising its stream and returns SEDI_OK, SEDI_EINVAL,
+ * SEDI_EDIVERGED, SEDI_ETIMEOUT or SEDI_ECUDA. */
 #define SEDI_STATIC_MAX_WORDS (1 << 20)
 int sedi_smooth_static(const sedi_params* p, int32_t n_fields, const double* in, double* out,
                        int32_t* iters, void* cuda_stream, char* msg, int32_t msg_len);

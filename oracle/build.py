@@ -1,7 +1,8 @@
 """Build the FP64 CPU oracle (test infrastructure only) into oracle/liborc.so.
 
 Plain g++ with fused multiply-add contraction disabled, so the oracle evaluates
-every expression in source order on x86-64 and aarch64 alike.
+every expression in source order on x86-64 and aarch64 alike; OpenMP for the
+optional multi-threaded particle loops (orc_set_threads), which give the same bits.
 """
 import os
 import subprocess
@@ -21,7 +22,7 @@ def build(force: bool = False) -> str:
         if os.path.getmtime(LIB) >= newest:
             return LIB
     cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", "-o", LIB + ".tmp"] + srcs
+           "-fno-fast-math", "-fopenmp", "-o", LIB + ".tmp"] + srcs
     subprocess.run(cmd, check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB

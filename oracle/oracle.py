@@ -50,6 +50,7 @@ def lib():
             "orc_set_fluid": [_P, _P, _P, _P],
             "orc_set_eps": [_P, _P],
             "orc_step": [_P, _I],
+            "orc_set_threads": [_P, _I],
             "orc_forces": [_P, _P, _P, _P, _P],
             "orc_get_particles": [_P, _P, _P, _P, _P],
             "orc_get_contacts": [_P, _L, _P, _P],
@@ -129,12 +130,18 @@ def _f64(a, shape=None):
 class Oracle:
     """One oracle instance: particles, fluid fields and contact history."""
 
-    def __init__(self, prm: dict):
+    def __init__(self, prm: dict, threads: int = 1):
         self.prm = dict(prm)
         self._p = make_params(prm)
         self.C = int(np.prod(prm["ncell"]))
         self.h = lib().orc_create(C.byref(self._p))
         self.n = 0
+        self.set_threads(threads)
+
+    def set_threads(self, threads: int):
+        """Threads of the particle loops and of the smoothing (same results for any count)."""
+        self.threads = max(1, int(threads))
+        lib().orc_set_threads(self.h, self.threads)
 
     def __del__(self):
         if getattr(self, "h", None):

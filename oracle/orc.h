@@ -84,6 +84,9 @@ int orc_set_fluid(orc_handle* h, const double* U, const double* grad_p, const do
 /* Smoothed solid fraction (C) seen by the drag law. */
 int orc_set_eps(orc_handle* h, const double* eps);
 
+/* Threads of the particle loops and of the smoothing (one field per thread); the
+   results do not depend on the count.  Default 1. */
+int orc_set_threads(orc_handle* h, int32_t threads);
 /* Advance n_sub substeps (contact, lubrication, fluid forces, leapfrog). */
 int orc_step(orc_handle* h, int32_t n_sub);
 /* Forces at the current state, without advancing: each n*3 (NULL to skip). */

@@ -307,7 +307,9 @@ int orc_smooth(orc_handle* h, int32_t nf, double* phi, const double* guess, int3
     gop2 = graded_op(p, zg, 2.0 / 3.0);
   }
   const int64_t nxy = (int64_t)p.ncell[0] * p.ncell[1];
-  int status = 0;
+  /* the fields are independent: one per thread with orc_set_threads(n > 1) */
+  std::vector<int> fstatus(nf, 0);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(h->threads > 1 ? h->threads : 1)
   for (int32_t f = 0; f < nf; ++f) {
     std::vector<double> x(phi + f * C, phi + (f + 1) * C);
     std::vector<double> x_prev;
@@ -332,7 +334,7 @@ int orc_smooth(orc_handle* h, int32_t nf, double* phi, const double* guess, int3
       }
       int it = zg.graded ? cg_graded(p, bdf2 ? gop2 : gop, b, x) : cg(p, bdf2 ? coef2 : coef, b, x);
       if (it < 0) {
-        status = -6;
+        fstatus[f] = -6;
         it = p.cg_max_iter;
       }
       total += it;
@@ -340,7 +342,9 @@ int orc_smooth(orc_handle* h, int32_t nf, double* phi, const double* guess, int3
     std::memcpy(phi + f * C, x.data(), sizeof(double) * C);
     if (iters) iters[f] = total;
   }
-  return status;
+  for (int32_t f = 0; f < nf; ++f)
+    if (fstatus[f]) return fstatus[f];
+  return 0;
 }
 
 int orc_average(orc_handle* h, double* eps, double* Us, double* Ffp) {

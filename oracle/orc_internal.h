@@ -86,10 +86,26 @@ V3 fluid_force(const orc_params& p, const FluidFields& ff, V3 x, V3 u, V3 a_prev
 V3 drag_force(const orc_params& p, double eps_s, V3 w, double d, double* Vr_out,
               double* Cdw_out);
 
-/* Pairs (i < j) with |x_j - x_i| < r_i + r_j + extra(i, j). */
+/* Pairs (i < j) with |x_j - x_i| < r_i + r_j + extra(i, j), sorted by (i, j).  With
+   threads > 1 the link-cell search runs over particles in parallel (same result). */
 void find_pairs(const orc_params& p, const std::vector<V3>& x, const std::vector<double>& r,
                 double h_out_frac, double skin, bool brute,
-                std::vector<std::pair<int64_t, int64_t>>& out);
+                std::vector<std::pair<int64_t, int64_t>>& out, int threads = 1);
+
+/* Tangential spring of one pair in contact, i < j. */
+struct HistEntry {
+  int64_t i, j;
+  V3 xi;
+};
+/* Springs sorted by (i, j) with the index of each particle's first entry:
+   entries of particle i are [first[i], first[i + 1]). */
+struct HistIndex {
+  const std::vector<HistEntry>* h;
+  std::vector<int64_t> first;
+};
+HistIndex hist_index(const std::vector<HistEntry>& h, int64_t n);
+/* Spring of the pair (i, j), i < j; null if the pair has none. */
+const V3* hist_find(const HistIndex& ix, int64_t i, int64_t j);
 
 }  // namespace orc
 
@@ -98,8 +114,10 @@ struct orc_handle {
   int64_t n = 0;
   std::vector<orc::V3> x, v, w, a_prev;
   std::vector<double> d, rho;
-  /* tangential spring of each pair in contact, keyed by (i, j) with i < j */
-  std::map<std::pair<int64_t, int64_t>, orc::V3> hist;
+  /* tangential spring of each pair in contact, i < j, sorted by (i, j) */
+  std::vector<orc::HistEntry> hist;
+  /* threads of the particle loops (orc_set_threads); 1 = the serial pair loop */
+  int threads = 1;
   /* tangential spring of each particle against each of the six walls */
   std::vector<orc::V3> whist; /* n*6 */
   std::vector<double> U, gradp, DUDt, eps;

@@ -32,9 +32,22 @@ bool listed(const orc_params& p, V3 xi, V3 xj, double ri, double rj, double frac
 
 }  // namespace
 
+HistIndex hist_index(const std::vector<HistEntry>& h, int64_t n) {
+  HistIndex ix{&h, std::vector<int64_t>(n + 1, 0)};
+  for (const HistEntry& e : h) ++ix.first[e.i + 1];
+  for (int64_t i = 0; i < n; ++i) ix.first[i + 1] += ix.first[i];
+  return ix;
+}
+
+const V3* hist_find(const HistIndex& ix, int64_t i, int64_t j) {
+  for (int64_t k = ix.first[i]; k < ix.first[i + 1]; ++k)
+    if ((*ix.h)[k].j == j) return &(*ix.h)[k].xi;
+  return nullptr;
+}
+
 void find_pairs(const orc_params& p, const std::vector<V3>& x, const std::vector<double>& r,
                 double frac, double skin, bool brute,
-                std::vector<std::pair<int64_t, int64_t>>& out) {
+                std::vector<std::pair<int64_t, int64_t>>& out, int threads) {
   out.clear();
   int64_t n = (int64_t)x.size();
   double rmax = 0.0;
@@ -59,35 +72,58 @@ void find_pairs(const orc_params& p, const std::vector<V3>& x, const std::vector
     if (b > nb[a] - 1) b = nb[a] - 1;
     return b;
   };
+  /* particles of each bin, in increasing index (counting sort) */
   int64_t nbins = (int64_t)nb[0] * nb[1] * nb[2];
-  std::vector<std::vector<int64_t>> bins(nbins);
-  std::vector<int64_t> bi(n);
+  std::vector<int64_t> bi(n), bstart(nbins + 1, 0), bitems(n);
   for (int64_t i = 0; i < n; ++i) {
     int b0 = bin_of(x[i], 0), b1 = bin_of(x[i], 1), b2 = bin_of(x[i], 2);
     bi[i] = ((int64_t)b2 * nb[1] + b1) * nb[0] + b0;
-    bins[bi[i]].push_back(i);
+    ++bstart[bi[i] + 1];
   }
-  for (int64_t i = 0; i < n; ++i) {
-    int c[3] = {(int)(bi[i] % nb[0]), (int)((bi[i] / nb[0]) % nb[1]),
-                (int)(bi[i] / ((int64_t)nb[0] * nb[1]))};
-    for (int oz = -1; oz <= 1; ++oz)
-      for (int oy = -1; oy <= 1; ++oy)
-        for (int ox = -1; ox <= 1; ++ox) {
-          int o[3] = {ox, oy, oz};
-          int t[3];
-          bool ok = true;
-          for (int a = 0; a < 3; ++a) {
-            t[a] = c[a] + o[a];
-            if (p.periodic[a]) t[a] = (t[a] + nb[a]) % nb[a];
-            else if (t[a] < 0 || t[a] >= nb[a]) ok = false;
+  for (int64_t b = 0; b < nbins; ++b) bstart[b + 1] += bstart[b];
+  {
+    std::vector<int64_t> fill(bstart.begin(), bstart.end() - 1);
+    for (int64_t i = 0; i < n; ++i) bitems[fill[bi[i]]++] = i;
+  }
+  /* the partners j > i of particle i, sorted, appended in increasing i: the pairs come
+     out sorted by (i, j).  Threads take contiguous ranges of i and their outputs are
+     joined in order. */
+  if (threads < 1) threads = 1;
+  std::vector<std::vector<std::pair<int64_t, int64_t>>> part(threads);
+#pragma omp parallel for schedule(static) num_threads(threads)
+  for (int t = 0; t < threads; ++t) {
+    const int64_t i0 = n * t / threads, i1 = n * (t + 1) / threads;
+    std::vector<int64_t> js;
+    for (int64_t i = i0; i < i1; ++i) {
+      js.clear();
+      int c[3] = {(int)(bi[i] % nb[0]), (int)((bi[i] / nb[0]) % nb[1]),
+                  (int)(bi[i] / ((int64_t)nb[0] * nb[1]))};
+      for (int oz = -1; oz <= 1; ++oz)
+        for (int oy = -1; oy <= 1; ++oy)
+          for (int ox = -1; ox <= 1; ++ox) {
+            int o[3] = {ox, oy, oz};
+            int cb[3];
+            bool ok = true;
+            for (int a = 0; a < 3; ++a) {
+              cb[a] = c[a] + o[a];
+              if (p.periodic[a]) cb[a] = (cb[a] + nb[a]) % nb[a];
+              else if (cb[a] < 0 || cb[a] >= nb[a]) ok = false;
+            }
+            if (!ok) continue;
+            int64_t b = ((int64_t)cb[2] * nb[1] + cb[1]) * nb[0] + cb[0];
+            for (int64_t q = bstart[b]; q < bstart[b + 1]; ++q) {
+              const int64_t j = bitems[q];
+              if (j > i && listed(p, x[i], x[j], r[i], r[j], frac, skin)) js.push_back(j);
+            }
           }
-          if (!ok) continue;
-          int64_t b = ((int64_t)t[2] * nb[1] + t[1]) * nb[0] + t[0];
-          for (int64_t j : bins[b])
-            if (j > i && listed(p, x[i], x[j], r[i], r[j], frac, skin)) out.emplace_back(i, j);
-        }
+      std::sort(js.begin(), js.end());
+      for (int64_t j : js) part[t].emplace_back(i, j);
+    }
   }
-  std::sort(out.begin(), out.end());
+  size_t total = 0;
+  for (auto& pt : part) total += pt.size();
+  out.reserve(total);
+  for (auto& pt : part) out.insert(out.end(), pt.begin(), pt.end());
 }
 
 }  // namespace orc
@@ -97,7 +133,7 @@ extern "C" int64_t orc_neighbors(orc_handle* h, double skin, int32_t brute, int6
   std::vector<double> r(h->n);
   for (int64_t i = 0; i < h->n; ++i) r[i] = 0.5 * h->d[i];
   std::vector<std::pair<int64_t, int64_t>> pairs;
-  orc::find_pairs(h->p, h->x, r, h->p.lub_h_out_frac, skin, brute != 0, pairs);
+  orc::find_pairs(h->p, h->x, r, h->p.lub_h_out_frac, skin, brute != 0, pairs, h->threads);
   int64_t total = 2 * (int64_t)pairs.size();
   if (total > cap) return -1;
   std::vector<std::vector<int64_t>> lists(h->n);

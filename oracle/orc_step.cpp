@@ -11,7 +11,8 @@
  *   x^(n+1) = x^n + dt v^(n+1/2), wrapped into [lo, hi) on periodic axes,
  * and a^n becomes the lagged acceleration of the added-mass force.
  * Pairs are visited in increasing (i, j), i < j; each pair is evaluated once with
- * i as body "a"; j receives the opposite force.
+ * i as body "a"; j receives the opposite force.  With orc_set_threads(n > 1) the
+ * particle loops run on n threads and give the same bits (see pair_forces).
  */
 #include <cstring>
 
@@ -25,8 +26,100 @@ struct Forces {
   std::vector<V3> fc, fl, ff, tq;
 };
 
-void evaluate(orc_handle* h, Forces& out,
-              std::map<std::pair<int64_t, int64_t>, V3>* new_hist,
+/* Pair forces.  Serial: pairs in increasing (i, j), each evaluated once with i as
+   body "a"; i receives +F, j receives -F.  Parallel (threads > 1): every particle
+   walks its own partners in increasing index and evaluates each of its pairs with
+   the lower index as body "a", adding +F (it is "a") or -F (it is "b") -- the same
+   evaluations, added to each particle in the same order as the serial loop, so the
+   two give identical bits; each pair is evaluated from both sides. */
+void pair_forces(orc_handle* h, const std::vector<double>& r, const std::vector<double>& m,
+                 Forces& out, std::vector<orc::HistEntry>* new_hist) {
+  const orc_params& p = h->p;
+  int64_t n = h->n;
+  std::vector<std::pair<int64_t, int64_t>> pairs;
+  double frac = p.lubrication ? p.lub_h_out_frac : 0.0;
+  orc::find_pairs(p, h->x, r, frac, 0.0, n <= 4096, pairs, h->threads);
+  const orc::HistIndex hix = orc::hist_index(h->hist, n);
+  if (h->threads <= 1) {
+    for (auto& pr : pairs) {
+      int64_t i = pr.first, j = pr.second;
+      V3 dx = orc::min_image(p, h->x[i], h->x[j]);
+      const V3* old = orc::hist_find(hix, i, j);
+      V3 xi_old = old ? *old : V3{0, 0, 0};
+      orc::ContactOut c =
+          orc::hm_pair(p, dx, r[i], r[j], m[i], m[j], h->v[i], h->v[j], h->w[i], h->w[j], xi_old);
+      if (c.active) {
+        out.fc[i] = orc::add(out.fc[i], c.F);
+        out.fc[j] = orc::sub(out.fc[j], c.F);
+        out.tq[i] = orc::add(out.tq[i], c.Ta);
+        out.tq[j] = orc::add(out.tq[j], c.Tb);
+        if (new_hist) new_hist->push_back(orc::HistEntry{i, j, c.xi});
+      }
+      if (p.lubrication) {
+        orc::LubOut l = orc::lub_pair(p, dx, r[i], r[j], h->v[i], h->v[j], h->w[i], h->w[j]);
+        out.fl[i] = orc::add(out.fl[i], l.F);
+        out.fl[j] = orc::sub(out.fl[j], l.F);
+        out.tq[i] = orc::add(out.tq[i], l.Ta);
+        out.tq[j] = orc::add(out.tq[j], l.Tb);
+      }
+    }
+    return;
+  }
+  /* full partner lists, sorted: partners below k come from pairs (j, k), above from
+     (k, j); pid is the pair's index in `pairs` */
+  const int64_t np = (int64_t)pairs.size();
+  std::vector<int64_t> off(n + 1, 0), nb(2 * np), pid(2 * np);
+  for (auto& pr : pairs) {
+    ++off[pr.first + 1];
+    ++off[pr.second + 1];
+  }
+  for (int64_t i = 0; i < n; ++i) off[i + 1] += off[i];
+  {
+    std::vector<int64_t> fill(off.begin(), off.end() - 1);
+    for (int64_t e = 0; e < np; ++e) {  /* increasing first index */
+      pid[fill[pairs[e].second]] = e;
+      nb[fill[pairs[e].second]++] = pairs[e].first;
+    }
+    for (int64_t e = 0; e < np; ++e) {  /* then increasing second index */
+      pid[fill[pairs[e].first]] = e;
+      nb[fill[pairs[e].first]++] = pairs[e].second;
+    }
+  }
+  /* the spring of pair e, written by its first particle; kept in pair order below */
+  std::vector<orc::HistEntry> slot(new_hist ? np : 0);
+  std::vector<char> live(new_hist ? np : 0, 0);
+#pragma omp parallel for schedule(dynamic, 1024) num_threads(h->threads)
+  for (int64_t k = 0; k < n; ++k) {
+    for (int64_t e = off[k]; e < off[k + 1]; ++e) {
+      const int64_t q = nb[e];
+      const int64_t i = k < q ? k : q, j = k < q ? q : k;
+      const bool is_a = i == k;
+      V3 dx = orc::min_image(p, h->x[i], h->x[j]);
+      const V3* old = orc::hist_find(hix, i, j);
+      V3 xi_old = old ? *old : V3{0, 0, 0};
+      orc::ContactOut c =
+          orc::hm_pair(p, dx, r[i], r[j], m[i], m[j], h->v[i], h->v[j], h->w[i], h->w[j], xi_old);
+      if (c.active) {
+        out.fc[k] = is_a ? orc::add(out.fc[k], c.F) : orc::sub(out.fc[k], c.F);
+        out.tq[k] = orc::add(out.tq[k], is_a ? c.Ta : c.Tb);
+        if (new_hist && is_a) {
+          slot[pid[e]] = orc::HistEntry{i, j, c.xi};
+          live[pid[e]] = 1;
+        }
+      }
+      if (p.lubrication) {
+        orc::LubOut l = orc::lub_pair(p, dx, r[i], r[j], h->v[i], h->v[j], h->w[i], h->w[j]);
+        out.fl[k] = is_a ? orc::add(out.fl[k], l.F) : orc::sub(out.fl[k], l.F);
+        out.tq[k] = orc::add(out.tq[k], is_a ? l.Ta : l.Tb);
+      }
+    }
+  }
+  if (new_hist)
+    for (int64_t e = 0; e < np; ++e)
+      if (live[e]) new_hist->push_back(slot[e]);
+}
+
+void evaluate(orc_handle* h, Forces& out, std::vector<orc::HistEntry>* new_hist,
               std::vector<V3>* new_whist) {
   const orc_params& p = h->p;
   int64_t n = h->n;
@@ -39,34 +132,11 @@ void evaluate(orc_handle* h, Forces& out,
   out.fl.assign(n, V3{0, 0, 0});
   out.ff.assign(n, V3{0, 0, 0});
   out.tq.assign(n, V3{0, 0, 0});
-  std::vector<std::pair<int64_t, int64_t>> pairs;
-  double frac = p.lubrication ? p.lub_h_out_frac : 0.0;
-  orc::find_pairs(p, h->x, r, frac, 0.0, n <= 4096, pairs);
-  for (auto& pr : pairs) {
-    int64_t i = pr.first, j = pr.second;
-    V3 dx = orc::min_image(p, h->x[i], h->x[j]);
-    V3 xi_old{0, 0, 0};
-    auto it = h->hist.find(pr);
-    if (it != h->hist.end()) xi_old = it->second;
-    orc::ContactOut c =
-        orc::hm_pair(p, dx, r[i], r[j], m[i], m[j], h->v[i], h->v[j], h->w[i], h->w[j], xi_old);
-    if (c.active) {
-      out.fc[i] = orc::add(out.fc[i], c.F);
-      out.fc[j] = orc::sub(out.fc[j], c.F);
-      out.tq[i] = orc::add(out.tq[i], c.Ta);
-      out.tq[j] = orc::add(out.tq[j], c.Tb);
-      if (new_hist) (*new_hist)[pr] = c.xi;
-    }
-    if (p.lubrication) {
-      orc::LubOut l = orc::lub_pair(p, dx, r[i], r[j], h->v[i], h->v[j], h->w[i], h->w[j]);
-      out.fl[i] = orc::add(out.fl[i], l.F);
-      out.fl[j] = orc::sub(out.fl[j], l.F);
-      out.tq[i] = orc::add(out.tq[i], l.Ta);
-      out.tq[j] = orc::add(out.tq[j], l.Tb);
-    }
-  }
+  pair_forces(h, r, m, out, new_hist);
   if (new_whist) new_whist->assign(n * 6, V3{0, 0, 0});
   orc::FluidFields ff{&h->U, &h->gradp, &h->DUDt, &h->eps, &h->curlU};
+  /* walls and fluid: each particle on its own */
+#pragma omp parallel for schedule(static) num_threads(h->threads > 1 ? h->threads : 1)
   for (int64_t i = 0; i < n; ++i) {
     for (int a = 0; a < 3; ++a) {
       if (p.periodic[a]) continue;
@@ -172,9 +242,10 @@ int orc_step(orc_handle* h, int32_t n_sub) {
   const orc_params& p = h->p;
   for (int32_t s = 0; s < n_sub; ++s) {
     Forces F;
-    std::map<std::pair<int64_t, int64_t>, V3> new_hist;
+    std::vector<orc::HistEntry> new_hist;
     std::vector<V3> new_whist;
     evaluate(h, F, &new_hist, &new_whist);
+#pragma omp parallel for schedule(static) num_threads(h->threads > 1 ? h->threads : 1)
     for (int64_t i = 0; i < h->n; ++i) {
       double d = h->d[i], r = 0.5 * d;
       double m = h->rho[i] * (M_PI / 6.0 * d * d * d);
@@ -215,13 +286,18 @@ int64_t orc_num_contacts(orc_handle* h) { return (int64_t)h->hist.size(); }
 
 int orc_get_contacts(orc_handle* h, int64_t cap, int64_t* ij, double* xi) {
   int64_t k = 0;
-  for (auto& kv : h->hist) {
+  for (auto& e : h->hist) {
     if (k >= cap) return -1;
-    ij[2 * k] = kv.first.first;
-    ij[2 * k + 1] = kv.first.second;
-    orc::store(xi, k, kv.second);
+    ij[2 * k] = e.i;
+    ij[2 * k + 1] = e.j;
+    orc::store(xi, k, e.xi);
     ++k;
   }
+  return 0;
+}
+
+int orc_set_threads(orc_handle* h, int32_t threads) {
+  h->threads = threads < 1 ? 1 : threads;
   return 0;
 }
 

@@ -24,6 +24,7 @@ using namespace sedi;
 struct sedi_handle {
   sedi_params prm{};
   std::string err;
+  long long barrier_spins = kBarrierSpins;  // grid-barrier polls before SEDI_ETIMEOUT
   cudaStream_t stream = nullptr;
   cudaStream_t side = nullptr;  // capture of conditional bodies
   cudaStream_t own = nullptr;   // default stream of the handle (graphs need a real stream)
@@ -820,6 +821,11 @@ int sedi_create(const sedi_params* p, sedi_handle** out) {
   }
   h->form = p->precision_form;
   h->variant = p->substep_variant >= 0 && h->form != FORM_FP64 ? p->substep_variant : SUBSTEP_B128_LOOP;
+  // a lower limit on the smoother's grid-barrier waits, for failure-detection tests
+  if (const char* lim = std::getenv("SEDI_BARRIER_SPIN_LIMIT")) {
+    const long long v = std::atoll(lim);
+    if (v > 0) h->barrier_spins = v;
+  }
   fill_params(h);
   const int64_t C = h->P.C;
   h->U.assign(3 * C, 0.0);
@@ -1144,7 +1150,7 @@ static int smooth_dev(sedi_handle* h, int nf, const void* guess, int n_tau = -1,
   int rc = launch_smooth(h->form, h->P, h->phi, guess, nf, h->work, h->st, h->iters_dev,
                          rtol, h->prm.cg_max_iter, n_tau > 0 ? n_tau : h->prm.n_tau,
                          h->prm.tau_scheme, h->coef, h->P.graded ? &h->zs : nullptr,
-                         h->stream);
+                         h->stream, h->barrier_spins);
   if (rc) return fail(h, SEDI_ECUDA, "cooperative launch of the smoother failed: %s", cudaGetErrorString(cudaGetLastError()));
   return 0;
 }
@@ -1391,7 +1397,8 @@ static int ens_average(sedi_handle* h) {
   CK(cudaMemsetAsync(h->ens_iters, 0, sizeof(int) * 8 * B, h->stream));
   const double rtol = h->form == FORM_PLAIN ? std::max(h->prm.cg_rtol, 2e-6) : h->prm.cg_rtol;
   if (launch_smooth_batch(h->form, m.data(), B, 7, h->ens_smooth, rtol, h->prm.cg_max_iter,
-                          h->prm.n_tau, h->prm.tau_scheme, h->st.ctl, 1 << 30, h->stream))
+                          h->prm.n_tau, h->prm.tau_scheme, h->st.ctl, 1 << 30, h->stream,
+                          h->barrier_spins))
     return fail(h, SEDI_ECUDA, "cooperative launch of the batched smoother failed: %s",
                 cudaGetErrorString(cudaGetLastError()));
   launch_eps_out_ens(h->form, h->ens, h->stream);

@@ -525,14 +525,20 @@ namespace {
 
 constexpr int64_t kStaticWords = SEDI_STATIC_MAX_WORDS;
 // The solver keeps 8 narrow words per cell whatever n_fields is, so the limit is
-// 8 * cells <= kStaticWords (n_fields <= 8).  Upper bound of the solver scratch then:
-// the wide right-hand side and the BDF2 previous step (n_fields * cells <=
-// kStaticWords words each), three narrow [cells][8] arrays (8-byte words at most),
-// per-unit sums of up to kStaticWords / 2048 + 1 units of 256 cells, and the batch
-// tables of one mesh.
-constexpr int64_t kStaticUnits = kStaticWords / 2048 + 1;
+// 8 * cells <= kStaticWords (n_fields <= 8).  Upper bound of the solver scratch then
+// (FP64 form with BDF2, the largest case): the wide right-hand side and the BDF2
+// previous step (n_fields * cells <= kStaticWords words of 8 bytes each), three
+// narrow [cells][8] arrays (8-byte words), kSmoothSums per-unit sums of every field
+// for up to kStaticWords / (8 * 256) + 1 units of 256 cells, the unit table (4 bytes a
+// unit), and 64 KB for the batch tables of one mesh and the 256-byte alignment of
+// each part.
+constexpr int64_t kStaticUnits = kStaticWords / (kSmoothMaxFields * kSmoothUnitCells) + 1;
 constexpr int64_t kStaticWork =
-    ((8 * 5 * kStaticWords + kStaticUnits * 8 * 3 * 8 + 4 * kStaticUnits + 64 * 1024) + 255) / 256 * 256;
+    ((8 * 5 * kStaticWords + kStaticUnits * kSmoothMaxFields * kSmoothSums * 8 + 4 * kStaticUnits +
+      64 * 1024) + 255) / 256 * 256;
+static_assert(kMaxF == kSmoothMaxFields, "the static limit assumes the solver's field count");
+static_assert(2 * sizeof(SmoothMeshDev) + 8 * 256 <= 64 * 1024,
+              "the batch tables of one mesh must fit the static slack");
 // layout: phi [W words] | solver scratch | iters[8] | ctl, every part 256-byte aligned
 // (the control block holds 8-byte words that the compiler may access in pairs)
 constexpr int64_t kStaticBytes = 8 * kStaticWords + kStaticWork + 256 + (int64_t)sizeof(Ctl) + 256;
@@ -574,6 +580,16 @@ extern "C" int sedi_smooth_static(const sedi_params* p, int32_t nf, const double
                   (long long)kMaxF * C, (long long)kStaticWords);
     put_msg(msg, msg_len, buf);
     return SEDI_EINVAL;
+  }
+  // both buffers must be device memory (a host pointer would be read by the kernels)
+  for (const void* ptr : {(const void*)in, (const void*)out}) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess ||
+        (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+      cudaGetLastError();  // clear a sticky "invalid value" from the query
+      put_msg(msg, msg_len, "sedi_smooth_static: in and out must be device memory");
+      return SEDI_EINVAL;
+    }
   }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {

@@ -51,9 +51,9 @@ namespace sedi {
 
 namespace {
 
-constexpr int kThreads = 256;  // threads per block = cells per work unit
-constexpr int kMaxF = 8;
-constexpr int kQ = 4;          // per-unit sums: |r|^2, sum r, |b|^2, sum w r (graded mesh)
+constexpr int kThreads = kSmoothUnitCells;  // threads per block = cells per work unit
+constexpr int kMaxF = kSmoothMaxFields;
+constexpr int kQ = kSmoothSums;  // per-unit sums: |r|^2, sum r, |b|^2, sum w r (graded mesh)
 constexpr int kMaxRounds = 64;
 
 // ---------------------------------------------------------------- words
@@ -132,7 +132,7 @@ __device__ __forceinline__ int ldi(const int* p) { return __ldcg(p); }
 __device__ __forceinline__ double ldd(const double* p) { return __ldcg(p); }
 
 // Bounded grid barrier (co-residency guaranteed by the cooperative launch).
-__device__ bool grid_barrier(Ctl* ctl, unsigned nblocks) {
+__device__ bool grid_barrier(Ctl* ctl, unsigned nblocks, long long spin_limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* gen = &ctl->bar_gen;
@@ -146,7 +146,7 @@ __device__ bool grid_barrier(Ctl* ctl, unsigned nblocks) {
     } else {
       long long spins = 0;
       while (*gen == g) {
-        if (++spins > (1ll << 22)) {  // ~0.3 s
+        if (++spins > spin_limit) {  // ~0.3 s at the default kBarrierSpins
           atomicCAS((int*)&ctl->cg_status, 0, SEDI_ETIMEOUT);
           break;
         }
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
         if (use_guess && md.guess) ((T*)md.x)[k] = W::ld((const T*)md.guess + k);
       }
     }
-    if (!grid_barrier(a.ctl, G)) return;
+    if (!grid_barrier(a.ctl, G, a.spin_limit)) return;
     for (int round = 0; round < kMaxRounds; ++round) {
       // ---- true residual r = b - A x (wide), its narrow copy (interleaved, in d[0])
       //      and the unit sums |r|^2, sum r, |b|^2
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
         if (in) st8((N*)md.d[0] + c * kMaxF, rn);
         unit_sums<Acc>(v, nf, md.part + (u - md.u0) * (kMaxF * kQ));
       }
-      if (!grid_barrier(a.ctl, G)) return;
+      if (!grid_barrier(a.ctl, G, a.spin_limit)) return;
       // ---- owners: per-(mesh, field) sums over the mesh's units, decisions
       for (int bi = blockIdx.x; bi < a.B; bi += G) {
         const SmoothMeshDev& md = a.mesh[bi];
@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
       }
       // the slot of the next round was last read before the previous barrier
       if (blockIdx.x == 0 && threadIdx.x == 0) a.gflag[slot ^ 1] = 0;
-      if (!grid_barrier(a.ctl, G)) return;
+      if (!grid_barrier(a.ctl, G, a.spin_limit)) return;
       if (threadIdx.x == 0) s_K = ldi(a.gflag + slot);
       __syncthreads();
       const int K = s_K;
@@ -629,7 +629,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
           st8(Q + c * kMaxF, q);
           st8(Dnew + c * kMaxF, dn);
         }
-        if (!grid_barrier(a.ctl, G)) return;
+        if (!grid_barrier(a.ctl, G, a.spin_limit)) return;
       }
       if (K == 0) break;
     }
@@ -1021,7 +1021,8 @@ size_t smooth_work_bytes(int form, int64_t C, int nf, int scheme) {
 
 int launch_smooth(int form, const DevParams& P, void* phi, const void* guess, int nf, void* work,
                   const DevState& st, int* iters_dev, double rtol, int max_iter, int n_tau,
-                  int scheme, const double coef[3], const SmoothZ* z, cudaStream_t s) {
+                  int scheme, const double coef[3], const SmoothZ* z, cudaStream_t s,
+                  long long spin_limit) {
   SmoothMesh m{};
   m.phi = phi;
   m.guess = guess;
@@ -1037,7 +1038,7 @@ int launch_smooth(int form, const DevParams& P, void* phi, const void* guess, in
   if (z) m.z = *z;
   void* batch = (char*)work + align256(smooth_mesh_bytes(form, P.C, nf, scheme));
   return launch_smooth_batch(form, &m, 1, nf, batch, rtol, max_iter, n_tau, scheme, st.ctl,
-                             1 << 30, s);
+                             1 << 30, s, spin_limit);
 }
 
 size_t smooth_batch_bytes(int64_t B, int64_t U) {
@@ -1165,7 +1166,7 @@ void cluster_plan(int form, const SmoothMeshDev& m, int* csize, int* planes) {
 
 int launch_smooth_batch(int form, const SmoothMesh* meshes, int B, int nf, void* batch_work,
                         double rtol, int max_iter, int n_tau, int scheme, Ctl* ctl,
-                        int max_blocks, cudaStream_t s) {
+                        int max_blocks, cudaStream_t s, long long spin_limit) {
   if (B < 1 || B > kMaxBeds || nf < 1 || nf > kMaxF || (scheme != TAU_EULER && scheme != TAU_BDF2))
     return -1;
   // every mesh of a batch is graded or none is (one kernel instantiation per launch)
@@ -1202,6 +1203,7 @@ int launch_smooth_batch(int form, const SmoothMesh* meshes, int B, int nf, void*
   a.n_tau = n_tau;
   a.scheme = scheme;
   a.ctl = ctl;
+  a.spin_limit = spin_limit > 0 ? spin_limit : 1;
   SmoothMeshDev* tab_g = (SmoothMeshDev*)p;
   p += align256((size_t)B * sizeof(SmoothMeshDev));
   SmoothMeshDev* tab_c = (SmoothMeshDev*)p;

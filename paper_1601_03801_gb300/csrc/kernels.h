@@ -172,7 +172,20 @@ struct SmoothBatchDev {
   double rtol2;
   int32_t max_iter, n_tau, scheme;
   Ctl* ctl;                   // grid barrier and cg_status
+  long long spin_limit;       // polls of a grid-barrier wait before SEDI_ETIMEOUT
 };
+
+// Polls of one grid-barrier wait before the smoother gives up with SEDI_ETIMEOUT
+// (~0.3 s).  A handle may lower it (environment variable SEDI_BARRIER_SPIN_LIMIT,
+// read at sedi_create) so that tests can make the wait run out.
+constexpr long long kBarrierSpins = 1ll << 22;
+
+// Sizes shared by the smoothing solvers and the static scratch of sedi_smooth_static:
+// cells per work unit of the grid solver, fields the solver keeps per cell, and the
+// per-unit sums of each field (|r|^2, sum r, |b|^2, sum w r on a graded mesh).
+constexpr int kSmoothUnitCells = 256;
+constexpr int kSmoothMaxFields = 8;
+constexpr int kSmoothSums = 4;
 
 int64_t smooth_units(int64_t C);
 // scratch of one mesh, and of the batch tables
@@ -183,13 +196,13 @@ size_t smooth_batch_bytes(int64_t B, int64_t U);
 // or -3 (launch failed).
 int launch_smooth_batch(int form, const SmoothMesh* meshes, int B, int nf, void* batch_work,
                         double rtol, int max_iter, int n_tau, int scheme, Ctl* ctl,
-                        int max_blocks, cudaStream_t s);
+                        int max_blocks, cudaStream_t s, long long spin_limit = kBarrierSpins);
 // Single mesh: work holds smooth_work_bytes(form, C, nf, scheme) = mesh + batch scratch.
 size_t smooth_work_bytes(int form, int64_t C, int nf, int scheme);
 int launch_smooth(int form, const DevParams& P, void* phi, const void* guess, int nf,
                   void* work, const DevState& st, int* iters_dev, double rtol, int max_iter,
                   int n_tau, int scheme, const double coef[3], const SmoothZ* z,
-                  cudaStream_t s);
+                  cudaStream_t s, long long spin_limit = kBarrierSpins);
 void launch_average_out(int form, const void* phi, const DevParams& P, void* ufe, double* eps,
                         double* Us, double* F, cudaStream_t s);
 void launch_phi_convert(int form, const void* phi, double* out, int64_t n, int to_double,

@@ -19,11 +19,12 @@ Sec. 4.1, 4.3 and 5.2, Table 1; every one is synthetic):
   of a 100 x 100 x H mm box of quiescent fluid, the paper's linear contact
   (k_n = 800 N/m, e = 0.97, mu = 0.1); the viscosity sets the Stokes number.
 
-Beds are made without any dynamics: a periodic block is seeded on an FCC
-lattice of spacing ~1.1 median diameters (packing fraction ~0.58), overlaps are
-removed by repeated geometric projection (each overlapping pair is pushed apart
-along its centre line, the wall pushes up), the few spheres still overlapping
-are shrunk to touch, and the block is tiled over the channel.
+Beds are made without the method (no contact law of the paper, no time
+integration of it, no GPU): a small periodic block is seeded on an FCC lattice
+near the final density and relaxed under gravity by FIRE energy minimisation of
+a harmonic overlap energy (_fire_block), which gives the structure of a settled
+bed (about five contacts per sphere at a packing fraction ~0.6); the block is
+tiled over the channel.  The same inputs feed the CUDA library and the oracle.
 """
 from __future__ import annotations
 
@@ -138,58 +139,88 @@ def _fcc_block(n, d_all, Lx, Ly, spacing, seed):
     return sites
 
 
-def _pairs(x, d, Lx, Ly):
+def _fire_block(d, Lx, Ly, seed, k=40.0, rho=2500.0, rho_f=1000.0, iters=6000):
+    """A load-bearing packing of spheres of diameters d in a periodic Lx x Ly column
+    standing on a floor at z = 0, made without the method's contact law or time
+    integration: from a jittered FCC start near the final density (packing fraction
+    ~0.56), the energy sum_pairs k/2 overlap^2 + sum_i buoyant weight_i z_i (a wall
+    spring of 2k keeps the spheres above the floor) is lowered by FIRE (Bitzek,
+    Koskinen, Gaehler, Moseler & Gumbsch, PRL 97, 170201, 2006) for a fixed number
+    of iterations.  The spheres sink until the weight rests on a network of small
+    overlaps (k = 40 N/m gives overlaps of ~1e-7 m under the weight of the bed, the
+    order of a Hertz contact under the same load): about five contacts per sphere at
+    a packing fraction ~0.6, the structure of a settled sediment bed.  The run is
+    not converged to force balance; the method's own dynamics finish the settling.
+    Pairs are kept in canonical (i, j) order so the sums run in a fixed order."""
+    from scipy.sparse import csr_matrix
     from scipy.spatial import cKDTree
 
-    tree = cKDTree(x, boxsize=(Lx, Ly, 1e3))
-    p = tree.query_pairs(d.max() * 1.0001, output_type="ndarray")
-    i, j = p[:, 0], p[:, 1]
-    dx = x[j] - x[i]
-    dx[:, 0] -= Lx * np.round(dx[:, 0] / Lx)
-    dx[:, 1] -= Ly * np.round(dx[:, 1] / Ly)
-    return i, j, dx, np.sqrt(np.einsum("ij,ij->i", dx, dx))
-
-
-def _relax(x, d, Lx, Ly, iters=150):
-    """Remove overlaps geometrically (no forces, no time): each overlapping pair is
-    pushed apart along its centre line, every particle moving by the mean of its
-    pushes; the wall pushes up.  Particles still overlapping afterwards are shrunk
-    to touch (the larger of each pair; a few percent of a diameter at most)."""
-    n = len(x)
+    n = len(d)
     r = 0.5 * d
+    m = rho * np.pi / 6 * d ** 3
+    g = G * (1.0 - rho_f / rho)
+    a = (0.74 * np.mean(d ** 3) / 0.56) ** (1.0 / 3.0)  # FCC spacing for phi ~ 0.56
+    x = _fcc_block(n, d, Lx, Ly, a, seed)
+    v = np.zeros_like(x)
+    skin = 0.2 * d.max()
+    cut = d.max() + skin
+    dt0 = 0.05 * np.sqrt(m.min() / k)
+    dt, dt_max, alpha, n_pos = dt0, 10.0 * dt0, 0.1, 0
+    per = np.array([Lx, Ly, 1.0])
+    wrap = np.array([1.0, 1.0, 0.0])
+
+    def pairs():
+        xx = x.copy()
+        xx[:, 0] %= Lx
+        xx[:, 1] %= Ly
+        p = cKDTree(xx, boxsize=(Lx, Ly, 1e9)).query_pairs(cut, output_type="ndarray")
+        p = p[np.lexsort((p[:, 1], p[:, 0]))]
+        i, j = p[:, 0], p[:, 1]
+        q = np.arange(len(i))
+        B = csr_matrix((np.concatenate([-np.ones(len(i)), np.ones(len(i))]),
+                        (np.concatenate([i, j]), np.concatenate([q, q]))), shape=(n, len(i)))
+        return i, j, r[i] + r[j], B
+
+    i, j, s, B = pairs()
+    x_ref = x.copy()
+    weight = m[:, None] * np.array([0.0, 0.0, -g])
+    inv_m = 1.0 / m[:, None]
+
+    def force():
+        dx = x[j] - x[i]
+        dx -= wrap * per * np.round(dx / per)
+        dist = np.sqrt(np.einsum("ij,ij->i", dx, dx))
+        ov = np.maximum(s - dist, 0.0)
+        F = weight + B @ ((k * ov / dist)[:, None] * dx)
+        below = r - x[:, 2]
+        F[:, 2] += np.where(below > 0, 2.0 * k * below, 0.0)
+        return F
+
+    F = force()
     for _ in range(iters):
-        x[:, 0] %= Lx; x[:, 1] %= Ly
-        x[:, 2] = np.maximum(x[:, 2], r)
-        i, j, dx, dist = _pairs(x, d, Lx, Ly)
-        ov = r[i] + r[j] - dist
-        m = ov > 0
-        if not np.any(m):
-            break
-        i, j, dx, dist, ov = i[m], j[m], dx[m], dist[m], ov[m]
-        u = dx / dist[:, None]
-        push = 0.51 * ov
-        cnt = np.bincount(i, minlength=n) + np.bincount(j, minlength=n)
-        disp = np.zeros_like(x)
-        for a in range(3):
-            disp[:, a] -= np.bincount(i, weights=push * u[:, a], minlength=n)
-            disp[:, a] += np.bincount(j, weights=push * u[:, a], minlength=n)
-        x += disp / np.maximum(cnt, 1)[:, None]
-    x[:, 0] %= Lx; x[:, 1] %= Ly
-    x[:, 2] = np.maximum(x[:, 2], r)
-    for _ in range(50):
-        i, j, dx, dist = _pairs(x, d, Lx, Ly)
-        m = 0.5 * (d[i] + d[j]) - dist > 0
-        if not np.any(m):
-            break
-        big = np.where(d[i] >= d[j], i, j)
-        other = np.where(big == i, j, i)
-        newd = np.full(n, np.inf)
-        np.minimum.at(newd, big[m], 2 * dist[m] - d[other[m]])
-        sel = np.isfinite(newd)
-        d[sel] = np.minimum(d[sel], newd[sel] * (1 - 1e-9))
-    wall = x[:, 2] < 0.5 * d
-    d[wall] = 2 * x[wall, 2]
-    return x, d
+        P = float(np.vdot(F, v))
+        if P > 0:
+            vn = np.sqrt(np.vdot(v, v))
+            fn = np.sqrt(np.vdot(F, F))
+            v = (1.0 - alpha) * v + (alpha * vn / max(fn, 1e-300)) * F
+            n_pos += 1
+            if n_pos > 5:
+                dt = min(1.1 * dt, dt_max)
+                alpha *= 0.99
+        else:
+            n_pos, dt, alpha = 0, 0.5 * dt, 0.1
+            v[:] = 0.0
+        v += dt * F * inv_m
+        x += dt * v
+        if np.abs(x - x_ref).max() > 0.5 * skin:
+            i, j, s, B = pairs()
+            x_ref = x.copy()
+        F = force()
+    x[:, 0] %= Lx
+    x[:, 1] %= Ly
+    x[:, 0] = np.where(x[:, 0] >= Lx, x[:, 0] - Lx, x[:, 0])
+    x[:, 1] = np.where(x[:, 1] >= Ly, x[:, 1] - Ly, x[:, 1])
+    return x
 
 
 def _cache_path(tag):
@@ -198,24 +229,24 @@ def _cache_path(tag):
     return os.path.join(root, tag + ".npz")
 
 
-def packed_bed(n_total, tiles, block_xy, dsample, seed, spacing):
-    """Tile a relaxed periodic block of n_total / prod(tiles) spheres."""
-    tag = f"bedv3_{n_total}_{tiles[0]}x{tiles[1]}_{block_xy[0]:.4g}_{block_xy[1]:.4g}_{seed}"
+def settled_bed(n_total, tiles, block_xy, dsample, seed, iters=6000):
+    """n_total spheres: one settled periodic block of n_total / prod(tiles) spheres
+    (_fire_block) repeated tiles[0] x tiles[1] times over the floor.  Cached on disk
+    (SEDI_CACHE, default /tmp/sedi_workloads) by its parameters."""
+    tag = (f"fire1_{n_total}_{tiles[0]}x{tiles[1]}_{block_xy[0]:.4g}_{block_xy[1]:.4g}_{seed}_{iters}")
     path = _cache_path(tag)
     if os.path.exists(path):
         z = np.load(path)
         return z["x"], z["d"]
     nb = n_total // (tiles[0] * tiles[1])
-    rng = _rng(seed)
-    d = dsample(rng, nb)
-    x = _fcc_block(nb, d, block_xy[0], block_xy[1], spacing, seed + 1)
-    x, d = _relax(x, d, block_xy[0], block_xy[1])
-    xs, ds = [], []
-    for tx in range(tiles[0]):
-        for ty in range(tiles[1]):
-            xs.append(x + np.array([tx * block_xy[0], ty * block_xy[1], 0.0]))
-            ds.append(d)
-    X = np.concatenate(xs); D = np.concatenate(ds)
+    d = dsample(_rng(seed), nb)
+    x = _fire_block(d, block_xy[0], block_xy[1], seed + 1, iters=iters)
+    off = np.stack(np.meshgrid(np.arange(tiles[0]) * block_xy[0], np.arange(tiles[1]) * block_xy[1],
+                               indexing="ij"), -1).reshape(-1, 2)
+    X = np.repeat(x[None], len(off), 0)
+    X[:, :, :2] += off[:, None, :]
+    X = X.reshape(-1, 3)
+    D = np.tile(d, len(off))
     # the offsets can round a coordinate up to the periodic bound: keep [0, L)
     for a in range(2):
         L = tiles[a] * block_xy[a]
@@ -223,6 +254,22 @@ def packed_bed(n_total, tiles, block_xy, dsample, seed, spacing):
         X[:, a] = np.minimum(X[:, a], np.nextafter(L, 0.0))
     np.savez(path, x=X, d=D)
     return X, D
+
+
+def storage_round(a, form):
+    """The value the CUDA library holds for an FP64 input in each arithmetic form: one
+    FP32 word (plain), a pair of FP32 words hi + lo with hi = fl32(a) and
+    lo = fl32(a - hi) (split: 48-bit significand), or the input itself (fp64).  Tests
+    give the oracle these values, so both sides start from the same state without
+    reading anything back from the CUDA path."""
+    a = np.asarray(a, dtype=np.float64)
+    if form == "fp64":
+        return a.copy()
+    hi = a.astype(np.float32).astype(np.float64)
+    if form == "plain":
+        return hi
+    lo = (a - hi).astype(np.float32).astype(np.float64)
+    return hi + lo
 
 
 def lognormal_d(d50, sigma):
@@ -254,78 +301,22 @@ def log_law(ncell, lo, hi, z_bed, u_star, z0):
     return U.reshape(-1, 3)
 
 
-def bed_case(seed=1601038012, n=200_000, settled=False):
-    """Sheared sediment bed: 200k lognormal spheres, log-law flow.  settled=True
-    runs the settling prep of the method on the GPU (see settle_bed) so that the
-    bed carries its weight through contacts; the flow profile starts at the
-    settled bed top."""
+def bed_case(seed=1601038012, n=200_000):
+    """Sheared sediment bed: 200,000 lognormal spheres (median 0.5 mm, sigma_ln 0.1,
+    cut at +-3 sigma) settled into a bed (settled_bed: an 8 x 4 mm block of 3,125
+    spheres tiled 8 x 8) in a periodic 64 x 32 x 64 mm channel, wall at z = 0, under
+    the log-law flow u* = 0.02 m/s that starts at the bed top; 64 x 32 x 64 mesh."""
     Lx, Ly, Lz = 64e-3, 32e-3, 64e-3
     d50 = 0.5e-3
-    tiles = (4, 2)
-    x, d = packed_bed(n, tiles, (Lx / tiles[0], Ly / tiles[1]), lognormal_d(d50, 0.1), seed,
-                      spacing=1.1 * d50)
+    tiles = (8, 8)
+    x, d = settled_bed(n, tiles, (Lx / tiles[0], Ly / tiles[1]), lognormal_d(d50, 0.1), seed)
     prm = default_params(hi=(Lx, Ly, Lz), ncell=(64, 32, 64), wall_hi=(0, 0, 0),
                          bandwidth=(3 * d50,) * 3)
     nn = len(x)
     parts = dict(x=x, v=np.zeros((nn, 3)), w=np.zeros((nn, 3)), d=d, rho=np.full(nn, 2500.0))
-    if settled:
-        parts = settle_bed(prm, parts)
-    z_bed = float(np.quantile(parts["x"][:, 2] + 0.5 * d, 0.99))
+    z_bed = float(np.quantile(x[:, 2] + 0.5 * d, 0.99))
     U = log_law(prm["ncell"], prm["lo"], prm["hi"], z_bed, 0.02, d50 / 30.0)
     return prm, parts, dict(U=U, z_bed=z_bed)
-
-
-def _library_tag():
-    """Short hash of the CUDA sources, so a bed settled by one build of the library
-    is not reused by another."""
-    import hashlib
-    root = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
-    h = hashlib.sha256()
-    for f in sorted(os.listdir(root)):
-        with open(os.path.join(root, f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:12]
-
-
-def settle_bed(prm, parts, substeps=40_000, chunk=2000, log=None):
-    """Settling prep run of the method itself (on the GPU, not timed): the packed bed
-    falls into load-bearing contact under gravity in quiescent water, with
-    lubrication off and a low restitution so the run dissipates quickly.  Returns
-    the settled parts with zero velocities and spins; cached on disk per library
-    build."""
-    from . import sedi
-
-    tag = "settled_" + _library_tag() + f"_{len(parts['x'])}_{substeps}_" + \
-        hashlib_of(parts["x"], parts["d"])
-    path = _cache_path(tag)
-    if os.path.exists(path):
-        z = np.load(path)
-        return dict(parts, x=z["x"], v=np.zeros_like(z["x"]), w=np.zeros_like(z["x"]))
-    # a fixed launch shape: the prep run's early, loose state is not the workload the
-    # autotuner should rank the shapes on
-    g = sedi.Sedi(dict(prm, precision_form="split", lubrication=0, added_mass=0, restitution=0.3,
-                       substep_variant=5))
-    g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
-    done = 0
-    while done < substeps:
-        k = min(chunk, substeps - done)
-        g.step(k)
-        done += k
-        if log is not None:
-            ij, _ = g.contacts()
-            _, v, _, _ = g.get_particles()
-            log(done, 2.0 * len(ij) / len(parts["x"]), float(np.abs(v).max()))
-    x = g.get_particles()[0]
-    np.savez(path, x=x)
-    return dict(parts, x=x, v=np.zeros_like(x), w=np.zeros_like(x))
-
-
-def hashlib_of(*arrays):
-    import hashlib
-    h = hashlib.sha256()
-    for a in arrays:
-        h.update(np.ascontiguousarray(a).tobytes())
-    return h.hexdigest()[:12]
 
 
 def lattice_bed(n, L, d, seed, jitter=0.01, spacing=1.05):
@@ -406,17 +397,39 @@ def turbulent_like(ncell, lo, hi, mean=(0.3, 0.0, 0.0), rms=0.03, sigma_cells=2.
 
 
 def large_case(seed=1601038013, n=10_000_000):
-    """10M spheres, d ~ U[0.4, 0.6] mm, 400 x 200 x 100 mm, noisy mean flow."""
+    """10M spheres, d ~ U[0.4, 0.6] mm, settled into a bed (settled_bed: a 4 x 4 mm
+    block of 2,000 spheres tiled 100 x 50, ~14 mm high at a packing fraction ~0.6) in
+    a periodic 400 x 200 x 100 mm box with a wall at z = 0; mean flow 0.3 m/s plus
+    Gaussian-filtered noise of rms 0.03 m/s on a 256 x 128 x 64 mesh."""
     Lx, Ly, Lz = 400e-3, 200e-3, 100e-3
-    tiles = (20, 10)
-    x, d = packed_bed(n, tiles, (Lx / tiles[0], Ly / tiles[1]), uniform_d(0.4e-3, 0.6e-3), seed,
-                      spacing=0.57e-3)
+    tiles = (100, 50)
+    x, d = settled_bed(n, tiles, (Lx / tiles[0], Ly / tiles[1]), uniform_d(0.4e-3, 0.6e-3), seed)
     prm = default_params(hi=(Lx, Ly, Lz), ncell=(256, 128, 64), wall_hi=(0, 0, 0),
                          bandwidth=(1.5e-3,) * 3)
     U, DU = turbulent_like(prm["ncell"], prm["lo"], prm["hi"], seed=seed + 5)
     nn = len(x)
     parts = dict(x=x, v=np.zeros((nn, 3)), w=np.zeros((nn, 3)), d=d, rho=np.full(nn, 2500.0))
     return prm, parts, dict(U=U, DUDt=DU)
+
+
+def large_patch(prm, parts, fl, cells=(64, 64)):
+    """A bounded sample of the large bed: the spheres and mesh cells of the corner
+    patch [0, cells[0] h) x [0, cells[1] h) (h = 1.5625 mm, so the default patch is
+    100 x 100 mm: 1/8 of the bed), periodic at the patch edges.  The bed repeats every
+    4 mm, so the patch is the same bed; the fluid fields are the patch's cells of the
+    full fields (they do not wrap smoothly at the patch edges, which changes no cost)."""
+    nc = prm["ncell"]
+    h = [(prm["hi"][a] - prm["lo"][a]) / nc[a] for a in range(3)]
+    hi = (cells[0] * h[0], cells[1] * h[1], prm["hi"][2])
+    x = parts["x"]
+    keep = (x[:, 0] < hi[0]) & (x[:, 1] < hi[1])
+    sub = {k: parts[k][keep] for k in ("x", "v", "w", "d", "rho")}
+    pprm = dict(prm, hi=hi, ncell=(cells[0], cells[1], nc[2]))
+
+    def cut(f):
+        return f.reshape(nc[2], nc[1], nc[0], 3)[:, :cells[1], :cells[0]].reshape(-1, 3)
+
+    return pprm, sub, dict(U=cut(fl["U"]), DUDt=cut(fl["DUDt"]))
 
 
 def random_fields(ncell, nf, seed, scale=1.0):

@@ -1,6 +1,7 @@
 """Ensembles of independent beds (n_beds > 1): one launch per phase over all beds
 must give every bed exactly the bits it gets when run alone in a single-bed
-handle (whose parity with the oracle the other GPU tests establish)."""
+handle, and an ensemble bed matches the FP64 oracle directly (forces, springs,
+100-step trajectory, averaging)."""
 import numpy as np
 import pytest
 
@@ -10,8 +11,9 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
+from oracle import oracle as orc  # noqa: E402
 from paper_1601_03801_gb300 import sedi  # noqa: E402
-from paper_1601_03801_gb300.workloads import ensemble_case  # noqa: E402
+from paper_1601_03801_gb300.workloads import ensemble_case, storage_round  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -132,3 +134,37 @@ def test_ensemble_errors(ens):
         single.set_bed(0, beds[0]["lo"], beds[0]["hi"], beds[0]["ncell"])
     with pytest.raises(sedi.SediError):
         sedi.Sedi(dict(prm, n_beds=2000))
+
+
+@pytest.mark.parametrize("b", [0, 4])
+def test_ensemble_beds_match_oracle(ens, b):
+    """One bed of the batched launches against the FP64 oracle on the same inputs:
+    forces at the start (1e-5 of the largest force of each kind), springs after 20
+    substeps (1e-5 of the largest spring), positions after 100 substeps (1e-4 d) and
+    the averaged solid fraction (1e-6 of its maximum)."""
+    prm, beds = ens
+    E = make_ensemble(prm, beds)
+    bd = beds[b]
+    p = bd["parts"]
+    o = orc.Oracle(dict(prm, lo=bd["lo"], hi=bd["hi"], ncell=bd["ncell"]))
+    o.set_particles(*(storage_round(p[k], "split") for k in ("x", "v", "w")), p["d"], p["rho"])
+    o.set_fluid(U=bd["U"])
+    fg, fo = E.compute_forces(bed=b), o.forces()
+    for k in ("contact", "lub", "fluid", "torque"):
+        ref = np.abs(fo[k]).max()
+        assert ref > 0 and np.abs(fg[k] - fo[k]).max() <= 1e-5 * ref, k
+    E.step(20)
+    o.step(20)
+    ijg, xig = E.contacts(bed=b)
+    ijo, xio = o.contacts()
+    assert len(ijo) > 10 and np.array_equal(ijg, ijo)
+    assert np.abs(xig - xio).max() <= 1e-5 * np.abs(xio).max()
+    E.step(80)
+    o.step(80)
+    L = np.array(bd["hi"]) - np.array(bd["lo"])
+    dx = E.get_particles(bed=b)[0] - o.get_particles()[0]
+    dx -= L * np.round(dx / L) * np.array(prm["periodic"])
+    assert (np.abs(dx).max(axis=1) / p["d"]).max() <= 1e-4
+    eg = E.average(bed=b)[0]
+    eo = o.average()[0]
+    assert np.abs(eg - eo).max() <= 1e-6 * np.abs(eo).max()
