@@ -56,6 +56,7 @@ struct ForceConsts {
 template <class S>
 struct BoxS {
   S lo[3], hi[3], L[3];
+  S h[3];  // uniform cell size (hi - lo) / ncell per axis
 };
 
 // Launch-time parameters (precomputed on the host from sedi_params).
@@ -319,6 +320,11 @@ __device__ __forceinline__ const BedView& bed_view(const BedView* views) {
 // A list entry holds the partner index in bits 0-30 and, in bit 31, whether the
 // owner comes first in canonical pair order (lower caller index).
 constexpr uint32_t kFirstBit = 0x80000000u;
+// Bring the line of p into L1 ahead of its use (no register is held while in flight).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 __host__ __device__ __forceinline__ int32_t nbr_index(int32_t e) { return e & 0x7fffffff; }
 __host__ __device__ __forceinline__ bool nbr_first(int32_t e) { return ((uint32_t)e & kFirstBit) != 0; }
 

@@ -220,6 +220,10 @@ void fill_params(sedi_handle* h) {
     split_double(p.lo[a], &P.bdd.lo[a]);
     split_double(p.hi[a], &P.bdd.hi[a]);
     split_double(P.L[a], &P.bdd.L[a]);
+    const double hc = P.L[a] / p.ncell[a];
+    P.bf.h[a] = (float)hc;
+    P.bdb.h[a] = hc;
+    split_double(hc, &P.bdd.h[a]);
   }
   P.lubrication = p.lubrication ? 1 : 0;
   P.drag = p.drag ? 1 : 0;

@@ -30,6 +30,44 @@ __device__ __forceinline__ void axis_w(F s, int n, int per, int* i0, int* i1, F*
   }
 }
 
+// The same weights from the integer part kf = floor(s) and a fraction f that may lie
+// within rounding outside [0, 1) (the cell-relative form below).
+template <class F>
+__device__ __forceinline__ void axis_w_kf(F kf, F f, int n, int per, int* i0, int* i1, F* fo) {
+  int k = (int)kf;
+  if (f < F(0)) {
+    k -= 1;
+    f += F(1);
+  } else if (f >= F(1)) {
+    k += 1;
+    f -= F(1);
+  }
+  if (per) {
+    if (k < 0) k += n;
+    if (k >= n) k -= n;
+    *i0 = k;
+    *i1 = (k + 1 == n) ? 0 : k + 1;
+    *fo = f;
+  } else if (n < 2) {
+    *i0 = 0;
+    *i1 = 0;
+    *fo = F(0);
+  } else {
+    // s = k + f clamped to [0, n - 1]
+    if (k < 0) {
+      k = 0;
+      f = F(0);
+    }
+    if (k > n - 2) {
+      k = n - 2;
+      f = F(1);
+    }
+    *i0 = k;
+    *i1 = k + 1;
+    *fo = f;
+  }
+}
+
 // Fluid force on one particle (Sec. 2.3): drag (Eq. 3-6, Syamlal-O'Brien), the
 // pressure-gradient force, added mass (Eq. 8) and, when switched on, Saffman lift
 // (Eq. 7, read as C_l rho_f nu^0.5 d^2 |omega|^-0.5 (w x omega), w = U_f - u_p).
@@ -80,7 +118,17 @@ __device__ __forceinline__ void fluid_force(const DevParams& P, const ForceConst
     }
     F rel = NS::f(NS::sub(x[a], B.lo[a]));
     F s = rel * K.inv_h[a] - F(0.5);
-    axis_w<F>(s, P.nc[a], P.periodic[a], &i0[a], &i1[a], &fr[a]);
+    if constexpr (NS::kExtended) {
+      // cell-relative: the cell k = floor(s) from FP32, the fraction from the
+      // double-float offset x - c_k to that cell's centre, so the weight keeps
+      // ~1e-7 of a cell on any box (s itself carries ~n 6e-8 of rounding)
+      const F kf = xfloor(s);
+      const S ck = NS::add(B.lo[a], NS::mul_f(B.h[a], kf + F(0.5)));
+      const F f = NS::f(NS::sub(x[a], ck)) * K.inv_h[a];
+      axis_w_kf<F>(kf, f, P.nc[a], P.periodic[a], &i0[a], &i1[a], &fr[a]);
+    } else {
+      axis_w<F>(s, P.nc[a], P.periodic[a], &i0[a], &i1[a], &fr[a]);
+    }
   }
   F U[3] = {0, 0, 0}, G[3] = {0, 0, 0}, Om[3] = {0, 0, 0}, eps = 0;
   const int64_t nx = P.nc[0], ny = P.nc[1];
@@ -131,13 +179,13 @@ __device__ __forceinline__ void fluid_force(const DevParams& P, const ForceConst
     F ef = F(1) - es;
     F w0 = U[0] - v[0], w1 = U[1] - v[1], w2 = U[2] - v[2];
     F wm = xsqrt(w0 * w0 + w1 * w1 + w2 * w2);
-    F Re = d * wm / K.nu_f;
+    F Re = xdiv(d * wm, K.nu_f);
     F A1 = xpow_drag(ef, F(4.14));
     F A2 = ef <= F(0.85) ? F(0.8) * xpow_drag(ef, F(1.28)) : xpow_drag(ef, F(2.65));
     F t = F(0.06) * Re;
     F Vr = F(0.5) * (A1 - t + xsqrt(t * t + F(0.12) * Re * (F(2) * A2 - A1) + A1 * A1));
-    F c = F(0.63) * xsqrt(wm) + F(4.8) * xsqrt(Vr * K.nu_f / d);
-    F coef = F(0.75) * Vp * K.rho_f * c * c / (Vr * Vr * d);
+    F c = F(0.63) * xsqrt(wm) + F(4.8) * xsqrt(xdiv(Vr * K.nu_f, d));
+    F coef = xdiv(F(0.75) * Vp * K.rho_f * c * c, Vr * Vr * d);
     out[0] += coef * w0;
     out[1] += coef * w1;
     out[2] += coef * w2;
@@ -145,7 +193,7 @@ __device__ __forceinline__ void fluid_force(const DevParams& P, const ForceConst
   if (LIFT && P.lift) {
     const F om = xsqrt(Om[0] * Om[0] + Om[1] * Om[1] + Om[2] * Om[2]);
     if (om > F(0)) {
-      const F s = K.lift_c * d * d / xsqrt(om);
+      const F s = K.lift_c * d * d * xrsqrt(om);
       const F w0 = U[0] - v[0], w1 = U[1] - v[1], w2 = U[2] - v[2];
       out[0] += s * (w1 * Om[2] - w2 * Om[1]);
       out[1] += s * (w2 * Om[0] - w0 * Om[2]);

@@ -12,6 +12,14 @@ __device__ __forceinline__ double xpow(double a, double b) { return pow(a, b); }
 // hardware approximations; relative error ~1e-6 for a in [0.1, 1], b <= 4.14).
 __device__ __forceinline__ float xpow_drag(float a, float b) { return __powf(a, b); }
 __device__ __forceinline__ double xpow_drag(double a, double b) { return pow(a, b); }
+// Quotient and reciprocal square root in the force word.  FP32: CUDA's fast forms
+// (__fdividef, rsqrtf: ~2 ulp, so ~2e-7 relative, far inside the 1e-5 force tolerance;
+// __fdividef returns 0 for |b| > 2^126, far outside any value here).  FP64: correctly
+// rounded, for the parity form.
+__device__ __forceinline__ float xdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double xdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float xrsqrt(float a) { return rsqrtf(a); }
+__device__ __forceinline__ double xrsqrt(double a) { return 1.0 / sqrt(a); }
 __device__ __forceinline__ float xlog(float a) { return logf(a); }
 __device__ __forceinline__ double xlog(double a) { return log(a); }
 __device__ __forceinline__ float xfloor(float a) { return floorf(a); }

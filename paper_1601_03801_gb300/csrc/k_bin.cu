@@ -61,10 +61,21 @@ __device__ __forceinline__ int bin_axis(S x, const DevParams& P, int a) {
   return b;
 }
 
+// Storage order of the bins: z fastest, then y, then x.  A bed is thin in z (gravity)
+// and the empty bins above it hold no particles, so every listed partner lies within
+// about (bins in y) x (occupied bins in z) bins of a particle in this order -- tens of
+// thousands of particles even for a 400 x 200 mm bed, against a whole bin layer
+// (hundreds of thousands) with x fastest -- and the partner records a kernel reads stay
+// in L2.  The order changes no list: slots are appended bin by bin in a fixed (oz,
+// oy, ox) sequence and by caller index inside a bin.
+__device__ __forceinline__ int64_t bin_key(int bx, int by, int bz, const DevParams& P) {
+  return ((int64_t)bx * P.nb[1] + by) * P.nb[2] + bz;
+}
+
 template <class S>
 __device__ __forceinline__ int64_t bin_index(const Quad<S>& p, const DevParams& P) {
   int bx = bin_axis<S>(p.a, P, 0), by = bin_axis<S>(p.b, P, 1), bz = bin_axis<S>(p.c, P, 2);
-  return ((int64_t)bz * P.nb[1] + by) * P.nb[0] + bx;
+  return bin_key(bx, by, bz, P);
 }
 
 template <int FORM>
@@ -287,7 +298,7 @@ __device__ __forceinline__ void build_body(const DevState& st, const DevParams& 
           int tx = c[0] + ox;
           if (P.periodic[0]) tx = (tx + P.nb[0]) % P.nb[0];
           else if (tx < 0 || tx >= P.nb[0]) continue;
-          const int64_t b = ((int64_t)tz * P.nb[1] + ty) * P.nb[0] + tx;
+          const int64_t b = bin_key(tx, ty, tz, P);
           const int s0 = st.bin_start[b], s1 = s0 + st.bin_count[b];
           for (int j = s0; j < s1; ++j) {
             if (j == i) continue;

@@ -63,10 +63,10 @@ __device__ __forceinline__ V3<F> hm_core(const ForceConsts<F>& K, V3<F> n, F del
     xi[1] = NS::fma_ff(xi_old[1], -proj, n.y);
     xi[2] = NS::fma_ff(xi_old[2], -proj, n.z);
     if (len2 > F(0)) {
-      F t = proj * proj / len2;
+      F t = xdiv(proj * proj, len2);
       if (t < F(1)) {
         F s1 = xsqrt(F(1) - t);
-        F scm1 = t / (s1 * (F(1) + s1));  // 1/sqrt(1-t) - 1
+        F scm1 = xdiv(t, s1 * (F(1) + s1));  // 1/sqrt(1-t) - 1
         F r0 = NS::f(xi[0]), r1 = NS::f(xi[1]), r2 = NS::f(xi[2]);
         xi[0] = NS::fma_ff(xi[0], scm1, r0);
         xi[1] = NS::fma_ff(xi[1], scm1, r1);
@@ -86,11 +86,11 @@ __device__ __forceinline__ V3<F> hm_core(const ForceConsts<F>& K, V3<F> n, F del
   F ft = xsqrt(Ft.x * Ft.x + Ft.y * Ft.y + Ft.z * Ft.z);
   F fnm = xabs(fn_s);
   if (ft > K.mu * fnm) {
-    F sc = K.mu * fnm / ft;
+    F sc = xdiv(K.mu * fnm, ft);
     Ft.x *= sc;
     Ft.y *= sc;
     Ft.z *= sc;
-    F inv = F(-1) / St;
+    F inv = xdiv(F(-1), St);
     xi[0] = NS::from_f((Ft.x + ct * vt.x) * inv);
     xi[1] = NS::from_f((Ft.y + ct * vt.y) * inv);
     xi[2] = NS::from_f((Ft.z + ct * vt.z) * inv);
@@ -159,12 +159,12 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
   const F dist = xsqrt(NS::f(d2));
   const F sF = NS::f(ssum);
   // r_A + r_B - |dx| without cancellation: (s^2 - d^2) / (s + d)
-  const F delta = NS::kExtended ? NS::f(num) / (sF + dist) : sF - dist;
+  const F delta = NS::kExtended ? xdiv(NS::f(num), sF + dist) : sF - dist;
   const F dxf[3] = {NS::f(dxs[0]), NS::f(dxs[1]), NS::f(dxs[2])};
   o.contact = delta > F(0);
   o.lub = P.lubrication && (-delta < K.lub_out * sF);
   if (!o.contact && !o.lub) return o;
-  const F inv_d = F(1) / dist;
+  const F inv_d = xrsqrt(NS::f(d2));
   const V3<F> n{dxf[0] * inv_d, dxf[1] * inv_d, dxf[2] * inv_d};
   const Quad<S> Vj = ldq(vel + j);
   const F vj[3] = {NS::f(Vj.a), NS::f(Vj.b), NS::f(Vj.c)};
@@ -192,8 +192,8 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
     const F rA = NS::f(A.d), rB = NS::f(Bq.d);
     const F mA = i_lo ? mi : NS::f(Vj.d);
     const F mB = i_lo ? NS::f(Vj.d) : mi;
-    const F Rs = rA * rB / (rA + rB);
-    const F ms = mA * mB / (mA + mB);
+    const F Rs = xdiv(rA * rB, rA + rB);
+    const F ms = xdiv(mA * mB, mA + mB);
     const F la = rA - F(0.5) * delta, lb = rB - F(0.5) * delta;
     V3<F> om{la * wA[0] + lb * wB[0], la * wA[1] + lb * wB[1], la * wA[2] + lb * wB[2]};
     V3<F> wxn = cross(om, n);
@@ -218,9 +218,9 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
     const F hin = K.lub_in * sF;
     const F hh = h > hin ? h : hin;
     const F rA = NS::f(A.d), rB = NS::f(Bq.d);
-    const F Rl = rA * rB / (rA + rB);
+    const F Rl = xdiv(rA * rB, rA + rB);
     const F vn = dv[0] * n.x + dv[1] * n.y + dv[2] * n.z;
-    F sl = -K.six_pi_mu * Rl * Rl * vn / hh;
+    F sl = xdiv(-K.six_pi_mu * Rl * Rl * vn, hh);
     if (!i_lo) sl = -sl;
     o.l = V3<F>{sl * n.x, sl * n.y, sl * n.z};
     if (EXT && P.lub_tangential) {
@@ -269,7 +269,6 @@ __device__ __forceinline__ void pair_forces_body(const DevState& st, const DevPa
   const Quad<S>* pos = (const Quad<S>*)st.pos[sb];
   const Quad<S>* vel = (const Quad<S>*)st.vel[sb];
   const Quad<S>* omg = (const Quad<S>*)st.omg[sb];
-  const int32_t* nbr = st.nbr[nl];
   const uint32_t* cmask = st.cmask[nl];
   Quad<S>* hist = (Quad<S>*)st.hist[nl];
   Quad<F>* prec = (Quad<F>*)st.prec;
@@ -281,19 +280,29 @@ __device__ __forceinline__ void pair_forces_body(const DevState& st, const DevPa
     const int64_t i = pr.x;
     const Quad<S> Pi = ldq(pos + i);
     const Quad<S> Pv = ldq(pos + pr.z);
+    const uint32_t cm = cmask[i];
+    // the records an interacting pair reads next, fetched with the positions
+    prefetch_l1(vel + i);
+    prefetch_l1(omg + i);
+    prefetch_l1(vel + pr.z);
+    prefetch_l1(omg + pr.z);
     float dx = (float)NS::dif(Pv.a, Pi.a), dy = (float)NS::dif(Pv.b, Pi.b), dz = (float)NS::dif(Pv.c, Pi.c);
     if (P.periodic[0]) dx = dx > P.cf.halfL[0] ? dx - P.cf.L[0] : (dx < -P.cf.halfL[0] ? dx + P.cf.L[0] : dx);
     if (P.periodic[1]) dy = dy > P.cf.halfL[1] ? dy - P.cf.L[1] : (dy < -P.cf.halfL[1] ? dy + P.cf.L[1] : dy);
     if (P.periodic[2]) dz = dz > P.cf.halfL[2] ? dz - P.cf.L[2] : (dz < -P.cf.halfL[2] ? dz + P.cf.L[2] : dz);
     const float cut = ((float)NS::f(Pi.d) + (float)NS::f(Pv.d)) * fac;
     if (!(dx * dx + dy * dy + dz * dz <= cut * cut * 1.0002f)) continue;
+    const int k = pr.y;
+    const bool has = (cm >> k) & 1u;
+    if (has) prefetch_l1(hist + (int64_t)k * N + i);
     const Quad<S> Vi = ldq(vel + i), Wi = ldq(omg + i);
     const F vi[3] = {NS::f(Vi.a), NS::f(Vi.b), NS::f(Vi.c)};
     const F vil[3] = {NS::lo(Vi.a), NS::lo(Vi.b), NS::lo(Vi.c)};
     const F wi[3] = {NS::f(Wi.a), NS::f(Wi.b), NS::f(Wi.c)};
-    const int k = pr.y;
+    // the first particle of a listed pair is pr.x, so its list entry is the partner
+    // with the first bit set
     const PairOut<F> o = pair_eval<FORM, INTEGRATE, false, true>(
-        P, Pi, vi, vil, wi, NS::f(Vi.d), nbr[(int64_t)k * N + i], k, (cmask[i] >> k) & 1u, i, N, pos,
+        P, Pi, vi, vil, wi, NS::f(Vi.d), (int32_t)((uint32_t)pr.z | kFirstBit), k, has, i, N, pos,
         vel, omg, hist, pr.w);
     // the pair's record; the slot masks tell the gather which slots hold this
     // substep's records (OR is order-free)
@@ -361,7 +370,9 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
   F vi[3] = {F(0), F(0), F(0)}, wi[3] = {F(0), F(0), F(0)}, vil[3] = {F(0), F(0), F(0)};
   V3<F> fc{0, 0, 0}, fl{0, 0, 0}, tq{0, 0, 0};
   uint32_t mask = 0, nmask = 0, live = 0;
-  if (valid) {
+  // the particle's own records (in the gather mode only after the pair phase, which
+  // does not need them: fewer live registers while the pair records are in flight)
+  auto load_own = [&]() {
     Pi = ldq(pos + i);
     Vi = ldq(vel + i);
     Wi = ldq(omg + i);
@@ -374,6 +385,9 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
       vil[a] = NS::lo(a == 0 ? Vi.a : (a == 1 ? Vi.b : Vi.c));
       wi[a] = NS::f(a == 0 ? Wi.a : (a == 1 ? Wi.b : Wi.c));
     }
+  };
+  if (valid) {
+    if constexpr (!GATHER) load_own();
     const int nn = st.nn[nl][i];
     mask = st.cmask[nl][i];
     if constexpr (GATHER) {
@@ -411,6 +425,11 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
     const int32_t* pid = st.pid + i * P.cap;
     uint32_t mc = 0, ml = 0, first = 0;
     if (valid) {
+      // the own records are read after the pair phase: fetch them now
+      prefetch_l1(pos + i);
+      prefetch_l1(vel + i);
+      prefetch_l1(omg + i);
+      prefetch_l1(accp + i);
       first = st.fmask[i];
       // this substep's contact and lubrication slots, cleared for the next substep
       mc = st.amask[i];
@@ -419,13 +438,14 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
       st.amask[N + i] = 0u;
     }
     live = mc | ml;
-    // two slots per round: their record loads are issued together, then added in
-    // slot order
+    // kGatherBatch slots per round: their pair ids, then their records, are loaded
+    // together (two dependent round trips per round), then added in slot order
+    constexpr int kGatherBatch = 4;
     while (live) {
-      int ks[2];
+      int ks[kGatherBatch];
       int cnt = 0;
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < kGatherBatch; ++u) {
         ks[u] = 0;
         if (live) {
           ks[u] = __ffs(live) - 1;
@@ -433,19 +453,21 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
           cnt = u + 1;
         }
       }
-      Quad<F> q[2][3];
+      int32_t ms[kGatherBatch];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int32_t m = u < cnt ? pid[ks[u]] : 0;
-        const bool ok = u < cnt && (uint64_t)(uint32_t)m < (uint64_t)st.pcap;
-        const Quad<F>* r = prec + 3 * (int64_t)(ok ? m : 0);
+      for (int u = 0; u < kGatherBatch; ++u) ms[u] = u < cnt ? pid[ks[u]] : 0;
+      Quad<F> q[kGatherBatch][3];
+#pragma unroll
+      for (int u = 0; u < kGatherBatch; ++u) {
+        const bool ok = u < cnt && (uint64_t)(uint32_t)ms[u] < (uint64_t)st.pcap;
+        const Quad<F>* r = prec + 3 * (int64_t)(ok ? ms[u] : 0);
         q[u][0] = ldq(r);
         q[u][1] = ldq(r + 1);
         q[u][2] = ldq(r + 2);
         if (!ok) ks[u] = -1;
       }
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < kGatherBatch; ++u) {
         if (u >= cnt || ks[u] < 0) continue;
         const int k = ks[u];
         const bool fi = (first >> k) & 1u;
@@ -576,6 +598,7 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
       }
   }
   if (valid) {
+    if constexpr (GATHER) load_own();
     // walls (planes of the same material)
     uint32_t wmask_old = st.wmask[pb][i], wmask_new = 0;
     S* whist = (S*)st.whist[pb];
@@ -621,7 +644,7 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
             const F hin = K.lub_in * dbar;
             const F hh = h > hin ? h : hin;
             const F vn = vi[0] * n.x + vi[1] * n.y + vi[2] * n.z;
-            const F s = -K.six_pi_mu * ri * ri * vn / hh;
+            const F s = xdiv(-K.six_pi_mu * ri * ri * vn, hh);
             fl.x += s * n.x; fl.y += s * n.y; fl.z += s * n.z;
             if (EXT && P.lub_tangential) {
               // shear term against the plane: -6 pi mu r (8/15) ln(r / h) v_t
@@ -657,10 +680,10 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
       o[3 * i + 0] = (double)tq.x; o[3 * i + 1] = (double)tq.y; o[3 * i + 2] = (double)tq.z;
     } else {
       // leapfrog: v += dt a, w += dt T / I, x += dt v (state word)
-      const F inv_m = F(1) / mi;
+      const F inv_m = xdiv(F(1), mi);
       F acc[3] = {xfma(fc.x + fl.x + ff[0], inv_m, K.g[0]), xfma(fc.y + fl.y + ff[1], inv_m, K.g[1]),
                   xfma(fc.z + fl.z + ff[2], inv_m, K.g[2])};
-      const F inv_I = F(2.5) / (mi * ri * ri);
+      const F inv_I = xdiv(F(2.5), mi * ri * ri);
       F alp[3] = {tq.x * inv_I, tq.y * inv_I, tq.z * inv_I};
       S vn[3] = {NS::fmaq(Vi.a, K.dt, acc[0]), NS::fmaq(Vi.b, K.dt, acc[1]),
                  NS::fmaq(Vi.c, K.dt, acc[2])};

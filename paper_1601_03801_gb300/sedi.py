@@ -150,14 +150,14 @@ def smooth_static(params: dict, phi, out, stream=None):
     allocation).  phi and out are CUDA tensors [n_fields, C] of float64."""
     import torch
     p = make_params(params)
-    C = int(np.prod([p.ncell[0], p.ncell[1], p.ncell[2]]))
+    cells = int(np.prod([p.ncell[0], p.ncell[1], p.ncell[2]]))
     for name, t in (("phi", phi), ("out", out)):
         if not isinstance(t, torch.Tensor) or not t.is_cuda:
             raise ValueError(f"smooth_static: {name} must be a CUDA tensor")
         if t.dtype != torch.float64 or not t.is_contiguous():
             raise ValueError(f"smooth_static: {name} must be contiguous float64")
-    if phi.dim() != 2 or not 1 <= phi.shape[0] <= 8 or phi.shape[1] != C:
-        raise ValueError(f"smooth_static: phi must be [n_fields <= 8, {C}], got {tuple(phi.shape)}")
+    if phi.dim() != 2 or not 1 <= phi.shape[0] <= 8 or phi.shape[1] != cells:
+        raise ValueError(f"smooth_static: phi must be [n_fields <= 8, {cells}], got {tuple(phi.shape)}")
     if tuple(out.shape) != tuple(phi.shape) or out.device != phi.device:
         raise ValueError("smooth_static: out must match phi's shape and device")
     nf = int(phi.shape[0])

@@ -65,22 +65,37 @@ SPRING_TOL = {"fp64": 1e-10, "split": 1e-5}
 def compare_springs(g, o, prm, parts, form):
     """Springs of the pairs in contact agree to SPRING_TOL of the largest spring; the
     contact sets are equal except for pairs whose overlap is within rounding of zero
-    (|delta| <= 1e-9 d at the oracle's positions), which may be in contact on one side."""
+    (|delta| <= 1e-9 d at the oracle's positions), which may be in contact on one side.
+    A spring that slid is reset from the capped force, -(F_t + c_t v_t) / S_t: in the
+    split form that force is FP32, and as a contact ends its elastic and damping normal
+    parts cancel while S_t -> 0, so the spring of a separating pair carries FP32
+    rounding amplified without bound (its forces stay within 1e-7).  Pairs whose final
+    overlap is <= 0 (separating: the spring is dropped at the next substep) are held to
+    1e-3 of the largest spring only."""
     ijg, xig = g.contacts()
     ijo, xio = o.contacts()
     assert len(ijo) > 10
     kg = {tuple(p): k for k, p in enumerate(ijg)}
     ko = {tuple(p): k for k, p in enumerate(ijo)}
+    xo = o.get_particles()[0]
+
+    def overlap(pairs):
+        ij = np.array(pairs).reshape(-1, 2)
+        dx = min_image(xo[ij[:, 1]] - xo[ij[:, 0]], prm)
+        return 0.5 * (parts["d"][ij[:, 0]] + parts["d"][ij[:, 1]]) - np.sqrt((dx * dx).sum(1))
+
     diff = sorted(set(kg) ^ set(ko))
     if diff:
-        xo = o.get_particles()[0]
-        ij = np.array(diff)
-        dx = min_image(xo[ij[:, 1]] - xo[ij[:, 0]], prm)
-        delta = 0.5 * (parts["d"][ij[:, 0]] + parts["d"][ij[:, 1]]) - np.sqrt((dx * dx).sum(1))
-        assert np.all(np.abs(delta) <= 1e-9 * parts["d"][ij[:, 0]]), (form, diff, delta)
+        delta = overlap(diff)
+        d_i = parts["d"][np.array(diff)[:, 0]]
+        assert np.all(np.abs(delta) <= 1e-9 * d_i), (form, diff, delta)
     common = sorted(set(kg) & set(ko))
     a = np.array([xig[kg[c]] for c in common]); b = np.array([xio[ko[c]] for c in common])
-    assert rel_err(a, b) <= SPRING_TOL[form], (form, rel_err(a, b))
+    scale = np.abs(b).max()
+    err = np.abs(a - b).max(axis=1) / scale
+    held = overlap(common) > 0
+    assert err[held].max() <= SPRING_TOL[form], (form, err[held].max())
+    assert err.max() <= max(SPRING_TOL[form], 1e-3 if form == "split" else 0.0), (form, err.max())
     return len(common)
 
 
