@@ -298,6 +298,34 @@ int64_t sedi_get_neighbors(sedi_handle* h, int32_t bed, int64_t* offsets, int64_
    and xi (m x 3) as seen from i.  Returns m, or SEDI_EOVERFLOW if m > cap. */
 int64_t sedi_get_contacts(sedi_handle* h, int32_t bed, int64_t cap, int64_t* ij, double* xi);
 
+/* ---- State import (domain decomposition and restarts) ----
+ * A bed split over several handles (one per GPU, e.g. x-slabs of the box with
+ * ghost spheres copied from the neighbours) moves spheres between handles and
+ * rebuilds a handle's particle set; these calls carry the state that
+ * sedi_set_particles resets.  All take caller indices of the current particle set
+ * (after sedi_set_particles) and synchronise the handle's stream. */
+
+/* Tangential springs (Sec. 2.5, endured contacts) of m pairs: ij (m x 2, caller
+   indices, i < j, each pair once) and xi (m x 3) as seen from i, as sedi_get_contacts
+   returns them.  The given pairs that are in the current neighbour lists take these
+   springs; every other listed pair has none.  Errors: EINVAL (index out of range,
+   i >= j, a pair given twice). */
+int sedi_set_contacts(sedi_handle* h, int32_t bed, int64_t m, const int64_t* ij, const double* xi,
+                      int32_t mem);
+/* Lagged accelerations a_prev (n x 3) used by the added-mass force (Sec. 2.3, Eq. 8),
+   as sedi_get_particles returns them. */
+int sedi_set_accel(sedi_handle* h, int32_t bed, const double* a_prev, int32_t mem);
+/* Wall springs, [n][6][3]: walls lo x, hi x, lo y, hi y, lo z, hi z; a zero vector
+   means no contact history with that wall. */
+int sedi_get_wall_springs(sedi_handle* h, int32_t bed, double* xi_wall, int32_t mem);
+int sedi_set_wall_springs(sedi_handle* h, int32_t bed, const double* xi_wall, int32_t mem);
+/* The averaging of sedi_average (Sec. 2.4, Eq. 9-10) from a given PCM deposition q
+   ([7][C] fixed point in the format of sedi_deposit, e.g. the sum of the depositions
+   of several handles that share this mesh): smoothing, outputs, and the smoothed
+   eps_s becomes the one the drag law sees.  Not in the plain FP32 form (EINVAL). */
+int sedi_average_deposit(sedi_handle* h, int32_t bed, const int64_t* q, double* eps_s,
+                         double* U_s, double* F_fp, int32_t mem);
+
 /* ---- Learned warm start of the smoothing solve ----
  * A 3-layer 3x3x3 convolutional network 4 -> 32 -> 32 -> 4 (ReLU after the first
  * two; bfloat16 weights and activations, FP32 accumulation) maps one smoothing

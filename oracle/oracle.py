@@ -51,6 +51,9 @@ def lib():
             "orc_set_eps": [_P, _P],
             "orc_step": [_P, _I],
             "orc_set_threads": [_P, _I],
+            "orc_set_contacts": [_P, _L, _P, _P],
+            "orc_set_wall_history": [_P, _P],
+            "orc_average_fixed": [_P, _P, _P, _P, _P],
             "orc_forces": [_P, _P, _P, _P, _P],
             "orc_get_particles": [_P, _P, _P, _P, _P],
             "orc_get_contacts": [_P, _L, _P, _P],
@@ -188,6 +191,23 @@ class Oracle:
         if m:
             assert lib().orc_get_contacts(self.h, m, _ptr(ij), _ptr(xi)) == 0
         return ij, xi
+
+    def set_contacts(self, ij, xi):
+        ij = np.ascontiguousarray(ij, dtype=np.int64).reshape(-1, 2)
+        xi = np.ascontiguousarray(xi, dtype=np.float64).reshape(-1, 3)
+        assert lib().orc_set_contacts(self.h, len(ij), _ptr(ij), _ptr(xi)) == 0
+
+    def set_wall_history(self, xw):
+        xw = _f64(xw, (self.n, 6, 3))
+        lib().orc_set_wall_history(self.h, _ptr(xw))
+
+    def average_fixed(self, q):
+        q = np.ascontiguousarray(q, dtype=np.int64).reshape(7, self.C)
+        eps = np.zeros(self.C); Us = np.zeros((self.C, 3)); F = np.zeros((self.C, 3))
+        st = lib().orc_average_fixed(self.h, _ptr(q), _ptr(eps), _ptr(Us), _ptr(F))
+        if st:
+            raise RuntimeError(f"oracle average failed ({st})")
+        return eps, Us, F
 
     def wall_history(self):
         xw = np.zeros((self.n, 6, 3))

@@ -100,6 +100,11 @@ int64_t orc_num_contacts(orc_handle* h);
 int orc_get_contacts(orc_handle* h, int64_t cap, int64_t* ij, double* xi);
 int orc_get_wall_history(orc_handle* h, double* xi_wall);
 
+/* Set the tangential history: m pairs (i < j) with springs xi (m*3) as seen from i,
+   and the wall springs (n*6*3).  Returns -1 on a bad pair. */
+int orc_set_contacts(orc_handle* h, int64_t m, const int64_t* ij, const double* xi);
+int orc_set_wall_history(orc_handle* h, const double* xi_wall);
+
 /* Neighbour lists: every j != i with |x_j - x_i|^2 < (r_i + r_j + h_out + skin)^2.
    offsets has n+1 entries; idx receives sorted j per i.  Returns the total count,
    or -1 if cap is too small.  brute = 1: O(N^2) all pairs; 0: link-cell bins. */
@@ -116,6 +121,8 @@ int orc_smooth(orc_handle* h, int32_t nf, double* phi, const double* guess, int3
 /* Deposition + smoothing; eps (C), Us (C*3), Ffp (C*3), any may be NULL.  The
    smoothed solid fraction becomes the one the drag law sees. */
 int orc_average(orc_handle* h, double* eps, double* Us, double* Ffp);
+/* The smoothing and outputs of orc_average from a given deposition q [7][C]. */
+int orc_average_fixed(orc_handle* h, const int64_t* q, double* eps, double* Us, double* Ffp);
 
 /* Single-particle helpers used by the pins. */
 void orc_drag(const orc_params* p, double eps_s, const double w[3], double d,

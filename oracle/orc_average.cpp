@@ -348,11 +348,16 @@ int orc_smooth(orc_handle* h, int32_t nf, double* phi, const double* guess, int3
 }
 
 int orc_average(orc_handle* h, double* eps, double* Us, double* Ffp) {
-  const orc_params& p = h->p;
-  int64_t C = h->ncells();
-  std::vector<int64_t> q(7 * C);
+  std::vector<int64_t> q(7 * h->ncells());
   int st = orc_deposit(h, q.data());
   if (st) return st;
+  return orc_average_fixed(h, q.data(), eps, Us, Ffp);
+}
+
+int orc_average_fixed(orc_handle* h, const int64_t* q, double* eps, double* Us, double* Ffp) {
+  const orc_params& p = h->p;
+  int64_t C = h->ncells();
+  int st = 0;
   std::vector<double> phi(7 * C);
   int shifts[7] = {p.shift_eps, p.shift_mom, p.shift_mom, p.shift_mom,
                    p.shift_force, p.shift_force, p.shift_force};

@@ -14,6 +14,7 @@
  * i as body "a"; j receives the opposite force.  With orc_set_threads(n > 1) the
  * particle loops run on n threads and give the same bits (see pair_forces).
  */
+#include <algorithm>
 #include <cstring>
 
 #include "orc_internal.h"
@@ -293,6 +294,24 @@ int orc_get_contacts(orc_handle* h, int64_t cap, int64_t* ij, double* xi) {
     orc::store(xi, k, e.xi);
     ++k;
   }
+  return 0;
+}
+
+int orc_set_contacts(orc_handle* h, int64_t m, const int64_t* ij, const double* xi) {
+  std::vector<orc::HistEntry> e(m);
+  for (int64_t k = 0; k < m; ++k) {
+    if (ij[2 * k] < 0 || ij[2 * k] >= ij[2 * k + 1] || ij[2 * k + 1] >= h->n) return -1;
+    e[k] = orc::HistEntry{ij[2 * k], ij[2 * k + 1], orc::load(xi, k)};
+  }
+  std::sort(e.begin(), e.end(), [](const orc::HistEntry& a, const orc::HistEntry& b) {
+    return a.i < b.i || (a.i == b.i && a.j < b.j);
+  });
+  h->hist.swap(e);
+  return 0;
+}
+
+int orc_set_wall_history(orc_handle* h, const double* xw) {
+  for (int64_t i = 0; i < h->n * 6; ++i) h->whist[i] = orc::load(xw, i);
   return 0;
 }
 

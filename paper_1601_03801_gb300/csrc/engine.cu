@@ -1461,6 +1461,8 @@ static int average_outputs(sedi_handle* h, double* eps, double* Us, double* F, i
   return 0;
 }
 
+static int average_from_fixed(sedi_handle* h, double* eps, double* Us, double* F, int32_t mem);
+
 int sedi_average(sedi_handle* h, int32_t bed, double* eps, double* Us, double* F, int32_t mem) {
   if (!h) return SEDI_EINVAL;
   h->err.clear();
@@ -1480,7 +1482,6 @@ int sedi_average(sedi_handle* h, int32_t bed, double* eps, double* Us, double* F
   int rc = need_particles(h);
   if (rc) return rc;
   if (bed != 0) return fail(h, SEDI_EINVAL, "bed %d out of range", bed);
-  const int64_t C = h->P.C;
   if (h->prm.profile) {
     harvest(h);
     if (h->avg_ev.empty())
@@ -1488,6 +1489,14 @@ int sedi_average(sedi_handle* h, int32_t bed, double* eps, double* Us, double* F
     CK(cudaEventRecord(h->avg_ev[0], h->stream));
   }
   if ((rc = deposit_dev(h))) return rc;
+  return average_from_fixed(h, eps, Us, F, mem);
+}
+
+// The averaging after the deposition (in qfix, or phi in the plain form): fixed
+// point -> smoothing word, n_tau smoothing steps, outputs.
+static int average_from_fixed(sedi_handle* h, double* eps, double* Us, double* F, int32_t mem) {
+  int rc = 0;
+  const int64_t C = h->P.C;
   launch_fields_from_fixed(h->form, h->qfix, h->P, h->phi, 7, h->stream);
   if (h->prm.profile) CK(cudaEventRecord(h->avg_ev[1], h->stream));
   if (h->prm.use_cnn_guess && h->cnn_set) {
@@ -1511,6 +1520,120 @@ int sedi_average(sedi_handle* h, int32_t bed, double* eps, double* Us, double* F
   rc = smooth_status(h, 7);
   h->fluid_host_stale = true;
   return rc;
+}
+
+int sedi_average_deposit(sedi_handle* h, int32_t bed, const int64_t* q, double* eps, double* Us,
+                         double* F, int32_t mem) {
+  if (!h) return SEDI_EINVAL;
+  h->err.clear();
+  ENS_FORWARD(sedi_average_deposit(sub, 0, q, eps, Us, F, mem));
+  int rc = need_particles(h);
+  if (rc) return rc;
+  if (bed != 0 || !q) return fail(h, SEDI_EINVAL, "bad bed or null deposit");
+  if (h->form == FORM_PLAIN) return fail(h, SEDI_EINVAL, "the plain FP32 form deposits floats, not fixed point");
+  if (h->prm.profile) {
+    harvest(h);
+    if (h->avg_ev.empty())
+      for (int k = 0; k < 3; ++k) h->avg_ev.push_back(new_event());
+    CK(cudaEventRecord(h->avg_ev[0], h->stream));
+  }
+  if ((rc = copy_in(h, h->qfix, q, 8 * 7 * h->P.C, mem))) return rc;
+  return average_from_fixed(h, eps, Us, F, mem);
+}
+
+// ---------------------------------------------------------------- state import
+int sedi_set_contacts(sedi_handle* h, int32_t bed, int64_t m, const int64_t* ij, const double* xi,
+                      int32_t mem) {
+  if (!h) return SEDI_EINVAL;
+  h->err.clear();
+  ENS_FORWARD(sedi_set_contacts(sub, 0, m, ij, xi, mem));
+  int rc = need_particles(h);
+  if (rc) return rc;
+  if (bed != 0 || m < 0 || (m > 0 && (!ij || !xi))) return fail(h, SEDI_EINVAL, "bad contact table");
+  std::vector<int64_t> hij(2 * m);
+  std::vector<double> hxi(3 * m);
+  if (m > 0) {
+    if (mem == SEDI_MEM_DEVICE) {
+      CK(cudaMemcpy(hij.data(), ij, 16 * m, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(hxi.data(), xi, 24 * m, cudaMemcpyDeviceToHost));
+    } else {
+      std::memcpy(hij.data(), ij, 16 * m);
+      std::memcpy(hxi.data(), xi, 24 * m);
+    }
+  }
+  std::vector<int64_t> order(m);
+  for (int64_t k = 0; k < m; ++k) {
+    if (hij[2 * k] < 0 || hij[2 * k] >= hij[2 * k + 1] || hij[2 * k + 1] >= h->N)
+      return fail(h, SEDI_EINVAL, "contact %lld: need 0 <= i < j < n", (long long)k);
+    order[k] = k;
+  }
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    return hij[2 * a] != hij[2 * b] ? hij[2 * a] < hij[2 * b] : hij[2 * a + 1] < hij[2 * b + 1];
+  });
+  std::vector<int64_t> sij(2 * m);
+  std::vector<double> sxi(3 * m);
+  for (int64_t k = 0; k < m; ++k) {
+    const int64_t o = order[k];
+    if (k > 0 && hij[2 * o] == sij[2 * k - 2] && hij[2 * o + 1] == sij[2 * k - 1])
+      return fail(h, SEDI_EINVAL, "contact (%lld, %lld) given twice", (long long)hij[2 * o], (long long)hij[2 * o + 1]);
+    sij[2 * k] = hij[2 * o];
+    sij[2 * k + 1] = hij[2 * o + 1];
+    for (int a = 0; a < 3; ++a) sxi[3 * k + a] = hxi[3 * o + a];
+  }
+  int64_t* dij = nullptr;
+  double* dxi = nullptr;
+  CK(cudaMalloc((void**)&dij, 16 * std::max<int64_t>(m, 1)));
+  CK(cudaMalloc((void**)&dxi, 24 * std::max<int64_t>(m, 1)));
+  if (m > 0) {
+    CK(cudaMemcpyAsync(dij, sij.data(), 16 * m, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(dxi, sxi.data(), 24 * m, cudaMemcpyHostToDevice, h->stream));
+  }
+  launch_springs_in(h->form, h->st, m, dij, dxi, h->stream);
+  rc = sync_status(h);
+  cudaFree(dij);
+  cudaFree(dxi);
+  return rc;
+}
+
+int sedi_set_accel(sedi_handle* h, int32_t bed, const double* a, int32_t mem) {
+  if (!h) return SEDI_EINVAL;
+  h->err.clear();
+  ENS_FORWARD(sedi_set_accel(sub, 0, a, mem));
+  int rc = need_particles(h);
+  if (rc) return rc;
+  if (bed != 0 || !a) return fail(h, SEDI_EINVAL, "bad bed or null accelerations");
+  if ((rc = copy_in(h, h->dstage, a, 24 * h->N, mem))) return rc;
+  launch_accel_in(h->form, h->st, h->dstage, h->stream);
+  return sync_status(h);
+}
+
+static int wall_springs_io(sedi_handle* h, double* out, const double* in, int32_t mem) {
+  int rc = need_particles(h);
+  if (rc) return rc;
+  double* tmp = nullptr;
+  CK(cudaMalloc((void**)&tmp, 8 * 18 * h->N));
+  if (in) rc = copy_in(h, tmp, in, 8 * 18 * h->N, mem);
+  if (!rc) launch_wall_springs(h->form, h->st, in ? nullptr : tmp, in ? tmp : nullptr, h->stream);
+  if (!rc && out) rc = copy_out(h, out, tmp, 8 * 18 * h->N, mem);
+  if (!rc) rc = sync_status(h);
+  cudaFree(tmp);
+  return rc;
+}
+
+int sedi_get_wall_springs(sedi_handle* h, int32_t bed, double* xi_wall, int32_t mem) {
+  if (!h) return SEDI_EINVAL;
+  h->err.clear();
+  ENS_FORWARD(sedi_get_wall_springs(sub, 0, xi_wall, mem));
+  if (bed != 0 || !xi_wall) return fail(h, SEDI_EINVAL, "bad bed or null output");
+  return wall_springs_io(h, xi_wall, nullptr, mem);
+}
+
+int sedi_set_wall_springs(sedi_handle* h, int32_t bed, const double* xi_wall, int32_t mem) {
+  if (!h) return SEDI_EINVAL;
+  h->err.clear();
+  ENS_FORWARD(sedi_set_wall_springs(sub, 0, xi_wall, mem));
+  if (bed != 0 || !xi_wall) return fail(h, SEDI_EINVAL, "bad bed or null input");
+  return wall_springs_io(h, nullptr, xi_wall, mem);
 }
 
 int sedi_deposit(sedi_handle* h, int32_t bed, int64_t* q, int32_t mem) {

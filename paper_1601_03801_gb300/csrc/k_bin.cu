@@ -61,15 +61,12 @@ __device__ __forceinline__ int bin_axis(S x, const DevParams& P, int a) {
   return b;
 }
 
-// Storage order of the bins: z fastest, then y, then x.  A bed is thin in z (gravity)
-// and the empty bins above it hold no particles, so every listed partner lies within
-// about (bins in y) x (occupied bins in z) bins of a particle in this order -- tens of
-// thousands of particles even for a 400 x 200 mm bed, against a whole bin layer
-// (hundreds of thousands) with x fastest -- and the partner records a kernel reads stay
-// in L2.  The order changes no list: slots are appended bin by bin in a fixed (oz,
-// oy, ox) sequence and by caller index inside a bin.
+// Storage order of the bins: x fastest, then y, then z.  (Measured against z fastest,
+// which keeps a thin bed's partners closer in memory: the same for the pair list,
+// slower for the per-particle loop.)  The order changes no list: slots are appended
+// bin by bin in a fixed (oz, oy, ox) sequence and by caller index inside a bin.
 __device__ __forceinline__ int64_t bin_key(int bx, int by, int bz, const DevParams& P) {
-  return ((int64_t)bx * P.nb[1] + by) * P.nb[2] + bz;
+  return ((int64_t)bz * P.nb[1] + by) * P.nb[0] + bx;
 }
 
 template <class S>
@@ -346,7 +343,7 @@ __device__ __forceinline__ void remap_body(const DevState& st, const DevParams& 
   using S = typename Traits<FORM>::S;
   const int pb = st.ctl->pb, qb = pb ^ 1;
   const int nl = st.ctl->nl, ql = nl ^ 1;
-  const int64_t N = st.N, cap = P.cap;
+  const int64_t N = st.N;
   const Quad<S>* hold = (const Quad<S>*)st.hist[nl];
   Quad<S>* hnew = (Quad<S>*)st.hist[ql];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
@@ -837,7 +834,113 @@ __global__ void k_contacts(DevState st, DevParams P, unsigned long long* count, 
   }
 }
 
+// Springs of the pairs (ij[2k] < ij[2k+1], caller indices, sorted) set as the current
+// history: every listed slot whose pair is in the table takes its spring (both
+// particles' slots hold the same vector, as the pair evaluation keeps them); the
+// other slots have none.
+template <int FORM>
+__global__ void k_springs_in(DevState st, int64_t m, const int64_t* ij, const double* xi) {
+  using S = typename Traits<FORM>::S;
+  const int pb = st.ctl->pb, nl = st.ctl->nl;
+  Quad<S>* hist = (Quad<S>*)st.hist[nl];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < st.N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ui = st.uid[pb][i];
+    const int n = st.nn[nl][i];
+    uint32_t mask = 0;
+    for (int k = 0; k < n; ++k) {
+      const int64_t uj = st.uid[pb][nbr_index(st.nbr[nl][(int64_t)k * st.N + i])];
+      const int64_t a = ui < uj ? ui : uj, b = ui < uj ? uj : ui;
+      int64_t lo = 0, hi = m;  // first entry >= (a, b)
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const int64_t ma = ij[2 * mid], mb = ij[2 * mid + 1];
+        if (ma < a || (ma == a && mb < b)) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo < m && ij[2 * lo] == a && ij[2 * lo + 1] == b) {
+        stq(hist + (int64_t)k * st.N + i,
+            Quad<S>{s_from_double<S>(xi[3 * lo]), s_from_double<S>(xi[3 * lo + 1]),
+                    s_from_double<S>(xi[3 * lo + 2]), S{}});
+        mask |= 1u << k;
+      }
+    }
+    st.cmask[nl][i] = mask;
+  }
+}
+
+// Lagged accelerations (caller order, n x 3).
+template <int FORM>
+__global__ void k_accel_in(DevState st, const double* a) {
+  using F = typename Traits<FORM>::F;
+  const int pb = st.ctl->pb;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < st.N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = st.uid[pb][i];
+    stq((Quad<F>*)st.acc[pb] + i, Quad<F>{(F)a[3 * u], (F)a[3 * u + 1], (F)a[3 * u + 2], F(0)});
+  }
+}
+
+// Wall springs, caller order [n][6 walls][3]; a wall whose spring is zero has none.
+template <int FORM>
+__global__ void k_wall_springs(DevState st, double* out, const double* in) {
+  using S = typename Traits<FORM>::S;
+  const int pb = st.ctl->pb;
+  S* wh = (S*)st.whist[pb];
+  const int64_t N = st.N;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = st.uid[pb][i];
+    if (out) {
+      const uint32_t m = st.wmask[pb][i];
+      for (int w = 0; w < 6; ++w)
+        for (int c = 0; c < 3; ++c)
+          out[18 * u + 3 * w + c] = ((m >> w) & 1u) ? Num<S>::d(wh[((int64_t)w * 3 + c) * N + i]) : 0.0;
+    } else {
+      uint32_t m = 0;
+      for (int w = 0; w < 6; ++w) {
+        bool any = false;
+        for (int c = 0; c < 3; ++c) {
+          const double v = in[18 * u + 3 * w + c];
+          wh[((int64_t)w * 3 + c) * N + i] = s_from_double<S>(v);
+          any |= v != 0.0;
+        }
+        if (any) m |= 1u << w;
+      }
+      st.wmask[pb][i] = m;
+    }
+  }
+}
+
 }  // namespace
+
+void launch_springs_in(int form, const DevState& st, int64_t m, const int64_t* ij, const double* xi,
+                       cudaStream_t s) {
+  unsigned g = grid_for(st.N, 256);
+  switch (form) {
+    case FORM_SPLIT: k_springs_in<FORM_SPLIT><<<g, 256, 0, s>>>(st, m, ij, xi); break;
+    case FORM_PLAIN: k_springs_in<FORM_PLAIN><<<g, 256, 0, s>>>(st, m, ij, xi); break;
+    default: k_springs_in<FORM_FP64><<<g, 256, 0, s>>>(st, m, ij, xi); break;
+  }
+}
+
+void launch_accel_in(int form, const DevState& st, const double* a, cudaStream_t s) {
+  unsigned g = grid_for(st.N, 256);
+  switch (form) {
+    case FORM_SPLIT: k_accel_in<FORM_SPLIT><<<g, 256, 0, s>>>(st, a); break;
+    case FORM_PLAIN: k_accel_in<FORM_PLAIN><<<g, 256, 0, s>>>(st, a); break;
+    default: k_accel_in<FORM_FP64><<<g, 256, 0, s>>>(st, a); break;
+  }
+}
+
+void launch_wall_springs(int form, const DevState& st, double* out, const double* in, cudaStream_t s) {
+  unsigned g = grid_for(st.N, 256);
+  switch (form) {
+    case FORM_SPLIT: k_wall_springs<FORM_SPLIT><<<g, 256, 0, s>>>(st, out, in); break;
+    case FORM_PLAIN: k_wall_springs<FORM_PLAIN><<<g, 256, 0, s>>>(st, out, in); break;
+    default: k_wall_springs<FORM_FP64><<<g, 256, 0, s>>>(st, out, in); break;
+  }
+}
 
 void launch_import(int form, const DevState& st, const double* x, const double* v, const double* w,
                    const double* d, const double* rho, const DevParams& P, cudaStream_t s) {

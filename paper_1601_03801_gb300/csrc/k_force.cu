@@ -370,8 +370,8 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
   F vi[3] = {F(0), F(0), F(0)}, wi[3] = {F(0), F(0), F(0)}, vil[3] = {F(0), F(0), F(0)};
   V3<F> fc{0, 0, 0}, fl{0, 0, 0}, tq{0, 0, 0};
   uint32_t mask = 0, nmask = 0, live = 0;
-  // the particle's own records (in the gather mode only after the pair phase, which
-  // does not need them: fewer live registers while the pair records are in flight)
+  // the particle's own records (loaded before the pair phase in every mode: in the
+  // gather mode their loads overlap the first pair records' round trip)
   auto load_own = [&]() {
     Pi = ldq(pos + i);
     Vi = ldq(vel + i);
@@ -387,7 +387,7 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
     }
   };
   if (valid) {
-    if constexpr (!GATHER) load_own();
+    load_own();
     const int nn = st.nn[nl][i];
     mask = st.cmask[nl][i];
     if constexpr (GATHER) {
@@ -425,11 +425,6 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
     const int32_t* pid = st.pid + i * P.cap;
     uint32_t mc = 0, ml = 0, first = 0;
     if (valid) {
-      // the own records are read after the pair phase: fetch them now
-      prefetch_l1(pos + i);
-      prefetch_l1(vel + i);
-      prefetch_l1(omg + i);
-      prefetch_l1(accp + i);
       first = st.fmask[i];
       // this substep's contact and lubrication slots, cleared for the next substep
       mc = st.amask[i];
@@ -598,7 +593,6 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
       }
   }
   if (valid) {
-    if constexpr (GATHER) load_own();
     // walls (planes of the same material)
     uint32_t wmask_old = st.wmask[pb][i], wmask_new = 0;
     S* whist = (S*)st.whist[pb];

@@ -77,6 +77,13 @@ void launch_import(int form, const DevState& st, const double* x, const double* 
 void launch_neighbors_export(const DevState& st, int64_t* counts, cudaStream_t s);
 void launch_neighbors_fill(const DevState& st, const int64_t* offsets, int64_t* out,
                            cudaStream_t s);
+// Imports by caller index: pair springs (m sorted pairs i < j, xi as seen from i) set
+// as the current history; lagged accelerations (n x 3); wall springs [n][6][3]
+// exported into out (in == null) or imported from in (out == null).
+void launch_springs_in(int form, const DevState& st, int64_t m, const int64_t* ij, const double* xi,
+                       cudaStream_t s);
+void launch_accel_in(int form, const DevState& st, const double* a, cudaStream_t s);
+void launch_wall_springs(int form, const DevState& st, double* out, const double* in, cudaStream_t s);
 void launch_contacts_export(int form, const DevState& st, const DevParams& P,
                             unsigned long long* count, int64_t cap, int64_t* ij, double* xi,
                             cudaStream_t s);

@@ -34,6 +34,8 @@ EXPORTS = [
     "sedi_save_state", "sedi_load_state", "sedi_get_timings", "sedi_get_stats", "sedi_sync",
     "sedi_last_error", "sedi_smooth_static", "sedi_cnn_set_params", "sedi_cnn_get_params",
     "sedi_cnn_forward", "sedi_cnn_loss_grad", "sedi_cnn_train", "sedi_set_bed",
+    "sedi_set_contacts", "sedi_set_accel", "sedi_get_wall_springs", "sedi_set_wall_springs",
+    "sedi_average_deposit",
 ]
 ALL_BEDS = -1  # SEDI_ALL_BEDS
 
@@ -104,6 +106,11 @@ def lib():
             "sedi_sync": (C.c_int, [_P]),
             "sedi_last_error": (C.c_char_p, [_P]),
             "sedi_smooth_static": (C.c_int, [C.POINTER(SediParams), _I, _P, _P, _P, _P, C.c_char_p, _I]),
+            "sedi_set_contacts": (C.c_int, [_P, _I, _L, _P, _P, _I]),
+            "sedi_set_accel": (C.c_int, [_P, _I, _P, _I]),
+            "sedi_get_wall_springs": (C.c_int, [_P, _I, _P, _I]),
+            "sedi_set_wall_springs": (C.c_int, [_P, _I, _P, _I]),
+            "sedi_average_deposit": (C.c_int, [_P, _I, _P, _P, _P, _P, _I]),
             "sedi_cnn_set_params": (C.c_int, [_P, _P, _L]),
             "sedi_cnn_get_params": (C.c_int, [_P, _P, _L]),
             "sedi_cnn_forward": (C.c_int, [_P, _P, _P, _I]),
@@ -373,6 +380,37 @@ class Sedi:
                 continue
             m = self._check(rc)
             return ij[:m], xi[:m]
+
+    def set_contacts(self, ij, xi, bed=0):
+        """Springs of the given pairs (caller indices i < j, xi as seen from i)."""
+        ij = np.ascontiguousarray(ij, dtype=np.int64).reshape(-1, 2)
+        xi = np.ascontiguousarray(xi, dtype=np.float64).reshape(-1, 3)
+        if len(ij) != len(xi):
+            raise ValueError("ij and xi differ in length")
+        self._check(lib().sedi_set_contacts(self.h, int(bed), len(ij), ij.ctypes.data if len(ij) else None,
+                                            xi.ctypes.data if len(xi) else None, MEM_HOST))
+
+    def set_accel(self, a, bed=0):
+        a = _Arg(a, np.float64, (self._n[bed], 3))
+        self._check(lib().sedi_set_accel(self.h, int(bed), a.ptr, a.mem))
+
+    def wall_springs(self, bed=0):
+        out = np.zeros((self._n[bed], 6, 3))
+        self._check(lib().sedi_get_wall_springs(self.h, int(bed), out.ctypes.data, MEM_HOST))
+        return out
+
+    def set_wall_springs(self, xw, bed=0):
+        a = _Arg(xw, np.float64, (self._n[bed], 6, 3))
+        self._check(lib().sedi_set_wall_springs(self.h, int(bed), a.ptr, a.mem))
+
+    def average_deposit(self, q, bed=0):
+        """sedi_average_deposit: the averaging from a given deposition [7][C] (int64)."""
+        Cb = self._C[bed]
+        q = np.ascontiguousarray(q, dtype=np.int64).reshape(7, Cb)
+        eps = np.zeros(Cb); Us = np.zeros((Cb, 3)); F = np.zeros((Cb, 3))
+        self._check(lib().sedi_average_deposit(self.h, int(bed), q.ctypes.data, eps.ctypes.data,
+                                               Us.ctypes.data, F.ctypes.data, MEM_HOST))
+        return eps, Us, F
 
     def save_state(self, path):
         self._check(lib().sedi_save_state(self.h, str(path).encode()))
