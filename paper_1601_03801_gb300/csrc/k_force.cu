@@ -814,10 +814,10 @@ static void launch_pairs(const DevState& st, const DevMesh& mesh, const DevParam
   const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)next;
   if (integrate) {
     k_pair_forces<FORM, true><<<(unsigned)g, 128, 0, s>>>(st, P, sub_off);
-    k_substep<FORM, true, 128, 6, false, false, true><<<(unsigned)grid, 128, 0, s>>>(st, mesh, P, sub_off, h, use_cond);
+    k_substep<FORM, true, 128, 5, false, false, true><<<(unsigned)grid, 128, 0, s>>>(st, mesh, P, sub_off, h, use_cond);
   } else {
     k_pair_forces<FORM, false><<<(unsigned)g, 128, 0, s>>>(st, P, sub_off);
-    k_substep<FORM, false, 128, 6, false, false, true><<<(unsigned)grid, 128, 0, s>>>(st, mesh, P, sub_off, h, 0);
+    k_substep<FORM, false, 128, 5, false, false, true><<<(unsigned)grid, 128, 0, s>>>(st, mesh, P, sub_off, h, 0);
   }
 }
 

