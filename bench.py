@@ -52,11 +52,11 @@ KERNEL_SOURCES = ["paper_1601_03801_gb300/csrc/k_force.cu", "paper_1601_03801_gb
 PAIRS_VARIANT = 8  # substep variant of the pair list (two kernels per substep)
 
 
-def substep_kernel_name(variant):
+def substep_kernel_name(variant, form="split"):
     """The kernel(s) the roofline line measures for a substep launch variant."""
-    if variant == PAIRS_VARIANT:
-        return "k_pair_forces<split> + k_substep<split, gather>"
-    return "k_substep<split>"
+    if variant == PAIRS_VARIANT and form != "fp64":
+        return f"k_pair_forces<{form}> + k_substep<{form}, gather>"
+    return f"k_substep<{form}>"
 
 
 def kernel_hash():
@@ -174,6 +174,8 @@ def algorithmic_bytes(kbar, cbar, cells, n, form="split"):
     state and springs: 72 + 16 + 12 + 4 kbar + 18 cbar + 40 C/N."""
     if form == "plain":
         return 72 + 16 + 12 + 4 * kbar + 18 * cbar + 40.0 * cells / n
+    if form == "fp64":  # FP64 mesh words too
+        return 144 + 16 + 12 + 4 * kbar + 36 * cbar + 80.0 * cells / n
     return 144 + 16 + 12 + 4 * kbar + 36 * cbar + 40.0 * cells / n
 
 
@@ -260,7 +262,7 @@ def roofline(prm, n, g, launch_ms, variant, form="split", traffic_scale=None):
     out = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
            "frac": round(achieved / peak, 4), "peak_source": peak_kind,
            "traffic": None if traffic_pp is None else round(traffic_pp * n),
-           "kernel": substep_kernel_name(variant),
+           "kernel": substep_kernel_name(variant, form),
            "algorithmic_bytes_per_particle_substep": round(alg, 1),
            "particles_per_launch": n, "launch_ms": round(launch_ms, 5),
            "kbar": round(kbar, 2), "cbar": round(cbar, 2), "cells": C}
@@ -355,7 +357,7 @@ def gpu_arm(args):
                 "phases_ms_per_step": phases, "rebuilds_in_timed_region": int(rebuilds),
                 "roofline": roof, "e2e": e2e,
                 "gpu_launches": int(launches_per_step(variant, rebuilds, args.steps, C)),
-                "clocks": m["clocks"], "cpu_baseline": cpu, "plain_form": plain, **extra}
+                "clocks": m["clocks"], "cpu_baseline": cpu, "other_forms": plain, **extra}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
@@ -404,22 +406,26 @@ def end_to_end(prm, parts, fl, stream, args, world):
 
 
 def plain_form_leg(prm, parts, fl, stream, args):
-    """The plain FP32 form on the same workload and GPU (comparison baseline of the
-    precision pattern): throughput and its substep roofline; plus, on the 200,000-
-    sphere bed, each form's force error at one identical state and its position error
-    after 100 substeps against the FP64 form (which matches the oracle to 1e-12)."""
+    """The other arithmetic forms on the same workload and GPU (the precision pattern):
+    the plain FP32 form (the comparison baseline; it cannot reach the 1e-5 force
+    tolerance) and the FP64 form (the one other form that meets it, i.e. the comparison
+    at matched error), each with throughput and its substep roofline; plus, on the
+    200,000-sphere bed, each form's force error at one identical state and its position
+    error after 100 substeps against the FP64 form (which matches the oracle to 1e-12)."""
     import torch
 
     n = len(parts["x"])
-    gp, mp = measure(prm, parts, fl, "plain", max(3, args.steps // 2), args.warmup, args.settle,
-                     stream, profile=1)
-    out = {"value": round(n * SUBSTEPS * len(mp["ms"]) / (np.sum(mp["ms"]) / 1e3), 1), "unit": UNIT,
-           "ms_per_step": round(float(np.mean(mp["ms"])), 4),
-           "roofline": roofline(prm, n, gp, mp["substep_launch_ms"], gp.stats()["substep_variant"],
-                                form="plain")}
-    gp.close()
-    del gp
-    torch.cuda.empty_cache()
+    out = {}
+    for form, steps in (("plain", max(3, args.steps // 2)), ("fp64", 2)):
+        gp, mp = measure(prm, parts, fl, form, steps, min(args.warmup, 1), 0 if form == "fp64" else args.settle,
+                         stream, profile=1)
+        out[form] = {"value": round(n * SUBSTEPS * len(mp["ms"]) / (np.sum(mp["ms"]) / 1e3), 1),
+                     "unit": UNIT, "ms_per_step": round(float(np.mean(mp["ms"])), 4),
+                     "roofline": roofline(prm, n, gp, mp["substep_launch_ms"],
+                                          gp.stats()["substep_variant"], form=form)}
+        gp.close()
+        del gp
+        torch.cuda.empty_cache()
     out["errors_vs_fp64_on_bed200k"] = form_errors(stream)
     return out
 
