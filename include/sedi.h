@@ -389,10 +389,10 @@ int sedi_get_stats(sedi_handle* h, sedi_stats* out);
  * Limit: 8 * C <= SEDI_STATIC_MAX_WORDS, i.e. up to 131,072 cells with any
  * n_fields <= 8 (the solver keeps 8 words per cell); larger meshes return
  * SEDI_EINVAL.  The scratch (about 50 MB) lives on every GPU that loads the
- * library until the process exits.  The first call on a device looks up the
- * scratch's device address (cudaGetSymbolAddress) for that device and keeps it;
- * that first call should come before any stream capture, and the library must not
- * be used across a cudaDeviceReset (the kept address would be stale).  Every call
+ * library until the process exits.  Every call looks up the scratch's device
+ * address on the current device (cudaGetSymbolAddress, which allocates nothing).
+ * The call copies its status to the host and synchronises its stream, so it must
+ * not be issued while the stream is being captured into a graph.  Every call
  * shares the one array and leaves its contents behind: calls whose GPU work
  * overlaps (two streams, two threads) race and must be serialised by the caller.
  * Each call ends by synchronising its stream and returns SEDI_OK, SEDI_EINVAL,

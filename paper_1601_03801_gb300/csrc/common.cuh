@@ -43,8 +43,10 @@ struct Ctl {
 template <class F>
 struct ForceConsts {
   F Es, Gs, cdamp, kn_fac, mu, dt;     // contact: E*, G*, -2 sqrt(5/6) beta, (4/3)E*, friction
+  F ct_ratio;                          // sqrt(S_t / S_n) = sqrt(4 G* / E*) (tangential damping)
   int32_t law;                         // 0 Hertz-Mindlin, 1 linear spring-dashpot
   F kn_lin, kt_lin, cdamp_lin;         // linear law: k_n, k_t, -2 beta
+  F ct_ratio_lin;                      // linear law: sqrt(k_t / k_n)
   F lub_in, lub_out, six_pi_mu;        // lubrication limits (fractions of mean diameter), 6 pi mu_f
   F lift_c;                            // lift: C_l rho_f sqrt(nu_f)
   F rho_f, nu_f, c_add_rho_f, eps_max; // fluid
@@ -256,14 +258,16 @@ struct DevState {
   void* hist[2];      // Quad<S> [cap][N] pair springs (x, y, z, 0) (nl parity)
   uint32_t* cmask[2]; // bit k: slot k holds a spring (nl parity)
   // pair list of the current lists (null: not kept): every listed pair once, from the
-  // particle that comes first in it, with the pair's record of the current substep.
+  // particle that comes first in it.  Each substep the pair kernel writes every listed
+  // pair's record (one 32-byte sector per pair, in pair order, so the writes are
+  // sequential): {F, delta/2} {G, flags}, with F the pair force on the first particle
+  // (contact plus lubrication), G = n x F_t (the contact torque on either particle is
+  // its lever r - delta/2 times G) and the kSlot* flags as the bits of the last word.
   // In the pair mode only the first particle's slot holds the pair's spring (see
   // launch_spring_sync).
   int4* pairs;        // [cap N / 2] (i, slot of j in i's list, j, slot of i in j's list)
-  int32_t* pid;       // [N][cap] pair of each list slot (particle-major)
-  uint32_t* fmask;    // [N] slots of the pairs the particle comes first in
-  uint32_t* amask;    // [2][N] slots of this substep's contact / lubrication pairs
-  void* prec;         // Quad<F> [cap N / 2][3] the pair's forces and torques
+  int32_t* pid;       // [cap][N] pair of each list slot | kFirstBit if the owner is first
+  float4* prec;       // [cap N / 2][2] the pair records of the current substep
   int64_t pcap;       // capacity of the pair arrays (cap N / 2)
   // binning scratch
   int32_t* bin_of;    // [N]
@@ -316,6 +320,11 @@ __device__ __forceinline__ const BedView& bed_view(const BedView* views) {
   return s_view;
 }
 #endif
+
+// Flags of a pair record: the pair interacts (the record holds its force: contact
+// plus lubrication), and it is in contact (the record holds the contact torque, and
+// the pair's spring is live).
+constexpr uint8_t kSlotForce = 1, kSlotContact = 2;
 
 // A list entry holds the partner index in bits 0-30 and, in bit 31, whether the
 // owner comes first in canonical pair order (lower caller index).

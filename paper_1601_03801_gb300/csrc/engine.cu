@@ -175,6 +175,8 @@ void fill_consts(const sedi_params& p, ForceConsts<F>& K) {
   K.Gs = (F)Gs;
   K.cdamp = (F)(-2.0 * std::sqrt(5.0 / 6.0) * beta);
   K.kn_fac = (F)(4.0 / 3.0 * Es);
+  K.ct_ratio = (F)std::sqrt(4.0 * Gs / Es);
+  K.ct_ratio_lin = (F)std::sqrt(p.kt_ratio);
   K.law = p.contact_law;
   K.kn_lin = (F)p.kn_linear;
   K.kt_lin = (F)(p.kt_ratio * p.kn_linear);
@@ -451,20 +453,18 @@ int alloc_particles(sedi_handle* h, int64_t N, double rmax) {
     if ((rc = dmalloc(h, h->part_allocs, &st.hist[b], q * cap * N))) return rc;
     if ((rc = dmalloc(h, h->part_allocs, (void**)&st.cmask[b], 4 * N))) return rc;
   }
-  if (form != FORM_FP64 && !h->is_bed) {
+  if (form != FORM_FP64 && !h->is_bed && cap * N / 2 + 1 < ((int64_t)1 << 31)) {
     // pair list (substep variant SUBSTEP_PAIRS; not for ensemble beds, which the
-    // ensemble steps with the per-particle loop): every listed pair once, cap N / 2 at most
+    // ensemble steps with the per-particle loop): every listed pair once, cap N / 2 at
+    // most (pair ids share a word with the first-particle bit, so fewer than 2^31)
     st.pcap = cap * N / 2 + 1;
     if ((rc = dmalloc(h, h->part_allocs, (void**)&st.pairs, 16 * st.pcap)) ||
         (rc = dmalloc(h, h->part_allocs, (void**)&st.pid, 4 * cap * N)) ||
-        (rc = dmalloc(h, h->part_allocs, (void**)&st.fmask, 4 * N)) ||
-        (rc = dmalloc(h, h->part_allocs, (void**)&st.amask, 8 * N)) ||
-        (rc = dmalloc(h, h->part_allocs, &st.prec, 3 * fq * st.pcap)))
+        (rc = dmalloc(h, h->part_allocs, (void**)&st.prec, 32 * st.pcap)))
       return rc;
     CK(cudaMemset(st.pairs, 0, 16 * st.pcap));
-    CK(cudaMemset(st.amask, 0, 8 * N));
     CK(cudaMemset(st.pid, 0, 4 * cap * N));
-    CK(cudaMemset(st.fmask, 0, 4 * N));
+    CK(cudaMemset(st.prec, 0, 32 * st.pcap));
   }
   // bins: edge >= the largest list cutoff (2 r_max (1 + f) + skin) with margin
   const sedi_params& p = h->prm;

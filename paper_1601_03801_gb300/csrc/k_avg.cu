@@ -14,7 +14,6 @@
 
 #include <cmath>
 #include <cstdio>
-#include <mutex>
 
 #include "../../include/sedi.h"
 #include "common.cuh"
@@ -516,8 +515,9 @@ void launch_eps_out_ens(int form, const EnsLaunch& e, cudaStream_t s) {
 // without any device allocation.  Its scratch is the file-scope array below,
 // sized for SEDI_STATIC_MAX_WORDS field words, which every GPU that loads this
 // library holds until the process exits.  Host code must not pass the array's
-// name to a kernel (on the host it is only a stand-in): the device address is
-// taken once per device with cudaGetSymbolAddress and passed instead.
+// name to a kernel (on the host it is only a stand-in): every call looks the
+// device address up with cudaGetSymbolAddress (no allocation; after a device reset
+// it names the reloaded module's array) and passes it instead.
 
 using namespace sedi;
 
@@ -546,12 +546,6 @@ static_assert(kStaticWork % 256 == 0 && (8 * kStaticWords) % 256 == 0,
               "parts of the static scratch must stay 256-byte aligned");
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
-
-struct StaticSlot {
-  unsigned char* base = nullptr;  // device address of g_static_scratch on this device
-};
-std::mutex g_static_mutex;
-StaticSlot g_static_slots[64];
 
 void put_msg(char* msg, int32_t len, const char* text) {
   if (msg && len > 0) std::snprintf(msg, (size_t)len, "%s", text);
@@ -591,24 +585,16 @@ extern "C" int sedi_smooth_static(const sedi_params* p, int32_t nf, const double
       return SEDI_EINVAL;
     }
   }
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
-    put_msg(msg, msg_len, "sedi_smooth_static: no current CUDA device");
-    return SEDI_ECUDA;
-  }
   unsigned char* base = nullptr;
   {
-    std::lock_guard<std::mutex> lock(g_static_mutex);
-    if (!g_static_slots[dev].base) {
-      void* ptr = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-      if (e != cudaSuccess || !ptr) {
-        put_msg(msg, msg_len, "sedi_smooth_static: cudaGetSymbolAddress of the scratch failed");
-        return SEDI_ECUDA;
-      }
-      g_static_slots[dev].base = (unsigned char*)ptr;
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      put_msg(msg, msg_len, "sedi_smooth_static: cudaGetSymbolAddress of the scratch failed");
+      return SEDI_ECUDA;
     }
-    base = g_static_slots[dev].base;
+    base = (unsigned char*)ptr;
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const int form = p->precision_form;

@@ -383,10 +383,9 @@ __device__ __forceinline__ void flip_body(const DevState& st, bool force) {
 // Pair list of the lists just built (before the flip): every particle appends, in
 // slot order, its pairs with partners of higher index (a warp's particles
 // contiguously, one atomic per warp), each stored from the particle that comes first
-// in it (list bit), and records the pair in both particles' slots.  The order
-// of the pairs in the list depends on scheduling; nothing computed from a pair does.
-__device__ __forceinline__ void pair_fill_body(const DevState& st, bool force, bool current,
-                                               int P_CAP) {
+// in it (list bit) with the pair's slot in both lists; both slots record the pair id.  The order of the pairs in the
+// list depends on scheduling; nothing computed from a pair does.
+__device__ __forceinline__ void pair_fill_body(const DevState& st, bool force, bool current) {
   if (skip(st.ctl, force)) return;
   const int ql = current ? st.ctl->nl : st.ctl->nl ^ 1;  // the new lists, or the current ones
   const int64_t N = st.N;
@@ -399,16 +398,14 @@ __device__ __forceinline__ void pair_fill_body(const DevState& st, bool force, b
        i += (int64_t)gridDim.x * blockDim.x) {
     const bool valid = i < N;
     const int ni = valid ? nn[i] : 0;
-    // first: the pairs this particle comes first in (evaluation order); own: the
-    // pairs it appends, those with a partner of higher index, so each particle's
-    // pairs sit next to those of its neighbours in the (cell-sorted) order
+    // the pairs this particle appends: those with a partner of higher index, so each
+    // particle's pairs sit next to those of its neighbours in the (cell-sorted) order
     uint32_t own = 0, first = 0;
     for (int k = 0; k < ni; ++k) {
       const int32_t e = nbr[(int64_t)k * N + i];
       if (nbr_first(e)) first |= 1u << k;
       if (nbr_index(e) > (int32_t)i) own |= 1u << k;
     }
-    if (valid) st.fmask[i] = first;
     const int cnt = __popc(own);
     int incl = cnt;
 #pragma unroll
@@ -440,10 +437,11 @@ __device__ __forceinline__ void pair_fill_body(const DevState& st, bool force, b
         atomicCAS(&st.ctl->error, 0, -9);
         break;
       }
-      // the pair from the particle that comes first in it
-      st.pairs[m] = ((first >> k) & 1u) ? make_int4((int)i, k, j, k2) : make_int4(j, k2, (int)i, k);
-      st.pid[(int64_t)i * P_CAP + k] = (int32_t)m;
-      st.pid[(int64_t)j * P_CAP + k2] = (int32_t)m;
+      // the pair from the particle that comes first in it; each slot's pair id
+      const bool i_first = (first >> k) & 1u;
+      st.pairs[m] = i_first ? make_int4((int)i, k, j, k2) : make_int4(j, k2, (int)i, k);
+      st.pid[(int64_t)k * N + i] = (int32_t)(m | (i_first ? kFirstBit : 0u));
+      st.pid[(int64_t)k2 * N + j] = (int32_t)(m | (i_first ? 0u : kFirstBit));
       ++m;
     }
   }
@@ -479,8 +477,8 @@ __global__ void k_flip(DevState st, bool force) { flip_body(st, force); }
 __global__ void k_pair_reset(DevState st, bool force) {
   if (!skip(st.ctl, force)) st.ctl->npair = 0u;
 }
-__global__ void k_pair_fill(DevState st, bool force, bool current, int cap) {
-  pair_fill_body(st, force, current, cap);
+__global__ void k_pair_fill(DevState st, bool force, bool current) {
+  pair_fill_body(st, force, current);
 }
 
 // Pair mode keeps a pair's spring in the first particle's slot only; this copies it
@@ -621,7 +619,7 @@ void rebuild_impl(const DevState& st, const DevParams& P, int sub_off, bool forc
   k_remap<FORM><<<grid_for(st.N, B), B, 0, s>>>(st, P, force);
   if (st.pairs) {
     k_pair_reset<<<1, 1, 0, s>>>(st, false);
-    k_pair_fill<<<grid_for(st.N, B), B, 0, s>>>(st, false, false, (int)P.cap);
+    k_pair_fill<<<grid_for(st.N, B), B, 0, s>>>(st, false, false);
   }
   k_flip<<<1, 1, 0, s>>>(st, false);
 }
@@ -665,7 +663,7 @@ void launch_rebuild(int form, const DevState& st, const DevParams& P, int sub_of
 void launch_pair_list(const DevState& st, const DevParams& P, cudaStream_t s) {
   if (!st.pairs) return;
   k_pair_reset<<<1, 1, 0, s>>>(st, true);
-  k_pair_fill<<<grid_for(st.N, 256), 256, 0, s>>>(st, true, true, (int)P.cap);
+  k_pair_fill<<<grid_for(st.N, 256), 256, 0, s>>>(st, true, true);
 }
 
 void launch_spring_sync(int form, const DevState& st, cudaStream_t s) {

@@ -34,43 +34,47 @@ __device__ __forceinline__ V3<F> hm_core(const ForceConsts<F>& K, V3<F> n, F del
                                          S* xi_new) {
   using NS = Num<S>;
   F Sn, St, cn, ct, fel;  // stiffnesses, damping coefficients, elastic normal force
+  // both laws: the tangential damping coefficient is the normal one times
+  // sqrt(S_t / S_n), a constant of the material (sqrt(4 G* / E*), or sqrt(k_t / k_n))
   if (K.law == 1) {
     // linear spring-dashpot (Sec. 2.5, Table 1)
     Sn = K.kn_lin;
     St = K.kt_lin;
-    cn = K.cdamp_lin * xsqrt(Sn * ms);
-    ct = K.cdamp_lin * xsqrt(St * ms);
+    cn = K.cdamp_lin * xsqrt_pos(Sn * ms);
+    ct = cn * K.ct_ratio_lin;
     fel = K.kn_lin * delta;
   } else {
-    F sq = xsqrt(Rs * delta);
+    // sqrt(R* delta) = sqrt(R*) sqrt(delta): two roots serve S_n, S_t and F_el
+    const F sr = xsqrt_pos(Rs), sd = xsqrt_pos(delta);
+    const F sq = sr * sd;
     Sn = F(2) * K.Es * sq;
     St = F(8) * K.Gs * sq;
-    cn = K.cdamp * xsqrt(Sn * ms);
-    ct = K.cdamp * xsqrt(St * ms);
-    F kn = K.kn_fac * xsqrt(Rs);
-    fel = kn * delta * xsqrt(delta);
+    cn = K.cdamp * xsqrt_pos(Sn * ms);
+    ct = cn * K.ct_ratio;
+    fel = K.kn_fac * sr * delta * sd;
   }
   F vn = vrel.x * n.x + vrel.y * n.y + vrel.z * n.z;
   V3<F> vt{vrel.x - vn * n.x, vrel.y - vn * n.y, vrel.z - vn * n.z};
   F fn_s = -fel - cn * vn;  // F_n = fn_s * n
-  // spring: rotate onto the tangent plane, keep the length, add v_t dt
+  // spring: rotate onto the tangent plane, keep the length, add v_t dt.  Every term
+  // is an exact product added to the state word (fmaq: error ~2^-44 of the operands)
   S xi[3];
   if (has_old) {
     F xf[3] = {NS::f(xi_old[0]), NS::f(xi_old[1]), NS::f(xi_old[2])};
     F proj = xf[0] * n.x + xf[1] * n.y + xf[2] * n.z;
     F len2 = xf[0] * xf[0] + xf[1] * xf[1] + xf[2] * xf[2];
-    xi[0] = NS::fma_ff(xi_old[0], -proj, n.x);
-    xi[1] = NS::fma_ff(xi_old[1], -proj, n.y);
-    xi[2] = NS::fma_ff(xi_old[2], -proj, n.z);
+    xi[0] = NS::fmaq(xi_old[0], -proj, n.x);
+    xi[1] = NS::fmaq(xi_old[1], -proj, n.y);
+    xi[2] = NS::fmaq(xi_old[2], -proj, n.z);
     if (len2 > F(0)) {
       F t = xdiv(proj * proj, len2);
       if (t < F(1)) {
-        F s1 = xsqrt(F(1) - t);
+        F s1 = xsqrt_pos(F(1) - t);
         F scm1 = xdiv(t, s1 * (F(1) + s1));  // 1/sqrt(1-t) - 1
         F r0 = NS::f(xi[0]), r1 = NS::f(xi[1]), r2 = NS::f(xi[2]);
-        xi[0] = NS::fma_ff(xi[0], scm1, r0);
-        xi[1] = NS::fma_ff(xi[1], scm1, r1);
-        xi[2] = NS::fma_ff(xi[2], scm1, r2);
+        xi[0] = NS::fmaq(xi[0], scm1, r0);
+        xi[1] = NS::fmaq(xi[1], scm1, r1);
+        xi[2] = NS::fmaq(xi[2], scm1, r2);
       }
     }
   } else {
@@ -78,15 +82,16 @@ __device__ __forceinline__ V3<F> hm_core(const ForceConsts<F>& K, V3<F> n, F del
     xi[1] = S{};
     xi[2] = S{};
   }
-  xi[0] = NS::fma_ff(xi[0], K.dt, vt.x);
-  xi[1] = NS::fma_ff(xi[1], K.dt, vt.y);
-  xi[2] = NS::fma_ff(xi[2], K.dt, vt.z);
+  xi[0] = NS::fmaq(xi[0], K.dt, vt.x);
+  xi[1] = NS::fmaq(xi[1], K.dt, vt.y);
+  xi[2] = NS::fmaq(xi[2], K.dt, vt.z);
   V3<F> Ft{-St * NS::f(xi[0]) - ct * vt.x, -St * NS::f(xi[1]) - ct * vt.y,
            -St * NS::f(xi[2]) - ct * vt.z};
-  F ft = xsqrt(Ft.x * Ft.x + Ft.y * Ft.y + Ft.z * Ft.z);
-  F fnm = xabs(fn_s);
-  if (ft > K.mu * fnm) {
-    F sc = xdiv(K.mu * fnm, ft);
+  // Coulomb limit |F_t| <= mu |F_n|, tested on the squares (no root unless sliding)
+  const F ft2 = Ft.x * Ft.x + Ft.y * Ft.y + Ft.z * Ft.z;
+  const F lim = K.mu * xabs(fn_s);
+  if (ft2 > lim * lim) {
+    F sc = lim * xrsqrt(ft2);
     Ft.x *= sc;
     Ft.y *= sc;
     Ft.z *= sc;
@@ -115,33 +120,48 @@ __device__ __forceinline__ V3<F> cross(V3<F> a, V3<F> b) {
 template <class F>
 struct PairOut {
   V3<F> fa, t, l, lt;  // contact force (on i), contact torque, lubrication force and torque
-  V3<F> tb;            // contact torque on the partner (BOTH only)
+  V3<F> G;             // n x F_t in canonical order: the contact torque is lever x G
+  F hd;                // delta / 2 (the lever of either sphere is its radius minus it)
   bool contact, lub;
+  bool first;          // the owner comes first in the pair (canonical order)
 };
+
+// The force of a pair on its owner as the integrating substep adds it: contact plus
+// lubrication as one term, summed in canonical order (on the first particle) and
+// negated for the second, so that every launch variant adds the same value per slot
+// (the pair list stores the canonical sum in the pair's record).
+template <class F>
+__device__ __forceinline__ V3<F> pair_total(const PairOut<F>& o) {
+  const V3<F> z{F(0), F(0), F(0)};
+  const V3<F> a = o.contact ? (o.first ? o.fa : V3<F>{-o.fa.x, -o.fa.y, -o.fa.z}) : z;
+  const V3<F> b = o.lub ? (o.first ? o.l : V3<F>{-o.l.x, -o.l.y, -o.l.z}) : z;
+  const V3<F> c{a.x + b.x, a.y + b.y, a.z + b.z};
+  return o.first ? c : V3<F>{-c.x, -c.y, -c.z};
+}
 
 // EXT: the optional terms (tangential lubrication here, lift in the fluid force)
 // are compiled in; without it the kernel carries none of their registers.
-// BOTH (pair list, i first in the pair): also the partner's contact torque, and the
-// spring stored in the partner's slot k2 as well.
-template <int FORM, bool INTEGRATE, bool EXT, bool BOTH = false>
+template <int FORM, bool INTEGRATE, bool EXT>
 __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
     const DevParams& P, const Quad<typename Traits<FORM>::S>& Pi,
     const typename Traits<FORM>::F* vi, const typename Traits<FORM>::F* vil,
     const typename Traits<FORM>::F* wi, typename Traits<FORM>::F mi, int32_t e, int k, bool has,
     int64_t i, int64_t N,
     const Quad<typename Traits<FORM>::S>* pos, const Quad<typename Traits<FORM>::S>* vel,
-    const Quad<typename Traits<FORM>::S>* omg, Quad<typename Traits<FORM>::S>* hist, int k2 = 0) {
+    const Quad<typename Traits<FORM>::S>* omg, Quad<typename Traits<FORM>::S>* hist) {
   using S = typename Traits<FORM>::S;
   using F = typename Traits<FORM>::F;
   using NS = Num<S>;
   const ForceConsts<F>& K = fconsts<F>(P);
   const BoxS<S>& B = sbox<S>(P);
   PairOut<F> o;
-  o.lt = V3<F>{F(0), F(0), F(0)};
+  o.t = o.lt = o.G = V3<F>{F(0), F(0), F(0)};
+  o.hd = F(0);
   o.contact = o.lub = false;
   const int j = nbr_index(e);
   const Quad<S> Pj = ldq(pos + j);
   const bool i_lo = nbr_first(e);
+  o.first = i_lo;
   const Quad<S>& A = i_lo ? Pi : Pj;
   const Quad<S>& Bq = i_lo ? Pj : Pi;
   // precise geometry in canonical order: dx = x_B - x_A (minimum image)
@@ -156,7 +176,9 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
   S d2 = NS::addq(NS::addq(NS::mul(dxs[0], dxs[0]), NS::mul(dxs[1], dxs[1])), NS::mul(dxs[2], dxs[2]));
   S ssum = NS::addq(A.d, Bq.d);
   S num = NS::subq(NS::mul(ssum, ssum), d2);
-  const F dist = xsqrt(NS::f(d2));
+  const F d2f = NS::f(d2);
+  const F inv_d = xrsqrt(d2f);
+  const F dist = d2f > F(0) ? d2f * inv_d : F(0);
   const F sF = NS::f(ssum);
   // r_A + r_B - |dx| without cancellation: (s^2 - d^2) / (s + d)
   const F delta = NS::kExtended ? xdiv(NS::f(num), sF + dist) : sF - dist;
@@ -164,7 +186,6 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
   o.contact = delta > F(0);
   o.lub = P.lubrication && (-delta < K.lub_out * sF);
   if (!o.contact && !o.lub) return o;
-  const F inv_d = xrsqrt(NS::f(d2));
   const V3<F> n{dxf[0] * inv_d, dxf[1] * inv_d, dxf[2] * inv_d};
   const Quad<S> Vj = ldq(vel + j);
   const F vj[3] = {NS::f(Vj.a), NS::f(Vj.b), NS::f(Vj.c)};
@@ -194,7 +215,8 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
     const F mB = i_lo ? NS::f(Vj.d) : mi;
     const F Rs = xdiv(rA * rB, rA + rB);
     const F ms = xdiv(mA * mB, mA + mB);
-    const F la = rA - F(0.5) * delta, lb = rB - F(0.5) * delta;
+    o.hd = F(0.5) * delta;
+    const F la = rA - o.hd, lb = rB - o.hd;
     V3<F> om{la * wA[0] + lb * wB[0], la * wA[1] + lb * wB[1], la * wA[2] + lb * wB[2]};
     V3<F> wxn = cross(om, n);
     V3<F> vrel{dv[0] + wxn.x, dv[1] + wxn.y, dv[2] + wxn.z};
@@ -209,8 +231,8 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
     V3<F> FA = hm_core<S, F>(K, n, delta, Rs, ms, vrel, xo, has, &Ft, xn_);
     if (INTEGRATE) stq(hist + (int64_t)k * N + i, Quad<S>{xn_[0], xn_[1], xn_[2], NS::from_f(F(0))});
     const F lev = i_lo ? la : lb;
-    o.t = cross(V3<F>{lev * n.x, lev * n.y, lev * n.z}, Ft);
-    if (BOTH) o.tb = cross(V3<F>{lb * n.x, lb * n.y, lb * n.z}, Ft);
+    o.G = cross(n, Ft);
+    o.t = V3<F>{lev * o.G.x, lev * o.G.y, lev * o.G.z};
     o.fa = i_lo ? FA : V3<F>{-FA.x, -FA.y, -FA.z};
   }
   if (o.lub) {
@@ -254,14 +276,19 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
 
 // Pair forces from the pair list: one thread per listed pair, from the particle
 // that comes first in it.  The same FP32 cull and the same pair evaluation as the
-// per-particle loop; the pair's flags and its forces and torques on both particles
-// go to the pair record, the spring to both particles' slots.  The pairs run
-// independently, so the grid-stride order does not change any result.
-template <int FORM, bool INTEGRATE>
+// per-particle loop.  Every listed pair's record is written each substep, in pair
+// order (one 32-byte sector per pair, so the writes are sequential and whole):
+// {F, delta/2} {G, flags} with F the pair force on the first particle, G = n x F_t,
+// and zero flags for a pair that does not interact.  The spring goes to the first
+// particle's slot.  The pairs run independently, so the grid-stride order does not
+// change any result.  Integrating substeps only: the force export runs the
+// per-particle loop, which keeps contact and lubrication apart.
+template <int FORM>
 __device__ __forceinline__ void pair_forces_body(const DevState& st, const DevParams& P, int sub_off) {
   using S = typename Traits<FORM>::S;
   using F = typename Traits<FORM>::F;
   using NS = Num<S>;
+  static_assert(sizeof(F) == 4, "pair records hold FP32 force words");
   const Ctl* ctl = st.ctl;
   const int sb = (ctl->st + sub_off) & 1;
   const int nl = ctl->nl;
@@ -271,7 +298,7 @@ __device__ __forceinline__ void pair_forces_body(const DevState& st, const DevPa
   const Quad<S>* omg = (const Quad<S>*)st.omg[sb];
   const uint32_t* cmask = st.cmask[nl];
   Quad<S>* hist = (Quad<S>*)st.hist[nl];
-  Quad<F>* prec = (Quad<F>*)st.prec;
+  float4* prec = st.prec;
   const int64_t M = (int64_t)ctl->npair < st.pcap ? (int64_t)ctl->npair : st.pcap;
   const float fac = P.lubrication ? (1.0f + P.lub_out_f) : 1.0f;
   for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
@@ -291,44 +318,35 @@ __device__ __forceinline__ void pair_forces_body(const DevState& st, const DevPa
     if (P.periodic[1]) dy = dy > P.cf.halfL[1] ? dy - P.cf.L[1] : (dy < -P.cf.halfL[1] ? dy + P.cf.L[1] : dy);
     if (P.periodic[2]) dz = dz > P.cf.halfL[2] ? dz - P.cf.L[2] : (dz < -P.cf.halfL[2] ? dz + P.cf.L[2] : dz);
     const float cut = ((float)NS::f(Pi.d) + (float)NS::f(Pv.d)) * fac;
-    if (!(dx * dx + dy * dy + dz * dz <= cut * cut * 1.0002f)) continue;
-    const int k = pr.y;
-    const bool has = (cm >> k) & 1u;
-    if (has) prefetch_l1(hist + (int64_t)k * N + i);
-    const Quad<S> Vi = ldq(vel + i), Wi = ldq(omg + i);
-    const F vi[3] = {NS::f(Vi.a), NS::f(Vi.b), NS::f(Vi.c)};
-    const F vil[3] = {NS::lo(Vi.a), NS::lo(Vi.b), NS::lo(Vi.c)};
-    const F wi[3] = {NS::f(Wi.a), NS::f(Wi.b), NS::f(Wi.c)};
-    // the first particle of a listed pair is pr.x, so its list entry is the partner
-    // with the first bit set
-    const PairOut<F> o = pair_eval<FORM, INTEGRATE, false, true>(
-        P, Pi, vi, vil, wi, NS::f(Vi.d), (int32_t)((uint32_t)pr.z | kFirstBit), k, has, i, N, pos,
-        vel, omg, hist, pr.w);
-    // the pair's record; the slot masks tell the gather which slots hold this
-    // substep's records (OR is order-free)
-    if (o.contact) {
-      atomicOr(st.amask + i, 1u << k);
-      atomicOr(st.amask + pr.z, 1u << pr.w);
+    float4 r0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), r1 = r0;
+    if (dx * dx + dy * dy + dz * dz <= cut * cut * 1.0002f) {
+      const int k = pr.y;
+      const bool has = (cm >> k) & 1u;
+      if (has) prefetch_l1(hist + (int64_t)k * N + i);
+      const Quad<S> Vi = ldq(vel + i), Wi = ldq(omg + i);
+      const F vi[3] = {NS::f(Vi.a), NS::f(Vi.b), NS::f(Vi.c)};
+      const F vil[3] = {NS::lo(Vi.a), NS::lo(Vi.b), NS::lo(Vi.c)};
+      const F wi[3] = {NS::f(Wi.a), NS::f(Wi.b), NS::f(Wi.c)};
+      // the first particle of a listed pair is pr.x, so its list entry is the partner
+      // with the first bit set
+      const PairOut<F> o = pair_eval<FORM, true, false>(
+          P, Pi, vi, vil, wi, NS::f(Vi.d), (int32_t)((uint32_t)pr.z | kFirstBit), k, has, i, N, pos,
+          vel, omg, hist);
+      const uint32_t fg = (o.contact || o.lub ? kSlotForce : 0u) | (o.contact ? kSlotContact : 0u);
+      if (fg) {
+        const V3<F> f = pair_total(o);
+        r0 = make_float4(f.x, f.y, f.z, o.hd);
+        r1 = make_float4(o.G.x, o.G.y, o.G.z, __uint_as_float(fg));
+      }
     }
-    if (o.lub) {
-      atomicOr(st.amask + N + i, 1u << k);
-      atomicOr(st.amask + N + pr.z, 1u << pr.w);
-    }
-    if (o.contact || o.lub) {
-      const V3<F> z{F(0), F(0), F(0)};
-      const V3<F> fa = o.contact ? o.fa : z, ta = o.contact ? o.t : z, tb = o.contact ? o.tb : z;
-      const V3<F> l = o.lub ? o.l : z;
-      Quad<F>* r = prec + 3 * m;
-      stq(r, Quad<F>{fa.x, fa.y, fa.z, ta.x});
-      stq(r + 1, Quad<F>{ta.y, ta.z, tb.x, tb.y});
-      stq(r + 2, Quad<F>{tb.z, l.x, l.y, l.z});
-    }
+    prec[2 * m] = r0;
+    prec[2 * m + 1] = r1;
   }
 }
 
-template <int FORM, bool INTEGRATE>
+template <int FORM>
 __global__ void __launch_bounds__(128, 6) k_pair_forces(DevState st, DevParams P, int sub_off) {
-  pair_forces_body<FORM, INTEGRATE>(st, P, sub_off);
+  pair_forces_body<FORM>(st, P, sub_off);
 }
 
 // BS threads per block, at least MINB resident blocks per SM (which caps the
@@ -419,73 +437,45 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
     }
     }
   }
-  // phase 2: interacting pairs only, in slot order
+  // phase 2: interacting pairs only, in slot order.  An integrating substep adds each
+  // pair's force (contact plus lubrication, pair_total) to fc as one term; the force
+  // export keeps contact (fc) and lubrication (fl) apart.
   if constexpr (GATHER) {
-    const Quad<F>* prec = (const Quad<F>*)st.prec;
-    const int32_t* pid = st.pid + i * P.cap;
-    uint32_t mc = 0, ml = 0, first = 0;
-    if (valid) {
-      first = st.fmask[i];
-      // this substep's contact and lubrication slots, cleared for the next substep
-      mc = st.amask[i];
-      ml = st.amask[N + i];
-      st.amask[i] = 0u;
-      st.amask[N + i] = 0u;
-    }
-    live = mc | ml;
-    // kGatherBatch slots per round: their pair ids, then their records, are loaded
-    // together (two dependent round trips per round), then added in slot order
+    static_assert(INTEGRATE, "the pair list serves integrating substeps only");
+    // the pair records of this particle's slots, in slot order: the slot's pair id
+    // (slot-major rows: a warp reads contiguous words), then the pair's sector
+    const int nn = valid ? st.nn[nl][i] : 0;
+    const int32_t* pid = st.pid;
+    const float4* prec = st.prec;
+    for (int k = 0; k < nn; ++k) prefetch_l1(pid + (int64_t)k * N + i);
     constexpr int kGatherBatch = 4;
-    while (live) {
-      int ks[kGatherBatch];
-      int cnt = 0;
+    for (int k0 = 0; k0 < nn; k0 += kGatherBatch) {
+      int32_t e[kGatherBatch];
+#pragma unroll
+      for (int u = 0; u < kGatherBatch; ++u) e[u] = k0 + u < nn ? pid[(int64_t)(k0 + u) * N + i] : -1;
+      float4 ra[kGatherBatch], rb[kGatherBatch];
 #pragma unroll
       for (int u = 0; u < kGatherBatch; ++u) {
-        ks[u] = 0;
-        if (live) {
-          ks[u] = __ffs(live) - 1;
-          live &= live - 1;
-          cnt = u + 1;
-        }
-      }
-      int32_t ms[kGatherBatch];
-#pragma unroll
-      for (int u = 0; u < kGatherBatch; ++u) ms[u] = u < cnt ? pid[ks[u]] : 0;
-      Quad<F> q[kGatherBatch][3];
-#pragma unroll
-      for (int u = 0; u < kGatherBatch; ++u) {
-        const bool ok = u < cnt && (uint64_t)(uint32_t)ms[u] < (uint64_t)st.pcap;
-        const Quad<F>* r = prec + 3 * (int64_t)(ok ? ms[u] : 0);
-        q[u][0] = ldq(r);
-        q[u][1] = ldq(r + 1);
-        q[u][2] = ldq(r + 2);
-        if (!ok) ks[u] = -1;
+        const int64_t m = (int64_t)nbr_index(e[u]);
+        const bool ok = e[u] != -1 && m < st.pcap;
+        ra[u] = ok ? prec[2 * m] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        rb[u] = ok ? prec[2 * m + 1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       }
 #pragma unroll
       for (int u = 0; u < kGatherBatch; ++u) {
-        if (u >= cnt || ks[u] < 0) continue;
-        const int k = ks[u];
-        const bool fi = (first >> k) & 1u;
-        const Quad<F>& q0 = q[u][0];
-        const Quad<F>& q1 = q[u][1];
-        const Quad<F>& q2 = q[u][2];
-        if ((mc >> k) & 1u) {
-          // the force on the partner is minus the force on the first particle
-          if (fi) {
-            fc.x += q0.a; fc.y += q0.b; fc.z += q0.c;
-            tq.x += q0.d; tq.y += q1.a; tq.z += q1.b;
+        const uint32_t fg = __float_as_uint(rb[u].w);
+        // the record holds the force on the first particle; the partner gets minus it
+        if (fg & kSlotForce) {
+          if (nbr_first(e[u])) {
+            fc.x += ra[u].x; fc.y += ra[u].y; fc.z += ra[u].z;
           } else {
-            fc.x += -q0.a; fc.y += -q0.b; fc.z += -q0.c;
-            tq.x += q1.c; tq.y += q1.d; tq.z += q2.a;
+            fc.x += -ra[u].x; fc.y += -ra[u].y; fc.z += -ra[u].z;
           }
-          if (INTEGRATE) nmask |= 1u << k;
         }
-        if ((ml >> k) & 1u) {
-          if (fi) {
-            fl.x += q2.b; fl.y += q2.c; fl.z += q2.d;
-          } else {
-            fl.x += -q2.b; fl.y += -q2.c; fl.z += -q2.d;
-          }
+        if (fg & kSlotContact) {
+          const F lev = ri - ra[u].w;
+          tq.x += lev * rb[u].x; tq.y += lev * rb[u].y; tq.z += lev * rb[u].z;
+          nmask |= 1u << (k0 + u);
         }
       }
     }
@@ -542,7 +532,8 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
                                                         (q_mask[wid][L] >> k) & 1u, iL, N, pos, vel,
                                                         omg, hist);
         F* r = q_res[wid][lane];
-        r[0] = o.fa.x; r[1] = o.fa.y; r[2] = o.fa.z;
+        const V3<F> f0 = INTEGRATE ? pair_total(o) : o.fa;
+        r[0] = f0.x; r[1] = f0.y; r[2] = f0.z;
         r[3] = o.t.x; r[4] = o.t.y; r[5] = o.t.z;
         r[6] = o.l.x; r[7] = o.l.y; r[8] = o.l.z;
         if constexpr (EXT) {
@@ -557,13 +548,23 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
       for (int q = q0; q < q1; ++q) {
         const F* r = q_res[wid][q - base];
         const int fg = q_flag[wid][q - base];
+        if (INTEGRATE) {
+          if (fg & 3) {
+            fc.x += r[0]; fc.y += r[1]; fc.z += r[2];
+          }
+        } else {
+          if (fg & 1) {
+            fc.x += r[0]; fc.y += r[1]; fc.z += r[2];
+          }
+          if (fg & 2) {
+            fl.x += r[6]; fl.y += r[7]; fl.z += r[8];
+          }
+        }
         if (fg & 1) {
-          fc.x += r[0]; fc.y += r[1]; fc.z += r[2];
           tq.x += r[3]; tq.y += r[4]; tq.z += r[5];
           if (INTEGRATE) nmask |= 1u << (q_pair[wid][q] & 255);
         }
         if (fg & 2) {
-          fl.x += r[6]; fl.y += r[7]; fl.z += r[8];
           if constexpr (EXT) {
             if (P.lub_tangential) {
               tq.x += r[9]; tq.y += r[10]; tq.z += r[11];
@@ -579,13 +580,24 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
         live &= live - 1;
         const PairOut<F> o = pair_eval<FORM, INTEGRATE, EXT>(P, Pi, vi, vil, wi, mi, nbr[(int64_t)k * N + i], k,
                                                         (mask >> k) & 1u, i, N, pos, vel, omg, hist);
+        if (INTEGRATE) {
+          if (o.contact || o.lub) {
+            const V3<F> f = pair_total(o);
+            fc.x += f.x; fc.y += f.y; fc.z += f.z;
+          }
+        } else {
+          if (o.contact) {
+            fc.x += o.fa.x; fc.y += o.fa.y; fc.z += o.fa.z;
+          }
+          if (o.lub) {
+            fl.x += o.l.x; fl.y += o.l.y; fl.z += o.l.z;
+          }
+        }
         if (o.contact) {
-          fc.x += o.fa.x; fc.y += o.fa.y; fc.z += o.fa.z;
           tq.x += o.t.x; tq.y += o.t.y; tq.z += o.t.z;
           if (INTEGRATE) nmask |= 1u << k;
         }
         if (o.lub) {
-          fl.x += o.l.x; fl.y += o.l.y; fl.z += o.l.z;
           if (EXT && P.lub_tangential) {
             tq.x += o.lt.x; tq.y += o.lt.y; tq.z += o.lt.z;
           }
@@ -802,7 +814,7 @@ static void launch_bs(const DevState& st, const DevMesh& mesh, const DevParams& 
 // count lives on the device), then the per-particle kernel gathering the records.
 template <int FORM>
 static void launch_pairs(const DevState& st, const DevMesh& mesh, const DevParams& P, int sub_off,
-                         bool integrate, unsigned long long next, int use_cond, cudaStream_t s) {
+                         unsigned long long next, int use_cond, cudaStream_t s) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -812,13 +824,8 @@ static void launch_pairs(const DevState& st, const DevMesh& mesh, const DevParam
   if (g < 1) g = 1;
   const int64_t grid = (st.N + 127) / 128;
   const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)next;
-  if (integrate) {
-    k_pair_forces<FORM, true><<<(unsigned)g, 128, 0, s>>>(st, P, sub_off);
-    k_substep<FORM, true, 128, 5, false, false, true><<<(unsigned)grid, 128, 0, s>>>(st, mesh, P, sub_off, h, use_cond);
-  } else {
-    k_pair_forces<FORM, false><<<(unsigned)g, 128, 0, s>>>(st, P, sub_off);
-    k_substep<FORM, false, 128, 5, false, false, true><<<(unsigned)grid, 128, 0, s>>>(st, mesh, P, sub_off, h, 0);
-  }
+  k_pair_forces<FORM><<<(unsigned)g, 128, 0, s>>>(st, P, sub_off);
+  k_substep<FORM, true, 128, 5, false, false, true><<<(unsigned)grid, 128, 0, s>>>(st, mesh, P, sub_off, h, use_cond);
 }
 
 template <int FORM>
@@ -841,7 +848,8 @@ static void launch_one(const DevState& st, const DevMesh& mesh, const DevParams&
       case SUBSTEP_B128_OCC8_LOOP: launch_bs<FORM, 128, 8, false>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
       case SUBSTEP_B64_LOOP: launch_bs<FORM, 64, 12, false>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
       case SUBSTEP_PAIRS:
-        if (st.pairs) launch_pairs<FORM>(st, mesh, P, sub_off, integrate, next, use_cond, s);
+        // the force export (not integrating) runs the per-particle loop
+        if (st.pairs && integrate) launch_pairs<FORM>(st, mesh, P, sub_off, next, use_cond, s);
         else launch_bs<FORM, 128, 6, false>(st, mesh, P, sub_off, integrate, next, use_cond, s);
         return;
       default: launch_bs<FORM, 128, 6, true>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
