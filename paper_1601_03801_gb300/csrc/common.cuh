@@ -140,6 +140,7 @@ struct Num<float> {
   __device__ static float addq(float a, float b) { return a + b; }
   __device__ static float subq(float a, float b) { return a - b; }
   __device__ static float fmaq(float a, float b, float c) { return fmaf(b, c, a); }
+  __device__ static float neg(float a) { return -a; }
   static constexpr bool kExtended = false;  // no wider word than the force word
 };
 
@@ -160,6 +161,7 @@ struct Num<double> {
   __device__ static double addq(double a, double b) { return a + b; }
   __device__ static double subq(double a, double b) { return a - b; }
   __device__ static double fmaq(double a, double b, double c) { return a + b * c; }
+  __device__ static double neg(double a) { return -a; }
   static constexpr bool kExtended = false;
 };
 
@@ -184,6 +186,7 @@ struct Num<dd> {
   __device__ static dd addq(dd a, dd b) { return dd_add_fast(a, b); }
   __device__ static dd subq(dd a, dd b) { return dd_sub_fast(a, b); }
   __device__ static dd fmaq(dd a, float b, float c) { return dd_add_fast(a, two_prod(b, c)); }
+  __device__ static dd neg(dd a) { return dd_neg(a); }
   static constexpr bool kExtended = true;   // state word wider than the force word
 };
 

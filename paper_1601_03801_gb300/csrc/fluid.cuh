@@ -116,15 +116,16 @@ __device__ __forceinline__ void fluid_force(const DevParams& P, const ForceConst
       }
       continue;
     }
-    F rel = NS::f(NS::sub(x[a], B.lo[a]));
+    F rel = NS::dif(x[a], B.lo[a]);
     F s = rel * K.inv_h[a] - F(0.5);
     if constexpr (NS::kExtended) {
-      // cell-relative: the cell k = floor(s) from FP32, the fraction from the
-      // double-float offset x - c_k to that cell's centre, so the weight keeps
-      // ~1e-7 of a cell on any box (s itself carries ~n 6e-8 of rounding)
+      // cell-relative: the cell k = floor(s) from FP32 (a wrong guess by one is
+      // corrected below), the fraction from the double-float offset x - c_k to that
+      // cell's centre, so the weight keeps ~1e-7 of a cell on any box (s itself
+      // carries ~n 6e-8 of rounding)
       const F kf = xfloor(s);
-      const S ck = NS::add(B.lo[a], NS::mul_f(B.h[a], kf + F(0.5)));
-      const F f = NS::f(NS::sub(x[a], ck)) * K.inv_h[a];
+      const S ck = NS::addq(B.lo[a], NS::mul_f(B.h[a], kf + F(0.5)));
+      const F f = NS::f(NS::subq(x[a], ck)) * K.inv_h[a];
       axis_w_kf<F>(kf, f, P.nc[a], P.periodic[a], &i0[a], &i1[a], &fr[a]);
     } else {
       axis_w<F>(s, P.nc[a], P.periodic[a], &i0[a], &i1[a], &fr[a]);
@@ -178,13 +179,13 @@ __device__ __forceinline__ void fluid_force(const DevParams& P, const ForceConst
     if (es > K.eps_max) es = K.eps_max;
     F ef = F(1) - es;
     F w0 = U[0] - v[0], w1 = U[1] - v[1], w2 = U[2] - v[2];
-    F wm = xsqrt(w0 * w0 + w1 * w1 + w2 * w2);
+    F wm = xsqrt_pos(w0 * w0 + w1 * w1 + w2 * w2);
     F Re = xdiv(d * wm, K.nu_f);
     F A1 = xpow_drag(ef, F(4.14));
     F A2 = ef <= F(0.85) ? F(0.8) * xpow_drag(ef, F(1.28)) : xpow_drag(ef, F(2.65));
     F t = F(0.06) * Re;
-    F Vr = F(0.5) * (A1 - t + xsqrt(t * t + F(0.12) * Re * (F(2) * A2 - A1) + A1 * A1));
-    F c = F(0.63) * xsqrt(wm) + F(4.8) * xsqrt(xdiv(Vr * K.nu_f, d));
+    F Vr = F(0.5) * (A1 - t + xsqrt_pos(t * t + F(0.12) * Re * (F(2) * A2 - A1) + A1 * A1));
+    F c = F(0.63) * xsqrt_pos(wm) + F(4.8) * xsqrt_pos(xdiv(Vr * K.nu_f, d));
     F coef = xdiv(F(0.75) * Vp * K.rho_f * c * c, Vr * Vr * d);
     out[0] += coef * w0;
     out[1] += coef * w1;

@@ -56,35 +56,37 @@ __device__ __forceinline__ V3<F> hm_core(const ForceConsts<F>& K, V3<F> n, F del
   F vn = vrel.x * n.x + vrel.y * n.y + vrel.z * n.z;
   V3<F> vt{vrel.x - vn * n.x, vrel.y - vn * n.y, vrel.z - vn * n.z};
   F fn_s = -fel - cn * vn;  // F_n = fn_s * n
-  // spring: rotate onto the tangent plane, keep the length, add v_t dt.  Every term
-  // is an exact product added to the state word (fmaq: error ~2^-44 of the operands)
+  // spring: rotate onto the tangent plane, keep the length, add v_t dt.  A substep's
+  // change, -(xi.n) n + (1/sqrt(1-t) - 1)(xi - (xi.n) n) + v_t dt, is formed in the
+  // force word (n, v_t and the projection carry force-word rounding already; a wrong
+  // normal part is projected out at the next substep) and added to the spring in the
+  // state word, so the history accumulates without losing small changes
   S xi[3];
+  F inc[3] = {K.dt * vt.x, K.dt * vt.y, K.dt * vt.z};
   if (has_old) {
-    F xf[3] = {NS::f(xi_old[0]), NS::f(xi_old[1]), NS::f(xi_old[2])};
-    F proj = xf[0] * n.x + xf[1] * n.y + xf[2] * n.z;
-    F len2 = xf[0] * xf[0] + xf[1] * xf[1] + xf[2] * xf[2];
-    xi[0] = NS::fmaq(xi_old[0], -proj, n.x);
-    xi[1] = NS::fmaq(xi_old[1], -proj, n.y);
-    xi[2] = NS::fmaq(xi_old[2], -proj, n.z);
+    const F xf[3] = {NS::f(xi_old[0]), NS::f(xi_old[1]), NS::f(xi_old[2])};
+    const F proj = xf[0] * n.x + xf[1] * n.y + xf[2] * n.z;
+    const F len2 = xf[0] * xf[0] + xf[1] * xf[1] + xf[2] * xf[2];
+    const F pr[3] = {xf[0] - proj * n.x, xf[1] - proj * n.y, xf[2] - proj * n.z};
+    F scm1 = F(0);  // 1/sqrt(1-t) - 1, t = (xi.n)^2 / |xi|^2
     if (len2 > F(0)) {
-      F t = xdiv(proj * proj, len2);
+      const F t = xdiv(proj * proj, len2);
       if (t < F(1)) {
-        F s1 = xsqrt_pos(F(1) - t);
-        F scm1 = xdiv(t, s1 * (F(1) + s1));  // 1/sqrt(1-t) - 1
-        F r0 = NS::f(xi[0]), r1 = NS::f(xi[1]), r2 = NS::f(xi[2]);
-        xi[0] = NS::fmaq(xi[0], scm1, r0);
-        xi[1] = NS::fmaq(xi[1], scm1, r1);
-        xi[2] = NS::fmaq(xi[2], scm1, r2);
+        const F s1 = xsqrt_pos(F(1) - t);
+        scm1 = xdiv(t, s1 * (F(1) + s1));
       }
     }
+    inc[0] = (scm1 * pr[0] - proj * n.x) + inc[0];
+    inc[1] = (scm1 * pr[1] - proj * n.y) + inc[1];
+    inc[2] = (scm1 * pr[2] - proj * n.z) + inc[2];
+    xi[0] = NS::add_f(xi_old[0], inc[0]);
+    xi[1] = NS::add_f(xi_old[1], inc[1]);
+    xi[2] = NS::add_f(xi_old[2], inc[2]);
   } else {
-    xi[0] = S{};
-    xi[1] = S{};
-    xi[2] = S{};
+    xi[0] = NS::from_f(inc[0]);
+    xi[1] = NS::from_f(inc[1]);
+    xi[2] = NS::from_f(inc[2]);
   }
-  xi[0] = NS::fmaq(xi[0], K.dt, vt.x);
-  xi[1] = NS::fmaq(xi[1], K.dt, vt.y);
-  xi[2] = NS::fmaq(xi[2], K.dt, vt.z);
   V3<F> Ft{-St * NS::f(xi[0]) - ct * vt.x, -St * NS::f(xi[1]) - ct * vt.y,
            -St * NS::f(xi[2]) - ct * vt.z};
   // Coulomb limit |F_t| <= mu |F_n|, tested on the squares (no root unless sliding)
@@ -169,9 +171,9 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (!P.periodic[a]) continue;
-    F c = NS::f(dxs[a]);
-    if (c > K.halfL[a]) dxs[a] = NS::subq(dxs[a], B.L[a]);
-    else if (c < -K.halfL[a]) dxs[a] = NS::addq(dxs[a], B.L[a]);
+    // across the periodic face: one shift by a box length toward zero
+    const F c = NS::f(dxs[a]);
+    if (xabs(c) > K.halfL[a]) dxs[a] = NS::addq(dxs[a], c > F(0) ? NS::neg(B.L[a]) : B.L[a]);
   }
   S d2 = NS::addq(NS::addq(NS::mul(dxs[0], dxs[0]), NS::mul(dxs[1], dxs[1])), NS::mul(dxs[2], dxs[2]));
   S ssum = NS::addq(A.d, Bq.d);
@@ -345,7 +347,7 @@ __device__ __forceinline__ void pair_forces_body(const DevState& st, const DevPa
 }
 
 template <int FORM>
-__global__ void __launch_bounds__(128, 6) k_pair_forces(DevState st, DevParams P, int sub_off) {
+__global__ void __launch_bounds__(128, 7) k_pair_forces(DevState st, DevParams P, int sub_off) {
   pair_forces_body<FORM>(st, P, sub_off);
 }
 
@@ -616,8 +618,8 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
       for (int side = 0; side < 2; ++side) {
         if (side == 0 ? !P.wall_lo[a] : !P.wall_hi[a]) continue;
         // overlap r - dist in the state word (dist = x - lo or hi - x)
-        S dist_s = side == 0 ? NS::sub(xi_s[a], B.lo[a]) : NS::sub(B.hi[a], xi_s[a]);
-        const F delta = NS::f(NS::sub(Pi.d, dist_s));
+        S dist_s = side == 0 ? NS::subq(xi_s[a], B.lo[a]) : NS::subq(B.hi[a], xi_s[a]);
+        const F delta = NS::f(NS::subq(Pi.d, dist_s));
         V3<F> n{0, 0, 0};
         const F sgn = side == 0 ? F(-1) : F(1);
         if (a == 0) n.x = sgn; else if (a == 1) n.y = sgn; else n.z = sgn;
@@ -825,7 +827,7 @@ static void launch_pairs(const DevState& st, const DevMesh& mesh, const DevParam
   const int64_t grid = (st.N + 127) / 128;
   const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)next;
   k_pair_forces<FORM><<<(unsigned)g, 128, 0, s>>>(st, P, sub_off);
-  k_substep<FORM, true, 128, 5, false, false, true><<<(unsigned)grid, 128, 0, s>>>(st, mesh, P, sub_off, h, use_cond);
+  k_substep<FORM, true, 128, 6, false, false, true><<<(unsigned)grid, 128, 0, s>>>(st, mesh, P, sub_off, h, use_cond);
 }
 
 template <int FORM>
