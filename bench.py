@@ -809,15 +809,19 @@ def reference_arm(args):
 
 def kernels_only(args):
     """Run a workload for a few steps without timing (profiling driver: the command
-    an ncu capture wraps).  --case bed200k (default), large, or small."""
+    an ncu capture wraps).  --case bed200k (default), large, patch, or small."""
     import torch
 
     from paper_1601_03801_gb300 import sedi
-    from paper_1601_03801_gb300.workloads import bed_case, large_case, small_case
+    from paper_1601_03801_gb300.workloads import bed_case, large_case, large_patch, small_case
 
     torch.cuda.set_device(0)
     if args.case == "large":
         prm, parts, fl = large_case()
+    elif args.case == "patch":
+        # a 100 x 100 mm patch of the large bed (1.25M spheres, a few GB on the device):
+        # the profiling case whose working set is larger than L2
+        prm, parts, fl = large_patch(*large_case())
     elif args.case == "small":
         prm, parts = small_case(parity_addon=True)
         fl = {"U": None}
@@ -859,7 +863,7 @@ def main():
                     help="untimed steps before the warm-up (the method settles the bed further)")
     ap.add_argument("--mode", default="bench", choices=["bench", "kernels"],
                     help="kernels: run a workload untimed (profiling driver)")
-    ap.add_argument("--case", default="bed200k", choices=["bed200k", "large", "small"],
+    ap.add_argument("--case", default="bed200k", choices=["bed200k", "large", "patch", "small"],
                     help="kernels mode: workload")
     ap.add_argument("--form", default="split", choices=["split", "plain", "fp64"])
     ap.add_argument("--with-cnn", action="store_true",

@@ -159,6 +159,14 @@ typedef struct sedi_params {
                                               (see sedi_get_timings) [0] */
   int32_t use_cnn_guess;                   /* start every smoothing pseudo-step from
                                               the learned guess (sedi_cnn_*) [0] */
+  int32_t bins_per_cutoff;                 /* link-cell bins per list cutoff of the list
+                                              build: 0 = autotuned with the launch shape
+                                              (1 until then, and whenever substep_variant
+                                              is fixed) [0]; 1 or 2 = fixed (2: bins of
+                                              half a cutoff, a 5 x 5 x 5 stencil; needs 5
+                                              bins on every periodic axis).  Lists hold
+                                              their partners in caller-index order, so
+                                              the choice changes no result. */
   double cnn_scale[4];                     /* network input/output scale of eps_s and
                                               F_fp x, y, z [1, 1, 1, 1] */
   uint64_t seed;                           /* reserved for stochastic extensions [0] */
@@ -176,6 +184,9 @@ typedef struct sedi_stats {
   int32_t nbr_capacity;   /* capacity in use */
   int32_t substep_variant; /* launch variant of the substep kernel in use (-1: not yet tuned) */
   int32_t substep_block;   /* its threads per block (0: not yet tuned) */
+  int32_t bins_per_cutoff; /* link-cell bins per list cutoff of the list build (1 or 2;
+                              picked with the launch variant) */
+  int32_t pad;
 } sedi_stats;
 
 /* Fill p with the defaults listed above (box 20 x 20 x 40 mm, periodic x/y,

@@ -86,6 +86,7 @@ struct DevParams {
   int32_t nb[3];                   // bins per axis
   int64_t nbins;
   float bin_inv[3];                // bins per metre
+  int32_t bin_reach;               // R: bins per list cutoff (the stencil spans +-R bins)
   // deposition
   int32_t shift[3];                // eps, momentum, force
   double two_shift[3];             // 2^shift
@@ -300,6 +301,7 @@ struct DevMesh {
 };
 
 constexpr int kWalls = 6;
+constexpr int kMaxCap = 32;  // listed neighbours per particle at most (slot masks are 32-bit)
 
 // One bed of an ensemble as the kernels see it: the single-bed views of its arrays
 // and parameters.  Batched launches take a device table of these and pick the bed

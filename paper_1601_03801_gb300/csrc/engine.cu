@@ -39,7 +39,9 @@ struct sedi_handle {
   DevParams P{};
   DevMesh mesh{};
   std::vector<void*> part_allocs;  // per-particle buffers
+  std::vector<void*> bin_allocs;   // link-cell bins (resized when the bin size changes)
   std::vector<void*> mesh_allocs;
+  double rc_max = 0.0;             // largest list cutoff 2 r_max (1 + f) + skin
   int64_t since_set = 0;               // substeps since the particles were set
   bool is_bed = false;                 // a bed of an ensemble (stepped by the ensemble)
   double* fdev = nullptr;              // FP64 U, grad p, DU/Dt [3][C][3] on the device
@@ -87,6 +89,7 @@ struct sedi_handle {
   Ctl* ens_ctl = nullptr;         // [B] gathered control blocks
   EnsLaunch ens{};
   bool ens_dirty = true;          // a bed's buffers changed: rebuild the table
+  int ens_variant = SUBSTEP_B128_LOOP;  // launch shape of the batched substep
   bool ens_fresh = false;         // the batched averaging is newer than the last step
 };
 
@@ -286,7 +289,8 @@ int check_params(sedi_handle* h, const sedi_params& p) {
   if (p.tau_scheme == SEDI_TAU_BDF2 && p.use_cnn_guess)
     return fail(h, SEDI_EINVAL, "the learned warm start runs backward-Euler pseudo-steps only");
   if (p.precision_form < 0 || p.precision_form > 2) return fail(h, SEDI_EINVAL, "unknown precision_form");
-  if (p.nbr_capacity < 1 || p.nbr_capacity > 32) return fail(h, SEDI_EINVAL, "nbr_capacity must be in [1, 32]");
+  if (p.bins_per_cutoff < 0 || p.bins_per_cutoff > 2) return fail(h, SEDI_EINVAL, "bins_per_cutoff must be 0, 1 or 2");
+  if (p.nbr_capacity < 1 || p.nbr_capacity > kMaxCap) return fail(h, SEDI_EINVAL, "nbr_capacity must be in [1, %d]", kMaxCap);
   if (p.n_beds < 1 || p.n_beds > kMaxBeds) return fail(h, SEDI_EINVAL, "n_beds must be in [1, %d]", kMaxBeds);
   if (p.substep_variant < -1 || p.substep_variant >= kSubstepVariants)
     return fail(h, SEDI_EINVAL, "substep_variant must be -1 (tuned) or in [0, %d]", kSubstepVariants - 1);
@@ -425,6 +429,54 @@ int upload_mesh(sedi_handle* h, bool velocity = true) {
   return 0;
 }
 
+// Link-cell bins of edge >= rc_max / R (R bins per list cutoff, with margin): the list
+// build visits the (2R + 1)^3 bins around a particle's bin.  Lists hold their partners
+// in caller-index order whatever the bins, so R changes no result, only the cost.
+// Nonzero when a periodic axis is shorter than 2R + 1 bins or the bins would not fit
+// 31-bit indices.
+int bins_for(const sedi_handle* h, int R, int32_t nb[3], int64_t* nbins) {
+  const sedi_params& p = h->prm;
+  const double hb = h->rc_max * 1.001 / R;
+  *nbins = 1;
+  for (int a = 0; a < 3; ++a) {
+    const double L = p.hi[a] - p.lo[a];
+    int64_t n = (int64_t)std::floor(L / hb);
+    if (n < 1) n = 1;
+    if (p.periodic[a] && n < 2 * R + 1) return 1;
+    if (n > ((int64_t)1 << 30)) return 2;
+    nb[a] = (int32_t)n;
+    *nbins *= n;
+    if (*nbins > ((int64_t)1 << 31) - 2) return 2;
+  }
+  return 0;
+}
+
+int set_bins(sedi_handle* h, int R) {
+  int32_t nb[3];
+  int64_t nbins = 0;
+  if (const int why = bins_for(h, R, nb, &nbins)) {
+    if (R == 1 && why == 1)
+      return fail(h, SEDI_EINVAL, "a periodic axis is shorter than 3 list cutoffs (%g m)", 3 * h->rc_max * 1.001);
+    return fail(h, SEDI_EINVAL, "%d bins per list cutoff do not fit this box", R);
+  }
+  free_list(h->bin_allocs);
+  DevState& st = h->st;
+  for (int a = 0; a < 3; ++a) {
+    h->P.nb[a] = nb[a];
+    h->P.bin_inv[a] = (float)((double)nb[a] / (h->prm.hi[a] - h->prm.lo[a]));
+  }
+  h->P.nbins = nbins;
+  h->P.bin_reach = R;
+  const int64_t nblk = (nbins + 1023) / 1024 + 1;
+  int rc;
+  if ((rc = dmalloc(h, h->bin_allocs, (void**)&st.bin_count, 4 * nbins)) ||
+      (rc = dmalloc(h, h->bin_allocs, (void**)&st.bin_start, 4 * (nbins + 1))) ||
+      (rc = dmalloc(h, h->bin_allocs, (void**)&st.bin_fill, 4 * nbins)) ||
+      (rc = dmalloc(h, h->bin_allocs, (void**)&st.scan_blk, 4 * nblk)))
+    return rc;
+  return 0;
+}
+
 int alloc_particles(sedi_handle* h, int64_t N, double rmax) {
   clear_graphs(h);
   free_list(h->part_allocs);
@@ -466,30 +518,20 @@ int alloc_particles(sedi_handle* h, int64_t N, double rmax) {
     CK(cudaMemset(st.pid, 0, 4 * cap * N));
     CK(cudaMemset(st.prec, 0, 32 * st.pcap));
   }
-  // bins: edge >= the largest list cutoff (2 r_max (1 + f) + skin) with margin
-  const sedi_params& p = h->prm;
-  const double rc_max = (2.0 * rmax) * (1.0 + p.lub_h_out_frac) + p.skin;
-  const double hb = rc_max * 1.001;
-  int64_t nbins = 1;
-  for (int a = 0; a < 3; ++a) {
-    const double L = p.hi[a] - p.lo[a];
-    int nb = (int)std::floor(L / hb);
-    if (nb < 1) nb = 1;
-    if (p.periodic[a] && nb < 3)
-      return fail(h, SEDI_EINVAL, "periodic axis %d is shorter than 3 list cutoffs (%g m)", a, 3 * hb);
-    h->P.nb[a] = nb;
-    h->P.bin_inv[a] = (float)((double)nb / L);
-    nbins *= nb;
+  // bins: R = 1 (edge >= the largest list cutoff) until the autotuner picks otherwise;
+  // a tuned R is kept while it fits the new particles
+  h->rc_max = (2.0 * rmax) * (1.0 + h->prm.lub_h_out_frac) + h->prm.skin;
+  if (h->prm.bins_per_cutoff > 0) {
+    if ((rc = set_bins(h, h->prm.bins_per_cutoff))) return rc;
+  } else {
+    int R = h->P.bin_reach > 1 ? h->P.bin_reach : 1;
+    int32_t nb[3];
+    int64_t nbins = 0;
+    if (R > 1 && bins_for(h, R, nb, &nbins)) R = 1;
+    if ((rc = set_bins(h, R))) return rc;
   }
-  if (nbins > (int64_t)1 << 31) return fail(h, SEDI_EINVAL, "too many bins");
-  h->P.nbins = nbins;
-  const int64_t nblk = (nbins + 1023) / 1024 + 1;
   if ((rc = dmalloc(h, h->part_allocs, (void**)&st.bin_of, 4 * N))) return rc;
-  if ((rc = dmalloc(h, h->part_allocs, (void**)&st.bin_count, 4 * nbins))) return rc;
-  if ((rc = dmalloc(h, h->part_allocs, (void**)&st.bin_start, 4 * (nbins + 1)))) return rc;
-  if ((rc = dmalloc(h, h->part_allocs, (void**)&st.bin_fill, 4 * nbins))) return rc;
   if ((rc = dmalloc(h, h->part_allocs, (void**)&st.order, 4 * N))) return rc;
-  if ((rc = dmalloc(h, h->part_allocs, (void**)&st.scan_blk, 4 * nblk))) return rc;
   if ((rc = dmalloc(h, h->part_allocs, (void**)&st.fdbg, 8 * 12 * N))) return rc;
   CK(cudaMemsetAsync(st.cmask[0], 0, 4 * N, h->stream));
   CK(cudaMemsetAsync(st.cmask[1], 0, 4 * N, h->stream));
@@ -597,16 +639,21 @@ int rebuild_now(sedi_handle* h) {
 
 // ---------------------------------------------------------------- autotuner
 // The launch variant of the substep kernel (threads per block x resident blocks,
-// which sets the register budget, the pair phase, or the pair list) is picked per
-// workload: one integrating substep of every variant is timed with events in
-// interleaved rounds, and the variant with the lowest median wins.  A substep
-// reads the state buffer the step starts from and writes the other one, so only
-// the arrays it updates in place (springs and their masks, wall springs, lagged
-// accelerations, the control block) are copied aside first and put back after
-// every timed launch: tuning leaves the state as it found it.  Results are keyed
-// by (GPU, N, diameter range, form), kept for the process and, when the
-// environment variable SEDI_AUTOTUNE_CACHE names a file, in that file as one JSON
-// object per line.
+// which sets the register budget, the pair phase, or the pair list) and the bin size
+// of the list build (R = 1 or 2 bins per list cutoff) are picked per workload.  For
+// each R the bins are resized and the lists rebuilt at once from the current
+// positions (springs carried over, as at any rebuild); then one integrating substep of
+// every variant is timed with events in interleaved rounds.  A substep reads the
+// state buffer the step starts from and writes the other one, so only the arrays it
+// updates in place (springs and their masks, wall springs, lagged accelerations, the
+// control block) are copied aside first and put back after every timed launch.  The
+// cost of a pair (R, variant) is its median substep plus the rebuild time of R times
+// the rebuilds per substep seen so far; the cheapest wins.  Neither choice changes a
+// result (lists are sorted by caller index, every variant adds the same terms in the
+// same order, and an extra rebuild lists the same interacting pairs), so tuning
+// leaves the trajectory as it found it.  Results are keyed by (GPU, N, diameter
+// range, form, terms), kept for the process and, when the environment variable
+// SEDI_AUTOTUNE_CACHE names a file, in that file as one JSON object per line.
 
 constexpr int kTuneRounds = 5;
 // Springs and lubrication gaps form over the first substeps after the particles are
@@ -614,8 +661,13 @@ constexpr int kTuneRounds = 5;
 // a state that has them.  Until then the per-particle loop at 128 x 6 runs.
 constexpr int64_t kTuneAfter = 200;
 
+struct TuneChoice {
+  int variant = -1;
+  int reach = 1;  // bins per list cutoff
+};
+
 std::mutex g_tune_mu;
-std::map<std::string, int> g_tune_cache;
+std::map<std::string, TuneChoice> g_tune_cache;
 
 std::string tune_key(sedi_handle* h) {
   int dev = 0;
@@ -635,38 +687,70 @@ std::string tune_key(sedi_handle* h) {
   return buf;
 }
 
-int tune_file_lookup(const std::string& key) {
+TuneChoice tune_file_lookup(const std::string& key) {
+  TuneChoice found;
   const char* path = std::getenv("SEDI_AUTOTUNE_CACHE");
-  if (!path || !*path) return -1;
+  if (!path || !*path) return found;
   FILE* f = std::fopen(path, "r");
-  if (!f) return -1;
-  int found = -1;
-  char line[1024];
+  if (!f) return found;
+  char line[2048];
   const std::string want = "\"key\": \"" + key + "\"";
   while (std::fgets(line, sizeof(line), f)) {
     const char* k = std::strstr(line, want.c_str());
     const char* v = std::strstr(line, "\"variant\": ");
-    if (!k || !v) continue;
-    const int var = std::atoi(v + 11);
-    if (var >= 0 && var < kSubstepVariants) found = var;  // the last entry wins
+    const char* r = std::strstr(line, "\"bins_per_cutoff\": ");
+    if (!k || !v || !r) continue;
+    const int var = std::atoi(v + 11), reach = std::atoi(r + 19);
+    if (var >= 0 && var < kSubstepVariants && (reach == 1 || reach == 2)) {
+      found.variant = var;  // the last entry wins
+      found.reach = reach;
+    }
   }
   std::fclose(f);
   return found;
 }
 
-void tune_file_store(const std::string& key, int variant, const double* us) {
+void tune_file_store(const std::string& key, const TuneChoice& best, const std::vector<int>& reaches,
+                     const std::vector<std::vector<double>>& us, const std::vector<double>& rebuild_us) {
   const char* path = std::getenv("SEDI_AUTOTUNE_CACHE");
   if (!path || !*path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "{\"key\": \"%s\", \"variant\": %d, \"block\": %d, \"median_us\": [", key.c_str(),
-               variant, substep_block(variant));
-  for (int v = 0; v < kSubstepVariants; ++v) std::fprintf(f, "%s%.3f", v ? ", " : "", us[v]);
+  std::fprintf(f, "{\"key\": \"%s\", \"variant\": %d, \"bins_per_cutoff\": %d, \"block\": %d, \"median_us\": {",
+               key.c_str(), best.variant, best.reach, substep_block(best.variant));
+  for (size_t r = 0; r < reaches.size(); ++r) {
+    std::fprintf(f, "%s\"R%d\": [", r ? ", " : "", reaches[r]);
+    for (int v = 0; v < kSubstepVariants; ++v) std::fprintf(f, "%s%.3f", v ? ", " : "", us[r][v]);
+    std::fprintf(f, "]");
+  }
+  std::fprintf(f, "}, \"rebuild_us\": [");
+  for (size_t r = 0; r < rebuild_us.size(); ++r) std::fprintf(f, "%s%.3f", r ? ", " : "", rebuild_us[r]);
   std::fprintf(f, "]}\n");
   std::fclose(f);
 }
 
-// Choose h->variant for the current particles (no-op when fixed or up to date).
+// Bins of R per cutoff and a rebuild at once; the rebuild counter is left as it was
+// (the tuner's rebuilds are not the run's).
+int retune_bins(sedi_handle* h, int R) {
+  Ctl c;
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(&c, h->st.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  const int64_t rebuilds = c.rebuilds;
+  int rc;
+  if (R != h->P.bin_reach) {
+    clear_graphs(h);  // graphs bake in the bin arrays
+    if ((rc = set_bins(h, R))) return rc;
+  }
+  launch_rebuild_now(h->form, h->st, h->P, h->stream);
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(&c, h->st.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  c.rebuilds = rebuilds;
+  CK(cudaMemcpy(h->st.ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice));
+  return sync_status(h);
+}
+
+// Choose h->variant and the bin size for the current particles (no-op when fixed or
+// up to date).
 int autotune(sedi_handle* h) {
   if (h->prm.substep_variant >= 0 || h->form == FORM_FP64) return 0;
   if (h->P.lift || h->P.lub_tangential) {
@@ -677,87 +761,150 @@ int autotune(sedi_handle* h) {
   if (h->since_set < kTuneAfter) return 0;
   const std::string key = tune_key(h);
   if (key == h->tuned_key) return 0;
-  int best = -1;
+  TuneChoice best;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) best = it->second;
   }
-  if (best < 0) best = tune_file_lookup(key);
-  if (best < 0) {
-    // lists must cover the current positions, exactly as the first substep would see them
-    launch_check(h->st, h->P, 0ull, 0, h->stream);
-    launch_rebuild(h->form, h->st, h->P, 0, false, h->stream);
+  if (best.variant < 0) best = tune_file_lookup(key);
+  if (best.variant < 0) {
+    int rc;
+    Ctl c0;
     CK(cudaStreamSynchronize(h->stream));
-    // the arrays an integrating substep updates in place, and their saved copies
-    Ctl c;
-    CK(cudaMemcpy(&c, h->st.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&c0, h->st.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    const double rate = (double)std::max<int64_t>(c0.rebuilds, 1) / (double)std::max<int64_t>(h->since_set, 1);
+    // R = 2 only while its bins stay few next to the particles (a bin array sweep per
+    // rebuild); a fixed bins_per_cutoff is the only candidate
+    std::vector<int> reaches = {1};
+    if (h->prm.bins_per_cutoff > 0) {
+      reaches = {h->prm.bins_per_cutoff};
+    } else {
+      int32_t nb[3];
+      int64_t nbins = 0;
+      if (!bins_for(h, 2, nb, &nbins) && nbins <= std::max<int64_t>(16 * h->N, (int64_t)1 << 22))
+        reaches.push_back(2);
+    }
+    // the current bin size last, so that a single candidate needs no extra resize
+    if (h->P.bin_reach == 1) std::reverse(reaches.begin(), reaches.end());
+    std::vector<std::vector<double>> med(reaches.size(), std::vector<double>(kSubstepVariants, 1e30));
+    std::vector<double> rebuild_us(reaches.size(), 0.0);
     const int64_t N = h->N, cap = h->P.cap;
     const size_t q = quad_bytes(h->form), fq = fquad_bytes(h->form), w = word_bytes(h->form);
-    struct Item { void* p; size_t n; };
-    const std::vector<Item> live = {
-        {h->st.hist[c.nl], q * cap * N}, {h->st.cmask[c.nl], 4 * (size_t)N},
-        {h->st.acc[c.pb], fq * N}, {h->st.whist[c.pb], (size_t)kWalls * 3 * w * N},
-        {h->st.wmask[c.pb], 4 * (size_t)N}, {h->st.ctl, sizeof(Ctl)}};
-    size_t total = 0;
-    for (const auto& it : live) total += (it.n + 255) & ~(size_t)255;
-    char* save = nullptr;
-    if (cudaMalloc((void**)&save, total) != cudaSuccess) {
-      // no room for the saved copies: keep the current launch shape, do not retry
-      cudaGetLastError();
-      h->tuned_key = key;
-      return 0;
-    }
-    auto copy_all = [&](bool to_save) {
-      size_t off = 0;
-      for (const auto& it : live) {
-        if (to_save) cudaMemcpyAsync(save + off, it.p, it.n, cudaMemcpyDeviceToDevice, h->stream);
-        else cudaMemcpyAsync(it.p, save + off, it.n, cudaMemcpyDeviceToDevice, h->stream);
-        off += (it.n + 255) & ~(size_t)255;
-      }
-    };
-    copy_all(true);
+    cudaEvent_t rb[2];
+    CK(cudaEventCreate(&rb[0]));
+    CK(cudaEventCreate(&rb[1]));
     std::vector<cudaEvent_t> ev(2 * kSubstepVariants * kTuneRounds, nullptr);
     for (auto& e : ev) CK(cudaEventCreate(&e));
-    for (int v = 0; v < kSubstepVariants; ++v) {  // warm-up: first launch of each variant
-      launch_substep(h->form, h->st, h->mesh, h->P, 0, true, v, 0ull, 0, h->stream);
-      copy_all(false);
-    }
-    for (int r = 0; r < kTuneRounds; ++r)
-      for (int v = 0; v < kSubstepVariants; ++v) {
-        cudaEvent_t* e = &ev[2 * (r * kSubstepVariants + v)];
-        CK(cudaEventRecord(e[0], h->stream));
+    rc = 0;
+    for (size_t ri = 0; ri < reaches.size() && !rc; ++ri) {
+      const int R = reaches[ri];
+      // the bins of R and lists built from the current positions (timed)
+      if (R != h->P.bin_reach) {
+        clear_graphs(h);
+        if ((rc = set_bins(h, R))) break;
+      }
+      {
+        Ctl c;
+        CK(cudaMemcpy(&c, h->st.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+        const int64_t rebuilds = c.rebuilds;
+        CK(cudaEventRecord(rb[0], h->stream));
+        launch_rebuild_now(h->form, h->st, h->P, h->stream);
+        CK(cudaEventRecord(rb[1], h->stream));
+        if ((rc = sync_status(h))) break;
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, rb[0], rb[1]) == cudaSuccess) rebuild_us[ri] = 1e3 * ms;
+        CK(cudaMemcpy(&c, h->st.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+        c.rebuilds = rebuilds;
+        CK(cudaMemcpy(h->st.ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice));
+      }
+      // the arrays an integrating substep updates in place, and their saved copies
+      Ctl c;
+      CK(cudaMemcpy(&c, h->st.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+      struct Item { void* p; size_t n; };
+      const std::vector<Item> live = {
+          {h->st.hist[c.nl], q * cap * N}, {h->st.cmask[c.nl], 4 * (size_t)N},
+          {h->st.acc[c.pb], fq * N}, {h->st.whist[c.pb], (size_t)kWalls * 3 * w * N},
+          {h->st.wmask[c.pb], 4 * (size_t)N}, {h->st.ctl, sizeof(Ctl)}};
+      size_t total = 0;
+      for (const auto& it : live) total += (it.n + 255) & ~(size_t)255;
+      char* save = nullptr;
+      if (cudaMalloc((void**)&save, total) != cudaSuccess) {
+        // no room for the saved copies: keep this bin size and the current launch shape
+        cudaGetLastError();
+        best.variant = h->variant;
+        best.reach = R;
+        reaches.resize(ri + 1);
+        med.resize(ri + 1);
+        rebuild_us.resize(ri + 1);
+        med[ri].assign(kSubstepVariants, 1e30);
+        med[ri][h->variant] = 0.0;
+        break;
+      }
+      auto copy_all = [&](bool to_save) {
+        size_t off = 0;
+        for (const auto& it : live) {
+          if (to_save) cudaMemcpyAsync(save + off, it.p, it.n, cudaMemcpyDeviceToDevice, h->stream);
+          else cudaMemcpyAsync(it.p, save + off, it.n, cudaMemcpyDeviceToDevice, h->stream);
+          off += (it.n + 255) & ~(size_t)255;
+        }
+      };
+      copy_all(true);
+      for (int v = 0; v < kSubstepVariants; ++v) {  // warm-up: first launch of each variant
         launch_substep(h->form, h->st, h->mesh, h->P, 0, true, v, 0ull, 0, h->stream);
-        CK(cudaEventRecord(e[1], h->stream));
         copy_all(false);
       }
-    int rc = sync_status(h);
-    cudaFree(save);
-    double med[kSubstepVariants];
-    for (int v = 0; v < kSubstepVariants && !rc; ++v) {
-      std::vector<double> t;
-      for (int r = 0; r < kTuneRounds; ++r) {
-        float ms = 0.0f;
-        cudaEvent_t* e = &ev[2 * (r * kSubstepVariants + v)];
-        if (cudaEventElapsedTime(&ms, e[0], e[1]) != cudaSuccess) ms = 1e30f;
-        t.push_back(1e3 * ms);
+      for (int r = 0; r < kTuneRounds; ++r)
+        for (int v = 0; v < kSubstepVariants; ++v) {
+          cudaEvent_t* e = &ev[2 * (r * kSubstepVariants + v)];
+          CK(cudaEventRecord(e[0], h->stream));
+          launch_substep(h->form, h->st, h->mesh, h->P, 0, true, v, 0ull, 0, h->stream);
+          CK(cudaEventRecord(e[1], h->stream));
+          copy_all(false);
+        }
+      rc = sync_status(h);
+      cudaFree(save);
+      for (int v = 0; v < kSubstepVariants && !rc; ++v) {
+        std::vector<double> t;
+        for (int r = 0; r < kTuneRounds; ++r) {
+          float ms = 0.0f;
+          cudaEvent_t* e = &ev[2 * (r * kSubstepVariants + v)];
+          if (cudaEventElapsedTime(&ms, e[0], e[1]) != cudaSuccess) ms = 1e30f;
+          t.push_back(1e3 * ms);
+        }
+        std::sort(t.begin(), t.end());
+        med[ri][v] = t[kTuneRounds / 2];
       }
-      std::sort(t.begin(), t.end());
-      med[v] = t[kTuneRounds / 2];
-      if (best < 0 || med[v] < med[best]) best = v;
     }
     for (auto& e : ev) cudaEventDestroy(e);
+    cudaEventDestroy(rb[0]);
+    cudaEventDestroy(rb[1]);
     if (rc) return rc;
-    tune_file_store(key, best, med);
+    double best_cost = 1e300;
+    for (size_t ri = 0; ri < reaches.size(); ++ri)
+      for (int v = 0; v < kSubstepVariants; ++v) {
+        const double cost = med[ri][v] + rebuild_us[ri] * rate;
+        if (cost < best_cost) {
+          best_cost = cost;
+          best.variant = v;
+          best.reach = reaches[ri];
+        }
+      }
+    tune_file_store(key, best, reaches, med, rebuild_us);
   }
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = best;
   }
-  if (best != h->variant) clear_graphs(h);  // graphs bake in the launch shape
+  // the chosen bins (lists rebuilt at once when they change)
+  if (best.reach != h->P.bin_reach) {
+    const int rc = retune_bins(h, best.reach);
+    if (rc) return rc;
+  }
+  if (best.variant != h->variant) clear_graphs(h);  // graphs bake in the launch shape
   // leaving the pair mode: the other variants read the partner copies of the springs
-  if (h->variant == SUBSTEP_PAIRS && best != SUBSTEP_PAIRS) launch_spring_sync(h->form, h->st, h->stream);
-  h->variant = best;
+  if (h->variant == SUBSTEP_PAIRS && best.variant != SUBSTEP_PAIRS) launch_spring_sync(h->form, h->st, h->stream);
+  h->variant = best.variant;
   h->tuned_key = key;
   return 0;
 }
@@ -905,6 +1052,7 @@ void sedi_destroy(sedi_handle* h) {
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->avg_ev) cudaEventDestroy(e);
   free_list(h->part_allocs);
+  free_list(h->bin_allocs);
   free_list(h->mesh_allocs);
   if (h->dstage) cudaFree(h->dstage);
   for (void* p : {(void*)h->cnn_master, (void*)h->cnn_m, (void*)h->cnn_v, (void*)h->cnn_grad,
@@ -1257,6 +1405,7 @@ static int ens_finalize(sedi_handle* h) {
   CK(cudaMemcpy(h->ens_views, v.data(), sizeof(BedView) * B, cudaMemcpyHostToDevice));
   h->ens.views = h->ens_views;
   h->ens.B = B;
+  h->ens.variant = h->ens_variant;
   h->ens.max_n = max_n;
   h->ens.max_bins = max_bins;
   h->ens.max_cells = max_c;
@@ -1286,6 +1435,206 @@ static int ens_status(sedi_handle* h) {
     if (c[b].error == SEDI_ENONFINITE) return fail(h, SEDI_ENONFINITE, "bed %d: non-finite force or state", b);
     if (c[b].error) return fail(h, c[b].error, "bed %d: device error %d", b, c[b].error);
   }
+  return 0;
+}
+
+// Ensembles: the launch shape of the batched substep (kEnsVariant) and the bins of
+// every bed (R per list cutoff), tuned as for a single bed.  For each R every bed's
+// bins are resized and all lists rebuilt at once (the batched rebuild, timed), then
+// one batched substep of every shape is timed in interleaved rounds, the arrays it
+// updates in place put back after each; cost = median substep + rebuild time x the
+// largest rebuild rate of a bed.  No choice changes a result (lists in caller-index
+// order, the same terms in the same order in every shape), so every bed keeps the bits
+// it has alone.  Keyed by (GPU, beds, particles, diameter range, form, terms).
+static int ens_autotune(sedi_handle* h) {
+  if (h->prm.substep_variant >= 0 || h->form == FORM_FP64 || ens_ext(h)) return 0;
+  const int B = (int)h->beds.size();
+  int64_t since = INT64_MAX, ntot = 0, nmin = INT64_MAX, nmax = 0;
+  double dmin = 1e300, dmax = 0.0;
+  for (sedi_handle* b : h->beds) {
+    since = std::min(since, b->since_set);
+    ntot += b->N;
+    nmin = std::min(nmin, b->N);
+    nmax = std::max(nmax, b->N);
+    for (double d : b->d_host) {
+      dmin = std::min(dmin, d);
+      dmax = std::max(dmax, d);
+    }
+  }
+  if (since < kTuneAfter) return 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) std::snprintf(prop.name, sizeof(prop.name), "device%d", dev);
+  char buf[512];
+  std::snprintf(buf, sizeof(buf), "%s sm%d|ensemble B=%d|N=%lld (%lld..%lld)|d=%.3e..%.3e|form=%d|law=%d|lub=%d|fluid=%d%d%d",
+                prop.name, prop.multiProcessorCount, B, (long long)ntot, (long long)nmin, (long long)nmax, dmin,
+                dmax, h->form, h->prm.contact_law, h->P.lubrication, h->P.drag, h->P.pressure_grad,
+                h->P.added_mass);
+  const std::string key = buf;
+  if (key == h->tuned_key) return 0;
+  int rc = ens_finalize(h);
+  if (rc) return rc;
+  TuneChoice best;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) best = it->second;
+  }
+  if (best.variant < 0) best = tune_file_lookup(key);
+  // the rebuild counters as they stand (the tuner's rebuilds are not the run's)
+  std::vector<Ctl> c(B);
+  launch_ctl_gather_ens(h->ens, h->ens_ctl, h->stream);
+  CK(cudaMemcpyAsync(c.data(), h->ens_ctl, sizeof(Ctl) * B, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  std::vector<int64_t> rebuilds(B);
+  double rate = 0.0;
+  for (int b = 0; b < B; ++b) {
+    rebuilds[b] = c[b].rebuilds;
+    rate = std::max(rate, (double)std::max<int64_t>(c[b].rebuilds, 1) / (double)std::max<int64_t>(h->beds[b]->since_set, 1));
+  }
+  int64_t* rb_dev = nullptr;
+  CK(cudaMalloc((void**)&rb_dev, 8 * B));
+  CK(cudaMemcpy(rb_dev, rebuilds.data(), 8 * B, cudaMemcpyHostToDevice));
+  // every bed on bins of R, rebuilt now; returns the rebuild time (us)
+  auto bins_and_rebuild = [&](int R, double* us) -> int {
+    bool changed = false;
+    for (sedi_handle* b : h->beds)
+      if (b->P.bin_reach != R) {
+        int r2 = set_bins(b, R);
+        if (r2) return fail(h, r2, "bed bins: %s", b->err.c_str());
+        changed = true;
+      }
+    if (changed) {
+      h->ens_dirty = true;
+      int r2 = ens_finalize(h);
+      if (r2) return r2;
+    }
+    cudaEvent_t e0 = new_event(), e1 = new_event();
+    launch_force_need_ens(h->ens, h->stream);
+    CK(cudaEventRecord(e0, h->stream));
+    launch_rebuild_ens(h->form, h->ens, 0, h->stream);
+    CK(cudaEventRecord(e1, h->stream));
+    launch_set_rebuilds_ens(h->ens, rb_dev, h->stream);
+    int r2 = ens_status(h);
+    float ms = 0.0f;
+    if (us) *us = cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess ? 1e3 * ms : 0.0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return r2;
+  };
+  if (best.variant < 0) {
+    std::vector<int> reaches = {1};
+    bool two = h->prm.bins_per_cutoff == 0;
+    for (sedi_handle* b : h->beds) {
+      int32_t nb[3];
+      int64_t nbins = 0;
+      if (bins_for(b, 2, nb, &nbins) || nbins > std::max<int64_t>(16 * b->N, (int64_t)1 << 16)) two = false;
+    }
+    if (two) reaches.push_back(2);
+    if (h->prm.bins_per_cutoff > 0) reaches = {h->prm.bins_per_cutoff};
+    if (h->beds[0]->P.bin_reach == 1) std::reverse(reaches.begin(), reaches.end());
+    std::vector<std::vector<double>> med(reaches.size(), std::vector<double>(kSubstepVariants, 1e30));
+    std::vector<double> rebuild_us(reaches.size(), 0.0);
+    std::vector<cudaEvent_t> ev(2 * kEnsVariants * kTuneRounds, nullptr);
+    for (auto& e : ev) e = new_event();
+    for (size_t ri = 0; ri < reaches.size() && !rc; ++ri) {
+      if ((rc = bins_and_rebuild(reaches[ri], &rebuild_us[ri]))) break;
+      launch_ctl_gather_ens(h->ens, h->ens_ctl, h->stream);
+      CK(cudaMemcpyAsync(c.data(), h->ens_ctl, sizeof(Ctl) * B, cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      // the arrays a substep updates in place, of every bed, and their saved copies
+      struct Item { void* p; size_t n; };
+      std::vector<Item> live;
+      for (int b = 0; b < B; ++b) {
+        sedi_handle* sb = h->beds[b];
+        const int64_t N = sb->N, cap = sb->P.cap;
+        const size_t q = quad_bytes(sb->form), fq = fquad_bytes(sb->form), w = word_bytes(sb->form);
+        live.push_back({sb->st.hist[c[b].nl], q * cap * N});
+        live.push_back({sb->st.cmask[c[b].nl], 4 * (size_t)N});
+        live.push_back({sb->st.acc[c[b].pb], fq * N});
+        live.push_back({sb->st.whist[c[b].pb], (size_t)kWalls * 3 * w * N});
+        live.push_back({sb->st.wmask[c[b].pb], 4 * (size_t)N});
+        live.push_back({sb->st.ctl, sizeof(Ctl)});
+      }
+      size_t total = 0;
+      for (const auto& it : live) total += (it.n + 255) & ~(size_t)255;
+      char* save = nullptr;
+      if (cudaMalloc((void**)&save, total) != cudaSuccess) {
+        cudaGetLastError();
+        best.variant = h->ens_variant;
+        best.reach = reaches[ri];
+        reaches.resize(ri + 1);
+        med.resize(ri + 1);
+        rebuild_us.resize(ri + 1);
+        med[ri].assign(kSubstepVariants, 1e30);
+        med[ri][h->ens_variant] = 0.0;
+        break;
+      }
+      auto copy_all = [&](bool to_save) {
+        size_t off = 0;
+        for (const auto& it : live) {
+          if (to_save) cudaMemcpyAsync(save + off, it.p, it.n, cudaMemcpyDeviceToDevice, h->stream);
+          else cudaMemcpyAsync(it.p, save + off, it.n, cudaMemcpyDeviceToDevice, h->stream);
+          off += (it.n + 255) & ~(size_t)255;
+        }
+      };
+      copy_all(true);
+      EnsLaunch e = h->ens;
+      for (int v = 0; v < kEnsVariants; ++v) {  // warm-up
+        e.variant = kEnsVariant[v];
+        launch_substep_ens(h->form, e, false, 0, 0ull, 0, h->stream);
+        copy_all(false);
+      }
+      for (int r = 0; r < kTuneRounds; ++r)
+        for (int v = 0; v < kEnsVariants; ++v) {
+          cudaEvent_t* ee = &ev[2 * (r * kEnsVariants + v)];
+          e.variant = kEnsVariant[v];
+          CK(cudaEventRecord(ee[0], h->stream));
+          launch_substep_ens(h->form, e, false, 0, 0ull, 0, h->stream);
+          CK(cudaEventRecord(ee[1], h->stream));
+          copy_all(false);
+        }
+      rc = ens_status(h);
+      cudaFree(save);
+      for (int v = 0; v < kEnsVariants && !rc; ++v) {
+        std::vector<double> t;
+        for (int r = 0; r < kTuneRounds; ++r) {
+          float ms = 0.0f;
+          cudaEvent_t* ee = &ev[2 * (r * kEnsVariants + v)];
+          if (cudaEventElapsedTime(&ms, ee[0], ee[1]) != cudaSuccess) ms = 1e30f;
+          t.push_back(1e3 * ms);
+        }
+        std::sort(t.begin(), t.end());
+        med[ri][kEnsVariant[v]] = t[kTuneRounds / 2];
+      }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (!rc) {
+      double best_cost = 1e300;
+      for (size_t ri = 0; ri < reaches.size(); ++ri)
+        for (int v = 0; v < kEnsVariants; ++v) {
+          const double cost = med[ri][kEnsVariant[v]] + rebuild_us[ri] * rate;
+          if (cost < best_cost) {
+            best_cost = cost;
+            best.variant = kEnsVariant[v];
+            best.reach = reaches[ri];
+          }
+        }
+      tune_file_store(key, best, reaches, med, rebuild_us);
+    }
+  }
+  if (!rc && h->beds[0]->P.bin_reach != best.reach) rc = bins_and_rebuild(best.reach, nullptr);
+  cudaFree(rb_dev);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  if (best.variant != h->ens_variant) clear_graphs(h);  // graphs bake in the launch shape
+  h->ens_variant = best.variant;
+  h->ens.variant = best.variant;
+  h->tuned_key = key;
   return 0;
 }
 
@@ -1332,6 +1681,7 @@ static int build_graph_ens(sedi_handle* h, int n, cudaGraphExec_t* out) {
 static int ens_step(sedi_handle* h, int n) {
   int rc = ens_finalize(h);
   if (rc) return rc;
+  if ((rc = ens_autotune(h))) return rc;
   if (h->prm.profile) {
     harvest(h);
     if (h->avg_ev.empty())
@@ -1362,7 +1712,10 @@ static int ens_step(sedi_handle* h, int n) {
   }
   CK(cudaGetLastError());
   h->stats.substeps += n;
-  for (sedi_handle* b : h->beds) b->stats.substeps += n;
+  for (sedi_handle* b : h->beds) {
+    b->stats.substeps += n;
+    b->since_set += n;
+  }
   h->ens_fresh = false;
   return 0;
 }
@@ -1858,7 +2211,8 @@ int64_t sedi_get_contacts(sedi_handle* h, int32_t bed, int64_t cap, int64_t* ij,
 namespace {
 struct CkHeader {
   char magic[8];
-  int32_t version, form, cap, pad;
+  int32_t version, form, cap;
+  int32_t bins_per_cutoff;  // R of the stored order (0 in older files: 1)
   int64_t N, C, nbins;
   sedi_stats stats;
 };
@@ -1924,6 +2278,7 @@ static int save_to(sedi_handle* h, FILE* f) {
   hd.N = h->N;
   hd.C = h->P.C;
   hd.nbins = h->P.nbins;
+  hd.bins_per_cutoff = h->P.bin_reach;
   hd.stats = h->stats;
   rc = ck_write(f, &hd, sizeof(hd)) ? fail(h, SEDI_EIO, "write failed") : 0;
   if (!rc) rc = ck_write(f, h->d_host.data(), 8 * h->N) || ck_write(f, h->rho_host.data(), 8 * h->N) ? fail(h, SEDI_EIO, "write failed") : 0;
@@ -1976,6 +2331,9 @@ static int load_from(sedi_handle* h, FILE* f) {
     h->P.cap = hd.cap;
     h->have_particles = false;
     rc = alloc_particles(h, hd.N, rmax);
+    // the stored order and lists follow the stored bins
+    const int R = hd.bins_per_cutoff > 0 ? hd.bins_per_cutoff : 1;
+    if (!rc && R != h->P.bin_reach) rc = set_bins(h, R);
     if (!rc && h->P.nbins != hd.nbins) rc = fail(h, SEDI_EINVAL, "checkpoint binning differs");
   }
   if (!rc) {
@@ -2193,8 +2551,9 @@ int sedi_get_stats(sedi_handle* h, sedi_stats* out) {
       st.max_neighbors = std::max(st.max_neighbors, b->stats.max_neighbors);
     }
     st.nbr_capacity = h->P.cap;
-    st.substep_variant = SUBSTEP_B128_LOOP;
-    st.substep_block = 128;
+    st.substep_variant = h->ens_variant;
+    st.substep_block = substep_block(h->ens_variant);
+    st.bins_per_cutoff = h->beds[0]->P.bin_reach > 0 ? h->beds[0]->P.bin_reach : 1;
     *out = st;
     return rc;
   }
@@ -2203,6 +2562,7 @@ int sedi_get_stats(sedi_handle* h, sedi_stats* out) {
   const bool tuned = h->prm.substep_variant >= 0 || h->form == FORM_FP64 || !h->tuned_key.empty();
   h->stats.substep_variant = tuned ? h->variant : -1;
   h->stats.substep_block = tuned ? substep_block(h->variant) : 0;
+  h->stats.bins_per_cutoff = h->P.bin_reach > 0 ? h->P.bin_reach : 1;
   *out = h->stats;
   return rc;
 }

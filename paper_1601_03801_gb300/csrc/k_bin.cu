@@ -7,11 +7,14 @@
 //   scatter  : particle -> slot of its bin; per-bin sort by caller index makes the
 //              order deterministic
 //   gather   : permute every per-particle array into the other buffer
-//   build    : one thread per particle scans the 27 surrounding bins; FP32 test
-//              with a relative margin, exact FP64 predicate
+//   build    : one thread per particle scans the (2R + 1)^3 surrounding bins (R bins
+//              per list cutoff, 1 or 2); FP32 test with a relative margin, exact FP64
+//              predicate
 //                 d2 = (dx*dx + dy*dy) + dz*dz  <  ((r_i + r_j)(1 + f) + skin)^2
 //              (no fused multiply-add) only when the FP32 test is inconclusive,
-//              so lists are bit-identical to an FP64 evaluation of the predicate
+//              so lists are bit-identical to an FP64 evaluation of the predicate;
+//              each list holds its partners in caller-index order, so neither the bin
+//              size nor the bin order changes a list (nor any sum over one)
 //   remap    : every new (i, k) entry looks its partner's caller index up in the
 //              particle's old list and carries the tangential spring over
 //   flip     : switch buffers, reset the displacement
@@ -62,9 +65,9 @@ __device__ __forceinline__ int bin_axis(S x, const DevParams& P, int a) {
 }
 
 // Storage order of the bins: x fastest, then y, then z.  (Measured against z fastest,
-// which keeps a thin bed's partners closer in memory: the same for the pair list,
-// slower for the per-particle loop.)  The order changes no list: slots are appended
-// bin by bin in a fixed (oz, oy, ox) sequence and by caller index inside a bin.
+// which keeps a thin bed's partners closer in memory: 2% faster for the pair list on
+// the 10M bed, 7% slower for the per-particle loop.)  The order changes no list:
+// every list is sorted by caller index.
 __device__ __forceinline__ int64_t bin_key(int bx, int by, int bz, const DevParams& P) {
   return ((int64_t)bz * P.nb[1] + by) * P.nb[0] + bx;
 }
@@ -282,16 +285,20 @@ __device__ __forceinline__ void build_body(const DevState& st, const DevParams& 
     const int32_t ui = uid[i];
     const float rif = (float)ri;
     int c[3] = {bin_axis<S>(pi.a, P, 0), bin_axis<S>(pi.b, P, 1), bin_axis<S>(pi.c, P, 2)};
+    // the partners found so far, ordered by caller index (insertion), so the list
+    // order does not depend on the bins
+    int32_t ent[kMaxCap], key[kMaxCap];
     int n = 0;
-    for (int oz = -1; oz <= 1; ++oz) {
+    const int R = P.bin_reach;
+    for (int oz = -R; oz <= R; ++oz) {
       int tz = c[2] + oz;
       if (P.periodic[2]) tz = (tz + P.nb[2]) % P.nb[2];
       else if (tz < 0 || tz >= P.nb[2]) continue;
-      for (int oy = -1; oy <= 1; ++oy) {
+      for (int oy = -R; oy <= R; ++oy) {
         int ty = c[1] + oy;
         if (P.periodic[1]) ty = (ty + P.nb[1]) % P.nb[1];
         else if (ty < 0 || ty >= P.nb[1]) continue;
-        for (int ox = -1; ox <= 1; ++ox) {
+        for (int ox = -R; ox <= R; ++ox) {
           int tx = c[0] + ox;
           if (P.periodic[0]) tx = (tx + P.nb[0]) % P.nb[0];
           else if (tx < 0 || tx >= P.nb[0]) continue;
@@ -321,14 +328,26 @@ __device__ __forceinline__ void build_body(const DevState& st, const DevParams& 
               in = listed_exact(xi, xj, ri, rj, P);
             }
             if (in) {
-              if (n < P.cap) nbr[(int64_t)n * N + i] = j | (ui < uid[j] ? (int32_t)kFirstBit : 0);
+              if (n < P.cap) {
+                const int32_t uj = uid[j];
+                int k = n;
+                while (k > 0 && key[k - 1] > uj) {
+                  key[k] = key[k - 1];
+                  ent[k] = ent[k - 1];
+                  --k;
+                }
+                key[k] = uj;
+                ent[k] = j | (ui < uj ? (int32_t)kFirstBit : 0);
+              }
               ++n;
             }
           }
         }
       }
     }
-    st.nn[ql][i] = n < P.cap ? n : P.cap;
+    const int nk = n < P.cap ? n : P.cap;
+    for (int k = 0; k < nk; ++k) nbr[(int64_t)k * N + i] = ent[k];
+    st.nn[ql][i] = nk;
     atomicMax(&st.ctl->max_nn, n);
     if (n > P.cap) {
       atomicMax(&st.ctl->overflow_nn, n);
@@ -587,6 +606,17 @@ __global__ void k_ctl_gather_e(const BedView* v, int B, Ctl* out) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) out[b] = *v[b].st.ctl;
 }
 
+// every bed: rebuild at the next rebuild launch; and each bed's rebuild counter set
+// (from / to a host-side table, so that the autotuner's rebuilds are not counted)
+__global__ void k_force_need_e(const BedView* v, int B) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x)
+    v[b].st.ctl->need_rebuild = 1;
+}
+__global__ void k_set_rebuilds_e(const BedView* v, int B, const int64_t* rebuilds) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x)
+    v[b].st.ctl->rebuilds = rebuilds[b];
+}
+
 __global__ void k_advance_e(const BedView* v, int B, int n) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
     Ctl* c = v[b].st.ctl;
@@ -660,6 +690,11 @@ void launch_rebuild(int form, const DevState& st, const DevParams& P, int sub_of
   }
 }
 
+void launch_rebuild_now(int form, const DevState& st, const DevParams& P, cudaStream_t s) {
+  k_force_need<<<1, 1, 0, s>>>(st.ctl);
+  launch_rebuild(form, st, P, 0, false, s);
+}
+
 void launch_pair_list(const DevState& st, const DevParams& P, cudaStream_t s) {
   if (!st.pairs) return;
   k_pair_reset<<<1, 1, 0, s>>>(st, true);
@@ -698,6 +733,14 @@ void launch_rebuild_ens(int form, const EnsLaunch& e, int sub_off, cudaStream_t 
 
 void launch_ctl_gather_ens(const EnsLaunch& e, Ctl* out, cudaStream_t s) {
   k_ctl_gather_e<<<(e.B + 127) / 128, 128, 0, s>>>(e.views, e.B, out);
+}
+
+void launch_force_need_ens(const EnsLaunch& e, cudaStream_t s) {
+  k_force_need_e<<<(e.B + 127) / 128, 128, 0, s>>>(e.views, e.B);
+}
+
+void launch_set_rebuilds_ens(const EnsLaunch& e, const int64_t* rebuilds, cudaStream_t s) {
+  k_set_rebuilds_e<<<(e.B + 127) / 128, 128, 0, s>>>(e.views, e.B, rebuilds);
 }
 
 void launch_advance_ens(const EnsLaunch& e, int n, cudaStream_t s) {

@@ -789,7 +789,7 @@ __global__ void __launch_bounds__(BS, MINB) k_substep(DevState st, DevMesh mesh,
 
 // Ensemble: blockIdx.y is the bed, blockIdx.x the block within it (blocks past the
 // bed's particles return at once).
-template <int FORM, int BS, int MINB, bool EXT>
+template <int FORM, int BS, int MINB, bool COOP, bool EXT>
 __global__ void __launch_bounds__(BS, MINB) k_substep_e(const BedView* v, int nbeds, Ctl* ectl,
                                                            int sub_off, cudaGraphConditionalHandle next,
                                                            int use_cond) {
@@ -797,8 +797,8 @@ __global__ void __launch_bounds__(BS, MINB) k_substep_e(const BedView* v, int nb
   const unsigned nblk = (unsigned)((N + BS - 1) / BS);
   if (blockIdx.x >= nblk) return;
   const BedView& b = bed_view(v);
-  substep_body<FORM, true, BS, false, EXT>(b.st, b.mesh, b.P, sub_off, next, use_cond, blockIdx.x,
-                                           nblk, ectl, nbeds);
+  substep_body<FORM, true, BS, COOP, EXT>(b.st, b.mesh, b.P, sub_off, next, use_cond, blockIdx.x,
+                                          nblk, ectl, nbeds);
 }
 
 template <int FORM, int BS, int MINB, bool COOP, bool EXT = false>
@@ -879,22 +879,40 @@ void launch_substep(int form, const DevState& st, const DevMesh& mesh, const Dev
 }
 
 
-template <bool EXT>
-static void launch_ens(int form, const EnsLaunch& e, int sub_off, unsigned long long next_cond,
-                       int use_cond, cudaStream_t s) {
-  const dim3 grid((unsigned)((e.max_n + 127) / 128), (unsigned)e.B);
+template <int FORM, int BS, int MINB, bool COOP, bool EXT>
+static void launch_ens_shape(const EnsLaunch& e, int sub_off, unsigned long long next_cond, int use_cond,
+                             cudaStream_t s) {
+  const dim3 grid((unsigned)((e.max_n + BS - 1) / BS), (unsigned)e.B);
   const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)next_cond;
-  switch (form) {
-    case FORM_SPLIT: k_substep_e<FORM_SPLIT, 128, 6, EXT><<<grid, 128, 0, s>>>(e.views, e.B, e.ectl, sub_off, h, use_cond); break;
-    case FORM_PLAIN: k_substep_e<FORM_PLAIN, 128, 6, EXT><<<grid, 128, 0, s>>>(e.views, e.B, e.ectl, sub_off, h, use_cond); break;
-    default: k_substep_e<FORM_FP64, 128, 6, EXT><<<grid, 128, 0, s>>>(e.views, e.B, e.ectl, sub_off, h, use_cond); break;
+  k_substep_e<FORM, BS, MINB, COOP, EXT><<<grid, BS, 0, s>>>(e.views, e.B, e.ectl, sub_off, h, use_cond);
+}
+
+template <int FORM>
+static void launch_ens(const EnsLaunch& e, bool ext, int sub_off, unsigned long long next_cond, int use_cond,
+                       cudaStream_t s) {
+  // the optional terms and the parity form: the per-particle loop at 128 x 6
+  if (ext) {
+    launch_ens_shape<FORM, 128, 6, false, true>(e, sub_off, next_cond, use_cond, s);
+    return;
   }
+  if constexpr (FORM != FORM_FP64) {
+    switch (e.variant) {
+      case SUBSTEP_B64_LOOP: launch_ens_shape<FORM, 64, 12, false, false>(e, sub_off, next_cond, use_cond, s); return;
+      case SUBSTEP_B128_OCC8_LOOP: launch_ens_shape<FORM, 128, 8, false, false>(e, sub_off, next_cond, use_cond, s); return;
+      case SUBSTEP_B128: launch_ens_shape<FORM, 128, 6, true, false>(e, sub_off, next_cond, use_cond, s); return;
+      default: break;
+    }
+  }
+  launch_ens_shape<FORM, 128, 6, false, false>(e, sub_off, next_cond, use_cond, s);
 }
 
 void launch_substep_ens(int form, const EnsLaunch& e, bool ext, int sub_off,
                         unsigned long long next_cond, int use_cond, cudaStream_t s) {
-  if (ext) launch_ens<true>(form, e, sub_off, next_cond, use_cond, s);
-  else launch_ens<false>(form, e, sub_off, next_cond, use_cond, s);
+  switch (form) {
+    case FORM_SPLIT: launch_ens<FORM_SPLIT>(e, ext, sub_off, next_cond, use_cond, s); break;
+    case FORM_PLAIN: launch_ens<FORM_PLAIN>(e, ext, sub_off, next_cond, use_cond, s); break;
+    default: launch_ens<FORM_FP64>(e, ext, sub_off, next_cond, use_cond, s); break;
+  }
 }
 
 }  // namespace sedi

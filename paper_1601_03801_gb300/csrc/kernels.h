@@ -25,6 +25,11 @@ enum SubstepVariant {
   SUBSTEP_PAIRS = 8
 };
 constexpr int kSubstepVariants = 9;
+// launch shapes of the batched ensemble substep (every bed with the per-particle pair
+// phase; the pair list is a single-bed mode)
+constexpr int kEnsVariants = 4;
+constexpr int kEnsVariant[kEnsVariants] = {SUBSTEP_B128_LOOP, SUBSTEP_B64_LOOP, SUBSTEP_B128_OCC8_LOOP,
+                                           SUBSTEP_B128};
 inline int substep_block(int variant) {
   return (variant == SUBSTEP_B64 || variant == SUBSTEP_B64_LOOP) ? 64 : variant == SUBSTEP_B256 ? 256 : 128;
 }
@@ -41,6 +46,9 @@ void launch_substep(int form, const DevState& st, const DevMesh& mesh, const Dev
 // unless ctl->need_rebuild is set.  sub_off: substep offset of the state buffer.
 void launch_rebuild(int form, const DevState& st, const DevParams& P, int sub_off, bool force,
                     cudaStream_t s);
+// A rebuild now (not forced by new particles): lists from the current positions, the
+// springs carried over, as at a rebuild due to motion.
+void launch_rebuild_now(int form, const DevState& st, const DevParams& P, cudaStream_t s);
 // Set ctl->need_rebuild from the displacement; optionally a graph conditional.
 void launch_check(const DevState& st, const DevParams& P, unsigned long long cond_handle,
                   int use_cond, cudaStream_t s);
@@ -51,6 +59,7 @@ void launch_advance_parity(const DevState& st, int n, cudaStream_t s);
 struct EnsLaunch {
   const BedView* views;  // [B] device table
   int32_t B;
+  int32_t variant;       // substep launch shape (one of kEnsVariants; the autotuner's)
   int64_t max_n;         // largest bed (particles)
   int64_t max_bins;      // largest bin grid
   int64_t max_cells;     // largest mesh
@@ -60,6 +69,10 @@ void launch_check_ens(const EnsLaunch& e, unsigned long long cond_handle, int us
                       cudaStream_t s);
 void launch_rebuild_ens(int form, const EnsLaunch& e, int sub_off, cudaStream_t s);
 void launch_advance_ens(const EnsLaunch& e, int n, cudaStream_t s);
+// every bed rebuilds at the next launch_rebuild_ens (autotuner)
+void launch_force_need_ens(const EnsLaunch& e, cudaStream_t s);
+// every bed's rebuild counter from rebuilds[B] (device)
+void launch_set_rebuilds_ens(const EnsLaunch& e, const int64_t* rebuilds, cudaStream_t s);
 void launch_ctl_gather_ens(const EnsLaunch& e, Ctl* out, cudaStream_t s);
 // ext: the beds run the optional terms (lift, tangential lubrication)
 void launch_substep_ens(int form, const EnsLaunch& e, bool ext, int sub_off,

@@ -168,3 +168,25 @@ def test_ensemble_beds_match_oracle(ens, b):
     eg = E.average(bed=b)[0]
     eo = o.average()[0]
     assert np.abs(eg - eo).max() <= 1e-6 * np.abs(eo).max()
+
+
+def test_tuned_ensemble_keeps_each_bed_bits(ens):
+    """After 200 substeps the ensemble times its launch shapes and bin sizes (every bed
+    on the same choice) and keeps the cheapest; every bed still gets the bits it gets
+    alone on a fixed shape and bins of one cutoff."""
+    prm, beds = ens
+    idx = [0, 1, 2]
+    g = make_ensemble(prm, [beds[b] for b in idx])
+    g.step(200)
+    assert g.stats()["bins_per_cutoff"] == 1
+    g.step(20)
+    st = g.stats()
+    assert st["substep_variant"] in (5, 7, 6, 0) and st["bins_per_cutoff"] in (1, 2)
+    got = [g.get_particles(bed=b) for b in range(len(idx))]
+    for k, b in enumerate(idx):
+        s = make_single(prm, beds[b], substep_variant=5, bins_per_cutoff=1)
+        s.step(200)
+        s.step(20)
+        for a, c in zip(got[k], s.get_particles()):
+            assert np.array_equal(a, c), b
+

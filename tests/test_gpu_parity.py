@@ -387,6 +387,25 @@ def test_substep_variants_bit_identical(small, form):
                 assert np.abs(a - b).max() <= 1e-5 * max(np.abs(a).max(), 1e-30), variant
 
 
+@pytest.mark.parametrize("variant", [5, 8])
+def test_bins_per_cutoff_change_no_result(small, variant):
+    """Bins of one list cutoff (27-bin stencil) or of half a cutoff (125 bins): every
+    list holds its partners in caller-index order, so lists, springs, trajectory and
+    averaging are the same bits."""
+    prm, parts = small
+    out = []
+    for R in (1, 2):
+        g = sedi.Sedi(dict(prm, precision_form="split", substep_variant=variant, bins_per_cutoff=R))
+        g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+        g.step(60)
+        eps, _, F = g.average()
+        assert g.stats()["bins_per_cutoff"] == R
+        out.append((*g.get_particles(), eps, F, *g.neighbors(), *g.contacts()))
+    assert len(out[0][-2]) > 10
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
 def test_pair_list_contacts_match_loop(small):
     # the pair list keeps each spring in the first particle's slot; the contact
     # export copies it to the partner's slot first, so both runs export the same
@@ -420,17 +439,20 @@ def test_autotuner_chooses_and_caches(small, tmp_path, monkeypatch):
     g.step(10)
     st = g.stats()
     assert 0 <= st["substep_variant"] < 9 and st["substep_block"] in (64, 128, 256)
+    assert st["bins_per_cutoff"] in (1, 2)
     lines = cache.read_text().splitlines()
     assert len(lines) == 1 and f"N={n}|" in lines[0] and '"median_us"' in lines[0]
+    assert f'"bins_per_cutoff": {st["bins_per_cutoff"]}' in lines[0] and '"R2"' in lines[0]
     # a second handle on the same workload takes the cached choice without re-timing
     h = sedi.Sedi(dict(prm, precision_form="split"))
     h.set_particles(sub["x"], sub["v"], sub["w"], sub["d"], sub["rho"])
     h.step(200)
     h.step(10)
     assert h.stats()["substep_variant"] == st["substep_variant"]
+    assert h.stats()["bins_per_cutoff"] == st["bins_per_cutoff"]
     assert len(cache.read_text().splitlines()) == 1
-    # the tuned run is the same trajectory as a fixed variant
-    f = sedi.Sedi(dict(prm, precision_form="split", substep_variant=0))
+    # the tuned run is the same trajectory as a fixed variant on bins of one cutoff
+    f = sedi.Sedi(dict(prm, precision_form="split", substep_variant=0, bins_per_cutoff=1))
     f.set_particles(sub["x"], sub["v"], sub["w"], sub["d"], sub["rho"])
     f.step(200)
     f.step(10)
