@@ -351,6 +351,7 @@ def gpu_arm(args):
                            "mesh_cells": C, "form": "split", "graphs": True,
                            "settle_steps_untimed": args.settle,
                            "substep_variant": {"variant": variant, "block": st1["substep_block"],
+                                               "bins_per_cutoff": st1["bins_per_cutoff"],
                                                "chosen_by": "autotuner"},
                            "l2": "not flushed: the particle state (~2 GB) is larger than L2",
                            "parallelism": "independent bed per GPU" if world > 1 else "1 GPU"},
@@ -516,12 +517,15 @@ def bounce_leg():
             "wall_s": round(time.time() - t0, 2)}
 
 
-def ensemble_leg(steps=3, warmup=2):
+def ensemble_leg(steps=3, warmup=2, settle=11):
     """256 independent beds of 2,000..50,000 spheres (log-uniform) on 16^3..48^3
     meshes: one ensemble handle (one launch per phase over all beds, one CUDA graph
     per fluid step, batched averaging) against the same beds in 256 single-bed
     handles stepped one after the other.  A step = 20 substeps + 1 averaging of
-    every bed; particle-steps/s of all beds together."""
+    every bed; particle-steps/s of all beds together.  The ensemble first runs
+    `settle` untimed steps, so that its autotuner (after 200 substeps) has picked the
+    batched substep's launch shape and the bins per list cutoff of every bed; the
+    single-bed handles run their default shape (the per-particle loop, 128 x 6)."""
     import torch
 
     from paper_1601_03801_gb300 import sedi
@@ -572,6 +576,10 @@ def ensemble_leg(steps=3, warmup=2):
     E.average_inplace()
     for g in singles:
         g.average_inplace()
+    for _ in range(settle):
+        step_batched()
+    torch.cuda.synchronize()
+    tuned = E.stats()
     ms_b = timed(step_batched)
     ms_p = timed(step_per_bed)
     rate = lambda ms: round(n_total * SUBSTEPS / (ms / 1e3), 1)
@@ -582,6 +590,12 @@ def ensemble_leg(steps=3, warmup=2):
             "batched": {"value": rate(ms_b), "unit": UNIT, "ms_per_step": round(ms_b, 3)},
             "per_bed_launches": {"value": rate(ms_p), "unit": UNIT, "ms_per_step": round(ms_p, 3)},
             "speedup": round(ms_p / ms_b, 3),
+            "launch_structure": "per fluid step: one CUDA graph of 20 substeps (a conditional "
+                                "batched rebuild node, then one batched substep launch over all "
+                                "beds, grid.y = bed), then one batched deposition and one "
+                                "persistent smoothing launch for all beds",
+            "tuned": {"substep_variant": tuned["substep_variant"], "block": tuned["substep_block"],
+                      "bins_per_cutoff": tuned["bins_per_cutoff"], "settle_steps_untimed": settle},
             "timing": "CUDA events on the launching stream around the steps (the averagings "
                       "synchronise the host once per handle per step)"}
 
