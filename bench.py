@@ -43,8 +43,10 @@ WORKLOAD_200K = ("sheared sediment bed: 200,000 lognormal spheres (median 0.5 mm
                  "settled (FIRE energy-minimised 8 x 4 mm block tiled 8 x 8) in a periodic "
                  "64x32x64 mm channel, wall z=0, log-law flow u*=0.02 m/s, 64x32x64 mesh; "
                  "step = 20 substeps + 1 averaging")
-PROFILE_FILE = os.path.join(ROOT, "profiles", "k_substep_bed200k.md")
-PAIRS_PROFILE_FILE = os.path.join(ROOT, "profiles", "k_pair_forces_gather_bed200k.md")
+# committed ncu summaries holding the DRAM bytes per particle-substep of the pair
+# list's substep launch (k_pair_forces + k_substep<gather>) with the kernel source hash
+TRAFFIC_LARGE = os.path.join(ROOT, "profiles", "traffic_large10M.md")
+TRAFFIC_200K = os.path.join(ROOT, "profiles", "k_pair_forces_gather_bed200k.md")
 KERNEL_SOURCES = ["paper_1601_03801_gb300/csrc/k_force.cu", "paper_1601_03801_gb300/csrc/fluid.cuh",
                   "paper_1601_03801_gb300/csrc/common.cuh", "paper_1601_03801_gb300/csrc/dd.cuh"]
 
@@ -67,12 +69,11 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(variant=None):
-    """DRAM bytes per particle-substep of the substep launch (the fused kernel, or the
-    pair-force and gather kernels of the pair list) from the committed ncu summary, if
-    it was taken on the current kernel source."""
-    path = PAIRS_PROFILE_FILE if variant == PAIRS_VARIANT else PROFILE_FILE
-    if not os.path.exists(path):
+def measured_traffic(variant, path):
+    """DRAM bytes per particle-substep of the pair list's substep launch (pair-force and
+    gather kernels) from a committed ncu summary, if it was taken on the current kernel
+    source (other launch variants: none committed)."""
+    if variant != PAIRS_VARIANT or not os.path.exists(path):
         return None, None
     txt = open(path).read()
     m = re.search(r"dram_bytes_per_particle_substep:\s*([0-9.eE+-]+)", txt)
@@ -249,16 +250,17 @@ def measure(prm, parts, fl, form, steps, warmup, settle, stream, flush=None, pro
     return g, out
 
 
-def roofline(prm, n, g, launch_ms, variant, form="split", traffic_scale=None):
+def roofline(prm, n, g, launch_ms, variant, form="split", traffic=TRAFFIC_LARGE):
     """Roofline of the substep launch: algorithmic bytes (algorithmic_bytes) of every
     particle-substep of one launch / the launch's mean duration (CUDA events inside
-    the graph), against the measured HBM copy bandwidth."""
+    the graph), against the measured HBM copy bandwidth.  `traffic`: the ncu summary
+    of this workload's DRAM bytes."""
     kbar, cbar = list_stats(g, n)
     C = int(np.prod(prm["ncell"]))
     alg = algorithmic_bytes(kbar, cbar, C, n, form)
     achieved = alg * n / (launch_ms / 1e3) / 1e9
     peak, peak_kind = peaks()
-    traffic_pp, _ = measured_traffic(variant) if form == "split" else (None, None)
+    traffic_pp, _ = measured_traffic(variant, traffic) if form == "split" else (None, None)
     out = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
            "frac": round(achieved / peak, 4), "peak_source": peak_kind,
            "traffic": None if traffic_pp is None else round(traffic_pp * n),
@@ -270,9 +272,10 @@ def roofline(prm, n, g, launch_ms, variant, form="split", traffic_scale=None):
         out["implementation_bytes_per_particle_substep"] = round(implementation_bytes(kbar, cbar, C, n), 1)
         if traffic_pp is not None:
             out["traffic_bytes_per_particle_substep"] = traffic_pp
-            out["traffic_note"] = ("DRAM bytes per particle-substep from the ncu capture of the "
-                                   "200,000-sphere bed (caches flushed before the launch), times the "
-                                   "particles of this launch")
+            out["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum of the launch's two "
+                                   "kernels per particle-substep, from the ncu capture of this "
+                                   "workload (" + os.path.basename(traffic) + "), times the particles "
+                                   "of this launch")
     return out
 
 
@@ -483,7 +486,8 @@ def bed200k_leg(args):
            "ms_per_step": round(float(np.mean(m["ms"])), 4),
            "l2": "flushed (256 MB write) between timed steps, outside the events",
            "phases_ms_per_step": m["phases"],
-           "roofline": roofline(prm, n, g, m["substep_launch_ms"], g.stats()["substep_variant"])}
+           "roofline": roofline(prm, n, g, m["substep_launch_ms"], g.stats()["substep_variant"],
+                                traffic=TRAFFIC_200K)}
     g.close()
     return out
 
