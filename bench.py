@@ -529,7 +529,10 @@ def ensemble_leg(steps=3, warmup=2, settle=11):
     every bed; particle-steps/s of all beds together.  The ensemble first runs
     `settle` untimed steps, so that its autotuner (after 200 substeps) has picked the
     batched substep's launch shape and the bins per list cutoff of every bed; the
-    single-bed handles run their default shape (the per-particle loop, 128 x 6)."""
+    single-bed handles run their default shape (the per-particle loop, 128 x 6).  A
+    second ensemble handle runs the substeps of each step in one persistent
+    cooperative launch instead of the graph (same launch shape after tuning, same
+    bits: checked on the first and last bed)."""
     import torch
 
     from paper_1601_03801_gb300 import sedi
@@ -544,10 +547,15 @@ def ensemble_leg(steps=3, warmup=2, settle=11):
         g.set_particles(p["x"], p["v"], p["w"], p["d"], p["rho"], **kw)
         g.set_fluid(U=bd["U"], **kw)
 
-    E = sedi.Sedi(dict(prm, n_beds=len(beds), precision_form="split"), stream=stream)
-    for b, bd in enumerate(beds):
-        E.set_bed(b, bd["lo"], bd["hi"], bd["ncell"])
-        load(E, b, bd, {"bed": b})
+    def ensemble(**extra):
+        h = sedi.Sedi(dict(prm, n_beds=len(beds), precision_form="split", **extra), stream=stream)
+        for b, bd in enumerate(beds):
+            h.set_bed(b, bd["lo"], bd["hi"], bd["ncell"])
+            load(h, b, bd, {"bed": b})
+        return h
+
+    E = ensemble()
+    Ep = ensemble(ens_persistent=1)
     singles = []
     for bd in beds:
         g = sedi.Sedi(dict(prm, lo=bd["lo"], hi=bd["hi"], ncell=bd["ncell"], precision_form="split"),
@@ -572,20 +580,29 @@ def ensemble_leg(steps=3, warmup=2, settle=11):
         E.step(SUBSTEPS)
         E.average_inplace()
 
+    def step_persistent():
+        Ep.step(SUBSTEPS)
+        Ep.average_inplace()
+
     def step_per_bed():
         for g in singles:
             g.step(SUBSTEPS)
             g.average_inplace()
 
     E.average_inplace()
+    Ep.average_inplace()
     for g in singles:
         g.average_inplace()
     for _ in range(settle):
         step_batched()
+        step_persistent()
     torch.cuda.synchronize()
     tuned = E.stats()
     ms_b = timed(step_batched)
+    ms_q = timed(step_persistent)
     ms_p = timed(step_per_bed)
+    same = all(np.array_equal(a, b) for bed in (0, len(beds) - 1)
+               for a, b in zip(E.get_particles(bed=bed), Ep.get_particles(bed=bed)))
     rate = lambda ms: round(n_total * SUBSTEPS / (ms / 1e3), 1)
     return {"workload": "256 beds, N_b = exp(U[ln 2000, ln 50000]) spheres of d = 0.5 mm on a jittered "
                         "lattice, n_b mm cubic periodic-x/y wall-z boxes, n_b^3 meshes (n_b = 16..48), "
@@ -593,6 +610,11 @@ def ensemble_leg(steps=3, warmup=2, settle=11):
             "beds": len(beds), "particles": n_total, "steps": steps, "warmup": warmup,
             "batched": {"value": rate(ms_b), "unit": UNIT, "ms_per_step": round(ms_b, 3)},
             "per_bed_launches": {"value": rate(ms_p), "unit": UNIT, "ms_per_step": round(ms_p, 3)},
+            "persistent": {"value": rate(ms_q), "unit": UNIT, "ms_per_step": round(ms_q, 3),
+                           "structure": "the 20 substeps of a step in one persistent cooperative "
+                                        "launch over all beds (bounded grid barrier between "
+                                        "substeps; a rebuild ends the launch, the next resumes)",
+                           "same_bits_as_graph": bool(same)},
             "speedup": round(ms_p / ms_b, 3),
             "launch_structure": "per fluid step: one CUDA graph of 20 substeps (a conditional "
                                 "batched rebuild node, then one batched substep launch over all "

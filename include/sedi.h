@@ -159,6 +159,14 @@ typedef struct sedi_params {
                                               (see sedi_get_timings) [0] */
   int32_t use_cnn_guess;                   /* start every smoothing pseudo-step from
                                               the learned guess (sedi_cnn_*) [0] */
+  int32_t ens_persistent;                  /* ensembles: run the substeps of a sedi_step
+                                              call for all beds in one persistent
+                                              cooperative launch (grid barrier between
+                                              substeps; a list rebuild ends the launch and
+                                              the next one resumes after it) instead of a
+                                              CUDA graph of one batched launch per substep
+                                              [0].  Same results either way; not with lift
+                                              or tangential lubrication. */
   int32_t bins_per_cutoff;                 /* link-cell bins per list cutoff of the list
                                               build: 0 = autotuned with the launch shape
                                               (1 until then, and whenever substep_variant

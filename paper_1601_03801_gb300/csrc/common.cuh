@@ -35,7 +35,7 @@ struct Ctl {
   uint32_t bar_count, bar_gen;  // grid barrier of the persistent smoother
   uint32_t blocks_done;    // completion counter of the substep kernel
   uint32_t npair;          // interaction pairs of the current lists (pair list)
-  int32_t pad;
+  int32_t ens_rebuild;     // ensembles: some bed needs a list rebuild after the last substep
 };
 
 // Constants of the force arithmetic, precomputed on the host in the force word

@@ -90,6 +90,7 @@ struct sedi_handle {
   EnsLaunch ens{};
   bool ens_dirty = true;          // a bed's buffers changed: rebuild the table
   int ens_variant = SUBSTEP_B128_LOOP;  // launch shape of the batched substep
+  int* ens_done = nullptr;        // substeps completed by the last persistent launch
   bool ens_fresh = false;         // the batched averaging is newer than the last step
 };
 
@@ -1048,7 +1049,8 @@ void sedi_destroy(sedi_handle* h) {
     sedi_destroy(b);
   }
   h->beds.clear();
-  for (void* p : {(void*)h->ens_views, h->ens_smooth, (void*)h->ens_iters, (void*)h->ens_ctl})
+  for (void* p : {(void*)h->ens_views, h->ens_smooth, (void*)h->ens_iters, (void*)h->ens_ctl,
+                  (void*)h->ens_done})
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->avg_ev) cudaEventDestroy(e);
   free_list(h->part_allocs);
@@ -1688,7 +1690,25 @@ static int ens_step(sedi_handle* h, int n) {
       for (int k = 0; k < 5; ++k) h->avg_ev.push_back(new_event());
     CK(cudaEventRecord(h->avg_ev[3], h->stream));
   }
-  if (h->prm.use_graphs && h->stream != nullptr) {
+  if (h->prm.ens_persistent && !ens_ext(h)) {
+    // persistent launches: rebuild the beds that need it, then run substeps until one
+    // leaves a bed needing a rebuild (or all are done)
+    if (!h->ens_done) CK(cudaMalloc((void**)&h->ens_done, sizeof(int)));
+    launch_check_ens(h->ens, 0ull, 0, h->stream);
+    int s = 0;
+    while (s < n) {
+      launch_rebuild_ens(h->form, h->ens, s, h->stream);
+      if (launch_substeps_persist_ens(h->form, h->ens, s, n, h->barrier_spins, h->ens_done, h->stream))
+        return fail(h, SEDI_ECUDA, "persistent ensemble launch refused: %s", cudaGetErrorString(cudaGetLastError()));
+      int done = 0;
+      CK(cudaMemcpyAsync(&done, h->ens_done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      if (done < 0) return fail(h, SEDI_ETIMEOUT, "persistent ensemble launch: a grid-barrier wait ran out");
+      if (done <= s) return fail(h, SEDI_ECUDA, "persistent ensemble launch made no progress");
+      s = done;
+    }
+    launch_advance_ens(h->ens, n, h->stream);
+  } else if (h->prm.use_graphs && h->stream != nullptr) {
     auto it = h->graphs.find(n);
     cudaGraphExec_t ex;
     if (it == h->graphs.end()) {

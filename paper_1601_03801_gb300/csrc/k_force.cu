@@ -9,6 +9,7 @@
 // identical copies of the pair's spring; no atomics and no second pass.
 // Particle state is double-buffered (read buffer, write buffer) so neighbours are
 // read at the old time level.
+#include "../../include/sedi.h"
 #include "common.cuh"
 #include "fluid.cuh"
 #include "fmath.cuh"
@@ -770,6 +771,7 @@ __device__ __forceinline__ void substep_body(const DevState& st, const DevMesh& 
           __threadfence();
           const int any = atomicExch(&ectl->need_rebuild, 0);
           ectl->blocks_done = 0u;
+          ectl->ens_rebuild = any;
           if (use_cond) cudaGraphSetConditional(next, any ? 1u : 0u);
         }
       } else if (use_cond) {
@@ -879,6 +881,123 @@ void launch_substep(int form, const DevState& st, const DevMesh& mesh, const Dev
 }
 
 
+// Bounded grid barrier of the persistent ensemble launch (co-residency guaranteed by
+// the cooperative launch): a waiting block gives up after spin_limit polls, records
+// SEDI_ETIMEOUT and returns; the others see the record and return at their next wait.
+__device__ bool ens_grid_barrier(Ctl* ctl, unsigned nblocks, long long spin_limit) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = &ctl->bar_gen;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&ctl->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&ctl->bar_gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == g) {
+        if (++spins > spin_limit) {
+          atomicCAS(&ctl->error, 0, (int)SEDI_ETIMEOUT);
+          break;
+        }
+        if ((spins & 1023) == 0 && *((volatile int*)&ctl->error) == (int)SEDI_ETIMEOUT) break;
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *((volatile int*)&ctl->error) != (int)SEDI_ETIMEOUT;
+}
+
+__global__ void k_ens_bar_reset(Ctl* ctl) {
+  ctl->bar_count = 0u;
+  ctl->bar_gen = 0u;
+  ctl->error = 0;
+  ctl->ens_rebuild = 0;
+}
+
+// Persistent ensemble launch: substeps s0 .. n-1 of every bed in one cooperative launch
+// (every block resident).  The (bed, block) items of a substep are spread over the CTAs
+// -- each item runs the same body, with the same arguments, as the batched launch's
+// block (bed, blk) -- and a bounded grid barrier separates substeps.  The launch stops
+// after the first substep that leaves a bed needing a list rebuild (the host rebuilds
+// and launches again from the next substep).  *done receives the substeps completed
+// (-1 when a barrier wait ran out).
+template <int FORM, int BS, int MINB, bool COOP>
+__global__ void __launch_bounds__(BS, MINB) k_substeps_persist_e(const BedView* v, int nbeds, Ctl* ectl,
+                                                                   int s0, int n, int maxblk,
+                                                                   long long spin_limit, int* done) {
+  __shared__ BedView s_view;
+  __shared__ int s_stop;
+  const int64_t items = (int64_t)nbeds * maxblk;
+  int s = s0;
+  bool ok = true;
+  while (s < n) {
+    for (int64_t t = blockIdx.x; t < items; t += gridDim.x) {
+      const int bed = (int)(t / maxblk), blk = (int)(t % maxblk);
+      const int64_t N = v[bed].st.N;
+      const unsigned nblk = (unsigned)((N + BS - 1) / BS);
+      if ((unsigned)blk >= nblk) continue;  // the same for the whole CTA
+      __syncthreads();                      // the previous item's readers of s_view are done
+      const int4* src = reinterpret_cast<const int4*>(v + bed);
+      int4* dst = reinterpret_cast<int4*>(&s_view);
+      for (int k = threadIdx.x; k < (int)(sizeof(BedView) / 16); k += blockDim.x) dst[k] = src[k];
+      __syncthreads();
+      substep_body<FORM, true, BS, COOP, false>(s_view.st, s_view.mesh, s_view.P, s, 0ull, 0, blk, nblk,
+                                                ectl, nbeds);
+    }
+    if (!ens_grid_barrier(ectl, gridDim.x, spin_limit)) {
+      ok = false;
+      break;
+    }
+    ++s;
+    // the last bed of the substep left the any-bed rebuild decision
+    if (threadIdx.x == 0) s_stop = *((volatile int*)&ectl->ens_rebuild);
+    __syncthreads();
+    if (s_stop) break;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *done = ok ? s : -1;
+}
+
+template <int FORM, int BS, int MINB, bool COOP>
+static int launch_persist_shape(const EnsLaunch& e, int s0, int n, long long spin_limit, int* done,
+                                cudaStream_t s) {
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_substeps_persist_e<FORM, BS, MINB, COOP>, BS, 0) !=
+          cudaSuccess || per_sm < 1)
+    return -1;
+  int maxblk = (int)((e.max_n + BS - 1) / BS);
+  int64_t G = (int64_t)nsm * per_sm;
+  if (G > (int64_t)e.B * maxblk) G = (int64_t)e.B * maxblk;
+  if (G < 1) G = 1;
+  k_ens_bar_reset<<<1, 1, 0, s>>>(e.ectl);
+  const BedView* views = e.views;
+  int B = e.B;
+  Ctl* ectl = e.ectl;
+  void* args[] = {(void*)&views, (void*)&B, (void*)&ectl, (void*)&s0, (void*)&n, (void*)&maxblk,
+                  (void*)&spin_limit, (void*)&done};
+  return cudaLaunchCooperativeKernel((const void*)k_substeps_persist_e<FORM, BS, MINB, COOP>, dim3((unsigned)G),
+                                     dim3(BS), args, 0, s) == cudaSuccess ? 0 : -1;
+}
+
+template <int FORM>
+static int launch_persist(const EnsLaunch& e, int s0, int n, long long spin_limit, int* done, cudaStream_t s) {
+  if constexpr (FORM != FORM_FP64) {
+    switch (e.variant) {
+      case SUBSTEP_B64_LOOP: return launch_persist_shape<FORM, 64, 12, false>(e, s0, n, spin_limit, done, s);
+      case SUBSTEP_B128_OCC8_LOOP: return launch_persist_shape<FORM, 128, 8, false>(e, s0, n, spin_limit, done, s);
+      case SUBSTEP_B128: return launch_persist_shape<FORM, 128, 6, true>(e, s0, n, spin_limit, done, s);
+      default: break;
+    }
+  }
+  return launch_persist_shape<FORM, 128, 6, false>(e, s0, n, spin_limit, done, s);
+}
+
 template <int FORM, int BS, int MINB, bool COOP, bool EXT>
 static void launch_ens_shape(const EnsLaunch& e, int sub_off, unsigned long long next_cond, int use_cond,
                              cudaStream_t s) {
@@ -904,6 +1023,15 @@ static void launch_ens(const EnsLaunch& e, bool ext, int sub_off, unsigned long 
     }
   }
   launch_ens_shape<FORM, 128, 6, false, false>(e, sub_off, next_cond, use_cond, s);
+}
+
+int launch_substeps_persist_ens(int form, const EnsLaunch& e, int s0, int n, long long spin_limit, int* done,
+                                cudaStream_t s) {
+  switch (form) {
+    case FORM_SPLIT: return launch_persist<FORM_SPLIT>(e, s0, n, spin_limit, done, s);
+    case FORM_PLAIN: return launch_persist<FORM_PLAIN>(e, s0, n, spin_limit, done, s);
+    default: return launch_persist<FORM_FP64>(e, s0, n, spin_limit, done, s);
+  }
 }
 
 void launch_substep_ens(int form, const EnsLaunch& e, bool ext, int sub_off,

@@ -74,6 +74,12 @@ void launch_force_need_ens(const EnsLaunch& e, cudaStream_t s);
 // every bed's rebuild counter from rebuilds[B] (device)
 void launch_set_rebuilds_ens(const EnsLaunch& e, const int64_t* rebuilds, cudaStream_t s);
 void launch_ctl_gather_ens(const EnsLaunch& e, Ctl* out, cudaStream_t s);
+// Substeps s0 .. n-1 of every bed in one persistent cooperative launch (no optional
+// terms), stopping after the first substep that leaves a bed needing a list rebuild;
+// *done (device) receives the substeps completed, or -1 when a grid-barrier wait ran
+// out (SEDI_ETIMEOUT in e.ectl->error).  Nonzero when the launch was refused.
+int launch_substeps_persist_ens(int form, const EnsLaunch& e, int s0, int n, long long spin_limit, int* done,
+                                cudaStream_t s);
 // ext: the beds run the optional terms (lift, tangential lubrication)
 void launch_substep_ens(int form, const EnsLaunch& e, bool ext, int sub_off,
                         unsigned long long next_cond, int use_cond, cudaStream_t s);

@@ -56,8 +56,8 @@ class SediParams(C.Structure):
         ("bandwidth", _D * 3), ("n_tau", _I), ("tau_scheme", _I), ("cg_rtol", _D), ("cg_max_iter", _I),
         ("shift_eps", _I), ("shift_mom", _I), ("shift_force", _I),
         ("precision_form", _I), ("nbr_capacity", _I), ("use_graphs", _I), ("substep_variant", _I),
-        ("n_beds", _I), ("profile", _I), ("use_cnn_guess", _I), ("bins_per_cutoff", _I),
-        ("cnn_scale", _D * 4),
+        ("n_beds", _I), ("profile", _I), ("use_cnn_guess", _I), ("ens_persistent", _I),
+        ("bins_per_cutoff", _I), ("cnn_scale", _D * 4),
         ("seed", C.c_uint64),
     ]
 

@@ -190,3 +190,43 @@ def test_tuned_ensemble_keeps_each_bed_bits(ens):
         for a, c in zip(got[k], s.get_particles()):
             assert np.array_equal(a, c), b
 
+
+@pytest.mark.parametrize("variant", [5, 0])
+def test_persistent_ensemble_launch_gives_the_graph_bits(ens, variant):
+    """The substeps of a step in one persistent cooperative launch (grid barrier between
+    substeps; a substep that leaves a bed needing a list rebuild ends the launch and the
+    next one resumes after the rebuild) against the CUDA graph of batched launches: the
+    same bits.  The beds move fast enough (0.5 m/s) to rebuild their lists mid-step."""
+    prm, beds = ens
+    rng = np.random.default_rng(21)
+    fast = []
+    for bd in beds[:3]:
+        b = dict(bd, parts=dict(bd["parts"]))
+        b["parts"]["v"] = rng.normal(0.0, 0.5, bd["parts"]["x"].shape)
+        fast.append(b)
+    out = []
+    for persistent in (0, 1):
+        g = make_ensemble(prm, fast, substep_variant=variant, ens_persistent=persistent)
+        res = run(g, range(len(fast)), single=False)
+        out.append((res, g.stats()))
+    (r0, s0), (r1, s1) = out
+    assert s1["rebuilds"] == s0["rebuilds"] and s1["rebuilds"] > 2 * len(fast)
+    for a, b in zip(r0, r1):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+
+
+def test_persistent_ensemble_barrier_timeout_is_reported(ens, monkeypatch):
+    """With the grid-barrier poll limit at 1 the first wait of the persistent launch runs
+    out: every block returns and the step reports SEDI_ETIMEOUT; the device stays usable."""
+    prm, beds = ens
+    monkeypatch.setenv("SEDI_BARRIER_SPIN_LIMIT", "1")
+    g = make_ensemble(prm, beds[:2], substep_variant=5, ens_persistent=1)
+    monkeypatch.delenv("SEDI_BARRIER_SPIN_LIMIT")
+    with pytest.raises(sedi.SediError) as e:
+        g.step(20)
+    assert e.value.code == -8
+    h = make_ensemble(prm, beds[:2], substep_variant=5, ens_persistent=1)
+    h.step(20)
+    h.sync()
+
