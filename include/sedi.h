@@ -167,6 +167,11 @@ typedef struct sedi_params {
                                               CUDA graph of one batched launch per substep
                                               [0].  Same results either way; not with lift
                                               or tangential lubrication. */
+  int32_t bin_order;                       /* storage order of the link-cell bins: -1 =
+                                              autotuned with the launch shape (x fastest
+                                              until then, and whenever substep_variant is
+                                              fixed) [-1]; 0 = x fastest, 1 = z fastest.
+                                              Changes no result. */
   int32_t bins_per_cutoff;                 /* link-cell bins per list cutoff of the list
                                               build: 0 = autotuned with the launch shape
                                               (1 until then, and whenever substep_variant
@@ -194,7 +199,8 @@ typedef struct sedi_stats {
   int32_t substep_block;   /* its threads per block (0: not yet tuned) */
   int32_t bins_per_cutoff; /* link-cell bins per list cutoff of the list build (1 or 2;
                               picked with the launch variant) */
-  int32_t pad;
+  int32_t bin_order;       /* storage order of the bins: 0 x fastest, 1 z fastest
+                              (picked with the launch variant) */
 } sedi_stats;
 
 /* Fill p with the defaults listed above (box 20 x 20 x 40 mm, periodic x/y,

@@ -87,6 +87,7 @@ struct DevParams {
   int64_t nbins;
   float bin_inv[3];                // bins per metre
   int32_t bin_reach;               // R: bins per list cutoff (the stencil spans +-R bins)
+  int32_t bin_zfast;               // bin storage order: 0 x fastest, 1 z fastest
   // deposition
   int32_t shift[3];                // eps, momentum, force
   double two_shift[3];             // 2^shift

@@ -291,6 +291,7 @@ int check_params(sedi_handle* h, const sedi_params& p) {
     return fail(h, SEDI_EINVAL, "the learned warm start runs backward-Euler pseudo-steps only");
   if (p.precision_form < 0 || p.precision_form > 2) return fail(h, SEDI_EINVAL, "unknown precision_form");
   if (p.bins_per_cutoff < 0 || p.bins_per_cutoff > 2) return fail(h, SEDI_EINVAL, "bins_per_cutoff must be 0, 1 or 2");
+  if (p.bin_order < -1 || p.bin_order > 1) return fail(h, SEDI_EINVAL, "bin_order must be -1, 0 or 1");
   if (p.nbr_capacity < 1 || p.nbr_capacity > kMaxCap) return fail(h, SEDI_EINVAL, "nbr_capacity must be in [1, %d]", kMaxCap);
   if (p.n_beds < 1 || p.n_beds > kMaxBeds) return fail(h, SEDI_EINVAL, "n_beds must be in [1, %d]", kMaxBeds);
   if (p.substep_variant < -1 || p.substep_variant >= kSubstepVariants)
@@ -522,6 +523,7 @@ int alloc_particles(sedi_handle* h, int64_t N, double rmax) {
   // bins: R = 1 (edge >= the largest list cutoff) until the autotuner picks otherwise;
   // a tuned R is kept while it fits the new particles
   h->rc_max = (2.0 * rmax) * (1.0 + h->prm.lub_h_out_frac) + h->prm.skin;
+  if (h->prm.bin_order >= 0) h->P.bin_zfast = h->prm.bin_order;
   if (h->prm.bins_per_cutoff > 0) {
     if ((rc = set_bins(h, h->prm.bins_per_cutoff))) return rc;
   } else {
@@ -662,9 +664,24 @@ constexpr int kTuneRounds = 5;
 // a state that has them.  Until then the per-particle loop at 128 x 6 runs.
 constexpr int64_t kTuneAfter = 200;
 
+// A bin configuration: R bins per list cutoff and the storage order of the bins.
+struct BinCfg {
+  int reach = 1;  // 1 or 2
+  int zfast = 0;  // 0: x fastest, 1: z fastest
+  bool operator==(const BinCfg& o) const { return reach == o.reach && zfast == o.zfast; }
+  bool operator!=(const BinCfg& o) const { return !(*this == o); }
+};
+
+BinCfg bin_cfg(const sedi_handle* h) {
+  BinCfg c;
+  c.reach = h->P.bin_reach > 1 ? h->P.bin_reach : 1;
+  c.zfast = h->P.bin_zfast ? 1 : 0;
+  return c;
+}
+
 struct TuneChoice {
   int variant = -1;
-  int reach = 1;  // bins per list cutoff
+  BinCfg bins;
 };
 
 std::mutex g_tune_mu;
@@ -700,27 +717,30 @@ TuneChoice tune_file_lookup(const std::string& key) {
     const char* k = std::strstr(line, want.c_str());
     const char* v = std::strstr(line, "\"variant\": ");
     const char* r = std::strstr(line, "\"bins_per_cutoff\": ");
-    if (!k || !v || !r) continue;
+    const char* o = std::strstr(line, "\"bin_order\": \"");
+    if (!k || !v || !r || !o) continue;
     const int var = std::atoi(v + 11), reach = std::atoi(r + 19);
     if (var >= 0 && var < kSubstepVariants && (reach == 1 || reach == 2)) {
       found.variant = var;  // the last entry wins
-      found.reach = reach;
+      found.bins.reach = reach;
+      found.bins.zfast = o[14] == 'z' ? 1 : 0;
     }
   }
   std::fclose(f);
   return found;
 }
 
-void tune_file_store(const std::string& key, const TuneChoice& best, const std::vector<int>& reaches,
+void tune_file_store(const std::string& key, const TuneChoice& best, const std::vector<BinCfg>& cfgs,
                      const std::vector<std::vector<double>>& us, const std::vector<double>& rebuild_us) {
   const char* path = std::getenv("SEDI_AUTOTUNE_CACHE");
   if (!path || !*path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "{\"key\": \"%s\", \"variant\": %d, \"bins_per_cutoff\": %d, \"block\": %d, \"median_us\": {",
-               key.c_str(), best.variant, best.reach, substep_block(best.variant));
-  for (size_t r = 0; r < reaches.size(); ++r) {
-    std::fprintf(f, "%s\"R%d\": [", r ? ", " : "", reaches[r]);
+  std::fprintf(f, "{\"key\": \"%s\", \"variant\": %d, \"bins_per_cutoff\": %d, \"bin_order\": \"%c\", "
+               "\"block\": %d, \"median_us\": {",
+               key.c_str(), best.variant, best.bins.reach, best.bins.zfast ? 'z' : 'x', substep_block(best.variant));
+  for (size_t r = 0; r < cfgs.size(); ++r) {
+    std::fprintf(f, "%s\"R%d%c\": [", r ? ", " : "", cfgs[r].reach, cfgs[r].zfast ? 'z' : 'x');
     for (int v = 0; v < kSubstepVariants; ++v) std::fprintf(f, "%s%.3f", v ? ", " : "", us[r][v]);
     std::fprintf(f, "]");
   }
@@ -730,18 +750,26 @@ void tune_file_store(const std::string& key, const TuneChoice& best, const std::
   std::fclose(f);
 }
 
-// Bins of R per cutoff and a rebuild at once; the rebuild counter is left as it was
-// (the tuner's rebuilds are not the run's).
-int retune_bins(sedi_handle* h, int R) {
+// The bins of a configuration (graphs cleared when it changes: they bake in the bin
+// arrays and parameters).
+int apply_bins(sedi_handle* h, const BinCfg& b) {
+  if (b == bin_cfg(h)) return 0;
+  clear_graphs(h);
+  int rc;
+  if (b.reach != h->P.bin_reach && (rc = set_bins(h, b.reach))) return rc;
+  h->P.bin_zfast = b.zfast;
+  return 0;
+}
+
+// Bins of a configuration and a rebuild at once; the rebuild counter is left as it
+// was (the tuner's rebuilds are not the run's).
+int retune_bins(sedi_handle* h, const BinCfg& b) {
   Ctl c;
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaMemcpy(&c, h->st.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
   const int64_t rebuilds = c.rebuilds;
   int rc;
-  if (R != h->P.bin_reach) {
-    clear_graphs(h);  // graphs bake in the bin arrays
-    if ((rc = set_bins(h, R))) return rc;
-  }
+  if ((rc = apply_bins(h, b))) return rc;
   launch_rebuild_now(h->form, h->st, h->P, h->stream);
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaMemcpy(&c, h->st.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
@@ -786,10 +814,22 @@ int autotune(sedi_handle* h) {
       if (!bins_for(h, 2, nb, &nbins) && nbins <= std::max<int64_t>(16 * h->N, (int64_t)1 << 22))
         reaches.push_back(2);
     }
-    // the current bin size last, so that a single candidate needs no extra resize
-    if (h->P.bin_reach == 1) std::reverse(reaches.begin(), reaches.end());
-    std::vector<std::vector<double>> med(reaches.size(), std::vector<double>(kSubstepVariants, 1e30));
-    std::vector<double> rebuild_us(reaches.size(), 0.0);
+    // every bin size in both storage orders, the current configuration last (a single
+    // candidate then needs no extra resize)
+    std::vector<BinCfg> cfgs;
+    for (int R : reaches)
+      for (int z = 0; z < 2; ++z) {
+        if (h->prm.bin_order >= 0 && z != h->prm.bin_order) continue;
+        BinCfg c;
+        c.reach = R;
+        c.zfast = z;
+        if (c != bin_cfg(h)) cfgs.push_back(c);
+      }
+    if (std::find(reaches.begin(), reaches.end(), bin_cfg(h).reach) != reaches.end() &&
+        (h->prm.bin_order < 0 || bin_cfg(h).zfast == h->prm.bin_order))
+      cfgs.push_back(bin_cfg(h));
+    std::vector<std::vector<double>> med(cfgs.size(), std::vector<double>(kSubstepVariants, 1e30));
+    std::vector<double> rebuild_us(cfgs.size(), 0.0);
     const int64_t N = h->N, cap = h->P.cap;
     const size_t q = quad_bytes(h->form), fq = fquad_bytes(h->form), w = word_bytes(h->form);
     cudaEvent_t rb[2];
@@ -798,13 +838,9 @@ int autotune(sedi_handle* h) {
     std::vector<cudaEvent_t> ev(2 * kSubstepVariants * kTuneRounds, nullptr);
     for (auto& e : ev) CK(cudaEventCreate(&e));
     rc = 0;
-    for (size_t ri = 0; ri < reaches.size() && !rc; ++ri) {
-      const int R = reaches[ri];
-      // the bins of R and lists built from the current positions (timed)
-      if (R != h->P.bin_reach) {
-        clear_graphs(h);
-        if ((rc = set_bins(h, R))) break;
-      }
+    for (size_t ri = 0; ri < cfgs.size() && !rc; ++ri) {
+      // the bins of this configuration and lists built from the current positions (timed)
+      if ((rc = apply_bins(h, cfgs[ri]))) break;
       {
         Ctl c;
         CK(cudaMemcpy(&c, h->st.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
@@ -834,8 +870,8 @@ int autotune(sedi_handle* h) {
         // no room for the saved copies: keep this bin size and the current launch shape
         cudaGetLastError();
         best.variant = h->variant;
-        best.reach = R;
-        reaches.resize(ri + 1);
+        best.bins = cfgs[ri];
+        cfgs.resize(ri + 1);
         med.resize(ri + 1);
         rebuild_us.resize(ri + 1);
         med[ri].assign(kSubstepVariants, 1e30);
@@ -882,24 +918,24 @@ int autotune(sedi_handle* h) {
     cudaEventDestroy(rb[1]);
     if (rc) return rc;
     double best_cost = 1e300;
-    for (size_t ri = 0; ri < reaches.size(); ++ri)
+    for (size_t ri = 0; ri < cfgs.size(); ++ri)
       for (int v = 0; v < kSubstepVariants; ++v) {
         const double cost = med[ri][v] + rebuild_us[ri] * rate;
         if (cost < best_cost) {
           best_cost = cost;
           best.variant = v;
-          best.reach = reaches[ri];
+          best.bins = cfgs[ri];
         }
       }
-    tune_file_store(key, best, reaches, med, rebuild_us);
+    tune_file_store(key, best, cfgs, med, rebuild_us);
   }
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = best;
   }
   // the chosen bins (lists rebuilt at once when they change)
-  if (best.reach != h->P.bin_reach) {
-    const int rc = retune_bins(h, best.reach);
+  if (best.bins != bin_cfg(h)) {
+    const int rc = retune_bins(h, best.bins);
     if (rc) return rc;
   }
   if (best.variant != h->variant) clear_graphs(h);  // graphs bake in the launch shape
@@ -955,6 +991,7 @@ void sedi_default_params(sedi_params* p) {
   p->nbr_capacity = 32;
   p->use_graphs = 1;
   p->substep_variant = -1;
+  p->bin_order = -1;
   p->n_beds = 1;
   p->cnn_scale[0] = p->cnn_scale[1] = p->cnn_scale[2] = p->cnn_scale[3] = 1.0;
 }
@@ -1498,12 +1535,12 @@ static int ens_autotune(sedi_handle* h) {
   int64_t* rb_dev = nullptr;
   CK(cudaMalloc((void**)&rb_dev, 8 * B));
   CK(cudaMemcpy(rb_dev, rebuilds.data(), 8 * B, cudaMemcpyHostToDevice));
-  // every bed on bins of R, rebuilt now; returns the rebuild time (us)
-  auto bins_and_rebuild = [&](int R, double* us) -> int {
+  // every bed on the bins of a configuration, rebuilt now; returns the rebuild time (us)
+  auto bins_and_rebuild = [&](const BinCfg& cfg, double* us) -> int {
     bool changed = false;
     for (sedi_handle* b : h->beds)
-      if (b->P.bin_reach != R) {
-        int r2 = set_bins(b, R);
+      if (bin_cfg(b) != cfg) {
+        int r2 = apply_bins(b, cfg);
         if (r2) return fail(h, r2, "bed bins: %s", b->err.c_str());
         changed = true;
       }
@@ -1535,13 +1572,25 @@ static int ens_autotune(sedi_handle* h) {
     }
     if (two) reaches.push_back(2);
     if (h->prm.bins_per_cutoff > 0) reaches = {h->prm.bins_per_cutoff};
-    if (h->beds[0]->P.bin_reach == 1) std::reverse(reaches.begin(), reaches.end());
-    std::vector<std::vector<double>> med(reaches.size(), std::vector<double>(kSubstepVariants, 1e30));
-    std::vector<double> rebuild_us(reaches.size(), 0.0);
+    const BinCfg cur = bin_cfg(h->beds[0]);
+    std::vector<BinCfg> cfgs;
+    for (int R : reaches)
+      for (int z = 0; z < 2; ++z) {
+        if (h->prm.bin_order >= 0 && z != h->prm.bin_order) continue;
+        BinCfg c;
+        c.reach = R;
+        c.zfast = z;
+        if (c != cur) cfgs.push_back(c);
+      }
+    if (std::find(reaches.begin(), reaches.end(), cur.reach) != reaches.end() &&
+        (h->prm.bin_order < 0 || cur.zfast == h->prm.bin_order))
+      cfgs.push_back(cur);
+    std::vector<std::vector<double>> med(cfgs.size(), std::vector<double>(kSubstepVariants, 1e30));
+    std::vector<double> rebuild_us(cfgs.size(), 0.0);
     std::vector<cudaEvent_t> ev(2 * kEnsVariants * kTuneRounds, nullptr);
     for (auto& e : ev) e = new_event();
-    for (size_t ri = 0; ri < reaches.size() && !rc; ++ri) {
-      if ((rc = bins_and_rebuild(reaches[ri], &rebuild_us[ri]))) break;
+    for (size_t ri = 0; ri < cfgs.size() && !rc; ++ri) {
+      if ((rc = bins_and_rebuild(cfgs[ri], &rebuild_us[ri]))) break;
       launch_ctl_gather_ens(h->ens, h->ens_ctl, h->stream);
       CK(cudaMemcpyAsync(c.data(), h->ens_ctl, sizeof(Ctl) * B, cudaMemcpyDeviceToHost, h->stream));
       CK(cudaStreamSynchronize(h->stream));
@@ -1565,8 +1614,8 @@ static int ens_autotune(sedi_handle* h) {
       if (cudaMalloc((void**)&save, total) != cudaSuccess) {
         cudaGetLastError();
         best.variant = h->ens_variant;
-        best.reach = reaches[ri];
-        reaches.resize(ri + 1);
+        best.bins = cfgs[ri];
+        cfgs.resize(ri + 1);
         med.resize(ri + 1);
         rebuild_us.resize(ri + 1);
         med[ri].assign(kSubstepVariants, 1e30);
@@ -1614,19 +1663,19 @@ static int ens_autotune(sedi_handle* h) {
     for (auto& e : ev) cudaEventDestroy(e);
     if (!rc) {
       double best_cost = 1e300;
-      for (size_t ri = 0; ri < reaches.size(); ++ri)
+      for (size_t ri = 0; ri < cfgs.size(); ++ri)
         for (int v = 0; v < kEnsVariants; ++v) {
           const double cost = med[ri][kEnsVariant[v]] + rebuild_us[ri] * rate;
           if (cost < best_cost) {
             best_cost = cost;
             best.variant = kEnsVariant[v];
-            best.reach = reaches[ri];
+            best.bins = cfgs[ri];
           }
         }
-      tune_file_store(key, best, reaches, med, rebuild_us);
+      tune_file_store(key, best, cfgs, med, rebuild_us);
     }
   }
-  if (!rc && h->beds[0]->P.bin_reach != best.reach) rc = bins_and_rebuild(best.reach, nullptr);
+  if (!rc && bin_cfg(h->beds[0]) != best.bins) rc = bins_and_rebuild(best.bins, nullptr);
   cudaFree(rb_dev);
   if (rc) return rc;
   {
@@ -2232,7 +2281,7 @@ namespace {
 struct CkHeader {
   char magic[8];
   int32_t version, form, cap;
-  int32_t bins_per_cutoff;  // R of the stored order (0 in older files: 1)
+  int32_t bins_per_cutoff;  // R | z-fastest << 8 of the stored order (0 in older files: 1, x)
   int64_t N, C, nbins;
   sedi_stats stats;
 };
@@ -2298,7 +2347,7 @@ static int save_to(sedi_handle* h, FILE* f) {
   hd.N = h->N;
   hd.C = h->P.C;
   hd.nbins = h->P.nbins;
-  hd.bins_per_cutoff = h->P.bin_reach;
+  hd.bins_per_cutoff = bin_cfg(h).reach | (bin_cfg(h).zfast << 8);
   hd.stats = h->stats;
   rc = ck_write(f, &hd, sizeof(hd)) ? fail(h, SEDI_EIO, "write failed") : 0;
   if (!rc) rc = ck_write(f, h->d_host.data(), 8 * h->N) || ck_write(f, h->rho_host.data(), 8 * h->N) ? fail(h, SEDI_EIO, "write failed") : 0;
@@ -2352,8 +2401,10 @@ static int load_from(sedi_handle* h, FILE* f) {
     h->have_particles = false;
     rc = alloc_particles(h, hd.N, rmax);
     // the stored order and lists follow the stored bins
-    const int R = hd.bins_per_cutoff > 0 ? hd.bins_per_cutoff : 1;
-    if (!rc && R != h->P.bin_reach) rc = set_bins(h, R);
+    BinCfg stored;
+    stored.reach = (hd.bins_per_cutoff & 0xff) > 0 ? (hd.bins_per_cutoff & 0xff) : 1;
+    stored.zfast = (hd.bins_per_cutoff >> 8) & 1;
+    if (!rc) rc = apply_bins(h, stored);
     if (!rc && h->P.nbins != hd.nbins) rc = fail(h, SEDI_EINVAL, "checkpoint binning differs");
   }
   if (!rc) {
@@ -2573,7 +2624,8 @@ int sedi_get_stats(sedi_handle* h, sedi_stats* out) {
     st.nbr_capacity = h->P.cap;
     st.substep_variant = h->ens_variant;
     st.substep_block = substep_block(h->ens_variant);
-    st.bins_per_cutoff = h->beds[0]->P.bin_reach > 0 ? h->beds[0]->P.bin_reach : 1;
+    st.bins_per_cutoff = bin_cfg(h->beds[0]).reach;
+    st.bin_order = bin_cfg(h->beds[0]).zfast;
     *out = st;
     return rc;
   }
@@ -2582,7 +2634,8 @@ int sedi_get_stats(sedi_handle* h, sedi_stats* out) {
   const bool tuned = h->prm.substep_variant >= 0 || h->form == FORM_FP64 || !h->tuned_key.empty();
   h->stats.substep_variant = tuned ? h->variant : -1;
   h->stats.substep_block = tuned ? substep_block(h->variant) : 0;
-  h->stats.bins_per_cutoff = h->P.bin_reach > 0 ? h->P.bin_reach : 1;
+  h->stats.bins_per_cutoff = bin_cfg(h).reach;
+  h->stats.bin_order = bin_cfg(h).zfast;
   *out = h->stats;
   return rc;
 }

@@ -57,7 +57,7 @@ class SediParams(C.Structure):
         ("shift_eps", _I), ("shift_mom", _I), ("shift_force", _I),
         ("precision_form", _I), ("nbr_capacity", _I), ("use_graphs", _I), ("substep_variant", _I),
         ("n_beds", _I), ("profile", _I), ("use_cnn_guess", _I), ("ens_persistent", _I),
-        ("bins_per_cutoff", _I), ("cnn_scale", _D * 4),
+        ("bin_order", _I), ("bins_per_cutoff", _I), ("cnn_scale", _D * 4),
         ("seed", C.c_uint64),
     ]
 
@@ -65,7 +65,7 @@ class SediParams(C.Structure):
 class SediStats(C.Structure):
     _fields_ = [("substeps", _L), ("rebuilds", _L), ("averages", _L), ("cg_iterations", _L),
                 ("max_neighbors", _I), ("nbr_capacity", _I), ("substep_variant", _I),
-                ("substep_block", _I), ("bins_per_cutoff", _I), ("pad", _I)]
+                ("substep_block", _I), ("bins_per_cutoff", _I), ("bin_order", _I)]
 
 
 class SediError(RuntimeError):
@@ -464,4 +464,4 @@ class Sedi:
     def stats(self) -> dict:
         s = SediStats()
         self._check(lib().sedi_get_stats(self.h, C.byref(s)))
-        return {k: getattr(s, k) for k, _ in SediStats._fields_ if k != "pad"}
+        return {k: getattr(s, k) for k, _ in SediStats._fields_}

@@ -182,9 +182,10 @@ def test_tuned_ensemble_keeps_each_bed_bits(ens):
     g.step(20)
     st = g.stats()
     assert st["substep_variant"] in (5, 7, 6, 0) and st["bins_per_cutoff"] in (1, 2)
+    assert st["bin_order"] in (0, 1)
     got = [g.get_particles(bed=b) for b in range(len(idx))]
     for k, b in enumerate(idx):
-        s = make_single(prm, beds[b], substep_variant=5, bins_per_cutoff=1)
+        s = make_single(prm, beds[b], substep_variant=5, bins_per_cutoff=1, bin_order=0)
         s.step(200)
         s.step(20)
         for a, c in zip(got[k], s.get_particles()):

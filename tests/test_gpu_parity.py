@@ -389,21 +389,24 @@ def test_substep_variants_bit_identical(small, form):
 
 @pytest.mark.parametrize("variant", [5, 8])
 def test_bins_per_cutoff_change_no_result(small, variant):
-    """Bins of one list cutoff (27-bin stencil) or of half a cutoff (125 bins): every
-    list holds its partners in caller-index order, so lists, springs, trajectory and
-    averaging are the same bits."""
+    """Bins of one list cutoff (27-bin stencil) or of half a cutoff (125 bins), stored x
+    fastest or z fastest: every list holds its partners in caller-index order, so lists,
+    springs, trajectory and averaging are the same bits."""
     prm, parts = small
     out = []
-    for R in (1, 2):
-        g = sedi.Sedi(dict(prm, precision_form="split", substep_variant=variant, bins_per_cutoff=R))
+    for R, order in ((1, 0), (2, 0), (1, 1), (2, 1)):
+        g = sedi.Sedi(dict(prm, precision_form="split", substep_variant=variant, bins_per_cutoff=R,
+                           bin_order=order))
         g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
         g.step(60)
         eps, _, F = g.average()
-        assert g.stats()["bins_per_cutoff"] == R
+        st = g.stats()
+        assert st["bins_per_cutoff"] == R and st["bin_order"] == order
         out.append((*g.get_particles(), eps, F, *g.neighbors(), *g.contacts()))
     assert len(out[0][-2]) > 10
-    for a, b in zip(*out):
-        assert np.array_equal(a, b)
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            assert np.array_equal(a, b)
 
 
 def test_pair_list_contacts_match_loop(small):
@@ -439,10 +442,11 @@ def test_autotuner_chooses_and_caches(small, tmp_path, monkeypatch):
     g.step(10)
     st = g.stats()
     assert 0 <= st["substep_variant"] < 9 and st["substep_block"] in (64, 128, 256)
-    assert st["bins_per_cutoff"] in (1, 2)
+    assert st["bins_per_cutoff"] in (1, 2) and st["bin_order"] in (0, 1)
     lines = cache.read_text().splitlines()
     assert len(lines) == 1 and f"N={n}|" in lines[0] and '"median_us"' in lines[0]
-    assert f'"bins_per_cutoff": {st["bins_per_cutoff"]}' in lines[0] and '"R2"' in lines[0]
+    assert f'"bins_per_cutoff": {st["bins_per_cutoff"]}' in lines[0] and '"R2z"' in lines[0]
+    assert '"bin_order": "%s"' % "xz"[st["bin_order"]] in lines[0]
     # a second handle on the same workload takes the cached choice without re-timing
     h = sedi.Sedi(dict(prm, precision_form="split"))
     h.set_particles(sub["x"], sub["v"], sub["w"], sub["d"], sub["rho"])
@@ -450,9 +454,10 @@ def test_autotuner_chooses_and_caches(small, tmp_path, monkeypatch):
     h.step(10)
     assert h.stats()["substep_variant"] == st["substep_variant"]
     assert h.stats()["bins_per_cutoff"] == st["bins_per_cutoff"]
+    assert h.stats()["bin_order"] == st["bin_order"]
     assert len(cache.read_text().splitlines()) == 1
     # the tuned run is the same trajectory as a fixed variant on bins of one cutoff
-    f = sedi.Sedi(dict(prm, precision_form="split", substep_variant=0, bins_per_cutoff=1))
+    f = sedi.Sedi(dict(prm, precision_form="split", substep_variant=0, bins_per_cutoff=1, bin_order=0))
     f.set_particles(sub["x"], sub["v"], sub["w"], sub["d"], sub["rho"])
     f.step(200)
     f.step(10)
