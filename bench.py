@@ -355,6 +355,7 @@ def gpu_arm(args):
                            "settle_steps_untimed": args.settle,
                            "substep_variant": {"variant": variant, "block": st1["substep_block"],
                                                "bins_per_cutoff": st1["bins_per_cutoff"],
+                                               "bin_order": "xz"[st1["bin_order"]] + " fastest",
                                                "chosen_by": "autotuner"},
                            "l2": "not flushed: the particle state (~2 GB) is larger than L2",
                            "parallelism": "independent bed per GPU" if world > 1 else "1 GPU"},
@@ -621,7 +622,8 @@ def ensemble_leg(steps=3, warmup=2, settle=11):
                                 "beds, grid.y = bed), then one batched deposition and one "
                                 "persistent smoothing launch for all beds",
             "tuned": {"substep_variant": tuned["substep_variant"], "block": tuned["substep_block"],
-                      "bins_per_cutoff": tuned["bins_per_cutoff"], "settle_steps_untimed": settle},
+                      "bins_per_cutoff": tuned["bins_per_cutoff"],
+                      "bin_order": "xz"[tuned["bin_order"]] + " fastest", "settle_steps_untimed": settle},
             "timing": "CUDA events on the launching stream around the steps (the averagings "
                       "synchronise the host once per handle per step)"}
 
