@@ -166,13 +166,19 @@ struct Stencil {
   int32_t nb[6];
 };
 
+// n / d for 32-bit n from M = ceil(2^64 / d) (M = 0 for d = 1): floor(n M / 2^64) is
+// exact, the excess n (M - 2^64/d) / 2^64 < 2^-32 <= 1/d.
+__device__ __forceinline__ uint32_t div_magic(uint32_t n, uint64_t M) {
+  return M ? (uint32_t)__umul64hi((uint64_t)n, M) : n;
+}
+
 __device__ __forceinline__ Stencil stencil_of(const SmoothMeshDev& m, int64_t c) {
   const uint32_t nx = m.nc[0], ny = m.nc[1], nz = m.nc[2];
   const uint32_t cc = (uint32_t)c;
-  const uint32_t ix = cc % nx;
-  const uint32_t t = cc / nx;
-  const uint32_t iy = t % ny;
-  const uint32_t iz = t / ny;
+  const uint32_t t = div_magic(cc, m.div_x);
+  const uint32_t iz = div_magic(cc, m.div_xy);
+  const uint32_t ix = cc - t * nx;
+  const uint32_t iy = t - iz * ny;
   const uint32_t idx[3] = {ix, iy, iz};
   const uint32_t n[3] = {nx, ny, nz};
   const int32_t stride[3] = {1, (int32_t)nx, (int32_t)(nx * ny)};
@@ -351,6 +357,28 @@ __global__ void __launch_bounds__(kThreads, smooth_blocks_per_sm<T>()) k_smooth(
   MeshState* ms = (MeshState*)a.pairs;
   __shared__ double s_sums[kMaxF * kQ];
   __shared__ int s_K;
+  // the mesh of the units being walked and its solver state for the current pass, in
+  // shared memory (every thread of a block walks the same units, so a change of mesh is
+  // seen by the whole block at once)
+  static_assert(sizeof(SmoothMeshDev) % 16 == 0, "mesh entries are copied as 16-byte words");
+  __shared__ SmoothMeshDev s_md;
+  __shared__ int s_kf[kMaxF], s_zero[kMaxF], s_done[kMaxF];
+  __shared__ double s_shd[kMaxF];
+  auto load_mesh = [&](int bi) {
+    __syncthreads();
+    const int4* src = reinterpret_cast<const int4*>(a.mesh + bi);
+    int4* dst = reinterpret_cast<int4*>(&s_md);
+    for (int q = threadIdx.x; q < (int)(sizeof(SmoothMeshDev) / 16); q += blockDim.x) dst[q] = src[q];
+    if (threadIdx.x < kMaxF) {
+      const int f = threadIdx.x;
+      const MeshState& st = ms[bi];
+      s_kf[f] = f < nf ? ldi(&st.k[f]) : 0;
+      s_zero[f] = f < nf ? ldi(&st.zero[f]) : 0;
+      s_done[f] = f < nf ? ldi(&st.done[f]) : 1;
+      s_shd[f] = f < nf ? ldd(&st.shift[f]) : 0.0;
+    }
+    __syncthreads();
+  };
   int slot = 0;
 
   for (int m = 0; m < a.n_tau; ++m) {
@@ -372,10 +400,14 @@ __global__ void __launch_bounds__(kThreads, smooth_blocks_per_sm<T>()) k_smooth(
     for (int round = 0; round < kMaxRounds; ++round) {
       // ---- true residual r = b - A x (wide), its narrow copy (interleaved, in d[0])
       //      and the unit sums |r|^2, sum r, |b|^2
+      int cur_bi = -1;
       for (int64_t u = u_begin; u < u_end; ++u) {
         const int bi = a.unit_bed[u];
-        const SmoothMeshDev& md = a.mesh[bi];
-        const MeshState& st = ms[bi];
+        if (bi != cur_bi) {
+          load_mesh(bi);
+          cur_bi = bi;
+        }
+        const SmoothMeshDev& md = s_md;
         const int64_t c = (u - md.u0) * kThreads + threadIdx.x;
         const bool in = c < md.C;
         Acc v[kMaxF][kQ];
@@ -386,7 +418,7 @@ __global__ void __launch_bounds__(kThreads, smooth_blocks_per_sm<T>()) k_smooth(
         T czm{}, czp{};
         Acc wz = Acc(1);
         if constexpr (GR) {
-          const int kz = (int)((uint32_t)(in ? c : 0) / (uint32_t)(md.nc[0] * md.nc[1]));
+          const int kz = (int)div_magic((uint32_t)(in ? c : 0), md.div_xy);
           czm = W::from_d(md.z.cz[ph][2 * kz]);
           czp = W::from_d(md.z.cz[ph][2 * kz + 1]);
           wz = (Acc)md.z.w[kz];
@@ -395,7 +427,7 @@ __global__ void __launch_bounds__(kThreads, smooth_blocks_per_sm<T>()) k_smooth(
         for (int f = 0; f < kMaxF; ++f) {
           v[f][0] = v[f][1] = v[f][2] = v[f][3] = Acc(0);
           rn.v[f] = N(0);
-          if (f >= nf || !in || (round > 0 && ldi(&st.done[f]))) continue;
+          if (f >= nf || !in || (round > 0 && s_done[f])) continue;
           const T* X = (const T*)md.x + f * md.C;
           const T xc = W::ld(X + c);
           auto subq = [](T p, T q) { return W::subq(p, q); };
@@ -503,10 +535,14 @@ __global__ void __launch_bounds__(kThreads, smooth_blocks_per_sm<T>()) k_smooth(
       // ---- Chebyshev steps j = 1..K; step 1 also applies the shift (or zeroes x)
       const int J = K > 0 ? K : 1;
       for (int j = 1; j <= J; ++j) {
+        int cur_bi = -1;
         for (int64_t u = u_begin; u < u_end; ++u) {
           const int bi = a.unit_bed[u];
-          const SmoothMeshDev& md = a.mesh[bi];
-          const MeshState& st = ms[bi];
+          if (bi != cur_bi) {
+            load_mesh(bi);
+            cur_bi = bi;
+          }
+          const SmoothMeshDev& md = s_md;
           const int64_t c = (u - md.u0) * kThreads + threadIdx.x;
           if (c >= md.C) continue;
           int kf[kMaxF];
@@ -516,7 +552,7 @@ __global__ void __launch_bounds__(kThreads, smooth_blocks_per_sm<T>()) k_smooth(
           for (int f = 0; f < kMaxF; ++f) sh[f] = N(0);
 #pragma unroll
           for (int f = 0; f < kMaxF; ++f) {
-            kf[f] = f < nf ? ldi(&st.k[f]) : 0;
+            kf[f] = s_kf[f];
             any |= kf[f] >= j;
           }
           if (j == 1) {
@@ -525,10 +561,10 @@ __global__ void __launch_bounds__(kThreads, smooth_blocks_per_sm<T>()) k_smooth(
 #pragma unroll
             for (int f = 0; f < kMaxF; ++f) {
               if (f >= nf) continue;
-              const double s = ldd(&st.shift[f]);
+              const double s = s_shd[f];
               sh[f] = (N)s;
               if (kf[f] == 0) {
-                if (round == 0 && ldi(&st.zero[f])) X[f * md.C + c] = W::zero();
+                if (round == 0 && s_zero[f]) X[f * md.C + c] = W::zero();
                 else if (s != 0.0) X[f * md.C + c] = W::add(W::ld(X + f * md.C + c), W::from_d(s));
               }
             }
@@ -565,7 +601,7 @@ __global__ void __launch_bounds__(kThreads, smooth_blocks_per_sm<T>()) k_smooth(
           bool any_axis = false;
           N czn[2] = {N(0), N(0)};
           if constexpr (GR) {
-            const int kz = (int)((uint32_t)c / (uint32_t)(md.nc[0] * md.nc[1]));
+            const int kz = (int)div_magic((uint32_t)c, md.div_xy);
             if constexpr (sizeof(N) == 4) {
               czn[0] = md.z.czf[ph][2 * kz];
               czn[1] = md.z.czf[ph][2 * kz + 1];
@@ -627,7 +663,7 @@ __global__ void __launch_bounds__(kThreads, smooth_blocks_per_sm<T>()) k_smooth(
             const int64_t k = f * md.C + c;
             T xv = W::ld(X + k);
             if (j == 1) {
-              xv = W::add(xv, W::from_d(ldd(&st.shift[f])));  // projection shift
+              xv = W::add(xv, W::from_d(s_shd[f]));  // projection shift
               q.v[f] = q.v[f] - sh[f];                         // narrow r - s
             }
             q.v[f] = q.v[f] - ad;
@@ -1111,6 +1147,9 @@ static void smooth_mesh_layout(int form, int scheme, const SmoothMesh& in, Smoot
     m.nc[k] = in.nc[k];
     m.per[k] = in.per[k];
   }
+  auto magic = [](uint64_t d) -> uint64_t { return d <= 1 ? 0 : ~(uint64_t)0 / d + 1; };
+  m.div_x = magic((uint64_t)in.nc[0]);
+  m.div_xy = magic((uint64_t)in.nc[0] * (uint64_t)in.nc[1]);
   m.z = in.z;
   const bool gr = in.z.cz[0] != nullptr;
   smooth_spec(in.coef, 1.0, gr ? in.z.zmax[0] : 0.0, &m.sp[0]);

@@ -171,8 +171,9 @@ struct SmoothSpec {
   float coef_hi[3], coef_lo[3];      // coef as an FP32 pair: hi = fl32(c), lo = fl32(c - hi)
 };
 
-// The same, as the kernel sees it (device table, built by launch_smooth_batch).
-struct SmoothMeshDev {
+// The same, as the kernel sees it (device table, built by launch_smooth_batch; the
+// grid solver copies an entry to shared memory as 16-byte words).
+struct alignas(16) SmoothMeshDev {
   void* x;
   const void* guess;
   void* b;           // [nf][C] right-hand side (wide word)
@@ -183,6 +184,7 @@ struct SmoothMeshDev {
   int* iters;
   int64_t C, u0, nu;  // cells, first unit, units
   int32_t nc[3], per[3];
+  uint64_t div_x, div_xy;            // ceil(2^64 / nx), ceil(2^64 / (nx ny)) (0: divisor 1)
   int32_t cl_size, cl_planes;        // cluster solver: CTAs, z-planes per CTA (0: grid solver)
   SmoothSpec sp[2];  // [0]: backward-Euler steps (coef); [1]: BDF2 steps (2/3 coef)
   SmoothZ z;         // graded z mesh (null: uniform)
