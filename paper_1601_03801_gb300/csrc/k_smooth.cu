@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(kThreads, smooth_blocks_per_sm<T>()) k_smooth(
   const int64_t U = a.U;
   const int64_t u_begin = (int64_t)blockIdx.x * U / G, u_end = (int64_t)(blockIdx.x + 1) * U / G;
   MeshState* ms = (MeshState*)a.pairs;
-  __shared__ double s_sums[kMaxF * kQ];
+  __shared__ double s_sums[(kThreads / 32) * kQ];
   __shared__ int s_K;
   // the mesh of the units being walked and its solver state for the current pass, in
   // shared memory (every thread of a block walks the same units, so a change of mesh is
@@ -453,67 +453,78 @@ __global__ void __launch_bounds__(kThreads, smooth_blocks_per_sm<T>()) k_smooth(
         unit_sums<Acc>(v, nf, md.part + (u - md.u0) * (kMaxF * kQ));
       }
       if (!grid_barrier(a.ctl, G, a.spin_limit)) return;
-      // ---- owners: per-(mesh, field) sums over the mesh's units, decisions
-      for (int bi = blockIdx.x; bi < a.B; bi += G) {
+      // ---- owners: one block per (mesh, field): the field's sums over the mesh's units
+      //      (thread t adds units t, t + 256, ... in order, then a fixed tree: the same
+      //      association whatever the grid or the batch), then its decisions
+      for (int64_t it = blockIdx.x; it < (int64_t)a.B * nf; it += G) {
+        const int bi = (int)(it / nf), f = (int)(it % nf);
         const SmoothMeshDev& md = a.mesh[bi];
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        for (int pq = wid; pq < nf * kQ; pq += kThreads / 32) {
-          const int f = pq / kQ, q = pq % kQ;
-          double s = 0.0;
-          for (int64_t u = lane; u < md.nu; u += 32) s += ldd(md.part + u * (kMaxF * kQ) + f * kQ + q);
+        double sq[kQ] = {0.0, 0.0, 0.0, 0.0};
+        for (int64_t u = threadIdx.x; u < md.nu; u += kThreads) {
+          const double* pu = md.part + u * (kMaxF * kQ) + f * kQ;
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-          if (lane == 0) s_sums[f * kQ + q] = s;
+          for (int q = 0; q < kQ; ++q) sq[q] += ldd(pu + q);
+        }
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+          double v = sq[q];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) s_sums[wid * kQ + q] = v;
         }
         __syncthreads();
-        if (threadIdx.x < kMaxF) {
-          const int f = threadIdx.x;
+        if (threadIdx.x == 0) {
+          double tot[kQ];
+#pragma unroll
+          for (int q = 0; q < kQ; ++q) {
+            tot[q] = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) tot[q] += s_sums[w * kQ + q];
+          }
           MeshState& st = ms[bi];
           int k = 0, done = 1, zero = 0, total = 0;
           double shift = 0.0, bb = 0.0;
-          if (f < nf) {
-            done = round == 0 ? 0 : st.done[f];
-            zero = round == 0 ? 0 : st.zero[f];
-            total = round == 0 ? 0 : st.total[f];
-            bb = round == 0 ? s_sums[f * kQ + 2] : st.bb[f];
-            if (round == 0) zero = !(bb > 0.0);
-            if (!done) {
-              const double rr = s_sums[f * kQ + 0], sr = s_sums[f * kQ + 1];
-              const double Cd = (double)md.C;
-              if (zero) {
+          done = round == 0 ? 0 : st.done[f];
+          zero = round == 0 ? 0 : st.zero[f];
+          total = round == 0 ? 0 : st.total[f];
+          bb = round == 0 ? tot[2] : st.bb[f];
+          if (round == 0) zero = !(bb > 0.0);
+          if (!done) {
+            const double rr = tot[0], sr = tot[1];
+            const double Cd = (double)md.C;
+            if (zero) {
+              done = 1;
+            } else {
+              double rrp;
+              if (GR) {
+                // the shift keeps sum(w x) = sum(w b); |r - s|^2 = |r|^2 - 2 s sum r + C s^2
+                shift = tot[3] / md.z.wsum;
+                rrp = fmax(rr - 2.0 * shift * sr + Cd * shift * shift, 0.0);
+              } else {
+                shift = sr / Cd;
+                rrp = fmax(rr - sr * sr / Cd, 0.0);
+              }
+              if (rrp <= a.rtol2 * bb) {
                 done = 1;
               } else {
-                double rrp;
-                if (GR) {
-                  // the shift keeps sum(w x) = sum(w b); |r - s|^2 = |r|^2 - 2 s sum r + C s^2
-                  shift = s_sums[f * kQ + 3] / md.z.wsum;
-                  rrp = fmax(rr - 2.0 * shift * sr + Cd * shift * shift, 0.0);
-                } else {
-                  shift = sr / Cd;
-                  rrp = fmax(rr - sr * sr / Cd, 0.0);
-                }
-                if (rrp <= a.rtol2 * bb) {
+                // |r_k| <= 2 sig^k |r_0|: enough steps for the tolerance, or for the
+                // reduction the narrow word can deliver in one round
+                const double need = fmax(0.5 * sqrt(a.rtol2 * bb / rrp), W::kFloor);
+                const double sig = md.sp[ph].sig;
+                k = sig > 0.0 ? (int)ceil(log(need) / log(sig)) : 1;
+                if (k < 1) k = 1;
+                if (k > kMaxStepsRound) k = kMaxStepsRound;
+                if (total + k > a.max_iter) k = a.max_iter - total;
+                if (k <= 0) {
+                  k = 0;
                   done = 1;
+                  atomicCAS((int*)&a.ctl->cg_status, 0, SEDI_EDIVERGED);
                 } else {
-                  // |r_k| <= 2 sig^k |r_0|: enough steps for the tolerance, or for the
-                  // reduction the narrow word can deliver in one round
-                  const double need = fmax(0.5 * sqrt(a.rtol2 * bb / rrp), W::kFloor);
-                  const double sig = md.sp[ph].sig;
-                  k = sig > 0.0 ? (int)ceil(log(need) / log(sig)) : 1;
-                  if (k < 1) k = 1;
-                  if (k > kMaxStepsRound) k = kMaxStepsRound;
-                  if (total + k > a.max_iter) k = a.max_iter - total;
-                  if (k <= 0) {
-                    k = 0;
-                    done = 1;
-                    atomicCAS((int*)&a.ctl->cg_status, 0, SEDI_EDIVERGED);
-                  } else {
-                    total += k;
-                  }
+                  total += k;
                 }
               }
-              if (done && md.iters) atomicAdd(md.iters + f, total);
             }
+            if (done && md.iters) atomicAdd(md.iters + f, total);
           }
           st.k[f] = k;
           st.done[f] = done;
