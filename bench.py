@@ -851,11 +851,12 @@ def reference_arm(args):
 
 def kernels_only(args):
     """Run a workload for a few steps without timing (profiling driver: the command
-    an ncu capture wraps).  --case bed200k (default), large, patch, or small."""
+    an ncu capture wraps).  --case bed200k (default), large, patch, smooth (the
+    smoother alone on the large bed's mesh) or small."""
     import torch
 
     from paper_1601_03801_gb300 import sedi
-    from paper_1601_03801_gb300.workloads import bed_case, large_case, large_patch, small_case
+    from paper_1601_03801_gb300.workloads import bed_case, default_params, large_case, large_patch, small_case
 
     torch.cuda.set_device(0)
     if args.case == "large":
@@ -864,6 +865,18 @@ def kernels_only(args):
         # a 100 x 100 mm patch of the large bed (1.25M spheres, a few GB on the device):
         # the profiling case whose working set is larger than L2
         prm, parts, fl = large_patch(*large_case())
+    elif args.case == "smooth":
+        # the smoother alone: 7 seeded fields on the large bed's 256 x 128 x 64 mesh
+        from paper_1601_03801_gb300.workloads import random_fields
+        prm = default_params(hi=(400e-3, 200e-3, 100e-3), ncell=(256, 128, 64), wall_hi=(0, 0, 0),
+                             bandwidth=(1.5e-3,) * 3)
+        g = sedi.Sedi(dict(prm, precision_form=args.form))
+        phi = random_fields(prm["ncell"], 7, 3)
+        for _ in range(args.settle + args.steps):
+            _, it = g.smooth(phi)
+        print(json.dumps({"mode": "kernels", "case": "smooth", "form": args.form,
+                          "calls": args.settle + args.steps, "steps_per_field": it.tolist()}))
+        return
     elif args.case == "small":
         prm, parts = small_case(parity_addon=True)
         fl = {"U": None}
@@ -905,7 +918,7 @@ def main():
                     help="untimed steps before the warm-up (the method settles the bed further)")
     ap.add_argument("--mode", default="bench", choices=["bench", "kernels"],
                     help="kernels: run a workload untimed (profiling driver)")
-    ap.add_argument("--case", default="bed200k", choices=["bed200k", "large", "patch", "small"],
+    ap.add_argument("--case", default="bed200k", choices=["bed200k", "large", "patch", "smooth", "small"],
                     help="kernels mode: workload")
     ap.add_argument("--form", default="split", choices=["split", "plain", "fp64"])
     ap.add_argument("--with-cnn", action="store_true",
