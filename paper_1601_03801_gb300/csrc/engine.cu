@@ -60,6 +60,7 @@ struct sedi_handle {
   sedi_stats stats{};
   int variant = SUBSTEP_B128;  // substep launch variant in use
   std::string tuned_key;       // workload the variant was tuned for (empty: not tuned)
+  std::string key_cache;       // the workload key of the current particles (empty: stale)
   // profiling: events per captured substep (A: before check, B: before the
   // substep kernel, C: after it) and around deposition / smoothing
   struct GraphEv {
@@ -481,6 +482,7 @@ int set_bins(sedi_handle* h, int R) {
 
 int alloc_particles(sedi_handle* h, int64_t N, double rmax) {
   clear_graphs(h);
+  h->key_cache.clear();
   free_list(h->part_allocs);
   DevState& st = h->st;
   Ctl* ctl = st.ctl;
@@ -687,7 +689,9 @@ struct TuneChoice {
 std::mutex g_tune_mu;
 std::map<std::string, TuneChoice> g_tune_cache;
 
+// The workload key, computed once per particle set (it reads every diameter).
 std::string tune_key(sedi_handle* h) {
+  if (!h->key_cache.empty()) return h->key_cache;
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceProp prop;
@@ -702,7 +706,8 @@ std::string tune_key(sedi_handle* h) {
   std::snprintf(buf, sizeof(buf), "%s sm%d|N=%lld|d=%.3e..%.3e|form=%d|law=%d|lub=%d|fluid=%d%d%d",
                 prop.name, prop.multiProcessorCount, (long long)h->N, dmin, dmax, h->form,
                 h->prm.contact_law, h->P.lubrication, h->P.drag, h->P.pressure_grad, h->P.added_mass);
-  return buf;
+  h->key_cache = buf;
+  return h->key_cache;
 }
 
 TuneChoice tune_file_lookup(const std::string& key) {
@@ -1136,6 +1141,7 @@ int sedi_set_bed(sedi_handle* h, int32_t bed, const double lo[3], const double h
   h->beds[bed] = nb;
   h->ens_dirty = true;
   h->ens_fresh = false;
+  h->key_cache.clear();
   clear_graphs(h);
   return 0;
 }
@@ -1148,6 +1154,7 @@ int sedi_set_particles(sedi_handle* h, int32_t bed, int64_t n, const int64_t* id
   if (!h->beds.empty()) {
     h->ens_dirty = true;
     h->ens_fresh = false;
+    h->key_cache.clear();
     clear_graphs(h);
   }
   ENS_FORWARD(sedi_set_particles(sub, 0, n, id, x, v, omega, d, rho, mem));
@@ -1488,10 +1495,14 @@ static int ens_status(sedi_handle* h) {
 static int ens_autotune(sedi_handle* h) {
   if (h->prm.substep_variant >= 0 || h->form == FORM_FP64 || ens_ext(h)) return 0;
   const int B = (int)h->beds.size();
-  int64_t since = INT64_MAX, ntot = 0, nmin = INT64_MAX, nmax = 0;
+  int64_t since = INT64_MAX;
+  for (sedi_handle* b : h->beds) since = std::min(since, b->since_set);
+  if (since < kTuneAfter) return 0;
+  // the key is computed once per set of beds (it reads every diameter)
+  if (!h->key_cache.empty() && h->key_cache == h->tuned_key) return 0;
+  int64_t ntot = 0, nmin = INT64_MAX, nmax = 0;
   double dmin = 1e300, dmax = 0.0;
   for (sedi_handle* b : h->beds) {
-    since = std::min(since, b->since_set);
     ntot += b->N;
     nmin = std::min(nmin, b->N);
     nmax = std::max(nmax, b->N);
@@ -1500,7 +1511,6 @@ static int ens_autotune(sedi_handle* h) {
       dmax = std::max(dmax, d);
     }
   }
-  if (since < kTuneAfter) return 0;
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceProp prop;
@@ -1511,6 +1521,7 @@ static int ens_autotune(sedi_handle* h) {
                 dmax, h->form, h->prm.contact_law, h->P.lubrication, h->P.drag, h->P.pressure_grad,
                 h->P.added_mass);
   const std::string key = buf;
+  h->key_cache = key;
   if (key == h->tuned_key) return 0;
   int rc = ens_finalize(h);
   if (rc) return rc;
@@ -2473,6 +2484,7 @@ int sedi_load_state(sedi_handle* h, const char* path) {
     if (!rc) h->stats = eh.stats;
     h->ens_dirty = true;
     h->ens_fresh = false;
+    h->key_cache.clear();
     clear_graphs(h);
   }
   std::fclose(f);
