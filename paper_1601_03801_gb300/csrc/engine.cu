@@ -808,15 +808,16 @@ int autotune(sedi_handle* h) {
     CK(cudaStreamSynchronize(h->stream));
     CK(cudaMemcpy(&c0, h->st.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
     const double rate = (double)std::max<int64_t>(c0.rebuilds, 1) / (double)std::max<int64_t>(h->since_set, 1);
-    // R = 2 only while its bins stay few next to the particles (a bin array sweep per
-    // rebuild); a fixed bins_per_cutoff is the only candidate
+    // R = 2 only while its bins stay few next to the particles (a sweep of the bin
+    // arrays per rebuild: 32 per particle at most); a fixed bins_per_cutoff is the only
+    // candidate
     std::vector<int> reaches = {1};
     if (h->prm.bins_per_cutoff > 0) {
       reaches = {h->prm.bins_per_cutoff};
     } else {
       int32_t nb[3];
       int64_t nbins = 0;
-      if (!bins_for(h, 2, nb, &nbins) && nbins <= std::max<int64_t>(16 * h->N, (int64_t)1 << 22))
+      if (!bins_for(h, 2, nb, &nbins) && nbins <= std::max<int64_t>(32 * h->N, (int64_t)1 << 22))
         reaches.push_back(2);
     }
     // every bin size in both storage orders, the current configuration last (a single

@@ -374,14 +374,31 @@ __device__ __forceinline__ void remap_body(const DevState& st, const DevParams& 
     if (omask) {
       const int onn = st.nn[nl][o];
       const int nn = st.nn[ql][i];
+      // the partners' caller indices of both lists (independent loads, issued together)
+      int32_t ou[kMaxCap], nu[kMaxCap];
+      bool sorted = true;
+      for (int kk = 0; kk < onn; ++kk) ou[kk] = st.uid[pb][nbr_index(st.nbr[nl][(int64_t)kk * N + o])];
+      for (int k = 0; k < nn; ++k) nu[k] = st.uid[qb][nbr_index(st.nbr[ql][(int64_t)k * N + i])];
+      for (int kk = 1; kk < onn; ++kk) sorted = sorted && ou[kk - 1] < ou[kk];
+      int kk = 0;
       for (int k = 0; k < nn; ++k) {
-        const int32_t uj = st.uid[qb][nbr_index(st.nbr[ql][(int64_t)k * N + i])];
-        for (int kk = 0; kk < onn; ++kk) {
-          if (!((omask >> kk) & 1u)) continue;
-          if (st.uid[pb][nbr_index(st.nbr[nl][(int64_t)kk * N + o])] != uj) continue;
-          stq(hnew + (int64_t)k * N + i, ldq(hold + (int64_t)kk * N + o));
+        const int32_t uj = nu[k];
+        int hit = -1;
+        if (sorted) {
+          // lists built here hold their partners in caller-index order: one merge walk
+          while (kk < onn && ou[kk] < uj) ++kk;
+          if (kk < onn && ou[kk] == uj) hit = kk;
+        } else {
+          // lists of another order (an imported checkpoint): search
+          for (int q = 0; q < onn; ++q)
+            if (ou[q] == uj) {
+              hit = q;
+              break;
+            }
+        }
+        if (hit >= 0 && ((omask >> hit) & 1u)) {
+          stq(hnew + (int64_t)k * N + i, ldq(hold + (int64_t)hit * N + o));
           nmask |= 1u << k;
-          break;
         }
       }
     }
