@@ -291,58 +291,74 @@ __device__ __forceinline__ void build_body(const DevState& st, const DevParams& 
     int32_t ent[kMaxCap], key[kMaxCap];
     int n = 0;
     const int R = P.bin_reach;
-    for (int oz = -R; oz <= R; ++oz) {
-      int tz = c[2] + oz;
-      if (P.periodic[2]) tz = (tz + P.nb[2]) % P.nb[2];
-      else if (tz < 0 || tz >= P.nb[2]) continue;
-      for (int oy = -R; oy <= R; ++oy) {
-        int ty = c[1] + oy;
-        if (P.periodic[1]) ty = (ty + P.nb[1]) % P.nb[1];
-        else if (ty < 0 || ty >= P.nb[1]) continue;
-        for (int ox = -R; ox <= R; ++ox) {
-          int tx = c[0] + ox;
-          if (P.periodic[0]) tx = (tx + P.nb[0]) % P.nb[0];
-          else if (tx < 0 || tx >= P.nb[0]) continue;
-          const int64_t b = bin_key(tx, ty, tz, P);
-          const int s0 = st.bin_start[b], s1 = s0 + st.bin_count[b];
-          for (int j = s0; j < s1; ++j) {
-            if (j == i) continue;
-            const Quad<S> pj = ldq(pos + j);
-            const double rj = r64[j];
-            float d[3] = {(float)NS::dif(pj.a, pi.a), (float)NS::dif(pj.b, pi.b),
-                          (float)NS::dif(pj.c, pi.c)};
+    // the candidates of sorted positions [s0, s1): FP32 test with a relative margin on
+    // the stored words (the radius from the position record), the exact FP64 predicate
+    // inside the margin
+    auto visit = [&](int s0, int s1) {
+      for (int j = s0; j < s1; ++j) {
+        if (j == i) continue;
+        const Quad<S> pj = ldq(pos + j);
+        float d[3] = {(float)NS::dif(pj.a, pi.a), (float)NS::dif(pj.b, pi.b), (float)NS::dif(pj.c, pi.c)};
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
-              if (P.periodic[a])
-                d[a] = d[a] > P.cf.halfL[a] ? d[a] - P.cf.L[a]
-                                            : (d[a] < -P.cf.halfL[a] ? d[a] + P.cf.L[a] : d[a]);
-            const float d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            const float s = rif + (float)rj;
-            const float rc = s + fr * s + sk;
-            const float rc2 = rc * rc;
-            bool in;
-            if (d2 < rc2 * (1.0f - 2e-4f)) in = true;
-            else if (d2 > rc2 * (1.0f + 2e-4f)) in = false;
-            else {
-              const double xi[3] = {NS::d(pi.a), NS::d(pi.b), NS::d(pi.c)};
-              const double xj[3] = {NS::d(pj.a), NS::d(pj.b), NS::d(pj.c)};
-              in = listed_exact(xi, xj, ri, rj, P);
+        for (int a = 0; a < 3; ++a)
+          if (P.periodic[a])
+            d[a] = d[a] > P.cf.halfL[a] ? d[a] - P.cf.L[a] : (d[a] < -P.cf.halfL[a] ? d[a] + P.cf.L[a] : d[a]);
+        const float d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        const float s = rif + (float)NS::f(pj.d);
+        const float rc = s + fr * s + sk;
+        const float rc2 = rc * rc;
+        bool in;
+        if (d2 < rc2 * (1.0f - 2e-4f)) in = true;
+        else if (d2 > rc2 * (1.0f + 2e-4f)) in = false;
+        else {
+          const double xi[3] = {NS::d(pi.a), NS::d(pi.b), NS::d(pi.c)};
+          const double xj[3] = {NS::d(pj.a), NS::d(pj.b), NS::d(pj.c)};
+          in = listed_exact(xi, xj, ri, r64[j], P);
+        }
+        if (in) {
+          if (n < P.cap) {
+            const int32_t uj = uid[j];
+            int k = n;
+            while (k > 0 && key[k - 1] > uj) {
+              key[k] = key[k - 1];
+              ent[k] = ent[k - 1];
+              --k;
             }
-            if (in) {
-              if (n < P.cap) {
-                const int32_t uj = uid[j];
-                int k = n;
-                while (k > 0 && key[k - 1] > uj) {
-                  key[k] = key[k - 1];
-                  ent[k] = ent[k - 1];
-                  --k;
-                }
-                key[k] = uj;
-                ent[k] = j | (ui < uj ? (int32_t)kFirstBit : 0);
-              }
-              ++n;
-            }
+            key[k] = uj;
+            ent[k] = j | (ui < uj ? (int32_t)kFirstBit : 0);
           }
+          ++n;
+        }
+      }
+    };
+    // the stencil as runs along the bins' fastest axis: 2R + 1 consecutive bins are
+    // one range of sorted positions unless the run wraps a periodic face
+    const int fa = P.bin_zfast ? 2 : 0;           // fastest axis
+    const int sa = 1, ta = P.bin_zfast ? 0 : 2;  // the other two
+    for (int ot = -R; ot <= R; ++ot) {
+      int ct = c[ta] + ot;
+      if (P.periodic[ta]) ct = (ct + P.nb[ta]) % P.nb[ta];
+      else if (ct < 0 || ct >= P.nb[ta]) continue;
+      for (int os = -R; os <= R; ++os) {
+        int cs = c[sa] + os;
+        if (P.periodic[sa]) cs = (cs + P.nb[sa]) % P.nb[sa];
+        else if (cs < 0 || cs >= P.nb[sa]) continue;
+        int t[3];
+        t[ta] = ct;
+        t[sa] = cs;
+        const int lo = c[fa] - R, hi = c[fa] + R;
+        if (P.periodic[fa] && (lo < 0 || hi >= P.nb[fa])) {
+          for (int of = lo; of <= hi; ++of) {
+            t[fa] = (of + P.nb[fa]) % P.nb[fa];
+            const int64_t bk = bin_key(t[0], t[1], t[2], P);
+            visit(st.bin_start[bk], st.bin_start[bk] + st.bin_count[bk]);
+          }
+        } else {
+          t[fa] = lo > 0 ? lo : 0;
+          const int64_t b0 = bin_key(t[0], t[1], t[2], P);
+          t[fa] = hi < P.nb[fa] - 1 ? hi : P.nb[fa] - 1;
+          const int64_t b1 = bin_key(t[0], t[1], t[2], P);
+          visit(st.bin_start[b0], st.bin_start[b1] + st.bin_count[b1]);
         }
       }
     }
