@@ -634,6 +634,30 @@ def test_checkpoint_resume_bit_identical(small, tmp_path, variant, resume_varian
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("bins,order", [(2, 1), (1, 1), (2, 0)])
+def test_checkpoint_keeps_its_bins(small, tmp_path, bins, order):
+    """A checkpoint stores its particles in the order of its bins (size and storage
+    order); a handle whose own bins differ loads it on the stored bins and resumes the
+    same trajectory."""
+    prm, parts = small
+    g = sedi.Sedi(dict(prm, precision_form="split", substep_variant=8, bins_per_cutoff=bins,
+                       bin_order=order))
+    g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+    g.step(30)
+    path = tmp_path / "ck.bin"
+    g.save_state(path)
+    g.step(30)
+    ref = g.get_particles()
+    h = sedi.Sedi(dict(prm, precision_form="split", substep_variant=8))
+    h.load_state(path)
+    h.n = len(parts["x"])
+    st = h.stats()
+    assert st["bins_per_cutoff"] == bins and st["bin_order"] == order
+    h.step(30)
+    for a, b in zip(ref, h.get_particles()):
+        assert np.array_equal(a, b)
+
+
 def test_single_particle_and_boundaries():
     prm = default_params()
     hi = np.array(prm["hi"])
