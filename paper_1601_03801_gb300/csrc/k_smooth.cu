@@ -298,27 +298,37 @@ struct alignas(16) MeshState {
   double bb[kMaxF];      // |b|^2
 };
 
-// Per-block reduction of the kQ sums of nf fields for one unit (fixed order).
+// Per-block reduction of the kQ sums of nf fields for one unit (fixed order).  The
+// warp stage is a butterfly reduce-scatter of the 32 (field, sum) slots: at each of
+// five rounds a lane keeps half of its slots and adds its partner's copy of them, so
+// lane l ends with the warp's sum of slot l after 31 additions (a plain shuffle
+// reduction of every slot would take 5 x 32; the FP64 pipe is the narrow one).
 template <class Acc>
 __device__ __forceinline__ void unit_sums(const Acc (&v)[kMaxF][kQ], int nf, double* out) {
-  __shared__ Acc red[kThreads / 32][kMaxF][kQ];
+  static_assert(kMaxF * kQ == 32, "one slot per lane");
+  __shared__ Acc red[kThreads / 32][kMaxF * kQ];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  Acc a[32];
 #pragma unroll
   for (int f = 0; f < kMaxF; ++f)
 #pragma unroll
-    for (int q = 0; q < kQ; ++q) {
-      if (f >= nf) continue;
-      Acc t = v[f][q];
+    for (int q = 0; q < kQ; ++q) a[f * kQ + q] = v[f][q];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) red[wid][f][q] = t;
+  for (int o = 16; o > 0; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < o; ++k) {
+      const Acc mine = up ? a[k + o] : a[k];
+      const Acc give = up ? a[k] : a[k + o];
+      a[k] = mine + __shfl_xor_sync(0xffffffffu, give, o);
     }
+  }
+  red[wid][lane] = a[0];
   __syncthreads();
   if (threadIdx.x < nf * kQ) {
-    const int f = threadIdx.x / kQ, q = threadIdx.x % kQ;
     double s = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) s += (double)red[w][f][q];
-    out[f * kQ + q] = s;
+    for (int w = 0; w < kThreads / 32; ++w) s += (double)red[w][threadIdx.x];
+    out[threadIdx.x] = s;
   }
   __syncthreads();
 }
