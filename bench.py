@@ -51,13 +51,14 @@ KERNEL_SOURCES = ["paper_1601_03801_gb300/csrc/k_force.cu", "paper_1601_03801_gb
                   "paper_1601_03801_gb300/csrc/common.cuh", "paper_1601_03801_gb300/csrc/dd.cuh"]
 
 
-PAIRS_VARIANT = 8  # substep variant of the pair list (two kernels per substep)
+PAIR_VARIANTS = (8, 9)  # substep variants of the pair list (two kernels per substep)
 
 
 def substep_kernel_name(variant, form="split"):
     """The kernel(s) the roofline line measures for a substep launch variant."""
-    if variant == PAIRS_VARIANT and form != "fp64":
-        return f"k_pair_forces<{form}> + k_substep<{form}, gather>"
+    if variant in PAIR_VARIANTS and form != "fp64":
+        sched = ", ordered" if variant == 9 else ""
+        return f"k_pair_forces<{form}{sched}> + k_substep<{form}, gather>"
     return f"k_substep<{form}>"
 
 
@@ -72,10 +73,13 @@ def kernel_hash():
 def measured_traffic(variant, path):
     """DRAM bytes per particle-substep of the pair list's substep launch (pair-force and
     gather kernels) from a committed ncu summary, if it was taken on the current kernel
-    source (other launch variants: none committed)."""
-    if variant != PAIRS_VARIANT or not os.path.exists(path):
+    source and launch variant (other launch variants: none committed)."""
+    if variant not in PAIR_VARIANTS or not os.path.exists(path):
         return None, None
     txt = open(path).read()
+    v = re.search(r"substep_variant:\s*(\d+)", txt)
+    if not v or int(v.group(1)) != variant:
+        return None, None
     m = re.search(r"dram_bytes_per_particle_substep:\s*([0-9.eE+-]+)", txt)
     k = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
     if not m or not k or k.group(1) != kernel_hash():
@@ -284,7 +288,7 @@ def launches_per_step(variant, rebuilds, steps, cells):
     with the pair list), 13 per list rebuild taken, then deposition, fixed point ->
     smoothing word, the smoother (the cluster solver: one launch; the grid solver:
     barrier reset + cooperative launch) and the outputs."""
-    per_sub = 2 if variant == PAIRS_VARIANT else 1
+    per_sub = 2 if variant in PAIR_VARIANTS else 1
     per_avg = 4 if cells <= 131072 else 5
     return steps * (1 + per_sub * SUBSTEPS + per_avg) + 13 * rebuilds
 

@@ -147,7 +147,10 @@ typedef struct sedi_params {
                                               6: 128 x 8, 7: 64 x 12 with a per-particle
                                               pair loop; 8: the pair list (each listed
                                               pair evaluated once by one thread, then a
-                                              per-particle gather; two launches).  With
+                                              per-particle gather; two launches); 9: the
+                                              pair list with its pairs taken in list
+                                              order from a work counter (one wave of
+                                              blocks, 128 consecutive pairs a claim).  With
                                               lift or lub_tangential on the loop at
                                               128 x 6 runs.  The split form gives
                                               bit-identical results across variants, the

@@ -36,6 +36,8 @@ struct Ctl {
   uint32_t blocks_done;    // completion counter of the substep kernel
   uint32_t npair;          // interaction pairs of the current lists (pair list)
   int32_t ens_rebuild;     // ensembles: some bed needs a list rebuild after the last substep
+  uint32_t pair_next;      // ordered pair schedule: next chunk of the pair list to claim
+  uint32_t pair_done;      // ordered pair schedule: blocks finished (the last resets both)
 };
 
 // Constants of the force arithmetic, precomputed on the host in the force word

@@ -510,7 +510,7 @@ int alloc_particles(sedi_handle* h, int64_t N, double rmax) {
     if ((rc = dmalloc(h, h->part_allocs, (void**)&st.cmask[b], 4 * N))) return rc;
   }
   if (form != FORM_FP64 && !h->is_bed && cap * N / 2 + 1 < ((int64_t)1 << 31)) {
-    // pair list (substep variant SUBSTEP_PAIRS; not for ensemble beds, which the
+    // pair list (substep variants SUBSTEP_PAIRS*; not for ensemble beds, which the
     // ensemble steps with the per-particle loop): every listed pair once, cap N / 2 at
     // most (pair ids share a word with the first-particle bit, so fewer than 2^31)
     st.pcap = cap * N / 2 + 1;
@@ -946,7 +946,7 @@ int autotune(sedi_handle* h) {
   }
   if (best.variant != h->variant) clear_graphs(h);  // graphs bake in the launch shape
   // leaving the pair mode: the other variants read the partner copies of the springs
-  if (h->variant == SUBSTEP_PAIRS && best.variant != SUBSTEP_PAIRS) launch_spring_sync(h->form, h->st, h->stream);
+  if (pair_variant(h->variant) && !pair_variant(best.variant)) launch_spring_sync(h->form, h->st, h->stream);
   h->variant = best.variant;
   h->tuned_key = key;
   return 0;

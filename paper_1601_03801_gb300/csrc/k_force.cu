@@ -283,16 +283,27 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
 // order (one 32-byte sector per pair, so the writes are sequential and whole):
 // {F, delta/2} {G, flags} with F the pair force on the first particle, G = n x F_t,
 // and zero flags for a pair that does not interact.  The spring goes to the first
-// particle's slot.  The pairs run independently, so the grid-stride order does not
-// change any result.  Integrating substeps only: the force export runs the
-// per-particle loop, which keeps contact and lubrication apart.
-template <int FORM>
+// particle's slot.  The pairs run independently, so the order in which they are
+// taken does not change any result.  Integrating substeps only: the force export
+// runs the per-particle loop, which keeps contact and lubrication apart.
+//
+// Two schedules.  Grid-stride (ORDERED false): thread t of a fixed grid takes pairs
+// t, t + T, t + 2T, ...; with more blocks than fit on the GPU at once, each wave of
+// resident blocks sweeps the whole list, so a particle's records are fetched again by
+// every wave that reaches one of its pairs.  Ordered (ORDERED true): one wave of
+// blocks takes blockDim.x consecutive pairs at a time from a counter (the next chunk
+// claimed while the current one runs), so the pairs in flight are one narrow window
+// of the list and the partners' records read by a pair are mostly still in L2 when
+// the partners' own pairs come up (on the 10M bed: 34% fewer DRAM reads, 6% shorter
+// substep launch; on beds whose lists fit in L2 the claims cost a little instead).
+// The last block to finish resets the counter for the next launch.
+template <int FORM, bool ORDERED>
 __device__ __forceinline__ void pair_forces_body(const DevState& st, const DevParams& P, int sub_off) {
   using S = typename Traits<FORM>::S;
   using F = typename Traits<FORM>::F;
   using NS = Num<S>;
   static_assert(sizeof(F) == 4, "pair records hold FP32 force words");
-  const Ctl* ctl = st.ctl;
+  Ctl* ctl = st.ctl;
   const int sb = (ctl->st + sub_off) & 1;
   const int nl = ctl->nl;
   const int64_t N = st.N;
@@ -302,11 +313,11 @@ __device__ __forceinline__ void pair_forces_body(const DevState& st, const DevPa
   const uint32_t* cmask = st.cmask[nl];
   Quad<S>* hist = (Quad<S>*)st.hist[nl];
   float4* prec = st.prec;
+  const int4* pairs = st.pairs;
   const int64_t M = (int64_t)ctl->npair < st.pcap ? (int64_t)ctl->npair : st.pcap;
   const float fac = P.lubrication ? (1.0f + P.lub_out_f) : 1.0f;
-  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
-       m += (int64_t)gridDim.x * blockDim.x) {
-    const int4 pr = st.pairs[m];
+  auto one = [&](const int64_t m) {
+    const int4 pr = pairs[m];
     const int64_t i = pr.x;
     const Quad<S> Pi = ldq(pos + i);
     const Quad<S> Pv = ldq(pos + pr.z);
@@ -344,12 +355,45 @@ __device__ __forceinline__ void pair_forces_body(const DevState& st, const DevPa
     }
     prec[2 * m] = r0;
     prec[2 * m + 1] = r1;
+  };
+  if constexpr (ORDERED) {
+    // chunk claims, two ahead of use: s_base[it % 3] is this round's chunk,
+    // s_base[(it + 1) % 3] the next one (claimed last round), and thread 0 claims the
+    // one after into the slot every thread finished reading before the last barrier
+    __shared__ int64_t s_base[3];
+    const int64_t chunk = blockDim.x;
+    if (threadIdx.x == 0) {
+      s_base[0] = (int64_t)atomicAdd(&ctl->pair_next, 1u) * chunk;
+      s_base[1] = (int64_t)atomicAdd(&ctl->pair_next, 1u) * chunk;
+    }
+    __syncthreads();
+    for (int it = 0;; ++it) {
+      const int64_t base = s_base[it % 3];
+      if (base >= M) break;  // the same value for the whole block
+      if (threadIdx.x == 0) s_base[(it + 2) % 3] = (int64_t)atomicAdd(&ctl->pair_next, 1u) * chunk;
+      const int64_t m = base + threadIdx.x;
+      if (m < M) one(m);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      // this block's claims are ordered before its completion count; the last block
+      // to finish sees every claim and resets the counter
+      __threadfence();
+      if (atomicAdd(&ctl->pair_done, 1u) == gridDim.x - 1) {
+        atomicExch(&ctl->pair_next, 0u);
+        atomicExch(&ctl->pair_done, 0u);
+      }
+    }
+  } else {
+    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
+         m += (int64_t)gridDim.x * blockDim.x)
+      one(m);
   }
 }
 
-template <int FORM>
+template <int FORM, bool ORDERED>
 __global__ void __launch_bounds__(128, 7) k_pair_forces(DevState st, DevParams P, int sub_off) {
-  pair_forces_body<FORM>(st, P, sub_off);
+  pair_forces_body<FORM, ORDERED>(st, P, sub_off);
 }
 
 // BS threads per block, at least MINB resident blocks per SM (which caps the
@@ -814,21 +858,33 @@ static void launch_bs(const DevState& st, const DevMesh& mesh, const DevParams& 
     k_substep<FORM, false, BS, MINB, COOP, EXT><<<(unsigned)grid, BS, 0, s>>>(st, mesh, P, sub_off, h, 0);
 }
 
-// Pair list: the pair forces (grid-stride over the pairs on a fixed grid, the pair
-// count lives on the device), then the per-particle kernel gathering the records.
+// Pair list: the pair forces (on a fixed grid: the pair count lives on the device),
+// then the per-particle kernel gathering the records.  The ordered schedule runs one
+// wave of blocks (every block resident at once, each claiming chunks until the list
+// is done); the grid-stride schedule up to 32 blocks per SM.
 template <int FORM>
 static void launch_pairs(const DevState& st, const DevMesh& mesh, const DevParams& P, int sub_off,
-                         unsigned long long next, int use_cond, cudaStream_t s) {
+                         bool ordered, unsigned long long next, int use_cond, cudaStream_t s) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int64_t g = (st.pcap + 127) / 128;
-  const int64_t gmax = (int64_t)nsm * 8 * 4;
-  if (g > gmax) g = gmax;
+  if (ordered) {
+    static int per_sm = 0;  // resident blocks of the ordered kernel per SM (one device)
+    if (per_sm <= 0 &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_forces<FORM, true>, 128, 0) != cudaSuccess)
+      per_sm = 1;
+    if (per_sm <= 0) per_sm = 1;
+    g = (int64_t)nsm * per_sm;
+  } else {
+    const int64_t gmax = (int64_t)nsm * 8 * 4;
+    if (g > gmax) g = gmax;
+  }
   if (g < 1) g = 1;
   const int64_t grid = (st.N + 127) / 128;
   const cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)next;
-  k_pair_forces<FORM><<<(unsigned)g, 128, 0, s>>>(st, P, sub_off);
+  if (ordered) k_pair_forces<FORM, true><<<(unsigned)g, 128, 0, s>>>(st, P, sub_off);
+  else k_pair_forces<FORM, false><<<(unsigned)g, 128, 0, s>>>(st, P, sub_off);
   k_substep<FORM, true, 128, 6, false, false, true><<<(unsigned)grid, 128, 0, s>>>(st, mesh, P, sub_off, h, use_cond);
 }
 
@@ -852,9 +908,12 @@ static void launch_one(const DevState& st, const DevMesh& mesh, const DevParams&
       case SUBSTEP_B128_OCC8_LOOP: launch_bs<FORM, 128, 8, false>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
       case SUBSTEP_B64_LOOP: launch_bs<FORM, 64, 12, false>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
       case SUBSTEP_PAIRS:
+      case SUBSTEP_PAIRS_ORDERED:
         // the force export (not integrating) runs the per-particle loop
-        if (st.pairs && integrate) launch_pairs<FORM>(st, mesh, P, sub_off, next, use_cond, s);
-        else launch_bs<FORM, 128, 6, false>(st, mesh, P, sub_off, integrate, next, use_cond, s);
+        if (st.pairs && integrate)
+          launch_pairs<FORM>(st, mesh, P, sub_off, variant == SUBSTEP_PAIRS_ORDERED, next, use_cond, s);
+        else
+          launch_bs<FORM, 128, 6, false>(st, mesh, P, sub_off, integrate, next, use_cond, s);
         return;
       default: launch_bs<FORM, 128, 6, true>(st, mesh, P, sub_off, integrate, next, use_cond, s); return;
     }

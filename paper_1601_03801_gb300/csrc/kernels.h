@@ -11,8 +11,10 @@ namespace sedi {
 // 128/5 at 96), all with the warp-cooperative pair phase; variants 5-7 run the
 // per-particle pair loop at 128/6, 128/8 and 64/12; variant 8 evaluates each listed
 // pair once from a pair list (one thread per pair) and gathers the pair records per
-// particle in slot order (two launches).  The FP64 parity form runs 128/6 with the
-// loop.
+// particle in slot order (two launches); variant 9 is variant 8 with the pairs taken
+// in list order from a work counter (one wave of blocks claiming 128 consecutive
+// pairs at a time) instead of a grid-stride sweep.  The FP64 parity form runs 128/6
+// with the loop.
 enum SubstepVariant {
   SUBSTEP_B128 = 0,
   SUBSTEP_B64 = 1,
@@ -22,9 +24,13 @@ enum SubstepVariant {
   SUBSTEP_B128_LOOP = 5,
   SUBSTEP_B128_OCC8_LOOP = 6,
   SUBSTEP_B64_LOOP = 7,
-  SUBSTEP_PAIRS = 8
+  SUBSTEP_PAIRS = 8,
+  SUBSTEP_PAIRS_ORDERED = 9
 };
-constexpr int kSubstepVariants = 9;
+constexpr int kSubstepVariants = 10;
+inline bool pair_variant(int variant) {
+  return variant == SUBSTEP_PAIRS || variant == SUBSTEP_PAIRS_ORDERED;
+}
 // launch shapes of the batched ensemble substep (every bed with the per-particle pair
 // phase; the pair list is a single-bed mode)
 constexpr int kEnsVariants = 4;

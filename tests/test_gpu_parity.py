@@ -363,7 +363,7 @@ def test_substep_variants_bit_identical(small, form):
     per-particle loop (variant 5).  The plain FP32 form agrees to FP32 rounding."""
     prm, parts = small
     ref = None
-    for variant in range(9):
+    for variant in range(10):
         g = sedi.Sedi(dict(prm, precision_form=form, substep_variant=variant))
         g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
         g.step(40)
@@ -371,7 +371,7 @@ def test_substep_variants_bit_identical(small, form):
         st = g.stats()
         assert st["substep_variant"] == variant
         assert st["substep_block"] == {0: 128, 1: 64, 2: 256, 3: 128, 4: 128, 5: 128, 6: 128,
-                                       7: 64, 8: 128}[variant]
+                                       7: 64, 8: 128, 9: 128}[variant]
         got = (*g.get_particles(), eps, F)
         if ref is None:
             ref = got
@@ -441,7 +441,7 @@ def test_autotuner_chooses_and_caches(small, tmp_path, monkeypatch):
     assert g.stats()["substep_variant"] == -1
     g.step(10)
     st = g.stats()
-    assert 0 <= st["substep_variant"] < 9 and st["substep_block"] in (64, 128, 256)
+    assert 0 <= st["substep_variant"] < 10 and st["substep_block"] in (64, 128, 256)
     assert st["bins_per_cutoff"] in (1, 2) and st["bin_order"] in (0, 1)
     lines = cache.read_text().splitlines()
     assert len(lines) == 1 and f"N={n}|" in lines[0] and '"median_us"' in lines[0]
@@ -611,7 +611,7 @@ def test_momentum_conserved_on_gpu(small):
     assert np.abs(F.sum(0)).max() <= 1e-6 * np.abs(F).sum()
 
 
-@pytest.mark.parametrize("variant,resume_variant", [(-1, -1), (8, 8), (8, 5)])
+@pytest.mark.parametrize("variant,resume_variant", [(-1, -1), (8, 8), (8, 5), (9, 8)])
 def test_checkpoint_resume_bit_identical(small, tmp_path, variant, resume_variant):
     # variant 8 keeps a pair list (rebuilt from the loaded neighbour lists) and each
     # pair's spring in one slot; the checkpoint holds both copies, so another
@@ -690,7 +690,7 @@ def test_errors_are_reported(small):
     with pytest.raises(sedi.SediError):
         sedi.Sedi(dict(prm, restitution=0.0))
     with pytest.raises(sedi.SediError):
-        sedi.Sedi(dict(prm, substep_variant=9))
+        sedi.Sedi(dict(prm, substep_variant=10))
     g = sedi.Sedi(dict(prm, precision_form="split", nbr_capacity=2))
     with pytest.raises(sedi.SediError) as e:
         g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
@@ -735,8 +735,8 @@ def test_full_size_bed_forces_springs_and_lists():
     bit-exact at the start, then both sides run 20 substeps from the same inputs, so
     the comparison carries tangential history -- springs (SPRING_TOL), positions
     (1e-4 d) and the forces at the reached state (1e-5 of the largest force of each
-    kind, springs included), and the same 20 substeps of the per-particle loop give
-    the same bits as the pair list."""
+    kind, springs included), and the same 20 substeps of the per-particle loop and of
+    the ordered pair schedule give the same bits as the pair list."""
     prm, parts, fl = bed_case()
     rng = np.random.default_rng(17)
     n = len(parts["x"])
@@ -759,13 +759,15 @@ def test_full_size_bed_forces_springs_and_lists():
     fg, fo = g.compute_forces(), o.forces()
     for k in ("contact", "lub", "fluid", "torque"):
         assert rel_err(fg[k], fo[k]) <= 1e-5, (k, rel_err(fg[k], fo[k]))
-    loop = sedi.Sedi(dict(prm, precision_form="split", use_graphs=1, substep_variant=5))
-    loop.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
-    loop.set_fluid(U=fl["U"])
-    loop.set_eps(eps)
-    loop.step(20)
-    for a, b in zip(loop.get_particles(), g.get_particles()):
-        assert np.array_equal(a, b)
+    # the per-particle loop and the ordered pair schedule: the same bits
+    for v in (5, 9):
+        loop = sedi.Sedi(dict(prm, precision_form="split", use_graphs=1, substep_variant=v))
+        loop.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+        loop.set_fluid(U=fl["U"])
+        loop.set_eps(eps)
+        loop.step(20)
+        for a, b in zip(loop.get_particles(), g.get_particles()):
+            assert np.array_equal(a, b), v
 
 
 @pytest.mark.skipif(os.environ.get("SEDI_SKIP_LARGE") == "1", reason="large case disabled")
