@@ -70,16 +70,22 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(variant, path):
+def measured_traffic(variant, path, bins=None):
     """DRAM bytes per particle-substep of the pair list's substep launch (pair-force and
     gather kernels) from a committed ncu summary, if it was taken on the current kernel
-    source and launch variant (other launch variants: none committed)."""
+    source, launch variant and bins (bins per cutoff, storage order) (other launch
+    variants: none committed)."""
     if variant not in PAIR_VARIANTS or not os.path.exists(path):
         return None, None
     txt = open(path).read()
     v = re.search(r"substep_variant:\s*(\d+)", txt)
     if not v or int(v.group(1)) != variant:
         return None, None
+    if bins is not None:
+        r = re.search(r"bins_per_cutoff:\s*(\d+)", txt)
+        o = re.search(r"bin_order:\s*(\d+)", txt)
+        if not r or not o or (int(r.group(1)), int(o.group(1))) != tuple(bins):
+            return None, None
     m = re.search(r"dram_bytes_per_particle_substep:\s*([0-9.eE+-]+)", txt)
     k = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
     if not m or not k or k.group(1) != kernel_hash():
@@ -264,7 +270,9 @@ def roofline(prm, n, g, launch_ms, variant, form="split", traffic=TRAFFIC_LARGE)
     alg = algorithmic_bytes(kbar, cbar, C, n, form)
     achieved = alg * n / (launch_ms / 1e3) / 1e9
     peak, peak_kind = peaks()
-    traffic_pp, _ = measured_traffic(variant, traffic) if form == "split" else (None, None)
+    st = g.stats()
+    bins = (st["bins_per_cutoff"], st["bin_order"])
+    traffic_pp, _ = measured_traffic(variant, traffic, bins) if form == "split" else (None, None)
     out = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
            "frac": round(achieved / peak, 4), "peak_source": peak_kind,
            "traffic": None if traffic_pp is None else round(traffic_pp * n),
@@ -281,6 +289,13 @@ def roofline(prm, n, g, launch_ms, variant, form="split", traffic=TRAFFIC_LARGE)
                                    "workload (" + os.path.basename(traffic) + "), times the particles "
                                    "of this launch")
     return out
+
+
+def tuned_launch(st):
+    """The substep launch and bins the autotuner chose (from a handle's stats)."""
+    return {"variant": st["substep_variant"], "block": st["substep_block"],
+            "bins_per_cutoff": st["bins_per_cutoff"], "bin_order": "xz"[st["bin_order"]] + " fastest",
+            "chosen_by": "autotuner"}
 
 
 def launches_per_step(variant, rebuilds, steps, cells):
@@ -357,10 +372,7 @@ def gpu_arm(args):
                 "config": {"workload": WORKLOAD, "particles_per_gpu": n, "substeps_per_step": SUBSTEPS,
                            "mesh_cells": C, "form": "split", "graphs": True,
                            "settle_steps_untimed": args.settle,
-                           "substep_variant": {"variant": variant, "block": st1["substep_block"],
-                                               "bins_per_cutoff": st1["bins_per_cutoff"],
-                                               "bin_order": "xz"[st1["bin_order"]] + " fastest",
-                                               "chosen_by": "autotuner"},
+                           "substep_variant": tuned_launch(st1),
                            "l2": "not flushed: the particle state (~2 GB) is larger than L2",
                            "parallelism": "independent bed per GPU" if world > 1 else "1 GPU"},
                 "phases_ms_per_step": phases, "rebuilds_in_timed_region": int(rebuilds),
@@ -491,6 +503,7 @@ def bed200k_leg(args):
            "ms_per_step": round(float(np.mean(m["ms"])), 4),
            "l2": "flushed (256 MB write) between timed steps, outside the events",
            "phases_ms_per_step": m["phases"],
+           "substep_variant": tuned_launch(g.stats()),
            "roofline": roofline(prm, n, g, m["substep_launch_ms"], g.stats()["substep_variant"],
                                 traffic=TRAFFIC_200K)}
     g.close()
@@ -890,7 +903,8 @@ def kernels_only(args):
     if args.with_cnn:
         extra = dict(use_cnn_guess=1, cnn_scale=(0.6, 1e4, 1e4, 1e4))
     g = sedi.Sedi(dict(prm, precision_form=args.form, use_graphs=int(args.graphs),
-                       substep_variant=args.variant, **extra))
+                       substep_variant=args.variant, bins_per_cutoff=args.bins,
+                       bin_order=args.bin_order, **extra))
     g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
     g.set_fluid(U=fl["U"], DUDt=fl.get("DUDt"))
     if args.with_cnn:
@@ -931,6 +945,10 @@ def main():
                     help="kernels mode: substep launch variant (-1: autotuned)")
     ap.add_argument("--graphs", type=int, default=1,
                     help="kernels mode: 0 launches kernels one by one (profilers see them)")
+    ap.add_argument("--bins", type=int, default=0,
+                    help="kernels mode: bins per list cutoff (0: the library's choice)")
+    ap.add_argument("--bin-order", type=int, default=-1,
+                    help="kernels mode: bin storage order, 0 x fastest, 1 z fastest (-1: the library's choice)")
     args = ap.parse_args()
     if args.mode == "kernels":
         kernels_only(args)
