@@ -46,7 +46,7 @@ WORKLOAD_200K = ("sheared sediment bed: 200,000 lognormal spheres (median 0.5 mm
 # committed ncu summaries holding the DRAM bytes per particle-substep of the pair
 # list's substep launch (k_pair_forces + k_substep<gather>) with the kernel source hash
 TRAFFIC_LARGE = os.path.join(ROOT, "profiles", "traffic_large10M.md")
-TRAFFIC_200K = os.path.join(ROOT, "profiles", "k_pair_forces_gather_bed200k.md")
+TRAFFIC_200K = os.path.join(ROOT, "profiles", "traffic_bed200k.md")
 KERNEL_SOURCES = ["paper_1601_03801_gb300/csrc/k_force.cu", "paper_1601_03801_gb300/csrc/fluid.cuh",
                   "paper_1601_03801_gb300/csrc/common.cuh", "paper_1601_03801_gb300/csrc/dd.cuh"]
 
@@ -73,24 +73,22 @@ def kernel_hash():
 def measured_traffic(variant, path, bins=None):
     """DRAM bytes per particle-substep of the pair list's substep launch (pair-force and
     gather kernels) from a committed ncu summary, if it was taken on the current kernel
-    source, launch variant and bins (bins per cutoff, storage order) (other launch
-    variants: none committed)."""
+    source, for this launch variant and these bins (bins per cutoff, storage order);
+    None for other launch variants (no summary committed)."""
     if variant not in PAIR_VARIANTS or not os.path.exists(path):
         return None, None
     txt = open(path).read()
-    v = re.search(r"substep_variant:\s*(\d+)", txt)
-    if not v or int(v.group(1)) != variant:
-        return None, None
-    if bins is not None:
-        r = re.search(r"bins_per_cutoff:\s*(\d+)", txt)
-        o = re.search(r"bin_order:\s*(\d+)", txt)
-        if not r or not o or (int(r.group(1)), int(o.group(1))) != tuple(bins):
-            return None, None
-    m = re.search(r"dram_bytes_per_particle_substep:\s*([0-9.eE+-]+)", txt)
     k = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
-    if not m or not k or k.group(1) != kernel_hash():
+    if not k or k.group(1) != kernel_hash():
         return None, None
-    return float(m.group(1)), k.group(1)
+    for m in re.finditer(r"traffic: variant=(\d+) bins_per_cutoff=(\d+) bin_order=(\d+) "
+                         r"bytes_per_particle_substep=([0-9.eE+-]+)", txt):
+        if int(m.group(1)) != variant:
+            continue
+        if bins is not None and (int(m.group(2)), int(m.group(3))) != tuple(bins):
+            continue
+        return float(m.group(4)), k.group(1)
+    return None, None
 
 
 def peaks():
@@ -300,12 +298,13 @@ def tuned_launch(st):
 
 def launches_per_step(variant, rebuilds, steps, cells):
     """Kernels of one step: the graph's rebuild check, 20 substeps of one kernel (two
-    with the pair list), 13 per list rebuild taken, then deposition, fixed point ->
-    smoothing word, the smoother (the cluster solver: one launch; the grid solver:
-    barrier reset + cooperative launch) and the outputs."""
+    with the pair list), 16 per list rebuild taken (the split form keeps the pair
+    list -- counts, scan, fill -- whatever the variant), then deposition,
+    fixed point -> smoothing word, the smoother (the cluster solver: one launch; the
+    grid solver: barrier reset + cooperative launch) and the outputs."""
     per_sub = 2 if variant in PAIR_VARIANTS else 1
     per_avg = 4 if cells <= 131072 else 5
-    return steps * (1 + per_sub * SUBSTEPS + per_avg) + 13 * rebuilds
+    return steps * (1 + per_sub * SUBSTEPS + per_avg) + 16 * rebuilds
 
 
 def gpu_arm(args):

@@ -273,6 +273,8 @@ struct DevState {
   // In the pair mode only the first particle's slot holds the pair's spring (see
   // launch_spring_sync).
   int4* pairs;        // [cap N / 2] (i, slot of j in i's list, j, slot of i in j's list)
+  int32_t* pstart;    // [N + 1] first pair of each appending particle (its count before the scan)
+  int32_t* pscan_blk; // tile sums of that scan
   int32_t* pid;       // [cap][N] pair of each list slot | kFirstBit if the owner is first
   float4* prec;       // [cap N / 2][2] the pair records of the current substep
   int64_t pcap;       // capacity of the pair arrays (cap N / 2)

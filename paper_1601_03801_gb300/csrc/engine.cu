@@ -516,7 +516,9 @@ int alloc_particles(sedi_handle* h, int64_t N, double rmax) {
     st.pcap = cap * N / 2 + 1;
     if ((rc = dmalloc(h, h->part_allocs, (void**)&st.pairs, 16 * st.pcap)) ||
         (rc = dmalloc(h, h->part_allocs, (void**)&st.pid, 4 * cap * N)) ||
-        (rc = dmalloc(h, h->part_allocs, (void**)&st.prec, 32 * st.pcap)))
+        (rc = dmalloc(h, h->part_allocs, (void**)&st.prec, 32 * st.pcap)) ||
+        (rc = dmalloc(h, h->part_allocs, (void**)&st.pstart, 4 * (N + 1))) ||
+        (rc = dmalloc(h, h->part_allocs, (void**)&st.pscan_blk, 4 * ((N + 1023) / 1024 + 1))))
       return rc;
     CK(cudaMemset(st.pairs, 0, 16 * st.pcap));
     CK(cudaMemset(st.pid, 0, 4 * cap * N));

@@ -126,15 +126,17 @@ __device__ __forceinline__ int block_excl_scan(int v, int* total) {
   return r;
 }
 
-__device__ __forceinline__ void scan1_body(const DevState& st, int64_t nbins, bool force) {
-  if (skip(st.ctl, force)) return;
+// Exclusive scan of cnt[0, n) into start[0, n] (start[n] = the total) in three
+// launches: tile sums (scan1), the tiles' prefix in one block (scan2), the tile
+// offsets added (scan3).  cnt and start may be the same array.
+__device__ __forceinline__ void scan1_of(const int32_t* cnt, int32_t* start, int32_t* blk, int64_t n) {
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
   int v[kScanItems];
   int s = 0;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     int64_t b = base + k;
-    v[k] = b < nbins ? st.bin_count[b] : 0;
+    v[k] = b < n ? cnt[b] : 0;
     s += v[k];
   }
   int total;
@@ -142,38 +144,51 @@ __device__ __forceinline__ void scan1_body(const DevState& st, int64_t nbins, bo
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     int64_t b = base + k;
-    if (b < nbins) st.bin_start[b] = ex;
+    if (b < n) start[b] = ex;
     ex += v[k];
   }
-  if (threadIdx.x == 0) st.scan_blk[blockIdx.x] = total;
+  if (threadIdx.x == 0) blk[blockIdx.x] = total;
 }
 
-__device__ __forceinline__ void scan2_body(const DevState& st, int64_t nblk, int64_t nbins, bool force) {
-  if (skip(st.ctl, force)) return;
+__device__ __forceinline__ void scan2_of(int32_t* blk, int64_t nblk, int32_t* start, int64_t n) {
   __shared__ int carry;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   for (int64_t base = 0; base < nblk; base += blockDim.x) {
     int64_t b = base + threadIdx.x;
-    int v = b < nblk ? st.scan_blk[b] : 0;
+    int v = b < nblk ? blk[b] : 0;
     int total;
     int ex = block_excl_scan(v, &total);
-    if (b < nblk) st.scan_blk[b] = ex + carry;
+    if (b < nblk) blk[b] = ex + carry;
     __syncthreads();
     if (threadIdx.x == 0) carry += total;
     __syncthreads();
   }
-  if (threadIdx.x == 0) st.bin_start[nbins] = carry;
+  if (threadIdx.x == 0) start[n] = carry;
+}
+
+__device__ __forceinline__ void scan3_of(int32_t* start, const int32_t* blk, int64_t n) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  const int add = blk[blockIdx.x];
+  for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
+    int64_t b = base + k;
+    if (b < n) start[b] += add;
+  }
+}
+
+__device__ __forceinline__ void scan1_body(const DevState& st, int64_t nbins, bool force) {
+  if (skip(st.ctl, force)) return;
+  scan1_of(st.bin_count, st.bin_start, st.scan_blk, nbins);
+}
+
+__device__ __forceinline__ void scan2_body(const DevState& st, int64_t nblk, int64_t nbins, bool force) {
+  if (skip(st.ctl, force)) return;
+  scan2_of(st.scan_blk, nblk, st.bin_start, nbins);
 }
 
 __device__ __forceinline__ void scan3_body(const DevState& st, int64_t nbins, bool force) {
   if (skip(st.ctl, force)) return;
-  const int64_t base = (int64_t)blockIdx.x * kScanTile;
-  const int add = st.scan_blk[blockIdx.x];
-  for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
-    int64_t b = base + k;
-    if (b < nbins) st.bin_start[b] += add;
-  }
+  scan3_of(st.bin_start, st.scan_blk, nbins);
 }
 
 __device__ __forceinline__ void scatter_body(const DevState& st, bool force) {
@@ -438,38 +453,44 @@ __device__ __forceinline__ void flip_body(const DevState& st, bool force) {
 // contiguously, one atomic per warp), each stored from the particle that comes first
 // in it (list bit) with the pair's slot in both lists; both slots record the pair id.  The order of the pairs in the
 // list depends on scheduling; nothing computed from a pair does.
-__device__ __forceinline__ void pair_fill_body(const DevState& st, bool force, bool current) {
+// The pairs a particle appends to the pair list: those with a partner of higher
+// storage index, so each particle's pairs sit next to those of its neighbours in the
+// (cell-sorted) order.  Their count per particle (pair_count), scanned into each
+// particle's first pair, then the pairs themselves (pair_fill): the list is in
+// storage order of the appending particle, the same for every run.
+__device__ __forceinline__ uint32_t own_pairs(const int32_t* nbr, int ni, int64_t i, int64_t N) {
+  uint32_t own = 0;
+  for (int k = 0; k < ni; ++k)
+    if (nbr_index(nbr[(int64_t)k * N + i]) > (int32_t)i) own |= 1u << k;
+  return own;
+}
+
+__device__ __forceinline__ void pair_count_body(const DevState& st, bool force, bool current) {
   if (skip(st.ctl, force)) return;
   const int ql = current ? st.ctl->nl : st.ctl->nl ^ 1;  // the new lists, or the current ones
   const int64_t N = st.N;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    st.pstart[i] = __popc(own_pairs(st.nbr[ql], st.nn[ql][i], i, N));
+}
+
+__device__ __forceinline__ void pair_fill_body(const DevState& st, bool force, bool current) {
+  if (skip(st.ctl, force)) return;
+  const int ql = current ? st.ctl->nl : st.ctl->nl ^ 1;
+  const int64_t N = st.N;
   const int32_t* nbr = st.nbr[ql];
   const int32_t* nn = st.nn[ql];
-  const int lane = threadIdx.x & 31;
-  // whole warps iterate together (the shuffles below need every lane)
-  const int64_t n_pad = (N + 31) & ~(int64_t)31;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const bool valid = i < N;
-    const int ni = valid ? nn[i] : 0;
-    // the pairs this particle appends: those with a partner of higher index, so each
-    // particle's pairs sit next to those of its neighbours in the (cell-sorted) order
-    uint32_t own = 0, first = 0;
-    for (int k = 0; k < ni; ++k) {
-      const int32_t e = nbr[(int64_t)k * N + i];
-      if (nbr_first(e)) first |= 1u << k;
-      if (nbr_index(e) > (int32_t)i) own |= 1u << k;
-    }
-    const int cnt = __popc(own);
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    uint32_t base = 0;
-    if (lane == 31) base = atomicAdd(&st.ctl->npair, (uint32_t)incl);
-    base = __shfl_sync(0xffffffffu, base, 31);
-    uint32_t m = base + (uint32_t)(incl - cnt);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // every listed pair once; more than the arrays hold is an internal error
+    const int64_t total = st.pstart[N];
+    if (total > st.pcap) atomicCAS(&st.ctl->error, 0, -9);
+    st.ctl->npair = (uint32_t)(total < st.pcap ? total : st.pcap);
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int ni = nn[i];
+    uint32_t own = own_pairs(nbr, ni, i, N), first = 0;
+    for (int k = 0; k < ni; ++k)
+      if (nbr_first(nbr[(int64_t)k * N + i])) first |= 1u << k;
+    int64_t m = st.pstart[i];
     while (own) {
       const int k = __ffs(own) - 1;
       own &= own - 1;
@@ -486,10 +507,7 @@ __device__ __forceinline__ void pair_fill_body(const DevState& st, bool force, b
         atomicCAS(&st.ctl->error, 0, -9);
         k2 = 0;
       }
-      if ((int64_t)m >= st.pcap) {
-        atomicCAS(&st.ctl->error, 0, -9);
-        break;
-      }
+      if (m >= st.pcap) break;  // reported above
       // the pair from the particle that comes first in it; each slot's pair id
       const bool i_first = (first >> k) & 1u;
       st.pairs[m] = i_first ? make_int4((int)i, k, j, k2) : make_int4(j, k2, (int)i, k);
@@ -527,12 +545,20 @@ __global__ void k_build(DevState st, DevParams P, int sub_off, bool force) {
 template <int FORM>
 __global__ void k_remap(DevState st, DevParams P, bool force) { remap_body<FORM>(st, P, force); }
 __global__ void k_flip(DevState st, bool force) { flip_body(st, force); }
-__global__ void k_pair_reset(DevState st, bool force) {
-  if (!skip(st.ctl, force)) st.ctl->npair = 0u;
+__global__ void k_pair_count(DevState st, bool force, bool current) { pair_count_body(st, force, current); }
+__global__ void k_pscan1(DevState st, bool force) {
+  if (!skip(st.ctl, force)) scan1_of(st.pstart, st.pstart, st.pscan_blk, st.N);
+}
+__global__ void k_pscan2(DevState st, int64_t nblk, bool force) {
+  if (!skip(st.ctl, force)) scan2_of(st.pscan_blk, nblk, st.pstart, st.N);
+}
+__global__ void k_pscan3(DevState st, bool force) {
+  if (!skip(st.ctl, force)) scan3_of(st.pstart, st.pscan_blk, st.N);
 }
 __global__ void k_pair_fill(DevState st, bool force, bool current) {
   pair_fill_body(st, force, current);
 }
+
 
 // Pair mode keeps a pair's spring in the first particle's slot only; this copies it
 // to the partner's slot, as the per-particle loop keeps it (before the lists are
@@ -666,6 +692,18 @@ inline unsigned grid_for(int64_t n, int block) {
   return (unsigned)g;
 }
 
+// The pair list of the new lists (current = false: in a rebuild, before the flip) or
+// of the current ones: counts, their scan, the pairs.
+static void launch_pair_fill(const DevState& st, bool force, bool current, cudaStream_t s) {
+  const int B = 256;
+  const int64_t nblk = (st.N + kScanTile - 1) / kScanTile;
+  k_pair_count<<<grid_for(st.N, B), B, 0, s>>>(st, force, current);
+  k_pscan1<<<(unsigned)nblk, kScanThreads, 0, s>>>(st, force);
+  k_pscan2<<<1, 1024, 0, s>>>(st, nblk, force);
+  k_pscan3<<<(unsigned)nblk, kScanThreads, 0, s>>>(st, force);
+  k_pair_fill<<<grid_for(st.N, B), B, 0, s>>>(st, force, current);
+}
+
 template <int FORM>
 void rebuild_impl(const DevState& st, const DevParams& P, int sub_off, bool force, cudaStream_t s) {
   const int B = 256;
@@ -681,10 +719,7 @@ void rebuild_impl(const DevState& st, const DevParams& P, int sub_off, bool forc
   k_gather<FORM><<<grid_for(st.N, B), B, 0, s>>>(st, sub_off, false);
   k_build<FORM><<<grid_for(st.N, 128), 128, 0, s>>>(st, P, sub_off, false);
   k_remap<FORM><<<grid_for(st.N, B), B, 0, s>>>(st, P, force);
-  if (st.pairs) {
-    k_pair_reset<<<1, 1, 0, s>>>(st, false);
-    k_pair_fill<<<grid_for(st.N, B), B, 0, s>>>(st, false, false);
-  }
+  if (st.pairs) launch_pair_fill(st, false, false, s);
   k_flip<<<1, 1, 0, s>>>(st, false);
 }
 
@@ -730,9 +765,7 @@ void launch_rebuild_now(int form, const DevState& st, const DevParams& P, cudaSt
 }
 
 void launch_pair_list(const DevState& st, const DevParams& P, cudaStream_t s) {
-  if (!st.pairs) return;
-  k_pair_reset<<<1, 1, 0, s>>>(st, true);
-  k_pair_fill<<<grid_for(st.N, 256), 256, 0, s>>>(st, true, true);
+  if (st.pairs) launch_pair_fill(st, true, true, s);
 }
 
 void launch_spring_sync(int form, const DevState& st, cudaStream_t s) {

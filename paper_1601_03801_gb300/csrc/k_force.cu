@@ -297,65 +297,99 @@ __device__ __forceinline__ PairOut<typename Traits<FORM>::F> pair_eval(
 // the partners' own pairs come up (on the 10M bed: 34% fewer DRAM reads, 6% shorter
 // substep launch; on beds whose lists fit in L2 the claims cost a little instead).
 // The last block to finish resets the counter for the next launch.
-template <int FORM, bool ORDERED>
-__device__ __forceinline__ void pair_forces_body(const DevState& st, const DevParams& P, int sub_off) {
+// The arrays of one pair pass (the pair kernel's views of the current substep).
+template <int FORM>
+struct PairPass {
+  using S = typename Traits<FORM>::S;
+  const Quad<S>* pos;
+  const Quad<S>* vel;
+  const Quad<S>* omg;
+  const uint32_t* cmask;
+  Quad<S>* hist;
+  float4* prec;
+  const int4* pairs;
+  int64_t N, M;  // particles; listed pairs
+  float fac;     // the FP32 cull's cutoff factor (lubrication range)
+};
+
+template <int FORM>
+__device__ __forceinline__ PairPass<FORM> pair_pass(const DevState& st, const DevParams& P, int sub_off) {
+  using S = typename Traits<FORM>::S;
+  const Ctl* ctl = st.ctl;
+  const int sb = (ctl->st + sub_off) & 1;
+  const int nl = ctl->nl;
+  PairPass<FORM> pp;
+  pp.pos = (const Quad<S>*)st.pos[sb];
+  pp.vel = (const Quad<S>*)st.vel[sb];
+  pp.omg = (const Quad<S>*)st.omg[sb];
+  pp.cmask = st.cmask[nl];
+  pp.hist = (Quad<S>*)st.hist[nl];
+  pp.prec = st.prec;
+  pp.pairs = st.pairs;
+  pp.N = st.N;
+  pp.M = (int64_t)ctl->npair < st.pcap ? (int64_t)ctl->npair : st.pcap;
+  pp.fac = P.lubrication ? (1.0f + P.lub_out_f) : 1.0f;
+  return pp;
+}
+
+// Listed pair m: its record (and the first particle's spring).
+template <int FORM>
+__device__ __forceinline__ void pair_record(const PairPass<FORM>& pp, const DevParams& P, const int64_t m) {
   using S = typename Traits<FORM>::S;
   using F = typename Traits<FORM>::F;
   using NS = Num<S>;
   static_assert(sizeof(F) == 4, "pair records hold FP32 force words");
-  Ctl* ctl = st.ctl;
-  const int sb = (ctl->st + sub_off) & 1;
-  const int nl = ctl->nl;
-  const int64_t N = st.N;
-  const Quad<S>* pos = (const Quad<S>*)st.pos[sb];
-  const Quad<S>* vel = (const Quad<S>*)st.vel[sb];
-  const Quad<S>* omg = (const Quad<S>*)st.omg[sb];
-  const uint32_t* cmask = st.cmask[nl];
-  Quad<S>* hist = (Quad<S>*)st.hist[nl];
-  float4* prec = st.prec;
-  const int4* pairs = st.pairs;
-  const int64_t M = (int64_t)ctl->npair < st.pcap ? (int64_t)ctl->npair : st.pcap;
-  const float fac = P.lubrication ? (1.0f + P.lub_out_f) : 1.0f;
-  auto one = [&](const int64_t m) {
-    const int4 pr = pairs[m];
-    const int64_t i = pr.x;
-    const Quad<S> Pi = ldq(pos + i);
-    const Quad<S> Pv = ldq(pos + pr.z);
-    const uint32_t cm = cmask[i];
-    // the records an interacting pair reads next, fetched with the positions
-    prefetch_l1(vel + i);
-    prefetch_l1(omg + i);
-    prefetch_l1(vel + pr.z);
-    prefetch_l1(omg + pr.z);
-    float dx = (float)NS::dif(Pv.a, Pi.a), dy = (float)NS::dif(Pv.b, Pi.b), dz = (float)NS::dif(Pv.c, Pi.c);
-    if (P.periodic[0]) dx = dx > P.cf.halfL[0] ? dx - P.cf.L[0] : (dx < -P.cf.halfL[0] ? dx + P.cf.L[0] : dx);
-    if (P.periodic[1]) dy = dy > P.cf.halfL[1] ? dy - P.cf.L[1] : (dy < -P.cf.halfL[1] ? dy + P.cf.L[1] : dy);
-    if (P.periodic[2]) dz = dz > P.cf.halfL[2] ? dz - P.cf.L[2] : (dz < -P.cf.halfL[2] ? dz + P.cf.L[2] : dz);
-    const float cut = ((float)NS::f(Pi.d) + (float)NS::f(Pv.d)) * fac;
-    float4 r0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), r1 = r0;
-    if (dx * dx + dy * dy + dz * dz <= cut * cut * 1.0002f) {
-      const int k = pr.y;
-      const bool has = (cm >> k) & 1u;
-      if (has) prefetch_l1(hist + (int64_t)k * N + i);
-      const Quad<S> Vi = ldq(vel + i), Wi = ldq(omg + i);
-      const F vi[3] = {NS::f(Vi.a), NS::f(Vi.b), NS::f(Vi.c)};
-      const F vil[3] = {NS::lo(Vi.a), NS::lo(Vi.b), NS::lo(Vi.c)};
-      const F wi[3] = {NS::f(Wi.a), NS::f(Wi.b), NS::f(Wi.c)};
-      // the first particle of a listed pair is pr.x, so its list entry is the partner
-      // with the first bit set
-      const PairOut<F> o = pair_eval<FORM, true, false>(
-          P, Pi, vi, vil, wi, NS::f(Vi.d), (int32_t)((uint32_t)pr.z | kFirstBit), k, has, i, N, pos,
-          vel, omg, hist);
-      const uint32_t fg = (o.contact || o.lub ? kSlotForce : 0u) | (o.contact ? kSlotContact : 0u);
-      if (fg) {
-        const V3<F> f = pair_total(o);
-        r0 = make_float4(f.x, f.y, f.z, o.hd);
-        r1 = make_float4(o.G.x, o.G.y, o.G.z, __uint_as_float(fg));
-      }
+  const Quad<S>* pos = pp.pos;
+  const Quad<S>* vel = pp.vel;
+  const Quad<S>* omg = pp.omg;
+  Quad<S>* hist = pp.hist;
+  const int64_t N = pp.N;
+  const float fac = pp.fac;
+  const int4 pr = pp.pairs[m];
+  const int64_t i = pr.x;
+  const Quad<S> Pi = ldq(pos + i);
+  const Quad<S> Pv = ldq(pos + pr.z);
+  const uint32_t cm = pp.cmask[i];
+  // the records an interacting pair reads next, fetched with the positions
+  prefetch_l1(vel + i);
+  prefetch_l1(omg + i);
+  prefetch_l1(vel + pr.z);
+  prefetch_l1(omg + pr.z);
+  float dx = (float)NS::dif(Pv.a, Pi.a), dy = (float)NS::dif(Pv.b, Pi.b), dz = (float)NS::dif(Pv.c, Pi.c);
+  if (P.periodic[0]) dx = dx > P.cf.halfL[0] ? dx - P.cf.L[0] : (dx < -P.cf.halfL[0] ? dx + P.cf.L[0] : dx);
+  if (P.periodic[1]) dy = dy > P.cf.halfL[1] ? dy - P.cf.L[1] : (dy < -P.cf.halfL[1] ? dy + P.cf.L[1] : dy);
+  if (P.periodic[2]) dz = dz > P.cf.halfL[2] ? dz - P.cf.L[2] : (dz < -P.cf.halfL[2] ? dz + P.cf.L[2] : dz);
+  const float cut = ((float)NS::f(Pi.d) + (float)NS::f(Pv.d)) * fac;
+  float4 r0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), r1 = r0;
+  if (dx * dx + dy * dy + dz * dz <= cut * cut * 1.0002f) {
+    const int k = pr.y;
+    const bool has = (cm >> k) & 1u;
+    if (has) prefetch_l1(hist + (int64_t)k * N + i);
+    const Quad<S> Vi = ldq(vel + i), Wi = ldq(omg + i);
+    const F vi[3] = {NS::f(Vi.a), NS::f(Vi.b), NS::f(Vi.c)};
+    const F vil[3] = {NS::lo(Vi.a), NS::lo(Vi.b), NS::lo(Vi.c)};
+    const F wi[3] = {NS::f(Wi.a), NS::f(Wi.b), NS::f(Wi.c)};
+    // the first particle of a listed pair is pr.x, so its list entry is the partner
+    // with the first bit set
+    const PairOut<F> o = pair_eval<FORM, true, false>(
+        P, Pi, vi, vil, wi, NS::f(Vi.d), (int32_t)((uint32_t)pr.z | kFirstBit), k, has, i, N, pos,
+        vel, omg, hist);
+    const uint32_t fg = (o.contact || o.lub ? kSlotForce : 0u) | (o.contact ? kSlotContact : 0u);
+    if (fg) {
+      const V3<F> f = pair_total(o);
+      r0 = make_float4(f.x, f.y, f.z, o.hd);
+      r1 = make_float4(o.G.x, o.G.y, o.G.z, __uint_as_float(fg));
     }
-    prec[2 * m] = r0;
-    prec[2 * m + 1] = r1;
-  };
+  }
+  pp.prec[2 * m] = r0;
+  pp.prec[2 * m + 1] = r1;
+}
+
+template <int FORM, bool ORDERED>
+__device__ __forceinline__ void pair_forces_body(const DevState& st, const DevParams& P, int sub_off) {
+  Ctl* ctl = st.ctl;
+  const PairPass<FORM> pp = pair_pass<FORM>(st, P, sub_off);
+  const int64_t M = pp.M;
   if constexpr (ORDERED) {
     // chunk claims, two ahead of use: s_base[it % 3] is this round's chunk,
     // s_base[(it + 1) % 3] the next one (claimed last round), and thread 0 claims the
@@ -372,7 +406,7 @@ __device__ __forceinline__ void pair_forces_body(const DevState& st, const DevPa
       if (base >= M) break;  // the same value for the whole block
       if (threadIdx.x == 0) s_base[(it + 2) % 3] = (int64_t)atomicAdd(&ctl->pair_next, 1u) * chunk;
       const int64_t m = base + threadIdx.x;
-      if (m < M) one(m);
+      if (m < M) pair_record<FORM>(pp, P, m);
       __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -387,7 +421,7 @@ __device__ __forceinline__ void pair_forces_body(const DevState& st, const DevPa
   } else {
     for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
          m += (int64_t)gridDim.x * blockDim.x)
-      one(m);
+      pair_record<FORM>(pp, P, m);
   }
 }
 
