@@ -673,6 +673,32 @@ def test_single_particle_and_boundaries():
         assert np.abs(min_image(g.get_particles()[0] - o.get_particles()[0], prm)).max() < 1e-9
 
 
+def test_pair_list_without_pairs():
+    """Spheres too far apart to be listed together: the pair list is empty, every
+    block of the ordered pair schedule finds its first claim past the end (and the last
+    resets the counter for the next launch); both pair-list variants give the bits of
+    the per-particle loop, and the oracle's trajectory."""
+    prm = default_params()
+    g1 = np.stack(np.meshgrid([5e-3, 15e-3], [5e-3, 15e-3], [10e-3, 20e-3], indexing="ij"), -1).reshape(-1, 3)
+    n = len(g1)
+    parts = dict(x=g1, v=np.zeros((n, 3)), w=np.zeros((n, 3)), d=np.full(n, 1e-3), rho=np.full(n, 2500.0))
+    out = []
+    for v in (5, 8, 9):
+        g = sedi.Sedi(dict(prm, precision_form="split", substep_variant=v))
+        g.set_particles(parts["x"], parts["v"], parts["w"], parts["d"], parts["rho"])
+        for _ in range(3):
+            g.step(20)
+        assert g.contacts()[0].shape[0] == 0
+        out.append(g.get_particles())
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            assert np.array_equal(a, b)
+    o = orc.Oracle(prm, threads=1)
+    o.set_particles(*(storage_round(parts[k], "split") for k in ("x", "v", "w")), parts["d"], parts["rho"])
+    o.step(60)
+    assert np.abs(min_image(out[0][0] - o.get_particles()[0], prm)).max() <= 1e-4 * 1e-3
+
+
 def test_profile_timings_in_graphs(small):
     prm, parts = small
     g = sedi.Sedi(dict(prm, precision_form="split", profile=1))
